@@ -1,0 +1,88 @@
+"""Pins of the oracle's P-ERK2 construction: the paper's printed coefficients,
+order conditions, internal consistency and the stability polynomial."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.perk import (disk_polynomial_alpha, perk2_family, perk2_free_coefficients, stability_polynomial)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "perk2_S16_E8_E16.txt")
+
+
+def load_golden():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        i, c, a8, a16 = line.split()
+        num, den = c.split("/")
+        rows.append((int(i), float(num) / float(den), float(a8), float(a16)))
+    return rows
+
+
+def test_printed_table_reproduced():
+    fam = perk2_family([8, 16])
+    a8_free = perk2_free_coefficients(16, 8, disk_polynomial_alpha(8))
+    a16_free = perk2_free_coefficients(16, 16, disk_polynomial_alpha(16))
+    rows = load_golden()
+    assert len(rows) == 16
+    for (i, c, a8, a16) in rows:
+        assert abs(fam.c[i - 1] - c) < 1e-16
+        # the printed digits carry the paper's own last-bit rounding: allow a few ulp
+        assert abs(a8_free[i] - a8) <= 1e-15 * a8
+        assert abs(a16_free[i] - a16) <= 1e-15 * a16
+        if i >= 3:
+            # the dense arrays carry the same entries below the diagonal ...
+            assert fam.A[0][i - 1, i - 2] == a8_free[i] and fam.A[1][i - 1, i - 2] == a16_free[i]
+        if i >= 2:
+            # ... and a_{i,1} = c_i - a_{i,i-1}
+            assert abs(fam.A[1][i - 1, 0] + (a16_free[i] if i >= 3 else 0.0) - c) < 1e-16
+
+
+@pytest.mark.parametrize("E_list", [[8, 16], [4, 8], [4, 6, 10, 16], [2, 3], [5]])
+def test_order_conditions_and_consistency(E_list):
+    fam = perk2_family(E_list)
+    ones = np.ones(fam.S)
+    assert abs(fam.b @ ones - 1.0) < 1e-15                  # p = 1
+    assert abs(fam.b @ fam.c - 0.5) < 1e-15                 # p = 2
+    for A in fam.A:
+        np.testing.assert_allclose(A @ ones, fam.c, atol=1e-15)   # internal consistency
+        assert np.all(np.triu(A) == 0.0)                     # explicit
+        # only K_1 and K_{i-1} enter stage i
+        for i in range(fam.S):
+            nz = np.nonzero(A[i])[0]
+            assert set(nz.tolist()) <= {0, i - 1}
+
+
+@pytest.mark.parametrize("E", [2, 3, 4, 6, 8, 10, 16])
+@pytest.mark.parametrize("S_extra", [0, 3])
+def test_stability_polynomial_matches_alpha(E, S_extra):
+    S = E + S_extra
+    fam = perk2_family([E], S=S)
+    P = stability_polynomial(fam.A[0], fam.b)
+    alpha = disk_polynomial_alpha(E)
+    np.testing.assert_allclose(P[:E + 1], alpha, rtol=1e-13, atol=1e-17)
+    assert np.all(np.abs(P[E + 1:]) < 1e-17)                 # degree E exactly: E evaluations
+
+
+@pytest.mark.parametrize("E", [3, 4, 8, 16])
+def test_disk_polynomial_stability_and_radius(E):
+    alpha = disk_polynomial_alpha(E)
+    r = E - 1.0
+    th = np.linspace(0, 2 * np.pi, 721)
+    z = -r + r * np.exp(1j * th)
+    # the monomial form loses ~1e-10 to cancellation at |z| ~ 2(E-1), hence the tolerance
+    assert np.max(np.abs(np.polyval(alpha[::-1], z))) <= 1.0 + 1e-8
+    # the second-order consistency of the closed form
+    assert alpha[0] == pytest.approx(1.0, abs=1e-15)
+    assert alpha[1] == pytest.approx(1.0, abs=1e-15)
+    assert alpha[2] == pytest.approx(0.5, abs=1e-15)
+    # a slightly larger disk leaves the stability region
+    zz = -1.02 * r + 1.02 * r * np.exp(1j * th)
+    assert np.max(np.abs(np.polyval(alpha[::-1], zz))) > 1.0 + 1e-3
+
+
+def test_free_coefficients_are_zero_before_first_shared_stage():
+    a = perk2_free_coefficients(16, 8, disk_polynomial_alpha(8))
+    assert np.all(a[:11] == 0.0) and np.all(a[11:] > 0.0)
