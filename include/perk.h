@@ -1,0 +1,169 @@
+/*
+ * libperk — P-ERK multirate time stepping of a quadtree DGSEM on one GB300.
+ *
+ * C ABI of the library.  The method is the Paired-Explicit Runge-Kutta (P-ERK)
+ * scheme applied to the partitioned ODE of a DGSEM semidiscretisation whose
+ * partitions are the refinement levels of an adaptively refined quadtree
+ * (Doehring et al., arXiv 2403.05144: Sec. 2, Eq. PartitionedODESys and
+ * Eq. PartitionedRKSystem; Sec. 3.1, Eq. PERK_ButcherTableauClassic; Sec. 6.2).
+ *
+ * Conventions shared by every call
+ *   - Solution and stage arrays are FP64, device memory owned by the caller,
+ *     laid out U[n_elem][4][n][n] in C order with n = N+1 = 4: conserved
+ *     variable (rho, rho v1, rho v2, E), then the node index j along y, then
+ *     the node index i along x.  Element e is the e-th cell passed to
+ *     perk_mesh_upload.  Pointers are not retained after a call returns.
+ *   - All device work is enqueued on the context's stream (perk_set_stream);
+ *     calls return once the work is enqueued unless stated otherwise.
+ *   - Host arrays are copied during the call.
+ *   - Every call returns a perk_status; no exception crosses the ABI.  On an
+ *     error the context keeps a message readable with perk_last_error().
+ */
+#ifndef PERK_H
+#define PERK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PERK_OK = 0,
+  PERK_E_INVALID_ARG = 1, /* bad pointer, size, level, or an unbalanced / non-periodic mesh */
+  PERK_E_CUDA = 2,        /* a CUDA runtime call failed; the message names it */
+  PERK_E_NONFINITE = 3,   /* a step produced NaN/Inf or non-positive density or pressure;
+                             the step was not committed and U is unchanged */
+  PERK_E_TIMEOUT = 4,     /* a bounded device wait expired */
+  PERK_E_NOT_READY = 5,   /* mesh or tableau missing */
+  PERK_E_OOM = 6          /* device allocation failed */
+} perk_status;
+
+typedef enum { PERK_SURFACE_HLL = 0, PERK_SURFACE_HLLC = 1, PERK_SURFACE_EC = 2 } perk_surface_flux;
+
+typedef struct perk_ctx perk_ctx;
+
+/* Problem description.  Only the compressible Euler equations with N = 3
+ * (4 x 4 Gauss-Lobatto nodes per quadrilateral) are built. */
+typedef struct {
+  int N;                 /* polynomial degree; must be 3 */
+  double gamma;          /* ratio of specific heats, > 1 */
+  int surface_flux;      /* perk_surface_flux */
+  int use_graph;         /* nonzero: perk_step replays a captured CUDA graph of the whole step */
+} perk_problem;
+
+/* Creates a context on the current CUDA device.  *out receives the handle. */
+perk_status perk_create(const perk_problem* prob, perk_ctx** out);
+/* Frees the context and every device buffer it owns.  NULL is ignored. */
+void perk_destroy(perk_ctx* ctx);
+/* Message of the last failed call on ctx ("" if none).  Valid until the next call.
+ * With ctx == NULL: the message of the last failed context-free call on this thread. */
+const char* perk_last_error(const perk_ctx* ctx);
+/* Sets the stream (a cudaStream_t cast to void*; NULL = legacy default stream). */
+perk_status perk_set_stream(perk_ctx* ctx, void* stream);
+
+/* Mesh upload (Sec. 6.2, TreeMesh).  cells[3*e + {0,1,2}] = (level, ix, iy) of
+ * leaf e: level 0 is the periodic square [x0, x0+length]^2 and the cell covers
+ * [ix, ix+1) x [iy, iy+1) in units of length / 2^level.  The leaves must tile
+ * the square exactly and be 2:1 balanced across faces (else INVALID_ARG).
+ * Builds interfaces (equal-size faces) and mortars (2:1 hanging faces) on the
+ * host, uploads them, and runs the level partition (perk_partition) if a
+ * tableau is set.  Invalidates any captured step graph. */
+perk_status perk_mesh_upload(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, double x0, double length);
+
+/* Host utility (no device work): the face connectivity perk_mesh_upload would
+ * build for the same cells.  Interfaces: ifs[4*q + {0,1,2,3}] = (left, right,
+ * dir, 0): the +dir face of `left` meets the -dir face of `right` (dir 0 = x,
+ * 1 = y).  Mortars: morts[4*q + {0,1,2,3}] = (large, small_lo, small_hi,
+ * dir | large_side << 1): the large cell's face against the two small cells
+ * (ordered by the tangential coordinate); large_side 0 means the large cell is
+ * on the -dir side.  *n_if and *n_mort receive the counts; the arrays are
+ * filled only if their capacities (in records) suffice. */
+perk_status perk_mesh_faces(int64_t n_cells, const int32_t* cells, int64_t* n_if, int32_t* ifs, int64_t if_cap,
+                            int64_t* n_mort, int32_t* morts, int64_t mort_cap);
+
+typedef struct {
+  int64_t n_elem;
+  int64_t n_interfaces;
+  int64_t n_mortars;
+  int32_t level_min, level_max;
+  int32_t S;                  /* stages of the current tableau (0 if none) */
+  int64_t dof_stage_updates;  /* sum over stages of active nodes, per step */
+  int64_t active_elements[64];/* active elements per stage (first S entries) */
+  int64_t active_interfaces[64];
+  int64_t active_mortars[64];
+  int64_t index_bytes;        /* device bytes of the partition data (method ids and sorted lists) */
+} perk_mesh_info;
+perk_status perk_mesh_query(const perk_ctx* ctx, perk_mesh_info* info);
+
+/* P-ERK coefficient table (Sec. 3.1, Eq. PERK_ButcherTableauClassic; Sec. 4.3).
+ * order: 2 (b = e_S) or 3 (b = 1/6 on K_1 and K_{S-1}, 2/3 on K_S; Eq. PERK_ThirdOrderShuOsher).
+ * S stages (2 <= S <= 64), R members (1 <= R <= 8) with ascending E[r] <= S.
+ * c[i], i = 0..S-1: shared abscissae.  a[r*S + i] = a_{i+1,i}^{(r)} (the
+ * coefficient of K_{i} in stage i+1, 1-based), zero where member r has no such
+ * entry; a_{i,1}^{(r)} = c_i - a_{i,i-1}^{(r)} by internal consistency.
+ * Member r evaluates K_1 and K_{S-E[r]+2} .. K_S.  Runs perk_partition if a
+ * mesh is present.  Invalidates any captured step graph. */
+perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32_t* E, const double* c,
+                             const double* a);
+
+/* Host utility (Sec. 4.3.1, Eq. PERKCoeffsConstruction): fills c[S] and
+ * a[R*S] of a second-order family whose member r has the stability polynomial
+ * P(z) = 1/E + ((E-1)/E)(1 + z/(E-1))^E, E = E[r] (the second-order optimum
+ * for the disk |z + E - 1| <= E - 1). */
+perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a);
+
+/* Level partition on the device (Sec. 6.2): member of every element from its
+ * level (finest present level -> member R-1, next -> R-2, ..., the rest -> 0),
+ * of every interface from its elements, of every mortar from its fine side;
+ * then the element, interface and mortar lists sorted finest-member-first so
+ * that the work active at every stage is a prefix of each list.  Blocks until
+ * the per-stage counts are back on the host.  Normally called implicitly. */
+perk_status perk_partition(perk_ctx* ctx);
+
+/* Host utility: the N+1 Gauss-Lobatto nodes x[] (ascending, on [-1, 1]) and
+ * weights w[] at which the library collocates the solution (only N = 3 is
+ * built for stepping; any 1 <= N <= 16 is returned here).  Node (i, j) of an
+ * element [x_lo, x_lo + h] x [y_lo, y_lo + h] sits at
+ * (x_lo + h (1 + x[i]) / 2, y_lo + h (1 + x[j]) / 2). */
+perk_status perk_reference_nodes(int N, double* x, double* w);
+
+/* Full right-hand side K = F(Y) on every element (no partitioning). */
+perk_status perk_rhs_full(perk_ctx* ctx, const double* d_Y, double* d_K);
+
+/* Partitioned right-hand side of stage `stage` (0-based): K = I^{act} F(Y)
+ * (Sec. 2.2 mask matrices).  Writes K only for elements of members active at
+ * that stage; other elements of d_K are left untouched.  d_Y is the full
+ * stage vector (active and inactive elements). */
+perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double* d_K);
+
+/* One P-ERK step of size dt, in place on d_U (Eq. PartitionedRKSystem).
+ * Stage i forms Y_i element-wise from U_n, K_1 and K_{i-1} with the element's
+ * member coefficients and evaluates F only on the active prefix.  The update
+ * is committed only if every new node state is finite with positive density
+ * and pressure; otherwise U is left unchanged and the context's sticky error
+ * flag is raised (read it with perk_check).  Asynchronous. */
+perk_status perk_step(perk_ctx* ctx, double* d_U, double dt);
+
+/* Synchronises the stream and returns PERK_E_NONFINITE if any step since the
+ * last check was rejected (then clears the flag), else PERK_OK. */
+perk_status perk_check(perk_ctx* ctx);
+
+/* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed
+ * on the device (Eq. CFL_DG, Eq. TimestepConstraint).  Blocks; *dt receives it. */
+perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double* dt);
+
+/* Counters accumulated since creation (reporting, Sec. 6.4.1). */
+typedef struct {
+  int64_t steps;
+  int64_t element_stage_evaluations; /* sum over steps and stages of active elements */
+  int64_t dof_stage_updates;         /* the same in nodes */
+  int64_t rejected_steps_checked;    /* steps found rejected by perk_check */
+} perk_counters;
+perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERK_H */

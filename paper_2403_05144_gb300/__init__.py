@@ -1,0 +1,176 @@
+"""GB300-native P-ERK multirate time stepping of a quadtree DGSEM (Python layer).
+
+``PerkSolver`` is a thin wrapper over libperk's C ABI (include/perk.h):
+PyTorch provides device memory and the stream, every step of the method runs
+in the library's sm_103a kernels.  There is no CPU path: without the built
+library or a CUDA device the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from typing import Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import PerkError
+
+__all__ = ["PerkSolver", "PerkError", "reference_nodes", "perk2_disk_tableau", "mesh_faces"]
+
+
+def _check(lib, ctx, status: int):
+    if status != _lib.PERK_OK:
+        msg = lib.perk_last_error(ctx).decode()
+        raise PerkError(status, msg)
+
+
+def reference_nodes(N: int = 3):
+    """Gauss-Lobatto nodes and weights the library collocates on."""
+    lib = _lib.load()
+    x = (C.c_double * (N + 1))()
+    w = (C.c_double * (N + 1))()
+    _check(lib, None, lib.perk_reference_nodes(N, x, w))
+    return np.array(x[:]), np.array(w[:])
+
+
+def perk2_disk_tableau(E: Sequence[int], S: int | None = None):
+    """(c[S], a[R, S]) of the second-order family with disk-optimal members E (ascending)."""
+    lib = _lib.load()
+    E = [int(e) for e in E]
+    S = int(S or max(E))
+    R = len(E)
+    Ea = (C.c_int32 * R)(*E)
+    c = (C.c_double * S)()
+    a = (C.c_double * (R * S))()
+    _check(lib, None, lib.perk_perk2_disk_tableau(S, R, Ea, c, a))
+    return np.array(c[:]), np.array(a[:]).reshape(R, S)
+
+
+def mesh_faces(cells):
+    """(interfaces [n_if, 4], mortars [n_mort, 4]) the library builds for a leaf list (host only)."""
+    lib = _lib.load()
+    arr = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 3))
+    ni, nm = C.c_int64(), C.c_int64()
+    cp = arr.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(lib, None, lib.perk_mesh_faces(len(arr), cp, C.byref(ni), None, 0, C.byref(nm), None, 0))
+    ifs = np.zeros((ni.value, 4), dtype=np.int32)
+    ms = np.zeros((nm.value, 4), dtype=np.int32)
+    _check(lib, None, lib.perk_mesh_faces(len(arr), cp, C.byref(ni), ifs.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          ni.value, C.byref(nm), ms.ctypes.data_as(C.POINTER(C.c_int32)), nm.value))
+    return ifs, ms
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class PerkSolver:
+    """One libperk context: mesh, partition, coefficient table and stage buffers."""
+
+    def __init__(self, gamma: float = 1.4, surface_flux: str = "hll", use_graph: bool = True, N: int = 3):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("PerkSolver needs a CUDA device")
+        self.torch = torch
+        self.lib = _lib.load()
+        prob = _lib.PerkProblem(N, gamma, _lib.SURFACE[surface_flux], 1 if use_graph else 0)
+        h = C.c_void_p()
+        torch.cuda.init()
+        _check(self.lib, None, self.lib.perk_create(C.byref(prob), C.byref(h)))
+        self.ctx = h
+        self.gamma = gamma
+        self.n_elem = 0
+        self.S = 0
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx:
+            self.lib.perk_destroy(ctx)
+            self.ctx = None
+
+    def _stream(self):
+        s = self.torch.cuda.current_stream().cuda_stream
+        _check(self.lib, self.ctx, self.lib.perk_set_stream(self.ctx, C.c_void_p(s)))
+
+    def _call(self, fn, *args):
+        self._stream()
+        _check(self.lib, self.ctx, fn(self.ctx, *args))
+
+    # ------------------------------------------------------------------ setup
+    def upload_mesh(self, cells, x0: float, length: float):
+        arr = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 3))
+        self._call(self.lib.perk_mesh_upload, C.c_int64(len(arr)), arr.ctypes.data_as(C.POINTER(C.c_int32)),
+                   C.c_double(x0), C.c_double(length))
+        self.n_elem = len(arr)
+        self.x0, self.length = float(x0), float(length)
+        self.cells = arr
+
+    def set_tableau(self, order: int, E: Sequence[int], c, a):
+        E = [int(e) for e in E]
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(len(E), len(c))
+        Ea = (C.c_int32 * len(E))(*E)
+        self._call(self.lib.perk_set_tableau, int(order), len(c), len(E), Ea, c.ctypes.data_as(C.POINTER(C.c_double)),
+                   a.ctypes.data_as(C.POINTER(C.c_double)))
+        self.S = len(c)
+        self.E = E
+
+    def set_perk2_disk(self, E: Sequence[int], S: int | None = None):
+        c, a = perk2_disk_tableau(E, S)
+        self.set_tableau(2, E, c, a)
+        return c, a
+
+    def info(self) -> dict:
+        inf = _lib.PerkMeshInfo()
+        _check(self.lib, self.ctx, self.lib.perk_mesh_query(self.ctx, C.byref(inf)))
+        S = inf.S
+        return {"n_elem": inf.n_elem, "n_interfaces": inf.n_interfaces, "n_mortars": inf.n_mortars,
+                "level_min": inf.level_min, "level_max": inf.level_max, "S": S,
+                "dof_stage_updates": inf.dof_stage_updates, "active_elements": list(inf.active_elements[:S]),
+                "active_interfaces": list(inf.active_interfaces[:S]), "active_mortars": list(inf.active_mortars[:S]),
+                "index_bytes": inf.index_bytes}
+
+    def counters(self) -> dict:
+        c = _lib.PerkCounters()
+        _check(self.lib, self.ctx, self.lib.perk_get_counters(self.ctx, C.byref(c)))
+        return {f: getattr(c, f) for f, _ in c._fields_}
+
+    # -------------------------------------------------------------- compute
+    def _state(self, t):
+        torch = self.torch
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        if tuple(t.shape) != (self.n_elem, 4, 4, 4):
+            raise ValueError(f"expected shape {(self.n_elem, 4, 4, 4)}, got {tuple(t.shape)}")
+        return t
+
+    def empty_state(self):
+        return self.torch.empty((self.n_elem, 4, 4, 4), dtype=self.torch.float64, device="cuda")
+
+    def rhs_full(self, Y, out=None):
+        Y = self._state(Y)
+        K = self.empty_state() if out is None else self._state(out)
+        self._call(self.lib.perk_rhs_full, C.c_void_p(_ptr(Y)), C.c_void_p(_ptr(K)))
+        return K
+
+    def rhs_active(self, stage: int, Y, out=None):
+        Y = self._state(Y)
+        K = self.torch.zeros_like(Y) if out is None else self._state(out)
+        self._call(self.lib.perk_rhs_active, int(stage), C.c_void_p(_ptr(Y)), C.c_void_p(_ptr(K)))
+        return K
+
+    def step(self, U, dt: float):
+        U = self._state(U)
+        self._call(self.lib.perk_step, C.c_void_p(_ptr(U)), C.c_double(dt))
+        return U
+
+    def check(self):
+        self._call(self.lib.perk_check)
+
+    def compute_dt(self, U, cfl: float) -> float:
+        U = self._state(U)
+        out = C.c_double()
+        self._call(self.lib.perk_compute_dt, C.c_void_p(_ptr(U)), C.c_double(cfl), C.byref(out))
+        return out.value

@@ -1,0 +1,771 @@
+// Host runtime of libperk: the C ABI declared in include/perk.h.
+//
+// Owns the reference-element operators, the quadtree connectivity built from a
+// leaf-cell list, the device copies of the mesh and of the level partition,
+// the P-ERK coefficient table and the stage buffers, and drives one P-ERK
+// step as 2S + 1 kernel launches (optionally replayed from a CUDA graph).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "perk.h"
+#include "perk_internal.h"
+
+using namespace perk;
+
+// ---------------------------------------------------------------------------
+// Reference-element operators (N = 3 is the built case; the routines are generic).
+namespace {
+
+double legendre(int n, double x, double* dp) {
+  // P_n(x) and P_n'(x) by the three-term recurrence
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (n == 0) {
+    if (dp) *dp = 0.0;
+    return 1.0;
+  }
+  for (int k = 2; k <= n; ++k) {
+    const double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    const double d2 = d0 + (2 * k - 1) * p1;
+    p0 = p1;
+    p1 = p2;
+    d0 = d1;
+    d1 = d2;
+  }
+  if (dp) *dp = d1;
+  return p1;
+}
+
+// Gauss-Lobatto nodes: end points and the roots of P_N', found by Newton from
+// Chebyshev-Gauss-Lobatto guesses using (1 - x^2) P_N' = N (P_{N-1} - x P_N).
+void lgl(int N, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(N + 1, 0.0);
+  w.assign(N + 1, 0.0);
+  for (int i = 0; i <= N; ++i) {
+    double xi = -std::cos(M_PI * i / N);
+    if (i > 0 && i < N) {
+      for (int it = 0; it < 100; ++it) {
+        // q(x) = P_{N+1} - P_{N-1} vanishes exactly at the interior LGL nodes
+        double dq1, dq0;
+        const double q = legendre(N + 1, xi, &dq1) - legendre(N - 1, xi, &dq0);
+        const double dx = q / (dq1 - dq0);
+        xi -= dx;
+        if (std::fabs(dx) < 1e-17) break;
+      }
+    }
+    x[i] = xi;
+    const double pn = legendre(N, xi, nullptr);
+    w[i] = 2.0 / (N * (N + 1) * pn * pn);
+  }
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double xi = -std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      const double p = legendre(n, xi, &dp);
+      const double dx = p / dp;
+      xi -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    legendre(n, xi, &dp);
+    x[i] = xi;
+    w[i] = 2.0 / ((1.0 - xi * xi) * dp * dp);
+  }
+}
+
+// Barycentric weights and Lagrange basis values l_j(t).
+void lagrange_values(const std::vector<double>& x, double t, double* out) {
+  const int n = (int)x.size();
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) v *= (t - x[k]) / (x[j] - x[k]);
+    out[j] = v;
+  }
+}
+
+bool invert4(const double A[NN][NN], double inv[NN][NN]) {
+  double M[NN][2 * NN];
+  for (int i = 0; i < NN; ++i)
+    for (int j = 0; j < 2 * NN; ++j) M[i][j] = j < NN ? A[i][j] : (j - NN == i ? 1.0 : 0.0);
+  for (int c = 0; c < NN; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < NN; ++r)
+      if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0) return false;
+    for (int j = 0; j < 2 * NN; ++j) std::swap(M[c][j], M[piv][j]);
+    const double d = M[c][c];
+    for (int j = 0; j < 2 * NN; ++j) M[c][j] /= d;
+    for (int r = 0; r < NN; ++r)
+      if (r != c) {
+        const double f = M[r][c];
+        for (int j = 0; j < 2 * NN; ++j) M[r][j] -= f * M[c][j];
+      }
+  }
+  for (int i = 0; i < NN; ++i)
+    for (int j = 0; j < NN; ++j) inv[i][j] = M[i][j + NN];
+  return true;
+}
+
+Ops build_ops(double gamma, int surface_flux) {
+  Ops o{};
+  std::vector<double> x, w;
+  lgl(NN - 1, x, w);
+  // derivative matrix from barycentric weights: D_ij = (lam_j / lam_i) / (x_i - x_j), rows sum to 0
+  double lam[NN];
+  for (int j = 0; j < NN; ++j) {
+    double p = 1.0;
+    for (int k = 0; k < NN; ++k)
+      if (k != j) p *= x[j] - x[k];
+    lam[j] = 1.0 / p;
+  }
+  for (int i = 0; i < NN; ++i)
+    for (int j = 0; j < NN; ++j) o.dsplit[i][j] = (i == j) ? 0.0 : 2.0 * (lam[j] / lam[i]) / (x[i] - x[j]);
+  o.inv_w0 = 1.0 / w[0];
+  // mortar operators: forward interpolation P_h[k][l] = l_l(position of node k of half h)
+  for (int k = 0; k < NN; ++k) {
+    lagrange_values(x, 0.5 * (x[k] - 1.0), o.p_lo[k]);
+    lagrange_values(x, 0.5 * (x[k] + 1.0), o.p_hi[k]);
+  }
+  // exact mass matrix M_lm = int l_l l_m (Gauss-Legendre, NN points: exact to degree 2NN-1)
+  std::vector<double> xg, wg;
+  gauss_legendre(NN, xg, wg);
+  double M[NN][NN] = {}, Mi[NN][NN];
+  for (int g = 0; g < NN; ++g) {
+    double L[NN];
+    lagrange_values(x, xg[g], L);
+    for (int l = 0; l < NN; ++l)
+      for (int m = 0; m < NN; ++m) M[l][m] += wg[g] * L[l] * L[m];
+  }
+  invert4(M, Mi);
+  // reverse (L2 projection) R_h = 1/2 M^{-1} P_h^T M
+  for (int h = 0; h < 2; ++h) {
+    const double(*P)[NN] = h ? o.p_hi : o.p_lo;
+    double PtM[NN][NN] = {};
+    for (int a = 0; a < NN; ++a)
+      for (int b = 0; b < NN; ++b)
+        for (int c = 0; c < NN; ++c) PtM[a][b] += P[c][a] * M[c][b];
+    double(*R)[NN] = h ? o.r_hi : o.r_lo;
+    for (int a = 0; a < NN; ++a)
+      for (int b = 0; b < NN; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < NN; ++c) s += Mi[a][c] * PtM[c][b];
+        R[a][b] = 0.5 * s;
+      }
+  }
+  o.gamma = gamma;
+  o.gm1 = gamma - 1.0;
+  o.inv_gm1 = 1.0 / (gamma - 1.0);
+  o.surface_flux = surface_flux;
+  return o;
+}
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = std::max<size_t>(n, 1);
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct perk_ctx {
+  perk_problem prob{};
+  Ops ops{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::string err;
+
+  // mesh (host)
+  bool has_mesh = false;
+  int64_t n_elem = 0, n_if = 0, n_mort = 0;
+  double x0 = 0.0, length = 1.0;
+  std::vector<int32_t> h_level;
+  std::vector<int4> h_if, h_mort;
+  int32_t lmin = 0, lmax = 0;
+
+  // tableau
+  bool has_tab = false;
+  int order = 2, S = 0, R = 0;
+  int32_t E[MAX_R] = {};
+  std::vector<double> c, a;  // c[S], a[R*S]
+
+  // partition results (host copies)
+  bool partitioned = false;
+  int part_S = 0;
+  int64_t act_el[MAX_S] = {}, act_if[MAX_S] = {}, act_mort[MAX_S] = {};
+
+  // device buffers
+  DevBuf<int32_t> d_level, d_method, d_elem_sorted, d_E, d_minmax;
+  DevBuf<int4> d_if_raw, d_mort_raw, d_if_sorted, d_mort_sorted;
+  DevBuf<int64_t> d_counts;
+  DevBuf<double> d_surf, d_K1, d_Ka, d_Kb, d_dt, d_block_min, d_dt_out;
+  DevBuf<StageCoef> d_coef;
+  DevBuf<int> d_flag;
+
+  // graph of one step
+  cudaGraphExec_t graph = nullptr;
+  double* graph_U = nullptr;
+  double cur_dt = NAN;
+
+  perk_counters counters{};
+};
+
+namespace {
+
+thread_local std::string g_err;  // message of the last failed context-free call on this thread
+
+perk_status fail(perk_ctx* ctx, perk_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx)
+    ctx->err = buf;
+  else
+    g_err = buf;
+  return s;
+}
+
+#define PERK_CUDA(ctx, call)                                                                        \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? PERK_E_OOM : PERK_E_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+  } while (0)
+
+void drop_graph(perk_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  ctx->graph_U = nullptr;
+}
+
+struct CellKey {
+  int64_t v;
+  bool operator==(const CellKey& o) const { return v == o.v; }
+};
+struct CellHash {
+  size_t operator()(const CellKey& k) const { return std::hash<int64_t>()(k.v); }
+};
+inline CellKey key_of(int l, int64_t ix, int64_t iy) { return CellKey{((int64_t)l << 56) | (ix << 28) | iy}; }
+
+// Interfaces and mortars of a periodic, 2:1-balanced leaf list by a walk over
+// each leaf's four face neighbourhoods in the implicit quadtree.
+perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, std::vector<int4>& ifs,
+                               std::vector<int4>& morts) {
+  std::unordered_map<CellKey, int32_t, CellHash> leaf;
+  leaf.reserve((size_t)n * 2);
+  int lmax = 0;
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = cells[3 * e], ix = cells[3 * e + 1], iy = cells[3 * e + 2];
+    if (l < 0 || l > 27) return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: level %d out of range", (long long)e, l);
+    const int64_t side = (int64_t)1 << l;
+    if (ix < 0 || iy < 0 || ix >= side || iy >= side)
+      return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: index outside level %d", (long long)e, l);
+    if (!leaf.emplace(key_of(l, ix, iy), (int32_t)e).second)
+      return fail(ctx, PERK_E_INVALID_ARG, "cell %lld duplicated", (long long)e);
+    lmax = std::max(lmax, l);
+  }
+  // exact tiling: areas sum to the square and no leaf has a leaf ancestor
+  long double area = 0.0L;
+  for (int64_t e = 0; e < n; ++e) area += std::ldexp(1.0L, -2 * cells[3 * e]);
+  if (std::fabs((double)(area - 1.0L)) > 1e-12) return fail(ctx, PERK_E_INVALID_ARG, "cells do not tile the domain");
+  for (int64_t e = 0; e < n; ++e) {
+    int l = cells[3 * e];
+    int64_t ix = cells[3 * e + 1], iy = cells[3 * e + 2];
+    while (l > 0) {
+      --l;
+      ix >>= 1;
+      iy >>= 1;
+      if (leaf.count(key_of(l, ix, iy))) return fail(ctx, PERK_E_INVALID_ARG, "cells overlap");
+    }
+  }
+  auto find = [&](int l, int64_t ix, int64_t iy) -> int32_t {
+    auto it = leaf.find(key_of(l, ix, iy));
+    return it == leaf.end() ? -1 : it->second;
+  };
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = cells[3 * e];
+    const int64_t ix = cells[3 * e + 1], iy = cells[3 * e + 2];
+    const int64_t side = (int64_t)1 << l;
+    for (int dir = 0; dir < 2; ++dir) {
+      // +dir neighbour region (same level)
+      const int64_t px = dir == 0 ? (ix + 1) % side : ix;
+      const int64_t py = dir == 1 ? (iy + 1) % side : iy;
+      const int32_t same = find(l, px, py);
+      if (same >= 0) {
+        ifs.push_back(make_int4((int)e, same, dir, 0));
+      } else if (l > 0 && find(l - 1, px >> 1, py >> 1) >= 0) {
+        // this leaf is the small side of a mortar whose large side is the +dir neighbour: built there
+      } else {
+        // the +dir region must be refined once: its two children along the face
+        const int64_t cx0 = dir == 0 ? 2 * px : 2 * px, cy0 = dir == 0 ? 2 * py : 2 * py;
+        const int32_t s0 = find(l + 1, cx0, cy0);
+        const int32_t s1 = find(l + 1, dir == 0 ? cx0 : cx0 + 1, dir == 0 ? cy0 + 1 : cy0);
+        if (s0 < 0 || s1 < 0) return fail(ctx, PERK_E_INVALID_ARG, "mesh not 2:1 balanced at cell %lld", (long long)e);
+        morts.push_back(make_int4((int)e, s0, s1, dir | (0 << 1)));
+      }
+      // -dir neighbour region: only detect mortars with this leaf as the large (right) side
+      const int64_t mx = dir == 0 ? (ix + side - 1) % side : ix;
+      const int64_t my = dir == 1 ? (iy + side - 1) % side : iy;
+      if (find(l, mx, my) >= 0) continue;                         // interface, built from the other side
+      if (l > 0 && find(l - 1, mx >> 1, my >> 1) >= 0) continue;  // small side of a mortar
+      const int64_t cx0 = dir == 0 ? 2 * mx + 1 : 2 * mx, cy0 = dir == 0 ? 2 * my : 2 * my + 1;
+      const int32_t s0 = find(l + 1, cx0, cy0);
+      const int32_t s1 = find(l + 1, dir == 0 ? cx0 : cx0 + 1, dir == 0 ? cy0 + 1 : cy0);
+      if (s0 < 0 || s1 < 0) return fail(ctx, PERK_E_INVALID_ARG, "mesh not 2:1 balanced at cell %lld", (long long)e);
+      morts.push_back(make_int4((int)e, s0, s1, dir | (1 << 1)));
+    }
+  }
+  return PERK_OK;
+}
+
+perk_status run_partition(perk_ctx* ctx) {
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  int R = 1, S = 1;
+  int32_t E[MAX_R] = {1};
+  if (ctx->has_tab) {
+    R = ctx->R;
+    S = ctx->S;
+    std::copy(ctx->E, ctx->E + R, E);
+  }
+  PERK_CUDA(ctx, ctx->d_E.ensure(MAX_R));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_E.p, E, sizeof(int32_t) * MAX_R, cudaMemcpyHostToDevice, ctx->stream));
+  PERK_CUDA(ctx, launch_partition(ctx->stream, ctx->n_elem, ctx->n_if, ctx->n_mort, ctx->d_level.p, ctx->d_if_raw.p,
+                                  ctx->d_mort_raw.p, R, S, ctx->d_E.p, ctx->d_method.p, ctx->d_elem_sorted.p,
+                                  ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_counts.p, ctx->d_minmax.p));
+  int64_t counts[3 * MAX_S];
+  int32_t mm[2];
+  PERK_CUDA(ctx, cudaMemcpyAsync(counts, ctx->d_counts.p, sizeof counts, cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaMemcpyAsync(mm, ctx->d_minmax.p, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < MAX_S; ++i) {
+    ctx->act_el[i] = i < S ? counts[i] : 0;
+    ctx->act_if[i] = i < S ? counts[MAX_S + i] : 0;
+    ctx->act_mort[i] = i < S ? counts[2 * MAX_S + i] : 0;
+  }
+  ctx->lmin = mm[0];
+  ctx->lmax = mm[1];
+  ctx->part_S = S;
+  ctx->partitioned = true;
+  drop_graph(ctx);
+  return PERK_OK;
+}
+
+// the stage launches of one step on stream st (also used under graph capture)
+perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U) {
+  const int S = ctx->S;
+  double* Kbuf[3] = {ctx->d_K1.p, ctx->d_Ka.p, ctx->d_Kb.p};
+  int prev = 0, cur = 0, prev_at_last = 0;
+  UpdateArgs ua{};
+  if (ctx->order == 3) {
+    ua.b1 = 1.0 / 6.0;
+    ua.bp = 1.0 / 6.0;
+    ua.bs = 2.0 / 3.0;
+  } else {
+    ua.b1 = 0.0;
+    ua.bp = 0.0;
+    ua.bs = 1.0;
+  }
+  ua.U = d_U;
+  ua.K1 = ctx->d_K1.p;
+  ua.flag = ctx->d_flag.p;
+  for (int i = 0; i < S; ++i) {
+    // K_1 has its own buffer; K_2, K_3, ... alternate between the two others
+    cur = (i == 0) ? 0 : (i % 2 == 1 ? 1 : 2);
+    StageArgs sa{};
+    sa.U = d_U;
+    sa.K1 = ctx->d_K1.p;
+    sa.Kp = Kbuf[prev];
+    sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
+    sa.dt = ctx->d_dt.p;
+    PERK_CUDA(ctx, launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
+                                ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
+    const bool last = (i == S - 1);
+    if (last) prev_at_last = prev;
+    UpdateArgs chk = ua;
+    chk.Kp = Kbuf[prev];
+    PERK_CUDA(ctx, launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
+                                 ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur],
+                                 last ? &chk : nullptr));
+    prev = cur;
+  }
+  ua.Kp = Kbuf[prev_at_last];  // K_{S-1}
+  PERK_CUDA(ctx, launch_commit(st, ctx->n_elem, ua, Kbuf[cur], ctx->d_dt.p, d_U));
+  return PERK_OK;
+}
+
+perk_status upload_coef(perk_ctx* ctx) {
+  std::vector<StageCoef> coef((size_t)MAX_S * MAX_R, StageCoef{0.0, 0.0});
+  for (int i = 1; i < ctx->S; ++i)
+    for (int r = 0; r < ctx->R; ++r) {
+      const double beta = ctx->a[(size_t)r * ctx->S + i];
+      coef[(size_t)i * MAX_R + r] = StageCoef{ctx->c[i] - beta, beta};
+    }
+  PERK_CUDA(ctx, ctx->d_coef.ensure((size_t)MAX_S * MAX_R));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_coef.p, coef.data(), coef.size() * sizeof(StageCoef), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return PERK_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
+  if (!prob || !out) return PERK_E_INVALID_ARG;
+  *out = nullptr;
+  if (prob->N != 3 || !(prob->gamma > 1.0) || prob->surface_flux < 0 || prob->surface_flux > 2)
+    return PERK_E_INVALID_ARG;
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return PERK_E_CUDA;
+  perk_ctx* ctx = new perk_ctx();
+  ctx->prob = *prob;
+  ctx->ops = build_ops(prob->gamma, prob->surface_flux);
+  if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
+      ctx->d_counts.ensure(3 * MAX_S) != cudaSuccess || ctx->d_minmax.ensure(2) != cudaSuccess ||
+      ctx->d_dt_out.ensure(1) != cudaSuccess) {
+    perk_destroy(ctx);
+    return PERK_E_CUDA;
+  }
+  cudaMemset(ctx->d_flag.p, 0, sizeof(int));
+  cudaDeviceSynchronize();
+  *out = ctx;
+  return PERK_OK;
+}
+
+void perk_destroy(perk_ctx* ctx) {
+  if (!ctx) return;
+  drop_graph(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  ctx->d_level.release();
+  ctx->d_method.release();
+  ctx->d_elem_sorted.release();
+  ctx->d_E.release();
+  ctx->d_minmax.release();
+  ctx->d_if_raw.release();
+  ctx->d_mort_raw.release();
+  ctx->d_if_sorted.release();
+  ctx->d_mort_sorted.release();
+  ctx->d_counts.release();
+  ctx->d_surf.release();
+  ctx->d_K1.release();
+  ctx->d_Ka.release();
+  ctx->d_Kb.release();
+  ctx->d_dt.release();
+  ctx->d_block_min.release();
+  ctx->d_dt_out.release();
+  ctx->d_coef.release();
+  ctx->d_flag.release();
+  delete ctx;
+}
+
+const char* perk_last_error(const perk_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+perk_status perk_set_stream(perk_ctx* ctx, void* stream) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return PERK_OK;
+}
+
+perk_status perk_mesh_upload(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, double x0, double length) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (n_cells <= 0 || !cells || !(length > 0.0) || n_cells > (int64_t)1 << 30)
+    return fail(ctx, PERK_E_INVALID_ARG, "invalid mesh arguments");
+  std::vector<int4> ifs, morts;
+  ifs.reserve((size_t)n_cells * 2);
+  perk_status s = build_connectivity(ctx, n_cells, cells, ifs, morts);
+  if (s != PERK_OK) return s;
+  drop_graph(ctx);
+  ctx->n_elem = n_cells;
+  ctx->n_if = (int64_t)ifs.size();
+  ctx->n_mort = (int64_t)morts.size();
+  ctx->x0 = x0;
+  ctx->length = length;
+  ctx->h_level.resize(n_cells);
+  for (int64_t e = 0; e < n_cells; ++e) ctx->h_level[e] = cells[3 * e];
+  ctx->h_if = std::move(ifs);
+  ctx->h_mort = std::move(morts);
+  const size_t ne = (size_t)n_cells;
+  PERK_CUDA(ctx, ctx->d_level.ensure(ne));
+  PERK_CUDA(ctx, ctx->d_method.ensure(ne));
+  PERK_CUDA(ctx, ctx->d_elem_sorted.ensure(ne));
+  PERK_CUDA(ctx, ctx->d_if_raw.ensure(ctx->h_if.size()));
+  PERK_CUDA(ctx, ctx->d_if_sorted.ensure(ctx->h_if.size()));
+  PERK_CUDA(ctx, ctx->d_mort_raw.ensure(ctx->h_mort.size()));
+  PERK_CUDA(ctx, ctx->d_mort_sorted.ensure(ctx->h_mort.size()));
+  PERK_CUDA(ctx, ctx->d_surf.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_K1.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_Ka.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_Kb.ensure(ne * ELEM));
+  const int nb = (int)std::min<int64_t>(1024, (n_cells * NODES + 255) / 256);
+  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(nb, 1)));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  if (!ctx->h_if.empty())
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_if_raw.p, ctx->h_if.data(), ctx->h_if.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  if (!ctx->h_mort.empty())
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_mort_raw.p, ctx->h_mort.data(), ctx->h_mort.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  ctx->has_mesh = true;
+  return run_partition(ctx);
+}
+
+perk_status perk_mesh_faces(int64_t n_cells, const int32_t* cells, int64_t* n_if, int32_t* ifs, int64_t if_cap,
+                            int64_t* n_mort, int32_t* morts, int64_t mort_cap) {
+  if (n_cells <= 0 || !cells || !n_if || !n_mort) return PERK_E_INVALID_ARG;
+  std::vector<int4> vi, vm;
+  perk_status s = build_connectivity(nullptr, n_cells, cells, vi, vm);
+  if (s != PERK_OK) return s;
+  *n_if = (int64_t)vi.size();
+  *n_mort = (int64_t)vm.size();
+  if (ifs && if_cap >= *n_if)
+    for (size_t q = 0; q < vi.size(); ++q) {
+      ifs[4 * q] = vi[q].x;
+      ifs[4 * q + 1] = vi[q].y;
+      ifs[4 * q + 2] = vi[q].z;
+      ifs[4 * q + 3] = vi[q].w;
+    }
+  if (morts && mort_cap >= *n_mort)
+    for (size_t q = 0; q < vm.size(); ++q) {
+      morts[4 * q] = vm[q].x;
+      morts[4 * q + 1] = vm[q].y;
+      morts[4 * q + 2] = vm[q].z;
+      morts[4 * q + 3] = vm[q].w;
+    }
+  return PERK_OK;
+}
+
+perk_status perk_mesh_query(const perk_ctx* ctx, perk_mesh_info* info) {
+  if (!ctx || !info) return PERK_E_INVALID_ARG;
+  std::memset(info, 0, sizeof *info);
+  if (!ctx->has_mesh) return PERK_E_NOT_READY;
+  info->n_elem = ctx->n_elem;
+  info->n_interfaces = ctx->n_if;
+  info->n_mortars = ctx->n_mort;
+  info->level_min = ctx->lmin;
+  info->level_max = ctx->lmax;
+  info->S = ctx->has_tab ? ctx->S : 0;
+  int64_t dof = 0;
+  for (int i = 0; i < ctx->part_S && i < 64; ++i) {
+    info->active_elements[i] = ctx->act_el[i];
+    info->active_interfaces[i] = ctx->act_if[i];
+    info->active_mortars[i] = ctx->act_mort[i];
+    dof += ctx->act_el[i] * NODES;
+  }
+  info->dof_stage_updates = ctx->has_tab ? dof : 0;
+  info->index_bytes = (int64_t)(ctx->n_elem * 2 * sizeof(int32_t) + ctx->n_if * sizeof(int4) +
+                                ctx->n_mort * sizeof(int4));
+  return PERK_OK;
+}
+
+perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a) {
+  if (S < 2 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !a) return PERK_E_INVALID_ARG;
+  for (int r = 0; r < R; ++r)
+    if (E[r] < 2 || E[r] > S || (r > 0 && E[r] < E[r - 1])) return PERK_E_INVALID_ARG;
+  for (int i = 0; i < S; ++i) c[i] = (double)i / (2.0 * (S - 1));
+  for (int r = 0; r < R; ++r) {
+    const int e = E[r];
+    // coefficients of P(z) = 1/e + ((e-1)/e) (1 + z/(e-1))^e: alpha_k = ((e-1)/e) C(e,k) / (e-1)^k
+    std::vector<double> alpha(e + 1);
+    double binom = 1.0;
+    for (int k = 0; k <= e; ++k) {
+      alpha[k] = ((e - 1.0) / e) * binom / std::pow(e - 1.0, k);
+      binom = binom * (e - k) / (k + 1);
+    }
+    double* ar = a + (size_t)r * S;
+    for (int i = 0; i < S; ++i) ar[i] = 0.0;
+    // z^{3+j} coefficient = c_{S-1-j} prod_{q=0}^{j} a_{S-q} (1-based stage indices), j = 0..e-3
+    double prod = 1.0;
+    for (int j = 0; j <= e - 3; ++j) {
+      const int stage = S - j;                    // 1-based stage whose a_{stage,stage-1} is found
+      const double cprev = (double)(stage - 2) / (2.0 * (S - 1));   // c_{stage-1}
+      const double v = alpha[3 + j] / (cprev * prod);
+      ar[stage - 1] = v;                           // a[r*S + i] = a_{i+1,i}, i = stage - 1
+      prod *= v;
+    }
+  }
+  return PERK_OK;
+}
+
+perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32_t* E, const double* c,
+                             const double* a) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if ((order != 2 && order != 3) || S < 1 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !a)
+    return fail(ctx, PERK_E_INVALID_ARG, "invalid tableau dimensions");
+  if (order == 3 && S < 3) return fail(ctx, PERK_E_INVALID_ARG, "third order needs S >= 3");
+  for (int r = 0; r < R; ++r)
+    if (E[r] < 1 || E[r] > S || (r > 0 && E[r] < E[r - 1]))
+      return fail(ctx, PERK_E_INVALID_ARG, "member evaluations must ascend within [1, S]");
+  if (E[R - 1] != S) return fail(ctx, PERK_E_INVALID_ARG, "the largest member must evaluate every stage");
+  ctx->order = order;
+  ctx->S = S;
+  ctx->R = R;
+  std::copy(E, E + R, ctx->E);
+  ctx->c.assign(c, c + S);
+  ctx->a.assign(a, a + (size_t)R * S);
+  // a_{i,i-1}^{(r)} may be nonzero only where member r evaluates stage i-1 (stage 1, or S-E+2 .. S);
+  // anything else would combine a stale stage
+  for (int r = 0; r < R; ++r)
+    for (int i0 = 1; i0 < S; ++i0) {
+      const bool evaluated = (i0 == 1) || (i0 >= S - E[r] + 2);
+      if (!evaluated && ctx->a[(size_t)r * S + i0] != 0.0)
+        return fail(ctx, PERK_E_INVALID_ARG, "member %d: a_{%d,%d} != 0 but stage %d is not evaluated", r, i0 + 1,
+                    i0, i0);
+    }
+  ctx->has_tab = true;
+  drop_graph(ctx);
+  perk_status s = upload_coef(ctx);
+  if (s != PERK_OK) return s;
+  if (ctx->has_mesh) return run_partition(ctx);
+  return PERK_OK;
+}
+
+perk_status perk_reference_nodes(int N, double* x, double* w) {
+  if (N < 1 || N > 16 || !x || !w) return PERK_E_INVALID_ARG;
+  std::vector<double> xv, wv;
+  lgl(N, xv, wv);
+  std::copy(xv.begin(), xv.end(), x);
+  std::copy(wv.begin(), wv.end(), w);
+  return PERK_OK;
+}
+
+perk_status perk_partition(perk_ctx* ctx) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  return run_partition(ctx);
+}
+
+static perk_status rhs_given(perk_ctx* ctx, int stage, const double* d_Y, double* d_K) {
+  if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_Y || !d_K) return fail(ctx, PERK_E_INVALID_ARG, "null array");
+  StageArgs sa{};
+  sa.Y = d_Y;
+  const int64_t ne = stage < 0 ? ctx->n_elem : ctx->act_el[stage];
+  const int64_t ni = stage < 0 ? ctx->n_if : ctx->act_if[stage];
+  const int64_t nm = stage < 0 ? ctx->n_mort : ctx->act_mort[stage];
+  PERK_CUDA(ctx, launch_faces(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
+                              ctx->d_method.p, sa, ctx->d_surf.p));
+  PERK_CUDA(ctx, launch_volume(ctx->stream, Y_GIVEN, ctx->ops, ne, ctx->d_elem_sorted.p, ctx->d_level.p,
+                               ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr));
+  return PERK_OK;
+}
+
+perk_status perk_rhs_full(perk_ctx* ctx, const double* d_Y, double* d_K) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  return rhs_given(ctx, -1, d_Y, d_K);
+}
+
+perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double* d_K) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_tab) return fail(ctx, PERK_E_NOT_READY, "no tableau");
+  if (stage < 0 || stage >= ctx->S) return fail(ctx, PERK_E_INVALID_ARG, "stage %d outside [0, %d)", stage, ctx->S);
+  return rhs_given(ctx, stage, d_Y, d_K);
+}
+
+perk_status perk_step(perk_ctx* ctx, double* d_U, double dt) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
+    return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
+  if (!d_U || !std::isfinite(dt) || !(dt > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or dt");
+  if (((uintptr_t)d_U & 15) != 0) return fail(ctx, PERK_E_INVALID_ARG, "U must be 16-byte aligned");
+  if (!(dt == ctx->cur_dt)) {
+    PERK_CUDA(ctx, launch_set_scalar(ctx->stream, ctx->d_dt.p, dt));
+    ctx->cur_dt = dt;
+  }
+  if (ctx->prob.use_graph) {
+    if (!ctx->graph || ctx->graph_U != d_U) {
+      drop_graph(ctx);
+      cudaGraph_t g = nullptr;
+      PERK_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      perk_status s = enqueue_step(ctx, ctx->cap_stream, d_U);
+      cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+      if (s != PERK_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      PERK_CUDA(ctx, ce);
+      cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+      cudaGraphDestroy(g);
+      PERK_CUDA(ctx, ie);
+      ctx->graph_U = d_U;
+    }
+    PERK_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+  } else {
+    perk_status s = enqueue_step(ctx, ctx->stream, d_U);
+    if (s != PERK_OK) return s;
+  }
+  ctx->counters.steps += 1;
+  for (int i = 0; i < ctx->S; ++i) {
+    ctx->counters.element_stage_evaluations += ctx->act_el[i];
+    ctx->counters.dof_stage_updates += ctx->act_el[i] * NODES;
+  }
+  return PERK_OK;
+}
+
+perk_status perk_check(perk_ctx* ctx) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  int flag = 0;
+  PERK_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (flag) {
+    PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), ctx->stream));
+    PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->counters.rejected_steps_checked += 1;
+    return fail(ctx, PERK_E_NONFINITE, "a step produced a non-admissible state and was not committed");
+  }
+  return PERK_OK;
+}
+
+perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double* dt) {
+  if (!ctx || !dt) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_U || !(cfl > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or cfl");
+  const int nb = (int)std::min<int64_t>(1024, (ctx->n_elem * NODES + 255) / 256);
+  PERK_CUDA(ctx, launch_dt(ctx->stream, ctx->n_elem, d_U, ctx->d_level.p, ctx->length, ctx->ops.gamma,
+                           ctx->d_block_min.p, nb, ctx->d_dt_out.p));
+  double m = 0.0;
+  PERK_CUDA(ctx, cudaMemcpyAsync(&m, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *dt = cfl * m / (double)NN;
+  return PERK_OK;
+}
+
+perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out) {
+  if (!ctx || !out) return PERK_E_INVALID_ARG;
+  *out = ctx->counters;
+  return PERK_OK;
+}
+
+}  // extern "C"

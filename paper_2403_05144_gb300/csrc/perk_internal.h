@@ -1,0 +1,80 @@
+// Internal declarations shared by the host runtime (perk_host.cpp) and the
+// kernels (perk_kernels.cu).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace perk {
+
+constexpr int NN = 4;             // LGL nodes per direction (N = 3)
+constexpr int NODES = NN * NN;    // nodes per element
+constexpr int NV = 4;             // conserved variables
+constexpr int ELEM = NV * NODES;  // doubles per element
+constexpr int MAX_S = 64;
+constexpr int MAX_R = 8;
+
+// Reference-element operators, computed on the host once per context.
+struct Ops {
+  double dsplit[NN][NN];  // 2 D_ij off the diagonal, 0 on it (LGL: 2 D_00 + 1/w_0 = 0 = 2 D_NN - 1/w_N)
+  double inv_w0;          // 1 / w_0 = 1 / w_N
+  double p_lo[NN][NN];    // large-face trace -> lower half-face nodes (interpolation)
+  double p_hi[NN][NN];    // large-face trace -> upper half-face nodes
+  double r_lo[NN][NN];    // lower half-face flux -> large face (exact L2 projection)
+  double r_hi[NN][NN];    // upper half-face flux -> large face
+  double gamma;
+  double inv_gm1;         // 1 / (gamma - 1)
+  double gm1;             // gamma - 1
+  int surface_flux;       // perk_surface_flux
+};
+
+// Y = U + dt * (alpha * K1 + beta * Kprev) for an element of a given member at a given stage.
+struct StageCoef {
+  double alpha;
+  double beta;
+};
+
+// Where the stage state comes from.
+enum YSource { Y_GIVEN = 0, Y_COMBINE = 1 };
+
+struct StageArgs {
+  const double* Y;        // Y_GIVEN: the stage vector
+  const double* U;        // Y_COMBINE: U_n
+  const double* K1;       //            K_1
+  const double* Kp;       //            K_{i-1}
+  const StageCoef* coef;  //            [R] coefficients of this stage
+  const double* dt;       //            device scalar
+};
+
+// Final-update description (P-ERK2: b = e_S; P-ERK3: b on K_1, K_{S-1}, K_S).
+struct UpdateArgs {
+  double b1, bp, bs;      // weights of K_1, K_{S-1}, K_S
+  const double* U;
+  const double* K1;
+  const double* Kp;
+  int* flag;              // raised (set to 1) when any new state is not admissible
+};
+
+// ---- kernel launchers (perk_kernels.cu); all return cudaGetLastError() ----
+
+cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
+                             const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
+                             int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
+                             int64_t* counts /* [3][MAX_S] */, int32_t* level_minmax /* [2] */);
+
+cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+                         const int4* morts, const int32_t* method, const StageArgs& sa, double* surf);
+
+cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
+                          const int32_t* level, const int32_t* method, double inv_len2, const StageArgs& sa,
+                          const double* surf, double* K, const UpdateArgs* check);
+
+cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua, const double* Ks, const double* dt,
+                          double* U);
+
+cudaError_t launch_set_scalar(cudaStream_t st, double* p, double v);
+
+cudaError_t launch_dt(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level, double length,
+                      double gamma, double* block_min, int n_blocks, double* out);
+
+}  // namespace perk

@@ -1,0 +1,694 @@
+// sm_103a kernels of the P-ERK / DGSEM hot path.
+//
+// One P-ERK stage (Eq. PartitionedRKSystem; Sec. 3.1) is two launches over the
+// active prefixes of the level-sorted lists:
+//   k_faces   numerical fluxes of the active interfaces and mortars (Sec. 6.2),
+//             stage states formed on the fly at the face nodes;
+//   k_volume  flux-differencing volume integral + surface lifting + Jacobian
+//             of the active elements, stage state formed on the fly.
+// The step ends with k_commit (guarded final update).  k_partition rebuilds
+// the level partition; k_dt_* reduce the CFL step size (Eq. CFL_DG).
+//
+// All arithmetic is FP64.  The FP64 pipe of GB300 is the binding resource of
+// the volume kernel, so it evaluates every symmetric node pair once (48 pairs
+// per element instead of 96 one-sided evaluations), takes the logarithms of
+// density and rho/p once per node, and forms each logarithmic mean with one
+// division.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "perk.h"
+#include "perk_internal.h"
+
+namespace perk {
+
+// ---------------------------------------------------------------------------
+// Logarithmic mean from per-node logarithms.
+//
+// With d = b - a, s = a + b, f = d/s and u = f^2:  ln(b/a) = 2 artanh(f)
+// = 2 f A(u), A(u) = sum_k u^k / (2k+1).  Hence
+//   {{x}}_ln = d / ln(b/a) = (s/2) G(u),  G = 1/A,
+//   1/{{x}}_ln = (2/s) A(u).
+// For u < 1e-2 the truncated series (k <= 7; remainder < 6e-18 relative) is
+// used; otherwise the quotient of the difference and the difference of the
+// precomputed logarithms, whose relative error there is below ~1e-15 |ln x|.
+// G's coefficients follow from A G = 1 term by term (exact rationals).
+__device__ __forceinline__ double series_A(double u) {
+  double r = 1.0 / 15.0;
+  r = fma(r, u, 1.0 / 13.0);
+  r = fma(r, u, 1.0 / 11.0);
+  r = fma(r, u, 1.0 / 9.0);
+  r = fma(r, u, 1.0 / 7.0);
+  r = fma(r, u, 1.0 / 5.0);
+  r = fma(r, u, 1.0 / 3.0);
+  return fma(r, u, 1.0);
+}
+__device__ __forceinline__ double series_G(double u) {
+  double r = -25865068.0 / 1915538625.0;
+  r = fma(r, u, -10719068.0 / 638512875.0);
+  r = fma(r, u, -10196.0 / 467775.0);
+  r = fma(r, u, -428.0 / 14175.0);
+  r = fma(r, u, -44.0 / 945.0);
+  r = fma(r, u, -4.0 / 45.0);
+  r = fma(r, u, -1.0 / 3.0);
+  return fma(r, u, 1.0);
+}
+__device__ __forceinline__ double ln_mean(double a, double b, double lna, double lnb) {
+  const double d = b - a, s = a + b;
+  if (d * d < 1e-2 * (s * s)) {
+    const double is = 1.0 / s;
+    const double f = d * is;
+    return 0.5 * s * series_G(f * f);
+  }
+  return d / (lnb - lna);
+}
+__device__ __forceinline__ double inv_ln_mean(double a, double b, double lna, double lnb) {
+  const double d = b - a, s = a + b;
+  if (d * d < 1e-2 * (s * s)) {
+    const double is = 1.0 / s;
+    const double f = d * is;
+    return 2.0 * is * series_A(f * f);
+  }
+  return (lnb - lna) / d;
+}
+
+// Ranocha's entropy-conservative, kinetic-energy-preserving two-point flux in
+// direction dir (0 = x, 1 = y), from node primitives and their logarithms.
+struct Prim {
+  double rho, v1, v2, p, lnrho, beta, lnbeta;  // beta = rho / p
+};
+
+__device__ __forceinline__ void ec_flux(const Prim& A, const Prim& B, int dir, double inv_gm1, double f[4]) {
+  const double rho_ln = ln_mean(A.rho, B.rho, A.lnrho, B.lnrho);
+  const double ibeta_ln = inv_ln_mean(A.beta, B.beta, A.lnbeta, B.lnbeta);
+  const double v1m = 0.5 * (A.v1 + B.v1);
+  const double v2m = 0.5 * (A.v2 + B.v2);
+  const double pm = 0.5 * (A.p + B.p);
+  const double vnA = dir ? A.v2 : A.v1;
+  const double vnB = dir ? B.v2 : B.v1;
+  const double frho = rho_ln * (dir ? v2m : v1m);
+  f[0] = frho;
+  f[1] = fma(frho, v1m, dir ? 0.0 : pm);
+  f[2] = fma(frho, v2m, dir ? pm : 0.0);
+  const double kin = 0.5 * fma(A.v1, B.v1, A.v2 * B.v2);
+  f[3] = fma(frho, fma(ibeta_ln, inv_gm1, kin), 0.5 * fma(A.p, vnB, B.p * vnA));
+}
+
+__device__ __forceinline__ Prim prim_from_cons(const double u[4], double gm1) {
+  Prim P;
+  const double ir = 1.0 / u[0];
+  P.rho = u[0];
+  P.v1 = u[1] * ir;
+  P.v2 = u[2] * ir;
+  P.p = gm1 * (u[3] - 0.5 * (u[1] * P.v1 + u[2] * P.v2));
+  P.beta = u[0] / P.p;
+  P.lnrho = log(P.rho);
+  P.lnbeta = log(P.beta);
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// Surface fluxes f*(uL, uR) in direction dir.
+__device__ __forceinline__ void phys_flux(const double u[4], double vn, double p, int dir, double f[4]) {
+  f[0] = u[0] * vn;
+  f[1] = fma(u[1], vn, dir ? 0.0 : p);
+  f[2] = fma(u[2], vn, dir ? p : 0.0);
+  f[3] = (u[3] + p) * vn;
+}
+
+// HLL with Davis wave-speed estimates S_L = min(vL - cL, vR - cR), S_R = max(vL + cL, vR + cR).
+__device__ void flux_hll(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
+  const double irL = 1.0 / uL[0], irR = 1.0 / uR[0];
+  const double pL = ops.gm1 * (uL[3] - 0.5 * (uL[1] * uL[1] + uL[2] * uL[2]) * irL);
+  const double pR = ops.gm1 * (uR[3] - 0.5 * (uR[1] * uR[1] + uR[2] * uR[2]) * irR);
+  const double vL = uL[1 + dir] * irL, vR = uR[1 + dir] * irR;
+  const double cL = sqrt(ops.gamma * pL * irL), cR = sqrt(ops.gamma * pR * irR);
+  const double SL = fmin(vL - cL, vR - cR), SR = fmax(vL + cL, vR + cR);
+  double fL[4], fR[4];
+  phys_flux(uL, vL, pL, dir, fL);
+  phys_flux(uR, vR, pR, dir, fR);
+  if (SL >= 0.0) {
+    for (int v = 0; v < 4; ++v) f[v] = fL[v];
+  } else if (SR <= 0.0) {
+    for (int v = 0; v < 4; ++v) f[v] = fR[v];
+  } else {
+    const double inv = 1.0 / (SR - SL);
+    const double SLSR = SL * SR;
+    for (int v = 0; v < 4; ++v) f[v] = (SR * fL[v] - SL * fR[v] + SLSR * (uR[v] - uL[v])) * inv;
+  }
+}
+
+// HLLC (Toro, Spruce, Speares 1994) with the same speeds and the standard contact speed.
+__device__ void flux_hllc(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
+  const double irL = 1.0 / uL[0], irR = 1.0 / uR[0];
+  const double pL = ops.gm1 * (uL[3] - 0.5 * (uL[1] * uL[1] + uL[2] * uL[2]) * irL);
+  const double pR = ops.gm1 * (uR[3] - 0.5 * (uR[1] * uR[1] + uR[2] * uR[2]) * irR);
+  const double vL = uL[1 + dir] * irL, vR = uR[1 + dir] * irR;
+  const double cL = sqrt(ops.gamma * pL * irL), cR = sqrt(ops.gamma * pR * irR);
+  const double SL = fmin(vL - cL, vR - cR), SR = fmax(vL + cL, vR + cR);
+  if (SL >= 0.0) {
+    phys_flux(uL, vL, pL, dir, f);
+    return;
+  }
+  if (SR <= 0.0) {
+    phys_flux(uR, vR, pR, dir, f);
+    return;
+  }
+  const double mL = uL[0] * (SL - vL), mR = uR[0] * (SR - vR);
+  const double Ss = (pR - pL + mL * vL - mR * vR) / (mL - mR);
+  const bool left = Ss >= 0.0;
+  const double* u = left ? uL : uR;
+  const double S = left ? SL : SR;
+  const double vn = left ? vL : vR;
+  const double p = left ? pL : pR;
+  const double m = left ? mL : mR;
+  const double ir = left ? irL : irR;
+  double fk[4];
+  phys_flux(u, vn, p, dir, fk);
+  const double fac = m / (S - Ss);          // rho_K (S_K - v_K) / (S_K - S*)
+  double us[4];
+  us[0] = fac;
+  us[1 + dir] = fac * Ss;
+  us[2 - dir] = fac * (u[2 - dir] * ir);
+  us[3] = fac * (u[3] * ir + (Ss - vn) * (Ss + p / m));
+  for (int v = 0; v < 4; ++v) f[v] = fk[v] + S * (us[v] - u[v]);
+}
+
+__device__ void flux_ec_surface(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
+  const Prim A = prim_from_cons(uL, ops.gm1), B = prim_from_cons(uR, ops.gm1);
+  ec_flux(A, B, dir, ops.inv_gm1, f);
+}
+
+__device__ __forceinline__ void surface_flux(const double uL[4], const double uR[4], int dir, const Ops& ops,
+                                             double f[4]) {
+  if (ops.surface_flux == PERK_SURFACE_HLLC)
+    flux_hllc(uL, uR, dir, ops, f);
+  else if (ops.surface_flux == PERK_SURFACE_EC)
+    flux_ec_surface(uL, uR, dir, ops, f);
+  else
+    flux_hll(uL, uR, dir, ops, f);
+}
+
+// ---------------------------------------------------------------------------
+// Stage state at one node of element e.
+__device__ __forceinline__ int face_node(int face, int k) {
+  // faces: 0 = -x (i = 0), 1 = +x (i = N), 2 = -y (j = 0), 3 = +y (j = N); node index = j * 4 + i
+  return face == 0 ? 4 * k : face == 1 ? 4 * k + 3 : face == 2 ? k : 12 + k;
+}
+
+template <int YS>
+__device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int m, int node, double y[4]) {
+  const int64_t base = e * ELEM + node;
+  if (YS == Y_GIVEN) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.Y + base + v * NODES);
+  } else {
+    const StageCoef c = sa.coef[m];
+    const double dt = *sa.dt;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.U + base + v * NODES);
+    if (c.alpha != 0.0) {
+      const double da = dt * c.alpha;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) y[v] = fma(da, __ldg(sa.K1 + base + v * NODES), y[v]);
+    }
+    if (c.beta != 0.0) {
+      const double db = dt * c.beta;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) y[v] = fma(db, __ldg(sa.Kp + base + v * NODES), y[v]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Faces: 4 threads per interface (one per face node), 8 per mortar (half, node).
+constexpr int FACE_THREADS = 128;
+constexpr int IF_PER_BLOCK = FACE_THREADS / 4;
+constexpr int MORT_PER_BLOCK = FACE_THREADS / 8;
+
+template <int YS>
+__global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                         int64_t n_mort, const int4* __restrict__ morts,
+                                                         int64_t if_blocks, const int32_t* __restrict__ method,
+                                                         StageArgs sa, double* __restrict__ surf) {
+  __shared__ double s_half[MORT_PER_BLOCK][2][4][NN];  // [mortar][half][var][node]
+  if (blockIdx.x < if_blocks) {
+    const int64_t idx = (int64_t)blockIdx.x * IF_PER_BLOCK + (threadIdx.x >> 2);
+    const int k = threadIdx.x & 3;
+    if (idx >= n_if) return;
+    const int4 r = ifs[idx];
+    const int dir = r.z;
+    double uL[4], uR[4], f[4];
+    stage_state<YS>(sa, r.x, r.w, face_node(2 * dir + 1, k), uL);
+    stage_state<YS>(sa, r.y, r.w, face_node(2 * dir, k), uR);
+    surface_flux(uL, uR, dir, ops, f);
+    double* sL = surf + (int64_t)r.x * ELEM + (2 * dir + 1) * 16 + k;
+    double* sR = surf + (int64_t)r.y * ELEM + (2 * dir) * 16 + k;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sL[4 * v] = f[v];
+      sR[4 * v] = f[v];
+    }
+    return;
+  }
+  // mortars
+  const int lm = threadIdx.x >> 3;
+  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * MORT_PER_BLOCK + lm;
+  const int half = (threadIdx.x >> 2) & 1;
+  const int k = threadIdx.x & 3;
+  const bool valid = idx < n_mort;
+  int4 r = make_int4(0, 0, 0, 0);
+  if (valid) r = morts[idx];
+  const int dir = r.w & 1, large_side = (r.w >> 1) & 1, m_fine = r.w >> 2;
+  const int large_face = large_side == 0 ? 2 * dir + 1 : 2 * dir;
+  const int small_face = large_side == 0 ? 2 * dir : 2 * dir + 1;
+  const int small = half ? r.z : r.y;
+  if (valid) {
+    // trace of the large element interpolated to node k of this half
+    double ul[4][4];
+    const int m_large = method[r.x];
+#pragma unroll
+    for (int l = 0; l < NN; ++l) stage_state<YS>(sa, r.x, m_large, face_node(large_face, l), ul[l]);
+    double ui[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int l = 0; l < NN; ++l) {
+      const double w = half ? ops.p_hi[k][l] : ops.p_lo[k][l];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) ui[v] = fma(w, ul[l][v], ui[v]);
+    }
+    double us[4], f[4];
+    stage_state<YS>(sa, small, m_fine, face_node(small_face, k), us);
+    if (large_side == 0)
+      surface_flux(ui, us, dir, ops, f);
+    else
+      surface_flux(us, ui, dir, ops, f);
+    double* s = surf + (int64_t)small * ELEM + small_face * 16 + k;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      s[4 * v] = f[v];
+      s_half[lm][half][v][k] = f[v];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    // projection onto the large face: thread (half, k) produces vars 2*half, 2*half+1 at node k
+#pragma unroll
+    for (int vv = 0; vv < 2; ++vv) {
+      const int v = 2 * half + vv;
+      double acc = 0.0;
+#pragma unroll
+      for (int l = 0; l < NN; ++l) {
+        acc = fma(ops.r_lo[k][l], s_half[lm][0][v][l], acc);
+        acc = fma(ops.r_hi[k][l], s_half[lm][1][v][l], acc);
+      }
+      surf[(int64_t)r.x * ELEM + large_face * 16 + 4 * v + k] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Volume integral (flux differencing) + surface lifting + Jacobian.
+// 16 threads per element (one per node), 8 elements per block.
+constexpr int VOL_THREADS = 128;
+constexpr int VOL_ELEMS = VOL_THREADS / NODES;
+constexpr int NPAIR = 48;  // 2 directions x 4 lines x 6 pairs
+
+__device__ __forceinline__ int pair_slot(int a, int b) {  // a < b, slots 0..5
+  return (a * (7 - a)) / 2 + b - a - 1;
+}
+
+template <int YS, bool CHECK>
+__global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
+                                                         const int32_t* __restrict__ level,
+                                                         const int32_t* __restrict__ method, double two_over_len,
+                                                         StageArgs sa, const double* __restrict__ surf,
+                                                         double* __restrict__ K, UpdateArgs ua) {
+  __shared__ Prim s_prim[VOL_ELEMS][NODES];
+  __shared__ double s_flux[VOL_ELEMS][4][NPAIR];
+  const int le = threadIdx.x >> 4;
+  const int t = threadIdx.x & 15;
+  const int i = t & 3, j = t >> 2;
+  const int64_t slot = (int64_t)blockIdx.x * VOL_ELEMS + le;
+  const bool valid = slot < n;
+  const int64_t e = valid ? elems[slot] : 0;
+  const int m = valid ? method[e] : 0;
+
+  double y[4];
+  if (valid) {
+    stage_state<YS>(sa, e, m, t, y);
+  } else {
+    y[0] = 1.0; y[1] = 0.0; y[2] = 0.0; y[3] = 2.5;
+  }
+  s_prim[le][t] = prim_from_cons(y, ops.gm1);
+  __syncwarp();
+
+  // the three pairs of this thread: slots t, t + 16, t + 32 of 48
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    const int p = t + 16 * kk;
+    const int dir = p >= 24;
+    const int q = dir ? p - 24 : p;
+    const int line = q / 6, qq = q - 6 * line;
+    const int a = (qq >= 3) + (qq >= 5);
+    const int b = qq + 1 - (a * (5 - a)) / 2;
+    const int na = dir ? a * 4 + line : line * 4 + a;
+    const int nb = dir ? b * 4 + line : line * 4 + b;
+    double f[4];
+    ec_flux(s_prim[le][na], s_prim[le][nb], dir, ops.inv_gm1, f);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) s_flux[le][v][p] = f[v];
+  }
+  __syncwarp();
+
+  double dx[4], dy[4];
+#pragma unroll
+  for (int mm = 0; mm < 4; ++mm) {
+    dx[mm] = ops.dsplit[i][mm];
+    dy[mm] = ops.dsplit[j][mm];
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int mm = 0; mm < 4; ++mm) {
+    if (mm != i) {
+      const int p = j * 6 + pair_slot(min(i, mm), max(i, mm));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] = fma(dx[mm], s_flux[le][v][p], acc[v]);
+    }
+    if (mm != j) {
+      const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] = fma(dy[mm], s_flux[le][v][p], acc[v]);
+    }
+  }
+  if (!valid) return;
+
+  // surface lifting with the numerical fluxes of the four faces (w_0 = w_N)
+  const double* sf = surf + e * ELEM;
+  const double iw = ops.inv_w0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    if (i == 0) acc[v] = fma(-iw, __ldg(sf + 0 * 16 + 4 * v + j), acc[v]);
+    if (i == 3) acc[v] = fma(iw, __ldg(sf + 1 * 16 + 4 * v + j), acc[v]);
+    if (j == 0) acc[v] = fma(-iw, __ldg(sf + 2 * 16 + 4 * v + i), acc[v]);
+    if (j == 3) acc[v] = fma(iw, __ldg(sf + 3 * 16 + 4 * v + i), acc[v]);
+  }
+  const double scale = -ldexp(two_over_len, level[e]);  // -(2/h)
+  double kv[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    kv[v] = scale * acc[v];
+    K[e * ELEM + v * NODES + t] = kv[v];
+  }
+  if (CHECK) {
+    // admissibility of the state this step would commit at this node
+    const double dt = *sa.dt;
+    const int64_t base = e * ELEM + t;
+    double un[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      double inc = ua.bs * kv[v];
+      if (ua.b1 != 0.0) inc = fma(ua.b1, __ldg(ua.K1 + base + v * NODES), inc);
+      if (ua.bp != 0.0) inc = fma(ua.bp, __ldg(ua.Kp + base + v * NODES), inc);
+      un[v] = fma(dt, inc, __ldg(ua.U + base + v * NODES));
+    }
+    const double p = ops.gm1 * (un[3] - 0.5 * (un[1] * un[1] + un[2] * un[2]) / un[0]);
+    const bool ok = isfinite(un[0]) && isfinite(un[1]) && isfinite(un[2]) && isfinite(un[3]) && un[0] > 0.0 &&
+                    p > 0.0 && isfinite(p);
+    if (!ok) *ua.flag = 1;
+  }
+}
+
+// Guarded final update U += dt (b1 K1 + bp Kp + bs Ks), skipped entirely when
+// the admissibility flag is raised.
+__global__ void k_commit(int64_t n2, UpdateArgs ua, const double2* __restrict__ Ks, const double* dtp,
+                         double2* __restrict__ U) {
+  if (*ua.flag != 0) return;
+  const double dt = *dtp;
+  const double2* K1 = reinterpret_cast<const double2*>(ua.K1);
+  const double2* Kp = reinterpret_cast<const double2*>(ua.Kp);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x) {
+    const double2 ks = Ks[q];
+    double2 inc = make_double2(ua.bs * ks.x, ua.bs * ks.y);
+    if (ua.b1 != 0.0) {
+      const double2 k1 = K1[q];
+      inc.x = fma(ua.b1, k1.x, inc.x);
+      inc.y = fma(ua.b1, k1.y, inc.y);
+    }
+    if (ua.bp != 0.0) {
+      const double2 kp = Kp[q];
+      inc.x = fma(ua.bp, kp.x, inc.x);
+      inc.y = fma(ua.bp, kp.y, inc.y);
+    }
+    double2 u = U[q];
+    u.x = fma(dt, inc.x, u.x);
+    u.y = fma(dt, inc.y, u.y);
+    U[q] = u;
+  }
+}
+
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+
+// ---------------------------------------------------------------------------
+// Level partition: one block; stable counting sort of the element, interface
+// and mortar lists by member, finest member first.
+constexpr int PART_THREADS = 1024;
+
+__device__ int block_scan_members(int key, int R, int* s_wtot /* [MAX_R][32] */, int* s_wscan, int* rank_out) {
+  // returns, for this thread, its rank among threads of the same key (exclusive),
+  // and writes the per-key chunk totals to s_wscan[r * 33 + 32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int my_rank = 0;
+  for (int r = 0; r < R; ++r) {
+    const unsigned bal = __ballot_sync(0xffffffffu, key == r);
+    if (key == r) my_rank = __popc(bal & lt);
+    if (lane == 0) s_wtot[r * 32 + warp] = __popc(bal);
+  }
+  __syncthreads();
+  if (warp < R) {
+    const int v = s_wtot[warp * 32 + lane];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += n;
+    }
+    s_wscan[warp * 33 + lane] = incl - v;
+    if (lane == 31) s_wscan[warp * 33 + 32] = incl;
+  }
+  __syncthreads();
+  *rank_out = (key >= 0) ? s_wscan[key * 33 + warp] + my_rank : 0;
+  return 0;
+}
+
+__global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int64_t n_if, int64_t n_mort,
+                                                              const int32_t* __restrict__ level,
+                                                              const int4* __restrict__ if_raw,
+                                                              const int4* __restrict__ mort_raw, int R, int S,
+                                                              const int32_t* __restrict__ E, int32_t* method,
+                                                              int32_t* elem_sorted, int4* if_sorted,
+                                                              int4* mort_sorted, int64_t* counts,
+                                                              int32_t* level_minmax) {
+  __shared__ int s_min, s_max;
+  __shared__ int s_cnt[3][MAX_R];
+  __shared__ int s_base[MAX_R];
+  __shared__ int s_run[MAX_R];
+  __shared__ int s_wtot[MAX_R * 32];
+  __shared__ int s_wscan[MAX_R * 33];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_min = 1 << 30;
+    s_max = -1;
+  }
+  if (tid < 3 * MAX_R) s_cnt[tid / MAX_R][tid % MAX_R] = 0;
+  __syncthreads();
+  int lmin = 1 << 30, lmax = -1;
+  for (int64_t e = tid; e < n_elem; e += PART_THREADS) {
+    const int l = level[e];
+    lmin = min(lmin, l);
+    lmax = max(lmax, l);
+  }
+  atomicMin(&s_min, lmin);
+  atomicMax(&s_max, lmax);
+  __syncthreads();
+  const int Lmax = s_max;
+  // members and their counts
+  for (int64_t e = tid; e < n_elem; e += PART_THREADS) {
+    const int mth = max(0, (R - 1) - (Lmax - level[e]));
+    method[e] = mth;
+    atomicAdd(&s_cnt[0][mth], 1);
+  }
+  __syncthreads();
+  for (int64_t q = tid; q < n_if; q += PART_THREADS) atomicAdd(&s_cnt[1][method[if_raw[q].x]], 1);
+  for (int64_t q = tid; q < n_mort; q += PART_THREADS) atomicAdd(&s_cnt[2][method[mort_raw[q].y]], 1);
+  __syncthreads();
+
+  for (int list = 0; list < 3; ++list) {
+    const int64_t n = list == 0 ? n_elem : list == 1 ? n_if : n_mort;
+    if (tid == 0) {
+      int b = 0;
+      for (int r = R - 1; r >= 0; --r) {
+        s_base[r] = b;
+        b += s_cnt[list][r];
+        s_run[r] = 0;
+      }
+    }
+    __syncthreads();
+    for (int64_t start = 0; start < n; start += PART_THREADS) {
+      const int64_t q = start + tid;
+      int key = -1;
+      int4 rec = make_int4(0, 0, 0, 0);
+      if (q < n) {
+        if (list == 0) {
+          key = method[q];
+        } else if (list == 1) {
+          rec = if_raw[q];
+          key = method[rec.x];
+          rec.w = key;
+        } else {
+          rec = mort_raw[q];
+          key = method[rec.y];
+          rec.w = (rec.w & 3) | (key << 2);
+        }
+      }
+      int rank;
+      block_scan_members(key, R, s_wtot, s_wscan, &rank);
+      if (key >= 0) {
+        const int pos = s_base[key] + s_run[key] + rank;
+        if (list == 0)
+          elem_sorted[pos] = (int32_t)q;
+        else if (list == 1)
+          if_sorted[pos] = rec;
+        else
+          mort_sorted[pos] = rec;
+      }
+      __syncthreads();
+      if (tid < R) s_run[tid] += s_wscan[tid * 33 + 32];
+      __syncthreads();
+    }
+  }
+  // active counts per stage: member r is active at stage i (0-based) iff i == 0 or E[r] >= S - i + 1
+  if (tid < S) {
+    int64_t ce = 0, ci = 0, cm = 0;
+    for (int r = 0; r < R; ++r) {
+      if (tid == 0 || E[r] >= S - tid + 1) {
+        ce += s_cnt[0][r];
+        ci += s_cnt[1][r];
+        cm += s_cnt[2][r];
+      }
+    }
+    counts[0 * MAX_S + tid] = ce;
+    counts[1 * MAX_S + tid] = ci;
+    counts[2 * MAX_S + tid] = cm;
+  }
+  if (tid == 0) {
+    level_minmax[0] = s_min;
+    level_minmax[1] = s_max;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CFL step size: min over elements of h_e / max_nodes(|v1| + |v2| + 2c).
+constexpr int DT_THREADS = 256;
+
+__global__ void __launch_bounds__(DT_THREADS) k_dt_partial(int64_t n_nodes, const double* __restrict__ U,
+                                                            const int32_t* __restrict__ level, double length,
+                                                            double gamma, double* block_min) {
+  __shared__ double s[DT_THREADS / 32];
+  double best = INFINITY;
+  for (int64_t q = (int64_t)blockIdx.x * DT_THREADS + threadIdx.x; q < n_nodes; q += (int64_t)gridDim.x * DT_THREADS) {
+    const int64_t e = q / NODES;
+    const int t = (int)(q - e * NODES);
+    const double* u = U + e * ELEM + t;
+    const double rho = u[0], ir = 1.0 / rho;
+    const double v1 = u[NODES] * ir, v2 = u[2 * NODES] * ir;
+    const double p = (gamma - 1.0) * (u[3 * NODES] - 0.5 * rho * (v1 * v1 + v2 * v2));
+    const double c = sqrt(gamma * p * ir);
+    const double lam = fabs(v1) + fabs(v2) + 2.0 * c;
+    const double h = ldexp(length, -level[e]);
+    best = fmin(best, h / lam);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < DT_THREADS / 32 ? s[threadIdx.x] : INFINITY;
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (threadIdx.x == 0) block_min[blockIdx.x] = best;
+  }
+}
+
+__global__ void k_dt_final(int n, const double* block_min, double* out) {
+  double best = INFINITY;
+  for (int q = threadIdx.x; q < n; q += 32) best = fmin(best, block_min[q]);
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (threadIdx.x == 0) *out = best;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
+                             const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
+                             int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
+                             int64_t* counts, int32_t* level_minmax) {
+  k_partition<<<1, PART_THREADS, 0, st>>>(n_elem, n_if, n_mort, level, if_raw, mort_raw, R, S, E, method,
+                                          elem_sorted, if_sorted, mort_sorted, counts, level_minmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+                         const int4* morts, const int32_t* method, const StageArgs& sa, double* surf) {
+  const int64_t bi = (n_if + IF_PER_BLOCK - 1) / IF_PER_BLOCK;
+  const int64_t bm = (n_mort + MORT_PER_BLOCK - 1) / MORT_PER_BLOCK;
+  if (bi + bm == 0) return cudaSuccess;
+  if (ysrc == Y_GIVEN)
+    k_faces<Y_GIVEN><<<(unsigned)(bi + bm), FACE_THREADS, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, method, sa, surf);
+  else
+    k_faces<Y_COMBINE><<<(unsigned)(bi + bm), FACE_THREADS, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, method, sa,
+                                                                     surf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
+                          const int32_t* level, const int32_t* method, double two_over_len, const StageArgs& sa,
+                          const double* surf, double* K, const UpdateArgs* check) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + VOL_ELEMS - 1) / VOL_ELEMS);
+  UpdateArgs ua{};
+  if (check) ua = *check;
+  if (ysrc == Y_GIVEN)
+    k_volume<Y_GIVEN, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K, ua);
+  else if (check)
+    k_volume<Y_COMBINE, true><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K, ua);
+  else
+    k_volume<Y_COMBINE, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
+                                                                ua);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua, const double* Ks, const double* dt,
+                          double* U) {
+  const int64_t n2 = n_elem * ELEM / 2;
+  if (n2 == 0) return cudaSuccess;
+  int64_t blocks = (n2 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_commit<<<(unsigned)blocks, 256, 0, st>>>(n2, ua, reinterpret_cast<const double2*>(Ks), dt,
+                                             reinterpret_cast<double2*>(U));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_scalar(cudaStream_t st, double* p, double v) {
+  k_set_scalar<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level, double length,
+                      double gamma, double* block_min, int n_blocks, double* out) {
+  k_dt_partial<<<n_blocks, DT_THREADS, 0, st>>>(n_elem * NODES, U, level, length, gamma, block_min);
+  k_dt_final<<<1, 32, 0, st>>>(n_blocks, block_min, out);
+  return cudaGetLastError();
+}
+
+}  // namespace perk

@@ -1,0 +1,103 @@
+"""CPU tests of libperk's host side: the library loads, exports every entry
+point of include/perk.h, and its host utilities (reference nodes, disk-polynomial
+tableau, quadtree connectivity) agree with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.lgl import lgl_nodes_weights
+from oracle.perk import disk_polynomial_alpha, perk2_family, perk2_free_coefficients
+from oracle.treemesh import TreeMesh
+from perk_inputs import kh_band_cells, uniform_cells, vortex_two_level_cells
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_05144_gb300.build import build
+    build()
+    from paper_2403_05144_gb300 import _lib
+    return _lib.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "perk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(perk_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2403_05144_gb300._lib import SIGNATURES
+    assert sorted(n for n, _, _ in SIGNATURES) == declared_symbols()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 7])
+def test_reference_nodes_match_oracle(lib, N):
+    from paper_2403_05144_gb300 import reference_nodes
+    x, w = reference_nodes(N)
+    xo, wo = lgl_nodes_weights(N)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=2e-16)
+    np.testing.assert_allclose(w, wo, rtol=0, atol=4e-16)
+
+
+@pytest.mark.parametrize("E_list", [[4, 8], [8, 16], [4, 6, 10, 16], [2, 3, 5], [6]])
+def test_disk_tableau_matches_oracle(lib, E_list):
+    from paper_2403_05144_gb300 import perk2_disk_tableau
+    c, a = perk2_disk_tableau(E_list)
+    fam = perk2_family(E_list)
+    np.testing.assert_allclose(c, fam.c, rtol=0, atol=1e-16)
+    for r, E in enumerate(E_list):
+        free = perk2_free_coefficients(fam.S, E, disk_polynomial_alpha(E))   # 1-based stage index
+        # a[r, i] = a_{i+1, i} (1-based), i.e. free[i + 1]
+        np.testing.assert_allclose(a[r, 1:], free[2:], rtol=2e-15, atol=0)
+
+
+def _faces_as_sets(cells):
+    from paper_2403_05144_gb300 import mesh_faces
+    ifs, ms = mesh_faces(cells)
+    conf = {(int(a), int(b), int(d)) for a, b, d, _ in ifs}
+    hang = set()
+    for large, s0, s1, w in ms:
+        d, side = int(w & 1), int((w >> 1) & 1)
+        for half, s in ((0, s0), (1, s1)):
+            A, B = (int(large), int(s)) if side == 0 else (int(s), int(large))
+            hang.add((A, B, d, int(large), half))
+    return conf, hang, len(ifs), len(ms)
+
+
+@pytest.mark.parametrize("cells_fn", [lambda: vortex_two_level_cells(), lambda: kh_band_cells(4, 7),
+                                      lambda: uniform_cells(2), lambda: [(0, 0, 0)],
+                                      lambda: vortex_two_level_cells(3, 2, 6)])
+def test_connectivity_matches_geometric_matching(lib, cells_fn):
+    cells = cells_fn()
+    conf, hang, n_if, n_m = _faces_as_sets(cells)
+    m = TreeMesh(cells, 0.0, 1.0)
+    assert n_if == len(m.conforming) and conf == set(m.conforming)
+    assert 2 * n_m == len(m.hanging) and hang == set(m.hanging)
+
+
+def test_connectivity_rejects_bad_meshes(lib):
+    from paper_2403_05144_gb300 import PerkError, mesh_faces
+    with pytest.raises(PerkError):
+        mesh_faces([(1, 0, 0), (1, 1, 0), (1, 0, 1)])                 # does not tile
+    with pytest.raises(PerkError):
+        mesh_faces([(1, 0, 0), (1, 1, 0), (1, 0, 1), (1, 1, 1), (1, 1, 1)])   # duplicate
+    # a level-1 cell next to level-3 cells: not 2:1 balanced
+    cells = [(1, 0, 0), (1, 0, 1), (1, 1, 1)]
+    for ix in range(4, 8):
+        for iy in range(0, 4):
+            if ix < 6 or iy >= 2:
+                cells.append((3, ix, iy))
+    cells += [(2, 3, 0)]
+    with pytest.raises(PerkError):
+        mesh_faces(cells)
