@@ -163,6 +163,24 @@ typedef struct {
 } perk_counters;
 perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out);
 
+/* Per-kernel timing of one step (tracing).  Runs the step like perk_step but
+ * without a graph, with CUDA events recorded on the context's stream around
+ * every launch, and blocks until the step is done.  Kernel kinds:
+ * 0 = face fluxes, 1 = volume integral, 2 = final update.  ms[k] and
+ * launches[k] are accumulated (not reset) so a caller can sum over steps. */
+typedef struct {
+  double ms[4];
+  int64_t launches[4];
+  int64_t element_stages; /* active elements summed over the profiled stages */
+} perk_kernel_times;
+perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kernel_times* acc);
+
+/* Throughput of the FP64 units of the current device, measured by short
+ * microbenchmarks (~0.3 s): dependent-free FMA chains (returns FLOP/s, an FMA
+ * counted as 2), and the division and natural-logarithm rates of CUDA's FP64
+ * implementations (operations/s).  Blocks. */
+perk_status perk_measure_fp64(double* fma_flops, double* div_per_s, double* log_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ import numpy as np
 from . import _lib
 from ._lib import PerkError
 
-__all__ = ["PerkSolver", "PerkError", "reference_nodes", "perk2_disk_tableau", "mesh_faces"]
+__all__ = ["PerkSolver", "PerkError", "reference_nodes", "perk2_disk_tableau", "mesh_faces", "measure_fp64"]
 
 
 def _check(lib, ctx, status: int):
@@ -59,6 +59,14 @@ def mesh_faces(cells):
     _check(lib, None, lib.perk_mesh_faces(len(arr), cp, C.byref(ni), ifs.ctypes.data_as(C.POINTER(C.c_int32)),
                                           ni.value, C.byref(nm), ms.ctypes.data_as(C.POINTER(C.c_int32)), nm.value))
     return ifs, ms
+
+
+def measure_fp64():
+    """Measured FP64 rates of the current device: (FMA flop/s, divisions/s, logarithms/s)."""
+    lib = _lib.load()
+    f, d, l = C.c_double(), C.c_double(), C.c_double()
+    _check(lib, None, lib.perk_measure_fp64(C.byref(f), C.byref(d), C.byref(l)))
+    return f.value, d.value, l.value
 
 
 def _ptr(t) -> int:
@@ -165,6 +173,13 @@ class PerkSolver:
         U = self._state(U)
         self._call(self.lib.perk_step, C.c_void_p(_ptr(U)), C.c_double(dt))
         return U
+
+    def step_profiled(self, U, dt: float, acc=None):
+        """One step with per-kernel CUDA-event timing; returns the accumulated times."""
+        U = self._state(U)
+        acc = acc if acc is not None else _lib.PerkKernelTimes()
+        self._call(self.lib.perk_step_profiled, C.c_void_p(_ptr(U)), C.c_double(dt), C.byref(acc))
+        return acc
 
     def check(self):
         self._call(self.lib.perk_check)

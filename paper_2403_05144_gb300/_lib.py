@@ -33,6 +33,10 @@ class PerkCounters(C.Structure):
                 ("rejected_steps_checked", C.c_int64)]
 
 
+class PerkKernelTimes(C.Structure):
+    _fields_ = [("ms", C.c_double * 4), ("launches", C.c_int64 * 4), ("element_stages", C.c_int64)]
+
+
 # (name, restype, argtypes) for every entry point of include/perk.h
 SIGNATURES = [
     ("perk_create", C.c_int, [C.POINTER(PerkProblem), C.POINTER(C.c_void_p)]),
@@ -55,6 +59,8 @@ SIGNATURES = [
     ("perk_check", C.c_int, [C.c_void_p]),
     ("perk_compute_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
+    ("perk_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
+    ("perk_measure_fp64", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 ]
 
 _lib = None

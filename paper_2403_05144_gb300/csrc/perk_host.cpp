@@ -380,8 +380,40 @@ perk_status run_partition(perk_ctx* ctx) {
   return PERK_OK;
 }
 
+// CUDA events around individual launches (perk_step_profiled)
+struct LaunchTimer {
+  std::vector<cudaEvent_t> start, stop;
+  std::vector<int> kind;
+  cudaError_t begin(cudaStream_t st) {
+    cudaEvent_t a;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    start.push_back(a);
+    return cudaEventRecord(a, st);
+  }
+  cudaError_t end(cudaStream_t st, int k) {
+    cudaEvent_t b;
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    stop.push_back(b);
+    kind.push_back(k);
+    return cudaEventRecord(b, st);
+  }
+  ~LaunchTimer() {
+    for (auto e : start) cudaEventDestroy(e);
+    for (auto e : stop) cudaEventDestroy(e);
+  }
+};
+
+#define TIMED(ctx, timer, st, kind, call)            \
+  do {                                               \
+    if (timer) PERK_CUDA(ctx, (timer)->begin(st));   \
+    PERK_CUDA(ctx, call);                            \
+    if (timer) PERK_CUDA(ctx, (timer)->end(st, kind)); \
+  } while (0)
+
 // the stage launches of one step on stream st (also used under graph capture)
-perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U) {
+perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTimer* timer = nullptr) {
   const int S = ctx->S;
   double* Kbuf[3] = {ctx->d_K1.p, ctx->d_Ka.p, ctx->d_Kb.p};
   int prev = 0, cur = 0, prev_at_last = 0;
@@ -407,19 +439,20 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U) {
     sa.Kp = Kbuf[prev];
     sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
     sa.dt = ctx->d_dt.p;
-    PERK_CUDA(ctx, launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
-                                ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
+    TIMED(ctx, timer, st, 0,
+          launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
+                       ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     const bool last = (i == S - 1);
     if (last) prev_at_last = prev;
     UpdateArgs chk = ua;
     chk.Kp = Kbuf[prev];
-    PERK_CUDA(ctx, launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                                 ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur],
-                                 last ? &chk : nullptr));
+    TIMED(ctx, timer, st, 1,
+          launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
+                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur], last ? &chk : nullptr));
     prev = cur;
   }
   ua.Kp = Kbuf[prev_at_last];  // K_{S-1}
-  PERK_CUDA(ctx, launch_commit(st, ctx->n_elem, ua, Kbuf[cur], ctx->d_dt.p, d_U));
+  TIMED(ctx, timer, st, 2, launch_commit(st, ctx->n_elem, ua, Kbuf[cur], ctx->d_dt.p, d_U));
   return PERK_OK;
 }
 
@@ -726,6 +759,34 @@ perk_status perk_step(perk_ctx* ctx, double* d_U, double dt) {
     perk_status s = enqueue_step(ctx, ctx->stream, d_U);
     if (s != PERK_OK) return s;
   }
+  ctx->counters.steps += 1;
+  for (int i = 0; i < ctx->S; ++i) {
+    ctx->counters.element_stage_evaluations += ctx->act_el[i];
+    ctx->counters.dof_stage_updates += ctx->act_el[i] * NODES;
+  }
+  return PERK_OK;
+}
+
+perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kernel_times* acc) {
+  if (!ctx || !acc) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
+    return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
+  if (!d_U || !std::isfinite(dt) || !(dt > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or dt");
+  if (!(dt == ctx->cur_dt)) {
+    PERK_CUDA(ctx, launch_set_scalar(ctx->stream, ctx->d_dt.p, dt));
+    ctx->cur_dt = dt;
+  }
+  LaunchTimer timer;
+  perk_status s = enqueue_step(ctx, ctx->stream, d_U, &timer);
+  if (s != PERK_OK) return s;
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (size_t q = 0; q < timer.stop.size(); ++q) {
+    float ms = 0.f;
+    PERK_CUDA(ctx, cudaEventElapsedTime(&ms, timer.start[q], timer.stop[q]));
+    acc->ms[timer.kind[q]] += ms;
+    acc->launches[timer.kind[q]] += 1;
+  }
+  for (int i = 0; i < ctx->S; ++i) acc->element_stages += ctx->act_el[i];
   ctx->counters.steps += 1;
   for (int i = 0; i < ctx->S; ++i) {
     ctx->counters.element_stage_evaluations += ctx->act_el[i];
