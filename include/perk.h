@@ -181,6 +181,25 @@ perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kerne
  * implementations (operations/s).  Blocks. */
 perk_status perk_measure_fp64(double* fma_flops, double* div_per_s, double* log_per_s);
 
+/* Allocation-free step size (no counterpart in the paper).  Computes the same
+ * dt as perk_compute_dt, without a context and without allocating any device
+ * memory, for callers that must not allocate: e.g. a solver invoked as a
+ * custom call inside another framework that owns the device memory and its
+ * allocator, where a cudaMalloc would bypass that pool and synchronise the
+ * device.  Inputs: d_U as everywhere (device), d_level[n_elem] the refinement
+ * level of each cell (device, int32), the domain length, gamma and cfl.
+ * Output: *dt (host).  Runs on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and blocks until the result is on the host.
+ * Scratch: a file-scope device array of 64 KiB + 8 B that every GPU which
+ * loads the library holds until the process exits; n_elem may not exceed
+ * PERK_NOALLOC_MAX_ELEM (else INVALID_ARG).  The first call on a device looks
+ * the array's device address up (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the one array, so calls that
+ * overlap on the GPU (other streams, other host threads) race; serialise them. */
+#define PERK_NOALLOC_MAX_ELEM 131072
+perk_status perk_compute_dt_noalloc(const double* d_U, const int32_t* d_level, int64_t n_elem, double length,
+                                    double gamma, double cfl, void* stream, double* dt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("perk_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
     ("perk_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
     ("perk_measure_fp64", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk_compute_dt_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                          C.c_void_p, C.POINTER(C.c_double)]),
 ]
 
 _lib = None

@@ -472,6 +472,8 @@ perk_status upload_coef(perk_ctx* ctx) {
 
 }  // namespace
 
+perk_status perk::set_context_free_error(perk_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }
+
 // ---------------------------------------------------------------------------
 extern "C" {
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "perk.h"
+
 namespace perk {
 
 constexpr int NN = 4;             // LGL nodes per direction (N = 3)
@@ -73,6 +75,9 @@ cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua,
                           double* U);
 
 cudaError_t launch_set_scalar(cudaStream_t st, double* p, double v);
+
+// Records the message of a failed context-free call (read by perk_last_error(NULL)).
+perk_status set_context_free_error(perk_status s, const char* msg);
 
 cudaError_t launch_dt(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level, double length,
                       double gamma, double* block_min, int n_blocks, double* out);
