@@ -40,12 +40,14 @@ from perk_inputs import isentropic_vortex, kelvin_helmholtz, kh_band_cells, noda
 METRIC = "P-ERK DoF-stage updates/s and wall time to t_end vs full-RK on same GB300"
 UNIT = "DoF-stage updates/s"
 
-# Per-element-stage work of the volume kernel (flux differencing + lifting +
-# combiner) in the library's formulation: plain FP64 operations (add, mul,
-# FMA, compare: one FP64 issue slot each), divisions and logarithms.
-VOL_PLAIN_PER_ELEM = 16 * 16 + 48 * 51 + 16 * 6 * 4 + 128 + 16 * 10
-VOL_DIV_PER_ELEM = 16 * 2 + 48 * 2
-VOL_LOG_PER_ELEM = 16 * 2
+# FP64 issue slots of one element-stage of the volume kernel (flux
+# differencing + surface lifting + stage combination) in the library's
+# formulation (add, mul, FMA, compare = 1 slot; reciprocal = 4 FMA after the
+# approximate seed; table logarithm = 15 slots):
+#   16 nodes x 60   (combination 10, pressure 5, reciprocal 5, primitives 10, two logarithms 30)
+# + 48 pairs x 44   (means' branches 9, reciprocal 5, quotients 3, two log-mean series 15, flux 12)
+# + 16 nodes x 6 pairs x 4 variables (accumulation) + 128 (lifting, Jacobian)
+VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
 
 
 def workload(name: str) -> dict:
@@ -254,7 +256,7 @@ def run_perk(args) -> None:
     # roofline of the volume kernel: per-launch CUDA events over K profiled steps
     fma_flops, div_s, log_s = measure_fp64()
     slot_rate = fma_flops / 2.0
-    slots_per_elem = VOL_PLAIN_PER_ELEM + VOL_DIV_PER_ELEM * slot_rate / div_s + VOL_LOG_PER_ELEM * slot_rate / log_s
+    slots_per_elem = VOL_SLOTS_PER_ELEM
     Up = Ud.clone()
     acc = None
     for _ in range(args.steps):
@@ -306,10 +308,10 @@ def run_perk(args) -> None:
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
-                     "work_per_element_stage": {"fp64_plain": VOL_PLAIN_PER_ELEM, "div": VOL_DIV_PER_ELEM,
-                                                "log": VOL_LOG_PER_ELEM,
-                                                "fma_slots_per_div": slot_rate / div_s,
-                                                "fma_slots_per_log": slot_rate / log_s}},
+                     "work_per_element_stage": {"fp64_slots": VOL_SLOTS_PER_ELEM,
+                                                "flops": 2 * VOL_SLOTS_PER_ELEM,
+                                                "note": "FMA-equivalent: every FP64 issue slot counted as 2 flops"},
+                     "cuda_fp64_rates": {"div_per_s": div_s, "log_per_s": log_s}},
         "e2e": {"value": world * dof_step * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": args.steps * (2 * S + 1),

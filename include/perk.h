@@ -175,6 +175,12 @@ typedef struct {
 } perk_kernel_times;
 perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kernel_times* acc);
 
+/* Diagnostics: the volume kernel's own logarithm and reciprocal (table-driven
+ * logarithm after Tang 1990; Newton-Raphson reciprocal) evaluated on d_x[n]
+ * (device, positive normal values): d_out[2q] = ln x_q, d_out[2q+1] = 1/x_q
+ * (device, 2n doubles).  For testing their error against reference values. */
+perk_status perk_selftest_math(perk_ctx* ctx, int64_t n, const double* d_x, double* d_out);
+
 /* Throughput of the FP64 units of the current device, measured by short
  * microbenchmarks (~0.3 s): dependent-free FMA chains (returns FLOP/s, an FMA
  * counted as 2), and the division and natural-logarithm rates of CUDA's FP64

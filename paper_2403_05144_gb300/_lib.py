@@ -59,6 +59,7 @@ SIGNATURES = [
     ("perk_check", C.c_int, [C.c_void_p]),
     ("perk_compute_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
+    ("perk_selftest_math", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("perk_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
     ("perk_measure_fp64", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_compute_dt_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double,

@@ -172,6 +172,19 @@ Ops build_ops(double gamma, int surface_flux) {
   return o;
 }
 
+// Table of the volume kernel's logarithm: inv_c[j] = fl(1/c_j), c_j = 1 + (j + 1/2)/128,
+// and ln_c[j] = -ln(inv_c[j]) evaluated in extended precision, then rounded.
+std::vector<double> log_table() {
+  std::vector<double> t(2 * LOG_TABLE_SIZE);
+  for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
+    const long double c = 1.0L + (j + 0.5L) / LOG_TABLE_SIZE;
+    const double inv = (double)(1.0L / c);
+    t[j] = inv;
+    t[LOG_TABLE_SIZE + j] = (double)(-logl((long double)inv));
+  }
+  return t;
+}
+
 template <class T>
 struct DevBuf {
   T* p = nullptr;
@@ -228,6 +241,7 @@ struct perk_ctx {
   DevBuf<double> d_surf, d_K1, d_Ka, d_Kb, d_dt, d_block_min, d_dt_out;
   DevBuf<StageCoef> d_coef;
   DevBuf<int> d_flag;
+  DevBuf<double> d_logtab;   // table of the volume kernel's logarithm
 
   // graph of one step
   cudaGraphExec_t graph = nullptr;
@@ -448,7 +462,8 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
     chk.Kp = Kbuf[prev];
     TIMED(ctx, timer, st, 1,
           launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur], last ? &chk : nullptr));
+                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur], last ? &chk : nullptr,
+                        ctx->d_logtab.p));
     prev = cur;
   }
   ua.Kp = Kbuf[prev_at_last];  // K_{S-1}
@@ -489,13 +504,21 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   ctx->ops = build_ops(prob->gamma, prob->surface_flux);
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
+      ctx->d_logtab.ensure(2 * LOG_TABLE_SIZE) != cudaSuccess ||
       ctx->d_counts.ensure(3 * MAX_S) != cudaSuccess || ctx->d_minmax.ensure(2) != cudaSuccess ||
       ctx->d_dt_out.ensure(1) != cudaSuccess) {
     perk_destroy(ctx);
     return PERK_E_CUDA;
   }
   cudaMemset(ctx->d_flag.p, 0, sizeof(int));
-  cudaDeviceSynchronize();
+  {
+    const std::vector<double> t = log_table();
+    cudaMemcpy(ctx->d_logtab.p, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    perk_destroy(ctx);
+    return PERK_E_CUDA;
+  }
   *out = ctx;
   return PERK_OK;
 }
@@ -523,6 +546,7 @@ void perk_destroy(perk_ctx* ctx) {
   ctx->d_dt_out.release();
   ctx->d_coef.release();
   ctx->d_flag.release();
+  ctx->d_logtab.release();
   delete ctx;
 }
 
@@ -713,7 +737,7 @@ static perk_status rhs_given(perk_ctx* ctx, int stage, const double* d_Y, double
   PERK_CUDA(ctx, launch_faces(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
                               ctx->d_method.p, sa, ctx->d_surf.p));
   PERK_CUDA(ctx, launch_volume(ctx->stream, Y_GIVEN, ctx->ops, ne, ctx->d_elem_sorted.p, ctx->d_level.p,
-                               ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr));
+                               ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr, ctx->d_logtab.p));
   return PERK_OK;
 }
 
@@ -822,6 +846,12 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
   PERK_CUDA(ctx, cudaMemcpyAsync(&m, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *dt = cfl * m / (double)NN;
+  return PERK_OK;
+}
+
+perk_status perk_selftest_math(perk_ctx* ctx, int64_t n, const double* d_x, double* d_out) {
+  if (!ctx || !d_x || !d_out || n < 0) return PERK_E_INVALID_ARG;
+  PERK_CUDA(ctx, launch_selftest_math(ctx->stream, n, d_x, d_out, ctx->d_logtab.p));
   return PERK_OK;
 }
 

@@ -69,7 +69,11 @@ cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t 
 
 cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
                           const int32_t* level, const int32_t* method, double inv_len2, const StageArgs& sa,
-                          const double* surf, double* K, const UpdateArgs* check);
+                          const double* surf, double* K, const UpdateArgs* check, const double* log_table);
+
+// log_table: [inv_c[128], ln_c[128]] of the volume kernel's logarithm (see perk_kernels.cu)
+constexpr int LOG_TABLE_SIZE = 128;
+cudaError_t launch_selftest_math(cudaStream_t st, int64_t n, const double* x, double* out, const double* log_table);
 
 cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua, const double* Ks, const double* dt,
                           double* U);

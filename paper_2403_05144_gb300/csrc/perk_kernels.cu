@@ -12,8 +12,8 @@
 // All arithmetic is FP64.  The FP64 pipe of GB300 is the binding resource of
 // the volume kernel, so it evaluates every symmetric node pair once (48 pairs
 // per element instead of 96 one-sided evaluations), takes the logarithms of
-// density and rho/p once per node, and forms each logarithmic mean with one
-// division.
+// density and rho/p once per node (table-driven), and forms both logarithmic
+// means of a pair from one Newton-Raphson reciprocal.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -25,7 +25,8 @@
 namespace perk {
 
 // ---------------------------------------------------------------------------
-// Logarithmic mean from per-node logarithms.
+// Logarithmic mean from per-node logarithms (used by the EC surface flux; the
+// volume kernel uses the cheaper forms further below).
 //
 // With d = b - a, s = a + b, f = d/s and u = f^2:  ln(b/a) = 2 artanh(f)
 // = 2 f A(u), A(u) = sum_k u^k / (2k+1).  Hence
@@ -72,6 +73,136 @@ __device__ __forceinline__ double inv_ln_mean(double a, double b, double lna, do
     return 2.0 * is * series_A(f * f);
   }
   return (lnb - lna) / d;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 building blocks of the volume kernel, written to spend few FP64 issue
+// slots (GB300 issues ~2 FP64 FMAs per clock per SM).
+
+// Reciprocal: two Newton-Raphson steps y <- y + y (1 - x y) from the hardware's
+// approximate reciprocal (PTX rcp.approx.ftz.f64); the relative error is
+// squared by each step, which brings the seed to full double precision
+// (within ~1 ulp, not correctly rounded).  Positive normal x only.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// Natural logarithm, table-driven (P. T. P. Tang, "Table-driven implementation
+// of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16,
+// 1990): x = 2^k m, m in [1, 2); with c_j the midpoint of the j-th of 128
+// mantissa intervals, ln x = k ln 2 + ln(1/inv_c[j]) + ln(1 + r),
+// r = m inv_c[j] - 1 (|r| < 2^-8), ln(1 + r) by its Taylor series to r^8.
+// The table (inv_c[j] = fl(1/c_j), ln_c[j] = -ln(inv_c[j]) rounded from
+// extended precision) is built on the host.  Positive normal x; any other
+// input returns NaN.
+constexpr int LOG_TABLE = 128;
+constexpr double LN2_HI = 0.6931471805599453;
+constexpr double LN2_LO = 2.3190468138462996e-17;
+
+__device__ __forceinline__ double log_tab(double x, const double* __restrict__ inv_c,
+                                          const double* __restrict__ ln_c) {
+  const long long bits = __double_as_longlong(x);
+  const int hi = (int)(bits >> 32);
+  const int j = (hi >> 13) & (LOG_TABLE - 1);
+  const long long eb = (bits >> 52) & 0x7FF;
+  const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  // k as a double without an int->double conversion: 2^52 + eb, minus 2^52 + 1023
+  const double kd = __longlong_as_double(0x4330000000000000LL | eb) - (4503599627370496.0 + 1023.0);
+  const double r = fma(m, inv_c[j], -1.0);
+  double q = -1.0 / 8.0;
+  q = fma(q, r, 1.0 / 7.0);
+  q = fma(q, r, -1.0 / 6.0);
+  q = fma(q, r, 1.0 / 5.0);
+  q = fma(q, r, -1.0 / 4.0);
+  q = fma(q, r, 1.0 / 3.0);
+  q = fma(q, r, -0.5);
+  const double l1p = fma(r * r, q, r);
+  const double v = fma(kd, LN2_HI, ln_c[j] + fma(kd, LN2_LO, l1p));
+  return x > 0.0 ? v : __longlong_as_double(0x7FF8000000000000LL);
+}
+
+// Node quantities of the two-point flux (half values fold the 1/2 of the means).
+struct NodeQ {
+  double rho, lnrho, beta, lnbeta, v1, v2, hv1, hv2, hp;
+};
+
+__device__ __forceinline__ NodeQ node_q(const double u[4], double gm1, const double* inv_c, const double* ln_c) {
+  NodeQ q;
+  // rho p = (gamma - 1) (rho E - |m|^2 / 2) needs no division; one reciprocal gives 1/rho and 1/p
+  const double rp = gm1 * fma(u[0], u[3], -0.5 * fma(u[1], u[1], u[2] * u[2]));
+  const double r = rcp_nr(u[0] * rp);        // 1 / (rho^2 p)
+  const double ir = rp * r;                  // 1 / rho
+  q.rho = u[0];
+  q.v1 = u[1] * ir;
+  q.v2 = u[2] * ir;
+  q.hp = 0.5 * (rp * ir);                    // p / 2
+  q.beta = (u[0] * u[0]) * (u[0] * r);       // rho / p
+  q.hv1 = 0.5 * q.v1;
+  q.hv2 = 0.5 * q.v2;
+  q.lnrho = log_tab(u[0], inv_c, ln_c);
+  q.lnbeta = log_tab(q.beta, inv_c, ln_c);
+  return q;
+}
+
+// Series of the logarithmic mean in u = f^2, f = (b - a)/(b + a), used when |f| < 0.03:
+//   ln(b/a) = 2 f A(u),  A(u) = sum_k u^k / (2k+1);   {{x}}_ln = (a + b) / (2 A(u)) = (a + b) H(u)
+// with H = 1/(2A) expanded term by term (exact rationals); truncation below 2e-17 relative.
+__device__ __forceinline__ double series_H(double u) {
+  double r = -5098.0 / 467775.0;
+  r = fma(r, u, -214.0 / 14175.0);
+  r = fma(r, u, -22.0 / 945.0);
+  r = fma(r, u, -2.0 / 45.0);
+  r = fma(r, u, -1.0 / 6.0);
+  return fma(r, u, 0.5);
+}
+__device__ __forceinline__ double series_2A(double u) {
+  double r = 2.0 / 11.0;
+  r = fma(r, u, 2.0 / 9.0);
+  r = fma(r, u, 2.0 / 7.0);
+  r = fma(r, u, 2.0 / 5.0);
+  r = fma(r, u, 2.0 / 3.0);
+  return fma(r, u, 2.0);
+}
+
+// Ranocha's two-point flux from NodeQ: one reciprocal serves both logarithmic means.
+__device__ __forceinline__ void ec_flux_q(const NodeQ& A, const NodeQ& B, int dir, double inv_gm1, double f[4]) {
+  const double dr = B.rho - A.rho, sr = A.rho + B.rho;
+  const double db = B.beta - A.beta, sb = A.beta + B.beta;
+  const bool ser_r = fabs(dr) < 0.03 * sr;
+  const bool ser_b = fabs(db) < 0.03 * sb;
+  const double den_r = ser_r ? sr : B.lnrho - A.lnrho;
+  const double den_b = ser_b ? sb : db;
+  const double r = rcp_nr(den_r * den_b);
+  const double qr = den_b * r;               // 1 / den_r
+  const double qb = den_r * r;               // 1 / den_b
+  const double fr = dr * qr;
+  double rho_ln, ibeta;
+  if (ser_r)
+    rho_ln = sr * series_H(fr * fr);
+  else
+    rho_ln = fr;
+  if (ser_b) {
+    const double fb = db * qb;
+    ibeta = qb * series_2A(fb * fb);
+  } else {
+    ibeta = (B.lnbeta - A.lnbeta) * qb;
+  }
+  const double v1m = A.hv1 + B.hv1;
+  const double v2m = A.hv2 + B.hv2;
+  const double pm = A.hp + B.hp;
+  const double vnA = dir ? A.v2 : A.v1;
+  const double vnB = dir ? B.v2 : B.v1;
+  const double frho = rho_ln * (dir ? v2m : v1m);
+  f[0] = frho;
+  f[1] = fma(frho, v1m, dir ? 0.0 : pm);
+  f[2] = fma(frho, v2m, dir ? pm : 0.0);
+  const double kin = fma(A.hv1, B.v1, A.hv2 * B.v2);
+  f[3] = fma(frho, fma(ibeta, inv_gm1, kin), fma(A.hp, vnB, B.hp * vnA));
 }
 
 // Ranocha's entropy-conservative, kinetic-energy-preserving two-point flux in
@@ -324,9 +455,13 @@ __global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, cons
                                                          const int32_t* __restrict__ level,
                                                          const int32_t* __restrict__ method, double two_over_len,
                                                          StageArgs sa, const double* __restrict__ surf,
-                                                         double* __restrict__ K, UpdateArgs ua) {
-  __shared__ Prim s_prim[VOL_ELEMS][NODES];
+                                                         double* __restrict__ K, UpdateArgs ua,
+                                                         const double* __restrict__ log_table) {
+  __shared__ NodeQ s_prim[VOL_ELEMS][NODES];
   __shared__ double s_flux[VOL_ELEMS][4][NPAIR];
+  __shared__ double s_log[2 * LOG_TABLE];
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_THREADS) s_log[q] = log_table[q];
+  __syncthreads();
   const int le = threadIdx.x >> 4;
   const int t = threadIdx.x & 15;
   const int i = t & 3, j = t >> 2;
@@ -341,7 +476,7 @@ __global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, cons
   } else {
     y[0] = 1.0; y[1] = 0.0; y[2] = 0.0; y[3] = 2.5;
   }
-  s_prim[le][t] = prim_from_cons(y, ops.gm1);
+  s_prim[le][t] = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE);
   __syncwarp();
 
   // the three pairs of this thread: slots t, t + 16, t + 32 of 48
@@ -356,7 +491,7 @@ __global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, cons
     const int na = dir ? a * 4 + line : line * 4 + a;
     const int nb = dir ? b * 4 + line : line * 4 + b;
     double f[4];
-    ec_flux(s_prim[le][na], s_prim[le][nb], dir, ops.inv_gm1, f);
+    ec_flux_q(s_prim[le][na], s_prim[le][nb], dir, ops.inv_gm1, f);
 #pragma unroll
     for (int v = 0; v < 4; ++v) s_flux[le][v][p] = f[v];
   }
@@ -653,18 +788,35 @@ cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t 
 
 cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
                           const int32_t* level, const int32_t* method, double two_over_len, const StageArgs& sa,
-                          const double* surf, double* K, const UpdateArgs* check) {
+                          const double* surf, double* K, const UpdateArgs* check, const double* log_table) {
   if (n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + VOL_ELEMS - 1) / VOL_ELEMS);
   UpdateArgs ua{};
   if (check) ua = *check;
   if (ysrc == Y_GIVEN)
-    k_volume<Y_GIVEN, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K, ua);
+    k_volume<Y_GIVEN, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
+                                                              ua, log_table);
   else if (check)
-    k_volume<Y_COMBINE, true><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K, ua);
+    k_volume<Y_COMBINE, true><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
+                                                               ua, log_table);
   else
     k_volume<Y_COMBINE, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
-                                                                ua);
+                                                                ua, log_table);
+  return cudaGetLastError();
+}
+
+// Diagnostics: the volume kernel's logarithm and reciprocal on n inputs.
+__global__ void k_selftest_math(int64_t n, const double* __restrict__ x, double* __restrict__ out,
+                                const double* __restrict__ log_table) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  out[2 * q] = log_tab(x[q], log_table, log_table + LOG_TABLE);
+  out[2 * q + 1] = rcp_nr(x[q]);
+}
+
+cudaError_t launch_selftest_math(cudaStream_t st, int64_t n, const double* x, double* out, const double* log_table) {
+  if (n <= 0) return cudaSuccess;
+  k_selftest_math<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, out, log_table);
   return cudaGetLastError();
 }
 
