@@ -163,6 +163,39 @@ typedef struct {
 } perk_counters;
 perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out);
 
+/* Adaptive mesh refinement (Sec. 7: the AMR callback every N_AMR steps, after
+ * which the partition is re-assigned, Sec. 6.2).  Indicator: the density
+ * gradient eta_e = h_e max_nodes |grad rho| / mean_e(rho) (dimensionless).
+ * Desired level of a cell: level + 1 if eta > refine_above (below level_max),
+ * level - 1 if eta < coarsen_below (above level_min), else level; raised to
+ * the least fixed point of two rules: a cell coarsens only together with its
+ * three siblings (all leaves, all wanting to coarsen), and face neighbours of
+ * the new mesh differ by at most one level. */
+typedef struct {
+  int32_t level_min, level_max;
+  double refine_above, coarsen_below;
+} perk_amr_params;
+
+/* eta of every cell of d_U into d_eta[n_elem] (device). */
+perk_status perk_amr_indicator(perk_ctx* ctx, const double* d_U, double* d_eta);
+
+/* Plans one adaptation.  With desired == NULL the indicator of d_U and `prm`
+ * decide; otherwise desired[n_elem] (host) gives each cell's wanted level
+ * (level - 1 .. level + 1) and prm/d_U are ignored.  Either way the two rules
+ * above are then enforced.  *n_new receives the number of cells of the new
+ * mesh (its leaves are kept in Morton order).  Blocks. */
+perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int32_t* desired, const double* d_U,
+                            int64_t* n_new);
+
+/* Executes the plan: d_Unew[n_new] (device, distinct from d_Uold) receives the
+ * solution on the new leaves: copied, interpolated exactly from the parent
+ * (refined cells) or the L2 projection of the four children (coarsened
+ * cells); then the mesh is replaced and re-partitioned on the device.  Blocks. */
+perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew);
+
+/* The current leaves (host, 3 * n_elem int32: level, ix, iy), cap in cells. */
+perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap);
+
 /* Per-kernel timing of one step (tracing).  Runs the step like perk_step but
  * without a graph, with CUDA events recorded on the context's stream around
  * every launch, and blocks until the step is done.  Kernel kinds:

@@ -181,6 +181,33 @@ class PerkSolver:
         self._call(self.lib.perk_step_profiled, C.c_void_p(_ptr(U)), C.c_double(dt), C.byref(acc))
         return acc
 
+    # ------------------------------------------------------------------ AMR
+    def amr_indicator(self, U):
+        U = self._state(U)
+        eta = self.torch.empty(self.n_elem, dtype=self.torch.float64, device="cuda")
+        self._call(self.lib.perk_amr_indicator, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(eta)))
+        return eta
+
+    def adapt(self, U, level_min: int = 4, level_max: int = 7, refine_above: float = 0.1,
+              coarsen_below: float = 0.02, desired=None):
+        """One AMR cycle: returns the solution on the new mesh (a new tensor)."""
+        U = self._state(U)
+        prm = _lib.PerkAmrParams(level_min, level_max, refine_above, coarsen_below)
+        n_new = C.c_int64()
+        if desired is not None:
+            d = np.ascontiguousarray(np.asarray(desired, dtype=np.int32))
+            self._call(self.lib.perk_adapt_plan, C.byref(prm), d.ctypes.data_as(C.POINTER(C.c_int32)),
+                       C.c_void_p(_ptr(U)), C.byref(n_new))
+        else:
+            self._call(self.lib.perk_adapt_plan, C.byref(prm), None, C.c_void_p(_ptr(U)), C.byref(n_new))
+        Unew = self.torch.empty((n_new.value, 4, 4, 4), dtype=self.torch.float64, device="cuda")
+        self._call(self.lib.perk_adapt_commit, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(Unew)))
+        self.n_elem = n_new.value
+        cells = np.zeros((self.n_elem, 3), dtype=np.int32)
+        self._call(self.lib.perk_get_cells, cells.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(self.n_elem))
+        self.cells = cells
+        return Unew
+
     def check(self):
         self._call(self.lib.perk_check)
 

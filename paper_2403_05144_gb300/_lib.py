@@ -33,6 +33,11 @@ class PerkCounters(C.Structure):
                 ("rejected_steps_checked", C.c_int64)]
 
 
+class PerkAmrParams(C.Structure):
+    _fields_ = [("level_min", C.c_int32), ("level_max", C.c_int32), ("refine_above", C.c_double),
+                ("coarsen_below", C.c_double)]
+
+
 class PerkKernelTimes(C.Structure):
     _fields_ = [("ms", C.c_double * 4), ("launches", C.c_int64 * 4), ("element_stages", C.c_int64)]
 
@@ -59,6 +64,11 @@ SIGNATURES = [
     ("perk_check", C.c_int, [C.c_void_p]),
     ("perk_compute_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
+    ("perk_amr_indicator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(PerkAmrParams), C.POINTER(C.c_int32), C.c_void_p,
+                                  C.POINTER(C.c_int64)]),
+    ("perk_adapt_commit", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk_get_cells", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
     ("perk_selftest_math", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("perk_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
     ("perk_measure_fp64", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),

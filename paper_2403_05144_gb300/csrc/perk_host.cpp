@@ -220,7 +220,15 @@ struct perk_ctx {
   int64_t n_elem = 0, n_if = 0, n_mort = 0;
   double x0 = 0.0, length = 1.0;
   std::vector<int32_t> h_level;
+  std::vector<int32_t> h_cells;   // [n_elem][3] (level, ix, iy)
   std::vector<int4> h_if, h_mort;
+
+  // pending AMR plan (perk_adapt_plan -> perk_adapt_commit)
+  bool has_plan = false;
+  std::vector<int32_t> plan_cells;   // new leaves [n][3]
+  std::vector<int32_t> plan_map;     // [n][5] transfer records
+  DevBuf<int32_t> d_map;
+  DevBuf<double> d_eta;
   int32_t lmin = 0, lmax = 0;
 
   // tableau
@@ -426,6 +434,100 @@ struct LaunchTimer {
     if (timer) PERK_CUDA(ctx, (timer)->end(st, kind)); \
   } while (0)
 
+perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, double x0, double length) {
+  std::vector<int4> ifs, morts;
+  ifs.reserve((size_t)n_cells * 2);
+  perk_status s = build_connectivity(ctx, n_cells, cells, ifs, morts);
+  if (s != PERK_OK) return s;
+  drop_graph(ctx);
+  ctx->n_elem = n_cells;
+  ctx->n_if = (int64_t)ifs.size();
+  ctx->n_mort = (int64_t)morts.size();
+  ctx->x0 = x0;
+  ctx->length = length;
+  ctx->h_cells.assign(cells, cells + 3 * n_cells);
+  ctx->h_level.resize(n_cells);
+  for (int64_t e = 0; e < n_cells; ++e) ctx->h_level[e] = cells[3 * e];
+  ctx->h_if = std::move(ifs);
+  ctx->h_mort = std::move(morts);
+  const size_t ne = (size_t)n_cells;
+  PERK_CUDA(ctx, ctx->d_level.ensure(ne));
+  PERK_CUDA(ctx, ctx->d_method.ensure(ne));
+  PERK_CUDA(ctx, ctx->d_elem_sorted.ensure(ne));
+  PERK_CUDA(ctx, ctx->d_if_raw.ensure(ctx->h_if.size()));
+  PERK_CUDA(ctx, ctx->d_if_sorted.ensure(ctx->h_if.size()));
+  PERK_CUDA(ctx, ctx->d_mort_raw.ensure(ctx->h_mort.size()));
+  PERK_CUDA(ctx, ctx->d_mort_sorted.ensure(ctx->h_mort.size()));
+  PERK_CUDA(ctx, ctx->d_surf.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_K1.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_Ka.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_Kb.ensure(ne * ELEM));
+  PERK_CUDA(ctx, ctx->d_eta.ensure(ne));
+  const int nb = (int)std::min<int64_t>(1024, (n_cells * NODES + 255) / 256);
+  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(nb, 1)));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  if (!ctx->h_if.empty())
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_if_raw.p, ctx->h_if.data(), ctx->h_if.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  if (!ctx->h_mort.empty())
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_mort_raw.p, ctx->h_mort.data(), ctx->h_mort.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  ctx->has_mesh = true;
+  return run_partition(ctx);
+}
+
+// Morton key of a leaf's lower-left corner at resolution lmax (bits interleaved x, y)
+uint64_t morton_key(int l, int64_t ix, int64_t iy, int lmax) {
+  const uint64_t X = (uint64_t)ix << (lmax - l), Y = (uint64_t)iy << (lmax - l);
+  uint64_t z = 0;
+  for (int b = 0; b < 31; ++b) z |= ((X >> b) & 1ull) << (2 * b) | ((Y >> b) & 1ull) << (2 * b + 1);
+  return z;
+}
+
+// Desired levels raised to the least fixed point of the sibling rule (a cell
+// coarsens only with all three siblings, all leaves that want to coarsen) and
+// the 2:1 rule across faces of the current mesh.
+void balance_levels(const perk_ctx* ctx, std::vector<int32_t>& d) {
+  const int64_t n = ctx->n_elem;
+  const int32_t* c = ctx->h_cells.data();
+  std::unordered_map<CellKey, std::vector<int32_t>, CellHash> groups;
+  for (int64_t e = 0; e < n; ++e)
+    if (c[3 * e] > 0) groups[key_of(c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)].push_back((int32_t)e);
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  for (const int4& f : ctx->h_if) pairs.emplace_back(f.x, f.y);
+  for (const int4& m : ctx->h_mort) {
+    pairs.emplace_back(m.x, m.y);
+    pairs.emplace_back(m.x, m.z);
+  }
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int64_t e = 0; e < n; ++e) {
+      if (d[e] >= c[3 * e]) continue;
+      const auto& g = groups[key_of(c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)];
+      bool ok = g.size() == 4;
+      for (int32_t m : g) ok = ok && d[m] < c[3 * m];
+      if (!ok)
+        for (int32_t m : g)
+          if (d[m] < c[3 * m]) {
+            d[m] = c[3 * m];
+            changed = true;
+          }
+    }
+    for (const auto& pr : pairs) {
+      const int32_t a = pr.first, b = pr.second;
+      if (d[a] > d[b] + 1) {
+        d[b] = d[a] - 1;
+        changed = true;
+      } else if (d[b] > d[a] + 1) {
+        d[a] = d[b] - 1;
+        changed = true;
+      }
+    }
+  }
+}
+
 // the stage launches of one step on stream st (also used under graph capture)
 perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTimer* timer = nullptr) {
   const int S = ctx->S;
@@ -547,6 +649,8 @@ void perk_destroy(perk_ctx* ctx) {
   ctx->d_coef.release();
   ctx->d_flag.release();
   ctx->d_logtab.release();
+  ctx->d_map.release();
+  ctx->d_eta.release();
   delete ctx;
 }
 
@@ -562,44 +666,8 @@ perk_status perk_mesh_upload(perk_ctx* ctx, int64_t n_cells, const int32_t* cell
   if (!ctx) return PERK_E_INVALID_ARG;
   if (n_cells <= 0 || !cells || !(length > 0.0) || n_cells > (int64_t)1 << 30)
     return fail(ctx, PERK_E_INVALID_ARG, "invalid mesh arguments");
-  std::vector<int4> ifs, morts;
-  ifs.reserve((size_t)n_cells * 2);
-  perk_status s = build_connectivity(ctx, n_cells, cells, ifs, morts);
-  if (s != PERK_OK) return s;
-  drop_graph(ctx);
-  ctx->n_elem = n_cells;
-  ctx->n_if = (int64_t)ifs.size();
-  ctx->n_mort = (int64_t)morts.size();
-  ctx->x0 = x0;
-  ctx->length = length;
-  ctx->h_level.resize(n_cells);
-  for (int64_t e = 0; e < n_cells; ++e) ctx->h_level[e] = cells[3 * e];
-  ctx->h_if = std::move(ifs);
-  ctx->h_mort = std::move(morts);
-  const size_t ne = (size_t)n_cells;
-  PERK_CUDA(ctx, ctx->d_level.ensure(ne));
-  PERK_CUDA(ctx, ctx->d_method.ensure(ne));
-  PERK_CUDA(ctx, ctx->d_elem_sorted.ensure(ne));
-  PERK_CUDA(ctx, ctx->d_if_raw.ensure(ctx->h_if.size()));
-  PERK_CUDA(ctx, ctx->d_if_sorted.ensure(ctx->h_if.size()));
-  PERK_CUDA(ctx, ctx->d_mort_raw.ensure(ctx->h_mort.size()));
-  PERK_CUDA(ctx, ctx->d_mort_sorted.ensure(ctx->h_mort.size()));
-  PERK_CUDA(ctx, ctx->d_surf.ensure(ne * ELEM));
-  PERK_CUDA(ctx, ctx->d_K1.ensure(ne * ELEM));
-  PERK_CUDA(ctx, ctx->d_Ka.ensure(ne * ELEM));
-  PERK_CUDA(ctx, ctx->d_Kb.ensure(ne * ELEM));
-  const int nb = (int)std::min<int64_t>(1024, (n_cells * NODES + 255) / 256);
-  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(nb, 1)));
-  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                 ctx->stream));
-  if (!ctx->h_if.empty())
-    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_if_raw.p, ctx->h_if.data(), ctx->h_if.size() * sizeof(int4),
-                                   cudaMemcpyHostToDevice, ctx->stream));
-  if (!ctx->h_mort.empty())
-    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_mort_raw.p, ctx->h_mort.data(), ctx->h_mort.size() * sizeof(int4),
-                                   cudaMemcpyHostToDevice, ctx->stream));
-  ctx->has_mesh = true;
-  return run_partition(ctx);
+  ctx->has_plan = false;
+  return set_mesh(ctx, n_cells, cells, x0, length);
 }
 
 perk_status perk_mesh_faces(int64_t n_cells, const int32_t* cells, int64_t* n_if, int32_t* ifs, int64_t if_cap,
@@ -852,6 +920,132 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
 perk_status perk_selftest_math(perk_ctx* ctx, int64_t n, const double* d_x, double* d_out) {
   if (!ctx || !d_x || !d_out || n < 0) return PERK_E_INVALID_ARG;
   PERK_CUDA(ctx, launch_selftest_math(ctx->stream, n, d_x, d_out, ctx->d_logtab.p));
+  return PERK_OK;
+}
+
+perk_status perk_amr_indicator(perk_ctx* ctx, const double* d_U, double* d_eta) {
+  if (!ctx || !d_U || !d_eta) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  std::vector<double> x, w;
+  lgl(NN - 1, x, w);
+  PERK_CUDA(ctx, launch_indicator(ctx->stream, ctx->n_elem, d_U, ctx->ops, w[0], w[1], d_eta));
+  return PERK_OK;
+}
+
+perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int32_t* desired, const double* d_U,
+                            int64_t* n_new) {
+  if (!ctx || !n_new) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  const int64_t n = ctx->n_elem;
+  const int32_t* c = ctx->h_cells.data();
+  std::vector<int32_t> d(n);
+  if (desired) {
+    for (int64_t e = 0; e < n; ++e) {
+      if (desired[e] < c[3 * e] - 1 || desired[e] > c[3 * e] + 1 || desired[e] < 0 || desired[e] > 27)
+        return fail(ctx, PERK_E_INVALID_ARG, "desired level of cell %lld must differ by at most one", (long long)e);
+      d[e] = desired[e];
+    }
+  } else {
+    if (!prm || !d_U) return fail(ctx, PERK_E_INVALID_ARG, "need AMR parameters and U");
+    std::vector<double> x, w;
+    lgl(NN - 1, x, w);
+    PERK_CUDA(ctx, launch_indicator(ctx->stream, n, d_U, ctx->ops, w[0], w[1], ctx->d_eta.p));
+    std::vector<double> eta(n);
+    PERK_CUDA(ctx, cudaMemcpyAsync(eta.data(), ctx->d_eta.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t e = 0; e < n; ++e) {
+      const int l = c[3 * e];
+      d[e] = l;
+      if (eta[e] > prm->refine_above && l < prm->level_max)
+        d[e] = l + 1;
+      else if (eta[e] < prm->coarsen_below && l > prm->level_min && !(eta[e] > prm->refine_above))
+        d[e] = l - 1;
+    }
+  }
+  balance_levels(ctx, d);
+  // new leaves and transfer records
+  std::unordered_map<CellKey, int32_t, CellHash> old;
+  old.reserve((size_t)n * 2);
+  for (int64_t e = 0; e < n; ++e) old.emplace(key_of(c[3 * e], c[3 * e + 1], c[3 * e + 2]), (int32_t)e);
+  struct NewCell {
+    int32_t l, ix, iy;
+  };
+  std::vector<NewCell> nc;
+  nc.reserve((size_t)n * 2);
+  std::unordered_map<CellKey, char, CellHash> seen;
+  int lmax = 0;
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = c[3 * e], ix = c[3 * e + 1], iy = c[3 * e + 2];
+    if (d[e] == l + 1) {
+      for (int cy = 0; cy < 2; ++cy)
+        for (int cx = 0; cx < 2; ++cx) nc.push_back({l + 1, 2 * ix + cx, 2 * iy + cy});
+    } else if (d[e] == l) {
+      nc.push_back({l, ix, iy});
+    } else if (seen.emplace(key_of(l - 1, ix >> 1, iy >> 1), 1).second) {
+      nc.push_back({l - 1, ix >> 1, iy >> 1});
+    }
+    lmax = std::max(lmax, d[e]);
+  }
+  std::vector<std::pair<uint64_t, int64_t>> order(nc.size());
+  for (size_t k = 0; k < nc.size(); ++k) order[k] = {morton_key(nc[k].l, nc[k].ix, nc[k].iy, lmax), (int64_t)k};
+  std::sort(order.begin(), order.end());
+  const int64_t m = (int64_t)nc.size();
+  ctx->plan_cells.resize(3 * m);
+  ctx->plan_map.resize(5 * m);
+  for (int64_t k = 0; k < m; ++k) {
+    const NewCell& q = nc[order[k].second];
+    ctx->plan_cells[3 * k] = q.l;
+    ctx->plan_cells[3 * k + 1] = q.ix;
+    ctx->plan_cells[3 * k + 2] = q.iy;
+    int32_t* r = &ctx->plan_map[5 * k];
+    auto it = old.find(key_of(q.l, q.ix, q.iy));
+    if (it != old.end()) {
+      r[0] = 0;
+      r[1] = it->second;
+      r[2] = r[3] = r[4] = 0;
+      continue;
+    }
+    auto par = old.find(key_of(q.l - 1, q.ix >> 1, q.iy >> 1));
+    if (par != old.end()) {
+      r[0] = 1 | ((q.ix & 1) << 2) | ((q.iy & 1) << 3);
+      r[1] = par->second;
+      r[2] = r[3] = r[4] = 0;
+      continue;
+    }
+    r[0] = 2;
+    for (int cc = 0; cc < 4; ++cc) {
+      auto ch = old.find(key_of(q.l + 1, 2 * q.ix + (cc & 1), 2 * q.iy + (cc >> 1)));
+      if (ch == old.end()) return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
+      r[1 + cc] = ch->second;
+    }
+  }
+  ctx->has_plan = true;
+  *n_new = m;
+  return PERK_OK;
+}
+
+perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_plan) return fail(ctx, PERK_E_NOT_READY, "no AMR plan");
+  if (!d_Uold || !d_Unew || d_Uold == d_Unew) return fail(ctx, PERK_E_INVALID_ARG, "need distinct old and new U");
+  const int64_t m = (int64_t)ctx->plan_cells.size() / 3;
+  PERK_CUDA(ctx, ctx->d_map.ensure((size_t)5 * m));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_map.p, ctx->plan_map.data(), ctx->plan_map.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  PERK_CUDA(ctx, launch_transfer(ctx->stream, m, ctx->d_map.p, d_Uold, ctx->ops, d_Unew));
+  // the map upload is read by the transfer before the host may touch plan_map again
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->has_plan = false;
+  const std::vector<int32_t> cells = std::move(ctx->plan_cells);
+  ctx->plan_cells.clear();
+  return set_mesh(ctx, m, cells.data(), ctx->x0, ctx->length);
+}
+
+perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap) {
+  if (!ctx || !cells) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return PERK_E_NOT_READY;
+  if (cap < ctx->n_elem) return PERK_E_INVALID_ARG;
+  std::copy(ctx->h_cells.begin(), ctx->h_cells.end(), cells);
   return PERK_OK;
 }
 

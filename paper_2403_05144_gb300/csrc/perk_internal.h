@@ -80,6 +80,11 @@ cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua,
 
 cudaError_t launch_set_scalar(cudaStream_t st, double* p, double v);
 
+cudaError_t launch_indicator(cudaStream_t st, int64_t n, const double* U, const Ops& ops, double w0, double w1,
+                             double* eta);
+cudaError_t launch_transfer(cudaStream_t st, int64_t n, const int32_t* map, const double* Uold, const Ops& ops,
+                            double* Unew);
+
 // Records the message of a failed context-free call (read by perk_last_error(NULL)).
 perk_status set_context_free_error(perk_status s, const char* msg);
 

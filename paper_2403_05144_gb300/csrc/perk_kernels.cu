@@ -763,7 +763,107 @@ __global__ void k_dt_final(int n, const double* block_min, double* out) {
 }
 
 // ---------------------------------------------------------------------------
+// AMR: density-gradient indicator and solution transfer (16 threads per cell).
+constexpr int AMR_THREADS = 128;
+constexpr int AMR_ELEMS = AMR_THREADS / NODES;
+
+// eta_e = h max_nodes |grad rho| / mean(rho) = 2 max_nodes |(D rho)_x, (D rho)_y| / mean(rho)
+__global__ void __launch_bounds__(AMR_THREADS) k_indicator(int64_t n, const double* __restrict__ U, Ops ops,
+                                                            double w0, double w1, double* __restrict__ eta) {
+  __shared__ double s_rho[AMR_ELEMS][NODES];
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
+  const int64_t e = (int64_t)blockIdx.x * AMR_ELEMS + le;
+  const bool valid = e < n;
+  const double rho = valid ? U[e * ELEM + t] : 1.0;
+  s_rho[le][t] = rho;
+  __syncwarp();
+  double gx = 0.0, gy = 0.0;
+#pragma unroll
+  for (int m = 0; m < NN; ++m) {
+    // the derivative matrix is dsplit/2 off the diagonal; its diagonal is -(row sum)
+    const double dxm = 0.5 * ops.dsplit[i][m], dym = 0.5 * ops.dsplit[j][m];
+    gx = fma(dxm, s_rho[le][j * 4 + m] - s_rho[le][j * 4 + i], gx);
+    gy = fma(dym, s_rho[le][m * 4 + i] - s_rho[le][j * 4 + i], gy);
+  }
+  double g2 = fma(gx, gx, gy * gy);
+  const double wi = (i == 0 || i == 3) ? w0 : w1, wj = (j == 0 || j == 3) ? w0 : w1;
+  double wr = wi * wj * rho;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    g2 = fmax(g2, __shfl_xor_sync(0xffffffffu, g2, o, 16));
+    wr += __shfl_xor_sync(0xffffffffu, wr, o, 16);
+  }
+  if (valid && t == 0) eta[e] = 2.0 * sqrt(g2) / (0.25 * wr);
+}
+
+// kind 0: copy src[0]; kind 1: child (cx, cy) of parent src[0] by interpolation;
+// kind 2: parent of the four children src[0..3] (order cx + 2 cy) by L2 projection.
+__global__ void __launch_bounds__(AMR_THREADS) k_transfer(int64_t n, const int32_t* __restrict__ map,
+                                                           const double* __restrict__ Uold, Ops ops,
+                                                           double* __restrict__ Unew) {
+  __shared__ double s_src[AMR_ELEMS][4][ELEM];
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
+  const int64_t e = (int64_t)blockIdx.x * AMR_ELEMS + le;
+  if (e >= n) return;   // whole half-warps drop out together; only __syncwarp below
+  const int32_t* rec = map + 5 * e;
+  const int kind = rec[0] & 3, cx = (rec[0] >> 2) & 1, cy = (rec[0] >> 3) & 1;
+  const int nsrc = kind == 2 ? 4 : 1;
+  for (int s = 0; s < nsrc; ++s)
+    for (int q = t; q < ELEM; q += NODES) s_src[le][s][q] = Uold[(int64_t)rec[1 + s] * ELEM + q];
+  __syncwarp(0xffffu << (threadIdx.x & 16));
+  double out[4];
+  if (kind == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = s_src[le][0][v * NODES + t];
+  } else if (kind == 1) {
+    const double(*Px)[NN] = cx ? ops.p_hi : ops.p_lo;
+    const double(*Py)[NN] = cy ? ops.p_hi : ops.p_lo;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      double acc = 0.0;
+      for (int b = 0; b < NN; ++b) {
+        double row = 0.0;
+        for (int a = 0; a < NN; ++a) row = fma(Px[i][a], s_src[le][0][v * NODES + b * 4 + a], row);
+        acc = fma(Py[j][b], row, acc);
+      }
+      out[v] = acc;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = 0.0;
+    for (int c = 0; c < 4; ++c) {
+      const double(*Rx)[NN] = (c & 1) ? ops.r_hi : ops.r_lo;
+      const double(*Ry)[NN] = (c & 2) ? ops.r_hi : ops.r_lo;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        for (int b = 0; b < NN; ++b) {
+          double row = 0.0;
+          for (int a = 0; a < NN; ++a) row = fma(Rx[i][a], s_src[le][c][v * NODES + b * 4 + a], row);
+          out[v] = fma(Ry[j][b], row, out[v]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) Unew[e * ELEM + v * NODES + t] = out[v];
+}
+
+// ---------------------------------------------------------------------------
 // launchers
+cudaError_t launch_indicator(cudaStream_t st, int64_t n, const double* U, const Ops& ops, double w0, double w1,
+                             double* eta) {
+  if (n == 0) return cudaSuccess;
+  k_indicator<<<(unsigned)((n + AMR_ELEMS - 1) / AMR_ELEMS), AMR_THREADS, 0, st>>>(n, U, ops, w0, w1, eta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer(cudaStream_t st, int64_t n, const int32_t* map, const double* Uold, const Ops& ops,
+                            double* Unew) {
+  if (n == 0) return cudaSuccess;
+  k_transfer<<<(unsigned)((n + AMR_ELEMS - 1) / AMR_ELEMS), AMR_THREADS, 0, st>>>(n, map, Uold, ops, Unew);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
                              const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
                              int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
