@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from perk_inputs import isentropic_vortex, kelvin_helmholtz, kh_band_cells, nodal_state, vortex_two_level_cells
+from perk_inputs import isentropic_vortex, kelvin_helmholtz, nodal_state, uniform_cells, vortex_two_level_cells
 
 METRIC = "P-ERK DoF-stage updates/s and wall time to t_end vs full-RK on same GB300"
 UNIT = "DoF-stage updates/s"
@@ -50,16 +50,64 @@ UNIT = "DoF-stage updates/s"
 VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
 
 
+AMR_KH = dict(level_min=4, level_max=7, refine_above=0.1, coarsen_below=0.02)
+
+
 def workload(name: str) -> dict:
     if name == "kh":
-        # Kelvin-Helmholtz on [-1, 1]^2, levels 4..7 graded towards the shear lines,
-        # P-ERK2 {4, 6, 10, 16}, HLLC, N = 3
-        return dict(name="kelvin_helmholtz_levels4-7_static_band", cells=kh_band_cells(4, 7, 0.06), x0=-1.0,
-                    L=2.0, ic=kelvin_helmholtz, E=[4, 6, 10, 16], flux="hllc", cfl=0.7, t_end=3.0)
+        # Kelvin-Helmholtz on [-1, 1]^2: base level 4, dynamic AMR up to level 7 every 5 steps
+        # (density-gradient indicator), P-ERK2 {4, 6, 10, 16}, HLLC, N = 3, t_end = 3
+        return dict(name="kelvin_helmholtz_amr_levels4-7", cells=uniform_cells(4), x0=-1.0, L=2.0,
+                    ic=kelvin_helmholtz, E=[4, 6, 10, 16], flux="hllc", cfl=0.7, t_end=3.0, amr=AMR_KH, n_amr=5,
+                    init_cycles=3)
     if name == "vortex":
+        # isentropic vortex, 16x16 base with the central 8x8 block refined (static), P-ERK2 {4, 8}, HLL
         return dict(name="isentropic_vortex_16x16_center8x8_refined", cells=vortex_two_level_cells(), x0=-10.0,
-                    L=20.0, ic=isentropic_vortex, E=[4, 8], flux="hll", cfl=0.5, t_end=20.0)
+                    L=20.0, ic=isentropic_vortex, E=[4, 8], flux="hll", cfl=0.5, t_end=20.0, amr=None, n_amr=0,
+                    init_cycles=0)
     raise SystemExit(f"unknown workload {name}")
+
+
+class Run:
+    """One simulation through the library: mesh, P-ERK family, state, AMR every n_amr steps."""
+
+    def __init__(self, torch, wl: dict, E, use_graph: bool = True):
+        from paper_2403_05144_gb300 import PerkSolver, perk2_disk_tableau, reference_nodes
+
+        self.torch = torch
+        self.wl = wl
+        self.solver = PerkSolver(surface_flux=wl["flux"], use_graph=use_graph)
+        self.solver.upload_mesh(wl["cells"], wl["x0"], wl["L"])
+        c, a = perk2_disk_tableau(E, max(wl["E"]))
+        self.solver.set_tableau(2, E, c, a)
+        self.x, _ = reference_nodes(3)
+        self.U = self._sample()
+        for _ in range(wl["init_cycles"]):          # initial adaptation on the initial condition itself
+            self.solver.adapt(self.U, **wl["amr"])
+            self.U = self._sample()
+        self.k = 0
+        self.t = 0.0
+        self.amr_cycles = 0
+        self._refresh()
+
+    def _sample(self):
+        return self.torch.from_numpy(nodal_state(self.wl["ic"], self.solver.cells, self.wl["x0"], self.wl["L"],
+                                                 self.x)).cuda()
+
+    def _refresh(self):
+        self.dt = self.solver.compute_dt(self.U, self.wl["cfl"])
+        self.dof = self.solver.info()["dof_stage_updates"]
+
+    def step(self):
+        """One step (preceded by an AMR cycle every n_amr steps); returns its DoF-stage updates."""
+        if self.wl["amr"] and self.k > 0 and self.k % self.wl["n_amr"] == 0:
+            self.U = self.solver.adapt(self.U, **self.wl["amr"])
+            self.amr_cycles += 1
+            self._refresh()
+        self.solver.step(self.U, self.dt)
+        self.k += 1
+        self.t += self.dt
+        return self.dof
 
 
 def dist_info():
@@ -117,32 +165,57 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def time_steps(torch, solver, U, dt, K, flush):
-    """Device time of K steps, L2 flushed (untimed) before each; returns total ms."""
+def time_steps(torch, run: Run, K: int, flush):
+    """Device time (CUDA events on the launching stream) of K steps of ``run``, each
+    including its AMR cycle when one falls due; the L2 flush before every step is
+    outside the events.  Returns (total ms, DoF-stage updates)."""
     st = torch.cuda.current_stream()
-    total = 0.0
-    evs = []
+    evs, units = [], 0
     for _ in range(K):
         flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(st)
-        solver.step(U, dt)
+        units += run.step()
         b.record(st)
         evs.append((a, b))
     torch.cuda.synchronize()
-    for a, b in evs:
-        total += a.elapsed_time(b)
-    return total
+    return sum(a.elapsed_time(b) for a, b in evs), units
 
 
-def cpu_baseline(wl: dict, U0: np.ndarray, dt: float) -> dict:
-    """The oracle as it stands on one dense P-ERK step of the same workload."""
+def run_to_t_end(torch, wl: dict, E, budget_s: float) -> dict:
+    """Wall time of a whole run from t = 0 to t_end (or to a rejected step, or the budget)."""
+    from paper_2403_05144_gb300 import PerkError
+
+    run = Run(torch, wl, E)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status = "reached t_end"
+    units = 0
+    try:
+        while run.t < wl["t_end"] - 1e-12:
+            units += run.step()
+            if run.k % 25 == 0:
+                run.solver.check()
+                if time.perf_counter() - t0 > budget_s:
+                    status = "wall budget exhausted"
+                    break
+        run.solver.check()
+    except PerkError as e:
+        status = f"step rejected ({e.status})"
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"status": status, "t": run.t, "steps": run.k, "wall_s": wall, "n_elem_final": run.solver.n_elem,
+            "dof_stage_updates": units}
+
+
+def cpu_baseline(wl: dict, cells, U0: np.ndarray, dt: float) -> dict:
+    """The oracle as it stands on one dense P-ERK step of the same workload's current mesh."""
     from oracle.dgsem import DGSEM
     from oracle.perk import element_methods, perk2_family, prkm_step
     from oracle.treemesh import TreeMesh
 
-    mesh = TreeMesh(wl["cells"], wl["x0"], wl["L"])
+    mesh = TreeMesh(cells, wl["x0"], wl["L"])
     fam = perk2_family(wl["E"])
     meth = element_methods(mesh.cells[:, 0], fam.R)
     dg = DGSEM(mesh, 3, wl["flux"])
@@ -151,7 +224,7 @@ def cpu_baseline(wl: dict, U0: np.ndarray, dt: float) -> dict:
     sec = time.perf_counter() - t0
     units = sum(16 * int(sum(1 for r in meth if fam.active(int(r), i))) for i in range(fam.S))
     return {"value": units / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one dense P-ERK step of the same mesh ({len(wl['cells'])} cells, S={fam.S}), "
+            "sample": f"one dense P-ERK step of the workload's current mesh ({len(cells)} cells, S={fam.S}), "
                       f"{sec:.1f} s, numpy float64 on one host thread"}
 
 
@@ -164,10 +237,17 @@ def run_reference(args) -> None:
     from oracle.perk import element_methods, perk2_family
     from oracle.treemesh import TreeMesh
 
+    from oracle.amr import desired_levels, indicator, new_cells
+
     wl = workload(args.workload)
     x, _ = lgl_nodes_weights(3)
-    U = nodal_state(wl["ic"], wl["cells"], wl["x0"], wl["L"], x)
-    mesh = TreeMesh(wl["cells"], wl["x0"], wl["L"])
+    cells = wl["cells"]
+    for _ in range(wl["init_cycles"]):          # the same initial adaptation as the library run
+        m0 = TreeMesh(cells, wl["x0"], wl["L"])
+        U0 = nodal_state(wl["ic"], cells, wl["x0"], wl["L"], x)
+        cells = new_cells(m0, desired_levels(m0, indicator(U0), **wl["amr"]))
+    U = nodal_state(wl["ic"], cells, wl["x0"], wl["L"], x)
+    mesh = TreeMesh(cells, wl["x0"], wl["L"])
     fam = perk2_family(wl["E"])
     meth = element_methods(mesh.cells[:, 0], fam.R)
     dg = DGSEM(mesh, 3, wl["flux"])
@@ -185,11 +265,12 @@ def run_reference(args) -> None:
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": wl["name"], "n_elem": len(wl["cells"]), "family": wl["E"],
-                       "surface_flux": wl["flux"], "step": "one partitioned RHS stage of the dense oracle step"},
+            "config": {"workload": wl["name"], "n_elem": len(cells), "family": wl["E"],
+                       "surface_flux": wl["flux"],
+                       "step": "one partitioned RHS stage of the dense oracle step on the initially adapted mesh"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} stage evaluations (cycling over the S={fam.S} stages) "
-                                       f"of the {len(wl['cells'])}-cell mesh"},
+                                       f"of the {len(cells)}-cell initially adapted mesh"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -202,34 +283,18 @@ def run_perk(args) -> None:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2403_05144_gb300 import PerkSolver, measure_fp64, perk2_disk_tableau, reference_nodes
+    from paper_2403_05144_gb300 import measure_fp64
     from paper_2403_05144_gb300.build import build
 
     build()
     wl = workload(args.workload)
-    x, _ = reference_nodes(3)
-    U0 = nodal_state(wl["ic"], wl["cells"], wl["x0"], wl["L"], x)
     S = max(wl["E"])
-
-    solver = PerkSolver(surface_flux=wl["flux"], use_graph=True)
-    solver.upload_mesh(wl["cells"], wl["x0"], wl["L"])
-    solver.set_perk2_disk(wl["E"])
-    full = PerkSolver(surface_flux=wl["flux"], use_graph=True)
-    full.upload_mesh(wl["cells"], wl["x0"], wl["L"])
-    c, a = perk2_disk_tableau([S])
-    full.set_tableau(2, [S], c, a)
-
-    Ud = torch.from_numpy(U0).cuda()
-    dt = solver.compute_dt(Ud, wl["cfl"])
-    info = solver.info()
-    finfo = full.info()
+    perk = Run(torch, wl, wl["E"])
+    full = Run(torch, wl, [S])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-
-    U = Ud.clone()
-    Uf = Ud.clone()
     for _ in range(args.warmup):
-        solver.step(U, dt)
-        full.step(Uf, dt)
+        perk.step()
+        full.step()
     torch.cuda.synchronize()
 
     def barrier():
@@ -237,88 +302,99 @@ def run_perk(args) -> None:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(vals):
+        if world == 1:
+            return vals
+        t = torch.tensor(vals, dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return [float(v) for v in t]
+
+    cycles0 = perk.amr_cycles
     with ClockSampler(local_rank) as clk:
         barrier()
-        ms = time_steps(torch, solver, U, dt, args.steps, flush)
+        ms, units = time_steps(torch, perk, args.steps, flush)
+        timed_cycles = perk.amr_cycles - cycles0
         barrier()
-        ms_full = time_steps(torch, full, Uf, dt, args.steps, flush)
+        ms_full, units_full = time_steps(torch, full, args.steps, flush)
         barrier()
-    solver.check()
-    full.check()
-    if world > 1:
-        t = torch.tensor([ms, ms_full], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_full = float(t[0]), float(t[1])
-    dof_step = info["dof_stage_updates"]
-    value = world * dof_step * args.steps / (ms * 1e-3)
-    value_full = world * finfo["dof_stage_updates"] * args.steps / (ms_full * 1e-3)
+    perk.solver.check()
+    full.solver.check()
+    ms, ms_full = max_over_ranks([ms, ms_full])
+    value = world * units / (ms * 1e-3)
+    value_full = world * units_full / (ms_full * 1e-3)
+    info = perk.solver.info()
 
-    # roofline of the volume kernel: per-launch CUDA events over K profiled steps
+    # roofline of the volume kernel: CUDA events around every launch of K profiled steps
     fma_flops, div_s, log_s = measure_fp64()
-    slot_rate = fma_flops / 2.0
-    slots_per_elem = VOL_SLOTS_PER_ELEM
-    Up = Ud.clone()
+    Up = perk.U.clone()
     acc = None
     for _ in range(args.steps):
-        acc = solver.step_profiled(Up, dt, acc)
-    vol_ms = acc.ms[1]
-    vol_launches = acc.launches[1]
-    achieved = 2.0 * slots_per_elem * acc.element_stages / (vol_ms * 1e-3)
+        acc = perk.solver.step_profiled(Up, perk.dt, acc)
+    vol_ms, vol_launches = acc.ms[1], acc.launches[1]
+    achieved = 2.0 * VOL_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
     kernel_ms_total = sum(acc.ms[k] for k in range(3))
 
-    # end to end through the public API: pinned host U, H2D + step + D2H every step
-    Uh = torch.from_numpy(U0.copy()).pin_memory()
-    Ue = torch.empty_like(Ud)
+    # end to end through the public API: the state lives in pinned host memory;
+    # every step copies it in, steps (adapting when due) and copies it back
     st = torch.cuda.current_stream()
+    Uh = perk.U.cpu().pin_memory()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    h2d = d2h = 0
+    units_e2e = 0
     barrier()
     e0.record(st)
     for _ in range(args.steps):
-        Ue.copy_(Uh, non_blocking=True)
-        solver.step(Ue, dt)
-        Uh.copy_(Ue, non_blocking=True)
+        perk.U = Uh.to("cuda", non_blocking=True)
+        h2d += Uh.numel() * 8
+        units_e2e += perk.step()
+        if perk.U.shape != Uh.shape:
+            Uh = torch.empty(perk.U.shape, dtype=torch.float64).pin_memory()
+        Uh.copy_(perk.U, non_blocking=True)
+        d2h += Uh.numel() * 8
     e1.record(st)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t[0])
-    nbytes = int(U0.nbytes)
+    (ms_e2e,) = max_over_ranks([e0.elapsed_time(e1)])
 
-    steps_to_end = math.ceil(wl["t_end"] / dt)
+    # wall time to t_end, P-ERK family against the full-RHS method (same S, same dt rule)
+    tend = {"perk": run_to_t_end(torch, wl, wl["E"], args.t_end_budget),
+            "full_rk": run_to_t_end(torch, wl, [S], args.t_end_budget)}
+    tend["t_end"] = wl["t_end"]
+    if tend["perk"]["status"] == tend["full_rk"]["status"] == "reached t_end":
+        tend["wall_ratio_full_over_perk"] = tend["full_rk"]["wall_s"] / tend["perk"]["wall_s"]
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "n_elem": info["n_elem"], "levels": [info["level_min"], info["level_max"]],
-                   "family": wl["E"], "stages": S, "surface_flux": wl["flux"], "cfl": wl["cfl"], "dt": dt,
-                   "dof_stage_updates_per_step": dof_step, "l2": "flushed (256 MB write) before every timed step",
+                   "family": wl["E"], "stages": S, "surface_flux": wl["flux"], "cfl": wl["cfl"], "dt": perk.dt,
+                   "amr": ({**wl["amr"], "every_steps": wl["n_amr"], "in_timed_region": True} if wl["amr"] else None),
+                   "dof_stage_updates_per_step": units / args.steps,
+                   "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"{world} independent replica(s)", "graph": True},
         "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps,
-                    "dof_stage_updates_per_step": finfo["dof_stage_updates"],
-                    "t_end": wl["t_end"], "steps_to_t_end": steps_to_end,
-                    "perk_wall_s_to_t_end": steps_to_end * ms / args.steps * 1e-3,
-                    "full_rk_wall_s_to_t_end": steps_to_end * ms_full / args.steps * 1e-3,
-                    "wall_ratio_full_over_perk": ms_full / ms,
-                    "note": "projected from the measured per-step device time at the fixed initial dt"},
+                    "dof_stage_updates_per_step": units_full / args.steps,
+                    "ratio_ms_per_step_full_over_perk": ms_full / ms},
+        "t_end": tend,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / fma_flops, "traffic": None, "kernel": "k_volume",
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
-                     "work_per_element_stage": {"fp64_slots": VOL_SLOTS_PER_ELEM,
-                                                "flops": 2 * VOL_SLOTS_PER_ELEM,
+                     "work_per_element_stage": {"fp64_slots": VOL_SLOTS_PER_ELEM, "flops": 2 * VOL_SLOTS_PER_ELEM,
                                                 "note": "FMA-equivalent: every FP64 issue slot counted as 2 flops"},
                      "cuda_fp64_rates": {"div_per_s": div_s, "log_per_s": log_s}},
-        "e2e": {"value": world * dof_step * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "gpu_launches": args.steps * (2 * S + 1),
+        "e2e": {"value": world * units_e2e / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        # per step 2 launches per stage + the commit; per AMR cycle: indicator, transfer,
+        # partition, two step-size reductions and the step-size store
+        "gpu_launches": args.steps * (2 * S + 1) + 6 * timed_cycles,
         "clocks": clk.summary(),
     }
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(wl, U0, dt) if world == 1 else None
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(wl, perk.solver.cells, perk.U.cpu().numpy(), perk.dt)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -331,6 +407,7 @@ def main():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="perk", choices=["perk", "reference"])
     p.add_argument("--workload", default="kh", choices=["kh", "vortex"])
+    p.add_argument("--t-end-budget", type=float, default=60.0, help="wall seconds per run to t_end")
     args = p.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
