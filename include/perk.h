@@ -163,6 +163,26 @@ typedef struct {
 } perk_counters;
 perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out);
 
+/* Derivatives of the partitioned right-hand side (the Jacobian apply that the
+ * spectrum estimation of Sec. 4.1 iterates with, and the discrete adjoint).
+ * stage = -1: the full F; stage = i >= 0: I^{act(i)} F as in perk_rhs_active.
+ * perk_rhs_jvp: d_Kd = J(Y) V on the active elements (others untouched).
+ * perk_rhs_vjp: d_g = J(Y)^T lam over every element; lam is read on the
+ * active elements only (its other entries are treated as zero).  Both
+ * differentiate the library's own discrete operator exactly (its branch
+ * decisions are taken on the values of Y).  Device arrays, U layout. */
+perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd);
+perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_lam, double* d_g);
+
+/* Adjoint of one P-ERK step (Eq. PartitionedRKSystem, reverse sweep): given
+ * U_n (device) and lam_np1 = dL/dU_{n+1}, writes lam_n = (dU_{n+1}/dU_n)^T
+ * lam_np1 (device, distinct from lam_np1).  Recomputes and stores the step's
+ * S stages (S x n_elem x 64 doubles of work space), then walks the stages
+ * backwards: adjoint of each partitioned RHS by perk_rhs_vjp's kernels and of
+ * the element-wise stage combinations.  The mesh must not change between the
+ * forward step and this call.  Asynchronous. */
+perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n);
+
 /* Adaptive mesh refinement (Sec. 7: the AMR callback every N_AMR steps, after
  * which the partition is re-assigned, Sec. 6.2).  Indicator: the density
  * gradient eta_e = h_e max_nodes |grad rho| / mean_e(rho) (dimensionless).

@@ -181,6 +181,26 @@ class PerkSolver:
         self._call(self.lib.perk_step_profiled, C.c_void_p(_ptr(U)), C.c_double(dt), C.byref(acc))
         return acc
 
+    # ----------------------------------------------------------- derivatives
+    def rhs_jvp(self, Y, V, stage: int = -1, out=None):
+        Y, V = self._state(Y), self._state(V)
+        Kd = self.torch.zeros_like(Y) if out is None else self._state(out)
+        self._call(self.lib.perk_rhs_jvp, int(stage), C.c_void_p(_ptr(Y)), C.c_void_p(_ptr(V)), C.c_void_p(_ptr(Kd)))
+        return Kd
+
+    def rhs_vjp(self, Y, lam, stage: int = -1, out=None):
+        Y, lam = self._state(Y), self._state(lam)
+        g = self.empty_state() if out is None else self._state(out)
+        self._call(self.lib.perk_rhs_vjp, int(stage), C.c_void_p(_ptr(Y)), C.c_void_p(_ptr(lam)), C.c_void_p(_ptr(g)))
+        return g
+
+    def step_vjp(self, Un, dt: float, lam_np1, out=None):
+        Un, lam_np1 = self._state(Un), self._state(lam_np1)
+        lam_n = self.empty_state() if out is None else self._state(out)
+        self._call(self.lib.perk_step_vjp, C.c_void_p(_ptr(Un)), C.c_double(dt), C.c_void_p(_ptr(lam_np1)),
+                   C.c_void_p(_ptr(lam_n)))
+        return lam_n
+
     # ------------------------------------------------------------------ AMR
     def amr_indicator(self, U):
         U = self._state(U)

@@ -64,6 +64,9 @@ SIGNATURES = [
     ("perk_check", C.c_int, [C.c_void_p]),
     ("perk_compute_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
+    ("perk_rhs_jvp", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk_rhs_vjp", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk_step_vjp", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     ("perk_amr_indicator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(PerkAmrParams), C.POINTER(C.c_int32), C.c_void_p,
                                   C.POINTER(C.c_int64)]),

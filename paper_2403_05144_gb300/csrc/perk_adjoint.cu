@@ -1,0 +1,853 @@
+// Derivatives of the partitioned DGSEM right-hand side: Jacobian-vector
+// products (JVP) and vector-Jacobian products (VJP), the building blocks of the
+// discrete adjoint of the P-ERK step.
+//
+// Both differentiate exactly the discrete operator of perk_kernels.cu (same
+// logarithm table, reciprocals and branch decisions, which are taken on the
+// values).  Forward-mode dual numbers carry the derivatives:
+//   * JVP: one tangent per value (Dual<1>): K and dK = J(Y) v in one pass.
+//   * VJP: the Jacobians of every two-point volume flux and every surface flux
+//     with respect to both of their states (Dual<8>: four tangents per side),
+//     contracted on the fly with the adjoint weights of the flux, so that
+//     J(Y)^T lambda is assembled pair by pair and face by face without ever
+//     forming the element Jacobian.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "perk.h"
+#include "perk_internal.h"
+
+namespace perk {
+namespace ad {
+
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+};
+
+template <int N>
+__device__ __forceinline__ Dual<N> cst(double a) {
+  Dual<N> r;
+  r.v = a;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = 0.0;
+  return r;
+}
+
+// ---- arithmetic on doubles and dual numbers (same names, overloaded) ----
+__device__ __forceinline__ double val(double a) { return a; }
+template <int N>
+__device__ __forceinline__ double val(const Dual<N>& a) { return a.v; }
+
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = fma(a.v, b.d[k], a.d[k] * b.v);
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(double a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a * b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& b, double a) {
+  return a * b;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, double b) {
+  Dual<N> r = a;
+  r.v += b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(double b, const Dual<N>& a) {
+  return a + b;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, double b) {
+  Dual<N> r = a;
+  r.v -= b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(double b, const Dual<N>& a) {
+  return -(a - b);
+}
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+template <int N>
+__device__ __forceinline__ Dual<N> fma_(const Dual<N>& a, const Dual<N>& b, const Dual<N>& c) {
+  Dual<N> r;
+  r.v = fma(a.v, b.v, c.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = fma(a.v, b.d[k], fma(a.d[k], b.v, c.d[k]));
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> fma_(double a, const Dual<N>& b, const Dual<N>& c) {
+  Dual<N> r;
+  r.v = fma(a, b.v, c.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = fma(a, b.d[k], c.d[k]);
+  return r;
+}
+
+// 1/x by the primal's Newton-Raphson reciprocal; d(1/x) = -dx / x^2
+__device__ __forceinline__ double rcp_val(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ double rcp_(double x) { return rcp_val(x); }
+template <int N>
+__device__ __forceinline__ Dual<N> rcp_(const Dual<N>& x) {
+  const double y = rcp_val(x.v);
+  const double m = -y * y;
+  Dual<N> r;
+  r.v = y;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = m * x.d[k];
+  return r;
+}
+
+// the primal's table logarithm; d ln x = dx / x
+__device__ __forceinline__ double log_val(double x, const double* inv_c, const double* ln_c) {
+  const long long bits = __double_as_longlong(x);
+  const int hi = (int)(bits >> 32);
+  const int j = (hi >> 13) & (LOG_TABLE_SIZE - 1);
+  const long long eb = (bits >> 52) & 0x7FF;
+  const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  const double kd = __longlong_as_double(0x4330000000000000LL | eb) - (4503599627370496.0 + 1023.0);
+  const double r = fma(m, inv_c[j], -1.0);
+  double q = -1.0 / 8.0;
+  q = fma(q, r, 1.0 / 7.0);
+  q = fma(q, r, -1.0 / 6.0);
+  q = fma(q, r, 1.0 / 5.0);
+  q = fma(q, r, -1.0 / 4.0);
+  q = fma(q, r, 1.0 / 3.0);
+  q = fma(q, r, -0.5);
+  const double l1p = fma(r * r, q, r);
+  const double v = fma(kd, 0.6931471805599453, ln_c[j] + fma(kd, 2.3190468138462996e-17, l1p));
+  return x > 0.0 ? v : __longlong_as_double(0x7FF8000000000000LL);
+}
+__device__ __forceinline__ double log_(double x, const double* ic, const double* lc) { return log_val(x, ic, lc); }
+template <int N>
+__device__ __forceinline__ Dual<N> log_(const Dual<N>& x, const double* ic, const double* lc) {
+  Dual<N> r;
+  r.v = log_val(x.v, ic, lc);
+  const double ix = rcp_val(x.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = x.d[k] * ix;
+  return r;
+}
+
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+template <int N>
+__device__ __forceinline__ Dual<N> sqrt_(const Dual<N>& x) {
+  Dual<N> r;
+  r.v = sqrt(x.v);
+  const double h = 0.5 / r.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = h * x.d[k];
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T min_(const T& a, const T& b) {
+  return val(a) <= val(b) ? a : b;
+}
+template <class T>
+__device__ __forceinline__ T max_(const T& a, const T& b) {
+  return val(a) >= val(b) ? a : b;
+}
+
+__device__ __forceinline__ double cst_like(double, double c) { return c; }
+template <int N>
+__device__ __forceinline__ Dual<N> cst_like(const Dual<N>&, double c) {
+  return cst<N>(c);
+}
+
+// ---- the discrete operator, generic in the scalar type ----
+template <class T>
+struct NodeQ {
+  T rho, lnrho, beta, lnbeta, v1, v2, hv1, hv2, hp;
+};
+
+template <class T>
+__device__ __forceinline__ NodeQ<T> node_q(const T u[4], double gm1, const double* ic, const double* lc) {
+  NodeQ<T> q;
+  const T rp = gm1 * fma_(u[0], u[3], -0.5 * fma_(u[1], u[1], u[2] * u[2]));
+  const T r = rcp_(u[0] * rp);
+  const T ir = rp * r;
+  q.rho = u[0];
+  q.v1 = u[1] * ir;
+  q.v2 = u[2] * ir;
+  q.hp = 0.5 * (rp * ir);
+  q.beta = (u[0] * u[0]) * (u[0] * r);
+  q.hv1 = 0.5 * q.v1;
+  q.hv2 = 0.5 * q.v2;
+  q.lnrho = log_(u[0], ic, lc);
+  q.lnbeta = log_(q.beta, ic, lc);
+  return q;
+}
+
+template <class T>
+__device__ __forceinline__ T series_H(const T& u) {
+  T r = cst_like(u, -5098.0 / 467775.0);
+  r = fma_(r, u, cst_like(u, -214.0 / 14175.0));
+  r = fma_(r, u, cst_like(u, -22.0 / 945.0));
+  r = fma_(r, u, cst_like(u, -2.0 / 45.0));
+  r = fma_(r, u, cst_like(u, -1.0 / 6.0));
+  return fma_(r, u, cst_like(u, 0.5));
+}
+template <class T>
+__device__ __forceinline__ T series_2A(const T& u) {
+  T r = cst_like(u, 2.0 / 11.0);
+  r = fma_(r, u, cst_like(u, 2.0 / 9.0));
+  r = fma_(r, u, cst_like(u, 2.0 / 7.0));
+  r = fma_(r, u, cst_like(u, 2.0 / 5.0));
+  r = fma_(r, u, cst_like(u, 2.0 / 3.0));
+  return fma_(r, u, cst_like(u, 2.0));
+}
+
+template <class T>
+__device__ __forceinline__ void ec_flux(const NodeQ<T>& A, const NodeQ<T>& B, int dir, double inv_gm1, T f[4]) {
+  const T dr = B.rho - A.rho, sr = A.rho + B.rho;
+  const T db = B.beta - A.beta, sb = A.beta + B.beta;
+  const bool ser_r = fabs(val(dr)) < 0.03 * val(sr);
+  const bool ser_b = fabs(val(db)) < 0.03 * val(sb);
+  const T den_r = ser_r ? sr : B.lnrho - A.lnrho;
+  const T den_b = ser_b ? sb : db;
+  const T r = rcp_(den_r * den_b);
+  const T qr = den_b * r;
+  const T qb = den_r * r;
+  const T fr = dr * qr;
+  const T rho_ln = ser_r ? sr * series_H(fr * fr) : fr;
+  T ibeta;
+  if (ser_b) {
+    const T fb = db * qb;
+    ibeta = qb * series_2A(fb * fb);
+  } else {
+    ibeta = (B.lnbeta - A.lnbeta) * qb;
+  }
+  const T v1m = A.hv1 + B.hv1;
+  const T v2m = A.hv2 + B.hv2;
+  const T pm = A.hp + B.hp;
+  const T vnA = dir ? A.v2 : A.v1;
+  const T vnB = dir ? B.v2 : B.v1;
+  const T frho = rho_ln * (dir ? v2m : v1m);
+  f[0] = frho;
+  f[1] = dir ? frho * v1m : fma_(frho, v1m, pm);
+  f[2] = dir ? fma_(frho, v2m, pm) : frho * v2m;
+  const T kin = fma_(A.hv1, B.v1, A.hv2 * B.v2);
+  f[3] = fma_(frho, fma_(ibeta, cst_like(ibeta, inv_gm1), kin), fma_(A.hp, vnB, B.hp * vnA));
+}
+
+template <class T>
+__device__ __forceinline__ void phys_flux(const T u[4], const T& vn, const T& p, int dir, T f[4]) {
+  f[0] = u[0] * vn;
+  f[1] = dir ? u[1] * vn : fma_(u[1], vn, p);
+  f[2] = dir ? fma_(u[2], vn, p) : u[2] * vn;
+  f[3] = (u[3] + p) * vn;
+}
+
+template <class T>
+__device__ void flux_hll(const T uL[4], const T uR[4], int dir, const Ops& ops, T f[4]) {
+  const T irL = rcp_(uL[0]), irR = rcp_(uR[0]);
+  const T pL = ops.gm1 * (uL[3] - 0.5 * (uL[1] * uL[1] + uL[2] * uL[2]) * irL);
+  const T pR = ops.gm1 * (uR[3] - 0.5 * (uR[1] * uR[1] + uR[2] * uR[2]) * irR);
+  const T vL = uL[1 + dir] * irL, vR = uR[1 + dir] * irR;
+  const T cL = sqrt_(ops.gamma * (pL * irL)), cR = sqrt_(ops.gamma * (pR * irR));
+  const T SL = min_(vL - cL, vR - cR), SR = max_(vL + cL, vR + cR);
+  T fL[4], fR[4];
+  phys_flux(uL, vL, pL, dir, fL);
+  phys_flux(uR, vR, pR, dir, fR);
+  if (val(SL) >= 0.0) {
+    for (int v = 0; v < 4; ++v) f[v] = fL[v];
+  } else if (val(SR) <= 0.0) {
+    for (int v = 0; v < 4; ++v) f[v] = fR[v];
+  } else {
+    const T inv = rcp_(SR - SL);
+    const T SLSR = SL * SR;
+    for (int v = 0; v < 4; ++v) f[v] = (SR * fL[v] - SL * fR[v] + SLSR * (uR[v] - uL[v])) * inv;
+  }
+}
+
+template <class T>
+__device__ void flux_hllc(const T uL[4], const T uR[4], int dir, const Ops& ops, T f[4]) {
+  const T irL = rcp_(uL[0]), irR = rcp_(uR[0]);
+  const T pL = ops.gm1 * (uL[3] - 0.5 * (uL[1] * uL[1] + uL[2] * uL[2]) * irL);
+  const T pR = ops.gm1 * (uR[3] - 0.5 * (uR[1] * uR[1] + uR[2] * uR[2]) * irR);
+  const T vL = uL[1 + dir] * irL, vR = uR[1 + dir] * irR;
+  const T cL = sqrt_(ops.gamma * (pL * irL)), cR = sqrt_(ops.gamma * (pR * irR));
+  const T SL = min_(vL - cL, vR - cR), SR = max_(vL + cL, vR + cR);
+  if (val(SL) >= 0.0) {
+    phys_flux(uL, vL, pL, dir, f);
+    return;
+  }
+  if (val(SR) <= 0.0) {
+    phys_flux(uR, vR, pR, dir, f);
+    return;
+  }
+  const T mL = uL[0] * (SL - vL), mR = uR[0] * (SR - vR);
+  const T Ss = (pR - pL + mL * vL - mR * vR) * rcp_(mL - mR);
+  const bool left = val(Ss) >= 0.0;
+  const T* u = left ? uL : uR;
+  const T S = left ? SL : SR;
+  const T vn = left ? vL : vR;
+  const T p = left ? pL : pR;
+  const T m = left ? mL : mR;
+  const T ir = left ? irL : irR;
+  T fk[4];
+  phys_flux(u, vn, p, dir, fk);
+  const T fac = m * rcp_(S - Ss);
+  T us[4];
+  us[0] = fac;
+  us[1 + dir] = fac * Ss;
+  us[2 - dir] = fac * (u[2 - dir] * ir);
+  us[3] = fac * (u[3] * ir + (Ss - vn) * (Ss + p * rcp_(m)));
+  for (int v = 0; v < 4; ++v) f[v] = fk[v] + S * (us[v] - u[v]);
+}
+
+template <class T>
+__device__ void flux_ec_surface(const T uL[4], const T uR[4], int dir, const Ops& ops, const double* ic,
+                                const double* lc, T f[4]) {
+  const NodeQ<T> A = node_q(uL, ops.gm1, ic, lc), B = node_q(uR, ops.gm1, ic, lc);
+  ec_flux(A, B, dir, ops.inv_gm1, f);
+}
+
+template <class T>
+__device__ __forceinline__ void surface_flux(const T uL[4], const T uR[4], int dir, const Ops& ops, const double* ic,
+                                             const double* lc, T f[4]) {
+  if (ops.surface_flux == PERK_SURFACE_HLLC)
+    flux_hllc(uL, uR, dir, ops, f);
+  else if (ops.surface_flux == PERK_SURFACE_EC)
+    flux_ec_surface(uL, uR, dir, ops, ic, lc, f);
+  else
+    flux_hll(uL, uR, dir, ops, f);
+}
+
+__device__ __forceinline__ int face_node(int face, int k) {
+  return face == 0 ? 4 * k : face == 1 ? 4 * k + 3 : face == 2 ? k : 12 + k;
+}
+__device__ __forceinline__ int pair_slot(int a, int b) { return (a * (7 - a)) / 2 + b - a - 1; }
+
+// ===========================================================================
+// JVP: surface fluxes and their tangents (value in surf, tangent in surf_d)
+__global__ void __launch_bounds__(128) k_jvp_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                    int64_t n_mort, const int4* __restrict__ morts, int64_t if_blocks,
+                                                    const double* __restrict__ Y, const double* __restrict__ V,
+                                                    const double* __restrict__ logt, double* __restrict__ surf,
+                                                    double* __restrict__ surf_d) {
+  using D1 = Dual<1>;
+  __shared__ double s_half[16][2][4][2][NN];   // [mortar][half][var][value, tangent][node]
+  const double* ic = logt;
+  const double* lc = logt + LOG_TABLE_SIZE;
+  auto load = [&](int64_t e, int node, D1 u[4]) {
+    for (int v = 0; v < 4; ++v) {
+      u[v].v = Y[e * ELEM + v * NODES + node];
+      u[v].d[0] = V[e * ELEM + v * NODES + node];
+    }
+  };
+  if (blockIdx.x < if_blocks) {
+    const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
+    const int k = threadIdx.x & 3;
+    if (idx >= n_if) return;
+    const int4 r = ifs[idx];
+    const int dir = r.z;
+    D1 uL[4], uR[4], f[4];
+    load(r.x, face_node(2 * dir + 1, k), uL);
+    load(r.y, face_node(2 * dir, k), uR);
+    surface_flux(uL, uR, dir, ops, ic, lc, f);
+    for (int v = 0; v < 4; ++v) {
+      surf[(int64_t)r.x * ELEM + (2 * dir + 1) * 16 + 4 * v + k] = f[v].v;
+      surf_d[(int64_t)r.x * ELEM + (2 * dir + 1) * 16 + 4 * v + k] = f[v].d[0];
+      surf[(int64_t)r.y * ELEM + (2 * dir) * 16 + 4 * v + k] = f[v].v;
+      surf_d[(int64_t)r.y * ELEM + (2 * dir) * 16 + 4 * v + k] = f[v].d[0];
+    }
+    return;
+  }
+  const int lm = threadIdx.x >> 3;
+  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * 16 + lm;
+  const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
+  const bool valid = idx < n_mort;
+  int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
+  const int dir = r.w & 1, large_side = (r.w >> 1) & 1;
+  const int large_face = large_side == 0 ? 2 * dir + 1 : 2 * dir;
+  const int small_face = large_side == 0 ? 2 * dir : 2 * dir + 1;
+  const int small = half ? r.z : r.y;
+  if (valid) {
+    D1 ui[4];
+    for (int v = 0; v < 4; ++v) ui[v] = cst<1>(0.0);
+    for (int l = 0; l < NN; ++l) {
+      D1 ul[4];
+      load(r.x, face_node(large_face, l), ul);
+      const double w = half ? ops.p_hi[k][l] : ops.p_lo[k][l];
+      for (int v = 0; v < 4; ++v) ui[v] = fma_(w, ul[v], ui[v]);
+    }
+    D1 us[4], f[4];
+    load(small, face_node(small_face, k), us);
+    if (large_side == 0)
+      surface_flux(ui, us, dir, ops, ic, lc, f);
+    else
+      surface_flux(us, ui, dir, ops, ic, lc, f);
+    for (int v = 0; v < 4; ++v) {
+      surf[(int64_t)small * ELEM + small_face * 16 + 4 * v + k] = f[v].v;
+      surf_d[(int64_t)small * ELEM + small_face * 16 + 4 * v + k] = f[v].d[0];
+      s_half[lm][half][v][0][k] = f[v].v;
+      s_half[lm][half][v][1][k] = f[v].d[0];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    for (int vv = 0; vv < 2; ++vv) {
+      const int v = 2 * half + vv;
+      double a0 = 0.0, a1 = 0.0;
+      for (int l = 0; l < NN; ++l) {
+        a0 = fma(ops.r_lo[k][l], s_half[lm][0][v][0][l], fma(ops.r_hi[k][l], s_half[lm][1][v][0][l], a0));
+        a1 = fma(ops.r_lo[k][l], s_half[lm][0][v][1][l], fma(ops.r_hi[k][l], s_half[lm][1][v][1][l], a1));
+      }
+      surf[(int64_t)r.x * ELEM + large_face * 16 + 4 * v + k] = a0;
+      surf_d[(int64_t)r.x * ELEM + large_face * 16 + 4 * v + k] = a1;
+    }
+  }
+}
+
+// JVP: volume integral + lifting in dual numbers; writes K (value) and dK (tangent)
+__global__ void __launch_bounds__(128) k_jvp_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
+                                                     const int32_t* __restrict__ level, double two_over_len,
+                                                     const double* __restrict__ Y, const double* __restrict__ V,
+                                                     const double* __restrict__ surf,
+                                                     const double* __restrict__ surf_d,
+                                                     const double* __restrict__ logt, double* __restrict__ K,
+                                                     double* __restrict__ Kd) {
+  using D1 = Dual<1>;
+  __shared__ NodeQ<D1> s_q[8][NODES];
+  __shared__ double s_f[8][4][2][48];
+  __shared__ double s_log[2 * LOG_TABLE_SIZE];
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 128) s_log[q] = logt[q];
+  __syncthreads();
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
+  const int64_t slot = (int64_t)blockIdx.x * 8 + le;
+  const bool valid = slot < n;
+  const int64_t e = valid ? elems[slot] : 0;
+  D1 y[4];
+  for (int v = 0; v < 4; ++v) {
+    y[v].v = valid ? Y[e * ELEM + v * NODES + t] : (v == 0 ? 1.0 : v == 3 ? 2.5 : 0.0);
+    y[v].d[0] = valid ? V[e * ELEM + v * NODES + t] : 0.0;
+  }
+  s_q[le][t] = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
+  __syncwarp();
+  for (int kk = 0; kk < 3; ++kk) {
+    const int p = t + 16 * kk;
+    const int dir = p >= 24;
+    const int q = dir ? p - 24 : p;
+    const int line = q / 6, qq = q - 6 * line;
+    const int a = (qq >= 3) + (qq >= 5);
+    const int b = qq + 1 - (a * (5 - a)) / 2;
+    const int na = dir ? a * 4 + line : line * 4 + a;
+    const int nb = dir ? b * 4 + line : line * 4 + b;
+    D1 f[4];
+    ec_flux(s_q[le][na], s_q[le][nb], dir, ops.inv_gm1, f);
+    for (int v = 0; v < 4; ++v) {
+      s_f[le][v][0][p] = f[v].v;
+      s_f[le][v][1][p] = f[v].d[0];
+    }
+  }
+  __syncwarp();
+  double acc[4][2] = {};
+  for (int mm = 0; mm < 4; ++mm) {
+    if (mm != i) {
+      const int p = j * 6 + pair_slot(min(i, mm), max(i, mm));
+      for (int v = 0; v < 4; ++v)
+        for (int c = 0; c < 2; ++c) acc[v][c] = fma(ops.dsplit[i][mm], s_f[le][v][c][p], acc[v][c]);
+    }
+    if (mm != j) {
+      const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
+      for (int v = 0; v < 4; ++v)
+        for (int c = 0; c < 2; ++c) acc[v][c] = fma(ops.dsplit[j][mm], s_f[le][v][c][p], acc[v][c]);
+    }
+  }
+  if (!valid) return;
+  const double iw = ops.inv_w0;
+  for (int c = 0; c < 2; ++c) {
+    const double* sf = (c ? surf_d : surf) + e * ELEM;
+    for (int v = 0; v < 4; ++v) {
+      if (i == 0) acc[v][c] = fma(-iw, sf[0 * 16 + 4 * v + j], acc[v][c]);
+      if (i == 3) acc[v][c] = fma(iw, sf[1 * 16 + 4 * v + j], acc[v][c]);
+      if (j == 0) acc[v][c] = fma(-iw, sf[2 * 16 + 4 * v + i], acc[v][c]);
+      if (j == 3) acc[v][c] = fma(iw, sf[3 * 16 + 4 * v + i], acc[v][c]);
+    }
+  }
+  const double scale = -ldexp(two_over_len, level[e]);
+  for (int v = 0; v < 4; ++v) {
+    if (K) K[e * ELEM + v * NODES + t] = scale * acc[v][0];
+    Kd[e * ELEM + v * NODES + t] = scale * acc[v][1];
+  }
+}
+
+// ===========================================================================
+// VJP.  lam is the adjoint of K (zero outside the active elements); g receives
+// J(Y)^T lam.  Face kernel: for every active face node, the adjoint weight of
+// the numerical flux (its lifting coefficients times lam on both sides) times
+// the flux Jacobian gives the adjoint of the two traces, written to
+// gsurf[e][face][var][node] (each element face is owned by one face record).
+__device__ __forceinline__ double lift_coef(int face, double two_over_len, int level, double iw) {
+  // K += -(2/h) (+iw f* on faces 1, 3; -iw f* on faces 0, 2)
+  const double s = ldexp(two_over_len, level);
+  return (face & 1) ? -s * iw : s * iw;
+}
+
+__global__ void __launch_bounds__(128) k_vjp_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                    int64_t n_mort, const int4* __restrict__ morts, int64_t if_blocks,
+                                                    const int32_t* __restrict__ level, double two_over_len,
+                                                    const double* __restrict__ Y, const double* __restrict__ lam,
+                                                    const double* __restrict__ logt, double* __restrict__ gsurf) {
+  using D8 = Dual<8>;
+  __shared__ double s_gphi[16][4][NN];       // adjoint of the projected large-face flux
+  __shared__ double s_gui[16][2][4][NN];     // adjoint of the interpolated large trace, per half
+  const double* ic = logt;
+  const double* lc = logt + LOG_TABLE_SIZE;
+  const double iw = ops.inv_w0;
+  auto load8 = [&](int64_t e, int node, int side, D8 u[4]) {
+    for (int v = 0; v < 4; ++v) {
+      u[v] = cst<8>(Y[e * ELEM + v * NODES + node]);
+      u[v].d[4 * side + v] = 1.0;
+    }
+  };
+  if (blockIdx.x < if_blocks) {
+    const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
+    const int k = threadIdx.x & 3;
+    if (idx >= n_if) return;
+    const int4 r = ifs[idx];
+    const int dir = r.z;
+    const int fL = 2 * dir + 1, fR = 2 * dir;
+    D8 uL[4], uR[4], f[4];
+    load8(r.x, face_node(fL, k), 0, uL);
+    load8(r.y, face_node(fR, k), 1, uR);
+    surface_flux(uL, uR, dir, ops, ic, lc, f);
+    const double cL = lift_coef(fL, two_over_len, level[r.x], iw);
+    const double cR = lift_coef(fR, two_over_len, level[r.y], iw);
+    double gf[4];
+    for (int v = 0; v < 4; ++v)
+      gf[v] = cL * lam[(int64_t)r.x * ELEM + v * NODES + face_node(fL, k)] +
+              cR * lam[(int64_t)r.y * ELEM + v * NODES + face_node(fR, k)];
+    for (int c = 0; c < 4; ++c) {
+      double gl = 0.0, gr = 0.0;
+      for (int v = 0; v < 4; ++v) {
+        gl = fma(gf[v], f[v].d[c], gl);
+        gr = fma(gf[v], f[v].d[4 + c], gr);
+      }
+      gsurf[(int64_t)r.x * ELEM + fL * 16 + 4 * c + k] = gl;
+      gsurf[(int64_t)r.y * ELEM + fR * 16 + 4 * c + k] = gr;
+    }
+    return;
+  }
+  const int lm = threadIdx.x >> 3;
+  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * 16 + lm;
+  const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
+  const bool valid = idx < n_mort;
+  int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
+  const int dir = r.w & 1, large_side = (r.w >> 1) & 1;
+  const int large_face = large_side == 0 ? 2 * dir + 1 : 2 * dir;
+  const int small_face = large_side == 0 ? 2 * dir : 2 * dir + 1;
+  const int small = half ? r.z : r.y;
+  // adjoint of the large face's projected flux phi at its node k (threads of half 0 write it)
+  if (valid && half == 0) {
+    const double cl = lift_coef(large_face, two_over_len, level[r.x], iw);
+    for (int v = 0; v < 4; ++v) s_gphi[lm][v][k] = cl * lam[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, k)];
+  }
+  __syncthreads();
+  if (valid) {
+    // flux at node k of this half, with tangents on the interpolated large trace (slots 0-3) and the small trace (4-7)
+    D8 ui[4], us[4], f[4];
+    for (int v = 0; v < 4; ++v) ui[v] = cst<8>(0.0);
+    for (int l = 0; l < NN; ++l) {
+      const double w = half ? ops.p_hi[k][l] : ops.p_lo[k][l];
+      for (int v = 0; v < 4; ++v) ui[v].v = fma(w, Y[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, l)], ui[v].v);
+    }
+    for (int v = 0; v < 4; ++v) ui[v].d[v] = 1.0;
+    load8(small, face_node(small_face, k), 1, us);
+    if (large_side == 0)
+      surface_flux(ui, us, dir, ops, ic, lc, f);
+    else {
+      // swap the roles so that slots 0-3 still belong to the large trace
+      surface_flux(us, ui, dir, ops, ic, lc, f);
+    }
+    const double cs = lift_coef(small_face, two_over_len, level[small], iw);
+    double gf[4];
+    for (int v = 0; v < 4; ++v) {
+      double g = cs * lam[(int64_t)small * ELEM + v * NODES + face_node(small_face, k)];
+      // projection phi[m] = sum_l R_h[m][l] f_h[l]: adjoint of f_h[k] gathers R_h[m][k] gphi[m]
+      for (int m = 0; m < NN; ++m) g = fma(half ? ops.r_hi[m][k] : ops.r_lo[m][k], s_gphi[lm][v][m], g);
+      gf[v] = g;
+    }
+    for (int c = 0; c < 4; ++c) {
+      double gl = 0.0, gs = 0.0;
+      for (int v = 0; v < 4; ++v) {
+        gl = fma(gf[v], f[v].d[c], gl);
+        gs = fma(gf[v], f[v].d[4 + c], gs);
+      }
+      gsurf[(int64_t)small * ELEM + small_face * 16 + 4 * c + k] = gs;
+      s_gui[lm][half][c][k] = gl;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    // adjoint of the large trace: u_interp_h[l] = sum_m P_h[l][m] u_large[m]; thread (half, k) writes
+    // variables 2 half, 2 half + 1 at large node k
+    for (int cc = 0; cc < 2; ++cc) {
+      const int c = 2 * half + cc;
+      double g = 0.0;
+      for (int l = 0; l < NN; ++l) {
+        g = fma(ops.p_lo[l][k], s_gui[lm][0][c][l], g);
+        g = fma(ops.p_hi[l][k], s_gui[lm][1][c][l], g);
+      }
+      gsurf[(int64_t)r.x * ELEM + large_face * 16 + 4 * c + k] = g;
+    }
+  }
+}
+
+// Element kernel over the sorted list: the first n_act elements are active
+// (volume adjoint with the pair Jacobians); every element adds the face
+// adjoints of its four faces from gsurf (zeroed beforehand, so faces that were
+// not active contribute nothing).
+constexpr int VJP_ELEMS = 4;  // 64 threads: the Dual<4> node data would exceed 48 KB at 8 elements
+
+__global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64_t n_act,
+                                                     const int32_t* __restrict__ elems,
+                                                     const int32_t* __restrict__ level, double two_over_len,
+                                                     const double* __restrict__ Y, const double* __restrict__ lam,
+                                                     const double* __restrict__ gsurf,
+                                                     const double* __restrict__ logt, double* __restrict__ g) {
+  using D4 = Dual<4>;
+  using D8 = Dual<8>;
+  __shared__ NodeQ<D4> s_q[VJP_ELEMS][NODES];
+  __shared__ double s_mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
+  __shared__ double s_g[VJP_ELEMS][8][48];           // per pair: adjoint of its two states
+  __shared__ double s_log[2 * LOG_TABLE_SIZE];
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
+  __syncthreads();
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
+  const int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le;
+  const bool valid = slot < n_all;
+  const bool active = slot < n_act;
+  const int64_t e = valid ? elems[slot] : 0;
+  // the volume part exists only for active elements; inactive slots run it on a dummy state
+  D4 y[4];
+  for (int v = 0; v < 4; ++v) {
+    y[v] = cst<4>(active ? Y[e * ELEM + v * NODES + t] : (v == 0 ? 1.0 : v == 3 ? 2.5 : 0.0));
+    y[v].d[v] = 1.0;
+  }
+  const double scale = valid ? -ldexp(two_over_len, level[e]) : 0.0;
+  for (int v = 0; v < 4; ++v) s_mu[le][v][t] = active ? scale * lam[e * ELEM + v * NODES + t] : 0.0;
+  s_q[le][t] = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
+  __syncwarp();
+  for (int kk = 0; kk < 3; ++kk) {
+    const int p = t + 16 * kk;
+    const int dir = p >= 24;
+    const int q = dir ? p - 24 : p;
+    const int line = q / 6, qq = q - 6 * line;
+    const int a = (qq >= 3) + (qq >= 5);
+    const int b = qq + 1 - (a * (5 - a)) / 2;
+    const int na = dir ? a * 4 + line : line * 4 + a;
+    const int nb = dir ? b * 4 + line : line * 4 + b;
+    // local indices along the pair's line
+    const int ia = a, ib = b;
+    const int li = dir ? line : line;  // (unused: the coefficients depend on ia, ib only)
+    (void)li;
+    NodeQ<D8> A, B;
+    {
+      const NodeQ<D4>& qa = s_q[le][na];
+      const NodeQ<D4>& qb = s_q[le][nb];
+      const D4* fa = &qa.rho;
+      const D4* fb = &qb.rho;
+      D8* ta = &A.rho;
+      D8* tb = &B.rho;
+      for (int m = 0; m < 9; ++m) {
+        ta[m].v = fa[m].v;
+        tb[m].v = fb[m].v;
+        for (int c = 0; c < 4; ++c) {
+          ta[m].d[c] = fa[m].d[c];
+          ta[m].d[4 + c] = 0.0;
+          tb[m].d[c] = 0.0;
+          tb[m].d[4 + c] = fb[m].d[c];
+        }
+      }
+    }
+    D8 f[4];
+    ec_flux(A, B, dir, ops.inv_gm1, f);
+    // f enters K_a with D_split[a][b] and K_b with D_split[b][a]
+    double gf[4];
+    for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[ia][ib] * s_mu[le][v][na] + ops.dsplit[ib][ia] * s_mu[le][v][nb];
+    for (int c = 0; c < 8; ++c) {
+      double acc = 0.0;
+      for (int v = 0; v < 4; ++v) acc = fma(gf[v], f[v].d[c], acc);
+      s_g[le][c][p] = acc;
+    }
+  }
+  __syncwarp();
+  if (!valid) return;
+  double out[4] = {0.0, 0.0, 0.0, 0.0};
+  if (active) {
+    for (int mm = 0; mm < 4; ++mm) {
+      if (mm != i) {
+        const int p = j * 6 + pair_slot(min(i, mm), max(i, mm));
+        const int side = i < mm ? 0 : 4;       // this node is the pair's first (a) or second (b) state
+        for (int c = 0; c < 4; ++c) out[c] += s_g[le][side + c][p];
+      }
+      if (mm != j) {
+        const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
+        const int side = j < mm ? 0 : 4;
+        for (int c = 0; c < 4; ++c) out[c] += s_g[le][side + c][p];
+      }
+    }
+  }
+  const double* gs = gsurf + e * ELEM;
+  for (int c = 0; c < 4; ++c) {
+    if (i == 0) out[c] += gs[0 * 16 + 4 * c + j];
+    if (i == 3) out[c] += gs[1 * 16 + 4 * c + j];
+    if (j == 0) out[c] += gs[2 * 16 + 4 * c + i];
+    if (j == 3) out[c] += gs[3 * 16 + 4 * c + i];
+  }
+  for (int c = 0; c < 4; ++c) g[e * ELEM + c * NODES + t] = out[c];
+}
+
+// Y = U + dt (alpha K1 + beta Kp) with the element's member coefficients (stage > 0), Y = U (stage 0)
+__global__ void k_combine(int64_t n, const int32_t* __restrict__ method, const StageCoef* __restrict__ coef,
+                          double dt, const double* __restrict__ U, const double* __restrict__ K1,
+                          const double* __restrict__ Kp, double* __restrict__ Y) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / ELEM;
+    double y = U[q];
+    if (coef) {
+      const StageCoef c = coef[method[e]];
+      if (c.alpha != 0.0) y = fma(dt * c.alpha, K1[q], y);
+      if (c.beta != 0.0) y = fma(dt * c.beta, Kp[q], y);
+    }
+    Y[q] = y;
+  }
+}
+
+// adjoint of the stage combination: lamU += g; lamK1 += dt alpha g; lamKp += dt beta g (lamKp may alias lamK1)
+__global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ method, const StageCoef* __restrict__ coef,
+                            double dt, const double* __restrict__ g, double* __restrict__ lamU,
+                            double* __restrict__ lamK1, double* lamKp) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / ELEM;
+    const double gq = g[q];
+    lamU[q] += gq;
+    if (coef) {
+      const StageCoef c = coef[method[e]];
+      if (lamKp == lamK1) {
+        lamK1[q] += dt * (c.alpha + c.beta) * gq;
+      } else {
+        lamK1[q] += dt * c.alpha * gq;
+        lamKp[q] += dt * c.beta * gq;
+      }
+    }
+  }
+}
+
+// final-update adjoint seed: lamU = lam; lamKs = dt bs lam; lamKp += dt bp lam; lamK1 += dt b1 lam
+__global__ void k_adj_seed(int64_t n, double dt, double b1, double bp, double bs, const double* __restrict__ lam,
+                           double* __restrict__ lamU, double* __restrict__ lamK1, double* __restrict__ lamKp,
+                           double* __restrict__ lamKs) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
+    const double l = lam[q];
+    lamU[q] = l;
+    lamKs[q] = dt * bs * l;
+    lamK1[q] = dt * b1 * l;
+    if (lamKp) lamKp[q] = dt * bp * l;
+  }
+}
+
+}  // namespace ad
+
+static unsigned ew_blocks(int64_t n) {
+  int64_t b = (n * ELEM + 255) / 256;
+  return (unsigned)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+
+cudaError_t launch_combine(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
+                           const double* U, const double* K1, const double* Kp, double* Y) {
+  ad::k_combine<<<ew_blocks(n), 256, 0, st>>>(n, method, coef, dt, U, K1, Kp, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
+                             const double* g, double* lamU, double* lamK1, double* lamKp) {
+  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, method, coef, dt, g, lamU, lamK1, lamKp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_seed(cudaStream_t st, int64_t n, double dt, double b1, double bp, double bs, const double* lam,
+                            double* lamU, double* lamK1, double* lamKp, double* lamKs) {
+  ad::k_adj_seed<<<ew_blocks(n), 256, 0, st>>>(n, dt, b1, bp, bs, lam, lamU, lamK1, lamKp, lamKs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+                       const int4* morts, int64_t n_el, const int32_t* elems, const int32_t* level,
+                       double two_over_len, const double* Y, const double* V, const double* logt, double* surf,
+                       double* surf_d, double* K, double* Kd) {
+  const int64_t bi = (n_if + 31) / 32, bm = (n_mort + 15) / 16;
+  if (bi + bm > 0)
+    ad::k_jvp_faces<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, Y, V, logt, surf, surf_d);
+  if (n_el > 0)
+    ad::k_jvp_volume<<<(unsigned)((n_el + 7) / 8), 128, 0, st>>>(ops, n_el, elems, level, two_over_len, Y, V, surf,
+                                                                 surf_d, logt, K, Kd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vjp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+                       const int4* morts, int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level,
+                       double two_over_len, const double* Y, const double* lam, const double* logt, double* gsurf,
+                       double* g) {
+  cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int64_t bi = (n_if + 31) / 32, bm = (n_mort + 15) / 16;
+  if (bi + bm > 0)
+    ad::k_vjp_faces<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level, two_over_len, Y,
+                                                         lam, logt, gsurf);
+  if (n_all > 0)
+    ad::k_vjp_volume<<<(unsigned)((n_all + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS), 64, 0, st>>>(ops, n_all, n_act, elems, level, two_over_len, Y,
+                                                                  lam, gsurf, logt, g);
+  return cudaGetLastError();
+}
+
+}  // namespace perk

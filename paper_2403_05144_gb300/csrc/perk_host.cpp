@@ -229,6 +229,9 @@ struct perk_ctx {
   std::vector<int32_t> plan_map;     // [n][5] transfer records
   DevBuf<int32_t> d_map;
   DevBuf<double> d_eta;
+
+  // adjoint work space
+  DevBuf<double> d_surf_d, d_Kall, d_Ystage, d_g, d_lamK1, d_lamKa, d_lamKb;
   int32_t lmin = 0, lmax = 0;
 
   // tableau
@@ -651,6 +654,13 @@ void perk_destroy(perk_ctx* ctx) {
   ctx->d_logtab.release();
   ctx->d_map.release();
   ctx->d_eta.release();
+  ctx->d_surf_d.release();
+  ctx->d_Kall.release();
+  ctx->d_Ystage.release();
+  ctx->d_g.release();
+  ctx->d_lamK1.release();
+  ctx->d_lamKa.release();
+  ctx->d_lamKb.release();
   delete ctx;
 }
 
@@ -914,6 +924,115 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
   PERK_CUDA(ctx, cudaMemcpyAsync(&m, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *dt = cfl * m / (double)NN;
+  return PERK_OK;
+}
+
+perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_Y || !d_V || !d_Kd) return fail(ctx, PERK_E_INVALID_ARG, "null array");
+  if (stage >= 0 && (!ctx->has_tab || stage >= ctx->S)) return fail(ctx, PERK_E_INVALID_ARG, "bad stage %d", stage);
+  const int64_t ne = stage < 0 ? ctx->n_elem : ctx->act_el[stage];
+  const int64_t ni = stage < 0 ? ctx->n_if : ctx->act_if[stage];
+  const int64_t nm = stage < 0 ? ctx->n_mort : ctx->act_mort[stage];
+  PERK_CUDA(ctx, ctx->d_surf_d.ensure((size_t)ctx->n_elem * ELEM));
+  PERK_CUDA(ctx, launch_jvp(ctx->stream, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p, ne,
+                            ctx->d_elem_sorted.p, ctx->d_level.p, 2.0 / ctx->length, d_Y, d_V, ctx->d_logtab.p,
+                            ctx->d_surf.p, ctx->d_surf_d.p, nullptr, d_Kd));
+  return PERK_OK;
+}
+
+perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_lam, double* d_g) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_Y || !d_lam || !d_g) return fail(ctx, PERK_E_INVALID_ARG, "null array");
+  if (stage >= 0 && (!ctx->has_tab || stage >= ctx->S)) return fail(ctx, PERK_E_INVALID_ARG, "bad stage %d", stage);
+  const int64_t na = stage < 0 ? ctx->n_elem : ctx->act_el[stage];
+  const int64_t ni = stage < 0 ? ctx->n_if : ctx->act_if[stage];
+  const int64_t nm = stage < 0 ? ctx->n_mort : ctx->act_mort[stage];
+  PERK_CUDA(ctx, ctx->d_surf_d.ensure((size_t)ctx->n_elem * ELEM));
+  PERK_CUDA(ctx, launch_vjp(ctx->stream, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p, ctx->n_elem, na,
+                            ctx->d_elem_sorted.p, ctx->d_level.p, 2.0 / ctx->length, d_Y, d_lam, ctx->d_logtab.p,
+                            ctx->d_surf_d.p, d_g));
+  return PERK_OK;
+}
+
+perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
+    return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
+  if (!d_Un || !d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1 || !(dt > 0.0) || !std::isfinite(dt))
+    return fail(ctx, PERK_E_INVALID_ARG, "bad arguments (lam_n and lam_np1 must be distinct)");
+  const int S = ctx->S;
+  const size_t nd = (size_t)ctx->n_elem * ELEM;
+  cudaStream_t st = ctx->stream;
+  PERK_CUDA(ctx, ctx->d_Kall.ensure(nd * S));
+  PERK_CUDA(ctx, ctx->d_Ystage.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_g.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_lamK1.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_lamKa.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_lamKb.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_surf_d.ensure(nd));
+  if (!(dt == ctx->cur_dt)) {
+    PERK_CUDA(ctx, launch_set_scalar(st, ctx->d_dt.p, dt));
+    ctx->cur_dt = dt;
+  }
+  double* K = ctx->d_Kall.p;
+  // forward: every stage of the step, stored (stage i in K + i * nd)
+  for (int i = 0; i < S; ++i) {
+    StageArgs sa{};
+    sa.U = d_Un;
+    sa.K1 = K;
+    sa.Kp = K + (size_t)(i > 0 ? i - 1 : 0) * nd;
+    sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
+    sa.dt = ctx->d_dt.p;
+    PERK_CUDA(ctx, launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
+                                ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
+    PERK_CUDA(ctx, launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
+                                 ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, K + (size_t)i * nd, nullptr,
+                                 ctx->d_logtab.p));
+  }
+  // reverse: seed with the final update U_{n+1} = U_n + dt (b1 K_1 + b_{S-1} K_{S-1} + b_S K_S)
+  double b1 = 0.0, bp = 0.0, bs = 1.0;
+  if (ctx->order == 3) {
+    b1 = 1.0 / 6.0;
+    bp = 1.0 / 6.0;
+    bs = 2.0 / 3.0;
+  }
+  double* lam_cur = ctx->d_lamKa.p;    // adjoint of K_i at the current stage i
+  double* lam_prev = ctx->d_lamKb.p;   // adjoint of K_{i-1}, being accumulated
+  double* lamK1 = ctx->d_lamK1.p;
+  if (S == 1) {
+    PERK_CUDA(ctx, launch_adj_seed(st, ctx->n_elem, dt, 0.0, 0.0, b1 + bp + bs, d_lam_np1, d_lam_n, lam_prev, nullptr,
+                                   lamK1));
+  } else {
+    PERK_CUDA(ctx, launch_adj_seed(st, ctx->n_elem, dt, b1, bp, bs, d_lam_np1, d_lam_n, lamK1,
+                                   S - 1 > 1 ? lam_prev : nullptr, lam_cur));
+    if (S - 1 == 1 && bp != 0.0) return fail(ctx, PERK_E_INVALID_ARG, "third order needs S >= 3");
+  }
+  for (int i = S - 1; i >= 0; --i) {
+    // adjoint of K_i is in lam_cur (for i == 0 it is the accumulated lamK1)
+    double* lam_i = (i == 0) ? lamK1 : lam_cur;
+    const StageCoef* coef = (i == 0) ? nullptr : ctx->d_coef.p + (size_t)i * MAX_R;
+    PERK_CUDA(ctx, launch_combine(st, ctx->n_elem, ctx->d_method.p, coef, dt, d_Un, K,
+                                  K + (size_t)(i > 0 ? i - 1 : 0) * nd, ctx->d_Ystage.p));
+    PERK_CUDA(ctx, launch_vjp(st, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p,
+                              ctx->n_elem, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, 2.0 / ctx->length,
+                              ctx->d_Ystage.p, lam_i, ctx->d_logtab.p, ctx->d_surf_d.p, ctx->d_g.p));
+    if (i == 0) {
+      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, nullptr, dt, ctx->d_g.p, d_lam_n, nullptr,
+                                      nullptr));
+    } else {
+      // contributions to K_{i-1}: into lamK1 when i - 1 == 0, else into lam_prev (zero unless seeded)
+      double* target = (i - 1 == 0) ? lamK1 : lam_prev;
+      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, coef, dt, ctx->d_g.p, d_lam_n, lamK1, target));
+      if (i - 1 > 0) {
+        std::swap(lam_cur, lam_prev);   // lam_cur <- adjoint of K_{i-1}
+        // the next stage's lam_prev must start at zero (only the seed may pre-fill K_{S-1})
+        PERK_CUDA(ctx, cudaMemsetAsync(lam_prev, 0, nd * sizeof(double), st));
+      }
+    }
+  }
   return PERK_OK;
 }
 
