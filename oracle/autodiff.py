@@ -38,10 +38,15 @@ def _phys(u, d, g):
 
 
 def _log_mean(a, b):
+    # as euler.log_mean: the artanh series for |f| < 1e-2 (smooth across a == b), log1p otherwise
     d = b - a
-    same = d == 0.0
-    safe = torch.where(same, torch.ones_like(d), d)
-    return torch.where(same, a, safe / torch.log1p(safe / a))
+    s = a + b
+    f = d / s
+    u = f * f
+    small = torch.abs(f) < 1e-2
+    series = s / (2.0 * (1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0))
+    safe = torch.where(small, torch.ones_like(d), d)
+    return torch.where(small, series, safe / torch.log1p(safe / a))
 
 
 def ec_flux(uL, uR, d, g=GAMMA):

@@ -36,15 +36,23 @@ def physical_flux(u, direction: int, gamma=GAMMA):
 def log_mean(a, b):
     """Logarithmic mean (b - a) / (ln b - ln a), equal to a when a == b.
 
-    Evaluated as (b - a) / log1p((b - a) / a): the difference is exact for
-    close arguments and log1p keeps full relative accuracy there.
+    With f = (b - a)/(b + a) and u = f^2:  ln(b/a) = 2 artanh f = 2 f sum_k u^k/(2k+1),
+    so the mean is (a + b) / (2 sum_k u^k/(2k+1)).  For |f| < 1e-2 this series
+    (to u^3; remainder below 1e-17 relative) is used, as in the stable
+    evaluation of Ismail and Roe (J. Comput. Phys. 228, 2009); it is smooth
+    across a == b.  Otherwise (b - a) / log1p((b - a)/a), where log1p keeps full
+    relative accuracy.
     """
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     d = b - a
-    same = d == 0.0
-    safe = np.where(same, 1.0, d)
-    return np.where(same, a, safe / np.log1p(safe / a))
+    s = a + b
+    f = d / s
+    u = f * f
+    small = np.abs(f) < 1e-2
+    series = s / (2.0 * (1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0))
+    safe = np.where(small, 1.0, d)
+    return np.where(small, series, safe / np.log1p(safe / a))
 
 
 def ec_flux(uL, uR, direction: int, gamma=GAMMA):

@@ -534,7 +534,9 @@ __device__ __forceinline__ double lift_coef(int face, double two_over_len, int l
 
 __global__ void __launch_bounds__(128) k_vjp_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
                                                     int64_t n_mort, const int4* __restrict__ morts, int64_t if_blocks,
-                                                    const int32_t* __restrict__ level, double two_over_len,
+                                                    const int32_t* __restrict__ level,
+                                                    const int32_t* __restrict__ method, int min_member,
+                                                    double two_over_len,
                                                     const double* __restrict__ Y, const double* __restrict__ lam,
                                                     const double* __restrict__ logt, double* __restrict__ gsurf) {
   using D8 = Dual<8>;
@@ -586,9 +588,10 @@ __global__ void __launch_bounds__(128) k_vjp_faces(Ops ops, int64_t n_if, const 
   const int large_face = large_side == 0 ? 2 * dir + 1 : 2 * dir;
   const int small_face = large_side == 0 ? 2 * dir : 2 * dir + 1;
   const int small = half ? r.z : r.y;
-  // adjoint of the large face's projected flux phi at its node k (threads of half 0 write it)
+  // adjoint of the large face's projected flux phi at its node k (threads of half 0 write it);
+  // a large element whose member is not active at this stage has no K here (lam counts as zero)
   if (valid && half == 0) {
-    const double cl = lift_coef(large_face, two_over_len, level[r.x], iw);
+    const double cl = method[r.x] >= min_member ? lift_coef(large_face, two_over_len, level[r.x], iw) : 0.0;
     for (int v = 0; v < 4; ++v) s_gphi[lm][v][k] = cl * lam[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, k)];
   }
   __syncthreads();
@@ -836,14 +839,14 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
 
 cudaError_t launch_vjp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                        const int4* morts, int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level,
-                       double two_over_len, const double* Y, const double* lam, const double* logt, double* gsurf,
-                       double* g) {
+                       const int32_t* method, int min_member, double two_over_len, const double* Y,
+                       const double* lam, const double* logt, double* gsurf, double* g) {
   cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int64_t bi = (n_if + 31) / 32, bm = (n_mort + 15) / 16;
   if (bi + bm > 0)
-    ad::k_vjp_faces<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level, two_over_len, Y,
-                                                         lam, logt, gsurf);
+    ad::k_vjp_faces<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level, method, min_member,
+                                                         two_over_len, Y, lam, logt, gsurf);
   if (n_all > 0)
     ad::k_vjp_volume<<<(unsigned)((n_all + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS), 64, 0, st>>>(ops, n_all, n_act, elems, level, two_over_len, Y,
                                                                   lam, gsurf, logt, g);

@@ -927,6 +927,15 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
   return PERK_OK;
 }
 
+// smallest member active at a stage (members are active from the finest down): K_1 everywhere,
+// otherwise members with E >= S - stage + 1
+static int min_active_member(const perk_ctx* ctx, int stage) {
+  if (stage <= 0 || !ctx->has_tab) return 0;
+  for (int r = 0; r < ctx->R; ++r)
+    if (ctx->E[r] >= ctx->S - stage + 1) return r;
+  return ctx->R;
+}
+
 perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd) {
   if (!ctx) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
@@ -952,8 +961,8 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
   const int64_t nm = stage < 0 ? ctx->n_mort : ctx->act_mort[stage];
   PERK_CUDA(ctx, ctx->d_surf_d.ensure((size_t)ctx->n_elem * ELEM));
   PERK_CUDA(ctx, launch_vjp(ctx->stream, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p, ctx->n_elem, na,
-                            ctx->d_elem_sorted.p, ctx->d_level.p, 2.0 / ctx->length, d_Y, d_lam, ctx->d_logtab.p,
-                            ctx->d_surf_d.p, d_g));
+                            ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, min_active_member(ctx, stage),
+                            2.0 / ctx->length, d_Y, d_lam, ctx->d_logtab.p, ctx->d_surf_d.p, d_g));
   return PERK_OK;
 }
 
@@ -1017,8 +1026,9 @@ perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const do
     PERK_CUDA(ctx, launch_combine(st, ctx->n_elem, ctx->d_method.p, coef, dt, d_Un, K,
                                   K + (size_t)(i > 0 ? i - 1 : 0) * nd, ctx->d_Ystage.p));
     PERK_CUDA(ctx, launch_vjp(st, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p,
-                              ctx->n_elem, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, 2.0 / ctx->length,
-                              ctx->d_Ystage.p, lam_i, ctx->d_logtab.p, ctx->d_surf_d.p, ctx->d_g.p));
+                              ctx->n_elem, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p,
+                              min_active_member(ctx, i), 2.0 / ctx->length, ctx->d_Ystage.p, lam_i, ctx->d_logtab.p,
+                              ctx->d_surf_d.p, ctx->d_g.p));
     if (i == 0) {
       PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, nullptr, dt, ctx->d_g.p, d_lam_n, nullptr,
                                       nullptr));

@@ -69,3 +69,23 @@ def test_step_adjoint_vs_central_differences():
     # the torch step equals the numpy step
     Ut = perk_step_torch(TorchDGSEM(m, 3, "hll"), torch.tensor(U), dt, fam, meth).numpy()
     assert np.max(np.abs(Ut - prkm_step(rhs, U, dt, fam, meth))) < 1e-13
+
+
+def test_derivatives_at_tied_arguments():
+    # the continuous Kelvin-Helmholtz state has exactly equal neighbouring values
+    # (density depends on y only, unit pressure): the logarithmic mean must be
+    # differentiated through its smooth series there, not through a tie branch
+    from perk_inputs import kelvin_helmholtz, nodal_state
+    m = TreeMesh(CELLS, -1.0, 2.0)
+    U = nodal_state(kelvin_helmholtz, CELLS, -1.0, 2.0, X3)
+    assert np.any(U[:, 0, :, 0] == U[:, 0, :, 1])          # ties present
+    rng = np.random.default_rng(6)
+    v, w = rng.normal(size=U.shape), rng.normal(size=U.shape)
+    dg = TorchDGSEM(m, 3, "hllc")
+    jv = jvp_rhs(dg, U, v)
+    rhs = DGSEM(m, 3, "hllc").rhs
+    eps = 1e-6
+    fd = (rhs(U + eps * v) - rhs(U - eps * v)) / (2 * eps)
+    assert np.max(np.abs(fd - jv)) < 1e-7 * np.max(np.abs(jv))
+    jt = vjp_rhs(dg, U, w)
+    assert abs(np.sum(jv * w) - np.sum(v * jt)) < 1e-12 * np.sum(np.abs(jv * w))
