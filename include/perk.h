@@ -65,7 +65,7 @@ perk_status perk_set_stream(perk_ctx* ctx, void* stream);
 
 /* Mesh upload (Sec. 6.2, TreeMesh).  cells[3*e + {0,1,2}] = (level, ix, iy) of
  * leaf e: level 0 is the periodic square [x0, x0+length]^2 and the cell covers
- * [ix, ix+1) x [iy, iy+1) in units of length / 2^level.  The leaves must tile
+ * [ix, ix+1) x [iy, iy+1) in units of length / 2^level (level <= 20).  The leaves must tile
  * the square exactly and be 2:1 balanced across faces (else INVALID_ARG).
  * Builds interfaces (equal-size faces) and mortars (2:1 hanging faces) on the
  * host, uploads them, and runs the level partition (perk_partition) if a
@@ -82,6 +82,20 @@ perk_status perk_mesh_upload(perk_ctx* ctx, int64_t n_cells, const int32_t* cell
  * filled only if their capacities (in records) suffice. */
 perk_status perk_mesh_faces(int64_t n_cells, const int32_t* cells, int64_t* n_if, int32_t* ifs, int64_t if_cap,
                             int64_t* n_mort, int32_t* morts, int64_t mort_cap);
+
+/* Ensemble of independent simulations in one context (batching): member m's
+ * leaves are cells[3 * (offset_m + k) + ...], k < n_cells[m], with the same
+ * conventions as perk_mesh_upload, every member on its own periodic square
+ * [x0, x0 + length]^2.  Elements are numbered member after member; faces never
+ * cross members.  Each member has its own level partition (its finest present
+ * level gets the finest P-ERK member), but all members share one coefficient
+ * table, so one launch per kernel and stage covers the active work of every
+ * member.  perk_step gives every member the same dt; perk_step_dts one dt per
+ * member.  AMR (perk_adapt_*) adapts every member's mesh. */
+perk_status perk_ensemble_upload(perk_ctx* ctx, int n_members, const int64_t* n_cells, const int32_t* cells, double x0,
+                                 double length);
+/* Member of every element (host, n_elem int32), cap in elements. */
+perk_status perk_get_members(const perk_ctx* ctx, int32_t* member, int64_t cap);
 
 typedef struct {
   int64_t n_elem;
@@ -146,6 +160,9 @@ perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double*
  * flag is raised (read it with perk_check).  Asynchronous. */
 perk_status perk_step(perk_ctx* ctx, double* d_U, double dt);
 
+/* perk_step with one step size per ensemble member (host array dts[n_members]). */
+perk_status perk_step_dts(perk_ctx* ctx, double* d_U, const double* dts);
+
 /* Synchronises the stream and returns PERK_E_NONFINITE if any step since the
  * last check was rejected (then clears the flag), else PERK_OK. */
 perk_status perk_check(perk_ctx* ctx);
@@ -153,6 +170,10 @@ perk_status perk_check(perk_ctx* ctx);
 /* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed
  * on the device (Eq. CFL_DG, Eq. TimestepConstraint).  Blocks; *dt receives it. */
 perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double* dt);
+
+/* The step size of every ensemble member (host array dts[n_members]); for a
+ * single mesh dts[0] equals perk_compute_dt's value.  Blocks. */
+perk_status perk_compute_dt_members(perk_ctx* ctx, const double* d_U, double cfl, double* dts);
 
 /* Counters accumulated since creation (reporting, Sec. 6.4.1). */
 typedef struct {

@@ -114,6 +114,24 @@ class PerkSolver:
         self.n_elem = len(arr)
         self.x0, self.length = float(x0), float(length)
         self.cells = arr
+        self.n_members = 1
+
+    def upload_ensemble(self, members, x0: float, length: float):
+        """Independent meshes (a list of leaf lists) advanced together by one context."""
+        arrs = [np.asarray(c, dtype=np.int32).reshape(-1, 3) for c in members]
+        counts = (C.c_int64 * len(arrs))(*[len(a) for a in arrs])
+        cat = np.ascontiguousarray(np.concatenate(arrs))
+        self._call(self.lib.perk_ensemble_upload, len(arrs), counts, cat.ctypes.data_as(C.POINTER(C.c_int32)),
+                   C.c_double(x0), C.c_double(length))
+        self.n_elem = len(cat)
+        self.x0, self.length = float(x0), float(length)
+        self.cells = cat
+        self.n_members = len(arrs)
+
+    def members(self):
+        m = np.zeros(self.n_elem, dtype=np.int32)
+        self._call(self.lib.perk_get_members, m.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(self.n_elem))
+        return m
 
     def set_tableau(self, order: int, E: Sequence[int], c, a):
         E = [int(e) for e in E]
@@ -169,10 +187,22 @@ class PerkSolver:
         self._call(self.lib.perk_rhs_active, int(stage), C.c_void_p(_ptr(Y)), C.c_void_p(_ptr(K)))
         return K
 
-    def step(self, U, dt: float):
+    def step(self, U, dt):
+        """One step; dt is a number, or one number per ensemble member."""
         U = self._state(U)
-        self._call(self.lib.perk_step, C.c_void_p(_ptr(U)), C.c_double(dt))
+        if np.ndim(dt) == 0:
+            self._call(self.lib.perk_step, C.c_void_p(_ptr(U)), C.c_double(float(dt)))
+        else:
+            d = np.ascontiguousarray(dt, dtype=np.float64)
+            self._call(self.lib.perk_step_dts, C.c_void_p(_ptr(U)), d.ctypes.data_as(C.POINTER(C.c_double)))
         return U
+
+    def compute_dt_members(self, U, cfl: float):
+        U = self._state(U)
+        out = np.zeros(getattr(self, "n_members", 1))
+        self._call(self.lib.perk_compute_dt_members, C.c_void_p(_ptr(U)), C.c_double(cfl),
+                   out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
 
     def step_profiled(self, U, dt: float, acc=None):
         """One step with per-kernel CUDA-event timing; returns the accumulated times."""
@@ -224,6 +254,7 @@ class PerkSolver:
         self._call(self.lib.perk_adapt_commit, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(Unew)))
         self.n_elem = n_new.value
         cells = np.zeros((self.n_elem, 3), dtype=np.int32)
+        self.n_members = getattr(self, "n_members", 1)
         self._call(self.lib.perk_get_cells, cells.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(self.n_elem))
         self.cells = cells
         return Unew

@@ -52,6 +52,11 @@ SIGNATURES = [
     ("perk_mesh_faces", C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                   C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int64]),
     ("perk_mesh_query", C.c_int, [C.c_void_p, C.POINTER(PerkMeshInfo)]),
+    ("perk_ensemble_upload", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_double,
+                                       C.c_double]),
+    ("perk_get_members", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
+    ("perk_step_dts", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    ("perk_compute_dt_members", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk_set_tableau", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_perk2_disk_tableau", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double),

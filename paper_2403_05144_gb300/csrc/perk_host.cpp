@@ -221,11 +221,15 @@ struct perk_ctx {
   double x0 = 0.0, length = 1.0;
   std::vector<int32_t> h_level;
   std::vector<int32_t> h_cells;   // [n_elem][3] (level, ix, iy)
+  int n_members = 1;              // ensemble members (independent meshes in one context)
+  std::vector<int32_t> h_member;  // [n_elem] member of each element
+  std::vector<double> cur_dts;    // dt of each member as last set on the device
   std::vector<int4> h_if, h_mort;
 
   // pending AMR plan (perk_adapt_plan -> perk_adapt_commit)
   bool has_plan = false;
   std::vector<int32_t> plan_cells;   // new leaves [n][3]
+  std::vector<int32_t> plan_member;  // their ensemble members
   std::vector<int32_t> plan_map;     // [n][5] transfer records
   DevBuf<int32_t> d_map;
   DevBuf<double> d_eta;
@@ -246,7 +250,7 @@ struct perk_ctx {
   int64_t act_el[MAX_S] = {}, act_if[MAX_S] = {}, act_mort[MAX_S] = {};
 
   // device buffers
-  DevBuf<int32_t> d_level, d_method, d_elem_sorted, d_E, d_minmax;
+  DevBuf<int32_t> d_level, d_method, d_elem_sorted, d_E, d_minmax, d_member, d_member_lmax;
   DevBuf<int4> d_if_raw, d_mort_raw, d_if_sorted, d_mort_sorted;
   DevBuf<int64_t> d_counts;
   DevBuf<double> d_surf, d_K1, d_Ka, d_Kb, d_dt, d_block_min, d_dt_out;
@@ -257,7 +261,6 @@ struct perk_ctx {
   // graph of one step
   cudaGraphExec_t graph = nullptr;
   double* graph_U = nullptr;
-  double cur_dt = NAN;
 
   perk_counters counters{};
 };
@@ -300,46 +303,57 @@ struct CellKey {
 struct CellHash {
   size_t operator()(const CellKey& k) const { return std::hash<int64_t>()(k.v); }
 };
-inline CellKey key_of(int l, int64_t ix, int64_t iy) { return CellKey{((int64_t)l << 56) | (ix << 28) | iy}; }
+// member (16 bits) | level (5 bits) | ix (21 bits) | iy (21 bits)
+inline CellKey key_of(int m, int l, int64_t ix, int64_t iy) {
+  return CellKey{((int64_t)m << 47) | ((int64_t)l << 42) | (ix << 21) | iy};
+}
+constexpr int MAX_LEVEL = 20;
+constexpr int MAX_MEMBERS = 65535;
 
 // Interfaces and mortars of a periodic, 2:1-balanced leaf list by a walk over
 // each leaf's four face neighbourhoods in the implicit quadtree.
-perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, std::vector<int4>& ifs,
-                               std::vector<int4>& morts) {
+perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, const int32_t* member,
+                               std::vector<int4>& ifs, std::vector<int4>& morts) {
   std::unordered_map<CellKey, int32_t, CellHash> leaf;
   leaf.reserve((size_t)n * 2);
-  int lmax = 0;
+  int n_members = 1;
   for (int64_t e = 0; e < n; ++e) {
     const int l = cells[3 * e], ix = cells[3 * e + 1], iy = cells[3 * e + 2];
-    if (l < 0 || l > 27) return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: level %d out of range", (long long)e, l);
+    const int m = member ? member[e] : 0;
+    if (l < 0 || l > MAX_LEVEL) return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: level %d out of range", (long long)e, l);
+    if (m < 0 || m >= MAX_MEMBERS) return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: member out of range", (long long)e);
+    n_members = std::max(n_members, m + 1);
     const int64_t side = (int64_t)1 << l;
     if (ix < 0 || iy < 0 || ix >= side || iy >= side)
       return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: index outside level %d", (long long)e, l);
-    if (!leaf.emplace(key_of(l, ix, iy), (int32_t)e).second)
+    if (!leaf.emplace(key_of(m, l, ix, iy), (int32_t)e).second)
       return fail(ctx, PERK_E_INVALID_ARG, "cell %lld duplicated", (long long)e);
-    lmax = std::max(lmax, l);
   }
-  // exact tiling: areas sum to the square and no leaf has a leaf ancestor
-  long double area = 0.0L;
-  for (int64_t e = 0; e < n; ++e) area += std::ldexp(1.0L, -2 * cells[3 * e]);
-  if (std::fabs((double)(area - 1.0L)) > 1e-12) return fail(ctx, PERK_E_INVALID_ARG, "cells do not tile the domain");
+  // exact tiling of every member's square and no leaf with a leaf ancestor
+  std::vector<long double> area(n_members, 0.0L);
+  for (int64_t e = 0; e < n; ++e) area[member ? member[e] : 0] += std::ldexp(1.0L, -2 * cells[3 * e]);
+  for (int m = 0; m < n_members; ++m)
+    if (std::fabs((double)(area[m] - 1.0L)) > 1e-12)
+      return fail(ctx, PERK_E_INVALID_ARG, "cells of member %d do not tile the domain", m);
   for (int64_t e = 0; e < n; ++e) {
     int l = cells[3 * e];
     int64_t ix = cells[3 * e + 1], iy = cells[3 * e + 2];
+    const int m = member ? member[e] : 0;
     while (l > 0) {
       --l;
       ix >>= 1;
       iy >>= 1;
-      if (leaf.count(key_of(l, ix, iy))) return fail(ctx, PERK_E_INVALID_ARG, "cells overlap");
+      if (leaf.count(key_of(m, l, ix, iy))) return fail(ctx, PERK_E_INVALID_ARG, "cells overlap");
     }
   }
-  auto find = [&](int l, int64_t ix, int64_t iy) -> int32_t {
-    auto it = leaf.find(key_of(l, ix, iy));
-    return it == leaf.end() ? -1 : it->second;
-  };
   for (int64_t e = 0; e < n; ++e) {
     const int l = cells[3 * e];
     const int64_t ix = cells[3 * e + 1], iy = cells[3 * e + 2];
+    const int mb = member ? member[e] : 0;
+    auto find = [&](int ll, int64_t x, int64_t y) -> int32_t {
+      auto it = leaf.find(key_of(mb, ll, x, y));
+      return it == leaf.end() ? -1 : it->second;
+    };
     const int64_t side = (int64_t)1 << l;
     for (int dir = 0; dir < 2; ++dir) {
       // +dir neighbour region (same level)
@@ -352,7 +366,7 @@ perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, s
         // this leaf is the small side of a mortar whose large side is the +dir neighbour: built there
       } else {
         // the +dir region must be refined once: its two children along the face
-        const int64_t cx0 = dir == 0 ? 2 * px : 2 * px, cy0 = dir == 0 ? 2 * py : 2 * py;
+        const int64_t cx0 = 2 * px, cy0 = 2 * py;
         const int32_t s0 = find(l + 1, cx0, cy0);
         const int32_t s1 = find(l + 1, dir == 0 ? cx0 : cx0 + 1, dir == 0 ? cy0 + 1 : cy0);
         if (s0 < 0 || s1 < 0) return fail(ctx, PERK_E_INVALID_ARG, "mesh not 2:1 balanced at cell %lld", (long long)e);
@@ -385,7 +399,8 @@ perk_status run_partition(perk_ctx* ctx) {
   PERK_CUDA(ctx, ctx->d_E.ensure(MAX_R));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_E.p, E, sizeof(int32_t) * MAX_R, cudaMemcpyHostToDevice, ctx->stream));
   PERK_CUDA(ctx, launch_partition(ctx->stream, ctx->n_elem, ctx->n_if, ctx->n_mort, ctx->d_level.p, ctx->d_if_raw.p,
-                                  ctx->d_mort_raw.p, R, S, ctx->d_E.p, ctx->d_method.p, ctx->d_elem_sorted.p,
+                                  ctx->d_mort_raw.p, R, S, ctx->d_E.p, ctx->n_members > 1 ? ctx->d_member.p : nullptr,
+                                  ctx->n_members, ctx->d_member_lmax.p, ctx->d_method.p, ctx->d_elem_sorted.p,
                                   ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_counts.p, ctx->d_minmax.p));
   int64_t counts[3 * MAX_S];
   int32_t mm[2];
@@ -402,6 +417,28 @@ perk_status run_partition(perk_ctx* ctx) {
   ctx->part_S = S;
   ctx->partitioned = true;
   drop_graph(ctx);
+  return PERK_OK;
+}
+
+// device dt of every member: dts[m] (per member) or the same dt for all; uploads only on change
+perk_status set_dts(perk_ctx* ctx, const double* dts, double dt) {
+  bool changed = false;
+  for (int m = 0; m < ctx->n_members; ++m) {
+    const double v = dts ? dts[m] : dt;
+    if (!std::isfinite(v) || !(v > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad dt of member %d", m);
+    if (!(ctx->cur_dts[m] == v)) {
+      ctx->cur_dts[m] = v;
+      changed = true;
+    }
+  }
+  if (!changed) return PERK_OK;
+  if (ctx->n_members == 1) {
+    PERK_CUDA(ctx, launch_set_scalar(ctx->stream, ctx->d_dt.p, ctx->cur_dts[0]));
+  } else {
+    // pageable source: the call returns once the values are staged, so the vector may change afterwards
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_dt.p, ctx->cur_dts.data(), ctx->n_members * sizeof(double),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+  }
   return PERK_OK;
 }
 
@@ -437,12 +474,29 @@ struct LaunchTimer {
     if (timer) PERK_CUDA(ctx, (timer)->end(st, kind)); \
   } while (0)
 
-perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, double x0, double length) {
+perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const int32_t* member, double x0,
+                     double length) {
   std::vector<int4> ifs, morts;
   ifs.reserve((size_t)n_cells * 2);
-  perk_status s = build_connectivity(ctx, n_cells, cells, ifs, morts);
+  perk_status s = build_connectivity(ctx, n_cells, cells, member, ifs, morts);
   if (s != PERK_OK) return s;
   drop_graph(ctx);
+  int n_members = 1;
+  ctx->h_member.assign(n_cells, 0);
+  if (member)
+    for (int64_t e = 0; e < n_cells; ++e) {
+      ctx->h_member[e] = member[e];
+      n_members = std::max(n_members, member[e] + 1);
+    }
+  if (n_members != ctx->n_members || (int)ctx->cur_dts.size() != n_members) {
+    ctx->n_members = n_members;
+    ctx->cur_dts.assign(n_members, NAN);
+  }
+  PERK_CUDA(ctx, ctx->d_dt.ensure((size_t)n_members));
+  PERK_CUDA(ctx, ctx->d_member_lmax.ensure((size_t)n_members));
+  PERK_CUDA(ctx, ctx->d_member.ensure((size_t)n_cells));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_member.p, ctx->h_member.data(), n_cells * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, ctx->stream));
   ctx->n_elem = n_cells;
   ctx->n_if = (int64_t)ifs.size();
   ctx->n_mort = (int64_t)morts.size();
@@ -495,8 +549,9 @@ void balance_levels(const perk_ctx* ctx, std::vector<int32_t>& d) {
   const int64_t n = ctx->n_elem;
   const int32_t* c = ctx->h_cells.data();
   std::unordered_map<CellKey, std::vector<int32_t>, CellHash> groups;
+  const int32_t* mb = ctx->h_member.data();
   for (int64_t e = 0; e < n; ++e)
-    if (c[3 * e] > 0) groups[key_of(c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)].push_back((int32_t)e);
+    if (c[3 * e] > 0) groups[key_of(mb[e], c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)].push_back((int32_t)e);
   std::vector<std::pair<int32_t, int32_t>> pairs;
   for (const int4& f : ctx->h_if) pairs.emplace_back(f.x, f.y);
   for (const int4& m : ctx->h_mort) {
@@ -508,7 +563,7 @@ void balance_levels(const perk_ctx* ctx, std::vector<int32_t>& d) {
     changed = false;
     for (int64_t e = 0; e < n; ++e) {
       if (d[e] >= c[3 * e]) continue;
-      const auto& g = groups[key_of(c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)];
+      const auto& g = groups[key_of(mb[e], c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)];
       bool ok = g.size() == 4;
       for (int32_t m : g) ok = ok && d[m] < c[3 * m];
       if (!ok)
@@ -549,6 +604,7 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
   ua.U = d_U;
   ua.K1 = ctx->d_K1.p;
   ua.flag = ctx->d_flag.p;
+  ua.member = ctx->n_members > 1 ? ctx->d_member.p : nullptr;
   for (int i = 0; i < S; ++i) {
     // K_1 has its own buffer; K_2, K_3, ... alternate between the two others
     cur = (i == 0) ? 0 : (i % 2 == 1 ? 1 : 2);
@@ -558,6 +614,7 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
     sa.Kp = Kbuf[prev];
     sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
     sa.dt = ctx->d_dt.p;
+    sa.member = ctx->n_members > 1 ? ctx->d_member.p : nullptr;
     TIMED(ctx, timer, st, 0,
           launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
                        ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
@@ -633,6 +690,8 @@ void perk_destroy(perk_ctx* ctx) {
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->d_level.release();
+  ctx->d_member.release();
+  ctx->d_member_lmax.release();
   ctx->d_method.release();
   ctx->d_elem_sorted.release();
   ctx->d_E.release();
@@ -677,14 +736,37 @@ perk_status perk_mesh_upload(perk_ctx* ctx, int64_t n_cells, const int32_t* cell
   if (n_cells <= 0 || !cells || !(length > 0.0) || n_cells > (int64_t)1 << 30)
     return fail(ctx, PERK_E_INVALID_ARG, "invalid mesh arguments");
   ctx->has_plan = false;
-  return set_mesh(ctx, n_cells, cells, x0, length);
+  return set_mesh(ctx, n_cells, cells, nullptr, x0, length);
+}
+
+perk_status perk_ensemble_upload(perk_ctx* ctx, int n_members, const int64_t* n_cells, const int32_t* cells, double x0,
+                                 double length) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (n_members < 1 || n_members > MAX_MEMBERS || !n_cells || !cells || !(length > 0.0))
+    return fail(ctx, PERK_E_INVALID_ARG, "invalid ensemble arguments");
+  std::vector<int32_t> member;
+  for (int m = 0; m < n_members; ++m) {
+    if (n_cells[m] <= 0) return fail(ctx, PERK_E_INVALID_ARG, "member %d has no cells", m);
+    member.insert(member.end(), (size_t)n_cells[m], m);
+  }
+  if ((int64_t)member.size() > (int64_t)1 << 30) return fail(ctx, PERK_E_INVALID_ARG, "ensemble too large");
+  ctx->has_plan = false;
+  return set_mesh(ctx, (int64_t)member.size(), cells, member.data(), x0, length);
+}
+
+perk_status perk_get_members(const perk_ctx* ctx, int32_t* member, int64_t cap) {
+  if (!ctx || !member) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return PERK_E_NOT_READY;
+  if (cap < ctx->n_elem) return PERK_E_INVALID_ARG;
+  std::copy(ctx->h_member.begin(), ctx->h_member.end(), member);
+  return PERK_OK;
 }
 
 perk_status perk_mesh_faces(int64_t n_cells, const int32_t* cells, int64_t* n_if, int32_t* ifs, int64_t if_cap,
                             int64_t* n_mort, int32_t* morts, int64_t mort_cap) {
   if (n_cells <= 0 || !cells || !n_if || !n_mort) return PERK_E_INVALID_ARG;
   std::vector<int4> vi, vm;
-  perk_status s = build_connectivity(nullptr, n_cells, cells, vi, vm);
+  perk_status s = build_connectivity(nullptr, n_cells, cells, nullptr, vi, vm);
   if (s != PERK_OK) return s;
   *n_if = (int64_t)vi.size();
   *n_mort = (int64_t)vm.size();
@@ -831,16 +913,7 @@ perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double*
   return rhs_given(ctx, stage, d_Y, d_K);
 }
 
-perk_status perk_step(perk_ctx* ctx, double* d_U, double dt) {
-  if (!ctx) return PERK_E_INVALID_ARG;
-  if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
-    return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
-  if (!d_U || !std::isfinite(dt) || !(dt > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or dt");
-  if (((uintptr_t)d_U & 15) != 0) return fail(ctx, PERK_E_INVALID_ARG, "U must be 16-byte aligned");
-  if (!(dt == ctx->cur_dt)) {
-    PERK_CUDA(ctx, launch_set_scalar(ctx->stream, ctx->d_dt.p, dt));
-    ctx->cur_dt = dt;
-  }
+static perk_status step_impl(perk_ctx* ctx, double* d_U) {
   if (ctx->prob.use_graph) {
     if (!ctx->graph || ctx->graph_U != d_U) {
       drop_graph(ctx);
@@ -871,14 +944,31 @@ perk_status perk_step(perk_ctx* ctx, double* d_U, double dt) {
   return PERK_OK;
 }
 
+static perk_status step_ready(perk_ctx* ctx, double* d_U) {
+  if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
+    return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
+  if (!d_U) return fail(ctx, PERK_E_INVALID_ARG, "null U");
+  if (((uintptr_t)d_U & 15) != 0) return fail(ctx, PERK_E_INVALID_ARG, "U must be 16-byte aligned");
+  return PERK_OK;
+}
+
+perk_status perk_step(perk_ctx* ctx, double* d_U, double dt) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  perk_status s = step_ready(ctx, d_U);
+  if (s != PERK_OK) return s;
+  s = set_dts(ctx, nullptr, dt);
+  if (s != PERK_OK) return s;
+  return step_impl(ctx, d_U);
+}
+
 perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kernel_times* acc) {
   if (!ctx || !acc) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
     return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
   if (!d_U || !std::isfinite(dt) || !(dt > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or dt");
-  if (!(dt == ctx->cur_dt)) {
-    PERK_CUDA(ctx, launch_set_scalar(ctx->stream, ctx->d_dt.p, dt));
-    ctx->cur_dt = dt;
+  {
+    perk_status s = set_dts(ctx, nullptr, dt);
+    if (s != PERK_OK) return s;
   }
   LaunchTimer timer;
   perk_status s = enqueue_step(ctx, ctx->stream, d_U, &timer);
@@ -896,6 +986,31 @@ perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kerne
     ctx->counters.element_stage_evaluations += ctx->act_el[i];
     ctx->counters.dof_stage_updates += ctx->act_el[i] * NODES;
   }
+  return PERK_OK;
+}
+
+perk_status perk_step_dts(perk_ctx* ctx, double* d_U, const double* dts) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!dts) return fail(ctx, PERK_E_INVALID_ARG, "null dts");
+  perk_status s = step_ready(ctx, d_U);
+  if (s != PERK_OK) return s;
+  s = set_dts(ctx, dts, 0.0);
+  if (s != PERK_OK) return s;
+  return step_impl(ctx, d_U);
+}
+
+perk_status perk_compute_dt_members(perk_ctx* ctx, const double* d_U, double cfl, double* dts) {
+  if (!ctx || !dts) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_U || !(cfl > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or cfl");
+  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(ctx->n_members, 1024)));
+  PERK_CUDA(ctx, launch_dt_members(ctx->stream, ctx->n_elem, d_U, ctx->d_level.p, ctx->d_member.p, ctx->n_members,
+                                   ctx->length, ctx->ops.gamma, ctx->d_block_min.p));
+  std::vector<double> m(ctx->n_members);
+  PERK_CUDA(ctx, cudaMemcpyAsync(m.data(), ctx->d_block_min.p, m.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < ctx->n_members; ++q) dts[q] = cfl * m[q] / (double)NN;
   return PERK_OK;
 }
 
@@ -982,9 +1097,10 @@ perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const do
   PERK_CUDA(ctx, ctx->d_lamKa.ensure(nd));
   PERK_CUDA(ctx, ctx->d_lamKb.ensure(nd));
   PERK_CUDA(ctx, ctx->d_surf_d.ensure(nd));
-  if (!(dt == ctx->cur_dt)) {
-    PERK_CUDA(ctx, launch_set_scalar(st, ctx->d_dt.p, dt));
-    ctx->cur_dt = dt;
+  if (ctx->n_members != 1) return fail(ctx, PERK_E_INVALID_ARG, "the step adjoint takes single-member contexts");
+  {
+    perk_status s = set_dts(ctx, nullptr, dt);
+    if (s != PERK_OK) return s;
   }
   double* K = ctx->d_Kall.p;
   // forward: every stage of the step, stored (stage i in K + i * nd)
@@ -1092,49 +1208,59 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
     }
   }
   balance_levels(ctx, d);
-  // new leaves and transfer records
+  // new leaves (member by member, Morton order within a member) and transfer records
+  const int32_t* mb = ctx->h_member.data();
   std::unordered_map<CellKey, int32_t, CellHash> old;
   old.reserve((size_t)n * 2);
-  for (int64_t e = 0; e < n; ++e) old.emplace(key_of(c[3 * e], c[3 * e + 1], c[3 * e + 2]), (int32_t)e);
+  for (int64_t e = 0; e < n; ++e) old.emplace(key_of(mb[e], c[3 * e], c[3 * e + 1], c[3 * e + 2]), (int32_t)e);
   struct NewCell {
-    int32_t l, ix, iy;
+    int32_t m, l, ix, iy;
   };
   std::vector<NewCell> nc;
   nc.reserve((size_t)n * 2);
   std::unordered_map<CellKey, char, CellHash> seen;
-  int lmax = 0;
+  std::vector<int> lmax(ctx->n_members, 0);
   for (int64_t e = 0; e < n; ++e) {
-    const int l = c[3 * e], ix = c[3 * e + 1], iy = c[3 * e + 2];
+    const int l = c[3 * e], ix = c[3 * e + 1], iy = c[3 * e + 2], me = mb[e];
     if (d[e] == l + 1) {
       for (int cy = 0; cy < 2; ++cy)
-        for (int cx = 0; cx < 2; ++cx) nc.push_back({l + 1, 2 * ix + cx, 2 * iy + cy});
+        for (int cx = 0; cx < 2; ++cx) nc.push_back({me, l + 1, 2 * ix + cx, 2 * iy + cy});
     } else if (d[e] == l) {
-      nc.push_back({l, ix, iy});
-    } else if (seen.emplace(key_of(l - 1, ix >> 1, iy >> 1), 1).second) {
-      nc.push_back({l - 1, ix >> 1, iy >> 1});
+      nc.push_back({me, l, ix, iy});
+    } else if (seen.emplace(key_of(me, l - 1, ix >> 1, iy >> 1), 1).second) {
+      nc.push_back({me, l - 1, ix >> 1, iy >> 1});
     }
-    lmax = std::max(lmax, d[e]);
+    lmax[me] = std::max(lmax[me], d[e]);
   }
-  std::vector<std::pair<uint64_t, int64_t>> order(nc.size());
-  for (size_t k = 0; k < nc.size(); ++k) order[k] = {morton_key(nc[k].l, nc[k].ix, nc[k].iy, lmax), (int64_t)k};
+  struct Ord {
+    int32_t m;
+    uint64_t z;
+    int64_t k;
+    bool operator<(const Ord& o) const { return m != o.m ? m < o.m : z < o.z; }
+  };
+  std::vector<Ord> order(nc.size());
+  for (size_t k = 0; k < nc.size(); ++k)
+    order[k] = {nc[k].m, morton_key(nc[k].l, nc[k].ix, nc[k].iy, lmax[nc[k].m]), (int64_t)k};
   std::sort(order.begin(), order.end());
   const int64_t m = (int64_t)nc.size();
   ctx->plan_cells.resize(3 * m);
+  ctx->plan_member.resize(m);
   ctx->plan_map.resize(5 * m);
   for (int64_t k = 0; k < m; ++k) {
-    const NewCell& q = nc[order[k].second];
+    const NewCell& q = nc[order[k].k];
     ctx->plan_cells[3 * k] = q.l;
     ctx->plan_cells[3 * k + 1] = q.ix;
     ctx->plan_cells[3 * k + 2] = q.iy;
+    ctx->plan_member[k] = q.m;
     int32_t* r = &ctx->plan_map[5 * k];
-    auto it = old.find(key_of(q.l, q.ix, q.iy));
+    auto it = old.find(key_of(q.m, q.l, q.ix, q.iy));
     if (it != old.end()) {
       r[0] = 0;
       r[1] = it->second;
       r[2] = r[3] = r[4] = 0;
       continue;
     }
-    auto par = old.find(key_of(q.l - 1, q.ix >> 1, q.iy >> 1));
+    auto par = old.find(key_of(q.m, q.l - 1, q.ix >> 1, q.iy >> 1));
     if (par != old.end()) {
       r[0] = 1 | ((q.ix & 1) << 2) | ((q.iy & 1) << 3);
       r[1] = par->second;
@@ -1143,7 +1269,7 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
     }
     r[0] = 2;
     for (int cc = 0; cc < 4; ++cc) {
-      auto ch = old.find(key_of(q.l + 1, 2 * q.ix + (cc & 1), 2 * q.iy + (cc >> 1)));
+      auto ch = old.find(key_of(q.m, q.l + 1, 2 * q.ix + (cc & 1), 2 * q.iy + (cc >> 1)));
       if (ch == old.end()) return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
       r[1 + cc] = ch->second;
     }
@@ -1166,8 +1292,10 @@ perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Une
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->has_plan = false;
   const std::vector<int32_t> cells = std::move(ctx->plan_cells);
+  const std::vector<int32_t> members = std::move(ctx->plan_member);
   ctx->plan_cells.clear();
-  return set_mesh(ctx, m, cells.data(), ctx->x0, ctx->length);
+  ctx->plan_member.clear();
+  return set_mesh(ctx, m, cells.data(), ctx->n_members > 1 ? members.data() : nullptr, ctx->x0, ctx->length);
 }
 
 perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap) {

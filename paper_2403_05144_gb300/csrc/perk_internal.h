@@ -45,7 +45,8 @@ struct StageArgs {
   const double* K1;       //            K_1
   const double* Kp;       //            K_{i-1}
   const StageCoef* coef;  //            [R] coefficients of this stage
-  const double* dt;       //            device scalar
+  const double* dt;       //            device array: dt of each ensemble member
+  const int32_t* member;  //            ensemble member of each element (nullptr: member 0)
 };
 
 // Final-update description (P-ERK2: b = e_S; P-ERK3: b on K_1, K_{S-1}, K_S).
@@ -55,14 +56,20 @@ struct UpdateArgs {
   const double* K1;
   const double* Kp;
   int* flag;              // raised (set to 1) when any new state is not admissible
+  const int32_t* member;  // ensemble member of each element (nullptr: member 0)
 };
 
 // ---- kernel launchers (perk_kernels.cu); all return cudaGetLastError() ----
 
 cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
                              const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
+                             const int32_t* member, int n_members, int32_t* member_lmax /* [n_members] */,
                              int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
                              int64_t* counts /* [3][MAX_S] */, int32_t* level_minmax /* [2] */);
+
+// per-member CFL reduction: out[m] = min over member m's elements of h_e / lambda_e (out pre-set to +inf)
+cudaError_t launch_dt_members(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level,
+                              const int32_t* member, int n_members, double length, double gamma, double* out);
 
 cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                          const int4* morts, const int32_t* method, const StageArgs& sa, double* surf);

@@ -19,6 +19,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "perk.h"
 #include "perk_internal.h"
 
@@ -337,7 +339,7 @@ __device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int 
     for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.Y + base + v * NODES);
   } else {
     const StageCoef c = sa.coef[m];
-    const double dt = *sa.dt;
+    const double dt = sa.dt[sa.member ? sa.member[e] : 0];
 #pragma unroll
     for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.U + base + v * NODES);
     if (c.alpha != 0.0) {
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, cons
   }
   if (CHECK) {
     // admissibility of the state this step would commit at this node
-    const double dt = *sa.dt;
+    const double dt = sa.dt[sa.member ? sa.member[e] : 0];
     const int64_t base = e * ELEM + t;
     double un[4];
 #pragma unroll
@@ -560,10 +562,10 @@ __global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, cons
 __global__ void k_commit(int64_t n2, UpdateArgs ua, const double2* __restrict__ Ks, const double* dtp,
                          double2* __restrict__ U) {
   if (*ua.flag != 0) return;
-  const double dt = *dtp;
   const double2* K1 = reinterpret_cast<const double2*>(ua.K1);
   const double2* Kp = reinterpret_cast<const double2*>(ua.Kp);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x) {
+    const double dt = dtp[ua.member ? ua.member[q / (ELEM / 2)] : 0];
     const double2 ks = Ks[q];
     double2 inc = make_double2(ua.bs * ks.x, ua.bs * ks.y);
     if (ua.b1 != 0.0) {
@@ -622,7 +624,9 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
                                                               const int32_t* __restrict__ level,
                                                               const int4* __restrict__ if_raw,
                                                               const int4* __restrict__ mort_raw, int R, int S,
-                                                              const int32_t* __restrict__ E, int32_t* method,
+                                                              const int32_t* __restrict__ E,
+                                                              const int32_t* __restrict__ member, int n_members,
+                                                              int32_t* member_lmax, int32_t* method,
                                                               int32_t* elem_sorted, int4* if_sorted,
                                                               int4* mort_sorted, int64_t* counts,
                                                               int32_t* level_minmax) {
@@ -647,10 +651,14 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
   }
   atomicMin(&s_min, lmin);
   atomicMax(&s_max, lmax);
+  // finest level present in every ensemble member (one member: the global maximum)
+  for (int m = tid; m < n_members; m += PART_THREADS) member_lmax[m] = -1;
   __syncthreads();
-  const int Lmax = s_max;
-  // members and their counts
+  for (int64_t e = tid; e < n_elem; e += PART_THREADS) atomicMax(&member_lmax[member ? member[e] : 0], level[e]);
+  __syncthreads();
+  // P-ERK members and their counts
   for (int64_t e = tid; e < n_elem; e += PART_THREADS) {
+    const int Lmax = member_lmax[member ? member[e] : 0];
     const int mth = max(0, (R - 1) - (Lmax - level[e]));
     method[e] = mth;
     atomicAdd(&s_cnt[0][mth], 1);
@@ -866,10 +874,45 @@ cudaError_t launch_transfer(cudaStream_t st, int64_t n, const int32_t* map, cons
 
 cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
                              const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
-                             int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
-                             int64_t* counts, int32_t* level_minmax) {
-  k_partition<<<1, PART_THREADS, 0, st>>>(n_elem, n_if, n_mort, level, if_raw, mort_raw, R, S, E, method,
-                                          elem_sorted, if_sorted, mort_sorted, counts, level_minmax);
+                             const int32_t* member, int n_members, int32_t* member_lmax, int32_t* method,
+                             int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted, int64_t* counts,
+                             int32_t* level_minmax) {
+  k_partition<<<1, PART_THREADS, 0, st>>>(n_elem, n_if, n_mort, level, if_raw, mort_raw, R, S, E, member, n_members,
+                                          member_lmax, method, elem_sorted, if_sorted, mort_sorted, counts,
+                                          level_minmax);
+  return cudaGetLastError();
+}
+
+// per-member minimum of h_e / lambda_e: positive doubles order like their bit patterns
+__global__ void __launch_bounds__(DT_THREADS) k_dt_members(int64_t n_nodes, const double* __restrict__ U,
+                                                            const int32_t* __restrict__ level,
+                                                            const int32_t* __restrict__ member, double length,
+                                                            double gamma, unsigned long long* out) {
+  for (int64_t q = (int64_t)blockIdx.x * DT_THREADS + threadIdx.x; q < n_nodes; q += (int64_t)gridDim.x * DT_THREADS) {
+    const int64_t e = q / NODES;
+    const int t = (int)(q - e * NODES);
+    const double* u = U + e * ELEM + t;
+    const double rho = u[0], ir = 1.0 / rho;
+    const double v1 = u[NODES] * ir, v2 = u[2 * NODES] * ir;
+    const double p = (gamma - 1.0) * (u[3 * NODES] - 0.5 * rho * (v1 * v1 + v2 * v2));
+    const double lam = fabs(v1) + fabs(v2) + 2.0 * sqrt(gamma * p * ir);
+    const double r = ldexp(length, -level[e]) / lam;
+    if (r > 0.0) atomicMin(out + member[e], (unsigned long long)__double_as_longlong(r));
+  }
+}
+
+__global__ void k_fill(double* p, int n, double v) {
+  for (int q = threadIdx.x; q < n; q += blockDim.x) p[q] = v;
+}
+
+cudaError_t launch_dt_members(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level,
+                              const int32_t* member, int n_members, double length, double gamma, double* out) {
+  k_fill<<<1, 256, 0, st>>>(out, n_members, INFINITY);
+  const int64_t nodes = n_elem * NODES;
+  const unsigned blocks = (unsigned)std::min<int64_t>(152 * 8, (nodes + DT_THREADS - 1) / DT_THREADS);
+  if (blocks > 0)
+    k_dt_members<<<blocks, DT_THREADS, 0, st>>>(nodes, U, level, member, length, gamma,
+                                                reinterpret_cast<unsigned long long*>(out));
   return cudaGetLastError();
 }
 
