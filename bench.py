@@ -400,19 +400,194 @@ def run_perk(args) -> None:
         torch.distributed.destroy_process_group()
 
 
+def run_ensemble(args) -> None:
+    """64 Kelvin-Helmholtz members (seeded amplitude U(0.05, 0.15), wavenumber 2 or 4, finest
+    level 6 or 7), each on its own adaptively refined mesh, advanced by one context: one
+    launch per kernel and P-ERK stage for all members, per-member dt, AMR every 5 steps."""
+    import torch
+
+    from paper_2403_05144_gb300 import PerkSolver, reference_nodes
+    from paper_2403_05144_gb300.build import build
+
+    build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(20240308 + 4)
+    n = 64
+    amps = rng.uniform(0.05, 0.15, n)
+    ks = rng.choice([2, 4], n)
+    lmaxs = rng.choice([6, 7], n)
+    x, _ = reference_nodes(3)
+    # initial meshes: three adaptation cycles of every member on its own initial state
+    meshes = []
+    for m in range(n):
+        s = PerkSolver(surface_flux="hllc", use_graph=False)
+        s.upload_mesh(uniform_cells(4), -1.0, 2.0)
+        amr = dict(AMR_KH, level_max=int(lmaxs[m]))
+        for _ in range(3):
+            U = torch.from_numpy(nodal_state(kelvin_helmholtz, s.cells, -1.0, 2.0, x, amplitude=float(amps[m]),
+                                             wavenumber=int(ks[m]))).cuda()
+            s.adapt(U, **amr)
+        meshes.append(s.cells.copy())
+        del s
+    ens = PerkSolver(surface_flux="hllc", use_graph=True)
+    ens.upload_ensemble(meshes, -1.0, 2.0)
+    ens.set_perk2_disk([4, 6, 10, 16])
+    U = torch.from_numpy(np.concatenate([nodal_state(kelvin_helmholtz, c, -1.0, 2.0, x, amplitude=float(a),
+                                                     wavenumber=int(k)) for c, a, k in zip(meshes, amps, ks)])).cuda()
+    amr = dict(AMR_KH, level_max=7)
+    dts = ens.compute_dt_members(U, 0.7)
+    dof_member = [16 * len(c) for c in meshes]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    k = 0
+
+    def step():
+        nonlocal U, dts, k
+        if k > 0 and k % 5 == 0:
+            U = ens.adapt(U, **amr)
+            dts = ens.compute_dt_members(U, 0.7)
+        ens.step(U, dts)
+        k += 1
+        return ens.info()["dof_stage_updates"]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs, units = [], 0
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            units += step()
+            b.record(st)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+    ens.check()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    info = ens.info()
+    line = {"metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "kelvin_helmholtz_ensemble_64_members", "members": n,
+                       "member_dof_initial_min_max": [min(dof_member), max(dof_member)],
+                       "n_elem_total": info["n_elem"], "family": [4, 6, 10, 16], "amr_every_steps": 5,
+                       "graph": True, "launches_per_stage": 2,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args) -> None:
+    """Discrete adjoint: gradient of the end-time kinetic energy with respect to the initial
+    state over 200 P-ERK2 {6, 10, 16} steps of the Kelvin-Helmholtz problem on a frozen
+    three-level mesh (the adapted mesh at t = 1, levels 5-7), checkpoints every 20 steps,
+    checked against central differences along 16 seeded directions."""
+    import torch
+
+    from paper_2403_05144_gb300 import PerkSolver, perk2_disk_tableau
+    from paper_2403_05144_gb300.adjoint import gradient, kinetic_energy
+    from paper_2403_05144_gb300.build import build
+
+    build()
+    torch.cuda.set_device(0)
+    wl = dict(workload("kh"), amr=dict(AMR_KH, level_min=5), E=[4, 6, 10, 16])
+    run = Run(torch, wl, wl["E"])
+    while run.t < 1.0:
+        run.step()
+    run.solver.check()
+    cells, U0 = run.solver.cells.copy(), run.U.clone()
+    s = PerkSolver(surface_flux="hllc", use_graph=True)
+    s.upload_mesh(cells, -1.0, 2.0)
+    c, a = perk2_disk_tableau([6, 10, 16])
+    s.set_tableau(2, [6, 10, 16], c, a)
+    dt = s.compute_dt(U0, 0.7)
+    x, w = lgl_weights_of(s)
+    h = torch.tensor(2.0 / 2.0 ** cells[:, 0], dtype=torch.float64, device="cuda")
+    J = lambda U: kinetic_energy(U, h, w)
+    n_steps = 200
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    Uw = U0.clone()
+    lam = torch.ones_like(U0)
+    lam_out = torch.empty_like(U0)
+    ms_fwd = timed(lambda: s.step(Uw, dt), 20)
+    ms_adj = timed(lambda: s.step_vjp(U0, dt, lam, out=lam_out), 20)
+    t0 = time.perf_counter()
+    Jv, grad = gradient(s, U0, dt, n_steps, J, checkpoint_every=20)
+    torch.cuda.synchronize()
+    wall_grad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Uf = U0.clone()
+    for _ in range(n_steps):
+        s.step(Uf, dt)
+    torch.cuda.synchronize()
+    wall_fwd = time.perf_counter() - t0
+
+    def J_of(U):
+        U = U.clone()
+        for _ in range(n_steps):
+            s.step(U, dt)
+        s.check()
+        return float(J(U))
+
+    rng = np.random.default_rng(20240308 + 5)
+    errs = []
+    for _ in range(16):
+        d = torch.from_numpy(rng.normal(size=U0.shape)).cuda() * U0.abs()
+        d = d / torch.linalg.vector_norm(d)
+        eps = 1e-6 * float(torch.linalg.vector_norm(U0))
+        fd = (J_of(U0 + eps * d) - J_of(U0 - eps * d)) / (2 * eps)
+        ad = float(torch.sum(grad * d))
+        errs.append(abs(fd - ad) / max(abs(fd), 1e-300))
+    line = {"metric": "discrete adjoint of the P-ERK step: cost per step relative to the forward step",
+            "value": ms_adj / ms_fwd, "unit": "x forward step", "n_gpus": 1, "steps": n_steps,
+            "warmup": 0, "ms_per_step": ms_adj, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "kelvin_helmholtz_t1_frozen_levels5-7", "n_elem": len(cells),
+                       "dof": 16 * len(cells), "family": [6, 10, 16], "dt": dt, "checkpoint_every": 20},
+            "forward_ms_per_step": ms_fwd, "adjoint_ms_per_step": ms_adj,
+            "gradient_wall_s_200_steps": wall_grad, "forward_wall_s_200_steps": wall_fwd,
+            "J": float(Jv), "fd_directions": 16, "fd_max_rel_err": max(errs), "fd_median_rel_err": float(np.median(errs))}
+    print(json.dumps(line), flush=True)
+
+
+def lgl_weights_of(solver):
+    import torch
+
+    from paper_2403_05144_gb300 import reference_nodes
+    x, w = reference_nodes(3)
+    return x, torch.tensor(w, dtype=torch.float64, device="cuda")
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="perk", choices=["perk", "reference"])
-    p.add_argument("--workload", default="kh", choices=["kh", "vortex"])
+    p.add_argument("--workload", default="kh", choices=["kh", "vortex", "ensemble", "adjoint"])
     p.add_argument("--t-end-budget", type=float, default=60.0, help="wall seconds per run to t_end")
     args = p.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_perk(args)
 
