@@ -42,15 +42,22 @@ typedef enum {
 
 typedef enum { PERK_SURFACE_HLL = 0, PERK_SURFACE_HLLC = 1, PERK_SURFACE_EC = 2 } perk_surface_flux;
 
+/* Equations: compressible Euler, or Navier-Stokes with BR1 viscous terms
+ * (Sec. 7.1; gradients of (v1, v2, T = p/rho), central lifting and viscous
+ * flux, constant viscosity mu, heat conductivity mu gamma / ((gamma-1) Pr)). */
+typedef enum { PERK_EULER = 0, PERK_NAVIER_STOKES = 1 } perk_equations;
+
 typedef struct perk_ctx perk_ctx;
 
-/* Problem description.  Only the compressible Euler equations with N = 3
- * (4 x 4 Gauss-Lobatto nodes per quadrilateral) are built. */
+/* Problem description; N = 3 (4 x 4 Gauss-Lobatto nodes per quadrilateral). */
 typedef struct {
   int N;                 /* polynomial degree; must be 3 */
   double gamma;          /* ratio of specific heats, > 1 */
   int surface_flux;      /* perk_surface_flux */
   int use_graph;         /* nonzero: perk_step replays a captured CUDA graph of the whole step */
+  int equations;         /* perk_equations */
+  double mu;             /* dynamic viscosity (Navier-Stokes), > 0 */
+  double prandtl;        /* Prandtl number (Navier-Stokes), > 0 */
 } perk_problem;
 
 /* Creates a context on the current CUDA device.  *out receives the handle. */
@@ -191,7 +198,8 @@ perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out);
  * perk_rhs_vjp: d_g = J(Y)^T lam over every element; lam is read on the
  * active elements only (its other entries are treated as zero).  Both
  * differentiate the library's own discrete operator exactly (its branch
- * decisions are taken on the values of Y).  Device arrays, U layout. */
+ * decisions are taken on the values of Y).  Device arrays, U layout.
+ * Built for the Euler equations (INVALID_ARG for Navier-Stokes contexts). */
 perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd);
 perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_lam, double* d_g);
 

@@ -76,14 +76,16 @@ def _ptr(t) -> int:
 class PerkSolver:
     """One libperk context: mesh, partition, coefficient table and stage buffers."""
 
-    def __init__(self, gamma: float = 1.4, surface_flux: str = "hll", use_graph: bool = True, N: int = 3):
+    def __init__(self, gamma: float = 1.4, surface_flux: str = "hll", use_graph: bool = True, N: int = 3,
+                 equations: str = "euler", mu: float = 0.0, prandtl: float = 0.72):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("PerkSolver needs a CUDA device")
         self.torch = torch
         self.lib = _lib.load()
-        prob = _lib.PerkProblem(N, gamma, _lib.SURFACE[surface_flux], 1 if use_graph else 0)
+        eq = {"euler": 0, "navier_stokes": 1}[equations]
+        prob = _lib.PerkProblem(N, gamma, _lib.SURFACE[surface_flux], 1 if use_graph else 0, eq, mu, prandtl)
         h = C.c_void_p()
         torch.cuda.init()
         _check(self.lib, None, self.lib.perk_create(C.byref(prob), C.byref(h)))

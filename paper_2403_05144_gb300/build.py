@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libperk.so")
-SOURCES = ["perk_kernels.cu", "perk_host.cpp", "perk_probe.cu", "perk_noalloc.cu", "perk_adjoint.cu"]
+SOURCES = ["perk_kernels.cu", "perk_host.cpp", "perk_probe.cu", "perk_noalloc.cu", "perk_adjoint.cu", "perk_br1.cu"]
 HEADERS = [os.path.join(INCLUDE, "perk.h"), os.path.join(CSRC, "perk_internal.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

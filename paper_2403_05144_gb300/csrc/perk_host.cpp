@@ -133,6 +133,15 @@ Ops build_ops(double gamma, int surface_flux) {
   }
   for (int i = 0; i < NN; ++i)
     for (int j = 0; j < NN; ++j) o.dsplit[i][j] = (i == j) ? 0.0 : 2.0 * (lam[j] / lam[i]) / (x[i] - x[j]);
+  for (int i = 0; i < NN; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < NN; ++j)
+      if (j != i) {
+        o.dmat[i][j] = 0.5 * o.dsplit[i][j];
+        row += o.dmat[i][j];
+      }
+    o.dmat[i][i] = -row;   // a derivative matrix annihilates constants
+  }
   o.inv_w0 = 1.0 / w[0];
   // mortar operators: forward interpolation P_h[k][l] = l_l(position of node k of half h)
   for (int k = 0; k < NN; ++k) {
@@ -236,6 +245,10 @@ struct perk_ctx {
 
   // adjoint work space
   DevBuf<double> d_surf_d, d_Kall, d_Ystage, d_g, d_lamK1, d_lamKa, d_lamKb;
+  // Navier-Stokes (BR1) work space
+  DevBuf<double> d_wsurf, d_q, d_vsurf;
+  bool viscous() const { return prob.equations == PERK_NAVIER_STOKES; }
+  double kappa() const { return prob.mu * prob.gamma / ((prob.gamma - 1.0) * prob.prandtl); }
   int32_t lmin = 0, lmax = 0;
 
   // tableau
@@ -520,6 +533,11 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
   PERK_CUDA(ctx, ctx->d_Ka.ensure(ne * ELEM));
   PERK_CUDA(ctx, ctx->d_Kb.ensure(ne * ELEM));
   PERK_CUDA(ctx, ctx->d_eta.ensure(ne));
+  if (ctx->viscous()) {
+    PERK_CUDA(ctx, ctx->d_wsurf.ensure(ne * 64));
+    PERK_CUDA(ctx, ctx->d_q.ensure(ne * 96));
+    PERK_CUDA(ctx, ctx->d_vsurf.ensure(ne * 64));
+  }
   const int nb = (int)std::min<int64_t>(1024, (n_cells * NODES + 255) / 256);
   PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(nb, 1)));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
@@ -622,10 +640,17 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
     if (last) prev_at_last = prev;
     UpdateArgs chk = ua;
     chk.Kp = Kbuf[prev];
+    const bool visc = ctx->viscous();
     TIMED(ctx, timer, st, 1,
           launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur], last ? &chk : nullptr,
-                        ctx->d_logtab.p));
+                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur],
+                        (last && !visc) ? &chk : nullptr, ctx->d_logtab.p));
+    if (visc)
+      TIMED(ctx, timer, st, 3,
+            launch_br1(st, Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ctx->act_if[i],
+                       ctx->act_mort[i], ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->n_elem, ctx->act_el[i],
+                       ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa,
+                       ctx->d_wsurf.p, ctx->d_q.p, ctx->d_vsurf.p, Kbuf[cur], last ? &chk : nullptr));
     prev = cur;
   }
   ua.Kp = Kbuf[prev_at_last];  // K_{S-1}
@@ -659,6 +684,8 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   *out = nullptr;
   if (prob->N != 3 || !(prob->gamma > 1.0) || prob->surface_flux < 0 || prob->surface_flux > 2)
     return PERK_E_INVALID_ARG;
+  if (prob->equations != PERK_EULER && prob->equations != PERK_NAVIER_STOKES) return PERK_E_INVALID_ARG;
+  if (prob->equations == PERK_NAVIER_STOKES && (!(prob->mu > 0.0) || !(prob->prandtl > 0.0))) return PERK_E_INVALID_ARG;
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return PERK_E_CUDA;
   perk_ctx* ctx = new perk_ctx();
@@ -720,6 +747,9 @@ void perk_destroy(perk_ctx* ctx) {
   ctx->d_lamK1.release();
   ctx->d_lamKa.release();
   ctx->d_lamKb.release();
+  ctx->d_wsurf.release();
+  ctx->d_q.release();
+  ctx->d_vsurf.release();
   delete ctx;
 }
 
@@ -898,6 +928,11 @@ static perk_status rhs_given(perk_ctx* ctx, int stage, const double* d_Y, double
                               ctx->d_method.p, sa, ctx->d_surf.p));
   PERK_CUDA(ctx, launch_volume(ctx->stream, Y_GIVEN, ctx->ops, ne, ctx->d_elem_sorted.p, ctx->d_level.p,
                                ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr, ctx->d_logtab.p));
+  if (ctx->viscous())
+    PERK_CUDA(ctx, launch_br1(ctx->stream, Y_GIVEN, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ni,
+                              nm, ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->n_elem, ne, ctx->d_elem_sorted.p,
+                              ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_wsurf.p, ctx->d_q.p,
+                              ctx->d_vsurf.p, d_K, nullptr));
   return PERK_OK;
 }
 
@@ -1053,6 +1088,7 @@ static int min_active_member(const perk_ctx* ctx, int stage) {
 
 perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd) {
   if (!ctx) return PERK_E_INVALID_ARG;
+  if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
   if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_Y || !d_V || !d_Kd) return fail(ctx, PERK_E_INVALID_ARG, "null array");
   if (stage >= 0 && (!ctx->has_tab || stage >= ctx->S)) return fail(ctx, PERK_E_INVALID_ARG, "bad stage %d", stage);
@@ -1068,6 +1104,7 @@ perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const doub
 
 perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_lam, double* d_g) {
   if (!ctx) return PERK_E_INVALID_ARG;
+  if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
   if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_Y || !d_lam || !d_g) return fail(ctx, PERK_E_INVALID_ARG, "null array");
   if (stage >= 0 && (!ctx->has_tab || stage >= ctx->S)) return fail(ctx, PERK_E_INVALID_ARG, "bad stage %d", stage);
@@ -1083,6 +1120,7 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
 
 perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n) {
   if (!ctx) return PERK_E_INVALID_ARG;
+  if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
   if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
     return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
   if (!d_Un || !d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1 || !(dt > 0.0) || !std::isfinite(dt))

@@ -19,6 +19,7 @@ constexpr int MAX_R = 8;
 // Reference-element operators, computed on the host once per context.
 struct Ops {
   double dsplit[NN][NN];  // 2 D_ij off the diagonal, 0 on it (LGL: 2 D_00 + 1/w_0 = 0 = 2 D_NN - 1/w_N)
+  double dmat[NN][NN];    // the derivative matrix D_ij = l_j'(x_i) itself
   double inv_w0;          // 1 / w_0 = 1 / w_N
   double p_lo[NN][NN];    // large-face trace -> lower half-face nodes (interpolation)
   double p_hi[NN][NN];    // large-face trace -> upper half-face nodes
@@ -107,6 +108,14 @@ cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, 
                              const double* g, double* lamU, double* lamK1, double* lamKp);
 cudaError_t launch_adj_seed(cudaStream_t st, int64_t n, double dt, double b1, double bp, double bs, const double* lam,
                             double* lamU, double* lamK1, double* lamKp, double* lamKs);
+
+// BR1 viscous terms of one stage (perk_br1.cu): gradients on every element and face, viscous
+// flux and divergence on the active ones; K += viscous part; check: admissibility on the last stage
+cudaError_t launch_br1(cudaStream_t st, YSource ysrc, const Ops& ops, double mu, double kappa, int64_t n_if_all,
+                       int64_t n_mort_all, int64_t n_if_act, int64_t n_mort_act, const int4* ifs, const int4* morts,
+                       int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level, const int32_t* method,
+                       double two_over_len, const StageArgs& sa, double* wsurf, double* q, double* vsurf, double* K,
+                       const UpdateArgs* check);
 
 // Records the message of a failed context-free call (read by perk_last_error(NULL)).
 perk_status set_context_free_error(perk_status s, const char* msg);
