@@ -135,6 +135,23 @@ perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32
  * for the disk |z + E - 1| <= E - 1). */
 perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a);
 
+/* Third-order members (Sec. 3.3, Eq. PERK_ThirdOrderShuOsher; Sec. 4.3.2).
+ * perk_perk3_disk_alpha: monomial coefficients alpha[0..E] of a degree-E,
+ * third-order polynomial stable on the largest disk |z + r| <= r among
+ * sum_k d_k (1 + z/r)^k, d >= 0, sum d = 1 (*radius receives r): feasibility
+ * of the three order conditions for d is a linear program, solved exactly by
+ * enumerating its basic solutions, and r is found by bisection.
+ * perk_perk3_member: the free entries a_{i,i-1} (written to a_out[S] in the
+ * layout of perk_set_tableau) of a member with E evaluations whose stability
+ * polynomial has the coefficients alpha_3..alpha_E, with 0 < a_i < c_i; the
+ * paper's nonlinear system, solved by damped Newton iterations from fixed
+ * starting points (several solutions may exist; the first admissible one is
+ * returned).  c_i = (i-1)/(S-3) for i <= S-2, c_{S-1} = 1, c_S = 1/2.
+ * perk_perk3_disk_tableau: c[S] and a[R*S] of a whole family from both. */
+perk_status perk_perk3_disk_alpha(int E, double* alpha, double* radius);
+perk_status perk_perk3_member(int S, int E, const double* alpha, double* a_out);
+perk_status perk_perk3_disk_tableau(int S, int R, const int32_t* E, double* c, double* a);
+
 /* Level partition on the device (Sec. 6.2): member of every element from its
  * level (finest present level -> member R-1, next -> R-2, ..., the rest -> 0),
  * of every interface from its elements, of every mortar from its fine side;

@@ -165,3 +165,106 @@ def max_wave_speed_dt(U: np.ndarray, h: np.ndarray, N: int, cfl: float, gamma: f
     c = np.sqrt(gamma * p / rho)
     lam = (np.abs(v1) + np.abs(v2) + 2.0 * c).reshape(len(h), -1).max(axis=1)
     return float(cfl * np.min(h / ((N + 1) * lam)))
+
+
+# ---------------------------------------------------------------------------
+# Third-order P-ERK (Sec. 3.3, Eq. PERK_ThirdOrderShuOsher and Eq. Free_Timesteps;
+# Sec. 4.3.2): abscissae c_i = (i-1)/(S-3) for i <= S-2, c_{S-1} = 1, c_S = 1/2,
+# weights b_1 = b_{S-1} = 1/6, b_S = 2/3.
+
+def perk3_abscissae(S: int) -> np.ndarray:
+    c = np.zeros(S)
+    for i in range(1, S - 2):                       # 1-based i = 2 .. S-2 (none for S = 3)
+        c[i] = i / (S - 3.0)
+    c[S - 2] = 1.0
+    c[S - 1] = 0.5
+    return c
+
+
+def perk3_weights(S: int) -> np.ndarray:
+    b = np.zeros(S)
+    b[0] = 1.0 / 6.0
+    b[S - 2] += 1.0 / 6.0
+    b[S - 1] += 2.0 / 3.0
+    return b
+
+
+def disk_polynomial3_alpha(E: int, tol: float = 1e-12):
+    """Third-order polynomial of degree E stable on the largest disk |z + r| <= r
+    among P(z) = sum_k d_k (1 + z/r)^k with d >= 0, sum d = 1 (then |P| <= 1 on
+    the disk): the three order conditions P'(0) = P''(0) = P'''(0) = 1 are
+    sum k d_k = r, sum k(k-1) d_k = r^2, sum k(k-1)(k-2) d_k = r^3; the largest
+    r with a feasible d is found by bisection on a linear-programming feasibility
+    test.  Returns (alpha[0..E], r)."""
+    from scipy.optimize import linprog
+
+    k = np.arange(E + 1, dtype=np.float64)
+
+    Aeq = np.stack([np.ones_like(k), k, k * (k - 1), k * (k - 1) * (k - 2)])
+
+    def feasible(r):
+        beq = np.array([1.0, r, r * r, r ** 3])
+        res = linprog(np.zeros(E + 1), A_eq=Aeq, b_eq=beq, bounds=[(0, None)] * (E + 1), method="highs")
+        if res.status != 0:
+            return None
+        # the solver's own feasibility tolerance is ~1e-7; accept only solutions that hold to rounding
+        d = np.maximum(res.x, 0.0)
+        return d if np.max(np.abs(Aeq @ d - beq) / np.maximum(1.0, beq)) < 1e-12 else None
+
+    lo, hi = 0.5, float(E)
+    assert feasible(lo) is not None
+    while hi - lo > tol * hi:
+        mid = 0.5 * (lo + hi)
+        if feasible(mid) is not None:
+            lo = mid
+        else:
+            hi = mid
+    d = feasible(lo)
+    alpha = np.array([sum(d[j] * math.comb(j, m) for j in range(m, E + 1)) / lo ** m for m in range(E + 1)])
+    return alpha, lo
+
+
+def perk3_member(S: int, E: int, alpha, seeds: int = 16):
+    """Free entries a_{i,i-1}, i = S-E+3..S, of a third-order member with E
+    evaluations: the stability polynomial 1 + z b^T (I - z A)^{-1} 1 must have
+    the coefficients alpha_3..alpha_E (alpha_3 = 1/6 is the coupling condition
+    b_S a_S + b_{S-1} a_{S-1} = 1/6), with 0 < a_i < c_i (Sec. 4.3.2: a trust-region
+    solve from seeded random starts; the first start that converges with all
+    entries positive is taken).  Returns the dense S x S array."""
+    from scipy.optimize import least_squares
+
+    c = perk3_abscissae(S)
+    b = perk3_weights(S)
+    idx = list(range(S - E + 2, S))                  # 0-based stage rows with a free a_{i,i-1}
+
+    def build(x):
+        A = np.zeros((S, S))
+        for i in range(1, S):
+            A[i, 0] = c[i]
+        for xi, i in zip(x, idx):
+            A[i, i - 1] = xi
+            A[i, 0] = c[i] - xi
+        return A
+
+    def residual(x):
+        p = stability_polynomial(build(x), b)
+        return (p[3:E + 1] - alpha[3:E + 1]) / alpha[3:E + 1]
+
+    rng = np.random.default_rng(20240308)
+    best = None
+    for _ in range(seeds):
+        x0 = rng.uniform(0.05, 0.95, len(idx)) * c[idx]
+        res = least_squares(residual, x0, bounds=(np.zeros(len(idx)), c[idx]), xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        if np.max(np.abs(res.fun)) < 1e-10 and np.all(res.x > 0) and np.all(c[idx] - res.x > 0):
+            best = res.x
+            break
+    if best is None:
+        raise RuntimeError(f"no admissible third-order member for S={S}, E={E}")
+    return build(best)
+
+
+def perk3_family(E_list: Sequence[int], S: int | None = None) -> PERKFamily:
+    E_list = [int(e) for e in E_list]
+    S = S or max(E_list)
+    A = [perk3_member(S, E, disk_polynomial3_alpha(E)[0]) for E in E_list]
+    return PERKFamily(S=S, E=E_list, c=perk3_abscissae(S), b=perk3_weights(S), A=A, order=3)

@@ -47,6 +47,36 @@ def perk2_disk_tableau(E: Sequence[int], S: int | None = None):
     return np.array(c[:]), np.array(a[:]).reshape(R, S)
 
 
+def perk3_disk_alpha(E: int):
+    """(alpha[0..E], r) of the library's third-order disk polynomial."""
+    lib = _lib.load()
+    al = (C.c_double * (E + 1))()
+    r = C.c_double()
+    _check(lib, None, lib.perk_perk3_disk_alpha(E, al, C.byref(r)))
+    return np.array(al[:]), r.value
+
+
+def perk3_member(S: int, E: int, alpha):
+    lib = _lib.load()
+    al = np.ascontiguousarray(alpha, dtype=np.float64)
+    out = (C.c_double * S)()
+    _check(lib, None, lib.perk_perk3_member(S, E, al.ctypes.data_as(C.POINTER(C.c_double)), out))
+    return np.array(out[:])
+
+
+def perk3_disk_tableau(E: Sequence[int], S: int | None = None):
+    """(c[S], a[R, S]) of the library's third-order family with members E (ascending)."""
+    lib = _lib.load()
+    E = [int(e) for e in E]
+    S = int(S or max(E))
+    R = len(E)
+    Ea = (C.c_int32 * R)(*E)
+    c = (C.c_double * S)()
+    a = (C.c_double * (R * S))()
+    _check(lib, None, lib.perk_perk3_disk_tableau(S, R, Ea, c, a))
+    return np.array(c[:]), np.array(a[:]).reshape(R, S)
+
+
 def mesh_faces(cells):
     """(interfaces [n_if, 4], mortars [n_mort, 4]) the library builds for a leaf list (host only)."""
     lib = _lib.load()

@@ -869,6 +869,228 @@ perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, d
   return PERK_OK;
 }
 
+// ---- third-order construction --------------------------------------------------------
+namespace {
+
+// 4x4 Gaussian elimination with partial pivoting; false if singular
+bool solve4(double M[4][4], double g[4], double x[4]) {
+  double A[4][5];
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) A[i][j] = M[i][j];
+    A[i][4] = g[i];
+  }
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (std::fabs(A[piv][c]) < 1e-300) return false;
+    for (int j = 0; j < 5; ++j) std::swap(A[c][j], A[piv][j]);
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        const double f = A[r][c] / A[c][c];
+        for (int j = c; j < 5; ++j) A[r][j] -= f * A[c][j];
+      }
+  }
+  for (int i = 0; i < 4; ++i) x[i] = A[i][4] / A[i][i];
+  return true;
+}
+
+// a feasible d >= 0 of sum d = 1, sum k d = r, sum k(k-1) d = r^2, sum k(k-1)(k-2) d = r^3 (k = 0..E),
+// by enumerating the basic solutions (at most four nonzeros); empty if none
+std::vector<double> order3_weights(int E, double r) {
+  const double g0[4] = {1.0, r, r * r, r * r * r};
+  for (int a = 0; a <= E; ++a)
+    for (int b = a + 1; b <= E; ++b)
+      for (int c = b + 1; c <= E; ++c)
+        for (int d = c + 1; d <= E; ++d) {
+          const int cols[4] = {a, b, c, d};
+          double M[4][4], g[4], x[4];
+          for (int j = 0; j < 4; ++j) {
+            const double k = cols[j];
+            M[0][j] = 1.0;
+            M[1][j] = k;
+            M[2][j] = k * (k - 1.0);
+            M[3][j] = k * (k - 1.0) * (k - 2.0);
+          }
+          for (int i = 0; i < 4; ++i) g[i] = g0[i];
+          if (!solve4(M, g, x)) continue;
+          bool ok = true;
+          for (int j = 0; j < 4; ++j) ok = ok && x[j] >= -1e-13;
+          if (!ok) continue;
+          std::vector<double> w(E + 1, 0.0);
+          for (int j = 0; j < 4; ++j) w[cols[j]] = std::max(0.0, x[j]);
+          return w;
+        }
+  return {};
+}
+
+double binom(int n, int k) {
+  double v = 1.0;
+  for (int j = 1; j <= k; ++j) v = v * (n - k + j) / j;
+  return v;
+}
+
+// coefficients p_0..p_S of 1 + z b^T (I - z A)^{-1} 1 of a P-ERK3 member (free entries x)
+void perk3_poly(int S, int E, const double* c, const double* b, const std::vector<double>& x, std::vector<double>& p) {
+  std::vector<double> A((size_t)S * S, 0.0);
+  for (int i = 1; i < S; ++i) A[(size_t)i * S] = c[i];
+  for (int q = 0; q < E - 2; ++q) {
+    const int i = S - E + 2 + q;  // 0-based row
+    A[(size_t)i * S + i - 1] = x[q];
+    A[(size_t)i * S] = c[i] - x[q];
+  }
+  std::vector<double> v(S, 1.0), w(S);
+  p.assign(S + 1, 0.0);
+  p[0] = 1.0;
+  for (int k = 1; k <= S; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < S; ++i) s += b[i] * v[i];
+    p[k] = s;
+    for (int i = 0; i < S; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < i; ++j) t += A[(size_t)i * S + j] * v[j];
+      w[i] = t;
+    }
+    v.swap(w);
+  }
+}
+
+// dense solve (n <= 64) with partial pivoting
+bool solve_dense(std::vector<double> A, std::vector<double>& b, int n) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (std::fabs(A[(size_t)piv * n + c]) < 1e-300) return false;
+    for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)piv * n + j]);
+    std::swap(b[c], b[piv]);
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+      for (int j = c; j < n; ++j) A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int j = r + 1; j < n; ++j) s -= A[(size_t)r * n + j] * b[j];
+    b[r] = s / A[(size_t)r * n + r];
+  }
+  return true;
+}
+
+}  // namespace
+
+perk_status perk_perk3_disk_alpha(int E, double* alpha, double* radius) {
+  if (E < 3 || E > MAX_S || !alpha) return PERK_E_INVALID_ARG;
+  double lo = 0.5, hi = (double)E;
+  if (order3_weights(E, lo).empty()) return fail(nullptr, PERK_E_INVALID_ARG, "no third-order disk polynomial");
+  for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!order3_weights(E, mid).empty())
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const std::vector<double> d = order3_weights(E, lo);
+  for (int m = 0; m <= E; ++m) {
+    double s = 0.0;
+    for (int j = m; j <= E; ++j) s += d[j] * binom(j, m);
+    alpha[m] = s / std::pow(lo, m);
+  }
+  if (radius) *radius = lo;
+  return PERK_OK;
+}
+
+perk_status perk_perk3_member(int S, int E, const double* alpha, double* a_out) {
+  if (S < 3 || S > MAX_S || E < 3 || E > S || !alpha || !a_out) return PERK_E_INVALID_ARG;
+  std::vector<double> c(S), b(S, 0.0);
+  for (int i = 1; i < S - 2; ++i) c[i] = (double)i / (S - 3.0);
+  c[0] = 0.0;
+  c[S - 2] = 1.0;
+  c[S - 1] = 0.5;
+  b[0] = 1.0 / 6.0;
+  b[S - 2] += 1.0 / 6.0;
+  b[S - 1] += 2.0 / 3.0;
+  const int n = E - 2;
+  auto residual = [&](const std::vector<double>& x, std::vector<double>& r) {
+    std::vector<double> p;
+    perk3_poly(S, E, c.data(), b.data(), x, p);
+    r.resize(n);
+    for (int k = 0; k < n; ++k) r[k] = (p[3 + k] - alpha[3 + k]) / alpha[3 + k];
+  };
+  auto norm = [](const std::vector<double>& r) {
+    double m = 0.0;
+    for (double v : r) m = std::max(m, std::fabs(v));
+    return m;
+  };
+  const double starts[] = {0.5, 0.3, 0.7, 0.2, 0.8, 0.4, 0.6, 0.1, 0.9};
+  for (double t0 : starts) {
+    std::vector<double> x(n), r, rt, xt;
+    for (int q = 0; q < n; ++q) x[q] = t0 * c[S - E + 2 + q];
+    residual(x, r);
+    for (int it = 0; it < 200 && norm(r) > 1e-14; ++it) {
+      // Jacobian by central differences
+      std::vector<double> J((size_t)n * n);
+      for (int j = 0; j < n; ++j) {
+        const double h = 1e-7 * std::max(1e-3, std::fabs(x[j]));
+        std::vector<double> xp = x, xm = x, rp, rm;
+        xp[j] += h;
+        xm[j] -= h;
+        residual(xp, rp);
+        residual(xm, rm);
+        for (int i = 0; i < n; ++i) J[(size_t)i * n + j] = (rp[i] - rm[i]) / (2.0 * h);
+      }
+      std::vector<double> dx(r);
+      if (!solve_dense(J, dx, n)) break;
+      // damped step keeping 0 < x < c
+      double lam = 1.0;
+      bool moved = false;
+      for (int ls = 0; ls < 40; ++ls, lam *= 0.5) {
+        xt = x;
+        bool inside = true;
+        for (int q = 0; q < n; ++q) {
+          xt[q] -= lam * dx[q];
+          const double cq = c[S - E + 2 + q];
+          inside = inside && xt[q] > 0.0 && xt[q] < cq;
+        }
+        if (!inside) continue;
+        residual(xt, rt);
+        if (norm(rt) < norm(r)) {
+          x = xt;
+          r = rt;
+          moved = true;
+          break;
+        }
+      }
+      if (!moved) break;
+    }
+    if (norm(r) < 1e-11) {
+      for (int i = 0; i < S; ++i) a_out[i] = 0.0;
+      for (int q = 0; q < n; ++q) a_out[S - E + 2 + q] = x[q];
+      return PERK_OK;
+    }
+  }
+  return fail(nullptr, PERK_E_INVALID_ARG, "no admissible third-order member found");
+}
+
+perk_status perk_perk3_disk_tableau(int S, int R, const int32_t* E, double* c, double* a) {
+  if (S < 3 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !a) return PERK_E_INVALID_ARG;
+  for (int r = 0; r < R; ++r)
+    if (E[r] < 3 || E[r] > S || (r > 0 && E[r] < E[r - 1])) return PERK_E_INVALID_ARG;
+  for (int i = 1; i < S - 2; ++i) c[i] = (double)i / (S - 3.0);
+  c[0] = 0.0;
+  c[S - 2] = 1.0;
+  c[S - 1] = 0.5;
+  std::vector<double> alpha(MAX_S + 1);
+  for (int r = 0; r < R; ++r) {
+    perk_status s = perk_perk3_disk_alpha(E[r], alpha.data(), nullptr);
+    if (s != PERK_OK) return s;
+    s = perk_perk3_member(S, E[r], alpha.data(), a + (size_t)r * S);
+    if (s != PERK_OK) return s;
+  }
+  return PERK_OK;
+}
+
 perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32_t* E, const double* c,
                              const double* a) {
   if (!ctx) return PERK_E_INVALID_ARG;

@@ -79,3 +79,37 @@ def test_shear_layer_steps():
     for _ in range(5):
         want = prkm_step(ns.rhs, want, dt, fam, element_methods(m.cells[:, 0], fam.R))
     assert np.max(np.abs(U.cpu().numpy() - want)) / np.max(np.abs(want)) < 1e-11
+
+
+def oracle_tableau_into(solver, fam):
+    """Hand the oracle's coefficient table to the library (order, E, c, a_{i,i-1})."""
+    S = fam.S
+    a = np.zeros((fam.R, S))
+    for r in range(fam.R):
+        for i in range(2, S):
+            a[r, i] = fam.A[r][i, i - 1]
+    solver.set_tableau(fam.order, fam.E, fam.c, a)
+
+
+@pytest.mark.parametrize("equations", ["euler", "navier_stokes"])
+def test_third_order_steps(equations):
+    from oracle.dgsem import DGSEM
+    from oracle.perk import perk3_family
+    from paper_2403_05144_gb300 import PerkSolver
+    cells = kh_band_cells(3, 5, 0.05)
+    m = TreeMesh(cells, 0.0, 1.0)
+    U0 = nodal_state(shear_layer, cells, 0.0, 1.0, X3)
+    fam = perk3_family([4, 8, 16])
+    dt = max_wave_speed_dt(U0, m.h, 3, 0.5)
+    s = PerkSolver(surface_flux="hll", equations=equations, mu=4e-4 if equations != "euler" else 0.0)
+    s.upload_mesh(cells, 0.0, 1.0)
+    oracle_tableau_into(s, fam)
+    U = cuda(U0.copy())
+    for _ in range(3):
+        s.step(U, dt)
+    s.check()
+    rhs = (NavierStokesDGSEM(m, 3, "hll", mu=4e-4) if equations != "euler" else DGSEM(m, 3, "hll")).rhs
+    want = U0
+    for _ in range(3):
+        want = prkm_step(rhs, want, dt, fam, element_methods(m.cells[:, 0], fam.R))
+    assert np.max(np.abs(U.cpu().numpy() - want)) / np.max(np.abs(want)) < 1e-11

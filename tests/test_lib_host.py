@@ -101,3 +101,34 @@ def test_connectivity_rejects_bad_meshes(lib):
     cells += [(2, 3, 0)]
     with pytest.raises(PerkError):
         mesh_faces(cells)
+
+
+@pytest.mark.parametrize("E", [3, 4, 8, 16])
+def test_third_order_disk_polynomial_matches_oracle(lib, E):
+    from oracle.perk import disk_polynomial3_alpha
+    from paper_2403_05144_gb300 import perk3_disk_alpha
+    al, r = perk3_disk_alpha(E)
+    alo, ro = disk_polynomial3_alpha(E)
+    np.testing.assert_allclose(al, alo, rtol=1e-10, atol=1e-18)
+    assert abs(r - ro) < 1e-6 * r
+
+
+@pytest.mark.parametrize("E_list", [[4, 8, 16], [3, 4, 7], [3]])
+def test_third_order_family_is_valid(lib, E_list):
+    # several members can satisfy the conditions; check the defining ones
+    from oracle.perk import disk_polynomial3_alpha, perk3_abscissae, perk3_weights, stability_polynomial
+    from paper_2403_05144_gb300 import perk3_disk_tableau
+    c, a = perk3_disk_tableau(E_list)
+    S = len(c)
+    np.testing.assert_allclose(c, perk3_abscissae(S), atol=1e-16)
+    b = perk3_weights(S)
+    for r, E in enumerate(E_list):
+        A = np.zeros((S, S))
+        for i in range(1, S):
+            A[i, i - 1] += a[r, i]
+            A[i, 0] += c[i] - a[r, i]
+        assert np.all(a[r] >= 0) and np.all(c - a[r] >= -1e-16)
+        assert abs(b @ A @ c - 1 / 6) < 1e-13
+        P = stability_polynomial(A, b)
+        np.testing.assert_allclose(P[:E + 1], disk_polynomial3_alpha(E)[0], rtol=1e-9, atol=1e-18)
+        assert np.all(np.abs(P[E + 1:]) < 1e-18)
