@@ -13,7 +13,6 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
-#include <unordered_map>
 #include <vector>
 
 #include "perk.h"
@@ -271,8 +270,9 @@ struct perk_ctx {
   DevBuf<int> d_flag;
   DevBuf<double> d_logtab;   // table of the volume kernel's logarithm
 
-  // graph of one step
+  // graph of one step (graph_valid: matches the current mesh, tableau and buffers)
   cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
   double* graph_U = nullptr;
 
   perk_counters counters{};
@@ -303,9 +303,13 @@ perk_status fail(perk_ctx* ctx, perk_status s, const char* fmt, ...) {
                   #call, cudaGetErrorString(e_), __FILE__, __LINE__);                               \
   } while (0)
 
-void drop_graph(perk_ctx* ctx) {
+// marks the step graph stale; the executable graph is kept for an in-place update
+void drop_graph(perk_ctx* ctx) { ctx->graph_valid = false; }
+
+void destroy_graph(perk_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   ctx->graph = nullptr;
+  ctx->graph_valid = false;
   ctx->graph_U = nullptr;
 }
 
@@ -323,49 +327,120 @@ inline CellKey key_of(int m, int l, int64_t ix, int64_t iy) {
 constexpr int MAX_LEVEL = 20;
 constexpr int MAX_MEMBERS = 65535;
 
+// Morton key of a leaf's lower-left corner at resolution lmax (bits interleaved x, y)
+uint64_t morton_key(int l, int64_t ix, int64_t iy, int lmax) {
+  const uint64_t X = (uint64_t)ix << (lmax - l), Y = (uint64_t)iy << (lmax - l);
+  uint64_t z = 0;
+  for (int b = 0; b < 31; ++b) z |= ((X >> b) & 1ull) << (2 * b) | ((Y >> b) & 1ull) << (2 * b + 1);
+  return z;
+}
+
+// Open-addressing hash table from cell keys to int32 values (linear probing,
+// capacity a power of two at least twice the number of entries).
+class FlatMap {
+ public:
+  explicit FlatMap(size_t n) {
+    size_t cap = 16;
+    while (cap < 2 * n + 2) cap <<= 1;
+    keys_.assign(cap, kEmpty);
+    vals_.resize(cap);
+    mask_ = cap - 1;
+  }
+  // inserts (key, v) unless present; returns false if the key was present
+  bool insert(int64_t key, int32_t v) {
+    size_t h = slot(key);
+    while (keys_[h] != kEmpty) {
+      if (keys_[h] == key) return false;
+      h = (h + 1) & mask_;
+    }
+    keys_[h] = key;
+    vals_[h] = v;
+    return true;
+  }
+  int32_t find(int64_t key) const {
+    size_t h = slot(key);
+    while (keys_[h] != kEmpty) {
+      if (keys_[h] == key) return vals_[h];
+      h = (h + 1) & mask_;
+    }
+    return -1;
+  }
+  int32_t* find_ptr(int64_t key) {
+    size_t h = slot(key);
+    while (keys_[h] != kEmpty) {
+      if (keys_[h] == key) return &vals_[h];
+      h = (h + 1) & mask_;
+    }
+    return nullptr;
+  }
+
+ private:
+  static constexpr int64_t kEmpty = -1;
+  size_t slot(int64_t key) const {
+    uint64_t z = (uint64_t)key + 0x9E3779B97F4A7C15ull;   // splitmix64 finaliser
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (size_t)(z ^ (z >> 31)) & mask_;
+  }
+  std::vector<int64_t> keys_;
+  std::vector<int32_t> vals_;
+  size_t mask_ = 0;
+};
+
 // Interfaces and mortars of a periodic, 2:1-balanced leaf list by a walk over
 // each leaf's four face neighbourhoods in the implicit quadtree.
 perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, const int32_t* member,
                                std::vector<int4>& ifs, std::vector<int4>& morts) {
-  std::unordered_map<CellKey, int32_t, CellHash> leaf;
-  leaf.reserve((size_t)n * 2);
+  FlatMap leaf((size_t)n);
   int n_members = 1;
+  int lmax = 0;
   for (int64_t e = 0; e < n; ++e) {
     const int l = cells[3 * e], ix = cells[3 * e + 1], iy = cells[3 * e + 2];
     const int m = member ? member[e] : 0;
     if (l < 0 || l > MAX_LEVEL) return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: level %d out of range", (long long)e, l);
     if (m < 0 || m >= MAX_MEMBERS) return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: member out of range", (long long)e);
     n_members = std::max(n_members, m + 1);
+    lmax = std::max(lmax, l);
     const int64_t side = (int64_t)1 << l;
     if (ix < 0 || iy < 0 || ix >= side || iy >= side)
       return fail(ctx, PERK_E_INVALID_ARG, "cell %lld: index outside level %d", (long long)e, l);
-    if (!leaf.emplace(key_of(m, l, ix, iy), (int32_t)e).second)
+    if (!leaf.insert(key_of(m, l, ix, iy).v, (int32_t)e))
       return fail(ctx, PERK_E_INVALID_ARG, "cell %lld duplicated", (long long)e);
   }
-  // exact tiling of every member's square and no leaf with a leaf ancestor
-  std::vector<long double> area(n_members, 0.0L);
-  for (int64_t e = 0; e < n; ++e) area[member ? member[e] : 0] += std::ldexp(1.0L, -2 * cells[3 * e]);
-  for (int m = 0; m < n_members; ++m)
-    if (std::fabs((double)(area[m] - 1.0L)) > 1e-12)
-      return fail(ctx, PERK_E_INVALID_ARG, "cells of member %d do not tile the domain", m);
-  for (int64_t e = 0; e < n; ++e) {
-    int l = cells[3 * e];
-    int64_t ix = cells[3 * e + 1], iy = cells[3 * e + 2];
-    const int m = member ? member[e] : 0;
-    while (l > 0) {
-      --l;
-      ix >>= 1;
-      iy >>= 1;
-      if (leaf.count(key_of(m, l, ix, iy))) return fail(ctx, PERK_E_INVALID_ARG, "cells overlap");
+  // exact tiling of every member's square: the cells' Morton intervals (at the finest
+  // level) must follow each other without gap or overlap from 0 to 4^lmax
+  {
+    std::vector<std::pair<std::pair<int32_t, uint64_t>, uint64_t>> iv((size_t)n);
+    for (int64_t e = 0; e < n; ++e) {
+      const int l = cells[3 * e];
+      const uint64_t z = morton_key(l, cells[3 * e + 1], cells[3 * e + 2], lmax);
+      iv[e] = {{member ? member[e] : 0, z}, z + (1ull << (2 * (lmax - l)))};
     }
+    std::sort(iv.begin(), iv.end());
+    int32_t cur_m = -1;
+    uint64_t next = 0;
+    for (const auto& q : iv) {
+      if (q.first.first != cur_m) {
+        if (cur_m >= 0 && next != (1ull << (2 * lmax)))
+          return fail(ctx, PERK_E_INVALID_ARG, "cells of member %d do not tile the domain", cur_m);
+        if (q.first.first != cur_m + 1 || q.first.second != 0)
+          return fail(ctx, PERK_E_INVALID_ARG, "cells of member %d do not tile the domain", q.first.first);
+        cur_m = q.first.first;
+        next = 0;
+      }
+      if (q.first.second != next) return fail(ctx, PERK_E_INVALID_ARG, "cells of member %d overlap or leave a gap", cur_m);
+      next = q.second;
+    }
+    if (next != (1ull << (2 * lmax)) || cur_m + 1 != n_members)
+      return fail(ctx, PERK_E_INVALID_ARG, "cells do not tile the domain");
   }
   for (int64_t e = 0; e < n; ++e) {
     const int l = cells[3 * e];
     const int64_t ix = cells[3 * e + 1], iy = cells[3 * e + 2];
     const int mb = member ? member[e] : 0;
     auto find = [&](int ll, int64_t x, int64_t y) -> int32_t {
-      auto it = leaf.find(key_of(mb, ll, x, y));
-      return it == leaf.end() ? -1 : it->second;
+      if (ll < 0 || ll > MAX_LEVEL) return -1;
+      return leaf.find(key_of(mb, ll, x, y).v);
     };
     const int64_t side = (int64_t)1 << l;
     for (int dir = 0; dir < 2; ++dir) {
@@ -552,13 +627,6 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
   return run_partition(ctx);
 }
 
-// Morton key of a leaf's lower-left corner at resolution lmax (bits interleaved x, y)
-uint64_t morton_key(int l, int64_t ix, int64_t iy, int lmax) {
-  const uint64_t X = (uint64_t)ix << (lmax - l), Y = (uint64_t)iy << (lmax - l);
-  uint64_t z = 0;
-  for (int b = 0; b < 31; ++b) z |= ((X >> b) & 1ull) << (2 * b) | ((Y >> b) & 1ull) << (2 * b + 1);
-  return z;
-}
 
 // Desired levels raised to the least fixed point of the sibling rule (a cell
 // coarsens only with all three siblings, all leaves that want to coarsen) and
@@ -566,10 +634,25 @@ uint64_t morton_key(int l, int64_t ix, int64_t iy, int lmax) {
 void balance_levels(const perk_ctx* ctx, std::vector<int32_t>& d) {
   const int64_t n = ctx->n_elem;
   const int32_t* c = ctx->h_cells.data();
-  std::unordered_map<CellKey, std::vector<int32_t>, CellHash> groups;
+  // sibling groups: members of the same parent, as a list per parent (group id by hash)
   const int32_t* mb = ctx->h_member.data();
-  for (int64_t e = 0; e < n; ++e)
-    if (c[3 * e] > 0) groups[key_of(mb[e], c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)].push_back((int32_t)e);
+  FlatMap gid((size_t)n);
+  std::vector<int32_t> group_of(n, -1), gcount, gfirst;
+  std::vector<int32_t> gmembers;            // 4 slots per group
+  for (int64_t e = 0; e < n; ++e) {
+    if (c[3 * e] == 0) continue;
+    const int64_t k = key_of(mb[e], c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1).v;
+    int32_t g = gid.find(k);
+    if (g < 0) {
+      g = (int32_t)gcount.size();
+      gid.insert(k, g);
+      gcount.push_back(0);
+      gmembers.insert(gmembers.end(), 4, -1);
+    }
+    if (gcount[g] < 4) gmembers[4 * g + gcount[g]] = (int32_t)e;
+    gcount[g] += 1;
+    group_of[e] = g;
+  }
   std::vector<std::pair<int32_t, int32_t>> pairs;
   for (const int4& f : ctx->h_if) pairs.emplace_back(f.x, f.y);
   for (const int4& m : ctx->h_mort) {
@@ -581,15 +664,24 @@ void balance_levels(const perk_ctx* ctx, std::vector<int32_t>& d) {
     changed = false;
     for (int64_t e = 0; e < n; ++e) {
       if (d[e] >= c[3 * e]) continue;
-      const auto& g = groups[key_of(mb[e], c[3 * e], c[3 * e + 1] >> 1, c[3 * e + 2] >> 1)];
-      bool ok = g.size() == 4;
-      for (int32_t m : g) ok = ok && d[m] < c[3 * m];
-      if (!ok)
-        for (int32_t m : g)
+      const int32_t g = group_of[e];
+      bool ok = g >= 0 && gcount[g] == 4;
+      if (ok)
+        for (int q = 0; q < 4; ++q) ok = ok && d[gmembers[4 * g + q]] < c[3 * gmembers[4 * g + q]];
+      if (!ok) {
+        if (g < 0) {
+          d[e] = c[3 * e];
+          changed = true;
+          continue;
+        }
+        for (int q = 0; q < 4 && q < gcount[g]; ++q) {
+          const int32_t m = gmembers[4 * g + q];
           if (d[m] < c[3 * m]) {
             d[m] = c[3 * m];
             changed = true;
           }
+        }
+      }
     }
     for (const auto& pr : pairs) {
       const int32_t a = pr.first, b = pr.second;
@@ -714,7 +806,7 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
 
 void perk_destroy(perk_ctx* ctx) {
   if (!ctx) return;
-  drop_graph(ctx);
+  destroy_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->d_level.release();
   ctx->d_member.release();
@@ -1172,8 +1264,7 @@ perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double*
 
 static perk_status step_impl(perk_ctx* ctx, double* d_U) {
   if (ctx->prob.use_graph) {
-    if (!ctx->graph || ctx->graph_U != d_U) {
-      drop_graph(ctx);
+    if (!ctx->graph_valid || ctx->graph_U != d_U) {
       cudaGraph_t g = nullptr;
       PERK_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
       perk_status s = enqueue_step(ctx, ctx->cap_stream, d_U);
@@ -1183,10 +1274,23 @@ static perk_status step_impl(perk_ctx* ctx, double* d_U) {
         return s;
       }
       PERK_CUDA(ctx, ce);
-      cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+      // a re-captured step usually differs from the previous one only in launch sizes and
+      // pointers: update the executable graph in place, instantiate only if that fails
+      bool updated = false;
+      if (ctx->graph) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(ctx->graph, g, &info) == cudaSuccess;
+        if (!updated) {
+          cudaGetLastError();
+          cudaGraphExecDestroy(ctx->graph);
+          ctx->graph = nullptr;
+        }
+      }
+      cudaError_t ie = updated ? cudaSuccess : cudaGraphInstantiate(&ctx->graph, g, 0);
       cudaGraphDestroy(g);
       PERK_CUDA(ctx, ie);
       ctx->graph_U = d_U;
+      ctx->graph_valid = true;
     }
     PERK_CUDA(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
   } else {
@@ -1470,15 +1574,14 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
   balance_levels(ctx, d);
   // new leaves (member by member, Morton order within a member) and transfer records
   const int32_t* mb = ctx->h_member.data();
-  std::unordered_map<CellKey, int32_t, CellHash> old;
-  old.reserve((size_t)n * 2);
-  for (int64_t e = 0; e < n; ++e) old.emplace(key_of(mb[e], c[3 * e], c[3 * e + 1], c[3 * e + 2]), (int32_t)e);
+  FlatMap old((size_t)n);
+  for (int64_t e = 0; e < n; ++e) old.insert(key_of(mb[e], c[3 * e], c[3 * e + 1], c[3 * e + 2]).v, (int32_t)e);
   struct NewCell {
     int32_t m, l, ix, iy;
   };
   std::vector<NewCell> nc;
   nc.reserve((size_t)n * 2);
-  std::unordered_map<CellKey, char, CellHash> seen;
+  FlatMap seen((size_t)n);
   std::vector<int> lmax(ctx->n_members, 0);
   for (int64_t e = 0; e < n; ++e) {
     const int l = c[3 * e], ix = c[3 * e + 1], iy = c[3 * e + 2], me = mb[e];
@@ -1487,7 +1590,7 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
         for (int cx = 0; cx < 2; ++cx) nc.push_back({me, l + 1, 2 * ix + cx, 2 * iy + cy});
     } else if (d[e] == l) {
       nc.push_back({me, l, ix, iy});
-    } else if (seen.emplace(key_of(me, l - 1, ix >> 1, iy >> 1), 1).second) {
+    } else if (seen.insert(key_of(me, l - 1, ix >> 1, iy >> 1).v, 1)) {
       nc.push_back({me, l - 1, ix >> 1, iy >> 1});
     }
     lmax[me] = std::max(lmax[me], d[e]);
@@ -1513,25 +1616,25 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
     ctx->plan_cells[3 * k + 2] = q.iy;
     ctx->plan_member[k] = q.m;
     int32_t* r = &ctx->plan_map[5 * k];
-    auto it = old.find(key_of(q.m, q.l, q.ix, q.iy));
-    if (it != old.end()) {
+    const int32_t it = old.find(key_of(q.m, q.l, q.ix, q.iy).v);
+    if (it >= 0) {
       r[0] = 0;
-      r[1] = it->second;
+      r[1] = it;
       r[2] = r[3] = r[4] = 0;
       continue;
     }
-    auto par = old.find(key_of(q.m, q.l - 1, q.ix >> 1, q.iy >> 1));
-    if (par != old.end()) {
+    const int32_t par = q.l > 0 ? old.find(key_of(q.m, q.l - 1, q.ix >> 1, q.iy >> 1).v) : -1;
+    if (par >= 0) {
       r[0] = 1 | ((q.ix & 1) << 2) | ((q.iy & 1) << 3);
-      r[1] = par->second;
+      r[1] = par;
       r[2] = r[3] = r[4] = 0;
       continue;
     }
     r[0] = 2;
     for (int cc = 0; cc < 4; ++cc) {
-      auto ch = old.find(key_of(q.m, q.l + 1, 2 * q.ix + (cc & 1), 2 * q.iy + (cc >> 1)));
-      if (ch == old.end()) return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
-      r[1 + cc] = ch->second;
+      const int32_t ch = old.find(key_of(q.m, q.l + 1, 2 * q.ix + (cc & 1), 2 * q.iy + (cc >> 1)).v);
+      if (ch < 0) return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
+      r[1 + cc] = ch;
     }
   }
   ctx->has_plan = true;
@@ -1547,9 +1650,8 @@ perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Une
   PERK_CUDA(ctx, ctx->d_map.ensure((size_t)5 * m));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_map.p, ctx->plan_map.data(), ctx->plan_map.size() * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, ctx->stream));
+  // (the pageable upload above is staged before the call returns, so plan_map may be reused)
   PERK_CUDA(ctx, launch_transfer(ctx->stream, m, ctx->d_map.p, d_Uold, ctx->ops, d_Unew));
-  // the map upload is read by the transfer before the host may touch plan_map again
-  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->has_plan = false;
   const std::vector<int32_t> cells = std::move(ctx->plan_cells);
   const std::vector<int32_t> members = std::move(ctx->plan_member);
