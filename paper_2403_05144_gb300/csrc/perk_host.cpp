@@ -236,6 +236,7 @@ struct perk_ctx {
 
   // pending AMR plan (perk_adapt_plan -> perk_adapt_commit)
   bool has_plan = false;
+  bool plan_identity = false;        // the plan changes no cell
   std::vector<int32_t> plan_cells;   // new leaves [n][3]
   std::vector<int32_t> plan_member;  // their ensemble members
   std::vector<int32_t> plan_map;     // [n][5] transfer records
@@ -416,7 +417,7 @@ perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, c
       const uint64_t z = morton_key(l, cells[3 * e + 1], cells[3 * e + 2], lmax);
       iv[e] = {{member ? member[e] : 0, z}, z + (1ull << (2 * (lmax - l)))};
     }
-    std::sort(iv.begin(), iv.end());
+    if (!std::is_sorted(iv.begin(), iv.end())) std::sort(iv.begin(), iv.end());
     int32_t cur_m = -1;
     uint64_t next = 0;
     for (const auto& q : iv) {
@@ -1572,6 +1573,9 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
     }
   }
   balance_levels(ctx, d);
+  bool identity = true;
+  for (int64_t e = 0; e < n && identity; ++e) identity = d[e] == c[3 * e];
+  ctx->plan_identity = identity;
   // new leaves (member by member, Morton order within a member) and transfer records
   const int32_t* mb = ctx->h_member.data();
   FlatMap old((size_t)n);
@@ -1604,7 +1608,8 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
   std::vector<Ord> order(nc.size());
   for (size_t k = 0; k < nc.size(); ++k)
     order[k] = {nc[k].m, morton_key(nc[k].l, nc[k].ix, nc[k].iy, lmax[nc[k].m]), (int64_t)k};
-  std::sort(order.begin(), order.end());
+  // leaves generated from a Morton-ordered mesh are already in order
+  if (!std::is_sorted(order.begin(), order.end())) std::sort(order.begin(), order.end());
   const int64_t m = (int64_t)nc.size();
   ctx->plan_cells.resize(3 * m);
   ctx->plan_member.resize(m);
@@ -1647,6 +1652,15 @@ perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Une
   if (!ctx->has_plan) return fail(ctx, PERK_E_NOT_READY, "no AMR plan");
   if (!d_Uold || !d_Unew || d_Uold == d_Unew) return fail(ctx, PERK_E_INVALID_ARG, "need distinct old and new U");
   const int64_t m = (int64_t)ctx->plan_cells.size() / 3;
+  if (ctx->plan_identity) {
+    // nothing changes: the new state is a copy and the mesh, partition and graph stay
+    PERK_CUDA(ctx, cudaMemcpyAsync(d_Unew, d_Uold, (size_t)m * ELEM * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+    ctx->has_plan = false;
+    ctx->plan_cells.clear();
+    ctx->plan_member.clear();
+    return PERK_OK;
+  }
   PERK_CUDA(ctx, ctx->d_map.ensure((size_t)5 * m));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_map.p, ctx->plan_map.data(), ctx->plan_map.size() * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, ctx->stream));

@@ -128,9 +128,10 @@ __device__ __forceinline__ double log_tab(double x, const double* __restrict__ i
   return x > 0.0 ? v : __longlong_as_double(0x7FF8000000000000LL);
 }
 
-// Node quantities of the two-point flux (half values fold the 1/2 of the means).
-struct NodeQ {
-  double rho, lnrho, beta, lnbeta, v1, v2, hv1, hv2, hp;
+// Node quantities of the two-point flux (half values fold the 1/2 of the means),
+// padded to 80 bytes so that shared-memory reads can use 16-byte loads.
+struct __align__(16) NodeQ {
+  double rho, lnrho, beta, lnbeta, v1, v2, hv1, hv2, hp, pad;
 };
 
 __device__ __forceinline__ NodeQ node_q(const double u[4], double gm1, const double* inv_c, const double* ln_c) {
@@ -251,62 +252,100 @@ __device__ __forceinline__ void phys_flux(const double u[4], double vn, double p
   f[3] = (u[3] + p) * vn;
 }
 
+// Surface fluxes in the face's frame: the state is rotated to (rho, m_n, m_t, E)
+// with selects (no dynamically indexed arrays), the flux computed there and
+// rotated back.  Reciprocals are Newton-Raphson ones; one reciprocal of
+// rho_L rho_R gives both 1/rho.
+struct FaceState {
+  double rho, mn, mt, E, ir, v, p, c;
+};
+
+__device__ __forceinline__ void face_pair(const double uL[4], const double uR[4], int dir, const Ops& ops,
+                                          FaceState& L, FaceState& R) {
+  const double r2 = rcp_nr(uL[0] * uR[0]);
+  L.rho = uL[0];
+  R.rho = uR[0];
+  L.ir = uR[0] * r2;
+  R.ir = uL[0] * r2;
+  L.mn = dir ? uL[2] : uL[1];
+  L.mt = dir ? uL[1] : uL[2];
+  R.mn = dir ? uR[2] : uR[1];
+  R.mt = dir ? uR[1] : uR[2];
+  L.E = uL[3];
+  R.E = uR[3];
+  L.v = L.mn * L.ir;
+  R.v = R.mn * R.ir;
+  L.p = ops.gm1 * fma(-0.5 * L.ir, fma(L.mn, L.mn, L.mt * L.mt), L.E);
+  R.p = ops.gm1 * fma(-0.5 * R.ir, fma(R.mn, R.mn, R.mt * R.mt), R.E);
+  L.c = sqrt(ops.gamma * L.p * L.ir);
+  R.c = sqrt(ops.gamma * R.p * R.ir);
+}
+
+__device__ __forceinline__ void face_flux_rot(const FaceState& s, double F[4]) {
+  F[0] = s.mn;
+  F[1] = fma(s.mn, s.v, s.p);
+  F[2] = s.mt * s.v;
+  F[3] = (s.E + s.p) * s.v;
+}
+
+__device__ __forceinline__ void rotate_back(const double F[4], int dir, double f[4]) {
+  f[0] = F[0];
+  f[1] = dir ? F[2] : F[1];
+  f[2] = dir ? F[1] : F[2];
+  f[3] = F[3];
+}
+
 // HLL with Davis wave-speed estimates S_L = min(vL - cL, vR - cR), S_R = max(vL + cL, vR + cR).
 __device__ void flux_hll(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
-  const double irL = 1.0 / uL[0], irR = 1.0 / uR[0];
-  const double pL = ops.gm1 * (uL[3] - 0.5 * (uL[1] * uL[1] + uL[2] * uL[2]) * irL);
-  const double pR = ops.gm1 * (uR[3] - 0.5 * (uR[1] * uR[1] + uR[2] * uR[2]) * irR);
-  const double vL = uL[1 + dir] * irL, vR = uR[1 + dir] * irR;
-  const double cL = sqrt(ops.gamma * pL * irL), cR = sqrt(ops.gamma * pR * irR);
-  const double SL = fmin(vL - cL, vR - cR), SR = fmax(vL + cL, vR + cR);
-  double fL[4], fR[4];
-  phys_flux(uL, vL, pL, dir, fL);
-  phys_flux(uR, vR, pR, dir, fR);
+  FaceState L, R;
+  face_pair(uL, uR, dir, ops, L, R);
+  const double SL = fmin(L.v - L.c, R.v - R.c), SR = fmax(L.v + L.c, R.v + R.c);
+  double F[4];
   if (SL >= 0.0) {
-    for (int v = 0; v < 4; ++v) f[v] = fL[v];
+    face_flux_rot(L, F);
   } else if (SR <= 0.0) {
-    for (int v = 0; v < 4; ++v) f[v] = fR[v];
+    face_flux_rot(R, F);
   } else {
-    const double inv = 1.0 / (SR - SL);
+    double FL[4], FR[4];
+    face_flux_rot(L, FL);
+    face_flux_rot(R, FR);
+    const double inv = rcp_nr(SR - SL);
     const double SLSR = SL * SR;
-    for (int v = 0; v < 4; ++v) f[v] = (SR * fL[v] - SL * fR[v] + SLSR * (uR[v] - uL[v])) * inv;
+    const double dU[4] = {R.rho - L.rho, R.mn - L.mn, R.mt - L.mt, R.E - L.E};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = fma(SLSR, dU[v], SR * FL[v] - SL * FR[v]) * inv;
   }
+  rotate_back(F, dir, f);
 }
 
 // HLLC (Toro, Spruce, Speares 1994) with the same speeds and the standard contact speed.
 __device__ void flux_hllc(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
-  const double irL = 1.0 / uL[0], irR = 1.0 / uR[0];
-  const double pL = ops.gm1 * (uL[3] - 0.5 * (uL[1] * uL[1] + uL[2] * uL[2]) * irL);
-  const double pR = ops.gm1 * (uR[3] - 0.5 * (uR[1] * uR[1] + uR[2] * uR[2]) * irR);
-  const double vL = uL[1 + dir] * irL, vR = uR[1 + dir] * irR;
-  const double cL = sqrt(ops.gamma * pL * irL), cR = sqrt(ops.gamma * pR * irR);
-  const double SL = fmin(vL - cL, vR - cR), SR = fmax(vL + cL, vR + cR);
+  FaceState L, R;
+  face_pair(uL, uR, dir, ops, L, R);
+  const double SL = fmin(L.v - L.c, R.v - R.c), SR = fmax(L.v + L.c, R.v + R.c);
+  double F[4];
   if (SL >= 0.0) {
-    phys_flux(uL, vL, pL, dir, f);
-    return;
+    face_flux_rot(L, F);
+  } else if (SR <= 0.0) {
+    face_flux_rot(R, F);
+  } else {
+    const double mL = L.rho * (SL - L.v), mR = R.rho * (SR - R.v);
+    const double Ss = (R.p - L.p + mL * L.v - mR * R.v) * rcp_nr(mL - mR);
+    const bool left = Ss >= 0.0;
+    const FaceState& K = left ? L : R;
+    const double S = left ? SL : SR;
+    const double m = left ? mL : mR;
+    face_flux_rot(K, F);
+    // one reciprocal for fac = m / (S - S*) and p / m
+    const double q = rcp_nr((S - Ss) * m);
+    const double fac = m * m * q;
+    const double p_over_m = K.p * (S - Ss) * q;
+    const double Us[4] = {fac, fac * Ss, fac * (K.mt * K.ir), fac * fma(Ss - K.v, Ss + p_over_m, K.E * K.ir)};
+    const double Uk[4] = {K.rho, K.mn, K.mt, K.E};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = fma(S, Us[v] - Uk[v], F[v]);
   }
-  if (SR <= 0.0) {
-    phys_flux(uR, vR, pR, dir, f);
-    return;
-  }
-  const double mL = uL[0] * (SL - vL), mR = uR[0] * (SR - vR);
-  const double Ss = (pR - pL + mL * vL - mR * vR) / (mL - mR);
-  const bool left = Ss >= 0.0;
-  const double* u = left ? uL : uR;
-  const double S = left ? SL : SR;
-  const double vn = left ? vL : vR;
-  const double p = left ? pL : pR;
-  const double m = left ? mL : mR;
-  const double ir = left ? irL : irR;
-  double fk[4];
-  phys_flux(u, vn, p, dir, fk);
-  const double fac = m / (S - Ss);          // rho_K (S_K - v_K) / (S_K - S*)
-  double us[4];
-  us[0] = fac;
-  us[1 + dir] = fac * Ss;
-  us[2 - dir] = fac * (u[2 - dir] * ir);
-  us[3] = fac * (u[3] * ir + (Ss - vn) * (Ss + p / m));
-  for (int v = 0; v < 4; ++v) f[v] = fk[v] + S * (us[v] - u[v]);
+  rotate_back(F, dir, f);
 }
 
 __device__ void flux_ec_surface(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
