@@ -645,23 +645,163 @@ __global__ void __launch_bounds__(128) k_vjp_faces(Ops ops, int64_t n_if, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Reverse (adjoint) sweep of the volume term, written out by hand.
+//
+// Field order of the node quantities and of their adjoints:
+//   0 rho, 1 ln rho, 2 beta = rho/p, 3 ln beta, 4 v1, 5 v2, 6 v1/2, 7 v2/2, 8 p/2
+enum { Q_RHO = 0, Q_LNRHO, Q_BETA, Q_LNBETA, Q_V1, Q_V2, Q_HV1, Q_HV2, Q_HP, NQ };
+
+// derivatives of the log-mean series in u
+__device__ __forceinline__ double series_H_d(double u) {   // H'(u)
+  double r = 5.0 * (-5098.0 / 467775.0);
+  r = fma(r, u, 4.0 * (-214.0 / 14175.0));
+  r = fma(r, u, 3.0 * (-22.0 / 945.0));
+  r = fma(r, u, 2.0 * (-2.0 / 45.0));
+  return fma(r, u, -1.0 / 6.0);
+}
+__device__ __forceinline__ double series_2A_d(double u) {  // (2A)'(u)
+  double r = 5.0 * (2.0 / 11.0);
+  r = fma(r, u, 4.0 * (2.0 / 9.0));
+  r = fma(r, u, 3.0 * (2.0 / 7.0));
+  r = fma(r, u, 2.0 * (2.0 / 5.0));
+  return fma(r, u, 2.0 / 3.0);
+}
+
+// Given the adjoint g of the flux f#(A, B) in direction dir, accumulate the
+// adjoints of A's and B's node quantities into gA, gB (the forward
+// intermediates are recomputed; branch decisions as in the forward flux).
+__device__ __forceinline__ void ec_flux_rev(const NodeQ<double>& A, const NodeQ<double>& B, int dir, double inv_gm1,
+                                            const double g[4], double gA[NQ], double gB[NQ]) {
+  // forward
+  const double dr = B.rho - A.rho, sr = A.rho + B.rho;
+  const double db = B.beta - A.beta, sb = A.beta + B.beta;
+  const bool ser_r = fabs(dr) < 0.03 * sr;
+  const bool ser_b = fabs(db) < 0.03 * sb;
+  const double den_r = ser_r ? sr : B.lnrho - A.lnrho;
+  const double den_b = ser_b ? sb : db;
+  const double r = rcp_val(den_r * den_b);
+  const double qr = den_b * r, qb = den_r * r;
+  const double fr = dr * qr;
+  const double ur = fr * fr;
+  const double Hr = ser_r ? series_H(ur) : 0.0;
+  const double rho_ln = ser_r ? sr * Hr : fr;
+  const double fb = db * qb;
+  const double ub = fb * fb;
+  const double A2 = ser_b ? series_2A(ub) : 0.0;
+  const double dlb = B.lnbeta - A.lnbeta;
+  const double ibeta = ser_b ? qb * A2 : dlb * qb;
+  const double v1m = A.hv1 + B.hv1, v2m = A.hv2 + B.hv2;
+  const double vnA = dir ? A.v2 : A.v1, vnB = dir ? B.v2 : B.v1;
+  const double vnm = dir ? v2m : v1m;
+  const double frho = rho_ln * vnm;
+  const double kin = fma(A.hv1, B.v1, A.hv2 * B.v2);
+  const double T = fma(ibeta, inv_gm1, kin);
+  // reverse
+  double g_v1m = g[1] * frho, g_v2m = g[2] * frho;
+  const double g_frho = g[0] + g[1] * v1m + g[2] * v2m + g[3] * T;
+  const double g_pm = dir ? g[2] : g[1];
+  const double g_T = g[3] * frho;
+  const double g_ibeta = g_T * inv_gm1;
+  const double g_kin = g_T;
+  gA[Q_HP] += g[3] * vnB + g_pm;
+  gB[Q_HP] += g[3] * vnA + g_pm;
+  const double g_vnB = g[3] * A.hp, g_vnA = g[3] * B.hp;
+  gA[Q_HV1] += g_kin * B.v1;
+  gB[Q_V1] += g_kin * A.hv1;
+  gA[Q_HV2] += g_kin * B.v2;
+  gB[Q_V2] += g_kin * A.hv2;
+  const double g_rho_ln = g_frho * vnm;
+  const double g_vnm = g_frho * rho_ln;
+  if (dir) {
+    g_v2m += g_vnm;
+    gA[Q_V2] += g_vnA;
+    gB[Q_V2] += g_vnB;
+  } else {
+    g_v1m += g_vnm;
+    gA[Q_V1] += g_vnA;
+    gB[Q_V1] += g_vnB;
+  }
+  gA[Q_HV1] += g_v1m;
+  gB[Q_HV1] += g_v1m;
+  gA[Q_HV2] += g_v2m;
+  gB[Q_HV2] += g_v2m;
+  // 1 / {{beta}}_ln
+  double g_qb = 0.0, g_db = 0.0, g_sb = 0.0;
+  if (ser_b) {
+    g_qb += g_ibeta * A2;
+    const double g_fb = 2.0 * fb * (g_ibeta * qb * series_2A_d(ub));
+    g_db += g_fb * qb;
+    g_qb += g_fb * db;
+  } else {
+    gB[Q_LNBETA] += g_ibeta * qb;
+    gA[Q_LNBETA] -= g_ibeta * qb;
+    g_qb += g_ibeta * dlb;
+  }
+  // {{rho}}_ln
+  double g_sr = 0.0, g_fr;
+  if (ser_r) {
+    g_sr += g_rho_ln * Hr;
+    g_fr = 2.0 * fr * (g_rho_ln * sr * series_H_d(ur));
+  } else {
+    g_fr = g_rho_ln;
+  }
+  const double g_dr = g_fr * qr;
+  const double g_qr = g_fr * dr;
+  // qr = 1/den_r, qb = 1/den_b
+  const double g_den_r = -g_qr * qr * qr;
+  const double g_den_b = -g_qb * qb * qb;
+  if (ser_r) {
+    g_sr += g_den_r;
+  } else {
+    gB[Q_LNRHO] += g_den_r;
+    gA[Q_LNRHO] -= g_den_r;
+  }
+  if (ser_b)
+    g_sb += g_den_b;
+  else
+    g_db += g_den_b;
+  gA[Q_RHO] += g_sr - g_dr;
+  gB[Q_RHO] += g_sr + g_dr;
+  gA[Q_BETA] += g_sb - g_db;
+  gB[Q_BETA] += g_sb + g_db;
+}
+
+// adjoint of the node quantities with respect to the conserved state u
+__device__ __forceinline__ void node_q_rev(const double u[4], const NodeQ<double>& q, double gm1, const double gq[NQ],
+                                           double gu[4]) {
+  const double rho = q.rho, ir = rcp_val(rho);
+  const double beta = q.beta;
+  const double ip = beta * ir;                 // 1/p = (rho/p)/rho
+  double g_rho = gq[Q_RHO] + gq[Q_LNRHO] * ir;
+  const double g_beta = gq[Q_BETA] + gq[Q_LNBETA] * rcp_val(beta);
+  const double g_v1 = gq[Q_V1] + 0.5 * gq[Q_HV1];
+  const double g_v2 = gq[Q_V2] + 0.5 * gq[Q_HV2];
+  double g_p = 0.5 * gq[Q_HP];
+  g_rho += g_beta * ip;                        // beta = rho / p
+  g_p -= g_beta * beta * ip;
+  const double v1 = q.v1, v2 = q.v2;
+  gu[0] = g_rho - (g_v1 * v1 + g_v2 * v2) * ir + g_p * gm1 * 0.5 * (v1 * v1 + v2 * v2);
+  gu[1] = g_v1 * ir - g_p * gm1 * v1;
+  gu[2] = g_v2 * ir - g_p * gm1 * v2;
+  gu[3] = g_p * gm1;
+}
+
 // Element kernel over the sorted list: the first n_act elements are active
-// (volume adjoint with the pair Jacobians); every element adds the face
+// (volume adjoint by the reverse sweep above); every element adds the face
 // adjoints of its four faces from gsurf (zeroed beforehand, so faces that were
 // not active contribute nothing).
-constexpr int VJP_ELEMS = 4;  // 64 threads: the Dual<4> node data would exceed 48 KB at 8 elements
+constexpr int VJP_ELEMS = 4;
 
 __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64_t n_act,
-                                                     const int32_t* __restrict__ elems,
-                                                     const int32_t* __restrict__ level, double two_over_len,
-                                                     const double* __restrict__ Y, const double* __restrict__ lam,
-                                                     const double* __restrict__ gsurf,
-                                                     const double* __restrict__ logt, double* __restrict__ g) {
-  using D4 = Dual<4>;
-  using D8 = Dual<8>;
-  __shared__ NodeQ<D4> s_q[VJP_ELEMS][NODES];
+                                                    const int32_t* __restrict__ elems,
+                                                    const int32_t* __restrict__ level, double two_over_len,
+                                                    const double* __restrict__ Y, const double* __restrict__ lam,
+                                                    const double* __restrict__ gsurf,
+                                                    const double* __restrict__ logt, double* __restrict__ g) {
+  __shared__ NodeQ<double> s_q[VJP_ELEMS][NODES];
   __shared__ double s_mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
-  __shared__ double s_g[VJP_ELEMS][8][48];           // per pair: adjoint of its two states
+  __shared__ double s_g[VJP_ELEMS][48][2 * NQ];       // per pair: adjoints of its two node records
   __shared__ double s_log[2 * LOG_TABLE_SIZE];
   for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
   __syncthreads();
@@ -670,15 +810,12 @@ __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64
   const bool valid = slot < n_all;
   const bool active = slot < n_act;
   const int64_t e = valid ? elems[slot] : 0;
-  // the volume part exists only for active elements; inactive slots run it on a dummy state
-  D4 y[4];
-  for (int v = 0; v < 4; ++v) {
-    y[v] = cst<4>(active ? Y[e * ELEM + v * NODES + t] : (v == 0 ? 1.0 : v == 3 ? 2.5 : 0.0));
-    y[v].d[v] = 1.0;
-  }
+  double y[4];
+  for (int v = 0; v < 4; ++v) y[v] = active ? Y[e * ELEM + v * NODES + t] : (v == 0 ? 1.0 : v == 3 ? 2.5 : 0.0);
   const double scale = valid ? -ldexp(two_over_len, level[e]) : 0.0;
   for (int v = 0; v < 4; ++v) s_mu[le][v][t] = active ? scale * lam[e * ELEM + v * NODES + t] : 0.0;
-  s_q[le][t] = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
+  const NodeQ<double> myq = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
+  s_q[le][t] = myq;
   __syncwarp();
   for (int kk = 0; kk < 3; ++kk) {
     const int p = t + 16 * kk;
@@ -689,56 +826,34 @@ __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64
     const int b = qq + 1 - (a * (5 - a)) / 2;
     const int na = dir ? a * 4 + line : line * 4 + a;
     const int nb = dir ? b * 4 + line : line * 4 + b;
-    // local indices along the pair's line
-    const int ia = a, ib = b;
-    const int li = dir ? line : line;  // (unused: the coefficients depend on ia, ib only)
-    (void)li;
-    NodeQ<D8> A, B;
-    {
-      const NodeQ<D4>& qa = s_q[le][na];
-      const NodeQ<D4>& qb = s_q[le][nb];
-      const D4* fa = &qa.rho;
-      const D4* fb = &qb.rho;
-      D8* ta = &A.rho;
-      D8* tb = &B.rho;
-      for (int m = 0; m < 9; ++m) {
-        ta[m].v = fa[m].v;
-        tb[m].v = fb[m].v;
-        for (int c = 0; c < 4; ++c) {
-          ta[m].d[c] = fa[m].d[c];
-          ta[m].d[4 + c] = 0.0;
-          tb[m].d[c] = 0.0;
-          tb[m].d[4 + c] = fb[m].d[c];
-        }
-      }
-    }
-    D8 f[4];
-    ec_flux(A, B, dir, ops.inv_gm1, f);
-    // f enters K_a with D_split[a][b] and K_b with D_split[b][a]
-    double gf[4];
-    for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[ia][ib] * s_mu[le][v][na] + ops.dsplit[ib][ia] * s_mu[le][v][nb];
-    for (int c = 0; c < 8; ++c) {
-      double acc = 0.0;
-      for (int v = 0; v < 4; ++v) acc = fma(gf[v], f[v].d[c], acc);
-      s_g[le][c][p] = acc;
+    double gf[4], gA[NQ], gB[NQ];
+    for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[a][b] * s_mu[le][v][na] + ops.dsplit[b][a] * s_mu[le][v][nb];
+    for (int m = 0; m < NQ; ++m) gA[m] = gB[m] = 0.0;
+    ec_flux_rev(s_q[le][na], s_q[le][nb], dir, ops.inv_gm1, gf, gA, gB);
+    for (int m = 0; m < NQ; ++m) {
+      s_g[le][p][m] = gA[m];
+      s_g[le][p][NQ + m] = gB[m];
     }
   }
   __syncwarp();
   if (!valid) return;
   double out[4] = {0.0, 0.0, 0.0, 0.0};
   if (active) {
+    double gq[NQ];
+    for (int m = 0; m < NQ; ++m) gq[m] = 0.0;
     for (int mm = 0; mm < 4; ++mm) {
       if (mm != i) {
         const int p = j * 6 + pair_slot(min(i, mm), max(i, mm));
-        const int side = i < mm ? 0 : 4;       // this node is the pair's first (a) or second (b) state
-        for (int c = 0; c < 4; ++c) out[c] += s_g[le][side + c][p];
+        const int side = i < mm ? 0 : NQ;
+        for (int m = 0; m < NQ; ++m) gq[m] += s_g[le][p][side + m];
       }
       if (mm != j) {
         const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
-        const int side = j < mm ? 0 : 4;
-        for (int c = 0; c < 4; ++c) out[c] += s_g[le][side + c][p];
+        const int side = j < mm ? 0 : NQ;
+        for (int m = 0; m < NQ; ++m) gq[m] += s_g[le][p][side + m];
       }
     }
+    node_q_rev(y, myq, ops.gm1, gq, out);
   }
   const double* gs = gsurf + e * ELEM;
   for (int c = 0; c < 4; ++c) {
