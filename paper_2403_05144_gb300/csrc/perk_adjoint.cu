@@ -6,11 +6,10 @@
 // logarithm table, reciprocals and branch decisions, which are taken on the
 // values).  Forward-mode dual numbers carry the derivatives:
 //   * JVP: one tangent per value (Dual<1>): K and dK = J(Y) v in one pass.
-//   * VJP: the Jacobians of every two-point volume flux and every surface flux
-//     with respect to both of their states (Dual<8>: four tangents per side),
-//     contracted on the fly with the adjoint weights of the flux, so that
-//     J(Y)^T lambda is assembled pair by pair and face by face without ever
-//     forming the element Jacobian.
+//   * VJP: hand-written reverse sweeps of the two-point volume flux, the node
+//     quantities and the surface fluxes, applied to the adjoint weight of every
+//     pair and face-node flux, so that J(Y)^T lambda is assembled pair by pair
+//     and face by face without ever forming a Jacobian.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -532,119 +531,6 @@ __device__ __forceinline__ double lift_coef(int face, double two_over_len, int l
   return (face & 1) ? -s * iw : s * iw;
 }
 
-__global__ void __launch_bounds__(128) k_vjp_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
-                                                    int64_t n_mort, const int4* __restrict__ morts, int64_t if_blocks,
-                                                    const int32_t* __restrict__ level,
-                                                    const int32_t* __restrict__ method, int min_member,
-                                                    double two_over_len,
-                                                    const double* __restrict__ Y, const double* __restrict__ lam,
-                                                    const double* __restrict__ logt, double* __restrict__ gsurf) {
-  using D8 = Dual<8>;
-  __shared__ double s_gphi[16][4][NN];       // adjoint of the projected large-face flux
-  __shared__ double s_gui[16][2][4][NN];     // adjoint of the interpolated large trace, per half
-  const double* ic = logt;
-  const double* lc = logt + LOG_TABLE_SIZE;
-  const double iw = ops.inv_w0;
-  auto load8 = [&](int64_t e, int node, int side, D8 u[4]) {
-    for (int v = 0; v < 4; ++v) {
-      u[v] = cst<8>(Y[e * ELEM + v * NODES + node]);
-      u[v].d[4 * side + v] = 1.0;
-    }
-  };
-  if (blockIdx.x < if_blocks) {
-    const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
-    const int k = threadIdx.x & 3;
-    if (idx >= n_if) return;
-    const int4 r = ifs[idx];
-    const int dir = r.z;
-    const int fL = 2 * dir + 1, fR = 2 * dir;
-    D8 uL[4], uR[4], f[4];
-    load8(r.x, face_node(fL, k), 0, uL);
-    load8(r.y, face_node(fR, k), 1, uR);
-    surface_flux(uL, uR, dir, ops, ic, lc, f);
-    const double cL = lift_coef(fL, two_over_len, level[r.x], iw);
-    const double cR = lift_coef(fR, two_over_len, level[r.y], iw);
-    double gf[4];
-    for (int v = 0; v < 4; ++v)
-      gf[v] = cL * lam[(int64_t)r.x * ELEM + v * NODES + face_node(fL, k)] +
-              cR * lam[(int64_t)r.y * ELEM + v * NODES + face_node(fR, k)];
-    for (int c = 0; c < 4; ++c) {
-      double gl = 0.0, gr = 0.0;
-      for (int v = 0; v < 4; ++v) {
-        gl = fma(gf[v], f[v].d[c], gl);
-        gr = fma(gf[v], f[v].d[4 + c], gr);
-      }
-      gsurf[(int64_t)r.x * ELEM + fL * 16 + 4 * c + k] = gl;
-      gsurf[(int64_t)r.y * ELEM + fR * 16 + 4 * c + k] = gr;
-    }
-    return;
-  }
-  const int lm = threadIdx.x >> 3;
-  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * 16 + lm;
-  const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
-  const bool valid = idx < n_mort;
-  int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
-  const int dir = r.w & 1, large_side = (r.w >> 1) & 1;
-  const int large_face = large_side == 0 ? 2 * dir + 1 : 2 * dir;
-  const int small_face = large_side == 0 ? 2 * dir : 2 * dir + 1;
-  const int small = half ? r.z : r.y;
-  // adjoint of the large face's projected flux phi at its node k (threads of half 0 write it);
-  // a large element whose member is not active at this stage has no K here (lam counts as zero)
-  if (valid && half == 0) {
-    const double cl = method[r.x] >= min_member ? lift_coef(large_face, two_over_len, level[r.x], iw) : 0.0;
-    for (int v = 0; v < 4; ++v) s_gphi[lm][v][k] = cl * lam[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, k)];
-  }
-  __syncthreads();
-  if (valid) {
-    // flux at node k of this half, with tangents on the interpolated large trace (slots 0-3) and the small trace (4-7)
-    D8 ui[4], us[4], f[4];
-    for (int v = 0; v < 4; ++v) ui[v] = cst<8>(0.0);
-    for (int l = 0; l < NN; ++l) {
-      const double w = half ? ops.p_hi[k][l] : ops.p_lo[k][l];
-      for (int v = 0; v < 4; ++v) ui[v].v = fma(w, Y[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, l)], ui[v].v);
-    }
-    for (int v = 0; v < 4; ++v) ui[v].d[v] = 1.0;
-    load8(small, face_node(small_face, k), 1, us);
-    if (large_side == 0)
-      surface_flux(ui, us, dir, ops, ic, lc, f);
-    else {
-      // swap the roles so that slots 0-3 still belong to the large trace
-      surface_flux(us, ui, dir, ops, ic, lc, f);
-    }
-    const double cs = lift_coef(small_face, two_over_len, level[small], iw);
-    double gf[4];
-    for (int v = 0; v < 4; ++v) {
-      double g = cs * lam[(int64_t)small * ELEM + v * NODES + face_node(small_face, k)];
-      // projection phi[m] = sum_l R_h[m][l] f_h[l]: adjoint of f_h[k] gathers R_h[m][k] gphi[m]
-      for (int m = 0; m < NN; ++m) g = fma(half ? ops.r_hi[m][k] : ops.r_lo[m][k], s_gphi[lm][v][m], g);
-      gf[v] = g;
-    }
-    for (int c = 0; c < 4; ++c) {
-      double gl = 0.0, gs = 0.0;
-      for (int v = 0; v < 4; ++v) {
-        gl = fma(gf[v], f[v].d[c], gl);
-        gs = fma(gf[v], f[v].d[4 + c], gs);
-      }
-      gsurf[(int64_t)small * ELEM + small_face * 16 + 4 * c + k] = gs;
-      s_gui[lm][half][c][k] = gl;
-    }
-  }
-  __syncthreads();
-  if (valid) {
-    // adjoint of the large trace: u_interp_h[l] = sum_m P_h[l][m] u_large[m]; thread (half, k) writes
-    // variables 2 half, 2 half + 1 at large node k
-    for (int cc = 0; cc < 2; ++cc) {
-      const int c = 2 * half + cc;
-      double g = 0.0;
-      for (int l = 0; l < NN; ++l) {
-        g = fma(ops.p_lo[l][k], s_gui[lm][0][c][l], g);
-        g = fma(ops.p_hi[l][k], s_gui[lm][1][c][l], g);
-      }
-      gsurf[(int64_t)r.x * ELEM + large_face * 16 + 4 * c + k] = g;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Reverse (adjoint) sweep of the volume term, written out by hand.
 //
@@ -785,6 +671,307 @@ __device__ __forceinline__ void node_q_rev(const double u[4], const NodeQ<double
   gu[1] = g_v1 * ir - g_p * gm1 * v1;
   gu[2] = g_v2 * ir - g_p * gm1 * v2;
   gu[3] = g_p * gm1;
+}
+
+// ---------------------------------------------------------------------------
+// Reverse sweeps of the surface fluxes (HLL, HLLC, EC), written out by hand.
+// Everything happens in the face frame (rho, m_n, m_t, E); the adjoint of the
+// rotated flux comes in, the adjoints of both rotated states go out.
+struct SideF {
+  double rho, mn, mt, E, ir, v, p, c;
+};
+struct SideG {
+  double rho = 0, mn = 0, mt = 0, E = 0, ir = 0, v = 0, p = 0, c = 0;
+};
+
+__device__ __forceinline__ void side_fwd(const double u[4], int dir, const Ops& ops, SideF& s) {
+  s.rho = u[0];
+  s.mn = dir ? u[2] : u[1];
+  s.mt = dir ? u[1] : u[2];
+  s.E = u[3];
+  s.ir = rcp_val(s.rho);
+  s.v = s.mn * s.ir;
+  s.p = ops.gm1 * (s.E - 0.5 * s.ir * (s.mn * s.mn + s.mt * s.mt));
+  s.c = sqrt(ops.gamma * s.p * s.ir);
+}
+
+// adjoints of (ir, v, p, c) -> adjoints of (rho, mn, mt, E), then rotated back to u's order
+__device__ __forceinline__ void side_rev(const SideF& s, SideG& g, int dir, const Ops& ops, double gu[4]) {
+  if (s.c > 0.0) {
+    const double h = 0.5 * ops.gamma / s.c;
+    g.p += g.c * h * s.ir;
+    g.ir += g.c * h * s.p;
+  }
+  g.E += ops.gm1 * g.p;
+  g.ir -= 0.5 * ops.gm1 * (s.mn * s.mn + s.mt * s.mt) * g.p;
+  const double g_e2 = -0.5 * ops.gm1 * s.ir * g.p;
+  g.mn += 2.0 * s.mn * g_e2 + s.ir * g.v;
+  g.mt += 2.0 * s.mt * g_e2;
+  g.ir += s.mn * g.v;
+  g.rho -= s.ir * s.ir * g.ir;
+  gu[0] = g.rho;
+  gu[1] = dir ? g.mt : g.mn;
+  gu[2] = dir ? g.mn : g.mt;
+  gu[3] = g.E;
+}
+
+// physical flux F = (mn, mn v + p, mt v, (E + p) v) of one side: adjoint G -> side adjoints
+__device__ __forceinline__ void phys_rev(const SideF& s, const double G[4], SideG& g) {
+  g.mn += G[0] + G[1] * s.v;
+  g.v += G[1] * s.mn + G[2] * s.mt + G[3] * (s.E + s.p);
+  g.p += G[1] + G[3] * s.v;
+  g.mt += G[2] * s.v;
+  g.E += G[3] * s.v;
+}
+__device__ __forceinline__ void phys_fwd(const SideF& s, double F[4]) {
+  F[0] = s.mn;
+  F[1] = s.mn * s.v + s.p;
+  F[2] = s.mt * s.v;
+  F[3] = (s.E + s.p) * s.v;
+}
+
+// Davis speeds: route the adjoints of S_L = min(..), S_R = max(..) to the chosen arguments
+__device__ __forceinline__ void speeds_rev(const SideF& L, const SideF& R, double gSL, double gSR, SideG& gl,
+                                           SideG& gr) {
+  if (L.v - L.c <= R.v - R.c) {
+    gl.v += gSL;
+    gl.c -= gSL;
+  } else {
+    gr.v += gSL;
+    gr.c -= gSL;
+  }
+  if (L.v + L.c >= R.v + R.c) {
+    gl.v += gSR;
+    gl.c += gSR;
+  } else {
+    gr.v += gSR;
+    gr.c += gSR;
+  }
+}
+
+__device__ void hll_rev(const double uL[4], const double uR[4], int dir, const Ops& ops, const double gf[4],
+                        double guL[4], double guR[4]) {
+  SideF L, R;
+  side_fwd(uL, dir, ops, L);
+  side_fwd(uR, dir, ops, R);
+  const double G[4] = {gf[0], dir ? gf[2] : gf[1], dir ? gf[1] : gf[2], gf[3]};
+  SideG gl, gr;
+  const double SL = fmin(L.v - L.c, R.v - R.c), SR = fmax(L.v + L.c, R.v + R.c);
+  if (SL >= 0.0) {
+    phys_rev(L, G, gl);
+  } else if (SR <= 0.0) {
+    phys_rev(R, G, gr);
+  } else {
+    double FL[4], FR[4], F[4];
+    phys_fwd(L, FL);
+    phys_fwd(R, FR);
+    const double iD = rcp_val(SR - SL);
+    const double dU[4] = {R.rho - L.rho, R.mn - L.mn, R.mt - L.mt, R.E - L.E};
+    double gSL = 0.0, gSR = 0.0, GL[4], GR[4];
+    for (int v = 0; v < 4; ++v) {
+      F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * dU[v]) * iD;
+      GL[v] = G[v] * SR * iD;
+      GR[v] = -G[v] * SL * iD;
+      gSR += G[v] * (FL[v] + SL * dU[v] - F[v]) * iD;
+      gSL += G[v] * (-FR[v] + SR * dU[v] + F[v]) * iD;
+    }
+    phys_rev(L, GL, gl);
+    phys_rev(R, GR, gr);
+    const double w = SL * SR * iD;   // adjoint of dU
+    gr.rho += G[0] * w; gl.rho -= G[0] * w;
+    gr.mn += G[1] * w;  gl.mn -= G[1] * w;
+    gr.mt += G[2] * w;  gl.mt -= G[2] * w;
+    gr.E += G[3] * w;   gl.E -= G[3] * w;
+    speeds_rev(L, R, gSL, gSR, gl, gr);
+  }
+  side_rev(L, gl, dir, ops, guL);
+  side_rev(R, gr, dir, ops, guR);
+}
+
+__device__ void hllc_rev(const double uL[4], const double uR[4], int dir, const Ops& ops, const double gf[4],
+                         double guL[4], double guR[4]) {
+  SideF L, R;
+  side_fwd(uL, dir, ops, L);
+  side_fwd(uR, dir, ops, R);
+  const double G[4] = {gf[0], dir ? gf[2] : gf[1], dir ? gf[1] : gf[2], gf[3]};
+  SideG gl, gr;
+  const double SL = fmin(L.v - L.c, R.v - R.c), SR = fmax(L.v + L.c, R.v + R.c);
+  if (SL >= 0.0) {
+    phys_rev(L, G, gl);
+  } else if (SR <= 0.0) {
+    phys_rev(R, G, gr);
+  } else {
+    const double mL = L.rho * (SL - L.v), mR = R.rho * (SR - R.v);
+    const double num = R.p - L.p + mL * L.v - mR * R.v, den = mL - mR;
+    const double iden = rcp_val(den);
+    const double Ss = num * iden;
+    const bool left = Ss >= 0.0;
+    const SideF& K = left ? L : R;
+    SideG& gk = left ? gl : gr;
+    const double S = left ? SL : SR;
+    const double m = left ? mL : mR;
+    const double iSmS = rcp_val(S - Ss), im = rcp_val(m);
+    const double fac = m * iSmS;
+    const double pm = K.p * im;
+    const double X = K.E * K.ir + (Ss - K.v) * (Ss + pm);
+    const double Us[4] = {fac, fac * Ss, fac * K.mt * K.ir, fac * X};
+    const double Uk[4] = {K.rho, K.mn, K.mt, K.E};
+    // F = F_K + S (Us - U_K)
+    phys_rev(K, G, gk);
+    double gS = 0.0;
+    for (int v = 0; v < 4; ++v) gS += G[v] * (Us[v] - Uk[v]);
+    gk.rho -= S * G[0];
+    gk.mn -= S * G[1];
+    gk.mt -= S * G[2];
+    gk.E -= S * G[3];
+    const double gUs[4] = {S * G[0], S * G[1], S * G[2], S * G[3]};
+    double g_fac = gUs[0] + gUs[1] * Ss + gUs[2] * K.mt * K.ir + gUs[3] * X;
+    double g_Ss = gUs[1] * fac;
+    gk.mt += gUs[2] * fac * K.ir;
+    gk.ir += gUs[2] * fac * K.mt;
+    const double gX = gUs[3] * fac;
+    gk.E += gX * K.ir;
+    gk.ir += gX * K.E;
+    g_Ss += gX * ((Ss + pm) + (Ss - K.v));
+    gk.v -= gX * (Ss + pm);
+    const double g_pm = gX * (Ss - K.v);
+    gk.p += g_pm * im;
+    double g_m = -g_pm * pm * im;
+    // fac = m / (S - S*)
+    g_m += g_fac * iSmS;
+    gS -= g_fac * fac * iSmS;
+    g_Ss += g_fac * fac * iSmS;
+    // S* = num / den
+    const double g_num = g_Ss * iden, g_den = -g_Ss * Ss * iden;
+    double g_mL = (left ? g_m : 0.0) + g_num * L.v + g_den;
+    double g_mR = (left ? 0.0 : g_m) - g_num * R.v - g_den;
+    gr.p += g_num;
+    gl.p -= g_num;
+    gl.v += g_num * mL;
+    gr.v -= g_num * mR;
+    // m_K = rho_K (S_K - v_K)
+    double gSL = left ? gS : 0.0, gSR = left ? 0.0 : gS;
+    gl.rho += g_mL * (SL - L.v);
+    gSL += g_mL * L.rho;
+    gl.v -= g_mL * L.rho;
+    gr.rho += g_mR * (SR - R.v);
+    gSR += g_mR * R.rho;
+    gr.v -= g_mR * R.rho;
+    speeds_rev(L, R, gSL, gSR, gl, gr);
+  }
+  side_rev(L, gl, dir, ops, guL);
+  side_rev(R, gr, dir, ops, guR);
+}
+
+__device__ void ec_surface_rev(const double uL[4], const double uR[4], int dir, const Ops& ops, const double* ic,
+                               const double* lc, const double gf[4], double guL[4], double guR[4]) {
+  const NodeQ<double> A = node_q(uL, ops.gm1, ic, lc), B = node_q(uR, ops.gm1, ic, lc);
+  double gA[NQ] = {}, gB[NQ] = {};
+  ec_flux_rev(A, B, dir, ops.inv_gm1, gf, gA, gB);
+  node_q_rev(uL, A, ops.gm1, gA, guL);
+  node_q_rev(uR, B, ops.gm1, gB, guR);
+}
+
+__device__ __forceinline__ void surface_flux_rev(const double uL[4], const double uR[4], int dir, const Ops& ops,
+                                                 const double* ic, const double* lc, const double gf[4],
+                                                 double guL[4], double guR[4]) {
+  if (ops.surface_flux == PERK_SURFACE_HLLC)
+    hllc_rev(uL, uR, dir, ops, gf, guL, guR);
+  else if (ops.surface_flux == PERK_SURFACE_EC)
+    ec_surface_rev(uL, uR, dir, ops, ic, lc, gf, guL, guR);
+  else
+    hll_rev(uL, uR, dir, ops, gf, guL, guR);
+}
+
+// Faces: the adjoint weight of every face-node flux (its lifting coefficients times
+// lam on both sides) through the hand-written reverse sweeps.
+__global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                        int64_t n_mort, const int4* __restrict__ morts,
+                                                        int64_t if_blocks, const int32_t* __restrict__ level,
+                                                        const int32_t* __restrict__ method, int min_member,
+                                                        double two_over_len, const double* __restrict__ Y,
+                                                        const double* __restrict__ lam,
+                                                        const double* __restrict__ logt, double* __restrict__ gsurf) {
+  __shared__ double s_gphi[16][4][NN];
+  __shared__ double s_gui[16][2][4][NN];
+  const double* ic = logt;
+  const double* lc = logt + LOG_TABLE_SIZE;
+  const double iw = ops.inv_w0;
+  auto load = [&](int64_t e, int node, double u[4]) {
+    for (int v = 0; v < 4; ++v) u[v] = Y[e * ELEM + v * NODES + node];
+  };
+  if (blockIdx.x < if_blocks) {
+    const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
+    const int k = threadIdx.x & 3;
+    if (idx >= n_if) return;
+    const int4 r = ifs[idx];
+    const int dir = r.z;
+    const int fL = 2 * dir + 1, fR = 2 * dir;
+    double uL[4], uR[4], gl[4], gr[4];
+    load(r.x, face_node(fL, k), uL);
+    load(r.y, face_node(fR, k), uR);
+    const double cL = lift_coef(fL, two_over_len, level[r.x], iw);
+    const double cR = lift_coef(fR, two_over_len, level[r.y], iw);
+    double gf[4];
+    for (int v = 0; v < 4; ++v)
+      gf[v] = cL * lam[(int64_t)r.x * ELEM + v * NODES + face_node(fL, k)] +
+              cR * lam[(int64_t)r.y * ELEM + v * NODES + face_node(fR, k)];
+    surface_flux_rev(uL, uR, dir, ops, ic, lc, gf, gl, gr);
+    for (int c = 0; c < 4; ++c) {
+      gsurf[(int64_t)r.x * ELEM + fL * 16 + 4 * c + k] = gl[c];
+      gsurf[(int64_t)r.y * ELEM + fR * 16 + 4 * c + k] = gr[c];
+    }
+    return;
+  }
+  const int lm = threadIdx.x >> 3;
+  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * 16 + lm;
+  const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
+  const bool valid = idx < n_mort;
+  int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
+  const int dir = r.w & 1, large_side = (r.w >> 1) & 1;
+  const int large_face = large_side == 0 ? 2 * dir + 1 : 2 * dir;
+  const int small_face = large_side == 0 ? 2 * dir : 2 * dir + 1;
+  const int small = half ? r.z : r.y;
+  if (valid && half == 0) {
+    const double cl = method[r.x] >= min_member ? lift_coef(large_face, two_over_len, level[r.x], iw) : 0.0;
+    for (int v = 0; v < 4; ++v) s_gphi[lm][v][k] = cl * lam[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, k)];
+  }
+  __syncthreads();
+  if (valid) {
+    double ui[4] = {0.0, 0.0, 0.0, 0.0}, us[4], gi[4], gs[4];
+    for (int l = 0; l < NN; ++l) {
+      const double w = half ? ops.p_hi[k][l] : ops.p_lo[k][l];
+      for (int v = 0; v < 4; ++v) ui[v] = fma(w, Y[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, l)], ui[v]);
+    }
+    load(small, face_node(small_face, k), us);
+    const double cs = lift_coef(small_face, two_over_len, level[small], iw);
+    double gf[4];
+    for (int v = 0; v < 4; ++v) {
+      double g = cs * lam[(int64_t)small * ELEM + v * NODES + face_node(small_face, k)];
+      for (int m = 0; m < NN; ++m) g = fma(half ? ops.r_hi[m][k] : ops.r_lo[m][k], s_gphi[lm][v][m], g);
+      gf[v] = g;
+    }
+    if (large_side == 0)
+      surface_flux_rev(ui, us, dir, ops, ic, lc, gf, gi, gs);
+    else
+      surface_flux_rev(us, ui, dir, ops, ic, lc, gf, gs, gi);
+    for (int c = 0; c < 4; ++c) {
+      gsurf[(int64_t)small * ELEM + small_face * 16 + 4 * c + k] = gs[c];
+      s_gui[lm][half][c][k] = gi[c];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    for (int cc = 0; cc < 2; ++cc) {
+      const int c = 2 * half + cc;
+      double g = 0.0;
+      for (int l = 0; l < NN; ++l) {
+        g = fma(ops.p_lo[l][k], s_gui[lm][0][c][l], g);
+        g = fma(ops.p_hi[l][k], s_gui[lm][1][c][l], g);
+      }
+      gsurf[(int64_t)r.x * ELEM + large_face * 16 + 4 * c + k] = g;
+    }
+  }
 }
 
 // Element kernel over the sorted list: the first n_act elements are active
@@ -960,8 +1147,8 @@ cudaError_t launch_vjp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
   if (e != cudaSuccess) return e;
   const int64_t bi = (n_if + 31) / 32, bm = (n_mort + 15) / 16;
   if (bi + bm > 0)
-    ad::k_vjp_faces<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level, method, min_member,
-                                                         two_over_len, Y, lam, logt, gsurf);
+    ad::k_vjp_faces_rev<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level, method,
+                                                             min_member, two_over_len, Y, lam, logt, gsurf);
   if (n_all > 0)
     ad::k_vjp_volume<<<(unsigned)((n_all + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS), 64, 0, st>>>(ops, n_all, n_act, elems, level, two_over_len, Y,
                                                                   lam, gsurf, logt, g);
