@@ -363,6 +363,23 @@ __device__ __forceinline__ void surface_flux(const T uL[4], const T uR[4], int d
 __device__ __forceinline__ int face_node(int face, int k) {
   return face == 0 ? 4 * k : face == 1 ? 4 * k + 3 : face == 2 ? k : 12 + k;
 }
+
+// stage state at one node: given, or U + dt (alpha K1 + beta Kp) with the element's member coefficients
+template <int YS>
+__device__ __forceinline__ void stage_y(const StageArgs& sa, const int32_t* method, int64_t e, int node, double y[4]) {
+  const int64_t base = e * ELEM + node;
+  if (YS == Y_GIVEN) {
+    for (int v = 0; v < 4; ++v) y[v] = sa.Y[base + v * NODES];
+  } else {
+    const StageCoef c = sa.coef ? sa.coef[method[e]] : StageCoef{0.0, 0.0};
+    const double dt = sa.dt[sa.member ? sa.member[e] : 0];
+    for (int v = 0; v < 4; ++v) y[v] = sa.U[base + v * NODES];
+    if (c.alpha != 0.0)
+      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.alpha, sa.K1[base + v * NODES], y[v]);
+    if (c.beta != 0.0)
+      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, sa.Kp[base + v * NODES], y[v]);
+  }
+}
 __device__ __forceinline__ int pair_slot(int a, int b) { return (a * (7 - a)) / 2 + b - a - 1; }
 
 // ===========================================================================
@@ -885,11 +902,12 @@ __device__ __forceinline__ void surface_flux_rev(const double uL[4], const doubl
 
 // Faces: the adjoint weight of every face-node flux (its lifting coefficients times
 // lam on both sides) through the hand-written reverse sweeps.
+template <int YS>
 __global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
                                                         int64_t n_mort, const int4* __restrict__ morts,
                                                         int64_t if_blocks, const int32_t* __restrict__ level,
                                                         const int32_t* __restrict__ method, int min_member,
-                                                        double two_over_len, const double* __restrict__ Y,
+                                                        double two_over_len, StageArgs sa,
                                                         const double* __restrict__ lam,
                                                         const double* __restrict__ logt, double* __restrict__ gsurf) {
   __shared__ double s_gphi[16][4][NN];
@@ -897,9 +915,7 @@ __global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, co
   const double* ic = logt;
   const double* lc = logt + LOG_TABLE_SIZE;
   const double iw = ops.inv_w0;
-  auto load = [&](int64_t e, int node, double u[4]) {
-    for (int v = 0; v < 4; ++v) u[v] = Y[e * ELEM + v * NODES + node];
-  };
+  auto load = [&](int64_t e, int node, double u[4]) { stage_y<YS>(sa, method, e, node, u); };
   if (blockIdx.x < if_blocks) {
     const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
     const int k = threadIdx.x & 3;
@@ -941,7 +957,9 @@ __global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, co
     double ui[4] = {0.0, 0.0, 0.0, 0.0}, us[4], gi[4], gs[4];
     for (int l = 0; l < NN; ++l) {
       const double w = half ? ops.p_hi[k][l] : ops.p_lo[k][l];
-      for (int v = 0; v < 4; ++v) ui[v] = fma(w, Y[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, l)], ui[v]);
+      double ul[4];
+      load(r.x, face_node(large_face, l), ul);
+      for (int v = 0; v < 4; ++v) ui[v] = fma(w, ul[v], ui[v]);
     }
     load(small, face_node(small_face, k), us);
     const double cs = lift_coef(small_face, two_over_len, level[small], iw);
@@ -980,10 +998,12 @@ __global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, co
 // not active contribute nothing).
 constexpr int VJP_ELEMS = 4;
 
+template <int YS>
 __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64_t n_act,
                                                     const int32_t* __restrict__ elems,
-                                                    const int32_t* __restrict__ level, double two_over_len,
-                                                    const double* __restrict__ Y, const double* __restrict__ lam,
+                                                    const int32_t* __restrict__ level,
+                                                    const int32_t* __restrict__ method, double two_over_len,
+                                                    StageArgs sa, const double* __restrict__ lam,
                                                     const double* __restrict__ gsurf,
                                                     const double* __restrict__ logt, double* __restrict__ g) {
   __shared__ NodeQ<double> s_q[VJP_ELEMS][NODES];
@@ -997,8 +1017,8 @@ __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64
   const bool valid = slot < n_all;
   const bool active = slot < n_act;
   const int64_t e = valid ? elems[slot] : 0;
-  double y[4];
-  for (int v = 0; v < 4; ++v) y[v] = active ? Y[e * ELEM + v * NODES + t] : (v == 0 ? 1.0 : v == 3 ? 2.5 : 0.0);
+  double y[4] = {1.0, 0.0, 0.0, 2.5};
+  if (active) stage_y<YS>(sa, method, e, t, y);
   const double scale = valid ? -ldexp(two_over_len, level[e]) : 0.0;
   for (int v = 0; v < 4; ++v) s_mu[le][v][t] = active ? scale * lam[e * ELEM + v * NODES + t] : 0.0;
   const NodeQ<double> myq = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
@@ -1068,10 +1088,11 @@ __global__ void k_combine(int64_t n, const int32_t* __restrict__ method, const S
   }
 }
 
-// adjoint of the stage combination: lamU += g; lamK1 += dt alpha g; lamKp += dt beta g (lamKp may alias lamK1)
+// adjoint of the stage combination: lamU += g; lamK1 += dt alpha g; lamKp (+)= dt beta g
+// (lamKp may alias lamK1; assign_p: lamKp receives its first contribution, no prior zeroing)
 __global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ method, const StageCoef* __restrict__ coef,
                             double dt, const double* __restrict__ g, double* __restrict__ lamU,
-                            double* __restrict__ lamK1, double* lamKp) {
+                            double* __restrict__ lamK1, double* lamKp, int assign_p) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = q / ELEM;
     const double gq = g[q];
@@ -1082,7 +1103,7 @@ __global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ method, const
         lamK1[q] += dt * (c.alpha + c.beta) * gq;
       } else {
         lamK1[q] += dt * c.alpha * gq;
-        lamKp[q] += dt * c.beta * gq;
+        lamKp[q] = assign_p ? dt * c.beta * gq : lamKp[q] + dt * c.beta * gq;
       }
     }
   }
@@ -1115,8 +1136,8 @@ cudaError_t launch_combine(cudaStream_t st, int64_t n, const int32_t* method, co
 }
 
 cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
-                             const double* g, double* lamU, double* lamK1, double* lamKp) {
-  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, method, coef, dt, g, lamU, lamK1, lamKp);
+                             const double* g, double* lamU, double* lamK1, double* lamKp, int assign_p) {
+  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, method, coef, dt, g, lamU, lamK1, lamKp, assign_p);
   return cudaGetLastError();
 }
 
@@ -1139,19 +1160,31 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
   return cudaGetLastError();
 }
 
-cudaError_t launch_vjp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+cudaError_t launch_vjp(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                        const int4* morts, int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level,
-                       const int32_t* method, int min_member, double two_over_len, const double* Y,
+                       const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
                        const double* lam, const double* logt, double* gsurf, double* g) {
   cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int64_t bi = (n_if + 31) / 32, bm = (n_mort + 15) / 16;
-  if (bi + bm > 0)
-    ad::k_vjp_faces_rev<<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level, method,
-                                                             min_member, two_over_len, Y, lam, logt, gsurf);
-  if (n_all > 0)
-    ad::k_vjp_volume<<<(unsigned)((n_all + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS), 64, 0, st>>>(ops, n_all, n_act, elems, level, two_over_len, Y,
-                                                                  lam, gsurf, logt, g);
+  const unsigned bv = (unsigned)((n_all + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS);
+  if (ysrc == Y_GIVEN) {
+    if (bi + bm > 0)
+      ad::k_vjp_faces_rev<Y_GIVEN><<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level,
+                                                                        method, min_member, two_over_len, sa, lam,
+                                                                        logt, gsurf);
+    if (n_all > 0)
+      ad::k_vjp_volume<Y_GIVEN><<<bv, 64, 0, st>>>(ops, n_all, n_act, elems, level, method, two_over_len, sa, lam,
+                                                     gsurf, logt, g);
+  } else {
+    if (bi + bm > 0)
+      ad::k_vjp_faces_rev<Y_COMBINE><<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level,
+                                                                          method, min_member, two_over_len, sa, lam,
+                                                                          logt, gsurf);
+    if (n_all > 0)
+      ad::k_vjp_volume<Y_COMBINE><<<bv, 64, 0, st>>>(ops, n_all, n_act, elems, level, method, two_over_len, sa, lam,
+                                                       gsurf, logt, g);
+  }
   return cudaGetLastError();
 }
 

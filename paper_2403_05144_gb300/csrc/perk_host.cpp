@@ -1439,9 +1439,12 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
   const int64_t ni = stage < 0 ? ctx->n_if : ctx->act_if[stage];
   const int64_t nm = stage < 0 ? ctx->n_mort : ctx->act_mort[stage];
   PERK_CUDA(ctx, ctx->d_surf_d.ensure((size_t)ctx->n_elem * ELEM));
-  PERK_CUDA(ctx, launch_vjp(ctx->stream, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p, ctx->n_elem, na,
-                            ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, min_active_member(ctx, stage),
-                            2.0 / ctx->length, d_Y, d_lam, ctx->d_logtab.p, ctx->d_surf_d.p, d_g));
+  StageArgs sa{};
+  sa.Y = d_Y;
+  PERK_CUDA(ctx, launch_vjp(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
+                            ctx->n_elem, na, ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p,
+                            min_active_member(ctx, stage), 2.0 / ctx->length, sa, d_lam, ctx->d_logtab.p,
+                            ctx->d_surf_d.p, d_g));
   return PERK_OK;
 }
 
@@ -1501,27 +1504,31 @@ perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const do
     if (S - 1 == 1 && bp != 0.0) return fail(ctx, PERK_E_INVALID_ARG, "third order needs S >= 3");
   }
   for (int i = S - 1; i >= 0; --i) {
-    // adjoint of K_i is in lam_cur (for i == 0 it is the accumulated lamK1)
+    // adjoint of K_i is in lam_cur (for i == 0 it is the accumulated lamK1); the stage state
+    // Y_i = U_n + dt (alpha K_1 + beta K_{i-1}) is formed inside the VJP kernels
     double* lam_i = (i == 0) ? lamK1 : lam_cur;
     const StageCoef* coef = (i == 0) ? nullptr : ctx->d_coef.p + (size_t)i * MAX_R;
-    PERK_CUDA(ctx, launch_combine(st, ctx->n_elem, ctx->d_method.p, coef, dt, d_Un, K,
-                                  K + (size_t)(i > 0 ? i - 1 : 0) * nd, ctx->d_Ystage.p));
-    PERK_CUDA(ctx, launch_vjp(st, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p,
-                              ctx->n_elem, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p,
-                              min_active_member(ctx, i), 2.0 / ctx->length, ctx->d_Ystage.p, lam_i, ctx->d_logtab.p,
-                              ctx->d_surf_d.p, ctx->d_g.p));
+    StageArgs sa{};
+    sa.U = d_Un;
+    sa.K1 = K;
+    sa.Kp = K + (size_t)(i > 0 ? i - 1 : 0) * nd;
+    sa.coef = coef;
+    sa.dt = ctx->d_dt.p;
+    PERK_CUDA(ctx, launch_vjp(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
+                              ctx->d_mort_sorted.p, ctx->n_elem, ctx->act_el[i], ctx->d_elem_sorted.p,
+                              ctx->d_level.p, ctx->d_method.p, min_active_member(ctx, i), 2.0 / ctx->length, sa,
+                              lam_i, ctx->d_logtab.p, ctx->d_surf_d.p, ctx->d_g.p));
     if (i == 0) {
       PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, nullptr, dt, ctx->d_g.p, d_lam_n, nullptr,
-                                      nullptr));
+                                      nullptr, 0));
     } else {
-      // contributions to K_{i-1}: into lamK1 when i - 1 == 0, else into lam_prev (zero unless seeded)
+      // contributions to K_{i-1}: into lamK1 when i - 1 == 0; else into lam_prev, which holds the
+      // final-update seed only for K_{S-1} (i == S-1) and is otherwise assigned here
       double* target = (i - 1 == 0) ? lamK1 : lam_prev;
-      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, coef, dt, ctx->d_g.p, d_lam_n, lamK1, target));
-      if (i - 1 > 0) {
-        std::swap(lam_cur, lam_prev);   // lam_cur <- adjoint of K_{i-1}
-        // the next stage's lam_prev must start at zero (only the seed may pre-fill K_{S-1})
-        PERK_CUDA(ctx, cudaMemsetAsync(lam_prev, 0, nd * sizeof(double), st));
-      }
+      const int assign = (i - 1 == 0 || i == S - 1) ? 0 : 1;
+      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, coef, dt, ctx->d_g.p, d_lam_n, lamK1, target,
+                                      assign));
+      if (i - 1 > 0) std::swap(lam_cur, lam_prev);   // lam_cur <- adjoint of K_{i-1}
     }
   }
   return PERK_OK;

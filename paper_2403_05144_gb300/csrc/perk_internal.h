@@ -98,14 +98,14 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
                        const int4* morts, int64_t n_el, const int32_t* elems, const int32_t* level,
                        double two_over_len, const double* Y, const double* V, const double* logt, double* surf,
                        double* surf_d, double* K, double* Kd);
-cudaError_t launch_vjp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+cudaError_t launch_vjp(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                        const int4* morts, int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level,
-                       const int32_t* method, int min_member, double two_over_len, const double* Y,
+                       const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
                        const double* lam, const double* logt, double* gsurf, double* g);
 cudaError_t launch_combine(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
                            const double* U, const double* K1, const double* Kp, double* Y);
 cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
-                             const double* g, double* lamU, double* lamK1, double* lamKp);
+                             const double* g, double* lamU, double* lamK1, double* lamKp, int assign_p);
 cudaError_t launch_adj_seed(cudaStream_t st, int64_t n, double dt, double b1, double bp, double bs, const double* lam,
                             double* lamU, double* lamK1, double* lamKp, double* lamKs);
 
