@@ -1010,13 +1010,28 @@ __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64
   __shared__ double s_mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
   __shared__ double s_g[VJP_ELEMS][48][2 * NQ];       // per pair: adjoints of its two node records
   __shared__ double s_log[2 * LOG_TABLE_SIZE];
-  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
-  __syncthreads();
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
   const int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le;
   const bool valid = slot < n_all;
   const bool active = slot < n_act;
   const int64_t e = valid ? elems[slot] : 0;
+  if ((int64_t)blockIdx.x * VJP_ELEMS >= n_act) {
+    // a block of inactive elements (the sorted list puts the active ones first): their K is
+    // not part of this stage, only the face adjoints of their traces are gathered
+    if (!valid) return;
+    const double* gs = gsurf + e * ELEM;
+    for (int c = 0; c < 4; ++c) {
+      double o = 0.0;
+      if (i == 0) o += gs[0 * 16 + 4 * c + j];
+      if (i == 3) o += gs[1 * 16 + 4 * c + j];
+      if (j == 0) o += gs[2 * 16 + 4 * c + i];
+      if (j == 3) o += gs[3 * 16 + 4 * c + i];
+      g[e * ELEM + c * NODES + t] = o;
+    }
+    return;
+  }
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
+  __syncthreads();
   double y[4] = {1.0, 0.0, 0.0, 2.5};
   if (active) stage_y<YS>(sa, method, e, t, y);
   const double scale = valid ? -ldexp(two_over_len, level[e]) : 0.0;
