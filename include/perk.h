@@ -229,6 +229,20 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
  * forward step and this call.  Asynchronous. */
 perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n);
 
+/* The same adjoint split in two, for callers that keep the stages of the steps
+ * they are going to reverse (the recomputation of a checkpoint window).
+ * perk_step_store: one step d_U <- U_{n+1} exactly as perk_step computes it
+ * (same kernels, same admissibility check and flag), additionally writing the
+ * S stage derivatives to d_K (caller-owned device memory, S x n_elem x 64
+ * doubles, stage i at d_K + i * n_elem * 64, U layout each).
+ * perk_step_vjp_stored: the reverse sweep of perk_step_vjp from those stored
+ * stages: d_Un is the state the stages were computed from (not the updated
+ * one), d_K is read only.  The mesh and dt must be those of the store call.
+ * Euler single-member contexts; INVALID_ARG otherwise.  Asynchronous. */
+perk_status perk_step_store(perk_ctx* ctx, double* d_U, double dt, double* d_K);
+perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, const double* d_K,
+                                 const double* d_lam_np1, double* d_lam_n);
+
 /* Adaptive mesh refinement (Sec. 7: the AMR callback every N_AMR steps, after
  * which the partition is re-assigned, Sec. 6.2).  Indicator: the density
  * gradient eta_e = h_e max_nodes |grad rho| / mean_e(rho) (dimensionless).

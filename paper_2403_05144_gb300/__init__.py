@@ -256,12 +256,34 @@ class PerkSolver:
         self._call(self.lib.perk_rhs_vjp, int(stage), C.c_void_p(_ptr(Y)), C.c_void_p(_ptr(lam)), C.c_void_p(_ptr(g)))
         return g
 
-    def step_vjp(self, Un, dt: float, lam_np1, out=None):
+    def step_vjp(self, Un, dt: float, lam_np1, out=None, stages=None):
+        """lam_n = (dU_{n+1}/dU_n)^T lam_np1; with ``stages`` (from ``step_store`` on Un) the
+        forward stages are not recomputed."""
         Un, lam_np1 = self._state(Un), self._state(lam_np1)
         lam_n = self.empty_state() if out is None else self._state(out)
-        self._call(self.lib.perk_step_vjp, C.c_void_p(_ptr(Un)), C.c_double(dt), C.c_void_p(_ptr(lam_np1)),
-                   C.c_void_p(_ptr(lam_n)))
+        if stages is None:
+            self._call(self.lib.perk_step_vjp, C.c_void_p(_ptr(Un)), C.c_double(dt), C.c_void_p(_ptr(lam_np1)),
+                       C.c_void_p(_ptr(lam_n)))
+        else:
+            self._call(self.lib.perk_step_vjp_stored, C.c_void_p(_ptr(Un)), C.c_double(dt),
+                       C.c_void_p(_ptr(self._stages(stages))), C.c_void_p(_ptr(lam_np1)), C.c_void_p(_ptr(lam_n)))
         return lam_n
+
+    def step_store(self, U, dt: float, stages=None):
+        """One step of U in place (as ``step``) that also returns its S stages [S, n_elem, 4, 4, 4]."""
+        U = self._state(U)
+        if stages is None:
+            stages = self.torch.empty((self.S, self.n_elem, 4, 4, 4), dtype=self.torch.float64, device="cuda")
+        self._call(self.lib.perk_step_store, C.c_void_p(_ptr(U)), C.c_double(dt), C.c_void_p(_ptr(self._stages(stages))))
+        return stages
+
+    def _stages(self, K):
+        torch = self.torch
+        if not (K.is_cuda and K.dtype == torch.float64 and K.is_contiguous()):
+            raise ValueError("expected a contiguous float64 CUDA tensor of stages")
+        if tuple(K.shape) != (self.S, self.n_elem, 4, 4, 4):
+            raise ValueError(f"expected stages of shape {(self.S, self.n_elem, 4, 4, 4)}, got {tuple(K.shape)}")
+        return K
 
     # ------------------------------------------------------------------ AMR
     def amr_indicator(self, U):

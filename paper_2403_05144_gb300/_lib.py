@@ -77,6 +77,8 @@ SIGNATURES = [
     ("perk_rhs_jvp", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk_rhs_vjp", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk_step_vjp", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    ("perk_step_store", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    ("perk_step_vjp_stored", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk_amr_indicator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(PerkAmrParams), C.POINTER(C.c_int32), C.c_void_p,
                                   C.POINTER(C.c_int64)]),

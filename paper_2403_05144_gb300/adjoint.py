@@ -6,8 +6,8 @@
 ``gradient`` differentiates a functional of the end state over many steps on a
 frozen mesh with step checkpointing: the state is stored every
 ``checkpoint_every`` steps and each window's steps are recomputed from its
-checkpoint during the reverse sweep, so memory holds one window of states plus
-the stages of the step being reversed.
+checkpoint during the reverse sweep, keeping their stages, so memory holds one
+window of states and stages.
 """
 
 from __future__ import annotations
@@ -46,8 +46,13 @@ def kinetic_energy(U: torch.Tensor, h: torch.Tensor, w: torch.Tensor) -> torch.T
 
 
 def gradient(solver: PerkSolver, U0: torch.Tensor, dt: float, n_steps: int,
-             functional: Callable[[torch.Tensor], torch.Tensor], checkpoint_every: int = 20):
-    """(J(U_N), dJ/dU_0) for N = n_steps P-ERK steps from U0 on the solver's (frozen) mesh."""
+             functional: Callable[[torch.Tensor], torch.Tensor], checkpoint_every: int = 20,
+             store_stages: bool = True):
+    """(J(U_N), dJ/dU_0) for N = n_steps P-ERK steps from U0 on the solver's (frozen) mesh.
+
+    With ``store_stages`` the recomputation of a window keeps every step's stages
+    (checkpoint_every x S states) and the reverse sweep reads them; otherwise each
+    reverse step recomputes its own stages."""
     checkpoints = {}
     U = U0.detach().clone()
     for n in range(n_steps):
@@ -58,15 +63,24 @@ def gradient(solver: PerkSolver, U0: torch.Tensor, dt: float, n_steps: int,
     J = functional(UN)
     (lam,) = torch.autograd.grad(J, UN)
     lam = lam.contiguous()
+    lam_next = torch.empty_like(lam)
     starts = sorted(checkpoints)
+    buf = None
+    if store_stages:
+        buf = torch.empty((min(checkpoint_every, n_steps), solver.S) + tuple(U0.shape), dtype=U0.dtype,
+                          device=U0.device)
     for w_start in reversed(starts):
         w_end = min(w_start + checkpoint_every, n_steps)
-        states = [checkpoints[w_start]]
         Uw = checkpoints[w_start].clone()
-        for _ in range(w_start, w_end - 1):
-            solver.step(Uw, dt)
+        states = []
+        for k in range(w_end - w_start):
             states.append(Uw.clone())
-        for Un in reversed(states):
-            lam = solver.step_vjp(Un, dt, lam)
+            if store_stages:
+                solver.step_store(Uw, dt, stages=buf[k])
+            elif k < w_end - w_start - 1:
+                solver.step(Uw, dt)
+        for k in reversed(range(len(states))):
+            solver.step_vjp(states[k], dt, lam, out=lam_next, stages=buf[k] if store_stages else None)
+            lam, lam_next = lam_next, lam
     solver.check()
     return J.detach(), lam

@@ -902,22 +902,25 @@ __device__ __forceinline__ void surface_flux_rev(const double uL[4], const doubl
 
 // Faces: the adjoint weight of every face-node flux (its lifting coefficients times
 // lam on both sides) through the hand-written reverse sweeps.
+// face reverse blocks: 4 threads per interface, 8 per mortar
+constexpr int FREV_THREADS = 64, FREV_IF = FREV_THREADS / 4, FREV_MORT = FREV_THREADS / 8;
+
 template <int YS>
-__global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+__global__ void __launch_bounds__(FREV_THREADS) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
                                                         int64_t n_mort, const int4* __restrict__ morts,
                                                         int64_t if_blocks, const int32_t* __restrict__ level,
                                                         const int32_t* __restrict__ method, int min_member,
                                                         double two_over_len, StageArgs sa,
                                                         const double* __restrict__ lam,
                                                         const double* __restrict__ logt, double* __restrict__ gsurf) {
-  __shared__ double s_gphi[16][4][NN];
-  __shared__ double s_gui[16][2][4][NN];
+  __shared__ double s_gphi[FREV_MORT][4][NN];
+  __shared__ double s_gui[FREV_MORT][2][4][NN];
   const double* ic = logt;
   const double* lc = logt + LOG_TABLE_SIZE;
   const double iw = ops.inv_w0;
   auto load = [&](int64_t e, int node, double u[4]) { stage_y<YS>(sa, method, e, node, u); };
   if (blockIdx.x < if_blocks) {
-    const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
+    const int64_t idx = (int64_t)blockIdx.x * FREV_IF + (threadIdx.x >> 2);
     const int k = threadIdx.x & 3;
     if (idx >= n_if) return;
     const int4 r = ifs[idx];
@@ -940,7 +943,7 @@ __global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, co
     return;
   }
   const int lm = threadIdx.x >> 3;
-  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * 16 + lm;
+  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * FREV_MORT + lm;
   const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
   const bool valid = idx < n_mort;
   int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
@@ -992,75 +995,57 @@ __global__ void __launch_bounds__(128) k_vjp_faces_rev(Ops ops, int64_t n_if, co
   }
 }
 
-// Element kernel over the sorted list: the first n_act elements are active
-// (volume adjoint by the reverse sweep above); every element adds the face
-// adjoints of its four faces from gsurf (zeroed beforehand, so faces that were
-// not active contribute nothing).
+// Element kernel over the active prefix of the sorted list (the volume adjoint
+// by the reverse sweep above); g receives the volume part only.  Each group of
+// 16 threads (one per node) strides over the active elements, so that a grid
+// sized to the resident capacity keeps every SM busy to the end.  The face
+// adjoints (gsurf) are gathered afterwards by face_gather.
 constexpr int VJP_ELEMS = 4;
 
 template <int YS>
-__global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64_t n_act,
-                                                    const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_act, const int32_t* __restrict__ elems,
                                                     const int32_t* __restrict__ level,
                                                     const int32_t* __restrict__ method, double two_over_len,
                                                     StageArgs sa, const double* __restrict__ lam,
-                                                    const double* __restrict__ gsurf,
                                                     const double* __restrict__ logt, double* __restrict__ g) {
   __shared__ NodeQ<double> s_q[VJP_ELEMS][NODES];
   __shared__ double s_mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
   __shared__ double s_g[VJP_ELEMS][48][2 * NQ];       // per pair: adjoints of its two node records
   __shared__ double s_log[2 * LOG_TABLE_SIZE];
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
-  const int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le;
-  const bool valid = slot < n_all;
-  const bool active = slot < n_act;
-  const int64_t e = valid ? elems[slot] : 0;
-  if ((int64_t)blockIdx.x * VJP_ELEMS >= n_act) {
-    // a block of inactive elements (the sorted list puts the active ones first): their K is
-    // not part of this stage, only the face adjoints of their traces are gathered
-    if (!valid) return;
-    const double* gs = gsurf + e * ELEM;
-    for (int c = 0; c < 4; ++c) {
-      double o = 0.0;
-      if (i == 0) o += gs[0 * 16 + 4 * c + j];
-      if (i == 3) o += gs[1 * 16 + 4 * c + j];
-      if (j == 0) o += gs[2 * 16 + 4 * c + i];
-      if (j == 3) o += gs[3 * 16 + 4 * c + i];
-      g[e * ELEM + c * NODES + t] = o;
-    }
-    return;
-  }
+  const unsigned gmask = 0xFFFFu << (threadIdx.x & 16);   // the 16 lanes of this group
   for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
   __syncthreads();
-  double y[4] = {1.0, 0.0, 0.0, 2.5};
-  if (active) stage_y<YS>(sa, method, e, t, y);
-  const double scale = valid ? -ldexp(two_over_len, level[e]) : 0.0;
-  for (int v = 0; v < 4; ++v) s_mu[le][v][t] = active ? scale * lam[e * ELEM + v * NODES + t] : 0.0;
-  const NodeQ<double> myq = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
-  s_q[le][t] = myq;
-  __syncwarp();
-  for (int kk = 0; kk < 3; ++kk) {
-    const int p = t + 16 * kk;
-    const int dir = p >= 24;
-    const int q = dir ? p - 24 : p;
-    const int line = q / 6, qq = q - 6 * line;
-    const int a = (qq >= 3) + (qq >= 5);
-    const int b = qq + 1 - (a * (5 - a)) / 2;
-    const int na = dir ? a * 4 + line : line * 4 + a;
-    const int nb = dir ? b * 4 + line : line * 4 + b;
-    double gf[4], gA[NQ], gB[NQ];
-    for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[a][b] * s_mu[le][v][na] + ops.dsplit[b][a] * s_mu[le][v][nb];
-    for (int m = 0; m < NQ; ++m) gA[m] = gB[m] = 0.0;
-    ec_flux_rev(s_q[le][na], s_q[le][nb], dir, ops.inv_gm1, gf, gA, gB);
-    for (int m = 0; m < NQ; ++m) {
-      s_g[le][p][m] = gA[m];
-      s_g[le][p][NQ + m] = gB[m];
+  const int64_t stride = (int64_t)gridDim.x * VJP_ELEMS;
+  for (int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le; slot < n_act; slot += stride) {
+    const int64_t e = elems[slot];
+    double y[4];
+    stage_y<YS>(sa, method, e, t, y);
+    const double scale = -ldexp(two_over_len, level[e]);
+    __syncwarp(gmask);   // the previous element's shared records are consumed
+    for (int v = 0; v < 4; ++v) s_mu[le][v][t] = scale * lam[e * ELEM + v * NODES + t];
+    const NodeQ<double> myq = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
+    s_q[le][t] = myq;
+    __syncwarp(gmask);
+    for (int kk = 0; kk < 3; ++kk) {
+      const int p = t + 16 * kk;
+      const int dir = p >= 24;
+      const int q = dir ? p - 24 : p;
+      const int line = q / 6, qq = q - 6 * line;
+      const int a = (qq >= 3) + (qq >= 5);
+      const int b = qq + 1 - (a * (5 - a)) / 2;
+      const int na = dir ? a * 4 + line : line * 4 + a;
+      const int nb = dir ? b * 4 + line : line * 4 + b;
+      double gf[4], gA[NQ], gB[NQ];
+      for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[a][b] * s_mu[le][v][na] + ops.dsplit[b][a] * s_mu[le][v][nb];
+      for (int m = 0; m < NQ; ++m) gA[m] = gB[m] = 0.0;
+      ec_flux_rev(s_q[le][na], s_q[le][nb], dir, ops.inv_gm1, gf, gA, gB);
+      for (int m = 0; m < NQ; ++m) {
+        s_g[le][p][m] = gA[m];
+        s_g[le][p][NQ + m] = gB[m];
+      }
     }
-  }
-  __syncwarp();
-  if (!valid) return;
-  double out[4] = {0.0, 0.0, 0.0, 0.0};
-  if (active) {
+    __syncwarp(gmask);
     double gq[NQ];
     for (int m = 0; m < NQ; ++m) gq[m] = 0.0;
     for (int mm = 0; mm < 4; ++mm) {
@@ -1075,45 +1060,51 @@ __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_all, int64
         for (int m = 0; m < NQ; ++m) gq[m] += s_g[le][p][side + m];
       }
     }
+    double out[4];
     node_q_rev(y, myq, ops.gm1, gq, out);
+    for (int c = 0; c < 4; ++c) g[e * ELEM + c * NODES + t] = out[c];
   }
-  const double* gs = gsurf + e * ELEM;
-  for (int c = 0; c < 4; ++c) {
-    if (i == 0) out[c] += gs[0 * 16 + 4 * c + j];
-    if (i == 3) out[c] += gs[1 * 16 + 4 * c + j];
-    if (j == 0) out[c] += gs[2 * 16 + 4 * c + i];
-    if (j == 3) out[c] += gs[3 * 16 + 4 * c + i];
-  }
-  for (int c = 0; c < 4; ++c) g[e * ELEM + c * NODES + t] = out[c];
 }
 
-// Y = U + dt (alpha K1 + beta Kp) with the element's member coefficients (stage > 0), Y = U (stage 0)
-__global__ void k_combine(int64_t n, const int32_t* __restrict__ method, const StageCoef* __restrict__ coef,
-                          double dt, const double* __restrict__ U, const double* __restrict__ K1,
-                          const double* __restrict__ Kp, double* __restrict__ Y) {
+// adjoint of the traces of element e at node t (= 4 j + i), variable c: the
+// sum over the element faces through that node of the face records in gsurf
+__device__ __forceinline__ double face_gather(const double* __restrict__ gs, int c, int t) {
+  const int i = t & 3, j = t >> 2;
+  double o = 0.0;
+  if (i == 0) o += gs[0 * 16 + 4 * c + j];
+  if (i == 3) o += gs[1 * 16 + 4 * c + j];
+  if (j == 0) o += gs[2 * 16 + 4 * c + i];
+  if (j == 3) o += gs[3 * 16 + 4 * c + i];
+  return o;
+}
+
+// g = (volume part if the element is active, else 0) + its face adjoints:
+// the complete J(Y)^T lam of one partitioned RHS evaluation
+__global__ void k_vjp_gather(int64_t n, const int32_t* __restrict__ method, int min_member,
+                             const double* __restrict__ gsurf, double* __restrict__ g) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = q / ELEM;
-    double y = U[q];
-    if (coef) {
-      const StageCoef c = coef[method[e]];
-      if (c.alpha != 0.0) y = fma(dt * c.alpha, K1[q], y);
-      if (c.beta != 0.0) y = fma(dt * c.beta, Kp[q], y);
-    }
-    Y[q] = y;
+    const int r = (int)(q - e * ELEM);
+    const double vol = method[e] >= min_member ? g[q] : 0.0;
+    g[q] = vol + face_gather(gsurf + e * ELEM, r >> 4, r & 15);
   }
 }
 
-// adjoint of the stage combination: lamU += g; lamK1 += dt alpha g; lamKp (+)= dt beta g
+// adjoint of the stage combination, with gq = J(Y_i)^T lam_i formed as in
+// k_vjp_gather: lamU += gq; lamK1 += dt alpha gq; lamKp (+)= dt beta gq
 // (lamKp may alias lamK1; assign_p: lamKp receives its first contribution, no prior zeroing)
-__global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ method, const StageCoef* __restrict__ coef,
-                            double dt, const double* __restrict__ g, double* __restrict__ lamU,
+__global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ method, int min_member,
+                            const StageCoef* __restrict__ coef, double dt, const double* __restrict__ g,
+                            const double* __restrict__ gsurf, double* __restrict__ lamU,
                             double* __restrict__ lamK1, double* lamKp, int assign_p) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = q / ELEM;
-    const double gq = g[q];
+    const int r = (int)(q - e * ELEM);
+    const int m = method[e];
+    const double gq = (m >= min_member ? g[q] : 0.0) + face_gather(gsurf + e * ELEM, r >> 4, r & 15);
     lamU[q] += gq;
     if (coef) {
-      const StageCoef c = coef[method[e]];
+      const StageCoef c = coef[m];
       if (lamKp == lamK1) {
         lamK1[q] += dt * (c.alpha + c.beta) * gq;
       } else {
@@ -1144,15 +1135,11 @@ static unsigned ew_blocks(int64_t n) {
   return (unsigned)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
 }
 
-cudaError_t launch_combine(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
-                           const double* U, const double* K1, const double* Kp, double* Y) {
-  ad::k_combine<<<ew_blocks(n), 256, 0, st>>>(n, method, coef, dt, U, K1, Kp, Y);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, const StageCoef* coef, double dt,
-                             const double* g, double* lamU, double* lamK1, double* lamKp, int assign_p) {
-  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, method, coef, dt, g, lamU, lamK1, lamKp, assign_p);
+cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const StageCoef* coef,
+                             double dt, const double* g, const double* gsurf, double* lamU, double* lamK1,
+                             double* lamKp, int assign_p) {
+  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, method, min_member, coef, dt, g, gsurf, lamU, lamK1, lamKp,
+                                                assign_p);
   return cudaGetLastError();
 }
 
@@ -1175,31 +1162,55 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
   return cudaGetLastError();
 }
 
-cudaError_t launch_vjp(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
-                       const int4* morts, int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level,
-                       const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
-                       const double* lam, const double* logt, double* gsurf, double* g) {
+cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs,
+                             int64_t n_mort, const int4* morts, int64_t n_all, const int32_t* level,
+                             const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
+                             const double* lam, const double* logt, double* gsurf) {
   cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  const int64_t bi = (n_if + 31) / 32, bm = (n_mort + 15) / 16;
-  const unsigned bv = (unsigned)((n_all + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS);
-  if (ysrc == Y_GIVEN) {
-    if (bi + bm > 0)
-      ad::k_vjp_faces_rev<Y_GIVEN><<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level,
-                                                                        method, min_member, two_over_len, sa, lam,
-                                                                        logt, gsurf);
-    if (n_all > 0)
-      ad::k_vjp_volume<Y_GIVEN><<<bv, 64, 0, st>>>(ops, n_all, n_act, elems, level, method, two_over_len, sa, lam,
-                                                     gsurf, logt, g);
-  } else {
-    if (bi + bm > 0)
-      ad::k_vjp_faces_rev<Y_COMBINE><<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, level,
-                                                                          method, min_member, two_over_len, sa, lam,
-                                                                          logt, gsurf);
-    if (n_all > 0)
-      ad::k_vjp_volume<Y_COMBINE><<<bv, 64, 0, st>>>(ops, n_all, n_act, elems, level, method, two_over_len, sa, lam,
-                                                       gsurf, logt, g);
+  const int64_t bi = (n_if + ad::FREV_IF - 1) / ad::FREV_IF, bm = (n_mort + ad::FREV_MORT - 1) / ad::FREV_MORT;
+  if (bi + bm == 0) return cudaSuccess;
+  if (ysrc == Y_GIVEN)
+    ad::k_vjp_faces_rev<Y_GIVEN><<<(unsigned)(bi + bm), ad::FREV_THREADS, 0, st>>>(
+        ops, n_if, ifs, n_mort, morts, bi, level, method, min_member, two_over_len, sa, lam, logt, gsurf);
+  else
+    ad::k_vjp_faces_rev<Y_COMBINE><<<(unsigned)(bi + bm), ad::FREV_THREADS, 0, st>>>(
+        ops, n_if, ifs, n_mort, morts, bi, level, method, min_member, two_over_len, sa, lam, logt, gsurf);
+  return cudaGetLastError();
+}
+
+// blocks of the volume VJP: at most what is resident at once (the kernel strides)
+template <int YS>
+static unsigned vjp_volume_blocks(int64_t n_act) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ad::k_vjp_volume<YS>, 64, 0);
+    resident = sms * (per_sm > 0 ? per_sm : 1);
   }
+  const int64_t need = (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS;
+  return (unsigned)(need < resident ? need : resident);
+}
+
+cudaError_t launch_vjp_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
+                              const int32_t* level, const int32_t* method, double two_over_len,
+                              const StageArgs& sa, const double* lam, const double* logt, double* g) {
+  if (n_act <= 0) return cudaSuccess;
+  if (ysrc == Y_GIVEN)
+    ad::k_vjp_volume<Y_GIVEN><<<vjp_volume_blocks<Y_GIVEN>(n_act), 64, 0, st>>>(ops, n_act, elems, level, method,
+                                                                              two_over_len, sa, lam, logt, g);
+  else
+    ad::k_vjp_volume<Y_COMBINE><<<vjp_volume_blocks<Y_COMBINE>(n_act), 64, 0, st>>>(ops, n_act, elems, level, method,
+                                                                                  two_over_len, sa, lam, logt, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vjp_gather(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const double* gsurf,
+                              double* g) {
+  if (n <= 0) return cudaSuccess;
+  ad::k_vjp_gather<<<ew_blocks(n), 256, 0, st>>>(n, method, min_member, gsurf, g);
   return cudaGetLastError();
 }
 

@@ -244,7 +244,10 @@ struct perk_ctx {
   DevBuf<double> d_eta;
 
   // adjoint work space
-  DevBuf<double> d_surf_d, d_Kall, d_Ystage, d_g, d_lamK1, d_lamKa, d_lamKb;
+  DevBuf<double> d_surf_d, d_Kall, d_g, d_lamK1, d_lamKa, d_lamKb;
+  // second stream of the reverse sweep: face adjoints run beside the volume adjoint
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Navier-Stokes (BR1) work space
   DevBuf<double> d_wsurf, d_q, d_vsurf;
   bool viscous() const { return prob.equations == PERK_NAVIER_STOKES; }
@@ -809,6 +812,9 @@ void perk_destroy(perk_ctx* ctx) {
   if (!ctx) return;
   destroy_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   ctx->d_level.release();
   ctx->d_member.release();
   ctx->d_member_lmax.release();
@@ -835,7 +841,6 @@ void perk_destroy(perk_ctx* ctx) {
   ctx->d_eta.release();
   ctx->d_surf_d.release();
   ctx->d_Kall.release();
-  ctx->d_Ystage.release();
   ctx->d_g.release();
   ctx->d_lamK1.release();
   ctx->d_lamKa.release();
@@ -1441,51 +1446,74 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
   PERK_CUDA(ctx, ctx->d_surf_d.ensure((size_t)ctx->n_elem * ELEM));
   StageArgs sa{};
   sa.Y = d_Y;
-  PERK_CUDA(ctx, launch_vjp(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
-                            ctx->n_elem, na, ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p,
-                            min_active_member(ctx, stage), 2.0 / ctx->length, sa, d_lam, ctx->d_logtab.p,
-                            ctx->d_surf_d.p, d_g));
+  const int mm = min_active_member(ctx, stage);
+  PERK_CUDA(ctx, launch_vjp_faces(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
+                                  ctx->n_elem, ctx->d_level.p, ctx->d_method.p, mm, 2.0 / ctx->length, sa, d_lam,
+                                  ctx->d_logtab.p, ctx->d_surf_d.p));
+  PERK_CUDA(ctx, launch_vjp_volume(ctx->stream, Y_GIVEN, ctx->ops, na, ctx->d_elem_sorted.p, ctx->d_level.p,
+                                   ctx->d_method.p, 2.0 / ctx->length, sa, d_lam, ctx->d_logtab.p, d_g));
+  PERK_CUDA(ctx, launch_vjp_gather(ctx->stream, ctx->n_elem, ctx->d_method.p, mm, ctx->d_surf_d.p, d_g));
   return PERK_OK;
 }
 
-perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n) {
-  if (!ctx) return PERK_E_INVALID_ARG;
+static perk_status step_ready_adjoint(perk_ctx* ctx, const double* d_Un, double dt) {
   if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
   if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
     return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
-  if (!d_Un || !d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1 || !(dt > 0.0) || !std::isfinite(dt))
-    return fail(ctx, PERK_E_INVALID_ARG, "bad arguments (lam_n and lam_np1 must be distinct)");
-  const int S = ctx->S;
+  if (ctx->n_members != 1) return fail(ctx, PERK_E_INVALID_ARG, "the step adjoint takes single-member contexts");
+  if (!d_Un || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or dt");
+  if (ctx->order == 3 && ctx->S < 3) return fail(ctx, PERK_E_INVALID_ARG, "third order needs S >= 3");
+  return set_dts(ctx, nullptr, dt);
+}
+
+// every stage of one step from U_n, stage i stored in K + i * n_elem * 64; when d_U is given,
+// the last stage checks admissibility and the commit updates d_U (as perk_step does)
+static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, double* d_U) {
   const size_t nd = (size_t)ctx->n_elem * ELEM;
   cudaStream_t st = ctx->stream;
-  PERK_CUDA(ctx, ctx->d_Kall.ensure(nd * S));
-  PERK_CUDA(ctx, ctx->d_Ystage.ensure(nd));
-  PERK_CUDA(ctx, ctx->d_g.ensure(nd));
-  PERK_CUDA(ctx, ctx->d_lamK1.ensure(nd));
-  PERK_CUDA(ctx, ctx->d_lamKa.ensure(nd));
-  PERK_CUDA(ctx, ctx->d_lamKb.ensure(nd));
-  PERK_CUDA(ctx, ctx->d_surf_d.ensure(nd));
-  if (ctx->n_members != 1) return fail(ctx, PERK_E_INVALID_ARG, "the step adjoint takes single-member contexts");
-  {
-    perk_status s = set_dts(ctx, nullptr, dt);
-    if (s != PERK_OK) return s;
-  }
-  double* K = ctx->d_Kall.p;
-  // forward: every stage of the step, stored (stage i in K + i * nd)
-  for (int i = 0; i < S; ++i) {
+  UpdateArgs ua{};
+  ua.b1 = ctx->order == 3 ? 1.0 / 6.0 : 0.0;
+  ua.bp = ctx->order == 3 ? 1.0 / 6.0 : 0.0;
+  ua.bs = ctx->order == 3 ? 2.0 / 3.0 : 1.0;
+  ua.U = d_U;
+  ua.K1 = K;
+  ua.Kp = K + (size_t)(ctx->S > 1 ? ctx->S - 2 : 0) * nd;   // K_{S-1}
+  ua.flag = ctx->d_flag.p;
+  for (int i = 0; i < ctx->S; ++i) {
     StageArgs sa{};
     sa.U = d_Un;
     sa.K1 = K;
     sa.Kp = K + (size_t)(i > 0 ? i - 1 : 0) * nd;
     sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
     sa.dt = ctx->d_dt.p;
+    const bool check = d_U && i == ctx->S - 1;
     PERK_CUDA(ctx, launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
                                 ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     PERK_CUDA(ctx, launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                                 ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, K + (size_t)i * nd, nullptr,
-                                 ctx->d_logtab.p));
+                                 ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, K + (size_t)i * nd,
+                                 check ? &ua : nullptr, ctx->d_logtab.p));
   }
-  // reverse: seed with the final update U_{n+1} = U_n + dt (b1 K_1 + b_{S-1} K_{S-1} + b_S K_S)
+  if (d_U) PERK_CUDA(ctx, launch_commit(st, ctx->n_elem, ua, K + (size_t)(ctx->S - 1) * nd, ctx->d_dt.p, d_U));
+  return PERK_OK;
+}
+
+// the reverse sweep of one step whose stages K (from U_n) are stored
+static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt, const double* K,
+                                   const double* d_lam_np1, double* d_lam_n) {
+  const int S = ctx->S;
+  const size_t nd = (size_t)ctx->n_elem * ELEM;
+  cudaStream_t st = ctx->stream;
+  PERK_CUDA(ctx, ctx->d_g.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_lamK1.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_lamKa.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_lamKb.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_surf_d.ensure(nd));
+  if (!ctx->aux_stream) {
+    PERK_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+    PERK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    PERK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
+  // seed with the final update U_{n+1} = U_n + dt (b1 K_1 + b_{S-1} K_{S-1} + b_S K_S)
   double b1 = 0.0, bp = 0.0, bs = 1.0;
   if (ctx->order == 3) {
     b1 = 1.0 / 6.0;
@@ -1501,37 +1529,81 @@ perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const do
   } else {
     PERK_CUDA(ctx, launch_adj_seed(st, ctx->n_elem, dt, b1, bp, bs, d_lam_np1, d_lam_n, lamK1,
                                    S - 1 > 1 ? lam_prev : nullptr, lam_cur));
-    if (S - 1 == 1 && bp != 0.0) return fail(ctx, PERK_E_INVALID_ARG, "third order needs S >= 3");
   }
   for (int i = S - 1; i >= 0; --i) {
     // adjoint of K_i is in lam_cur (for i == 0 it is the accumulated lamK1); the stage state
     // Y_i = U_n + dt (alpha K_1 + beta K_{i-1}) is formed inside the VJP kernels
     double* lam_i = (i == 0) ? lamK1 : lam_cur;
     const StageCoef* coef = (i == 0) ? nullptr : ctx->d_coef.p + (size_t)i * MAX_R;
+    const int mm = min_active_member(ctx, i);
     StageArgs sa{};
     sa.U = d_Un;
     sa.K1 = K;
     sa.Kp = K + (size_t)(i > 0 ? i - 1 : 0) * nd;
     sa.coef = coef;
     sa.dt = ctx->d_dt.p;
-    PERK_CUDA(ctx, launch_vjp(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
-                              ctx->d_mort_sorted.p, ctx->n_elem, ctx->act_el[i], ctx->d_elem_sorted.p,
-                              ctx->d_level.p, ctx->d_method.p, min_active_member(ctx, i), 2.0 / ctx->length, sa,
-                              lam_i, ctx->d_logtab.p, ctx->d_surf_d.p, ctx->d_g.p));
+    // face adjoints on the second stream, beside the volume adjoint
+    PERK_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
+    PERK_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0));
+    PERK_CUDA(ctx, launch_vjp_faces(ctx->aux_stream, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p,
+                                    ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->n_elem, ctx->d_level.p,
+                                    ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p,
+                                    ctx->d_surf_d.p));
+    PERK_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux_stream));
+    PERK_CUDA(ctx, launch_vjp_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
+                                     ctx->d_method.p, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p));
+    PERK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
     if (i == 0) {
-      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, nullptr, dt, ctx->d_g.p, d_lam_n, nullptr,
-                                      nullptr, 0));
+      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, mm, nullptr, dt, ctx->d_g.p, ctx->d_surf_d.p,
+                                      d_lam_n, nullptr, nullptr, 0));
     } else {
       // contributions to K_{i-1}: into lamK1 when i - 1 == 0; else into lam_prev, which holds the
       // final-update seed only for K_{S-1} (i == S-1) and is otherwise assigned here
       double* target = (i - 1 == 0) ? lamK1 : lam_prev;
       const int assign = (i - 1 == 0 || i == S - 1) ? 0 : 1;
-      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, coef, dt, ctx->d_g.p, d_lam_n, lamK1, target,
-                                      assign));
+      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, mm, coef, dt, ctx->d_g.p, ctx->d_surf_d.p,
+                                      d_lam_n, lamK1, target, assign));
       if (i - 1 > 0) std::swap(lam_cur, lam_prev);   // lam_cur <- adjoint of K_{i-1}
     }
   }
   return PERK_OK;
+}
+
+perk_status perk_step_store(perk_ctx* ctx, double* d_U, double dt, double* d_K) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  perk_status s = step_ready_adjoint(ctx, d_U, dt);
+  if (s != PERK_OK) return s;
+  if (!d_K) return fail(ctx, PERK_E_INVALID_ARG, "null stage array");
+  s = enqueue_stages(ctx, d_U, d_K, d_U);
+  if (s != PERK_OK) return s;
+  ctx->counters.steps += 1;
+  for (int i = 0; i < ctx->S; ++i) {
+    ctx->counters.element_stage_evaluations += ctx->act_el[i];
+    ctx->counters.dof_stage_updates += ctx->act_el[i] * NODES;
+  }
+  return PERK_OK;
+}
+
+perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, const double* d_K,
+                                 const double* d_lam_np1, double* d_lam_n) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  perk_status s = step_ready_adjoint(ctx, d_Un, dt);
+  if (s != PERK_OK) return s;
+  if (!d_K || !d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1)
+    return fail(ctx, PERK_E_INVALID_ARG, "bad arguments (lam_n and lam_np1 must be distinct)");
+  return enqueue_reverse(ctx, d_Un, dt, d_K, d_lam_np1, d_lam_n);
+}
+
+perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  perk_status s = step_ready_adjoint(ctx, d_Un, dt);
+  if (s != PERK_OK) return s;
+  if (!d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1)
+    return fail(ctx, PERK_E_INVALID_ARG, "bad arguments (lam_n and lam_np1 must be distinct)");
+  PERK_CUDA(ctx, ctx->d_Kall.ensure((size_t)ctx->n_elem * ELEM * ctx->S));
+  s = enqueue_stages(ctx, d_Un, ctx->d_Kall.p, nullptr);
+  if (s != PERK_OK) return s;
+  return enqueue_reverse(ctx, d_Un, dt, ctx->d_Kall.p, d_lam_np1, d_lam_n);
 }
 
 perk_status perk_selftest_math(perk_ctx* ctx, int64_t n, const double* d_x, double* d_out) {

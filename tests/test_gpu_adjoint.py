@@ -130,3 +130,46 @@ def test_checkpointed_gradient_vs_central_differences():
         fd = (J_of(U0 + eps * d) - J_of(U0 - eps * d)) / (2 * eps)
         ad = float(torch.sum(grad * d))
         assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-12) + 1e-9 * float(torch.linalg.vector_norm(grad)), (k, fd, ad)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_stored_stages_match_recomputation(order):
+    # perk_step_store is perk_step bit for bit, and the reverse sweep from the stored
+    # stages is the recomputing reverse sweep bit for bit (same kernels, same inputs)
+    cells = kh_band_cells(3, 5, 0.05)
+    m = TreeMesh(cells, -1.0, 2.0)
+    U = cuda(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3))
+    if order == 2:
+        s = solver_for(cells, -1.0, 2.0, "hllc", [4, 6, 10, 16])
+    else:
+        from paper_2403_05144_gb300 import perk3_disk_tableau
+        s = solver_for(cells, -1.0, 2.0, "hllc")
+        c, a = perk3_disk_tableau([4, 8, 16])
+        s.set_tableau(3, [4, 8, 16], c, a)
+    dt = s.compute_dt(U, 0.5)
+    lam = cuda(np.random.default_rng(13).normal(size=U.shape))
+    Ua, Ub = U.clone(), U.clone()
+    s.step(Ua, dt)
+    K = s.step_store(Ub, dt)
+    assert torch.equal(Ua, Ub)
+    assert K.shape == (s.S, len(cells), 4, 4, 4)
+    got = s.step_vjp(U, dt, lam, stages=K)
+    want = s.step_vjp(U, dt, lam)
+    assert torch.equal(got, want)
+    s.check()
+
+
+def test_gradient_with_and_without_stored_stages():
+    from paper_2403_05144_gb300.adjoint import gradient, kinetic_energy
+    cells = kh_band_cells(3, 5, 0.05)
+    m = TreeMesh(cells, -1.0, 2.0)
+    U0 = cuda(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3))
+    s = solver_for(cells, -1.0, 2.0, "hllc", [4, 6, 10, 16])
+    dt = s.compute_dt(U0, 0.5)
+    h = torch.tensor(m.h, device="cuda")
+    w = torch.tensor(lgl_nodes_weights(3)[1], device="cuda")
+    J = lambda U: kinetic_energy(U, h, w)
+    Ja, ga = gradient(s, U0, dt, 13, J, checkpoint_every=5, store_stages=True)
+    Jb, gb = gradient(s, U0, dt, 13, J, checkpoint_every=5, store_stages=False)
+    assert float(Ja) == float(Jb)
+    assert torch.equal(ga, gb)
