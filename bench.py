@@ -1,15 +1,20 @@
 #!/usr/bin/env python
 """Throughput benchmark of the P-ERK step on one or more GB300s.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl perk|reference] [--workload kh|vortex]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl perk|reference]
+                    [--workload kh|vortex|shear|ensemble|adjoint]
 
 Prints one JSON line (rank 0).  Metric: P-ERK DoF-stage updates per second,
 i.e. the active DoF (nodes) summed over the stages of a step, divided by the
 step's device time; the same job also reports the wall time to t_end against
 the full-RHS S-stage method (every element evaluated at every stage, same S
-and dt) on the same GPU, the roofline of the dominant kernel against the
-measured FP64 rate, the end-to-end rate through the public API with host
-buffers, and the CPU oracle on a bounded sample.
+and dt) on the same GPU, the accuracy of both against a reference solution,
+the roofline of the dominant kernel against the measured FP64 rate, the
+end-to-end rate through the public API with host buffers, and the CPU oracle
+on a bounded sample.  Workloads: kh (default: Kelvin-Helmholtz with dynamic
+AMR), vortex (static two-level isentropic vortex), shear (Navier-Stokes shear
+layer, third order, dynamic AMR), ensemble (64 KH members in one context),
+adjoint (discrete-adjoint gradient over 200 steps).
 
 Multi-GPU: the step does not shard across GPUs here; N ranks run N
 independent replicas of the workload (weak scaling, no collective on the
@@ -35,7 +40,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from perk_inputs import isentropic_vortex, kelvin_helmholtz, nodal_state, uniform_cells, vortex_two_level_cells
+from perk_inputs import (isentropic_vortex, kelvin_helmholtz, nodal_state, shear_layer, uniform_cells,
+                         vortex_two_level_cells)
 
 METRIC = "P-ERK DoF-stage updates/s and wall time to t_end vs full-RK on same GB300"
 UNIT = "DoF-stage updates/s"
@@ -51,6 +57,8 @@ VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
 
 
 AMR_KH = dict(level_min=4, level_max=7, refine_above=0.1, coarsen_below=0.02)
+AMR_SHEAR = dict(level_min=6, level_max=8, refine_above=0.1, coarsen_below=0.02, indicator="lohner_vx")
+SHEAR_CFL = 0.7
 
 
 def workload(name: str) -> dict:
@@ -60,6 +68,14 @@ def workload(name: str) -> dict:
         return dict(name="kelvin_helmholtz_amr_levels4-7", cells=uniform_cells(4), x0=-1.0, L=2.0,
                     ic=kelvin_helmholtz, E=[4, 6, 10, 16], flux="hllc", cfl=0.7, t_end=3.0, amr=AMR_KH, n_amr=5,
                     init_cycles=3)
+    if name == "shear":
+        # doubly periodic shear layer on [0, 1]^2 (Sec. 7.1.1 set-up at Mach 0.3, Re 2500, Pr 0.72):
+        # Navier-Stokes with BR1, P-ERK3 {4, 8, 16}, HLL, N = 3, base level 6, dynamic AMR between
+        # levels 6 and 8 every 20 steps driven by Loehner's indicator of v_x, t_end = 1.2
+        return dict(name="shear_layer_navier_stokes_amr_levels6-8", cells=uniform_cells(6), x0=0.0, L=1.0,
+                    ic=shear_layer, E=[4, 8, 16], order=3, flux="hll", cfl=SHEAR_CFL, t_end=1.2,
+                    equations="navier_stokes", mu=1.0 / 2500.0, prandtl=0.72, amr=AMR_SHEAR, n_amr=20,
+                    init_cycles=2)
     if name == "vortex":
         # isentropic vortex, 16x16 base with the central 8x8 block refined (static), P-ERK2 {4, 8}, HLL
         return dict(name="isentropic_vortex_16x16_center8x8_refined", cells=vortex_two_level_cells(), x0=-10.0,
@@ -72,14 +88,20 @@ class Run:
     """One simulation through the library: mesh, P-ERK family, state, AMR every n_amr steps."""
 
     def __init__(self, torch, wl: dict, E, use_graph: bool = True):
-        from paper_2403_05144_gb300 import PerkSolver, perk2_disk_tableau, reference_nodes
+        from paper_2403_05144_gb300 import PerkSolver, perk2_disk_tableau, perk3_disk_tableau, reference_nodes
 
         self.torch = torch
         self.wl = wl
-        self.solver = PerkSolver(surface_flux=wl["flux"], use_graph=use_graph)
+        self.solver = PerkSolver(surface_flux=wl["flux"], use_graph=use_graph,
+                                 equations=wl.get("equations", "euler"), mu=wl.get("mu", 0.0),
+                                 prandtl=wl.get("prandtl", 0.72))
         self.solver.upload_mesh(wl["cells"], wl["x0"], wl["L"])
-        c, a = perk2_disk_tableau(E, max(wl["E"]))
-        self.solver.set_tableau(2, E, c, a)
+        if wl.get("order", 2) == 3:
+            c, a = perk3_disk_tableau(E)
+            self.solver.set_tableau(3, E, c, a)
+        else:
+            c, a = perk2_disk_tableau(E, max(wl["E"]))
+            self.solver.set_tableau(2, E, c, a)
         self.x, _ = reference_nodes(3)
         self.U = self._sample()
         for _ in range(wl["init_cycles"]):          # initial adaptation on the initial condition itself
@@ -209,57 +231,137 @@ def run_to_t_end(torch, wl: dict, E, budget_s: float) -> dict:
             "dof_stage_updates": units}
 
 
-def cpu_baseline(wl: dict, cells, U0: np.ndarray, dt: float) -> dict:
-    """The oracle as it stands on one dense P-ERK step of the same workload's current mesh."""
+def density_errors(torch, solver, U, exact: np.ndarray, x0: float, L: float) -> dict:
+    """(1/|Omega|) ||e_rho||_L1 by the LGL quadrature of every cell, and max |e_rho| over the nodes."""
+    from paper_2403_05144_gb300 import reference_nodes
+    _, w = reference_nodes(3)
+    e = np.abs(U[:, 0].cpu().numpy() - exact[:, 0])
+    h = L / 2.0 ** solver.cells[:, 0]
+    l1 = float(np.sum((0.5 * h) ** 2 * np.einsum("eji,j,i->e", e, w, w))) / (L * L)
+    return {"l1": l1, "linf": float(e.max())}
+
+
+def equal_error_vortex(torch) -> dict:
+    """Density errors at t = 20 (one period of the periodic vortex) against the exact
+    translated vortex, for the P-ERK2 {4, 8} family and the standalone 8-stage member at the
+    same dt (the accuracy comparison of Sec. 5)."""
+    from paper_2403_05144_gb300 import reference_nodes
+    wl = workload("vortex")
+    x, _ = reference_nodes(3)
+    t_end = wl["t_end"]
+    out = {}
+    for name, E in (("perk", wl["E"]), ("full_rk", [max(wl["E"])])):
+        run = Run(torch, wl, E)
+        n = math.ceil(t_end / run.dt)
+        run.dt = t_end / n
+        for _ in range(n):
+            run.step()
+        run.solver.check()
+        exact = nodal_state(lambda X, Y: isentropic_vortex(X, Y, t_end), run.solver.cells, wl["x0"], wl["L"], x)
+        out[name] = {**density_errors(torch, run.solver, run.U, exact, wl["x0"], wl["L"]), "steps": n, "dt": run.dt}
+    out["ratio_l1"] = out["perk"]["l1"] / out["full_rk"]["l1"]
+    out["ratio_linf"] = out["perk"]["linf"] / out["full_rk"]["linf"]
+    out["t_end"] = t_end
+    out["mesh"] = wl["name"]
+    return out
+
+
+def equal_error_kh(torch, t_end: float = 0.5) -> dict:
+    """Density errors at t = 0.5 of the P-ERK2 family and of the full-RK method (same dt) against
+    the full-RK method at dt/4, all on the frozen initially adapted KH mesh (the flow is chaotic
+    later, so only this early window is compared)."""
+    wl = dict(workload("kh"))
+    runs = {}
+    base = Run(torch, wl, wl["E"])
+    cells, U0 = base.solver.cells.copy(), base.U.clone()
+    dt0 = base.dt
+    frozen = dict(wl, amr=None, cells=cells, init_cycles=0)
+    for name, E, div in (("perk", wl["E"], 1), ("full_rk", [max(wl["E"])], 1), ("reference", [max(wl["E"])], 4)):
+        run = Run(torch, frozen, E)
+        run.U = U0.clone()
+        n = div * math.ceil(t_end / dt0)
+        run.dt = t_end / n
+        for _ in range(n):
+            run.step()
+        run.solver.check()
+        runs[name] = run
+    ref = runs["reference"].U.cpu().numpy()
+    out = {k: {**density_errors(torch, runs[k].solver, runs[k].U, ref, wl["x0"], wl["L"]), "dt": runs[k].dt}
+           for k in ("perk", "full_rk")}
+    out["ratio_l1"] = out["perk"]["l1"] / out["full_rk"]["l1"]
+    out["ratio_linf"] = out["perk"]["linf"] / out["full_rk"]["linf"]
+    out["t_end"] = t_end
+    out["mesh"] = f"kelvin_helmholtz initially adapted, frozen, {len(cells)} cells"
+    out["reference"] = "full-RK S=16 at dt/4"
+    return out
+
+
+def oracle_problem(wl: dict, cells):
+    """The oracle's mesh, P-ERK family, member of each cell and RHS for a workload."""
+    from oracle.br1 import NavierStokesDGSEM
     from oracle.dgsem import DGSEM
-    from oracle.perk import element_methods, perk2_family, prkm_step
+    from oracle.perk import element_methods, perk2_family, perk3_family
     from oracle.treemesh import TreeMesh
 
     mesh = TreeMesh(cells, wl["x0"], wl["L"])
-    fam = perk2_family(wl["E"])
+    fam = (perk3_family if wl.get("order", 2) == 3 else perk2_family)(wl["E"])
     meth = element_methods(mesh.cells[:, 0], fam.R)
-    dg = DGSEM(mesh, 3, wl["flux"])
+    if wl.get("equations", "euler") == "navier_stokes":
+        dg = NavierStokesDGSEM(mesh, 3, wl["flux"], mu=wl["mu"], prandtl=wl["prandtl"])
+    else:
+        dg = DGSEM(mesh, 3, wl["flux"])
+    return mesh, fam, meth, dg
+
+
+def oracle_stage_sample(wl: dict, cells, U: np.ndarray, n_stages: int = 0, budget_s: float = 10.0):
+    """Times the oracle's partitioned RHS I^(act(i)) F(U) for stages i = 0, 1, ... (cycling over
+    the S stages): n_stages evaluations, or as many as fit in budget_s (at least one).
+    Returns (DoF-stage updates, seconds, evaluations, S)."""
+    mesh, fam, meth, dg = oracle_problem(wl, cells)
+    act = [np.array([fam.active(int(r), i) for r in meth]) for i in range(fam.S)]
+    units, k = 0, 0
     t0 = time.perf_counter()
-    prkm_step(dg.rhs, U0, dt, fam, meth)
-    sec = time.perf_counter() - t0
-    units = sum(16 * int(sum(1 for r in meth if fam.active(int(r), i))) for i in range(fam.S))
+    while True:
+        dg.rhs_masked(U, act[k % fam.S])
+        units += 16 * int(act[k % fam.S].sum())
+        k += 1
+        sec = time.perf_counter() - t0
+        if (n_stages and k >= n_stages) or (not n_stages and sec >= budget_s):
+            break
+    return units, sec, k, fam.S
+
+
+def cpu_baseline(wl: dict, cells, U0: np.ndarray, dt: float) -> dict:
+    """The oracle as it stands, on a bounded sample of the same workload: partitioned stage
+    evaluations of the workload's current mesh for about ten seconds."""
+    units, sec, k, S = oracle_stage_sample(wl, cells, U0)
     return {"value": units / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one dense P-ERK step of the workload's current mesh ({len(cells)} cells, S={fam.S}), "
-                      f"{sec:.1f} s, numpy float64 on one host thread"}
+            "sample": f"{k} partitioned stage evaluations (stages 0.. of S={S}, cycling) of the workload's "
+                      f"current mesh ({len(cells)} cells), {sec:.1f} s, numpy float64 on one host thread"}
 
 
 def run_reference(args) -> None:
     rank, _, world = dist_info()
     if rank != 0:
         return
-    from oracle.dgsem import DGSEM
+    from oracle.amr import desired_levels, indicator, new_cells
     from oracle.lgl import lgl_nodes_weights
-    from oracle.perk import element_methods, perk2_family
     from oracle.treemesh import TreeMesh
 
-    from oracle.amr import desired_levels, indicator, new_cells
-
+    if args.workload not in ("kh", "vortex", "shear"):
+        raise SystemExit("--impl reference times the oracle on the kh, vortex or shear workload")
     wl = workload(args.workload)
     x, _ = lgl_nodes_weights(3)
     cells = wl["cells"]
+    amr = dict(wl["amr"] or {})
+    kind = amr.pop("indicator", "density")
     for _ in range(wl["init_cycles"]):          # the same initial adaptation as the library run
         m0 = TreeMesh(cells, wl["x0"], wl["L"])
         U0 = nodal_state(wl["ic"], cells, wl["x0"], wl["L"], x)
-        cells = new_cells(m0, desired_levels(m0, indicator(U0), **wl["amr"]))
+        cells = new_cells(m0, desired_levels(m0, indicator(U0, kind=kind), **amr))
     U = nodal_state(wl["ic"], cells, wl["x0"], wl["L"], x)
-    mesh = TreeMesh(cells, wl["x0"], wl["L"])
-    fam = perk2_family(wl["E"])
-    meth = element_methods(mesh.cells[:, 0], fam.R)
-    dg = DGSEM(mesh, 3, wl["flux"])
-    act = [16 * int(sum(1 for r in meth if fam.active(int(r), i))) for i in range(fam.S)]
-    for w in range(args.warmup):
-        dg.rhs(U)
-    units = 0
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        dg.rhs_masked(U, np.array([fam.active(int(r), k % fam.S) for r in meth]))
-        units += act[k % fam.S]
-    sec = time.perf_counter() - t0
+    oracle_stage_sample(wl, cells, U, n_stages=args.warmup)
+    units, sec, k, S = oracle_stage_sample(wl, cells, U, n_stages=args.steps)
     value = units / sec
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
@@ -267,9 +369,9 @@ def run_reference(args) -> None:
             "impl": "reference",
             "config": {"workload": wl["name"], "n_elem": len(cells), "family": wl["E"],
                        "surface_flux": wl["flux"],
-                       "step": "one partitioned RHS stage of the dense oracle step on the initially adapted mesh"},
+                       "step": "one partitioned stage evaluation of the oracle on the initially adapted mesh"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} stage evaluations (cycling over the S={fam.S} stages) "
+                             "sample": f"{args.steps} stage evaluations (cycling over the S={S} stages) "
                                        f"of the {len(cells)}-cell initially adapted mesh"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -362,6 +464,11 @@ def run_perk(args) -> None:
     tend["t_end"] = wl["t_end"]
     if tend["perk"]["status"] == tend["full_rk"]["status"] == "reached t_end":
         tend["wall_ratio_full_over_perk"] = tend["full_rk"]["wall_s"] / tend["perk"]["wall_s"]
+    equal_error = None
+    if args.workload in ("kh", "vortex"):
+        equal_error = {"vortex": equal_error_vortex(torch)}
+    if args.workload == "kh":
+        equal_error["kelvin_helmholtz"] = equal_error_kh(torch)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -377,6 +484,7 @@ def run_perk(args) -> None:
                     "dof_stage_updates_per_step": units_full / args.steps,
                     "ratio_ms_per_step_full_over_perk": ms_full / ms},
         "t_end": tend,
+        "equal_error": equal_error,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / fma_flops, "traffic": None, "kernel": "k_volume",
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
@@ -450,6 +558,7 @@ def run_ensemble(args) -> None:
         k += 1
         return ens.info()["dof_stage_updates"]
 
+    epb = ens.autotune(U)          # elements per block of the volume kernel, timed on this mesh
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -473,7 +582,7 @@ def run_ensemble(args) -> None:
             "config": {"workload": "kelvin_helmholtz_ensemble_64_members", "members": n,
                        "member_dof_initial_min_max": [min(dof_member), max(dof_member)],
                        "n_elem_total": info["n_elem"], "family": [4, 6, 10, 16], "amr_every_steps": 5,
-                       "graph": True, "launches_per_stage": 2,
+                       "graph": True, "launches_per_stage": 2, "volume_elems_per_block_autotuned": epb,
                        "l2": "flushed (256 MB write) before every timed step"},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -590,7 +699,7 @@ def main():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="perk", choices=["perk", "reference"])
-    p.add_argument("--workload", default="kh", choices=["kh", "vortex", "ensemble", "adjoint"])
+    p.add_argument("--workload", default="kh", choices=["kh", "vortex", "shear", "ensemble", "adjoint"])
     p.add_argument("--t-end-budget", type=float, default=60.0, help="wall seconds per run to t_end")
     args = p.parse_args()
     if args.warmup < 3:

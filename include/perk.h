@@ -243,21 +243,45 @@ perk_status perk_step_store(perk_ctx* ctx, double* d_U, double dt, double* d_K);
 perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, const double* d_K,
                                  const double* d_lam_np1, double* d_lam_n);
 
+/* Chooses the elements per block of the volume kernel (2, 4 or 8; 2 until
+ * this is called) for this context: the volume term of every element of the
+ * current mesh at the stage state d_U (device, U layout) is timed with each
+ * choice (CUDA events, one untimed and five timed launches each) and the
+ * fastest is kept for every later launch, including a re-captured step graph.
+ * *elems_per_block (may be NULL) receives the choice.  Results do not depend
+ * on the choice.  Blocks. */
+perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elems_per_block);
+/* Sets the elements per block of the volume kernel (2, 4 or 8; INVALID_ARG
+ * otherwise) without timing. */
+perk_status perk_set_volume_blocks(perk_ctx* ctx, int32_t elems_per_block);
+
 /* Adaptive mesh refinement (Sec. 7: the AMR callback every N_AMR steps, after
- * which the partition is re-assigned, Sec. 6.2).  Indicator: the density
- * gradient eta_e = h_e max_nodes |grad rho| / mean_e(rho) (dimensionless).
+ * which the partition is re-assigned, Sec. 6.2).  Indicators (dimensionless):
+ *   PERK_INDICATOR_DENSITY: the density gradient
+ *     eta_e = h_e max_nodes |grad rho| / mean_e(rho);
+ *   PERK_INDICATOR_LOHNER_VX: Loehner's second-difference estimator of the
+ *     velocity v_x (the shear-layer indicator of Sec. 7.1.1; Loehner 1987 in
+ *     the nodal form of Fryxell et al. 2000): the largest, over every three
+ *     consecutive nodes u_-, u_0, u_+ of a grid line of the element in both
+ *     directions, of |u_+ - 2 u_0 + u_-| / (|u_+ - u_0| + |u_0 - u_-|
+ *     + eps (|u_+| + 2 |u_0| + |u_-|)), eps = PERK_LOHNER_EPS (0 where the
+ *     denominator vanishes); in [0, 1].
  * Desired level of a cell: level + 1 if eta > refine_above (below level_max),
  * level - 1 if eta < coarsen_below (above level_min), else level; raised to
  * the least fixed point of two rules: a cell coarsens only together with its
  * three siblings (all leaves, all wanting to coarsen), and face neighbours of
  * the new mesh differ by at most one level. */
+typedef enum { PERK_INDICATOR_DENSITY = 0, PERK_INDICATOR_LOHNER_VX = 1 } perk_indicator;
+#define PERK_LOHNER_EPS 0.2
 typedef struct {
   int32_t level_min, level_max;
   double refine_above, coarsen_below;
+  int32_t indicator; /* perk_indicator */
 } perk_amr_params;
 
-/* eta of every cell of d_U into d_eta[n_elem] (device). */
-perk_status perk_amr_indicator(perk_ctx* ctx, const double* d_U, double* d_eta);
+/* eta of every cell of d_U into d_eta[n_elem] (device) by the given indicator
+ * (INVALID_ARG for an unknown one). */
+perk_status perk_amr_indicator(perk_ctx* ctx, int32_t indicator, const double* d_U, double* d_eta);
 
 /* Plans one adaptation.  With desired == NULL the indicator of d_U and `prm`
  * decide; otherwise desired[n_elem] (host) gives each cell's wanted level

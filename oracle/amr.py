@@ -3,9 +3,16 @@
 The paper adapts the TreeMesh every N_AMR steps (Sec. 7; the AMR callback
 before the partition is re-assigned, Sec. 6.2).  The oracle follows these steps:
 
-1. Indicator (density gradient): eta_e = h_e max_nodes |grad rho| / mean_e(rho),
-   with grad rho = (2/h_e) (D rho along x, D rho along y) at the nodes and the
-   mean by the LGL quadrature; eta is dimensionless.
+1. Indicator, one of
+   - density gradient: eta_e = h_e max_nodes |grad rho| / mean_e(rho), with
+     grad rho = (2/h_e) (D rho along x, D rho along y) at the nodes and the mean
+     by the LGL quadrature; eta is dimensionless;
+   - Loehner's second-difference estimator (Loehner 1987, in the nodal form of
+     the FLASH code, Fryxell et al. 2000) of the velocity v_x, the indicator of
+     the shear-layer run (Sec. 7.1.1): for every three consecutive nodes
+     u_-, u_0, u_+ along a grid line of the element, in both directions,
+       |u_+ - 2 u_0 + u_-| / (|u_+ - u_0| + |u_0 - u_-| + eps (|u_+| + 2|u_0| + |u_-|)),
+     eta_e = the largest of these (0 where the denominator vanishes), eps = 0.2.
 2. Desired level: level + 1 where eta > refine_above (up to level_max),
    level - 1 where eta < coarsen_below (down to level_min), else level.
 3. Constraints, raised to their least fixed point: a cell may only coarsen
@@ -29,7 +36,28 @@ from .lgl import derivative_matrix, lagrange_basis, lgl_nodes_weights, mass_matr
 from .treemesh import TreeMesh
 
 
-def indicator(U: np.ndarray, N: int = 3) -> np.ndarray:
+LOHNER_EPS = 0.2
+
+
+def lohner_indicator(f: np.ndarray, eps: float = LOHNER_EPS) -> np.ndarray:
+    """Loehner's estimator of the nodal field f [e, j, i] (largest over the node triples)."""
+    out = np.zeros(len(f))
+    for line_major in (False, True):
+        g = np.swapaxes(f, 1, 2) if line_major else f        # triples along i (x), then along j (y)
+        for c in range(1, g.shape[2] - 1):
+            um, u0, up = g[:, :, c - 1], g[:, :, c], g[:, :, c + 1]
+            num = np.abs(up - 2.0 * u0 + um)
+            den = np.abs(up - u0) + np.abs(u0 - um) + eps * (np.abs(up) + 2.0 * np.abs(u0) + np.abs(um))
+            r = np.where(den > 0.0, num / np.where(den > 0.0, den, 1.0), 0.0)
+            out = np.maximum(out, r.max(axis=1))
+    return out
+
+
+def indicator(U: np.ndarray, N: int = 3, kind: str = "density") -> np.ndarray:
+    if kind == "lohner_vx":
+        return lohner_indicator(U[:, 1] / U[:, 0])
+    if kind != "density":
+        raise ValueError(kind)
     x, w = lgl_nodes_weights(N)
     D = derivative_matrix(x)
     rho = U[:, 0]                                              # [e, j, i]
@@ -134,10 +162,10 @@ def transfer(old_cells, U_old: np.ndarray, cells, N: int = 3) -> np.ndarray:
 
 
 def adapt(mesh: TreeMesh, U: np.ndarray, level_min: int, level_max: int, refine_above: float, coarsen_below: float,
-          desired=None):
+          desired=None, kind: str = "density"):
     """One AMR cycle; returns (new TreeMesh, transferred U, desired levels)."""
     if desired is None:
-        desired = desired_levels(mesh, indicator(U), level_min, level_max, refine_above, coarsen_below)
+        desired = desired_levels(mesh, indicator(U, kind=kind), level_min, level_max, refine_above, coarsen_below)
     cells = new_cells(mesh, desired)
     U_new = transfer([tuple(c) for c in mesh.cells.tolist()], U, cells)
     return TreeMesh(cells, mesh.x0, mesh.length), U_new, desired

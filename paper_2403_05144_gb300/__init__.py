@@ -286,17 +286,31 @@ class PerkSolver:
         return K
 
     # ------------------------------------------------------------------ AMR
-    def amr_indicator(self, U):
+    def autotune(self, U) -> int:
+        """Times the volume kernel with 2, 4 and 8 elements per block on the current mesh and keeps
+        the fastest; returns the choice."""
+        U = self._state(U)
+        out = C.c_int32()
+        self._call(self.lib.perk_autotune_volume, C.c_void_p(_ptr(U)), C.byref(out))
+        return out.value
+
+    def set_volume_blocks(self, elems_per_block: int):
+        self._call(self.lib.perk_set_volume_blocks, C.c_int32(elems_per_block))
+
+    INDICATORS = {"density": 0, "lohner_vx": 1}
+
+    def amr_indicator(self, U, indicator: str = "density"):
         U = self._state(U)
         eta = self.torch.empty(self.n_elem, dtype=self.torch.float64, device="cuda")
-        self._call(self.lib.perk_amr_indicator, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(eta)))
+        self._call(self.lib.perk_amr_indicator, C.c_int32(self.INDICATORS[indicator]), C.c_void_p(_ptr(U)),
+                   C.c_void_p(_ptr(eta)))
         return eta
 
     def adapt(self, U, level_min: int = 4, level_max: int = 7, refine_above: float = 0.1,
-              coarsen_below: float = 0.02, desired=None):
+              coarsen_below: float = 0.02, desired=None, indicator: str = "density"):
         """One AMR cycle: returns the solution on the new mesh (a new tensor)."""
         U = self._state(U)
-        prm = _lib.PerkAmrParams(level_min, level_max, refine_above, coarsen_below)
+        prm = _lib.PerkAmrParams(level_min, level_max, refine_above, coarsen_below, self.INDICATORS[indicator])
         n_new = C.c_int64()
         if desired is not None:
             d = np.ascontiguousarray(np.asarray(desired, dtype=np.int32))

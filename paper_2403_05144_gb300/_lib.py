@@ -36,7 +36,7 @@ class PerkCounters(C.Structure):
 
 class PerkAmrParams(C.Structure):
     _fields_ = [("level_min", C.c_int32), ("level_max", C.c_int32), ("refine_above", C.c_double),
-                ("coarsen_below", C.c_double)]
+                ("coarsen_below", C.c_double), ("indicator", C.c_int32)]
 
 
 class PerkKernelTimes(C.Structure):
@@ -79,7 +79,9 @@ SIGNATURES = [
     ("perk_step_vjp", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     ("perk_step_store", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     ("perk_step_vjp_stored", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
-    ("perk_amr_indicator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk_autotune_volume", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    ("perk_set_volume_blocks", C.c_int, [C.c_void_p, C.c_int32]),
+    ("perk_amr_indicator", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("perk_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(PerkAmrParams), C.POINTER(C.c_int32), C.c_void_p,
                                   C.POINTER(C.c_int64)]),
     ("perk_adapt_commit", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -245,6 +245,8 @@ struct perk_ctx {
 
   // adjoint work space
   DevBuf<double> d_surf_d, d_Kall, d_g, d_lamK1, d_lamKa, d_lamKb;
+  // elements per block of the volume kernel (perk_autotune_volume)
+  int vol_epb = VOL_EPB_DEFAULT;
   // second stream of the reverse sweep: face adjoints run beside the volume adjoint
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -740,7 +742,7 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
     TIMED(ctx, timer, st, 1,
           launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
                         ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur],
-                        (last && !visc) ? &chk : nullptr, ctx->d_logtab.p));
+                        (last && !visc) ? &chk : nullptr, ctx->d_logtab.p, ctx->vol_epb));
     if (visc)
       TIMED(ctx, timer, st, 3,
             launch_br1(st, Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ctx->act_if[i],
@@ -1247,7 +1249,8 @@ static perk_status rhs_given(perk_ctx* ctx, int stage, const double* d_Y, double
   PERK_CUDA(ctx, launch_faces(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
                               ctx->d_method.p, sa, ctx->d_surf.p));
   PERK_CUDA(ctx, launch_volume(ctx->stream, Y_GIVEN, ctx->ops, ne, ctx->d_elem_sorted.p, ctx->d_level.p,
-                               ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr, ctx->d_logtab.p));
+                               ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr, ctx->d_logtab.p,
+                               ctx->vol_epb));
   if (ctx->viscous())
     PERK_CUDA(ctx, launch_br1(ctx->stream, Y_GIVEN, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ni,
                               nm, ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->n_elem, ne, ctx->d_elem_sorted.p,
@@ -1491,7 +1494,7 @@ static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, 
                                 ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     PERK_CUDA(ctx, launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
                                  ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, K + (size_t)i * nd,
-                                 check ? &ua : nullptr, ctx->d_logtab.p));
+                                 check ? &ua : nullptr, ctx->d_logtab.p, ctx->vol_epb));
   }
   if (d_U) PERK_CUDA(ctx, launch_commit(st, ctx->n_elem, ua, K + (size_t)(ctx->S - 1) * nd, ctx->d_dt.p, d_U));
   return PERK_OK;
@@ -1606,18 +1609,81 @@ perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const do
   return enqueue_reverse(ctx, d_Un, dt, ctx->d_Kall.p, d_lam_np1, d_lam_n);
 }
 
+perk_status perk_set_volume_blocks(perk_ctx* ctx, int32_t elems_per_block) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (elems_per_block != 2 && elems_per_block != 4 && elems_per_block != 8)
+    return fail(ctx, PERK_E_INVALID_ARG, "elements per block must be 2, 4 or 8");
+  if (elems_per_block != ctx->vol_epb) {
+    ctx->vol_epb = elems_per_block;
+    ctx->graph_valid = false;
+  }
+  return PERK_OK;
+}
+
+perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elems_per_block) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_U) return fail(ctx, PERK_E_INVALID_ARG, "null U");
+  const size_t nd = (size_t)ctx->n_elem * ELEM;
+  PERK_CUDA(ctx, ctx->d_g.ensure(nd));   // scratch output (the adjoint's work array)
+  DevBuf<double>& K = ctx->d_g;
+  StageArgs sa{};
+  sa.Y = d_U;
+  cudaStream_t st = ctx->stream;
+  PERK_CUDA(ctx, launch_faces(st, Y_GIVEN, ctx->ops, ctx->n_if, ctx->d_if_sorted.p, ctx->n_mort,
+                              ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
+  cudaEvent_t a = nullptr, b = nullptr;
+  PERK_CUDA(ctx, cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(ctx, PERK_E_CUDA, "event creation failed");
+  }
+  const int cand[3] = {2, 4, 8};
+  float best_ms = 0.f;
+  int best = VOL_EPB_DEFAULT;
+  cudaError_t err = cudaSuccess;
+  for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+    // one untimed launch, then five timed ones over every element of the mesh
+    err = launch_volume(st, Y_GIVEN, ctx->ops, ctx->n_elem, ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p,
+                        2.0 / ctx->length, sa, ctx->d_surf.p, K.p, nullptr, ctx->d_logtab.p, cand[k]);
+    if (err == cudaSuccess) err = cudaEventRecord(a, st);
+    for (int r = 0; r < 5 && err == cudaSuccess; ++r)
+      err = launch_volume(st, Y_GIVEN, ctx->ops, ctx->n_elem, ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p,
+                          2.0 / ctx->length, sa, ctx->d_surf.p, K.p, nullptr, ctx->d_logtab.p, cand[k]);
+    if (err == cudaSuccess) err = cudaEventRecord(b, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+    if (err == cudaSuccess && (k == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = cand[k];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  PERK_CUDA(ctx, err);
+  if (best != ctx->vol_epb) {
+    ctx->vol_epb = best;
+    ctx->graph_valid = false;   // the next step re-captures its launches
+  }
+  if (elems_per_block) *elems_per_block = best;
+  return PERK_OK;
+}
+
 perk_status perk_selftest_math(perk_ctx* ctx, int64_t n, const double* d_x, double* d_out) {
   if (!ctx || !d_x || !d_out || n < 0) return PERK_E_INVALID_ARG;
   PERK_CUDA(ctx, launch_selftest_math(ctx->stream, n, d_x, d_out, ctx->d_logtab.p));
   return PERK_OK;
 }
 
-perk_status perk_amr_indicator(perk_ctx* ctx, const double* d_U, double* d_eta) {
+perk_status perk_amr_indicator(perk_ctx* ctx, int32_t indicator, const double* d_U, double* d_eta) {
   if (!ctx || !d_U || !d_eta) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (indicator != PERK_INDICATOR_DENSITY && indicator != PERK_INDICATOR_LOHNER_VX)
+    return fail(ctx, PERK_E_INVALID_ARG, "unknown indicator %d", indicator);
   std::vector<double> x, w;
   lgl(NN - 1, x, w);
-  PERK_CUDA(ctx, launch_indicator(ctx->stream, ctx->n_elem, d_U, ctx->ops, w[0], w[1], d_eta));
+  PERK_CUDA(ctx, launch_indicator(ctx->stream, ctx->n_elem, d_U, ctx->ops, w[0], w[1], indicator, d_eta));
   return PERK_OK;
 }
 
@@ -1636,9 +1702,11 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
     }
   } else {
     if (!prm || !d_U) return fail(ctx, PERK_E_INVALID_ARG, "need AMR parameters and U");
+    if (prm->indicator != PERK_INDICATOR_DENSITY && prm->indicator != PERK_INDICATOR_LOHNER_VX)
+      return fail(ctx, PERK_E_INVALID_ARG, "unknown indicator %d", prm->indicator);
     std::vector<double> x, w;
     lgl(NN - 1, x, w);
-    PERK_CUDA(ctx, launch_indicator(ctx->stream, n, d_U, ctx->ops, w[0], w[1], ctx->d_eta.p));
+    PERK_CUDA(ctx, launch_indicator(ctx->stream, n, d_U, ctx->ops, w[0], w[1], prm->indicator, ctx->d_eta.p));
     std::vector<double> eta(n);
     PERK_CUDA(ctx, cudaMemcpyAsync(eta.data(), ctx->d_eta.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

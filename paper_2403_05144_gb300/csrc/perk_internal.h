@@ -75,9 +75,12 @@ cudaError_t launch_dt_members(cudaStream_t st, int64_t n_elem, const double* U, 
 cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                          const int4* morts, const int32_t* method, const StageArgs& sa, double* surf);
 
+// elems_per_block: 2, 4 or 8 (cudaErrorInvalidValue otherwise)
+constexpr int VOL_EPB_DEFAULT = 2;
 cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
                           const int32_t* level, const int32_t* method, double inv_len2, const StageArgs& sa,
-                          const double* surf, double* K, const UpdateArgs* check, const double* log_table);
+                          const double* surf, double* K, const UpdateArgs* check, const double* log_table,
+                          int elems_per_block = VOL_EPB_DEFAULT);
 
 // log_table: [inv_c[128], ln_c[128]] of the volume kernel's logarithm (see perk_kernels.cu)
 constexpr int LOG_TABLE_SIZE = 128;
@@ -89,7 +92,7 @@ cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua,
 cudaError_t launch_set_scalar(cudaStream_t st, double* p, double v);
 
 cudaError_t launch_indicator(cudaStream_t st, int64_t n, const double* U, const Ops& ops, double w0, double w1,
-                             double* eta);
+                             int kind, double* eta);
 cudaError_t launch_transfer(cudaStream_t st, int64_t n, const int32_t* map, const double* Uold, const Ops& ops,
                             double* Unew);
 

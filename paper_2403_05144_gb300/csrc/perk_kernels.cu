@@ -396,7 +396,7 @@ __device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int 
 
 // ---------------------------------------------------------------------------
 // Faces: 4 threads per interface (one per face node), 8 per mortar (half, node).
-constexpr int FACE_THREADS = 128;
+constexpr int FACE_THREADS = 32;
 constexpr int IF_PER_BLOCK = FACE_THREADS / 4;
 constexpr int MORT_PER_BLOCK = FACE_THREADS / 8;
 
@@ -482,17 +482,17 @@ __global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, c
 
 // ---------------------------------------------------------------------------
 // Volume integral (flux differencing) + surface lifting + Jacobian.
-// 16 threads per element (one per node), 8 elements per block.
-constexpr int VOL_THREADS = 128;
-constexpr int VOL_ELEMS = VOL_THREADS / NODES;
+// 16 threads per element (one per node), VOL_ELEMS = 2, 4 or 8 elements per block (chosen per
+// context by perk_autotune_volume; 2 by default: small blocks spread the element-stages evenly
+// over the SMs when a stage has only a few thousand active elements).
 constexpr int NPAIR = 48;  // 2 directions x 4 lines x 6 pairs
 
 __device__ __forceinline__ int pair_slot(int a, int b) {  // a < b, slots 0..5
   return (a * (7 - a)) / 2 + b - a - 1;
 }
 
-template <int YS, bool CHECK>
-__global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
+template <int YS, bool CHECK, int VOL_ELEMS>
+__global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
                                                          const int32_t* __restrict__ level,
                                                          const int32_t* __restrict__ method, double two_over_len,
                                                          StageArgs sa, const double* __restrict__ surf,
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(VOL_THREADS) k_volume(Ops ops, int64_t n, cons
   __shared__ NodeQ s_prim[VOL_ELEMS][NODES];
   __shared__ double s_flux[VOL_ELEMS][4][NPAIR];
   __shared__ double s_log[2 * LOG_TABLE];
-  for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_THREADS) s_log[q] = log_table[q];
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_ELEMS * NODES) s_log[q] = log_table[q];
   __syncthreads();
   const int le = threadIdx.x >> 4;
   const int t = threadIdx.x & 15;
@@ -816,21 +816,45 @@ constexpr int AMR_ELEMS = AMR_THREADS / NODES;
 
 // eta_e = h max_nodes |grad rho| / mean(rho) = 2 max_nodes |(D rho)_x, (D rho)_y| / mean(rho)
 __global__ void __launch_bounds__(AMR_THREADS) k_indicator(int64_t n, const double* __restrict__ U, Ops ops,
-                                                            double w0, double w1, double* __restrict__ eta) {
-  __shared__ double s_rho[AMR_ELEMS][NODES];
+                                                            double w0, double w1, int kind,
+                                                            double* __restrict__ eta) {
+  __shared__ double s_f[AMR_ELEMS][NODES];
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
   const int64_t e = (int64_t)blockIdx.x * AMR_ELEMS + le;
   const bool valid = e < n;
   const double rho = valid ? U[e * ELEM + t] : 1.0;
-  s_rho[le][t] = rho;
+  if (kind == PERK_INDICATOR_LOHNER_VX) {
+    // Loehner's estimator of v_x; round-to-nearest operations in a fixed order
+    const double vx = valid ? U[e * ELEM + NODES + t] / rho : 0.0;
+    s_f[le][t] = vx;
+    __syncwarp();
+    double r = 0.0;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int c = d ? j : i;                       // position of this node along the line
+      if (c == 0 || c == 3) continue;
+      const int step = d ? 4 : 1;
+      const double um = s_f[le][t - step], u0 = vx, up = s_f[le][t + step];
+      const double num = fabs(__dadd_rn(__dsub_rn(up, __dmul_rn(2.0, u0)), um));
+      const double den = __dadd_rn(__dadd_rn(fabs(__dsub_rn(up, u0)), fabs(__dsub_rn(u0, um))),
+                                   __dmul_rn(PERK_LOHNER_EPS,
+                                             __dadd_rn(__dadd_rn(fabs(up), __dmul_rn(2.0, fabs(u0))), fabs(um))));
+      if (den > 0.0) r = fmax(r, num / den);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o, 16));
+    if (valid && t == 0) eta[e] = r;
+    return;
+  }
+  s_f[le][t] = rho;
   __syncwarp();
   double gx = 0.0, gy = 0.0;
 #pragma unroll
   for (int m = 0; m < NN; ++m) {
     // the derivative matrix is dsplit/2 off the diagonal; its diagonal is -(row sum)
     const double dxm = 0.5 * ops.dsplit[i][m], dym = 0.5 * ops.dsplit[j][m];
-    gx = fma(dxm, s_rho[le][j * 4 + m] - s_rho[le][j * 4 + i], gx);
-    gy = fma(dym, s_rho[le][m * 4 + i] - s_rho[le][j * 4 + i], gy);
+    gx = fma(dxm, s_f[le][j * 4 + m] - s_f[le][j * 4 + i], gx);
+    gy = fma(dym, s_f[le][m * 4 + i] - s_f[le][j * 4 + i], gy);
   }
   double g2 = fma(gx, gx, gy * gy);
   const double wi = (i == 0 || i == 3) ? w0 : w1, wj = (j == 0 || j == 3) ? w0 : w1;
@@ -898,9 +922,9 @@ __global__ void __launch_bounds__(AMR_THREADS) k_transfer(int64_t n, const int32
 // ---------------------------------------------------------------------------
 // launchers
 cudaError_t launch_indicator(cudaStream_t st, int64_t n, const double* U, const Ops& ops, double w0, double w1,
-                             double* eta) {
+                             int kind, double* eta) {
   if (n == 0) return cudaSuccess;
-  k_indicator<<<(unsigned)((n + AMR_ELEMS - 1) / AMR_ELEMS), AMR_THREADS, 0, st>>>(n, U, ops, w0, w1, eta);
+  k_indicator<<<(unsigned)((n + AMR_ELEMS - 1) / AMR_ELEMS), AMR_THREADS, 0, st>>>(n, U, ops, w0, w1, kind, eta);
   return cudaGetLastError();
 }
 
@@ -968,22 +992,45 @@ cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t 
   return cudaGetLastError();
 }
 
+template <int VE>
+static void volume_grid(YSource ysrc, bool check, cudaStream_t st, const Ops& ops, int64_t n, const int32_t* elems,
+                        const int32_t* level, const int32_t* method, double two_over_len, const StageArgs& sa,
+                        const double* surf, double* K, const UpdateArgs& ua, const double* log_table) {
+  const unsigned blocks = (unsigned)((n + VE - 1) / VE);
+  if (ysrc == Y_GIVEN)
+    k_volume<Y_GIVEN, false, VE><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf,
+                                                                K, ua, log_table);
+  else if (check)
+    k_volume<Y_COMBINE, true, VE><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len, sa,
+                                                                 surf, K, ua, log_table);
+  else
+    k_volume<Y_COMBINE, false, VE><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len, sa,
+                                                                  surf, K, ua, log_table);
+}
+
 cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
                           const int32_t* level, const int32_t* method, double two_over_len, const StageArgs& sa,
-                          const double* surf, double* K, const UpdateArgs* check, const double* log_table) {
+                          const double* surf, double* K, const UpdateArgs* check, const double* log_table,
+                          int elems_per_block) {
   if (n == 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((n + VOL_ELEMS - 1) / VOL_ELEMS);
   UpdateArgs ua{};
   if (check) ua = *check;
-  if (ysrc == Y_GIVEN)
-    k_volume<Y_GIVEN, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
-                                                              ua, log_table);
-  else if (check)
-    k_volume<Y_COMBINE, true><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
-                                                               ua, log_table);
-  else
-    k_volume<Y_COMBINE, false><<<blocks, VOL_THREADS, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf, K,
-                                                                ua, log_table);
+  switch (elems_per_block) {
+    case 2:
+      volume_grid<2>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
+                     log_table);
+      break;
+    case 4:
+      volume_grid<4>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
+                     log_table);
+      break;
+    case 8:
+      volume_grid<8>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
+                     log_table);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -36,6 +36,34 @@ def test_indicator_parity():
     np.testing.assert_allclose(got, indicator(U), rtol=1e-12)
 
 
+def test_lohner_indicator_parity_bitwise():
+    # the kernel evaluates the estimator in the oracle's operation order with
+    # round-to-nearest operations, so the values agree bit for bit
+    cells = kh_band_cells(4, 6, 0.05)
+    U = discontinuous_state(cells, -1.0, 2.0)
+    s = solver_for(cells, -1.0, 2.0, "hllc")
+    got = s.amr_indicator(cuda(U), indicator="lohner_vx").cpu().numpy()
+    want = indicator(U, kind="lohner_vx")
+    assert np.array_equal(got, want)
+    assert want.max() > 0.1
+
+
+def test_lohner_driven_cycles_on_the_shear_layer_match_oracle():
+    from perk_inputs import shear_layer
+    cells = uniform_cells(4)
+    U = nodal_state(shear_layer, cells, 0.0, 1.0, X3)
+    s = solver_for(cells, 0.0, 1.0, "hll")
+    m = TreeMesh(cells, 0.0, 1.0)
+    Ug = cuda(U)
+    prm = dict(level_min=4, level_max=6, refine_above=0.3, coarsen_below=0.05)
+    for _ in range(3):
+        m, U, _ = oracle_adapt(m, U, **prm, kind="lohner_vx")
+        Ug = s.adapt(Ug, **prm, indicator="lohner_vx")
+        assert [tuple(c) for c in s.cells.tolist()] == [tuple(c) for c in m.cells.tolist()]
+        np.testing.assert_allclose(Ug.cpu().numpy(), U, rtol=0, atol=1e-13 * np.max(np.abs(U)))
+    assert m.cells[:, 0].max() == 6
+
+
 def test_plan_and_transfer_match_oracle_with_given_levels():
     cells = kh_band_cells(4, 6, 0.05)
     m = TreeMesh(cells, -1.0, 2.0)

@@ -189,3 +189,33 @@ def test_partition_counts_match_oracle():
             fine[(large, d, large == A)] = meth[small]
         assert info["active_mortars"][i] == sum(1 for r in fine.values() if fam.active(int(r), i))
     assert info["dof_stage_updates"] == 16 * sum(info["active_elements"])
+
+
+def test_volume_block_sizes_give_identical_steps():
+    # the elements per block of the volume kernel change only the launch shape
+    from paper_2403_05144_gb300 import PerkSolver
+    cells = kh_band_cells(4, 6, 0.05)
+    U0 = torch.from_numpy(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)).cuda()
+    outs = []
+    for epb in (2, 4, 8):
+        s = PerkSolver(surface_flux="hllc")
+        s.upload_mesh(cells, -1.0, 2.0)
+        s.set_perk2_disk([4, 6, 10, 16])
+        s.set_volume_blocks(epb)
+        U = U0.clone()
+        dt = s.compute_dt(U, 0.5)
+        for _ in range(3):
+            s.step(U, dt)
+        outs.append(U)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    s = PerkSolver(surface_flux="hllc")
+    s.upload_mesh(cells, -1.0, 2.0)
+    s.set_perk2_disk([4, 6, 10, 16])
+    assert s.autotune(U0) in (2, 4, 8)
+    U = U0.clone()
+    dt = s.compute_dt(U, 0.5)
+    for _ in range(3):
+        s.step(U, dt)
+    assert torch.equal(U, outs[0])
+    with pytest.raises(Exception):
+        s.set_volume_blocks(3)

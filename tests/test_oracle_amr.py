@@ -24,6 +24,30 @@ def test_indicator_linear_density_closed_form():
     np.testing.assert_allclose(eta, h * b / (a + b * xc), rtol=1e-13)
 
 
+def test_lohner_indicator_hand_computed_values():
+    # v_x on every row of the element: (1, 1, 3, 1) at the four x nodes; rho = 2.
+    # Triples along x: (1, 1, 3): |3 - 2 + 1| / (2 + 0 + 0.2 (3 + 2 + 1)) = 2 / 3.2;
+    # (1, 3, 1): |1 - 6 + 1| / (2 + 2 + 0.2 (1 + 6 + 1)) = 4 / 5.6.  Along y every
+    # column is constant: 0.  Largest: 4 / 5.6.
+    from oracle.amr import indicator, lohner_indicator
+    row = np.array([1.0, 1.0, 3.0, 1.0])
+    vx = np.tile(row, (4, 1))[None]                        # [1, j, i]
+    U = np.zeros((1, 4, 4, 4))
+    U[:, 0] = 2.0
+    U[:, 1] = 2.0 * vx
+    U[:, 3] = 5.0
+    assert abs(indicator(U, kind="lohner_vx")[0] - 4.0 / 5.6) < 1e-15
+    # the same pattern along y gives the same value; constants give 0; scale-free
+    assert abs(lohner_indicator(np.swapaxes(vx, 1, 2))[0] - 4.0 / 5.6) < 1e-15
+    assert lohner_indicator(np.full((1, 4, 4), 3.7))[0] == 0.0
+    assert abs(lohner_indicator(-7.5 * vx)[0] - 4.0 / 5.6) < 1e-15
+    # a resolved tanh layer scores lower than the same layer on a four times coarser cell
+    x = np.array([-1.0, -np.sqrt(0.2), np.sqrt(0.2), 1.0])
+    fine = np.tanh(0.5 * x)[None, None, :].repeat(4, axis=1)
+    coarse = np.tanh(2.0 * x)[None, None, :].repeat(4, axis=1)
+    assert lohner_indicator(fine)[0] < lohner_indicator(coarse)[0]
+
+
 def test_single_flag_propagates_for_balance():
     # refining one fine cell next to a coarse neighbour forces the neighbour to refine
     cells = vortex_two_level_cells(3, 2, 6)             # levels 3 and 4
