@@ -135,6 +135,15 @@ perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32
  * for the disk |z + E - 1| <= E - 1). */
 perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a);
 
+/* Host utility (Sec. 4.3.1, Eq. PERKCoeffsConstruction) for any second-order
+ * stability polynomial, e.g. one optimised for a spectrum (Sec. 4.2): a[S]
+ * receives the a_{i+1,i} (layout of one row of perk_set_tableau's a) of the
+ * member with E evaluations in an S-stage family whose stability polynomial
+ * has the monomial coefficients alpha[0..E]; alpha[0..2] must be 1, 1, 1/2.
+ * The abscissae are those of perk_perk2_disk_tableau.  INVALID_ARG when a
+ * product in the construction vanishes. */
+perk_status perk_perk2_member(int S, int E, const double* alpha, double* a);
+
 /* Third-order members (Sec. 3.3, Eq. PERK_ThirdOrderShuOsher; Sec. 4.3.2).
  * perk_perk3_disk_alpha: monomial coefficients alpha[0..E] of a degree-E,
  * third-order polynomial stable on the largest disk |z + r| <= r among

@@ -47,6 +47,18 @@ def perk2_disk_tableau(E: Sequence[int], S: int | None = None):
     return np.array(c[:]), np.array(a[:]).reshape(R, S)
 
 
+def perk2_member(S: int, E: int, alpha) -> np.ndarray:
+    """a[S] (one row of a tableau) of the second-order member with E evaluations whose stability
+    polynomial has the monomial coefficients alpha[0..E] (alpha[0..2] = 1, 1, 1/2)."""
+    lib = _lib.load()
+    al = np.ascontiguousarray(alpha, dtype=np.float64)
+    if al.shape != (E + 1,):
+        raise ValueError(f"alpha must have E + 1 = {E + 1} coefficients")
+    a = (C.c_double * S)()
+    _check(lib, None, lib.perk_perk2_member(int(S), int(E), al.ctypes.data_as(C.POINTER(C.c_double)), a))
+    return np.array(a[:])
+
+
 def perk3_disk_alpha(E: int):
     """(alpha[0..E], r) of the library's third-order disk polynomial."""
     lib = _lib.load()

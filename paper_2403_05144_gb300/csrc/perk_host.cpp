@@ -940,6 +940,28 @@ perk_status perk_mesh_query(const perk_ctx* ctx, perk_mesh_info* info) {
   return PERK_OK;
 }
 
+namespace {
+// Eq. PERKCoeffsConstruction: the a_{i,i-1} of a second-order member with e stage evaluations
+// from the monomial coefficients alpha[0..e] of its stability polynomial; the coefficient of
+// z^{3+j} is c_{S-1-j} prod_{q=0}^{j} a_{S-q} (1-based stage indices), j = 0..e-3.
+// False if a product vanishes or a coefficient is not finite.
+bool perk2_member_from_alpha(int S, int e, const double* alpha, double* ar) {
+  for (int i = 0; i < S; ++i) ar[i] = 0.0;
+  double prod = 1.0;
+  for (int j = 0; j <= e - 3; ++j) {
+    const int stage = S - j;                    // 1-based stage whose a_{stage,stage-1} is found
+    const double cprev = (double)(stage - 2) / (2.0 * (S - 1));   // c_{stage-1}
+    const double den = cprev * prod;
+    if (!(den != 0.0)) return false;
+    const double v = alpha[3 + j] / den;
+    if (!std::isfinite(v)) return false;
+    ar[stage - 1] = v;                           // a[r*S + i] = a_{i+1,i}, i = stage - 1
+    prod *= v;
+  }
+  return true;
+}
+}  // namespace
+
 perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a) {
   if (S < 2 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !a) return PERK_E_INVALID_ARG;
   for (int r = 0; r < R; ++r)
@@ -954,18 +976,17 @@ perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, d
       alpha[k] = ((e - 1.0) / e) * binom / std::pow(e - 1.0, k);
       binom = binom * (e - k) / (k + 1);
     }
-    double* ar = a + (size_t)r * S;
-    for (int i = 0; i < S; ++i) ar[i] = 0.0;
-    // z^{3+j} coefficient = c_{S-1-j} prod_{q=0}^{j} a_{S-q} (1-based stage indices), j = 0..e-3
-    double prod = 1.0;
-    for (int j = 0; j <= e - 3; ++j) {
-      const int stage = S - j;                    // 1-based stage whose a_{stage,stage-1} is found
-      const double cprev = (double)(stage - 2) / (2.0 * (S - 1));   // c_{stage-1}
-      const double v = alpha[3 + j] / (cprev * prod);
-      ar[stage - 1] = v;                           // a[r*S + i] = a_{i+1,i}, i = stage - 1
-      prod *= v;
-    }
+    if (!perk2_member_from_alpha(S, e, alpha.data(), a + (size_t)r * S)) return PERK_E_INVALID_ARG;
   }
+  return PERK_OK;
+}
+
+perk_status perk_perk2_member(int S, int E, const double* alpha, double* a) {
+  if (S < 2 || S > MAX_S || E < 2 || E > S || !alpha || !a) return PERK_E_INVALID_ARG;
+  if (std::fabs(alpha[0] - 1.0) > 1e-12 || std::fabs(alpha[1] - 1.0) > 1e-12 || std::fabs(alpha[2] - 0.5) > 1e-12)
+    return fail(nullptr, PERK_E_INVALID_ARG, "alpha[0..2] must be 1, 1, 1/2 (second order)");
+  if (!perk2_member_from_alpha(S, E, alpha, a))
+    return fail(nullptr, PERK_E_INVALID_ARG, "the polynomial has no member of this form (a zero product)");
   return PERK_OK;
 }
 
