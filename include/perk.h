@@ -129,20 +129,36 @@ perk_status perk_mesh_query(const perk_ctx* ctx, perk_mesh_info* info);
 perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32_t* E, const double* c,
                              const double* a);
 
+/* Weights of the final update of a second-order tableau (Sec. 3.1):
+ * U_{n+1} = U_n + dt (b1 K_1 + bS K_S), b1 + bS = 1, bS > 0, with bS c_S = 1/2
+ * for the abscissae already set (INVALID_ARG otherwise; NOT_READY without a
+ * second-order tableau).  perk_set_tableau resets the weights to b = e_S
+ * (second order) or (1/6, ..., 1/6, 2/3) on K_1, K_{S-1}, K_S (third order).
+ * The step, its admissibility check and the step adjoint use them. */
+perk_status perk_set_weights(perk_ctx* ctx, double b1, double bS);
+
 /* Host utility (Sec. 4.3.1, Eq. PERKCoeffsConstruction): fills c[S] and
  * a[R*S] of a second-order family whose member r has the stability polynomial
  * P(z) = 1/E + ((E-1)/E)(1 + z/(E-1))^E, E = E[r] (the second-order optimum
  * for the disk |z + E - 1| <= E - 1). */
 perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a);
 
+/* The same family for the weights b_1 = 1 - bS, b_S = bS (0 < bS <= 1) of the
+ * variants in Sec. 3.1: abscissae c_i = (i-1)/(2 bS (S-1)), so c_S = 1/(2 bS)
+ * (bS = 1/2: Heun's weights, c_S = 1; bS = 3/4: Ralston's, c_S = 2/3); the
+ * construction divides the polynomial's coefficients by bS.  bS = 1 gives
+ * perk_perk2_disk_tableau.  Use with perk_set_weights. */
+perk_status perk_perk2_disk_tableau_weights(int S, int R, const int32_t* E, double bS, double* c, double* a);
+
 /* Host utility (Sec. 4.3.1, Eq. PERKCoeffsConstruction) for any second-order
  * stability polynomial, e.g. one optimised for a spectrum (Sec. 4.2): a[S]
  * receives the a_{i+1,i} (layout of one row of perk_set_tableau's a) of the
- * member with E evaluations in an S-stage family whose stability polynomial
- * has the monomial coefficients alpha[0..E]; alpha[0..2] must be 1, 1, 1/2.
- * The abscissae are those of perk_perk2_disk_tableau.  INVALID_ARG when a
- * product in the construction vanishes. */
-perk_status perk_perk2_member(int S, int E, const double* alpha, double* a);
+ * member with E evaluations in an S-stage family with weights b_1 = 1 - bS,
+ * b_S = bS whose stability polynomial has the monomial coefficients
+ * alpha[0..E]; alpha[0..2] must be 1, 1, 1/2.  The abscissae are those of
+ * perk_perk2_disk_tableau_weights.  INVALID_ARG when a product in the
+ * construction vanishes. */
+perk_status perk_perk2_member(int S, int E, double bS, const double* alpha, double* a);
 
 /* Third-order members (Sec. 3.3, Eq. PERK_ThirdOrderShuOsher; Sec. 4.3.2).
  * perk_perk3_disk_alpha: monomial coefficients alpha[0..E] of a degree-E,

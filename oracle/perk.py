@@ -40,22 +40,27 @@ def disk_polynomial_alpha(E: int) -> np.ndarray:
     return alpha
 
 
-def perk2_abscissae(S: int) -> np.ndarray:
-    return np.arange(S, dtype=np.float64) / (2.0 * (S - 1))
+def perk2_abscissae(S: int, b_S: float = 1.0) -> np.ndarray:
+    """c_i = c_S (i - 1)/(S - 1) with c_S = 1/(2 b_S): 1/2 for the weights b = e_S of
+    Eq. PERK_ButcherTableauClassic; the variants of Sec. 3.1 with b_1 = 1 - b_S take
+    c_S = 1 (Heun, b_S = 1/2) and c_S = 2/3 (Ralston, b_S = 3/4)."""
+    return np.arange(S, dtype=np.float64) / (2.0 * b_S * (S - 1))
 
 
-def perk2_free_coefficients(S: int, E: int, alpha: Sequence[float]) -> np.ndarray:
+def perk2_free_coefficients(S: int, E: int, alpha: Sequence[float], b_S: float = 1.0) -> np.ndarray:
     """a_{i,i-1} for i = 1..S (entries 0 where the member has no such entry),
     from alpha_3..alpha_E by Eq. PERKCoeffsConstruction:
-        a_{S-i} = alpha_{3+i} / (c_{S-i-1} prod_{j=0}^{i-1} a_{S-j}),  i = 0, ..., E-3.
+        a_{S-i} = alpha_{3+i} / (b_S c_{S-i-1} prod_{j=0}^{i-1} a_{S-j}),  i = 0, ..., E-3.
+    (The coefficient of z^k, k >= 2, of 1 + z b^T (I - zA)^{-1} 1 is b^T A^{k-1} 1, and only
+    b_S contributes because the first row of A is zero.)
     Returned array is indexed by the 1-based stage number (index 0 unused)."""
-    c = np.concatenate([[np.nan], perk2_abscissae(S)])   # 1-based c
+    c = np.concatenate([[np.nan], perk2_abscissae(S, b_S)])   # 1-based c
     a = np.zeros(S + 1)
     for i in range(0, E - 2):
         prod = 1.0
         for j in range(i):
             prod *= a[S - j]
-        a[S - i] = alpha[3 + i] / (c[S - i - 1] * prod)
+        a[S - i] = alpha[3 + i] / (b_S * c[S - i - 1] * prod)
     return a
 
 
@@ -78,17 +83,19 @@ class PERKFamily:
         return i == 0 or (i + 1) >= self.S - self.E[r] + 2
 
 
-def perk2_family(E_list: Sequence[int], S: int | None = None, alphas=None) -> PERKFamily:
-    """Second-order P-ERK family with members E_list (ascending) and S = max(E) stages."""
+def perk2_family(E_list: Sequence[int], S: int | None = None, alphas=None, b_S: float = 1.0) -> PERKFamily:
+    """Second-order P-ERK family with members E_list (ascending) and S = max(E) stages; weights
+    b_1 = 1 - b_S, b_S (b_S = 1: Eq. PERK_ButcherTableauClassic)."""
     E_list = [int(e) for e in E_list]
     S = S or max(E_list)
-    c = perk2_abscissae(S)
+    c = perk2_abscissae(S, b_S)
     b = np.zeros(S)
-    b[-1] = 1.0
+    b[-1] = b_S
+    b[0] += 1.0 - b_S
     A = []
     for r, E in enumerate(E_list):
         alpha = disk_polynomial_alpha(E) if alphas is None else np.asarray(alphas[r])
-        a_free = perk2_free_coefficients(S, E, alpha)
+        a_free = perk2_free_coefficients(S, E, alpha, b_S)
         M = np.zeros((S, S))
         for i1 in range(2, S + 1):                 # 1-based stage number
             ai = a_free[i1]

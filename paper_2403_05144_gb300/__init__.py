@@ -34,8 +34,9 @@ def reference_nodes(N: int = 3):
     return np.array(x[:]), np.array(w[:])
 
 
-def perk2_disk_tableau(E: Sequence[int], S: int | None = None):
-    """(c[S], a[R, S]) of the second-order family with disk-optimal members E (ascending)."""
+def perk2_disk_tableau(E: Sequence[int], S: int | None = None, b_S: float = 1.0):
+    """(c[S], a[R, S]) of the second-order family with disk-optimal members E (ascending) and
+    weights b_1 = 1 - b_S, b_S (1: the classic b = e_S; 1/2: Heun; 3/4: Ralston)."""
     lib = _lib.load()
     E = [int(e) for e in E]
     S = int(S or max(E))
@@ -43,11 +44,14 @@ def perk2_disk_tableau(E: Sequence[int], S: int | None = None):
     Ea = (C.c_int32 * R)(*E)
     c = (C.c_double * S)()
     a = (C.c_double * (R * S))()
-    _check(lib, None, lib.perk_perk2_disk_tableau(S, R, Ea, c, a))
+    if b_S == 1.0:
+        _check(lib, None, lib.perk_perk2_disk_tableau(S, R, Ea, c, a))
+    else:
+        _check(lib, None, lib.perk_perk2_disk_tableau_weights(S, R, Ea, C.c_double(b_S), c, a))
     return np.array(c[:]), np.array(a[:]).reshape(R, S)
 
 
-def perk2_member(S: int, E: int, alpha) -> np.ndarray:
+def perk2_member(S: int, E: int, alpha, b_S: float = 1.0) -> np.ndarray:
     """a[S] (one row of a tableau) of the second-order member with E evaluations whose stability
     polynomial has the monomial coefficients alpha[0..E] (alpha[0..2] = 1, 1, 1/2)."""
     lib = _lib.load()
@@ -55,7 +59,8 @@ def perk2_member(S: int, E: int, alpha) -> np.ndarray:
     if al.shape != (E + 1,):
         raise ValueError(f"alpha must have E + 1 = {E + 1} coefficients")
     a = (C.c_double * S)()
-    _check(lib, None, lib.perk_perk2_member(int(S), int(E), al.ctypes.data_as(C.POINTER(C.c_double)), a))
+    _check(lib, None, lib.perk_perk2_member(int(S), int(E), C.c_double(b_S),
+                                            al.ctypes.data_as(C.POINTER(C.c_double)), a))
     return np.array(a[:])
 
 
@@ -187,10 +192,15 @@ class PerkSolver:
         self.S = len(c)
         self.E = E
 
-    def set_perk2_disk(self, E: Sequence[int], S: int | None = None):
-        c, a = perk2_disk_tableau(E, S)
+    def set_perk2_disk(self, E: Sequence[int], S: int | None = None, b_S: float = 1.0):
+        c, a = perk2_disk_tableau(E, S, b_S)
         self.set_tableau(2, E, c, a)
+        if b_S != 1.0:
+            self.set_weights(1.0 - b_S, b_S)
         return c, a
+
+    def set_weights(self, b1: float, bS: float):
+        self._call(self.lib.perk_set_weights, C.c_double(b1), C.c_double(bS))
 
     def info(self) -> dict:
         inf = _lib.PerkMeshInfo()

@@ -62,7 +62,10 @@ SIGNATURES = [
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_perk2_disk_tableau", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double)]),
-    ("perk_perk2_member", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk_perk2_disk_tableau_weights", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.c_double,
+                                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk_perk2_member", C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk_set_weights", C.c_int, [C.c_void_p, C.c_double, C.c_double]),
     ("perk_partition", C.c_int, [C.c_void_p]),
     ("perk_perk3_disk_alpha", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_perk3_member", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),

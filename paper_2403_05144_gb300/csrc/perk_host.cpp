@@ -256,9 +256,10 @@ struct perk_ctx {
   double kappa() const { return prob.mu * prob.gamma / ((prob.gamma - 1.0) * prob.prandtl); }
   int32_t lmin = 0, lmax = 0;
 
-  // tableau
+  // tableau; weights of the final update U + dt (w_b1 K_1 + w_bp K_{S-1} + w_bs K_S)
   bool has_tab = false;
   int order = 2, S = 0, R = 0;
+  double w_b1 = 0.0, w_bp = 0.0, w_bs = 1.0;
   int32_t E[MAX_R] = {};
   std::vector<double> c, a;  // c[S], a[R*S]
 
@@ -708,15 +709,9 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
   double* Kbuf[3] = {ctx->d_K1.p, ctx->d_Ka.p, ctx->d_Kb.p};
   int prev = 0, cur = 0, prev_at_last = 0;
   UpdateArgs ua{};
-  if (ctx->order == 3) {
-    ua.b1 = 1.0 / 6.0;
-    ua.bp = 1.0 / 6.0;
-    ua.bs = 2.0 / 3.0;
-  } else {
-    ua.b1 = 0.0;
-    ua.bp = 0.0;
-    ua.bs = 1.0;
-  }
+  ua.b1 = ctx->w_b1;
+  ua.bp = ctx->w_bp;
+  ua.bs = ctx->w_bs;
   ua.U = d_U;
   ua.K1 = ctx->d_K1.p;
   ua.flag = ctx->d_flag.p;
@@ -942,16 +937,17 @@ perk_status perk_mesh_query(const perk_ctx* ctx, perk_mesh_info* info) {
 
 namespace {
 // Eq. PERKCoeffsConstruction: the a_{i,i-1} of a second-order member with e stage evaluations
-// from the monomial coefficients alpha[0..e] of its stability polynomial; the coefficient of
-// z^{3+j} is c_{S-1-j} prod_{q=0}^{j} a_{S-q} (1-based stage indices), j = 0..e-3.
+// from the monomial coefficients alpha[0..e] of its stability polynomial, for the weights
+// b_1 = 1 - bs, b_S = bs and abscissae c_i = (i-1)/(2 bs (S-1)); the coefficient of z^{3+j} is
+// bs c_{S-1-j} prod_{q=0}^{j} a_{S-q} (1-based stage indices), j = 0..e-3.
 // False if a product vanishes or a coefficient is not finite.
-bool perk2_member_from_alpha(int S, int e, const double* alpha, double* ar) {
+bool perk2_member_from_alpha(int S, int e, double bs, const double* alpha, double* ar) {
   for (int i = 0; i < S; ++i) ar[i] = 0.0;
   double prod = 1.0;
   for (int j = 0; j <= e - 3; ++j) {
     const int stage = S - j;                    // 1-based stage whose a_{stage,stage-1} is found
-    const double cprev = (double)(stage - 2) / (2.0 * (S - 1));   // c_{stage-1}
-    const double den = cprev * prod;
+    const double cprev = (double)(stage - 2) / (2.0 * bs * (S - 1));   // c_{stage-1}
+    const double den = bs * cprev * prod;
     if (!(den != 0.0)) return false;
     const double v = alpha[3 + j] / den;
     if (!std::isfinite(v)) return false;
@@ -963,10 +959,15 @@ bool perk2_member_from_alpha(int S, int e, const double* alpha, double* ar) {
 }  // namespace
 
 perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, double* a) {
-  if (S < 2 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !a) return PERK_E_INVALID_ARG;
+  return perk_perk2_disk_tableau_weights(S, R, E, 1.0, c, a);
+}
+
+perk_status perk_perk2_disk_tableau_weights(int S, int R, const int32_t* E, double bs, double* c, double* a) {
+  if (S < 2 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !a || !(bs > 0.0) || !(bs <= 1.0))
+    return PERK_E_INVALID_ARG;
   for (int r = 0; r < R; ++r)
     if (E[r] < 2 || E[r] > S || (r > 0 && E[r] < E[r - 1])) return PERK_E_INVALID_ARG;
-  for (int i = 0; i < S; ++i) c[i] = (double)i / (2.0 * (S - 1));
+  for (int i = 0; i < S; ++i) c[i] = (double)i / (2.0 * bs * (S - 1));
   for (int r = 0; r < R; ++r) {
     const int e = E[r];
     // coefficients of P(z) = 1/e + ((e-1)/e) (1 + z/(e-1))^e: alpha_k = ((e-1)/e) C(e,k) / (e-1)^k
@@ -976,16 +977,17 @@ perk_status perk_perk2_disk_tableau(int S, int R, const int32_t* E, double* c, d
       alpha[k] = ((e - 1.0) / e) * binom / std::pow(e - 1.0, k);
       binom = binom * (e - k) / (k + 1);
     }
-    if (!perk2_member_from_alpha(S, e, alpha.data(), a + (size_t)r * S)) return PERK_E_INVALID_ARG;
+    if (!perk2_member_from_alpha(S, e, bs, alpha.data(), a + (size_t)r * S)) return PERK_E_INVALID_ARG;
   }
   return PERK_OK;
 }
 
-perk_status perk_perk2_member(int S, int E, const double* alpha, double* a) {
-  if (S < 2 || S > MAX_S || E < 2 || E > S || !alpha || !a) return PERK_E_INVALID_ARG;
+perk_status perk_perk2_member(int S, int E, double bs, const double* alpha, double* a) {
+  if (S < 2 || S > MAX_S || E < 2 || E > S || !alpha || !a || !(bs > 0.0) || !(bs <= 1.0))
+    return PERK_E_INVALID_ARG;
   if (std::fabs(alpha[0] - 1.0) > 1e-12 || std::fabs(alpha[1] - 1.0) > 1e-12 || std::fabs(alpha[2] - 0.5) > 1e-12)
     return fail(nullptr, PERK_E_INVALID_ARG, "alpha[0..2] must be 1, 1, 1/2 (second order)");
-  if (!perk2_member_from_alpha(S, E, alpha, a))
+  if (!perk2_member_from_alpha(S, E, bs, alpha, a))
     return fail(nullptr, PERK_E_INVALID_ARG, "the polynomial has no member of this form (a zero product)");
   return PERK_OK;
 }
@@ -1225,6 +1227,9 @@ perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32
   ctx->order = order;
   ctx->S = S;
   ctx->R = R;
+  ctx->w_b1 = order == 3 ? 1.0 / 6.0 : 0.0;
+  ctx->w_bp = order == 3 ? 1.0 / 6.0 : 0.0;
+  ctx->w_bs = order == 3 ? 2.0 / 3.0 : 1.0;
   std::copy(E, E + R, ctx->E);
   ctx->c.assign(c, c + S);
   ctx->a.assign(a, a + (size_t)R * S);
@@ -1242,6 +1247,20 @@ perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32
   perk_status s = upload_coef(ctx);
   if (s != PERK_OK) return s;
   if (ctx->has_mesh) return run_partition(ctx);
+  return PERK_OK;
+}
+
+perk_status perk_set_weights(perk_ctx* ctx, double b1, double bs) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_tab || ctx->order != 2 || ctx->S < 2) return fail(ctx, PERK_E_NOT_READY, "needs a second-order tableau");
+  if (!(bs > 0.0) || !std::isfinite(b1) || std::fabs(b1 + bs - 1.0) > 1e-14)
+    return fail(ctx, PERK_E_INVALID_ARG, "weights must satisfy b1 + bS = 1, bS > 0");
+  if (std::fabs(bs * ctx->c[ctx->S - 1] - 0.5) > 1e-12)
+    return fail(ctx, PERK_E_INVALID_ARG, "second order needs bS c_S = 1/2 (c_S = %.17g)", ctx->c[ctx->S - 1]);
+  ctx->w_b1 = b1;
+  ctx->w_bp = 0.0;
+  ctx->w_bs = bs;
+  drop_graph(ctx);
   return PERK_OK;
 }
 
@@ -1496,9 +1515,9 @@ static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, 
   const size_t nd = (size_t)ctx->n_elem * ELEM;
   cudaStream_t st = ctx->stream;
   UpdateArgs ua{};
-  ua.b1 = ctx->order == 3 ? 1.0 / 6.0 : 0.0;
-  ua.bp = ctx->order == 3 ? 1.0 / 6.0 : 0.0;
-  ua.bs = ctx->order == 3 ? 2.0 / 3.0 : 1.0;
+  ua.b1 = ctx->w_b1;
+  ua.bp = ctx->w_bp;
+  ua.bs = ctx->w_bs;
   ua.U = d_U;
   ua.K1 = K;
   ua.Kp = K + (size_t)(ctx->S > 1 ? ctx->S - 2 : 0) * nd;   // K_{S-1}
@@ -1538,12 +1557,7 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
     PERK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   }
   // seed with the final update U_{n+1} = U_n + dt (b1 K_1 + b_{S-1} K_{S-1} + b_S K_S)
-  double b1 = 0.0, bp = 0.0, bs = 1.0;
-  if (ctx->order == 3) {
-    b1 = 1.0 / 6.0;
-    bp = 1.0 / 6.0;
-    bs = 2.0 / 3.0;
-  }
+  const double b1 = ctx->w_b1, bp = ctx->w_bp, bs = ctx->w_bs;
   double* lam_cur = ctx->d_lamKa.p;    // adjoint of K_i at the current stage i
   double* lam_prev = ctx->d_lamKb.p;   // adjoint of K_{i-1}, being accumulated
   double* lamK1 = ctx->d_lamK1.p;

@@ -173,3 +173,19 @@ def test_gradient_with_and_without_stored_stages():
     Jb, gb = gradient(s, U0, dt, 13, J, checkpoint_every=5, store_stages=False)
     assert float(Ja) == float(Jb)
     assert torch.equal(ga, gb)
+
+
+def test_step_vjp_with_heun_weights_matches_autodiff():
+    from oracle.perk import perk2_family as fam_of
+    cells = SMALL
+    m = TreeMesh(cells, -1.0, 2.0)
+    U = nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)
+    dt = max_wave_speed_dt(U, m.h, 3, 0.4)
+    lam = np.random.default_rng(14).normal(size=U.shape)
+    fam = fam_of([4, 8], b_S=0.5)
+    meth = element_methods(m.cells[:, 0], fam.R)
+    want = vjp_steps(TorchDGSEM(m, 3, "hllc"), U, lam, dt, fam, meth, 1)
+    s = solver_for(cells, -1.0, 2.0, "hllc")
+    s.set_perk2_disk([4, 8], b_S=0.5)
+    got = s.step_vjp(cuda(U), dt, cuda(lam)).cpu().numpy()
+    assert rel(got, want) < 1e-10

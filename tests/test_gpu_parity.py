@@ -219,3 +219,24 @@ def test_volume_block_sizes_give_identical_steps():
     assert torch.equal(U, outs[0])
     with pytest.raises(Exception):
         s.set_volume_blocks(3)
+
+
+@pytest.mark.parametrize("b_S", [0.5, 0.75])
+def test_heun_and_ralston_weighted_steps(b_S):
+    # the weight variants of Sec. 3.1 (b_1 = 1 - b_S) against the oracle's dense step
+    cells = vortex_two_level_cells()
+    m = TreeMesh(cells, -10.0, 20.0)
+    U0 = nodal_state(isentropic_vortex, cells, -10.0, 20.0, X3)
+    fam = perk2_family([4, 8], b_S=b_S)
+    meth = element_methods(m.cells[:, 0], fam.R)
+    dt = max_wave_speed_dt(U0, m.h, 3, 0.4)
+    s = solver_for(cells, -10.0, 20.0, "hll")
+    s.set_perk2_disk([4, 8], b_S=b_S)
+    U = torch.from_numpy(U0.copy()).cuda()
+    want = U0
+    dg = DGSEM(m, 3, "hll")
+    for _ in range(3):
+        s.step(U, dt)
+        want = prkm_step(dg.rhs, want, dt, fam, meth)
+    s.check()
+    assert np.max(np.abs(U.cpu().numpy() - want)) / np.max(np.abs(want)) < 1e-12

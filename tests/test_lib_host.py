@@ -132,3 +132,15 @@ def test_third_order_family_is_valid(lib, E_list):
         P = stability_polynomial(A, b)
         np.testing.assert_allclose(P[:E + 1], disk_polynomial3_alpha(E)[0], rtol=1e-9, atol=1e-18)
         assert np.all(np.abs(P[E + 1:]) < 1e-18)
+
+
+@pytest.mark.parametrize("b_S", [0.5, 0.75])
+def test_weighted_disk_tableau_matches_oracle(lib, b_S):
+    from paper_2403_05144_gb300 import perk2_disk_tableau
+    E = [4, 6, 10, 16]
+    c, a = perk2_disk_tableau(E, b_S=b_S)
+    fam = perk2_family(E, b_S=b_S)
+    np.testing.assert_allclose(c, fam.c, rtol=1e-15, atol=0)
+    for r, e in enumerate(E):
+        free = perk2_free_coefficients(fam.S, e, disk_polynomial_alpha(e), b_S)   # 1-based stage index
+        np.testing.assert_allclose(a[r, 1:], free[2:], rtol=2e-15, atol=0)

@@ -86,3 +86,27 @@ def test_disk_polynomial_stability_and_radius(E):
 def test_free_coefficients_are_zero_before_first_shared_stage():
     a = perk2_free_coefficients(16, 8, disk_polynomial_alpha(8))
     assert np.all(a[:11] == 0.0) and np.all(a[11:] > 0.0)
+
+
+@pytest.mark.parametrize("b_S,c2", [(0.5, 1.0), (0.75, 2.0 / 3.0)])
+def test_two_stage_weight_variants_are_heun_and_ralston(b_S, c2):
+    # S = E = 2 with b_1 = 1 - b_S: Heun's method (b = (1/2, 1/2), c_2 = 1) and Ralston's
+    # (b = (1/4, 3/4), c_2 = 2/3), the variants named in Sec. 3.1
+    from oracle.perk import perk2_family
+    fam = perk2_family([2], b_S=b_S)
+    np.testing.assert_allclose(fam.b, [1.0 - b_S, b_S], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(fam.c, [0.0, c2], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(fam.A[0], [[0.0, 0.0], [c2, 0.0]], rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("b_S", [0.5, 0.75])
+def test_weight_variants_keep_order_and_polynomial(b_S):
+    from oracle.perk import disk_polynomial_alpha, perk2_family, stability_polynomial
+    fam = perk2_family([4, 8, 16], b_S=b_S)
+    for r, E in enumerate(fam.E):
+        A = fam.A[r]
+        assert abs(fam.b.sum() - 1.0) < 1e-15 and abs(fam.b @ fam.c - 0.5) < 1e-15
+        np.testing.assert_allclose(A.sum(axis=1), fam.c, rtol=0, atol=1e-15)
+        P = stability_polynomial(A, fam.b)
+        np.testing.assert_allclose(P[: E + 1], disk_polynomial_alpha(E), rtol=1e-11, atol=1e-15)
+        assert np.all(np.abs(P[E + 1:]) < 1e-12)
