@@ -55,6 +55,11 @@ UNIT = "DoF-stage updates/s"
 # + 48 pairs x 44   (means' branches 9, reciprocal 5, quotients 3, two log-mean series 15, flux 12)
 # + 16 nodes x 6 pairs x 4 variables (accumulation) + 128 (lifting, Jacobian)
 VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
+# DRAM bytes per element-stage of the same kernel (two elements per block, stage state formed from
+# U_n, K_1, K_{i-1}), measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum = 8.07 MB for a
+# launch over 3,904 elements); the algorithmic minimum is the 4 x 512 B read of U_n, K_1, K_{i-1}
+# and the face fluxes (K_i stays in L2 within the launch)
+VOL_DRAM_BYTES_PER_ELEM = 8.073984e6 / 3904
 
 
 AMR_KH = dict(level_min=4, level_max=7, refine_above=0.1, coarsen_below=0.02)
@@ -487,7 +492,10 @@ def run_perk(args) -> None:
         "t_end": tend,
         "equal_error": equal_error,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / fma_flops, "traffic": None, "kernel": "k_volume",
+                     "frac": achieved / fma_flops,
+                     "traffic": VOL_DRAM_BYTES_PER_ELEM * acc.element_stages / max(vol_launches, 1),
+                     "traffic_note": "DRAM bytes per launch: ncu bytes per element-stage x element-stages "
+                                     "per launch", "kernel": "k_volume",
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
