@@ -142,6 +142,23 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(vals, world: int, device: str):
+    """Element-wise maximum of a list of timings over the ranks (identity for one rank)."""
+    if world == 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def replica_rate(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job rate of N independent replicas: every rank processes the same units, the job
+    takes the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -410,13 +427,6 @@ def run_perk(args) -> None:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(vals):
-        if world == 1:
-            return vals
-        t = torch.tensor(vals, dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return [float(v) for v in t]
-
     cycles0 = perk.amr_cycles
     with ClockSampler(local_rank) as clk:
         barrier()
@@ -427,9 +437,9 @@ def run_perk(args) -> None:
         barrier()
     perk.solver.check()
     full.solver.check()
-    ms, ms_full = max_over_ranks([ms, ms_full])
-    value = world * units / (ms * 1e-3)
-    value_full = world * units_full / (ms_full * 1e-3)
+    ms, ms_full = max_over_ranks([ms, ms_full], world, "cuda")
+    value = replica_rate(units, ms, world)
+    value_full = replica_rate(units_full, ms_full, world)
     info = perk.solver.info()
 
     # roofline of the volume kernel: CUDA events around every launch of K profiled steps
@@ -462,7 +472,7 @@ def run_perk(args) -> None:
         d2h += Uh.numel() * 8
     e1.record(st)
     torch.cuda.synchronize()
-    (ms_e2e,) = max_over_ranks([e0.elapsed_time(e1)])
+    (ms_e2e,) = max_over_ranks([e0.elapsed_time(e1)], world, "cuda")
 
     # wall time to t_end, P-ERK family against the full-RHS method (same S, same dt rule)
     tend = {"perk": run_to_t_end(torch, wl, wl["E"], args.t_end_budget),
@@ -502,7 +512,7 @@ def run_perk(args) -> None:
                      "work_per_element_stage": {"fp64_slots": VOL_SLOTS_PER_ELEM, "flops": 2 * VOL_SLOTS_PER_ELEM,
                                                 "note": "FMA-equivalent: every FP64 issue slot counted as 2 flops"},
                      "cuda_fp64_rates": {"div_per_s": div_s, "log_per_s": log_s}},
-        "e2e": {"value": world * units_e2e / (ms_e2e * 1e-3), "unit": UNIT,
+        "e2e": {"value": replica_rate(units_e2e, ms_e2e, world), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         # per step 2 launches per stage + the commit; per AMR cycle: indicator, transfer,
         # partition, two step-size reductions and the step-size store
