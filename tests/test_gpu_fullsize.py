@@ -15,7 +15,7 @@ from oracle.dgsem import DGSEM
 from oracle.perk import element_methods, perk2_family, prkm_step
 from oracle.treemesh import TreeMesh
 from perk_inputs import kelvin_helmholtz, nodal_state, shear_layer, uniform_cells
-from tests.gpu_common import X3, rel_err_per_var
+from tests.gpu_common import X3
 
 pytestmark = pytest.mark.gpu
 
@@ -75,9 +75,15 @@ def test_shear_layer_partitioned_rhs_at_bench_size():
     fam = perk2_family(E)                    # the members' activity pattern is the same at third order
     meth = element_methods(m.cells[:, 0], fam.R)
     full = NavierStokesDGSEM(m, 3, "hll", mu=1.0 / 2500.0, prandtl=0.72).rhs(U)
+    # the density right-hand side of this state vanishes analytically (rho = 1, v_x depends on y
+    # only, v_y on x only): its maximum is ~2e-6, the sum of cancelling flux terms of size ~1, so
+    # each variable is measured against at least 1e-3 of the largest variable's scale
+    scale = 1e-3 * np.max(np.abs(full))
     for i in (0, 9, 15):
         active = np.array([fam.active(int(r), i) for r in meth])
         got = s.rhs_active(i, torch.from_numpy(U).cuda(),
                            out=torch.from_numpy(np.full_like(U, 7.0)).cuda()).cpu().numpy()
         assert np.all(got[~active] == 7.0)
-        assert rel_err_per_var(got[active], full[active]) < 1e-12
+        for v in range(4):
+            den = max(np.max(np.abs(full[active][:, v])), scale)
+            assert np.max(np.abs(got[active][:, v] - full[active][:, v])) / den < 1e-12, (i, v)
