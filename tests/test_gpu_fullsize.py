@@ -75,16 +75,18 @@ def test_shear_layer_partitioned_rhs_at_bench_size():
     fam = perk2_family(E)                    # the members' activity pattern is the same at third order
     meth = element_methods(m.cells[:, 0], fam.R)
     full = NavierStokesDGSEM(m, 3, "hll", mu=1.0 / 2500.0, prandtl=0.72).rhs(U)
-    # the density right-hand side of this state vanishes analytically (rho = 1, v_x depends on y
-    # only, v_y on x only): it is rounding noise of ~1e-13 on both sides, left by cancelling flux
-    # terms as large as the momentum ones, so every variable is measured against the largest
-    # variable's scale
-    scale = np.max(np.abs(full))
+    # The right-hand side is a sum of derivative terms of size up to (2/h) |f(u)|.  In this
+    # low-Mach state they cancel almost completely: the pressure (~7.9) has no gradient at t = 0
+    # and the density RHS vanishes analytically (rho = 1, v_x depends on y only, v_y on x only),
+    # so what remains (momentum RHS <= 5, density RHS ~1e-13) is far below the terms whose
+    # rounding it carries (~1e-11 absolute).  Errors are therefore measured against the scale of
+    # the derivative terms, (2/h_min) max |u|; a wrong term would be 1e-3 of that, not 1e-12.
+    scale = (2.0 / m.h.min()) * np.max(np.abs(U))
     for i in (0, 9, 15):
         active = np.array([fam.active(int(r), i) for r in meth])
         got = s.rhs_active(i, torch.from_numpy(U).cuda(),
                            out=torch.from_numpy(np.full_like(U, 7.0)).cuda()).cpu().numpy()
         assert np.all(got[~active] == 7.0)
-        for v in range(4):
-            den = max(np.max(np.abs(full[active][:, v])), scale)
-            assert np.max(np.abs(got[active][:, v] - full[active][:, v])) / den < 1e-12, (i, v)
+        assert np.max(np.abs(got[active] - full[active])) / scale < 1e-12, i
+        # and against the RHS itself where it is not a cancellation remainder (energy)
+        assert np.max(np.abs(got[active][:, 3] - full[active][:, 3])) / np.max(np.abs(full[:, 3])) < 1e-10
