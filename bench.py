@@ -712,8 +712,8 @@ def run_spectrum(args) -> None:
     Jacobian assembled by the JVP kernels and its eigendecomposition, scaled to the finest cells,
     joined with the Ritz values of 500 Arnoldi steps on the full mesh.  Members {4, 6, 10, 16}
     optimised for it.  Stability by experiment: a step size is stable when a seeded 1e-8 nodal
-    perturbation of the state does not grow more than a hundredfold in 400 steps; the largest
-    stable step of each family is found by bisection."""
+    perturbation of the state does not grow more than tenfold in 1,000 steps (a growth factor
+    per step below 1.0023); the largest stable step of each family is found by bisection."""
     import torch
 
     from paper_2403_05144_gb300 import PerkError, PerkSolver, perk2_disk_tableau, reference_nodes
@@ -765,7 +765,7 @@ def run_spectrum(args) -> None:
     dt_rule = sf.compute_dt(U0, wl["cfl"])
     noise = 1e-8 * torch.from_numpy(np.random.default_rng(20240308 + 6).normal(size=U0.shape)).cuda()
 
-    def stable(cc, aa, dt, n=400):
+    def stable(cc, aa, dt, n=1000):
         runs = []
         for U in (U0.clone(), U0 + noise):
             sv = PerkSolver(surface_flux="hllc")
@@ -779,7 +779,7 @@ def run_spectrum(args) -> None:
                 return False
             runs.append(U)
         growth = float((runs[1] - runs[0]).abs().max()) / float(noise.abs().max())
-        return bool(np.isfinite(growth) and growth <= 100.0)
+        return bool(np.isfinite(growth) and growth <= 10.0)
 
     def largest_stable(cc, aa, guess):
         lo, hi = 0.0, guess
@@ -803,13 +803,13 @@ def run_spectrum(args) -> None:
     emp_disk = largest_stable(*perk2_disk_tableau(E), dt_fam_disk)
     times["stability_search_s"] = time.perf_counter() - t0
     line = {"metric": "spectrum-optimised P-ERK2 family: largest stable step relative to the disk polynomials",
-            "value": emp_opt / emp_disk, "unit": "x disk-family dt", "n_gpus": 1, "steps": 400,
+            "value": emp_opt / emp_disk, "unit": "x disk-family dt", "n_gpus": 1, "steps": 1000,
             "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "kelvin_helmholtz_initially_adapted_mesh_smooth_state", "n_elem": len(cells),
                        "family": E, "reduced_mesh": f"uniform level {red_level} ({len(red)} cells, {J.shape[0]} unknowns)",
                        "arnoldi_steps": 500, "boundary_points": len(sigma),
-                       "stable": "a 1e-8 nodal perturbation grows at most 100x in 400 steps, no rejected step"},
+                       "stable": "a 1e-8 nodal perturbation grows at most 10x in 1000 steps, no rejected step"},
             "predicted": {"dt_member_optimised": list(map(float, dt_opt)), "dt_member_disk": dt_disk,
                           "dt_family_optimised": dt_fam_opt, "dt_family_disk": dt_fam_disk,
                           "ratio": dt_fam_opt / dt_fam_disk},
