@@ -69,3 +69,25 @@ def test_dense_jacobian_of_a_linear_map():
         return torch.tensor(A) @ U.reshape(-1)
 
     np.testing.assert_allclose(dense_jacobian(rhs, np.zeros(6)), A, rtol=0, atol=1e-15)
+
+
+def test_cfl_reading_of_the_disk_polynomials():
+    # the stable CFL of member E (time-step rule of the runs) on the dense spectrum of the
+    # oracle's Jacobian: 2 x 2 periodic cells, N = 3, HLLC, smooth seeded state, modes with
+    # Re > 0 left out; the numbers recorded as a reading of Sec. 4.1
+    from oracle.autodiff import TorchDGSEM
+    from oracle.lgl import lgl_nodes_weights
+    from oracle.perk import disk_polynomial_alpha, max_wave_speed_dt
+    from oracle.treemesh import TreeMesh
+    from perk_inputs import smooth_random_state, uniform_cells
+    x, _ = lgl_nodes_weights(3)
+    cells = uniform_cells(1)
+    m = TreeMesh(cells, -1.0, 2.0)
+    U = smooth_random_state(cells, -1.0, 2.0, x)
+    ev = np.linalg.eigvals(dense_jacobian(lambda V: TorchDGSEM(m, 3, "hllc").rhs(V), U))
+    ev = ev[ev.real <= 1e-12]
+    dt1 = max_wave_speed_dt(U, m.h, 3, 1.0)
+    for E, cfl in ((4, 1.15), (16, 2.25)):
+        al = disk_polynomial_alpha(E)
+        modulus = lambda c: np.max(np.abs(np.polyval(al[::-1], c * dt1 * ev)))
+        assert modulus(0.99 * cfl) <= 1.0 + 1e-10 < modulus(1.01 * cfl)
