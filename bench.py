@@ -12,7 +12,8 @@ and dt) on the same GPU, the accuracy of both against a reference solution,
 the roofline of the dominant kernel against the measured FP64 rate, the
 end-to-end rate through the public API with host buffers, and the CPU oracle
 on a bounded sample.  Workloads: kh (default: Kelvin-Helmholtz with dynamic
-AMR), vortex (static two-level isentropic vortex), shear (Navier-Stokes shear
+AMR), vortex (static two-level isentropic vortex, 448 cells), vortex_large (the same
+pattern at 114,688 cells, the roofline case), shear (Navier-Stokes shear
 layer, third order, dynamic AMR), ensemble (64 KH members in one context),
 adjoint (discrete-adjoint gradient over 200 steps), spectrum (spectrum-optimised
 stability polynomials against the disk polynomials).
@@ -82,6 +83,13 @@ def workload(name: str) -> dict:
                     ic=shear_layer, E=[4, 8, 16], order=3, flux="hll", cfl=SHEAR_CFL, t_end=1.2,
                     equations="navier_stokes", mu=1.0 / 2500.0, prandtl=0.72, amr=AMR_SHEAR, n_amr=20,
                     init_cycles=2)
+    if name == "vortex_large":
+        # the same two-level pattern scaled up to saturate the GPU: base 256 x 256 with the central
+        # 128 x 128 block refined once (114,688 cells, 1.8M DoF), P-ERK2 {4, 8}, HLL
+        return dict(name="isentropic_vortex_256x256_center128x128_refined",
+                    cells=vortex_two_level_cells(base_level=8, lo=64, hi=192), x0=-10.0, L=20.0,
+                    ic=isentropic_vortex, E=[4, 8], flux="hll", cfl=0.5, t_end=20.0, amr=None, n_amr=0,
+                    init_cycles=0)
     if name == "vortex":
         # isentropic vortex, 16x16 base with the central 8x8 block refined (static), P-ERK2 {4, 8}, HLL
         return dict(name="isentropic_vortex_16x16_center8x8_refined", cells=vortex_two_level_cells(), x0=-10.0,
@@ -354,11 +362,26 @@ def oracle_stage_sample(wl: dict, cells, U: np.ndarray, n_stages: int = 0, budge
     return units, sec, k, fam.S
 
 
+def host_cpu() -> dict:
+    """The host's logical core count and CPU model (from /proc/cpuinfo where present)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(wl: dict, cells, U0: np.ndarray, dt: float) -> dict:
     """The oracle as it stands, on a bounded sample of the same workload: partitioned stage
     evaluations of the workload's current mesh for about ten seconds."""
     units, sec, k, S = oracle_stage_sample(wl, cells, U0)
-    return {"value": units / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": units / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"{k} partitioned stage evaluations (stages 0.. of S={S}, cycling) of the workload's "
                       f"current mesh ({len(cells)} cells), {sec:.1f} s, numpy float64 on one host thread"}
 
@@ -371,8 +394,8 @@ def run_reference(args) -> None:
     from oracle.lgl import lgl_nodes_weights
     from oracle.treemesh import TreeMesh
 
-    if args.workload not in ("kh", "vortex", "shear"):
-        raise SystemExit("--impl reference times the oracle on the kh, vortex or shear workload")
+    if args.workload not in ("kh", "vortex", "vortex_large", "shear"):
+        raise SystemExit("--impl reference times the oracle on the kh, vortex, vortex_large or shear workload")
     wl = workload(args.workload)
     x, _ = lgl_nodes_weights(3)
     cells = wl["cells"]
@@ -393,7 +416,7 @@ def run_reference(args) -> None:
             "config": {"workload": wl["name"], "n_elem": len(cells), "family": wl["E"],
                        "surface_flux": wl["flux"],
                        "step": "one partitioned stage evaluation of the oracle on the initially adapted mesh"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"{args.steps} stage evaluations (cycling over the S={S} stages) "
                                        f"of the {len(cells)}-cell initially adapted mesh"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -834,7 +857,8 @@ def main():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="perk", choices=["perk", "reference"])
-    p.add_argument("--workload", default="kh", choices=["kh", "vortex", "shear", "ensemble", "adjoint", "spectrum"])
+    p.add_argument("--workload", default="kh",
+                   choices=["kh", "vortex", "vortex_large", "shear", "ensemble", "adjoint", "spectrum"])
     p.add_argument("--t-end-budget", type=float, default=60.0, help="wall seconds per run to t_end")
     args = p.parse_args()
     if args.warmup < 3:
