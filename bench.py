@@ -114,8 +114,11 @@ class Run:
             c, a = perk3_disk_tableau(E)
             self.solver.set_tableau(3, E, c, a)
         else:
-            c, a = perk2_disk_tableau(E, max(wl["E"]))
+            b_S = wl.get("b_S", 1.0)
+            c, a = perk2_disk_tableau(E, max(wl["E"]), b_S)
             self.solver.set_tableau(2, E, c, a)
+            if b_S != 1.0:
+                self.solver.set_weights(1.0 - b_S, b_S)
         self.x, _ = reference_nodes(3)
         self.U = self._sample()
         for _ in range(wl["init_cycles"]):          # initial adaptation on the initial condition itself
@@ -298,17 +301,21 @@ def equal_error_vortex(torch) -> dict:
 
 
 def equal_error_kh(torch, t_end: float = 0.5) -> dict:
-    """Density errors at t = 0.5 of the P-ERK2 family and of the full-RK method (same dt) against
-    the full-RK method at dt/4, all on the frozen initially adapted KH mesh (the flow is chaotic
-    later, so only this early window is compared)."""
+    """Density errors at t = 0.5 of the P-ERK2 family (weights b = e_S, and the Heun and Ralston
+    variants of Sec. 3.1) and of the full-RK method (same dt) against the full-RK method at dt/4,
+    all on the frozen initially adapted KH mesh (the flow is chaotic later, so only this early
+    window is compared)."""
     wl = dict(workload("kh"))
     runs = {}
     base = Run(torch, wl, wl["E"])
     cells, U0 = base.solver.cells.copy(), base.U.clone()
     dt0 = base.dt
     frozen = dict(wl, amr=None, cells=cells, init_cycles=0)
-    for name, E, div in (("perk", wl["E"], 1), ("full_rk", [max(wl["E"])], 1), ("reference", [max(wl["E"])], 4)):
-        run = Run(torch, frozen, E)
+    cases = (("perk", wl["E"], 1, 1.0), ("perk_heun_weights", wl["E"], 1, 0.5),
+             ("perk_ralston_weights", wl["E"], 1, 0.75), ("full_rk", [max(wl["E"])], 1, 1.0),
+             ("reference", [max(wl["E"])], 4, 1.0))
+    for name, E, div, b_S in cases:
+        run = Run(torch, dict(frozen, b_S=b_S), E)
         run.U = U0.clone()
         n = div * math.ceil(t_end / dt0)
         run.dt = t_end / n
@@ -318,7 +325,7 @@ def equal_error_kh(torch, t_end: float = 0.5) -> dict:
         runs[name] = run
     ref = runs["reference"].U.cpu().numpy()
     out = {k: {**density_errors(torch, runs[k].solver, runs[k].U, ref, wl["x0"], wl["L"]), "dt": runs[k].dt}
-           for k in ("perk", "full_rk")}
+           for k in ("perk", "perk_heun_weights", "perk_ralston_weights", "full_rk")}
     out["ratio_l1"] = out["perk"]["l1"] / out["full_rk"]["l1"]
     out["ratio_linf"] = out["perk"]["linf"] / out["full_rk"]["linf"]
     out["t_end"] = t_end
