@@ -31,7 +31,7 @@ from . import euler
 from .lgl import derivative_matrix, lagrange_eval, l2_project_two_halves, lgl_nodes_weights
 from .treemesh import TreeMesh
 
-SURFACE_FLUXES = {"hll": euler.hll_flux, "hllc": euler.hllc_flux, "ec": euler.ec_flux}
+SURFACE_FLUXES = {"hll": euler.hll_flux, "hllc": euler.hllc_flux, "ec": euler.ec_flux, "hlle": euler.hlle_flux}
 
 
 class DGSEM:

@@ -102,6 +102,34 @@ def hll_flux(uL, uR, direction: int, gamma=GAMMA):
     return np.where(SL >= 0.0, fL, np.where(SR <= 0.0, fR, mid))
 
 
+def einfeldt_speeds(uL, uR, direction: int, gamma=GAMMA):
+    """Einfeldt's bounds (1988): S_L = min(v_L - c_L, v~ - c~), S_R = max(v_R + c_R, v~ + c~), with
+    the Roe averages v~ = (sqrt(rho_L) v_L + sqrt(rho_R) v_R)/(sqrt(rho_L) + sqrt(rho_R)) (both
+    components), H~ likewise for the enthalpy H = (E + p)/rho, c~^2 = (gamma - 1)(H~ - |v~|^2/2)."""
+    rL, v1L, v2L, pL = primitives(uL, gamma)
+    rR, v1R, v2R, pR = primitives(uR, gamma)
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    wL, wR = sL / (sL + sR), sR / (sL + sR)
+    v1 = wL * v1L + wR * v1R
+    v2 = wL * v2L + wR * v2R
+    H = wL * (uL[3] + pL) / rL + wR * (uR[3] + pR) / rR
+    c = np.sqrt((gamma - 1.0) * (H - 0.5 * (v1 * v1 + v2 * v2)))
+    vL, vR, vm = (v1L, v1R, v1) if direction == 0 else (v2L, v2R, v2)
+    cL = np.sqrt(gamma * pL / rL)
+    cR = np.sqrt(gamma * pR / rR)
+    return np.minimum(vL - cL, vm - c), np.maximum(vR + cR, vm + c)
+
+
+def hlle_flux(uL, uR, direction: int, gamma=GAMMA):
+    """HLL flux with Einfeldt's wave-speed bounds (HLLE, the surface flux of the paper's
+    shock-capturing runs, Sec. 7.2)."""
+    SL, SR = einfeldt_speeds(uL, uR, direction, gamma)
+    fL = physical_flux(uL, direction, gamma)
+    fR = physical_flux(uR, direction, gamma)
+    mid = (SR * fL - SL * fR + SL * SR * (uR - uL)) / (SR - SL)
+    return np.where(SL >= 0.0, fL, np.where(SR <= 0.0, fR, mid))
+
+
 def hllc_flux(uL, uR, direction: int, gamma=GAMMA):
     """HLLC flux (Toro, Spruce, Speares 1994; Toro's textbook, Sec. 10.4) with
     the Davis speeds S_L, S_R and the contact speed
