@@ -40,7 +40,20 @@ typedef enum {
   PERK_E_OOM = 6          /* device allocation failed */
 } perk_status;
 
-typedef enum { PERK_SURFACE_HLL = 0, PERK_SURFACE_HLLC = 1, PERK_SURFACE_EC = 2 } perk_surface_flux;
+/* Surface fluxes: HLL with Davis' wave speeds, HLLC (Toro), the entropy-conservative two-point
+ * flux, and HLLE (HLL with Einfeldt's Roe-averaged bounds, the flux of the paper's
+ * shock-capturing runs, Sec. 7.2). */
+typedef enum { PERK_SURFACE_HLL = 0, PERK_SURFACE_HLLC = 1, PERK_SURFACE_EC = 2, PERK_SURFACE_HLLE = 3 } perk_surface_flux;
+
+/* Subcell shock capturing of the volume term (Sec. 7.2; Hennemann, Rueda-Ramirez, Hindenlang
+ * and Gassner 2021).  Per element, from the nodal indicator variable epsilon (rho p, or rho as
+ * in the paper's KH run): its orthonormal-Legendre modes m_ab, the shares of the highest mode
+ * shells, energy = max(E_{max(a,b)=N} / E_all, E_{max(a,b)=N-1} / E_{max(a,b)<=N-1}), and the
+ * blending factor alpha = 1 / (1 + exp(-(s/T)(energy - T))), T = 0.5 10^(-1.8 (N+1)^(1/4)),
+ * s = ln((1 - 1e-4)/1e-4), set to 0 below 1e-3 and capped at alpha_max.  The volume term becomes
+ * (1 - alpha) (flux differencing) + alpha (first-order finite volumes on the LGL subcells, the
+ * surface flux between neighbouring nodes); the surface term is unchanged. */
+typedef enum { PERK_SHOCK_OFF = 0, PERK_SHOCK_DENSITY_PRESSURE = 1, PERK_SHOCK_DENSITY = 2 } perk_shock;
 
 /* Equations: compressible Euler, or Navier-Stokes with BR1 viscous terms
  * (Sec. 7.1; gradients of (v1, v2, T = p/rho), central lifting and viscous
@@ -58,6 +71,8 @@ typedef struct {
   int equations;         /* perk_equations */
   double mu;             /* dynamic viscosity (Navier-Stokes), > 0 */
   double prandtl;        /* Prandtl number (Navier-Stokes), > 0 */
+  int shock_capturing;   /* perk_shock; PERK_SHOCK_OFF (0) for the plain volume term */
+  double alpha_max;      /* cap of the blending factor, in (0, 1] when shock capturing is on */
 } perk_problem;
 
 /* Creates a context on the current CUDA device.  *out receives the handle. */

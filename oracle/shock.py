@@ -4,7 +4,8 @@ The paper's hyperbolic runs (Sec. 7.2) blend the flux-differencing volume term w
 first-order finite-volume term on the LGL subcells of each element (Hennemann, Rueda-Ramirez,
 Hindenlang and Gassner, J. Comput. Phys. 2021), element by element:
 
-1. Indicator.  epsilon = rho p at the nodes, written in the orthonormal Legendre basis
+1. Indicator.  epsilon = rho p at the nodes (Hennemann et al.'s variable; the paper's KH run
+   bases it on the density, epsilon = rho, Sec. 7.2.1), written in the orthonormal Legendre basis
    (modes a along x, b along y): m = V^{-1} epsilon V^{-T}, V_ik = L_k(x_i).  With
    E_k = sum_{max(a,b) <= k} m_ab^2, the share of the highest modes is
        energy = max((E_N - E_{N-1}) / E_N, (E_{N-1} - E_{N-2}) / E_{N-1}).
@@ -30,6 +31,7 @@ import numpy as np
 from numpy.polynomial import legendre as npleg
 
 from . import euler
+from .br1 import NavierStokesDGSEM
 from .dgsem import DGSEM
 
 ALPHA_MIN = 1e-3
@@ -48,11 +50,12 @@ def legendre_vandermonde(x: np.ndarray) -> np.ndarray:
 
 
 def blending_factor(U: np.ndarray, x: np.ndarray, gamma: float = euler.GAMMA,
-                    alpha_max: float = ALPHA_MAX) -> np.ndarray:
-    """alpha per element of the nodal state U [e, 4, j, i] (step 1 above)."""
+                    alpha_max: float = ALPHA_MAX, variable: str = "density_pressure") -> np.ndarray:
+    """alpha per element of the nodal state U [e, 4, j, i] (step 1 above); variable is
+    "density_pressure" (epsilon = rho p) or "density" (epsilon = rho)."""
     N = len(x) - 1
     rho, _, _, p = euler.primitives(np.moveaxis(U, 1, 0), gamma)
-    eps = rho * p                                                   # [e, j, i]
+    eps = rho * p if variable == "density_pressure" else rho        # [e, j, i]
     Vinv = np.linalg.inv(legendre_vandermonde(x))
     m = np.einsum("bj,eji,ai->eba", Vinv, eps, Vinv)                # modes [e, b, a]
     a_idx = np.arange(N + 1)
@@ -87,18 +90,38 @@ def finite_volume_term(V: np.ndarray, w: np.ndarray, fstar, gamma: float = euler
     return out
 
 
+def blended_volume(dg: DGSEM, V: np.ndarray, alpha_max: float, variable: str) -> np.ndarray:
+    """Step 3 for the scheme dg (its flux-differencing volume term, nodes, weights and surface
+    flux); V = [4, e, j, i]."""
+    vol = DGSEM._volume(dg, V)
+    alpha = blending_factor(np.moveaxis(V, 0, 1), dg.x, dg.gamma, alpha_max, variable)
+    fv = finite_volume_term(V, dg.w, dg.fstar, dg.gamma)
+    a = alpha[None, :, None, None]
+    return (1.0 - a) * vol + a * fv
+
+
 class ShockCapturingDGSEM(DGSEM):
     """The DGSEM of dgsem.py with the blended volume term (steps 1-3); the subcells use the
     surface flux of the scheme."""
 
     def __init__(self, mesh, N: int = 3, surface_flux: str = "hlle", gamma: float = euler.GAMMA,
-                 alpha_max: float = ALPHA_MAX, chunk: int = 4096):
+                 alpha_max: float = ALPHA_MAX, variable: str = "density_pressure", chunk: int = 4096):
         super().__init__(mesh, N, surface_flux, gamma, chunk)
         self.alpha_max = alpha_max
+        self.variable = variable
 
     def _volume(self, V: np.ndarray) -> np.ndarray:
-        dg = super()._volume(V)
-        alpha = blending_factor(np.moveaxis(V, 0, 1), self.x, self.gamma, self.alpha_max)
-        fv = finite_volume_term(V, self.w, self.fstar, self.gamma)
-        a = alpha[None, :, None, None]
-        return (1.0 - a) * dg + a * fv
+        return blended_volume(self, V, self.alpha_max, self.variable)
+
+
+class ShockCapturingNavierStokesDGSEM(NavierStokesDGSEM):
+    """The Navier-Stokes DGSEM of br1.py with the blended inviscid volume term."""
+
+    def __init__(self, mesh, N: int = 3, surface_flux: str = "hlle", gamma: float = euler.GAMMA, mu: float = 1e-3,
+                 prandtl: float = 0.72, alpha_max: float = ALPHA_MAX, variable: str = "density_pressure"):
+        super().__init__(mesh, N, surface_flux, gamma, mu, prandtl)
+        self.alpha_max = alpha_max
+        self.variable = variable
+
+    def _volume(self, V: np.ndarray) -> np.ndarray:
+        return blended_volume(self, V, self.alpha_max, self.variable)

@@ -124,7 +124,10 @@ class PerkSolver:
     """One libperk context: mesh, partition, coefficient table and stage buffers."""
 
     def __init__(self, gamma: float = 1.4, surface_flux: str = "hll", use_graph: bool = True, N: int = 3,
-                 equations: str = "euler", mu: float = 0.0, prandtl: float = 0.72):
+                 equations: str = "euler", mu: float = 0.0, prandtl: float = 0.72, shock_capturing=None,
+                 alpha_max: float = 0.5):
+        """shock_capturing: None, "density_pressure" or "density" (the indicator variable of the
+        subcell blending of the volume term)."""
         import torch
 
         if not torch.cuda.is_available():
@@ -132,7 +135,8 @@ class PerkSolver:
         self.torch = torch
         self.lib = _lib.load()
         eq = {"euler": 0, "navier_stokes": 1}[equations]
-        prob = _lib.PerkProblem(N, gamma, _lib.SURFACE[surface_flux], 1 if use_graph else 0, eq, mu, prandtl)
+        prob = _lib.PerkProblem(N, gamma, _lib.SURFACE[surface_flux], 1 if use_graph else 0, eq, mu, prandtl,
+                                _lib.SHOCK[shock_capturing], alpha_max)
         h = C.c_void_p()
         torch.cuda.init()
         _check(self.lib, None, self.lib.perk_create(C.byref(prob), C.byref(h)))

@@ -13,12 +13,14 @@ from .build import LIB
 
 PERK_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NONFINITE", 4: "TIMEOUT", 5: "NOT_READY", 6: "OOM"}
-SURFACE = {"hll": 0, "hllc": 1, "ec": 2}
+SURFACE = {"hll": 0, "hllc": 1, "ec": 2, "hlle": 3}
+SHOCK = {None: 0, "density_pressure": 1, "density": 2}
 
 
 class PerkProblem(C.Structure):
     _fields_ = [("N", C.c_int), ("gamma", C.c_double), ("surface_flux", C.c_int), ("use_graph", C.c_int),
-                ("equations", C.c_int), ("mu", C.c_double), ("prandtl", C.c_double)]
+                ("equations", C.c_int), ("mu", C.c_double), ("prandtl", C.c_double), ("shock_capturing", C.c_int),
+                ("alpha_max", C.c_double)]
 
 
 class PerkMeshInfo(C.Structure):

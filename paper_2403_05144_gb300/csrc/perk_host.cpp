@@ -118,10 +118,36 @@ bool invert4(const double A[NN][NN], double inv[NN][NN]) {
   return true;
 }
 
-Ops build_ops(double gamma, int surface_flux) {
+Ops build_ops(double gamma, int surface_flux, int shock = PERK_SHOCK_OFF, double alpha_max = 0.5) {
   Ops o{};
   std::vector<double> x, w;
   lgl(NN - 1, x, w);
+  // shock capturing: V_ik = L_k(x_i) sqrt(k + 1/2) (orthonormal Legendre), its inverse, 1/w_i
+  o.shock = shock;
+  o.alpha_max = alpha_max;
+  {
+    double V[NN][NN];
+    for (int i = 0; i < NN; ++i) {
+      double p0 = 1.0, p1 = x[i];
+      for (int k = 0; k < NN; ++k) {
+        double pk;
+        if (k == 0) {
+          pk = 1.0;
+        } else if (k == 1) {
+          pk = x[i];
+        } else {
+          pk = ((2.0 * k - 1.0) * x[i] * p1 - (k - 1.0) * p0) / k;   // Bonnet's recursion
+          p0 = p1;
+          p1 = pk;
+        }
+        V[i][k] = pk * std::sqrt(k + 0.5);
+      }
+    }
+    invert4(V, o.vinv);
+    for (int i = 0; i < NN; ++i) o.inv_w[i] = 1.0 / w[i];
+    o.sc_T = 0.5 * std::pow(10.0, -1.8 * std::pow((double)NN, 0.25));
+    o.sc_s_over_T = std::log((1.0 - 1e-4) / 1e-4) / o.sc_T;
+  }
   // derivative matrix from barycentric weights: D_ij = (lam_j / lam_i) / (x_i - x_j), rows sum to 0
   double lam[NN];
   for (int j = 0; j < NN; ++j) {
@@ -253,6 +279,7 @@ struct perk_ctx {
   // Navier-Stokes (BR1) work space
   DevBuf<double> d_wsurf, d_q, d_vsurf;
   bool viscous() const { return prob.equations == PERK_NAVIER_STOKES; }
+  bool differentiable() const { return prob.shock_capturing == PERK_SHOCK_OFF && prob.surface_flux != PERK_SURFACE_HLLE; }
   double kappa() const { return prob.mu * prob.gamma / ((prob.gamma - 1.0) * prob.prandtl); }
   int32_t lmin = 0, lmax = 0;
 
@@ -775,7 +802,10 @@ extern "C" {
 perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   if (!prob || !out) return PERK_E_INVALID_ARG;
   *out = nullptr;
-  if (prob->N != 3 || !(prob->gamma > 1.0) || prob->surface_flux < 0 || prob->surface_flux > 2)
+  if (prob->N != 3 || !(prob->gamma > 1.0) || prob->surface_flux < 0 || prob->surface_flux > 3)
+    return PERK_E_INVALID_ARG;
+  if (prob->shock_capturing < PERK_SHOCK_OFF || prob->shock_capturing > PERK_SHOCK_DENSITY) return PERK_E_INVALID_ARG;
+  if (prob->shock_capturing != PERK_SHOCK_OFF && !(prob->alpha_max > 0.0 && prob->alpha_max <= 1.0))
     return PERK_E_INVALID_ARG;
   if (prob->equations != PERK_EULER && prob->equations != PERK_NAVIER_STOKES) return PERK_E_INVALID_ARG;
   if (prob->equations == PERK_NAVIER_STOKES && (!(prob->mu > 0.0) || !(prob->prandtl > 0.0))) return PERK_E_INVALID_ARG;
@@ -783,7 +813,7 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return PERK_E_CUDA;
   perk_ctx* ctx = new perk_ctx();
   ctx->prob = *prob;
-  ctx->ops = build_ops(prob->gamma, prob->surface_flux);
+  ctx->ops = build_ops(prob->gamma, prob->surface_flux, prob->shock_capturing, prob->alpha_max);
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
       ctx->d_logtab.ensure(2 * LOG_TABLE_SIZE) != cudaSuccess ||
@@ -1463,6 +1493,8 @@ static int min_active_member(const perk_ctx* ctx, int stage) {
 
 perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd) {
   if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->differentiable())
+    return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for HLL, HLLC and EC surface fluxes without shock capturing");
   if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
   if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_Y || !d_V || !d_Kd) return fail(ctx, PERK_E_INVALID_ARG, "null array");
@@ -1479,6 +1511,8 @@ perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const doub
 
 perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_lam, double* d_g) {
   if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->differentiable())
+    return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for HLL, HLLC and EC surface fluxes without shock capturing");
   if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
   if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_Y || !d_lam || !d_g) return fail(ctx, PERK_E_INVALID_ARG, "null array");
@@ -1501,6 +1535,8 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
 
 static perk_status step_ready_adjoint(perk_ctx* ctx, const double* d_Un, double dt) {
   if (ctx->viscous()) return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for the Euler equations");
+  if (!ctx->differentiable())
+    return fail(ctx, PERK_E_INVALID_ARG, "derivatives are built for HLL, HLLC and EC surface fluxes without shock capturing");
   if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
     return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
   if (ctx->n_members != 1) return fail(ctx, PERK_E_INVALID_ARG, "the step adjoint takes single-member contexts");

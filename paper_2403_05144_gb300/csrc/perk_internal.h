@@ -29,6 +29,13 @@ struct Ops {
   double inv_gm1;         // 1 / (gamma - 1)
   double gm1;             // gamma - 1
   int surface_flux;       // perk_surface_flux
+  // subcell shock capturing (perk_shock): indicator variable, cap, inverse of the orthonormal
+  // Legendre Vandermonde matrix at the nodes, 1/w_i, threshold T and sharpness s / T
+  int shock;
+  double alpha_max;
+  double vinv[NN][NN];
+  double inv_w[NN];
+  double sc_T, sc_s_over_T;
 };
 
 // Y = U + dt * (alpha * K1 + beta * Kprev) for an element of a given member at a given stage.

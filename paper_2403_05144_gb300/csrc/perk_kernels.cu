@@ -318,6 +318,38 @@ __device__ void flux_hll(const double uL[4], const double uR[4], int dir, const 
   rotate_back(F, dir, f);
 }
 
+// HLLE: the HLL flux with Einfeldt's bounds S_L = min(v_L - c_L, v~ - c~), S_R = max(v_R + c_R,
+// v~ + c~), from the Roe averages (weights sqrt(rho)) of both velocity components and of the
+// enthalpy (E + p)/rho, c~^2 = (gamma - 1)(H~ - |v~|^2 / 2).
+__device__ void flux_hlle(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
+  FaceState L, R;
+  face_pair(uL, uR, dir, ops, L, R);
+  const double sl = sqrt(L.rho), sr = sqrt(R.rho);
+  const double iws = rcp_nr(sl + sr);
+  const double wl = sl * iws, wr = sr * iws;
+  const double vn = fma(wl, L.v, wr * R.v);
+  const double vt = fma(wl, L.mt * L.ir, wr * (R.mt * R.ir));
+  const double H = fma(wl, (L.E + L.p) * L.ir, wr * ((R.E + R.p) * R.ir));
+  const double c = sqrt(ops.gm1 * fma(-0.5, fma(vn, vn, vt * vt), H));
+  const double SL = fmin(L.v - L.c, vn - c), SR = fmax(R.v + R.c, vn + c);
+  double F[4];
+  if (SL >= 0.0) {
+    face_flux_rot(L, F);
+  } else if (SR <= 0.0) {
+    face_flux_rot(R, F);
+  } else {
+    double FL[4], FR[4];
+    face_flux_rot(L, FL);
+    face_flux_rot(R, FR);
+    const double inv = rcp_nr(SR - SL);
+    const double SLSR = SL * SR;
+    const double dU[4] = {R.rho - L.rho, R.mn - L.mn, R.mt - L.mt, R.E - L.E};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = fma(SLSR, dU[v], SR * FL[v] - SL * FR[v]) * inv;
+  }
+  rotate_back(F, dir, f);
+}
+
 // HLLC (Toro, Spruce, Speares 1994) with the same speeds and the standard contact speed.
 __device__ void flux_hllc(const double uL[4], const double uR[4], int dir, const Ops& ops, double f[4]) {
   FaceState L, R;
@@ -359,6 +391,8 @@ __device__ __forceinline__ void surface_flux(const double uL[4], const double uR
     flux_hllc(uL, uR, dir, ops, f);
   else if (ops.surface_flux == PERK_SURFACE_EC)
     flux_ec_surface(uL, uR, dir, ops, f);
+  else if (ops.surface_flux == PERK_SURFACE_HLLE)
+    flux_hlle(uL, uR, dir, ops, f);
   else
     flux_hll(uL, uR, dir, ops, f);
 }
@@ -491,7 +525,7 @@ __device__ __forceinline__ int pair_slot(int a, int b) {  // a < b, slots 0..5
   return (a * (7 - a)) / 2 + b - a - 1;
 }
 
-template <int YS, bool CHECK, int VOL_ELEMS>
+template <int YS, bool CHECK, int VOL_ELEMS, bool SHOCK>
 __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
                                                          const int32_t* __restrict__ level,
                                                          const int32_t* __restrict__ method, double two_over_len,
@@ -501,6 +535,8 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   __shared__ NodeQ s_prim[VOL_ELEMS][NODES];
   __shared__ double s_flux[VOL_ELEMS][4][NPAIR];
   __shared__ double s_log[2 * LOG_TABLE];
+  __shared__ double s_u[SHOCK ? VOL_ELEMS : 1][4][NODES];     // stage state (shock capturing)
+  __shared__ double s_eps[SHOCK ? VOL_ELEMS : 1][NODES];      // indicator variable
   for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_ELEMS * NODES) s_log[q] = log_table[q];
   __syncthreads();
   const int le = threadIdx.x >> 4;
@@ -556,6 +592,67 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
       const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[v] = fma(dy[mm], s_flux[le][v][p], acc[v]);
+    }
+  }
+
+  if (SHOCK) {
+    // subcell shock capturing: the element's blending factor from the modes of its indicator
+    // variable, then (1 - alpha) (flux differencing) + alpha (subcell finite volumes)
+    const unsigned gmask = 0xFFFFu << (threadIdx.x & 16);   // the 16 lanes of this element
+    s_eps[le][t] = ops.shock == PERK_SHOCK_DENSITY ? y[0] : y[0] * (2.0 * s_prim[le][t].hp);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) s_u[le][v][t] = y[v];
+    __syncwarp(gmask);   // also: every lane of the element has consumed the pair fluxes
+    double md = 0.0;     // mode (a, b) = (i, j) in the orthonormal Legendre basis
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      double r = 0.0;
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) r = fma(ops.vinv[i][ii], s_eps[le][jj * 4 + ii], r);
+      md = fma(ops.vinv[j][jj], r, md);
+    }
+    const double m2 = md * md;
+    const int shell = max(i, j);
+    double top = shell == 3 ? m2 : 0.0, mid = shell == 2 ? m2 : 0.0, low = shell <= 1 ? m2 : 0.0;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      top += __shfl_xor_sync(0xffffffffu, top, o, 16);
+      mid += __shfl_xor_sync(0xffffffffu, mid, o, 16);
+      low += __shfl_xor_sync(0xffffffffu, low, o, 16);
+    }
+    const double energy = fmax(top / (top + mid + low), mid / (mid + low));
+    double alpha = 1.0 / (1.0 + exp(-ops.sc_s_over_T * (energy - ops.sc_T)));
+    alpha = alpha < 1e-3 ? 0.0 : fmin(alpha, ops.alpha_max);
+    if (alpha > 0.0) {   // the same for the element's 16 lanes
+      // the 24 subcell fluxes: q < 12 along x (row q / 3, between nodes q % 3 and q % 3 + 1),
+      // q >= 12 along y (column (q - 12) / 3); stored over the consumed pair fluxes
+      for (int qq = t; qq < 24; qq += 16) {
+        const int dq = qq >= 12, r = dq ? qq - 12 : qq, line = r / 3, k = r - 3 * line;
+        const int na = dq ? k * 4 + line : line * 4 + k;
+        const int nb = dq ? (k + 1) * 4 + line : line * 4 + k + 1;
+        double ua[4], ub[4], f[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          ua[v] = s_u[le][v][na];
+          ub[v] = s_u[le][v][nb];
+        }
+        surface_flux(ua, ub, dq, ops, f);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) s_flux[le][v][qq] = f[v];
+      }
+      __syncwarp(gmask);
+      // finite-volume term at this node, (F_{i+1/2} - F_{i-1/2}) / w_i in x plus the same in y, with
+      // zero at the element ends: there the physical flux of the strong form's surface term cancels,
+      // as it does against the diagonal of the flux-differencing term
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double fxr = i < 3 ? s_flux[le][v][j * 3 + i] : 0.0;
+        const double fxl = i > 0 ? s_flux[le][v][j * 3 + i - 1] : 0.0;
+        const double fyr = j < 3 ? s_flux[le][v][12 + i * 3 + j] : 0.0;
+        const double fyl = j > 0 ? s_flux[le][v][12 + i * 3 + j - 1] : 0.0;
+        const double fv = (fxr - fxl) * ops.inv_w[i] + (fyr - fyl) * ops.inv_w[j];
+        acc[v] = fma(alpha, fv - acc[v], acc[v]);
+      }
     }
   }
   if (!valid) return;
@@ -992,20 +1089,31 @@ cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t 
   return cudaGetLastError();
 }
 
-template <int VE>
+template <int VE, bool SHOCK>
 static void volume_grid(YSource ysrc, bool check, cudaStream_t st, const Ops& ops, int64_t n, const int32_t* elems,
                         const int32_t* level, const int32_t* method, double two_over_len, const StageArgs& sa,
                         const double* surf, double* K, const UpdateArgs& ua, const double* log_table) {
   const unsigned blocks = (unsigned)((n + VE - 1) / VE);
   if (ysrc == Y_GIVEN)
-    k_volume<Y_GIVEN, false, VE><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len, sa, surf,
-                                                                K, ua, log_table);
+    k_volume<Y_GIVEN, false, VE, SHOCK><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len,
+                                                                       sa, surf, K, ua, log_table);
   else if (check)
-    k_volume<Y_COMBINE, true, VE><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len, sa,
-                                                                 surf, K, ua, log_table);
+    k_volume<Y_COMBINE, true, VE, SHOCK><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len,
+                                                                        sa, surf, K, ua, log_table);
   else
-    k_volume<Y_COMBINE, false, VE><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method, two_over_len, sa,
-                                                                  surf, K, ua, log_table);
+    k_volume<Y_COMBINE, false, VE, SHOCK><<<blocks, VE * NODES, 0, st>>>(ops, n, elems, level, method,
+                                                                         two_over_len, sa, surf, K, ua, log_table);
+}
+
+template <int VE>
+static void volume_grid_any(YSource ysrc, bool check, cudaStream_t st, const Ops& ops, int64_t n,
+                            const int32_t* elems, const int32_t* level, const int32_t* method, double two_over_len,
+                            const StageArgs& sa, const double* surf, double* K, const UpdateArgs& ua,
+                            const double* log_table) {
+  if (ops.shock != PERK_SHOCK_OFF)
+    volume_grid<VE, true>(ysrc, check, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua, log_table);
+  else
+    volume_grid<VE, false>(ysrc, check, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua, log_table);
 }
 
 cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n, const int32_t* elems,
@@ -1017,15 +1125,15 @@ cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t
   if (check) ua = *check;
   switch (elems_per_block) {
     case 2:
-      volume_grid<2>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
+      volume_grid_any<2>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
                      log_table);
       break;
     case 4:
-      volume_grid<4>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
+      volume_grid_any<4>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
                      log_table);
       break;
     case 8:
-      volume_grid<8>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
+      volume_grid_any<8>(ysrc, check != nullptr, st, ops, n, elems, level, method, two_over_len, sa, surf, K, ua,
                      log_table);
       break;
     default:
