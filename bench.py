@@ -12,7 +12,8 @@ and dt) on the same GPU, the accuracy of both against a reference solution,
 the roofline of the dominant kernel against the measured FP64 rate, the
 end-to-end rate through the public API with host buffers, and the CPU oracle
 on a bounded sample.  Workloads: kh (default: Kelvin-Helmholtz with dynamic
-AMR), vortex (static two-level isentropic vortex, 448 cells), vortex_large (the same
+AMR), kh_shock (the same with HLLE and subcell shock capturing), vortex (static
+two-level isentropic vortex, 448 cells), vortex_large (the same
 pattern at 114,688 cells, the roofline case), shear (Navier-Stokes shear
 layer, third order, dynamic AMR), ensemble (64 KH members in one context),
 adjoint (discrete-adjoint gradient over 200 steps), spectrum (spectrum-optimised
@@ -75,6 +76,11 @@ def workload(name: str) -> dict:
         return dict(name="kelvin_helmholtz_amr_levels4-7", cells=uniform_cells(4), x0=-1.0, L=2.0,
                     ic=kelvin_helmholtz, E=[4, 6, 10, 16], flux="hllc", cfl=0.7, t_end=3.0, amr=AMR_KH, n_amr=5,
                     init_cycles=3)
+    if name == "kh_shock":
+        # the Kelvin-Helmholtz run with the paper's spatial scheme of Sec. 7.2.1: HLLE surface flux and
+        # subcell shock capturing with the density as indicator variable (alpha_max 0.5)
+        return dict(workload("kh"), name="kelvin_helmholtz_amr_levels4-7_hlle_shock_capturing", flux="hlle",
+                    shock="density")
     if name == "shear":
         # doubly periodic shear layer on [0, 1]^2 (Sec. 7.1.1 set-up at Mach 0.3, Re 2500, Pr 0.72):
         # Navier-Stokes with BR1, P-ERK3 {4, 8, 16}, HLL, N = 3, base level 6, dynamic AMR between
@@ -108,7 +114,7 @@ class Run:
         self.wl = wl
         self.solver = PerkSolver(surface_flux=wl["flux"], use_graph=use_graph,
                                  equations=wl.get("equations", "euler"), mu=wl.get("mu", 0.0),
-                                 prandtl=wl.get("prandtl", 0.72))
+                                 prandtl=wl.get("prandtl", 0.72), shock_capturing=wl.get("shock"))
         self.solver.upload_mesh(wl["cells"], wl["x0"], wl["L"])
         if wl.get("order", 2) == 3:
             c, a = perk3_disk_tableau(E)
@@ -346,6 +352,9 @@ def oracle_problem(wl: dict, cells):
     meth = element_methods(mesh.cells[:, 0], fam.R)
     if wl.get("equations", "euler") == "navier_stokes":
         dg = NavierStokesDGSEM(mesh, 3, wl["flux"], mu=wl["mu"], prandtl=wl["prandtl"])
+    elif wl.get("shock"):
+        from oracle.shock import ShockCapturingDGSEM
+        dg = ShockCapturingDGSEM(mesh, 3, wl["flux"], variable=wl["shock"])
     else:
         dg = DGSEM(mesh, 3, wl["flux"])
     return mesh, fam, meth, dg
@@ -401,8 +410,9 @@ def run_reference(args) -> None:
     from oracle.lgl import lgl_nodes_weights
     from oracle.treemesh import TreeMesh
 
-    if args.workload not in ("kh", "vortex", "vortex_large", "shear"):
-        raise SystemExit("--impl reference times the oracle on the kh, vortex, vortex_large or shear workload")
+    if args.workload not in ("kh", "kh_shock", "vortex", "vortex_large", "shear"):
+        raise SystemExit("--impl reference times the oracle on the kh, kh_shock, vortex, vortex_large or shear "
+                         "workload")
     wl = workload(args.workload)
     x, _ = lgl_nodes_weights(3)
     cells = wl["cells"]
@@ -865,7 +875,7 @@ def main():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="perk", choices=["perk", "reference"])
     p.add_argument("--workload", default="kh",
-                   choices=["kh", "vortex", "vortex_large", "shear", "ensemble", "adjoint", "spectrum"])
+                   choices=["kh", "kh_shock", "vortex", "vortex_large", "shear", "ensemble", "adjoint", "spectrum"])
     p.add_argument("--t-end-budget", type=float, default=60.0, help="wall seconds per run to t_end")
     args = p.parse_args()
     if args.warmup < 3:
