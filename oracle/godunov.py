@@ -59,12 +59,13 @@ def total_variation(U: np.ndarray) -> float:
     return float(np.sum(np.abs(np.roll(U, -1) - U)))
 
 
-def tv_increase(n_coarse: int, alpha: float, E1: int, E2: int, cfl: float = 1.0) -> float:
+def tv_increase(n_coarse: int, alpha: float, E1: int, E2: int, cfl: float = 1.0, pattern: str = "classic") -> float:
     """Relative total-variation increase after one step with the coarse cells
     on member E1 and the refined cells on member E2, dt = cfl * (E1 - 1) * dx_1
-    (the largest stable step of the E1 disk polynomial on the coarse cells)."""
+    (the largest stable step of the E1 disk polynomial on the coarse cells);
+    stage pattern classic, alternating or early (Sec. 3.2.4)."""
     edges, dx, fine = two_region_grid(n_coarse, alpha)
-    fam = perk2_family([E1, E2])
+    fam = perk2_family([E1, E2], pattern=pattern)
     method = fine.astype(np.int64)
     dt = cfl * (E1 - 1) * dx[0]
     U0 = cell_averages(edges)

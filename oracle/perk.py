@@ -72,26 +72,78 @@ class PERKFamily:
     b: np.ndarray                # [S]
     A: List[np.ndarray]          # R dense S x S Butcher arrays
     order: int = 2
+    evaluated: List[List[int]] | None = None   # per member, the 1-based stages it evaluates
 
     @property
     def R(self) -> int:
         return len(self.E)
 
     def active(self, r: int, i: int) -> bool:
-        """Whether member r (0-based) evaluates stage i (0-based): K_1 always,
-        otherwise stages S-E+2 .. S (1-based)."""
+        """Whether member r (0-based) evaluates stage i (0-based): K_1 always, otherwise
+        stages S-E+2 .. S (1-based) in the classic pattern, or the pattern's stages."""
+        if self.evaluated is not None:
+            return (i + 1) in self.evaluated[r]
         return i == 0 or (i + 1) >= self.S - self.E[r] + 2
 
 
-def perk2_family(E_list: Sequence[int], S: int | None = None, alphas=None, b_S: float = 1.0) -> PERKFamily:
+def pattern_stages(S: int, E: int, pattern: str) -> List[int]:
+    """The 1-based stages a member with E evaluations computes in an S-stage family.
+    classic (Eq. PERK_ButcherTableauClassic): 1 and S-E+2 .. S; early (shared evaluations
+    first, Eq. PERK_ButcherTableauEarlyShared): 1 .. E-1 and S; alternating
+    (Eq. PERK_ButcherTableauAlternating): 1 and s_k = S - floor((E-1-k)(S-1)/(E-1) + 1/2),
+    k = 1 .. E-1, which spreads the evaluations evenly (S = 6, E = 4: 1, 3, 4, 6 as printed)."""
+    if E == S or pattern == "classic":
+        return [1] + list(range(S - E + 2, S + 1))
+    if pattern == "early":
+        return list(range(1, E)) + [S]
+    if pattern == "alternating":
+        return [1] + [S - math.floor((E - 1 - k) * (S - 1) / (E - 1) + 0.5) for k in range(1, E)]
+    raise ValueError(pattern)
+
+
+def pattern_member(S: int, E: int, alpha: Sequence[float], pattern: str, b_S: float = 1.0) -> np.ndarray:
+    """Dense S x S array of a second-order member with stage pattern `pattern`: every evaluated
+    stage after the first one past K_1 couples to the previous evaluated stage, s_k -> s_{k-1}
+    (k >= 2), the rest of its abscissa on K_1 (internal consistency).  With b = (1 - b_S) e_1 +
+    b_S e_S the coefficient of z^{3+j} of the stability polynomial is
+    b_S c_{s_{E-2-j}} prod_{q=0}^{j} a_{s_{E-1-q}, s_{E-2-q}}, which gives the couplings from
+    alpha_3 .. alpha_E one after the other, from the last stage backwards (the recursion of
+    Eq. PERKCoeffsConstruction along the member's own stages)."""
+    c = perk2_abscissae(S, b_S)
+    st = pattern_stages(S, E, pattern)                   # s_0 = 1 < s_1 < ... < s_{E-1} = S
+    a = {}
+    prod = 1.0
+    for j in range(E - 2):
+        hi, lo = st[E - 1 - j], st[E - 2 - j]
+        v = alpha[3 + j] / (b_S * c[lo - 1] * prod)
+        a[(hi, lo)] = v
+        prod *= v
+    M = np.zeros((S, S))
+    for i1 in range(2, S + 1):
+        src = [lo for (hi, lo) in a if hi == i1]
+        ai = a[(i1, src[0])] if src else 0.0
+        if src:
+            M[i1 - 1, src[0] - 1] += ai
+        M[i1 - 1, 0] += c[i1 - 1] - ai
+    return M
+
+
+def perk2_family(E_list: Sequence[int], S: int | None = None, alphas=None, b_S: float = 1.0,
+                 pattern: str = "classic") -> PERKFamily:
     """Second-order P-ERK family with members E_list (ascending) and S = max(E) stages; weights
-    b_1 = 1 - b_S, b_S (b_S = 1: Eq. PERK_ButcherTableauClassic)."""
+    b_1 = 1 - b_S, b_S (b_S = 1: Eq. PERK_ButcherTableauClassic); stage pattern classic,
+    alternating or early (Sec. 3.2.4)."""
     E_list = [int(e) for e in E_list]
     S = S or max(E_list)
     c = perk2_abscissae(S, b_S)
     b = np.zeros(S)
     b[-1] = b_S
     b[0] += 1.0 - b_S
+    if pattern != "classic":
+        A = [pattern_member(S, E, disk_polynomial_alpha(E) if alphas is None else np.asarray(alphas[r]), pattern, b_S)
+             for r, E in enumerate(E_list)]
+        return PERKFamily(S=S, E=E_list, c=c, b=b, A=A, order=2,
+                          evaluated=[pattern_stages(S, E, pattern) for E in E_list])
     A = []
     for r, E in enumerate(E_list):
         alpha = disk_polynomial_alpha(E) if alphas is None else np.asarray(alphas[r])

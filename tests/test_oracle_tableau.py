@@ -110,3 +110,47 @@ def test_weight_variants_keep_order_and_polynomial(b_S):
         P = stability_polynomial(A, fam.b)
         np.testing.assert_allclose(P[: E + 1], disk_polynomial_alpha(E), rtol=1e-11, atol=1e-15)
         assert np.all(np.abs(P[E + 1:]) < 1e-12)
+
+
+@pytest.mark.parametrize("pattern,stages,couplings", [
+    ("alternating", [1, 3, 4, 6], [(4, 3), (6, 4)]),       # Eq. PERK_ButcherTableauAlternating
+    ("early", [1, 2, 3, 6], [(3, 2), (6, 3)]),             # Eq. PERK_ButcherTableauEarlyShared
+    ("classic", [1, 4, 5, 6], [(5, 4), (6, 5)]),           # Eq. PERK_ButcherTableauClassic, A^(1)
+])
+def test_stage_patterns_reproduce_the_printed_tableaux(pattern, stages, couplings):
+    # the S = 6, E = 4 member of the paper's examples: evaluated stages and the nonzero
+    # entries off the first column
+    from oracle.perk import pattern_stages
+    fam = perk2_family([4, 6], pattern=pattern)
+    assert pattern_stages(6, 4, pattern) == stages
+    A = fam.A[0]
+    off = {(i + 1, j + 1) for i in range(6) for j in range(1, 6) if A[i, j] != 0.0}
+    assert off == set(couplings)
+    np.testing.assert_allclose(A.sum(axis=1), fam.c, rtol=0, atol=1e-15)
+    assert [i + 1 for i in range(6) if fam.active(0, i)] == stages
+
+
+@pytest.mark.parametrize("pattern", ["alternating", "early"])
+def test_stage_patterns_keep_polynomial_and_order(pattern):
+    fam = perk2_family([4, 8, 16], pattern=pattern)
+    for r, E in enumerate(fam.E):
+        P = stability_polynomial(fam.A[r], fam.b)
+        np.testing.assert_allclose(P[: E + 1], disk_polynomial_alpha(E), rtol=1e-11, atol=1e-15)
+        assert np.all(np.abs(P[E + 1:]) < 1e-12)
+        assert abs(fam.b @ fam.c - 0.5) < 1e-15
+        # a member only couples to stages it evaluates
+        ev = [i for i in range(fam.S) if fam.active(r, i)]
+        for i in range(fam.S):
+            for j in range(1, fam.S):
+                if fam.A[r][i, j] != 0.0:
+                    assert j in ev and i in ev
+
+
+def test_stage_pattern_total_variation_trend():
+    # Sec. 3.2.4: the stage pattern changes the nonlinear behaviour at the scheme interfaces; on
+    # the 1D bench (6-12 family) the classic pattern increases the total variation least and the
+    # alternating one most (trend only: the paper prints no numbers for this comparison)
+    from oracle.godunov import tv_increase
+    for alpha, cfl in ((1.5, 1.0), (1.5, 0.8), (2.0, 0.8)):
+        tv = {p: tv_increase(64, alpha, 6, 12, cfl, p) for p in ("classic", "alternating", "early")}
+        assert tv["classic"] < tv["early"] < tv["alternating"]
