@@ -144,6 +144,27 @@ perk_status perk_mesh_query(const perk_ctx* ctx, perk_mesh_info* info);
 perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32_t* E, const double* c,
                              const double* a);
 
+/* Stage patterns (Sec. 3.2.4).  eval[r*S + i] (0 or 1): member r evaluates stage i (0-based);
+ * src[r*S + i]: the stage it couples to at stage i besides K_1, with the coefficient a[r*S + i]
+ * (Y_i = U + dt ((c_i - a) K_1 + a K_src)).  Second order, b = e_S.  Each member evaluates the
+ * first and the last stage and E[r] stages in all; a member's stages are also evaluated by every
+ * finer member (so each stage's active elements stay a prefix of the sorted lists); a nonzero
+ * coupling needs src < i and an evaluated source stage; the largest member evaluates every stage.
+ * INVALID_ARG otherwise.  When some member couples to a stage other than K_{i-1}, the step keeps
+ * all S stages (S x n_elem x 512 B of device memory), and derivatives are refused. */
+perk_status perk_set_tableau_pattern(perk_ctx* ctx, int order, int S, int R, const int32_t* E,
+                                     const uint8_t* eval, const int32_t* src, const double* c, const double* a);
+
+/* Host utility: the disk-polynomial family of perk_perk2_disk_tableau with a stage pattern:
+ * 0 classic (1, S-E+2 .. S), 1 alternating (1 and S - floor((E-1-k)(S-1)/(E-1) + 1/2),
+ * k = 1 .. E-1; S = 6, E = 4 gives 1, 3, 4, 6 as in Eq. PERK_ButcherTableauAlternating), 2 early
+ * shared evaluations (1 .. E-1 and S, Eq. PERK_ButcherTableauEarlyShared).  Each evaluated stage
+ * after the first one past K_1 couples to the member's previous evaluated stage; the couplings
+ * follow from the polynomial's coefficients along that chain (Eq. PERKCoeffsConstruction).
+ * Fills c[S], eval[R*S], src[R*S], a[R*S] for perk_set_tableau_pattern. */
+perk_status perk_perk2_pattern_tableau(int S, int R, const int32_t* E, int pattern, double* c, uint8_t* eval,
+                                       int32_t* src, double* a);
+
 /* Weights of the final update of a second-order tableau (Sec. 3.1):
  * U_{n+1} = U_n + dt (b1 K_1 + bS K_S), b1 + bS = 1, bS > 0, with bS c_S = 1/2
  * for the abscissae already set (INVALID_ARG otherwise; NOT_READY without a

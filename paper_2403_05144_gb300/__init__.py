@@ -51,6 +51,26 @@ def perk2_disk_tableau(E: Sequence[int], S: int | None = None, b_S: float = 1.0)
     return np.array(c[:]), np.array(a[:]).reshape(R, S)
 
 
+PATTERNS = {"classic": 0, "alternating": 1, "early": 2}
+
+
+def perk2_pattern_tableau(E: Sequence[int], pattern: str, S: int | None = None):
+    """(c[S], eval[R, S], src[R, S], a[R, S]) of the disk-polynomial family with a stage pattern
+    (classic, alternating or early)."""
+    lib = _lib.load()
+    E = [int(e) for e in E]
+    S = int(S or max(E))
+    R = len(E)
+    Ea = (C.c_int32 * R)(*E)
+    c = (C.c_double * S)()
+    ev = (C.c_uint8 * (R * S))()
+    src = (C.c_int32 * (R * S))()
+    a = (C.c_double * (R * S))()
+    _check(lib, None, lib.perk_perk2_pattern_tableau(S, R, Ea, PATTERNS[pattern], c, ev, src, a))
+    return (np.array(c[:]), np.array(ev[:], dtype=np.uint8).reshape(R, S),
+            np.array(src[:], dtype=np.int32).reshape(R, S), np.array(a[:]).reshape(R, S))
+
+
 def perk2_member(S: int, E: int, alpha, b_S: float = 1.0) -> np.ndarray:
     """a[S] (one row of a tableau) of the second-order member with E evaluations whose stability
     polynomial has the monomial coefficients alpha[0..E] (alpha[0..2] = 1, 1, 1/2)."""
@@ -202,6 +222,25 @@ class PerkSolver:
         if b_S != 1.0:
             self.set_weights(1.0 - b_S, b_S)
         return c, a
+
+    def set_tableau_pattern(self, E: Sequence[int], c, evaluated, src, a):
+        E = [int(e) for e in E]
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        S, R = len(c), len(E)
+        ev = np.ascontiguousarray(evaluated, dtype=np.uint8).reshape(R, S)
+        sr = np.ascontiguousarray(src, dtype=np.int32).reshape(R, S)
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(R, S)
+        Ea = (C.c_int32 * R)(*E)
+        self._call(self.lib.perk_set_tableau_pattern, 2, S, R, Ea, ev.ctypes.data_as(C.POINTER(C.c_uint8)),
+                   sr.ctypes.data_as(C.POINTER(C.c_int32)), c.ctypes.data_as(C.POINTER(C.c_double)),
+                   a.ctypes.data_as(C.POINTER(C.c_double)))
+        self.S = S
+        self.E = E
+
+    def set_perk2_pattern(self, E: Sequence[int], pattern: str, S: int | None = None):
+        c, ev, src, a = perk2_pattern_tableau(E, pattern, S)
+        self.set_tableau_pattern(E, c, ev, src, a)
+        return c, ev, src, a
 
     def set_weights(self, b1: float, bS: float):
         self._call(self.lib.perk_set_weights, C.c_double(b1), C.c_double(bS))

@@ -68,6 +68,11 @@ SIGNATURES = [
                                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_perk2_member", C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_set_weights", C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    ("perk_set_tableau_pattern", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_uint8), C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double)]),
+    ("perk_perk2_pattern_tableau", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_uint8), C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     ("perk_partition", C.c_int, [C.c_void_p]),
     ("perk_perk3_disk_alpha", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("perk_perk3_member", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),

@@ -371,13 +371,15 @@ __device__ __forceinline__ void stage_y(const StageArgs& sa, const int32_t* meth
   if (YS == Y_GIVEN) {
     for (int v = 0; v < 4; ++v) y[v] = sa.Y[base + v * NODES];
   } else {
-    const StageCoef c = sa.coef ? sa.coef[method[e]] : StageCoef{0.0, 0.0};
+    const StageCoef c = sa.coef ? sa.coef[method[e]] : StageCoef{0.0, 0.0, 0, 0};
     const double dt = sa.dt[sa.member ? sa.member[e] : 0];
     for (int v = 0; v < 4; ++v) y[v] = sa.U[base + v * NODES];
     if (c.alpha != 0.0)
       for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.alpha, sa.K1[base + v * NODES], y[v]);
-    if (c.beta != 0.0)
-      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, sa.Kp[base + v * NODES], y[v]);
+    if (c.beta != 0.0) {
+      const double* Kp = coupled_stage(sa, c);
+      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, Kp[base + v * NODES], y[v]);
+    }
   }
 }
 __device__ __forceinline__ int pair_slot(int a, int b) { return (a * (7 - a)) / 2 + b - a - 1; }

@@ -279,13 +279,22 @@ struct perk_ctx {
   // Navier-Stokes (BR1) work space
   DevBuf<double> d_wsurf, d_q, d_vsurf;
   bool viscous() const { return prob.equations == PERK_NAVIER_STOKES; }
-  bool differentiable() const { return prob.shock_capturing == PERK_SHOCK_OFF && prob.surface_flux != PERK_SURFACE_HLLE; }
+  bool differentiable() const {
+    return prob.shock_capturing == PERK_SHOCK_OFF && prob.surface_flux != PERK_SURFACE_HLLE && !pattern_mode;
+  }
   double kappa() const { return prob.mu * prob.gamma / ((prob.gamma - 1.0) * prob.prandtl); }
   int32_t lmin = 0, lmax = 0;
 
   // tableau; weights of the final update U + dt (w_b1 K_1 + w_bp K_{S-1} + w_bs K_S)
   bool has_tab = false;
   int order = 2, S = 0, R = 0;
+  // stage pattern: src[r*S + i] = the stage (0-based) member r couples to at stage i besides K_1;
+  // stage_minmem[i] = the coarsest member active at stage i (members are nested);
+  // pattern_mode: some member does not couple to K_{i-1}, so the step keeps every stage
+  std::vector<int32_t> src;
+  int32_t stage_minmem[MAX_S] = {};
+  bool pattern_mode = false;
+  DevBuf<double> d_Kpat;
   double w_b1 = 0.0, w_bp = 0.0, w_bs = 1.0;
   int32_t E[MAX_R] = {};
   std::vector<double> c, a;  // c[S], a[R*S]
@@ -512,14 +521,14 @@ perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, c
 perk_status run_partition(perk_ctx* ctx) {
   if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   int R = 1, S = 1;
-  int32_t E[MAX_R] = {1};
+  int32_t minmem[MAX_S] = {0};
   if (ctx->has_tab) {
     R = ctx->R;
     S = ctx->S;
-    std::copy(ctx->E, ctx->E + R, E);
+    std::copy(ctx->stage_minmem, ctx->stage_minmem + MAX_S, minmem);
   }
-  PERK_CUDA(ctx, ctx->d_E.ensure(MAX_R));
-  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_E.p, E, sizeof(int32_t) * MAX_R, cudaMemcpyHostToDevice, ctx->stream));
+  PERK_CUDA(ctx, ctx->d_E.ensure(MAX_S));
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_E.p, minmem, sizeof(int32_t) * MAX_S, cudaMemcpyHostToDevice, ctx->stream));
   PERK_CUDA(ctx, launch_partition(ctx->stream, ctx->n_elem, ctx->n_if, ctx->n_mort, ctx->d_level.p, ctx->d_if_raw.p,
                                   ctx->d_mort_raw.p, R, S, ctx->d_E.p, ctx->n_members > 1 ? ctx->d_member.p : nullptr,
                                   ctx->n_members, ctx->d_member_lmax.p, ctx->d_method.p, ctx->d_elem_sorted.p,
@@ -733,23 +742,35 @@ void balance_levels(const perk_ctx* ctx, std::vector<int32_t>& d) {
 // the stage launches of one step on stream st (also used under graph capture)
 perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTimer* timer = nullptr) {
   const int S = ctx->S;
+  const size_t nd = (size_t)ctx->n_elem * ELEM;
+  // classic pattern: K_1 has its own buffer and K_2, K_3, ... alternate between two others;
+  // a stage pattern keeps every stage (stage i at Kall + i * nd), since a member may couple to
+  // any earlier stage it evaluated
+  double* Kall = nullptr;
+  if (ctx->pattern_mode) {
+    PERK_CUDA(ctx, ctx->d_Kpat.ensure(nd * S));
+    Kall = ctx->d_Kpat.p;
+  }
   double* Kbuf[3] = {ctx->d_K1.p, ctx->d_Ka.p, ctx->d_Kb.p};
-  int prev = 0, cur = 0, prev_at_last = 0;
+  auto stage_out = [&](int i, int cur) { return Kall ? Kall + (size_t)i * nd : Kbuf[cur]; };
+  int prev = 0, cur = 0;
+  double* K_before_last = Kall ? Kall + (size_t)(S > 1 ? S - 2 : 0) * nd : nullptr;   // K_{S-1}
   UpdateArgs ua{};
   ua.b1 = ctx->w_b1;
   ua.bp = ctx->w_bp;
   ua.bs = ctx->w_bs;
   ua.U = d_U;
-  ua.K1 = ctx->d_K1.p;
+  ua.K1 = Kall ? Kall : ctx->d_K1.p;
   ua.flag = ctx->d_flag.p;
   ua.member = ctx->n_members > 1 ? ctx->d_member.p : nullptr;
   for (int i = 0; i < S; ++i) {
-    // K_1 has its own buffer; K_2, K_3, ... alternate between the two others
     cur = (i == 0) ? 0 : (i % 2 == 1 ? 1 : 2);
     StageArgs sa{};
     sa.U = d_U;
-    sa.K1 = ctx->d_K1.p;
-    sa.Kp = Kbuf[prev];
+    sa.K1 = Kall ? Kall : ctx->d_K1.p;
+    sa.Kp = Kall ? nullptr : Kbuf[prev];
+    sa.Kall = Kall;
+    sa.nd = (int64_t)nd;
     sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
     sa.dt = ctx->d_dt.p;
     sa.member = ctx->n_members > 1 ? ctx->d_member.p : nullptr;
@@ -757,33 +778,33 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
           launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
                        ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     const bool last = (i == S - 1);
-    if (last) prev_at_last = prev;
+    if (last && !Kall) K_before_last = Kbuf[prev];
     UpdateArgs chk = ua;
-    chk.Kp = Kbuf[prev];
+    chk.Kp = K_before_last;
     const bool visc = ctx->viscous();
     TIMED(ctx, timer, st, 1,
           launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, Kbuf[cur],
+                        ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, stage_out(i, cur),
                         (last && !visc) ? &chk : nullptr, ctx->d_logtab.p, ctx->vol_epb));
     if (visc)
       TIMED(ctx, timer, st, 3,
             launch_br1(st, Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ctx->act_if[i],
                        ctx->act_mort[i], ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->n_elem, ctx->act_el[i],
                        ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa,
-                       ctx->d_wsurf.p, ctx->d_q.p, ctx->d_vsurf.p, Kbuf[cur], last ? &chk : nullptr));
+                       ctx->d_wsurf.p, ctx->d_q.p, ctx->d_vsurf.p, stage_out(i, cur), last ? &chk : nullptr));
     prev = cur;
   }
-  ua.Kp = Kbuf[prev_at_last];  // K_{S-1}
-  TIMED(ctx, timer, st, 2, launch_commit(st, ctx->n_elem, ua, Kbuf[cur], ctx->d_dt.p, d_U));
+  ua.Kp = K_before_last;
+  TIMED(ctx, timer, st, 2, launch_commit(st, ctx->n_elem, ua, stage_out(S - 1, cur), ctx->d_dt.p, d_U));
   return PERK_OK;
 }
 
 perk_status upload_coef(perk_ctx* ctx) {
-  std::vector<StageCoef> coef((size_t)MAX_S * MAX_R, StageCoef{0.0, 0.0});
+  std::vector<StageCoef> coef((size_t)MAX_S * MAX_R, StageCoef{0.0, 0.0, 0, 0});
   for (int i = 1; i < ctx->S; ++i)
     for (int r = 0; r < ctx->R; ++r) {
       const double beta = ctx->a[(size_t)r * ctx->S + i];
-      coef[(size_t)i * MAX_R + r] = StageCoef{ctx->c[i] - beta, beta};
+      coef[(size_t)i * MAX_R + r] = StageCoef{ctx->c[i] - beta, beta, ctx->src[(size_t)r * ctx->S + i], 0};
     }
   PERK_CUDA(ctx, ctx->d_coef.ensure((size_t)MAX_S * MAX_R));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_coef.p, coef.data(), coef.size() * sizeof(StageCoef), cudaMemcpyHostToDevice,
@@ -868,6 +889,7 @@ void perk_destroy(perk_ctx* ctx) {
   ctx->d_eta.release();
   ctx->d_surf_d.release();
   ctx->d_Kall.release();
+  ctx->d_Kpat.release();
   ctx->d_g.release();
   ctx->d_lamK1.release();
   ctx->d_lamKa.release();
@@ -1019,6 +1041,60 @@ perk_status perk_perk2_member(int S, int E, double bs, const double* alpha, doub
     return fail(nullptr, PERK_E_INVALID_ARG, "alpha[0..2] must be 1, 1, 1/2 (second order)");
   if (!perk2_member_from_alpha(S, E, bs, alpha, a))
     return fail(nullptr, PERK_E_INVALID_ARG, "the polynomial has no member of this form (a zero product)");
+  return PERK_OK;
+}
+
+perk_status perk_perk2_pattern_tableau(int S, int R, const int32_t* E, int pattern, double* c, uint8_t* eval,
+                                       int32_t* src, double* a) {
+  if (S < 2 || S > MAX_S || R < 1 || R > MAX_R || !E || !c || !eval || !src || !a || pattern < 0 || pattern > 2)
+    return PERK_E_INVALID_ARG;
+  for (int r = 0; r < R; ++r)
+    if (E[r] < 2 || E[r] > S || (r > 0 && E[r] < E[r - 1])) return PERK_E_INVALID_ARG;
+  for (int i = 0; i < S; ++i) c[i] = (double)i / (2.0 * (S - 1));
+  for (int r = 0; r < R; ++r) {
+    const int e = E[r];
+    // the member's stages (1-based), ascending: classic 1, S-E+2 .. S; early 1 .. E-1, S;
+    // alternating 1 and S - floor((E-1-k)(S-1)/(E-1) + 1/2), k = 1 .. E-1
+    std::vector<int> st(e);
+    st[0] = 1;
+    for (int k = 1; k < e; ++k) {
+      if (e == S || pattern == 0)
+        st[k] = S - e + 1 + k;
+      else if (pattern == 2)
+        st[k] = k < e - 1 ? k + 1 : S;
+      else
+        st[k] = S - (int)std::floor((double)(e - 1 - k) * (S - 1) / (e - 1) + 0.5);
+    }
+    for (int k = 1; k < e; ++k)
+      if (st[k] <= st[k - 1]) return PERK_E_INVALID_ARG;
+    uint8_t* ev = eval + (size_t)r * S;
+    int32_t* sr = src + (size_t)r * S;
+    double* ar = a + (size_t)r * S;
+    for (int i = 0; i < S; ++i) {
+      ev[i] = 0;
+      sr[i] = i > 0 ? i - 1 : 0;
+      ar[i] = 0.0;
+    }
+    for (int k = 0; k < e; ++k) ev[st[k] - 1] = 1;
+    // coefficients of the disk polynomial and the couplings s_k -> s_{k-1} from the last stage
+    // backwards: the coefficient of z^{3+j} is c_{s_{E-2-j}} prod_{q=0}^{j} a_{s_{E-1-q}, s_{E-2-q}}
+    std::vector<double> alpha(e + 1);
+    double binom = 1.0;
+    for (int k = 0; k <= e; ++k) {
+      alpha[k] = ((e - 1.0) / e) * binom / std::pow(e - 1.0, k);
+      binom = binom * (e - k) / (k + 1);
+    }
+    double prod = 1.0;
+    for (int j = 0; j <= e - 3; ++j) {
+      const int hi = st[e - 1 - j], lo = st[e - 2 - j];
+      const double den = c[lo - 1] * prod;
+      if (!(den != 0.0)) return PERK_E_INVALID_ARG;
+      const double v = alpha[3 + j] / den;
+      ar[hi - 1] = v;
+      sr[hi - 1] = lo - 1;
+      prod *= v;
+    }
+  }
   return PERK_OK;
 }
 
@@ -1272,6 +1348,73 @@ perk_status perk_set_tableau(perk_ctx* ctx, int order, int S, int R, const int32
         return fail(ctx, PERK_E_INVALID_ARG, "member %d: a_{%d,%d} != 0 but stage %d is not evaluated", r, i0 + 1,
                     i0, i0);
     }
+  // classic pattern: stage i couples to K_{i-1}; member r is active at stage i >= 1 iff E[r] >= S - i + 1
+  ctx->src.assign((size_t)R * S, 0);
+  for (int r = 0; r < R; ++r)
+    for (int i = 1; i < S; ++i) ctx->src[(size_t)r * S + i] = i - 1;
+  for (int i = 0; i < MAX_S; ++i) {
+    int mm = R;
+    for (int r = R - 1; r >= 0; --r)
+      if (i == 0 || E[r] >= S - i + 1) mm = r;
+    ctx->stage_minmem[i] = i < S ? mm : R;
+  }
+  ctx->pattern_mode = false;
+  ctx->has_tab = true;
+  drop_graph(ctx);
+  perk_status s = upload_coef(ctx);
+  if (s != PERK_OK) return s;
+  if (ctx->has_mesh) return run_partition(ctx);
+  return PERK_OK;
+}
+
+perk_status perk_set_tableau_pattern(perk_ctx* ctx, int order, int S, int R, const int32_t* E,
+                                     const uint8_t* eval, const int32_t* src, const double* c, const double* a) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (order != 2 || S < 2 || S > MAX_S || R < 1 || R > MAX_R || !E || !eval || !src || !c || !a)
+    return fail(ctx, PERK_E_INVALID_ARG, "invalid pattern tableau (second order, 2 <= S <= %d)", MAX_S);
+  for (int r = 0; r < R; ++r) {
+    if (E[r] < 2 || E[r] > S || (r > 0 && E[r] < E[r - 1]))
+      return fail(ctx, PERK_E_INVALID_ARG, "member evaluations must ascend within [2, S]");
+    const uint8_t* ev = eval + (size_t)r * S;
+    int count = 0;
+    for (int i = 0; i < S; ++i) count += ev[i] ? 1 : 0;
+    if (!ev[0] || !ev[S - 1] || count != E[r])
+      return fail(ctx, PERK_E_INVALID_ARG, "member %d must evaluate stage 1, stage S and E = %d stages in all", r, E[r]);
+    if (r > 0)
+      for (int i = 0; i < S; ++i)
+        if (eval[(size_t)(r - 1) * S + i] && !ev[i])
+          return fail(ctx, PERK_E_INVALID_ARG, "member %d evaluates stage %d but the finer member %d does not", r - 1,
+                      i + 1, r);
+    for (int i = 1; i < S; ++i) {
+      const int32_t sr = src[(size_t)r * S + i];
+      const double ar = a[(size_t)r * S + i];
+      if (sr < 0 || sr >= i) return fail(ctx, PERK_E_INVALID_ARG, "member %d, stage %d: source stage out of range", r, i + 1);
+      if (ar != 0.0 && !ev[sr])
+        return fail(ctx, PERK_E_INVALID_ARG, "member %d, stage %d couples to stage %d, which it does not evaluate", r,
+                    i + 1, sr + 1);
+    }
+  }
+  if (E[R - 1] != S) return fail(ctx, PERK_E_INVALID_ARG, "the largest member must evaluate every stage");
+  ctx->order = order;
+  ctx->S = S;
+  ctx->R = R;
+  ctx->w_b1 = 0.0;
+  ctx->w_bp = 0.0;
+  ctx->w_bs = 1.0;
+  std::copy(E, E + R, ctx->E);
+  ctx->c.assign(c, c + S);
+  ctx->a.assign(a, a + (size_t)R * S);
+  ctx->src.assign(src, src + (size_t)R * S);
+  bool classic = true;
+  for (int r = 0; r < R; ++r)
+    for (int i = 1; i < S; ++i) classic = classic && (ctx->a[(size_t)r * S + i] == 0.0 || ctx->src[(size_t)r * S + i] == i - 1);
+  for (int i = 0; i < MAX_S; ++i) {
+    int mm = R;
+    for (int r = R - 1; r >= 0; --r)
+      if (i < S && eval[(size_t)r * S + i]) mm = r;
+    ctx->stage_minmem[i] = mm;
+  }
+  ctx->pattern_mode = !classic;
   ctx->has_tab = true;
   drop_graph(ctx);
   perk_status s = upload_coef(ctx);
@@ -1486,9 +1629,7 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
 // otherwise members with E >= S - stage + 1
 static int min_active_member(const perk_ctx* ctx, int stage) {
   if (stage <= 0 || !ctx->has_tab) return 0;
-  for (int r = 0; r < ctx->R; ++r)
-    if (ctx->E[r] >= ctx->S - stage + 1) return r;
-  return ctx->R;
+  return ctx->stage_minmem[stage];
 }
 
 perk_status perk_rhs_jvp(perk_ctx* ctx, int stage, const double* d_Y, const double* d_V, double* d_Kd) {

@@ -38,10 +38,13 @@ struct Ops {
   double sc_T, sc_s_over_T;
 };
 
-// Y = U + dt * (alpha * K1 + beta * Kprev) for an element of a given member at a given stage.
+// Y = U + dt * (alpha * K1 + beta * Kprev) for an element of a given member at a given stage;
+// Kprev = K_{i-1}, or with all stages stored (StageArgs::Kall, stage patterns) K_src.
 struct StageCoef {
   double alpha;
   double beta;
+  int32_t src;   // 0-based stage of Kprev when StageArgs::Kall is set
+  int32_t pad;
 };
 
 // Where the stage state comes from.
@@ -55,7 +58,16 @@ struct StageArgs {
   const StageCoef* coef;  //            [R] coefficients of this stage
   const double* dt;       //            device array: dt of each ensemble member
   const int32_t* member;  //            ensemble member of each element (nullptr: member 0)
+  const double* Kall;     //            all stages, stage s at Kall + s * nd (nullptr: use Kp)
+  int64_t nd;
 };
+
+#ifdef __CUDACC__
+// the stage a member couples to besides K_1
+__device__ __forceinline__ const double* coupled_stage(const StageArgs& sa, const StageCoef& c) {
+  return sa.Kall ? sa.Kall + (int64_t)c.src * sa.nd : sa.Kp;
+}
+#endif
 
 // Final-update description (P-ERK2: b = e_S; P-ERK3: b on K_1, K_{S-1}, K_S).
 struct UpdateArgs {
@@ -70,7 +82,7 @@ struct UpdateArgs {
 // ---- kernel launchers (perk_kernels.cu); all return cudaGetLastError() ----
 
 cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
-                             const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
+                             const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* stage_minmem,
                              const int32_t* member, int n_members, int32_t* member_lmax /* [n_members] */,
                              int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
                              int64_t* counts /* [3][MAX_S] */, int32_t* level_minmax /* [2] */);

@@ -422,8 +422,9 @@ __device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int 
     }
     if (c.beta != 0.0) {
       const double db = dt * c.beta;
+      const double* Kp = coupled_stage(sa, c);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) y[v] = fma(db, __ldg(sa.Kp + base + v * NODES), y[v]);
+      for (int v = 0; v < 4; ++v) y[v] = fma(db, __ldg(Kp + base + v * NODES), y[v]);
     }
   }
 }
@@ -760,7 +761,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
                                                               const int32_t* __restrict__ level,
                                                               const int4* __restrict__ if_raw,
                                                               const int4* __restrict__ mort_raw, int R, int S,
-                                                              const int32_t* __restrict__ E,
+                                                              const int32_t* __restrict__ stage_minmem,
                                                               const int32_t* __restrict__ member, int n_members,
                                                               int32_t* member_lmax, int32_t* method,
                                                               int32_t* elem_sorted, int4* if_sorted,
@@ -848,11 +849,12 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
       __syncthreads();
     }
   }
-  // active counts per stage: member r is active at stage i (0-based) iff i == 0 or E[r] >= S - i + 1
+  // active counts per stage: member r is active at stage i (0-based) iff r >= stage_minmem[i]
+  // (the members active at a stage are the finest ones, so each active set is a prefix)
   if (tid < S) {
     int64_t ce = 0, ci = 0, cm = 0;
     for (int r = 0; r < R; ++r) {
-      if (tid == 0 || E[r] >= S - tid + 1) {
+      if (r >= stage_minmem[tid]) {
         ce += s_cnt[0][r];
         ci += s_cnt[1][r];
         cm += s_cnt[2][r];
@@ -1033,11 +1035,11 @@ cudaError_t launch_transfer(cudaStream_t st, int64_t n, const int32_t* map, cons
 }
 
 cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
-                             const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* E,
+                             const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* stage_minmem,
                              const int32_t* member, int n_members, int32_t* member_lmax, int32_t* method,
                              int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted, int64_t* counts,
                              int32_t* level_minmax) {
-  k_partition<<<1, PART_THREADS, 0, st>>>(n_elem, n_if, n_mort, level, if_raw, mort_raw, R, S, E, member, n_members,
+  k_partition<<<1, PART_THREADS, 0, st>>>(n_elem, n_if, n_mort, level, if_raw, mort_raw, R, S, stage_minmem, member, n_members,
                                           member_lmax, method, elem_sorted, if_sorted, mort_sorted, counts,
                                           level_minmax);
   return cudaGetLastError();

@@ -144,3 +144,19 @@ def test_weighted_disk_tableau_matches_oracle(lib, b_S):
     for r, e in enumerate(E):
         free = perk2_free_coefficients(fam.S, e, disk_polynomial_alpha(e), b_S)   # 1-based stage index
         np.testing.assert_allclose(a[r, 1:], free[2:], rtol=2e-15, atol=0)
+
+
+@pytest.mark.parametrize("E,pattern", [([4, 8, 16], "early"), ([4, 6], "alternating"), ([6, 12], "alternating"),
+                                       ([4, 6, 10, 16], "classic")])
+def test_pattern_tableau_matches_oracle(lib, E, pattern):
+    from paper_2403_05144_gb300 import perk2_pattern_tableau
+    c, ev, src, a = perk2_pattern_tableau(E, pattern)
+    fam = perk2_family(E, pattern=pattern)
+    np.testing.assert_allclose(c, fam.c, rtol=0, atol=1e-16)
+    for r in range(len(E)):
+        A = np.zeros((fam.S, fam.S))
+        for i in range(1, fam.S):
+            A[i, src[r, i]] += a[r, i]
+            A[i, 0] += c[i] - a[r, i]
+        np.testing.assert_allclose(A, fam.A[r], rtol=1e-13, atol=1e-15)
+        assert [bool(x) for x in ev[r]] == [fam.active(r, i) for i in range(fam.S)]
