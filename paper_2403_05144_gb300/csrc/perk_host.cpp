@@ -748,7 +748,8 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
   // any earlier stage it evaluated
   double* Kall = nullptr;
   if (ctx->pattern_mode) {
-    PERK_CUDA(ctx, ctx->d_Kpat.ensure(nd * S));
+    // allocated by prepare_step before any capture
+    if (!ctx->d_Kpat.p || ctx->d_Kpat.cap < nd * S) return fail(ctx, PERK_E_NOT_READY, "stage storage not prepared");
     Kall = ctx->d_Kpat.p;
   }
   double* Kbuf[3] = {ctx->d_K1.p, ctx->d_Ka.p, ctx->d_Kb.p};
@@ -1484,7 +1485,17 @@ perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double*
   return rhs_given(ctx, stage, d_Y, d_K);
 }
 
+// device memory a step needs beyond the mesh buffers (allocated outside any graph capture)
+static perk_status prepare_step(perk_ctx* ctx) {
+  if (ctx->pattern_mode) PERK_CUDA(ctx, ctx->d_Kpat.ensure((size_t)ctx->n_elem * ELEM * ctx->S));
+  return PERK_OK;
+}
+
 static perk_status step_impl(perk_ctx* ctx, double* d_U) {
+  {
+    perk_status s = prepare_step(ctx);
+    if (s != PERK_OK) return s;
+  }
   if (ctx->prob.use_graph) {
     if (!ctx->graph_valid || ctx->graph_U != d_U) {
       cudaGraph_t g = nullptr;
@@ -1493,6 +1504,7 @@ static perk_status step_impl(perk_ctx* ctx, double* d_U) {
       cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
       if (s != PERK_OK) {
         if (g) cudaGraphDestroy(g);
+        cudaGetLastError();   // the failed capture's error is reported once, not by later calls
         return s;
       }
       PERK_CUDA(ctx, ce);
@@ -1551,6 +1563,10 @@ perk_status perk_step_profiled(perk_ctx* ctx, double* d_U, double dt, perk_kerne
   if (!d_U || !std::isfinite(dt) || !(dt > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or dt");
   {
     perk_status s = set_dts(ctx, nullptr, dt);
+    if (s != PERK_OK) return s;
+  }
+  {
+    perk_status s = prepare_step(ctx);
     if (s != PERK_OK) return s;
   }
   LaunchTimer timer;
