@@ -119,6 +119,8 @@ class Run:
         if wl.get("order", 2) == 3:
             c, a = perk3_disk_tableau(E)
             self.solver.set_tableau(3, E, c, a)
+        elif wl.get("pattern", "classic") != "classic":
+            self.solver.set_perk2_pattern(E, wl["pattern"], max(wl["E"]))
         else:
             b_S = wl.get("b_S", 1.0)
             c, a = perk2_disk_tableau(E, max(wl["E"]), b_S)
@@ -307,8 +309,9 @@ def equal_error_vortex(torch) -> dict:
 
 
 def equal_error_kh(torch, t_end: float = 0.5) -> dict:
-    """Density errors at t = 0.5 of the P-ERK2 family (weights b = e_S, and the Heun and Ralston
-    variants of Sec. 3.1) and of the full-RK method (same dt) against the full-RK method at dt/4,
+    """Density errors at t = 0.5 of the P-ERK2 family (weights b = e_S, the Heun and Ralston
+    variants of Sec. 3.1, and the early-shared stage pattern of Sec. 3.2.4) and of the full-RK
+    method (same dt) against the full-RK method at dt/4,
     all on the frozen initially adapted KH mesh (the flow is chaotic later, so only this early
     window is compared)."""
     wl = dict(workload("kh"))
@@ -317,11 +320,12 @@ def equal_error_kh(torch, t_end: float = 0.5) -> dict:
     cells, U0 = base.solver.cells.copy(), base.U.clone()
     dt0 = base.dt
     frozen = dict(wl, amr=None, cells=cells, init_cycles=0)
-    cases = (("perk", wl["E"], 1, 1.0), ("perk_heun_weights", wl["E"], 1, 0.5),
-             ("perk_ralston_weights", wl["E"], 1, 0.75), ("full_rk", [max(wl["E"])], 1, 1.0),
-             ("reference", [max(wl["E"])], 4, 1.0))
-    for name, E, div, b_S in cases:
-        run = Run(torch, dict(frozen, b_S=b_S), E)
+    cases = (("perk", wl["E"], 1, 1.0, "classic"), ("perk_heun_weights", wl["E"], 1, 0.5, "classic"),
+             ("perk_ralston_weights", wl["E"], 1, 0.75, "classic"),
+             ("perk_early_pattern", wl["E"], 1, 1.0, "early"), ("full_rk", [max(wl["E"])], 1, 1.0, "classic"),
+             ("reference", [max(wl["E"])], 4, 1.0, "classic"))
+    for name, E, div, b_S, pattern in cases:
+        run = Run(torch, dict(frozen, b_S=b_S, pattern=pattern), E)
         run.U = U0.clone()
         n = div * math.ceil(t_end / dt0)
         run.dt = t_end / n
@@ -331,7 +335,7 @@ def equal_error_kh(torch, t_end: float = 0.5) -> dict:
         runs[name] = run
     ref = runs["reference"].U.cpu().numpy()
     out = {k: {**density_errors(torch, runs[k].solver, runs[k].U, ref, wl["x0"], wl["L"]), "dt": runs[k].dt}
-           for k in ("perk", "perk_heun_weights", "perk_ralston_weights", "full_rk")}
+           for k in ("perk", "perk_heun_weights", "perk_ralston_weights", "perk_early_pattern", "full_rk")}
     out["ratio_l1"] = out["perk"]["l1"] / out["full_rk"]["l1"]
     out["ratio_linf"] = out["perk"]["linf"] / out["full_rk"]["linf"]
     out["t_end"] = t_end
