@@ -521,6 +521,19 @@ def run_perk(args) -> None:
     # wall time to t_end, P-ERK family against the full-RHS method (same S, same dt rule)
     tend = {"perk": run_to_t_end(torch, wl, wl["E"], args.t_end_budget),
             "full_rk": run_to_t_end(torch, wl, [S], args.t_end_budget)}
+    if wl.get("order", 2) == 3:
+        # the Shu-Osher scheme (the third-order member with E = S = 3) as a standalone comparator, at
+        # the step its disk radius allows relative to the family's largest member, with the AMR
+        # interval scaled so that the mesh adapts at about the same physical times
+        from paper_2403_05144_gb300 import perk3_disk_alpha
+        ratio = perk3_disk_alpha(3)[1] / perk3_disk_alpha(S)[1]
+        tend["ssp33"] = run_to_t_end(torch, dict(wl, cfl=wl["cfl"] * ratio,
+                                                 n_amr=max(1, int(round(wl["n_amr"] / ratio)))), [3],
+                                     args.t_end_budget)
+        tend["ssp33"]["cfl"] = wl["cfl"] * ratio
+    for k in ("perk", "full_rk", "ssp33"):
+        if k in tend:
+            tend[k]["sim_time_per_wall_s"] = tend[k]["t"] / tend[k]["wall_s"]
     tend["t_end"] = wl["t_end"]
     if tend["perk"]["status"] == tend["full_rk"]["status"] == "reached t_end":
         tend["wall_ratio_full_over_perk"] = tend["full_rk"]["wall_s"] / tend["perk"]["wall_s"]
