@@ -1181,16 +1181,21 @@ cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int6
   return cudaGetLastError();
 }
 
-// blocks of the volume VJP: at most what is resident at once (the kernel strides)
+// blocks of the volume VJP: at most what is resident at once (the kernel strides); the capacity is
+// computed once per device (a repeated computation by racing threads gives the same value)
 template <int YS>
 static unsigned vjp_volume_blocks(int64_t n_act) {
-  static int resident = 0;
+  constexpr int MAX_DEVICES = 64;
+  static int cached[MAX_DEVICES] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int resident = (dev >= 0 && dev < MAX_DEVICES) ? cached[dev] : 0;
   if (resident == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
+    int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ad::k_vjp_volume<YS>, 64, 0);
-    resident = sms * (per_sm > 0 ? per_sm : 1);
+    resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < MAX_DEVICES) cached[dev] = resident;
   }
   const int64_t need = (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS;
   return (unsigned)(need < resident ? need : resident);
