@@ -1702,8 +1702,10 @@ static perk_status step_ready_adjoint(perk_ctx* ctx, const double* d_Un, double 
   return set_dts(ctx, nullptr, dt);
 }
 
-// every stage of one step from U_n, stage i stored in K + i * n_elem * 64; when d_U is given,
-// the last stage checks admissibility and the commit updates d_U (as perk_step does)
+// the stages of one step from U_n, stage i stored in K + i * n_elem * 64; when d_U is given,
+// all S stages are evaluated, the last one checks admissibility and the commit updates d_U (as
+// perk_step does); without d_U only K_1 .. K_{S-1} are evaluated: the reverse sweep needs the
+// stage states Y_1 .. Y_S, and none of them is formed from K_S
 static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, double* d_U) {
   const size_t nd = (size_t)ctx->n_elem * ELEM;
   cudaStream_t st = ctx->stream;
@@ -1715,7 +1717,8 @@ static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, 
   ua.K1 = K;
   ua.Kp = K + (size_t)(ctx->S > 1 ? ctx->S - 2 : 0) * nd;   // K_{S-1}
   ua.flag = ctx->d_flag.p;
-  for (int i = 0; i < ctx->S; ++i) {
+  const int n_stages = d_U ? ctx->S : ctx->S - 1;
+  for (int i = 0; i < n_stages; ++i) {
     StageArgs sa{};
     sa.U = d_Un;
     sa.K1 = K;
