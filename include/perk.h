@@ -364,8 +364,10 @@ perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap);
 /* Per-kernel timing of one step (tracing).  Runs the step like perk_step but
  * without a graph, with CUDA events recorded on the context's stream around
  * every launch, and blocks until the step is done.  Kernel kinds:
- * 0 = face fluxes, 1 = volume integral, 2 = final update.  ms[k] and
- * launches[k] are accumulated (not reset) so a caller can sum over steps. */
+ * 0 = face fluxes, 1 = volume integral, 2 = final update, 3 = viscous terms
+ * (Navier-Stokes: the four BR1 kernels of a stage, timed and counted as one
+ * group).  ms[k] and launches[k] are accumulated (not reset) so a caller can
+ * sum over steps. */
 typedef struct {
   double ms[4];
   int64_t launches[4];

@@ -303,6 +303,8 @@ struct perk_ctx {
   bool partitioned = false;
   int part_S = 0;
   int64_t act_el[MAX_S] = {}, act_if[MAX_S] = {}, act_mort[MAX_S] = {};
+  // per stage, the prefixes of the one-level halo of the active members (BR1 gradients)
+  int64_t halo_el[MAX_S] = {}, halo_if[MAX_S] = {}, halo_mort[MAX_S] = {};
 
   // device buffers
   DevBuf<int32_t> d_level, d_method, d_elem_sorted, d_E, d_minmax, d_member, d_member_lmax;
@@ -533,7 +535,7 @@ perk_status run_partition(perk_ctx* ctx) {
                                   ctx->d_mort_raw.p, R, S, ctx->d_E.p, ctx->n_members > 1 ? ctx->d_member.p : nullptr,
                                   ctx->n_members, ctx->d_member_lmax.p, ctx->d_method.p, ctx->d_elem_sorted.p,
                                   ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_counts.p, ctx->d_minmax.p));
-  int64_t counts[3 * MAX_S];
+  int64_t counts[6 * MAX_S];
   int32_t mm[2];
   PERK_CUDA(ctx, cudaMemcpyAsync(counts, ctx->d_counts.p, sizeof counts, cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaMemcpyAsync(mm, ctx->d_minmax.p, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream));
@@ -542,6 +544,9 @@ perk_status run_partition(perk_ctx* ctx) {
     ctx->act_el[i] = i < S ? counts[i] : 0;
     ctx->act_if[i] = i < S ? counts[MAX_S + i] : 0;
     ctx->act_mort[i] = i < S ? counts[2 * MAX_S + i] : 0;
+    ctx->halo_el[i] = i < S ? counts[3 * MAX_S + i] : 0;
+    ctx->halo_if[i] = i < S ? counts[4 * MAX_S + i] : 0;
+    ctx->halo_mort[i] = i < S ? counts[5 * MAX_S + i] : 0;
   }
   ctx->lmin = mm[0];
   ctx->lmax = mm[1];
@@ -789,8 +794,9 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
                         (last && !visc) ? &chk : nullptr, ctx->d_logtab.p, ctx->vol_epb));
     if (visc)
       TIMED(ctx, timer, st, 3,
-            launch_br1(st, Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ctx->act_if[i],
-                       ctx->act_mort[i], ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->n_elem, ctx->act_el[i],
+            launch_br1(st, Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->halo_if[i], ctx->halo_mort[i],
+                       ctx->act_if[i], ctx->act_mort[i], ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->halo_el[i],
+                       ctx->act_el[i],
                        ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa,
                        ctx->d_wsurf.p, ctx->d_q.p, ctx->d_vsurf.p, stage_out(i, cur), last ? &chk : nullptr));
     prev = cur;
@@ -839,7 +845,7 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
       ctx->d_logtab.ensure(2 * LOG_TABLE_SIZE) != cudaSuccess ||
-      ctx->d_counts.ensure(3 * MAX_S) != cudaSuccess || ctx->d_minmax.ensure(2) != cudaSuccess ||
+      ctx->d_counts.ensure(6 * MAX_S) != cudaSuccess || ctx->d_minmax.ensure(2) != cudaSuccess ||
       ctx->d_dt_out.ensure(1) != cudaSuccess) {
     perk_destroy(ctx);
     return PERK_E_CUDA;
@@ -1466,8 +1472,10 @@ static perk_status rhs_given(perk_ctx* ctx, int stage, const double* d_Y, double
                                ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr, ctx->d_logtab.p,
                                ctx->vol_epb));
   if (ctx->viscous())
-    PERK_CUDA(ctx, launch_br1(ctx->stream, Y_GIVEN, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->n_if, ctx->n_mort, ni,
-                              nm, ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->n_elem, ne, ctx->d_elem_sorted.p,
+    PERK_CUDA(ctx, launch_br1(ctx->stream, Y_GIVEN, ctx->ops, ctx->prob.mu, ctx->kappa(),
+                              stage < 0 ? ctx->n_if : ctx->halo_if[stage], stage < 0 ? ctx->n_mort : ctx->halo_mort[stage],
+                              ni, nm, ctx->d_if_sorted.p, ctx->d_mort_sorted.p,
+                              stage < 0 ? ctx->n_elem : ctx->halo_el[stage], ne, ctx->d_elem_sorted.p,
                               ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_wsurf.p, ctx->d_q.p,
                               ctx->d_vsurf.p, d_K, nullptr));
   return PERK_OK;

@@ -850,19 +850,30 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
     }
   }
   // active counts per stage: member r is active at stage i (0-based) iff r >= stage_minmem[i]
-  // (the members active at a stage are the finest ones, so each active set is a prefix)
+  // (the members active at a stage are the finest ones, so each active set is a prefix).
+  // Halo counts: members r >= stage_minmem[i] - 1.  Face neighbours differ by at most one level
+  // (2:1 balance), so their members differ by at most one: the halo prefix holds every element
+  // that shares a face with an active one, and every face of those elements.
   if (tid < S) {
-    int64_t ce = 0, ci = 0, cm = 0;
+    int64_t ce = 0, ci = 0, cm = 0, he = 0, hi = 0, hm = 0;
     for (int r = 0; r < R; ++r) {
       if (r >= stage_minmem[tid]) {
         ce += s_cnt[0][r];
         ci += s_cnt[1][r];
         cm += s_cnt[2][r];
       }
+      if (r >= stage_minmem[tid] - 1) {
+        he += s_cnt[0][r];
+        hi += s_cnt[1][r];
+        hm += s_cnt[2][r];
+      }
     }
     counts[0 * MAX_S + tid] = ce;
     counts[1 * MAX_S + tid] = ci;
     counts[2 * MAX_S + tid] = cm;
+    counts[3 * MAX_S + tid] = he;
+    counts[4 * MAX_S + tid] = hi;
+    counts[5 * MAX_S + tid] = hm;
   }
   if (tid == 0) {
     level_minmax[0] = s_min;
