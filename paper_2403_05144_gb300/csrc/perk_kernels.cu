@@ -538,8 +538,6 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   __shared__ double s_log[2 * LOG_TABLE];
   __shared__ double s_u[SHOCK ? VOL_ELEMS : 1][4][NODES];     // stage state (shock capturing)
   __shared__ double s_eps[SHOCK ? VOL_ELEMS : 1][NODES];      // indicator variable
-  for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_ELEMS * NODES) s_log[q] = log_table[q];
-  __syncthreads();
   const int le = threadIdx.x >> 4;
   const int t = threadIdx.x & 15;
   const int i = t & 3, j = t >> 2;
@@ -548,12 +546,28 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   const int64_t e = valid ? elems[slot] : 0;
   const int m = valid ? method[e] : 0;
 
+  // every global load of the launch is issued here, before the first barrier: the grid is
+  // usually a single wave, so a load issued later would stall all warps at the same time
   double y[4];
   if (valid) {
     stage_state<YS>(sa, e, m, t, y);
   } else {
     y[0] = 1.0; y[1] = 0.0; y[2] = 0.0; y[3] = 2.5;
   }
+  // numerical fluxes of the faces through this node (x face at i = 0 or 3, y face at j = 0 or 3)
+  double fsx[4] = {0.0, 0.0, 0.0, 0.0}, fsy[4] = {0.0, 0.0, 0.0, 0.0};
+  if (valid) {
+    const double* sf = surf + e * ELEM;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (i == 0) fsx[v] = __ldg(sf + 0 * 16 + 4 * v + j);
+      if (i == 3) fsx[v] = __ldg(sf + 1 * 16 + 4 * v + j);
+      if (j == 0) fsy[v] = __ldg(sf + 2 * 16 + 4 * v + i);
+      if (j == 3) fsy[v] = __ldg(sf + 3 * 16 + 4 * v + i);
+    }
+  }
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_ELEMS * NODES) s_log[q] = log_table[q];
+  __syncthreads();
   s_prim[le][t] = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE);
   __syncwarp();
 
@@ -659,14 +673,13 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   if (!valid) return;
 
   // surface lifting with the numerical fluxes of the four faces (w_0 = w_N)
-  const double* sf = surf + e * ELEM;
   const double iw = ops.inv_w0;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    if (i == 0) acc[v] = fma(-iw, __ldg(sf + 0 * 16 + 4 * v + j), acc[v]);
-    if (i == 3) acc[v] = fma(iw, __ldg(sf + 1 * 16 + 4 * v + j), acc[v]);
-    if (j == 0) acc[v] = fma(-iw, __ldg(sf + 2 * 16 + 4 * v + i), acc[v]);
-    if (j == 3) acc[v] = fma(iw, __ldg(sf + 3 * 16 + 4 * v + i), acc[v]);
+    if (i == 0) acc[v] = fma(-iw, fsx[v], acc[v]);
+    if (i == 3) acc[v] = fma(iw, fsx[v], acc[v]);
+    if (j == 0) acc[v] = fma(-iw, fsy[v], acc[v]);
+    if (j == 3) acc[v] = fma(iw, fsy[v], acc[v]);
   }
   const double scale = -ldexp(two_over_len, level[e]);  // -(2/h)
   double kv[4];
