@@ -191,7 +191,7 @@ def prkm_step(rhs: Callable[[np.ndarray], np.ndarray], U: np.ndarray, dt: float,
         for j in range(i):
             a_e = coef[method, i, j]                       # a_ij^(r(e)) per element
             if np.any(a_e != 0.0):
-                Y = Y + dt * a_e[:, None, None, None] * K[j]
+                Y = Y + dt * a_e.reshape((-1,) + (1,) * (U.ndim - 1)) * K[j]
         K.append(rhs(Y))
     Un = U.copy()
     for i in range(S):
