@@ -2,7 +2,7 @@
 """Throughput benchmark of the P-ERK step on one or more GB300s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl perk|reference]
-                    [--workload kh|vortex|shear|ensemble|adjoint]
+                    [--workload kh|kh_shock|vortex|vortex_large|shear|ensemble|adjoint|spectrum|tgv]
 
 Prints one JSON line (rank 0).  Metric: P-ERK DoF-stage updates per second,
 i.e. the active DoF (nodes) summed over the stages of a step, divided by the
@@ -17,7 +17,8 @@ two-level isentropic vortex, 448 cells), vortex_large (the same
 pattern at 114,688 cells, the roofline case), shear (Navier-Stokes shear
 layer, third order, dynamic AMR), ensemble (64 KH members in one context),
 adjoint (discrete-adjoint gradient over 200 steps), spectrum (spectrum-optimised
-stability polynomials against the disk polynomials).
+stability polynomials against the disk polynomials), tgv (3D Taylor-Green vortex on
+a three-level octree, P-ERK3 {3,4,6}, N = 2).
 
 Multi-GPU: the step does not shard across GPUs here; N ranks run N
 independent replicas of the workload (weak scaling, no collective on the
@@ -878,6 +879,228 @@ def run_spectrum(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# FP64 issue slots of one element-stage of the 3D volume kernel at N = 2 (27 nodes, 81 symmetric
+# pairs), counted as for the 2D kernel:
+#   27 nodes x 64   (combination 15, pressure 6, reciprocal 5, primitives 8, two logarithms 30)
+# + 81 pairs x 50   (the 2D pair's 44 plus the third velocity's mean, product and flux component)
+# + 27 nodes x 6 partners x 5 variables (accumulation) + 270 (lifting on up to three faces, Jacobian)
+VOL3_SLOTS_PER_ELEM = 27 * 64 + 81 * 50 + 27 * 6 * 5 + 270
+TGV = dict(name="taylor_green_3d_octree_levels4-6_slab_n2_hlle", N=2, flux="hlle", E=[3, 4, 6], cfl=0.5,
+           level_min=4, level_max=6, width=1.0 / 32.0, x0=0.0, L=2.0 * math.pi, mach=0.1, t_end=20.0)
+
+
+def tgv_problem():
+    from perk_inputs.octree import nodal_state3, slab_cells3, taylor_green
+    from paper_2403_05144_gb300 import reference_nodes
+
+    cells = slab_cells3(TGV["level_min"], TGV["level_max"], TGV["width"])
+    x, _ = reference_nodes(TGV["N"])
+    U0 = nodal_state3(taylor_green, cells, TGV["x0"], TGV["L"], x, mach=TGV["mach"])
+    return cells, U0
+
+
+def tgv_oracle_sample(cells, U, n_stages: int = 0, budget_s: float = 10.0):
+    """The 3D oracle's partitioned RHS I^(act(i)) F(U) for stages i = 0, 1, ... (cycling): n_stages
+    evaluations or as many as fit in budget_s.  Returns (DoF-stage updates, seconds, evaluations, S)."""
+    from oracle.dgsem3d import DGSEM3D
+    from oracle.octree import OctreeMesh
+    from oracle.perk import element_methods, perk3_family
+
+    mesh = OctreeMesh(np.asarray(cells), TGV["x0"], TGV["L"])
+    fam = perk3_family(TGV["E"])
+    meth = element_methods(mesh.cells[:, 0], fam.R)
+    dg = DGSEM3D(mesh, TGV["N"], TGV["flux"])
+    nodes = (TGV["N"] + 1) ** 3
+    act = [np.array([fam.active(int(r), i) for r in meth]) for i in range(fam.S)]
+    units, k = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        dg.rhs_masked(U, act[k % fam.S])
+        units += nodes * int(act[k % fam.S].sum())
+        k += 1
+        sec = time.perf_counter() - t0
+        if (n_stages and k >= n_stages) or (not n_stages and sec >= budget_s):
+            break
+    return units, sec, k, fam.S
+
+
+def run_tgv(args) -> None:
+    """3D Taylor-Green vortex (the paper's Sec. 7.1.3 initial state, Mach 0.1) on a static
+    three-level octree (levels 4-6, 25,600 cells, N = 2: 691,200 nodes), HLLE surface flux,
+    P-ERK3 {3, 4, 6} against the standalone six-stage member (full RHS every stage)."""
+    import torch
+
+    rank, local_rank, world = dist_info()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2403_05144_gb300 import PerkError, measure_fp64
+    from paper_2403_05144_gb300.build import build
+    from paper_2403_05144_gb300.perk3d import Perk3DSolver
+
+    build()
+    cells, U0 = tgv_problem()
+    S = max(TGV["E"])
+
+    def make(E):
+        s = Perk3DSolver(N=TGV["N"], surface_flux=TGV["flux"], use_graph=True)
+        s.upload_mesh(cells, TGV["x0"], TGV["L"])
+        s.set_perk3_disk(E)
+        return s
+
+    perk, full = make(TGV["E"]), make([S])
+    Up = torch.from_numpy(U0).cuda()
+    Uf = Up.clone()
+    dt = perk.compute_dt(Up, TGV["cfl"])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(args.warmup):
+        perk.step(Up, dt)
+        full.step(Uf, dt)
+    torch.cuda.synchronize()
+    units_step = perk.info()["dof_stage_updates"]
+    units_full = full.info()["dof_stage_updates"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(solver, U):
+        st = torch.cuda.current_stream()
+        evs = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            solver.step(U, dt)
+            b.record(st)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ms = timed(perk, Up)
+        barrier()
+        ms_full = timed(full, Uf)
+        barrier()
+    perk.check()
+    full.check()
+    ms, ms_full = max_over_ranks([ms, ms_full], world, "cuda")
+    value = replica_rate(units_step * args.steps, ms, world)
+    value_full = replica_rate(units_full * args.steps, ms_full, world)
+    info = perk.info()
+
+    fma_flops, _, _ = measure_fp64()
+    Upr = Up.clone()
+    acc = None
+    for _ in range(args.steps):
+        acc = perk.step_profiled(Upr, dt, acc)
+    vol_ms, vol_launches = acc.ms[1], acc.launches[1]
+    achieved = 2.0 * VOL3_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
+    kernel_ms_total = sum(acc.ms[k] for k in range(3))
+
+    # end to end through the public API with the state in pinned host memory
+    st = torch.cuda.current_stream()
+    Uh = Up.cpu().pin_memory()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(st)
+    for _ in range(args.steps):
+        Ud = Uh.to("cuda", non_blocking=True)
+        perk.step(Ud, dt)
+        Uh.copy_(Ud, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    (ms_e2e,) = max_over_ranks([e0.elapsed_time(e1)], world, "cuda")
+    nbytes = Uh.numel() * 8
+
+    # simulated time per wall second over a fixed wall budget (t_end = 20 is out of reach of it)
+    tend = {"t_end": TGV["t_end"]}
+    for key, E in (("perk", TGV["E"]), ("full_rk", [S])):
+        s = make(E)
+        U = torch.from_numpy(U0).cuda()
+        torch.cuda.synchronize()
+        t, n, status = 0.0, 0, "budget"
+        t0 = time.perf_counter()
+        try:
+            while t < TGV["t_end"] - 1e-12 and time.perf_counter() - t0 < args.t_end_budget:
+                for _ in range(50):
+                    s.step(U, dt)
+                s.check()
+                t += 50 * dt
+                n += 50
+            if t >= TGV["t_end"] - 1e-12:
+                status = "reached t_end"
+        except PerkError:
+            status = "rejected step"
+        wall = time.perf_counter() - t0
+        tend[key] = {"t": t, "steps": n, "wall_s": wall, "status": status, "sim_time_per_wall_s": t / wall}
+    tend["sim_time_ratio_perk_over_full_rk"] = (tend["perk"]["sim_time_per_wall_s"]
+                                               / tend["full_rk"]["sim_time_per_wall_s"])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": TGV["name"], "n_elem": info["n_elem"], "levels": [info["level_min"], info["level_max"]],
+                   "N": TGV["N"], "family": TGV["E"], "stages": S, "surface_flux": TGV["flux"], "cfl": TGV["cfl"],
+                   "dt": dt, "mach": TGV["mach"], "equations": "euler",
+                   "dof_stage_updates_per_step": units_step, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"{world} independent replica(s)", "graph": True},
+        "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps, "dof_stage_updates_per_step": units_full,
+                    "ratio_ms_per_step_full_over_perk": ms_full / ms},
+        "t_end": tend,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / fma_flops, "traffic": None, "kernel": "k3_volume",
+                     "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
+                     "share_of_kernel_time": vol_ms / kernel_ms_total,
+                     "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
+                     "work_per_element_stage": {"fp64_slots": VOL3_SLOTS_PER_ELEM, "flops": 2 * VOL3_SLOTS_PER_ELEM}},
+        "e2e": {"value": replica_rate(units_step * args.steps, ms_e2e, world), "unit": UNIT,
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": args.steps * (2 * S + 1),
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        if world == 1:
+            u, sec, k, SS = tgv_oracle_sample(cells, U0)
+            line["cpu_baseline"] = {"value": u / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                                    "sample": f"{k} partitioned stage evaluations (cycling over S={SS}) of the "
+                                              f"{len(cells)}-cell octree, {sec:.1f} s, numpy float64, one thread"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference_tgv(args) -> None:
+    rank, _, world = dist_info()
+    if rank != 0:
+        return
+    from oracle.lgl import lgl_nodes_weights
+    from perk_inputs.octree import nodal_state3, slab_cells3, taylor_green
+
+    cells = slab_cells3(TGV["level_min"], TGV["level_max"], TGV["width"])
+    x, _ = lgl_nodes_weights(TGV["N"])
+    U = nodal_state3(taylor_green, cells, TGV["x0"], TGV["L"], x, mach=TGV["mach"])
+    tgv_oracle_sample(cells, U, n_stages=args.warmup)
+    units, sec, k, S = tgv_oracle_sample(cells, U, n_stages=args.steps)
+    value = units / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": TGV["name"], "n_elem": len(cells), "family": TGV["E"], "surface_flux": TGV["flux"],
+                       "step": "one partitioned stage evaluation of the 3D oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+                             "sample": f"{args.steps} stage evaluations (cycling over the S={S} stages) of the "
+                                       f"{len(cells)}-cell octree"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def lgl_weights_of(solver):
     import torch
 
@@ -893,13 +1116,16 @@ def main():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="perk", choices=["perk", "reference"])
     p.add_argument("--workload", default="kh",
-                   choices=["kh", "kh_shock", "vortex", "vortex_large", "shear", "ensemble", "adjoint", "spectrum"])
+                   choices=["kh", "kh_shock", "vortex", "vortex_large", "shear", "ensemble", "adjoint", "spectrum",
+                            "tgv"])
     p.add_argument("--t-end-budget", type=float, default=60.0, help="wall seconds per run to t_end")
     args = p.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
-        run_reference(args)
+        run_reference_tgv(args) if args.workload == "tgv" else run_reference(args)
+    elif args.workload == "tgv":
+        run_tgv(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
     elif args.workload == "adjoint":

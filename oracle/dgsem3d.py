@@ -98,24 +98,33 @@ class DGSEM3D:
         return vol
 
     # ----------------------------------------------------------------- surface
-    def trace(self, V: np.ndarray, e: int, face: int) -> np.ndarray:
-        """Face trace [5, n (t2), n (t1)]; faces 0/1 = -x/+x, 2/3 = -y/+y, 4/5 = -z/+z."""
+    def trace(self, V: np.ndarray, face: int) -> np.ndarray:
+        """Face traces of every element [5, e, n (t2), n (t1)]; faces 0/1 = -x/+x, 2/3 = -y/+y,
+        4/5 = -z/+z."""
         idx = 0 if face % 2 == 0 else self.N
         d = face // 2
         if d == 0:
-            return V[:, e, :, :, idx]       # [5, k, j]: t2 = z, t1 = y
+            return V[:, :, :, :, idx]       # [5, e, k, j]: t2 = z, t1 = y
         if d == 1:
-            return V[:, e, :, idx, :]       # [5, k, i]: t2 = z, t1 = x
-        return V[:, e, idx, :, :]           # [5, j, i]: t2 = y, t1 = x
+            return V[:, :, :, idx, :]       # [5, e, k, i]: t2 = z, t1 = x
+        return V[:, :, idx, :, :]           # [5, e, j, i]: t2 = y, t1 = x
 
     def _face_fluxes(self, V: np.ndarray):
-        """Numerical flux at the nodes of every element face: Fs[(e, face)] -> [5, n, n]."""
+        """Numerical flux at the nodes of every element face: Fs[face] -> [5, e, n, n]."""
         g = self.gamma
-        Fs = {}
-        for (A, B, d) in self.mesh.conforming:
-            f = self.fstar(self.trace(V, A, 2 * d + 1), self.trace(V, B, 2 * d), d, g)
-            Fs[(A, 2 * d + 1)] = f
-            Fs[(B, 2 * d)] = f
+        n = self.N + 1
+        ne = V.shape[1]
+        Fs = [np.full((5, ne, n, n), np.nan) for _ in range(6)]
+        tr = [self.trace(V, f) for f in range(6)]
+        conf = np.asarray(self.mesh.conforming, dtype=np.int64).reshape(-1, 3)
+        for d in (0, 1, 2):
+            sel = conf[conf[:, 2] == d]
+            if len(sel) == 0:
+                continue
+            A, B = sel[:, 0], sel[:, 1]
+            f = self.fstar(tr[2 * d + 1][:, A], tr[2 * d][:, B], d, g)
+            Fs[2 * d + 1][:, A] = f
+            Fs[2 * d][:, B] = f
         quads = defaultdict(dict)
         for (A, B, d, large, q1, q2) in self.mesh.hanging:
             if large == A:
@@ -124,14 +133,14 @@ class DGSEM3D:
                 small, small_face, large_face = A, 2 * d + 1, 2 * d
             s1 = 0.5 * (self.x + (2 * q1 - 1))
             s2 = 0.5 * (self.x + (2 * q2 - 1))
-            UL = self.trace(V, large, large_face)                                  # [5, b, a]
+            UL = tr[large_face][:, large]                                           # [5, b, a]
             u_large = np.einsum("pb,vba,qa->vpq", lagrange_basis(self.x, s2), UL, lagrange_basis(self.x, s1))
-            u_small = self.trace(V, small, small_face)
+            u_small = tr[small_face][:, small]
             f = self.fstar(u_large, u_small, d, g) if large == A else self.fstar(u_small, u_large, d, g)
-            Fs[(small, small_face)] = f
+            Fs[small_face][:, small] = f
             quads[(large, large_face)][(q1, q2)] = f
-        for key, qv in quads.items():
-            Fs[key] = face_l2_projection(self.x, qv)
+        for (large, large_face), qv in quads.items():
+            Fs[large_face][:, large] = face_l2_projection(self.x, qv)
         return Fs
 
     # --------------------------------------------------------------------- rhs
@@ -147,19 +156,17 @@ class DGSEM3D:
         Fs = self._face_fluxes(V)
         Sf = np.zeros_like(V)
         w0, wN = self.w[0], self.w[N]
-        for e in range(ne):
-            for face in range(6):
-                d = face // 2
-                tr = self.trace(V, e, face)
-                jump = Fs[(e, face)] - euler3d.physical_flux(tr, d, g)
-                idx = 0 if face % 2 == 0 else N
-                sign = -1.0 / w0 if face % 2 == 0 else 1.0 / wN
-                if d == 0:
-                    Sf[:, e, :, :, idx] += sign * jump
-                elif d == 1:
-                    Sf[:, e, :, idx, :] += sign * jump
-                else:
-                    Sf[:, e, idx, :, :] += sign * jump
+        for face in range(6):
+            d = face // 2
+            jump = Fs[face] - euler3d.physical_flux(self.trace(V, face), d, g)
+            idx = 0 if face % 2 == 0 else N
+            sign = -1.0 / w0 if face % 2 == 0 else 1.0 / wN
+            if d == 0:
+                Sf[:, :, :, :, idx] += sign * jump
+            elif d == 1:
+                Sf[:, :, :, idx, :] += sign * jump
+            else:
+                Sf[:, :, idx, :, :] += sign * jump
         h = self.mesh.h
         K = -(2.0 / h)[None, :, None, None, None] * (vol + Sf)
         return np.ascontiguousarray(np.moveaxis(K, 0, 1))

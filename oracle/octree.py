@@ -55,32 +55,46 @@ def match_faces3(lo: np.ndarray, size: np.ndarray, D: int):
                   unequal sizes; ``large`` is A or B; (q1, q2) is the quadrant of the
                   large face that the small face covers (0 = lower half, 1 = upper half
                   along t1 and along t2).
+
+    Candidate neighbours are looked up by the position and size their -d face would have
+    (equal size, half size in each of four quadrants, or the aligned double-size square); the
+    overlapping areas found must cover the +d face exactly, else the mesh is not a 2:1-balanced
+    tiling and ValueError is raised.
     """
     conforming = []
     hanging = []
     n = len(size)
     for d in (0, 1, 2):
         t1, t2 = TANGENTIAL[d]
-        minus_faces = defaultdict(list)
-        for e in range(n):
-            minus_faces[int(lo[e, d])].append(e)
+        minus = {(int(lo[e, d]), int(lo[e, t1]), int(lo[e, t2]), int(size[e])): e for e in range(n)}
         for A in range(n):
             plane = int((lo[A, d] + size[A]) % D)
             a1, a2 = int(lo[A, t1]), int(lo[A, t2])
             sa = int(size[A])
-            for B in minus_faces[plane]:
+            cands = [(plane, a1, a2, sa), (plane, a1 - a1 % (2 * sa), a2 - a2 % (2 * sa), 2 * sa)]
+            if sa > 1:
+                h = sa // 2
+                cands += [(plane, a1 + i * h, a2 + j * h, h) for j in (0, 1) for i in (0, 1)]
+            covered = 0
+            for key in cands:
+                B = minus.get(key)
+                if B is None:
+                    continue
                 b1, b2 = int(lo[B, t1]), int(lo[B, t2])
                 sb = int(size[B])
                 o1 = min(a1 + sa, b1 + sb) - max(a1, b1)
                 o2 = min(a2 + sa, b2 + sb) - max(a2, b2)
                 if o1 <= 0 or o2 <= 0:
                     continue
+                covered += o1 * o2
                 if sa == sb:
                     conforming.append((A, B, d))
                 elif sa > sb:
                     hanging.append((A, B, d, A, int(b1 != a1), int(b2 != a2)))
                 else:
                     hanging.append((A, B, d, B, int(a1 != b1), int(a2 != b2)))
+            if covered != sa * sa:
+                raise ValueError(f"cell {A}: its +{d} face is not covered by 2:1-balanced neighbours")
     return conforming, hanging
 
 

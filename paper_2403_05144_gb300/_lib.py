@@ -104,6 +104,33 @@ SIGNATURES = [
                                           C.c_void_p, C.POINTER(C.c_double)]),
 ]
 
+
+class Perk3DProblem(C.Structure):
+    _fields_ = [("N", C.c_int), ("gamma", C.c_double), ("surface_flux", C.c_int), ("use_graph", C.c_int)]
+
+
+# the entry points of include/perk3d.h
+SIGNATURES_3D = [
+    ("perk3d_create", C.c_int, [C.POINTER(Perk3DProblem), C.POINTER(C.c_void_p)]),
+    ("perk3d_destroy", None, [C.c_void_p]),
+    ("perk3d_last_error", C.c_char_p, [C.c_void_p]),
+    ("perk3d_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("perk3d_mesh_upload", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.c_double, C.c_double]),
+    ("perk3d_mesh_faces", C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                    C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int64]),
+    ("perk3d_mesh_query", C.c_int, [C.c_void_p, C.POINTER(PerkMeshInfo)]),
+    ("perk3d_set_tableau", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk3d_rhs_full", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk3d_rhs_active", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("perk3d_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
+    ("perk3d_check", C.c_int, [C.c_void_p]),
+    ("perk3d_compute_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    ("perk3d_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
+    ("perk3d_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
+]
+SIGNATURES = SIGNATURES + SIGNATURES_3D
+
 _lib = None
 
 

@@ -21,8 +21,9 @@
 using namespace perk;
 
 // ---------------------------------------------------------------------------
-// Reference-element operators (N = 3 is the built case; the routines are generic).
-namespace {
+// Reference-element operators (N = 3 is the built case of the 2D path; the
+// routines are generic in N and shared with the 3D runtime).
+namespace perk {
 
 double legendre(int n, double x, double* dp) {
   // P_n(x) and P_n'(x) by the three-term recurrence
@@ -94,6 +95,23 @@ void lagrange_values(const std::vector<double>& x, double t, double* out) {
     out[j] = v;
   }
 }
+
+// Table of the volume kernel's logarithm: inv_c[j] = fl(1/c_j), c_j = 1 + (j + 1/2)/128,
+// and ln_c[j] = -ln(inv_c[j]) evaluated in extended precision, then rounded.
+std::vector<double> log_table() {
+  std::vector<double> t(2 * LOG_TABLE_SIZE);
+  for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
+    const long double c = 1.0L + (j + 0.5L) / LOG_TABLE_SIZE;
+    const double inv = (double)(1.0L / c);
+    t[j] = inv;
+    t[LOG_TABLE_SIZE + j] = (double)(-logl((long double)inv));
+  }
+  return t;
+}
+
+}  // namespace perk
+
+namespace {
 
 bool invert4(const double A[NN][NN], double inv[NN][NN]) {
   double M[NN][2 * NN];
@@ -206,18 +224,6 @@ Ops build_ops(double gamma, int surface_flux, int shock = PERK_SHOCK_OFF, double
   return o;
 }
 
-// Table of the volume kernel's logarithm: inv_c[j] = fl(1/c_j), c_j = 1 + (j + 1/2)/128,
-// and ln_c[j] = -ln(inv_c[j]) evaluated in extended precision, then rounded.
-std::vector<double> log_table() {
-  std::vector<double> t(2 * LOG_TABLE_SIZE);
-  for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
-    const long double c = 1.0L + (j + 0.5L) / LOG_TABLE_SIZE;
-    const double inv = (double)(1.0L / c);
-    t[j] = inv;
-    t[LOG_TABLE_SIZE + j] = (double)(-logl((long double)inv));
-  }
-  return t;
-}
 
 template <class T>
 struct DevBuf {

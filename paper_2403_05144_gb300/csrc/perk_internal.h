@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "perk.h"
 
 namespace perk {
@@ -79,13 +81,23 @@ struct UpdateArgs {
   const int32_t* member;  // ensemble member of each element (nullptr: member 0)
 };
 
+// ---- reference-element routines for any degree N (perk_host.cpp; host only) ----
+double legendre(int n, double x, double* dp);                              // P_n(x), P_n'(x)
+void lgl(int N, std::vector<double>& x, std::vector<double>& w);          // Gauss-Lobatto nodes, weights
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+void lagrange_values(const std::vector<double>& x, double t, double* out);  // l_j(t), j < x.size()
+std::vector<double> log_table();   // [inv_c[128], ln_c[128]] of the table-driven logarithm
+
 // ---- kernel launchers (perk_kernels.cu); all return cudaGetLastError() ----
 
+// mort_flag_bits: low bits of a mortar record's .w that carry its geometry (2 in 2D: dir,
+// large side; 3 in 3D: dir in two bits, large side); the P-ERK member is stored above them.
 cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int64_t n_mort, const int32_t* level,
                              const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* stage_minmem,
                              const int32_t* member, int n_members, int32_t* member_lmax /* [n_members] */,
                              int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
-                             int64_t* counts /* [3][MAX_S] */, int32_t* level_minmax /* [2] */);
+                             int64_t* counts /* [3][MAX_S] */, int32_t* level_minmax /* [2] */,
+                             int mort_flag_bits = 2);
 
 // per-member CFL reduction: out[m] = min over member m's elements of h_e / lambda_e (out pre-set to +inf)
 cudaError_t launch_dt_members(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level,

@@ -67,8 +67,8 @@ def slab_cells3(level_min: int = 4, level_max: int = 6, width: float = 1.0 / 32.
     """Graded mesh refined towards the plane z = L/2: within ``width`` (in domain units)
     of the plane the target level is ``level_max``; each further band of the next
     coarser level is two of its own cells thick, so face neighbours differ by at most
-    one level.  ``4, 6, 1/32``: a level-6 slab four cells thick, level-5 bands of two
-    cells on either side and a level-4 background (23,808 cells)."""
+    one level.  ``4, 6, 1/32``: a level-6 slab four cells thick (16,384 cells), level-5 bands
+    three cells thick on either side (6,144) and a level-4 background (3,072): 25,600 cells."""
 
     def target(l: int, iz: int) -> int:
         zc = (iz + 0.5) / (1 << l)

@@ -1,5 +1,5 @@
 """CPU tests of libperk's host side: the library loads, exports every entry
-point of include/perk.h, and its host utilities (reference nodes, disk-polynomial
+point of include/perk.h and include/perk3d.h, and its host utilities (reference nodes, disk-polynomial
 tableau, quadtree connectivity) agree with the oracle."""
 import os
 import re
@@ -24,9 +24,13 @@ def lib():
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "perk.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(perk_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(perk(?:3d)?_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(lib):
