@@ -25,6 +25,8 @@
 namespace perk3 {
 
 using perk::LOG_TABLE;
+using perk::dbits;
+using perk::series_only;
 using perk::log_tab;
 using perk::rcp_nr;
 using perk::series_2A;
@@ -83,7 +85,8 @@ struct __align__(16) NodeQ3 {
   double rho, lnrho, beta, lnbeta, v1, v2, v3, hv1, hv2, hv3, hp, pad;
 };
 
-__device__ __forceinline__ NodeQ3 node_q3(const double u[5], double gm1, const double* inv_c, const double* ln_c) {
+// node quantities without the two logarithms (set to 0; see series_only)
+__device__ __forceinline__ NodeQ3 node_q3_nolog(const double u[5], double gm1) {
   NodeQ3 q;
   // rho p = (gamma - 1)(rho E - |m|^2 / 2); one reciprocal gives 1/rho and rho/p
   const double rp = gm1 * fma(u[0], u[4], -0.5 * fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3])));
@@ -98,9 +101,16 @@ __device__ __forceinline__ NodeQ3 node_q3(const double u[5], double gm1, const d
   q.hv1 = 0.5 * q.v1;
   q.hv2 = 0.5 * q.v2;
   q.hv3 = 0.5 * q.v3;
-  q.lnrho = log_tab(u[0], inv_c, ln_c);
-  q.lnbeta = log_tab(q.beta, inv_c, ln_c);
+  q.lnrho = 0.0;
+  q.lnbeta = 0.0;
   q.pad = 0.0;
+  return q;
+}
+
+__device__ __forceinline__ NodeQ3 node_q3(const double u[5], double gm1, const double* inv_c, const double* ln_c) {
+  NodeQ3 q = node_q3_nolog(u, gm1);
+  q.lnrho = log_tab(q.rho, inv_c, ln_c);
+  q.lnbeta = log_tab(q.beta, inv_c, ln_c);
   return q;
 }
 
@@ -213,9 +223,9 @@ __device__ void flux3_hll(const double uL[5], const double uR[5], int d, const O
 __device__ void flux3_hlle(const double uL[5], const double uR[5], int d, const Ops3& o, double f[5]) {
   FS3 L, R;
   face_pair3(uL, uR, d, o, L, R);
-  const double sl = sqrt(L.rho), sr = sqrt(R.rho);
-  const double iws = rcp_nr(sl + sr);
-  const double wl = sl * iws, wr = sr * iws;
+  // Roe weights sqrt(rho_L) / (sqrt(rho_L) + sqrt(rho_R)) = 1 / (1 + q), q = sqrt(rho_R / rho_L)
+  const double qw = sqrt(R.rho * L.ir);
+  const double wl = rcp_nr(1.0 + qw), wr = qw * wl;
   const double vn = fma(wl, L.v, wr * R.v);
   const double vt1 = fma(wl, L.mt1 * L.ir, wr * (R.mt1 * R.ir));
   const double vt2 = fma(wl, L.mt2 * L.ir, wr * (R.mt2 * R.ir));
@@ -405,7 +415,7 @@ __device__ __forceinline__ int pslot3(int a, int b) {   // a < b
 }
 
 template <int NN, int YS, bool CHECK>
-__global__ void __launch_bounds__(V3_THREADS) k3_volume(Ops3 ops, int64_t n, const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(V3_THREADS, 6) k3_volume(Ops3 ops, int64_t n, const int32_t* __restrict__ elems,
                                                          const int32_t* __restrict__ level,
                                                          const int32_t* __restrict__ method, double two_over_len,
                                                          StageArgs sa, const double* __restrict__ surf,
@@ -417,6 +427,7 @@ __global__ void __launch_bounds__(V3_THREADS) k3_volume(Ops3 ops, int64_t n, con
   __shared__ NodeQ3 s_q[VE][NODES];
   __shared__ double s_flux[VE][5][NP];
   __shared__ double s_log[2 * LOG_TABLE];
+  __shared__ unsigned long long s_ext[VE][4];   // bit-pattern extremes: min rho, max rho, min rho/p, max rho/p
   const int t = threadIdx.x;
   const int le = t / NODES, node = t - le * NODES;
   const bool inblk = le < VE;
@@ -447,8 +458,24 @@ __global__ void __launch_bounds__(V3_THREADS) k3_volume(Ops3 ops, int64_t n, con
     }
   }
   for (int q = t; q < 2 * LOG_TABLE; q += V3_THREADS) s_log[q] = logt[q];
+  if (t < 4 * VE) s_ext[t >> 2][t & 3] = (t & 1) ? 0ull : ~0ull;
   __syncthreads();
-  if (inblk) s_q[le][node] = node_q3(y, ops.gm1, s_log, s_log + LOG_TABLE);
+  // node logarithms only in elements where some pair leaves the series range of the means
+  NodeQ3 q = node_q3_nolog(y, ops.gm1);
+  if (inblk) {
+    atomicMin(&s_ext[le][0], dbits(q.rho));
+    atomicMax(&s_ext[le][1], dbits(q.rho));
+    atomicMin(&s_ext[le][2], dbits(q.beta));
+    atomicMax(&s_ext[le][3], dbits(q.beta));
+  }
+  __syncthreads();
+  if (inblk) {
+    if (!series_only(s_ext[le][0], s_ext[le][1], s_ext[le][2], s_ext[le][3])) {
+      q.lnrho = log_tab(q.rho, s_log, s_log + LOG_TABLE);
+      q.lnbeta = log_tab(q.beta, s_log, s_log + LOG_TABLE);
+    }
+    s_q[le][node] = q;
+  }
   __syncthreads();
 
   // the symmetric pairs of the block's elements: pair pp = (dir, line, slot)

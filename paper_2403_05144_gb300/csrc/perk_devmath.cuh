@@ -74,4 +74,21 @@ __device__ __forceinline__ double series_2A(double u) {
   return fma(r, u, 2.0);
 }
 
+// Positive doubles order like their bit patterns: element-wide extremes by integer min/max.
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Whether every node pair of an element takes the series branch of both logarithmic means
+// (|b - a| < 0.03 (a + b) for rho and for rho/p), judged from the element's extremes of the two
+// variables (bit-pattern minima and maxima): max <= 1.06 min bounds (b - a)/(b + a) by
+// 0.06/2.06 < 0.0292 for every pair, far inside 0.03 whatever the rounding, so no node
+// logarithm is read and the element's logarithms need not be computed.  A non-positive or NaN
+// value anywhere makes the test fail (its bit pattern is the maximum), and the logarithms are
+// then computed as usual.
+__device__ __forceinline__ bool series_only(unsigned long long rmin, unsigned long long rmax, unsigned long long bmin,
+                                            unsigned long long bmax) {
+  const double r0 = bitsd(rmin), r1 = bitsd(rmax), b0 = bitsd(bmin), b1 = bitsd(bmax);
+  return r0 > 0.0 && r1 > 0.0 && b0 > 0.0 && b1 > 0.0 && r1 <= 1.06 * r0 && b1 <= 1.06 * b0;
+}
+
 }  // namespace perk

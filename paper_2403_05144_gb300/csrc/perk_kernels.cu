@@ -88,7 +88,8 @@ struct __align__(16) NodeQ {
   double rho, lnrho, beta, lnbeta, v1, v2, hv1, hv2, hp, pad;
 };
 
-__device__ __forceinline__ NodeQ node_q(const double u[4], double gm1, const double* inv_c, const double* ln_c) {
+// node quantities without the two logarithms (set to 0; see series_only)
+__device__ __forceinline__ NodeQ node_q_nolog(const double u[4], double gm1) {
   NodeQ q;
   // rho p = (gamma - 1) (rho E - |m|^2 / 2) needs no division; one reciprocal gives 1/rho and 1/p
   const double rp = gm1 * fma(u[0], u[3], -0.5 * fma(u[1], u[1], u[2] * u[2]));
@@ -101,7 +102,15 @@ __device__ __forceinline__ NodeQ node_q(const double u[4], double gm1, const dou
   q.beta = (u[0] * u[0]) * (u[0] * r);       // rho / p
   q.hv1 = 0.5 * q.v1;
   q.hv2 = 0.5 * q.v2;
-  q.lnrho = log_tab(u[0], inv_c, ln_c);
+  q.lnrho = 0.0;
+  q.lnbeta = 0.0;
+  q.pad = 0.0;
+  return q;
+}
+
+__device__ __forceinline__ NodeQ node_q(const double u[4], double gm1, const double* inv_c, const double* ln_c) {
+  NodeQ q = node_q_nolog(u, gm1);
+  q.lnrho = log_tab(q.rho, inv_c, ln_c);
   q.lnbeta = log_tab(q.beta, inv_c, ln_c);
   return q;
 }
@@ -502,7 +511,23 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   }
   for (int q = threadIdx.x; q < 2 * LOG_TABLE; q += VOL_ELEMS * NODES) s_log[q] = log_table[q];
   __syncthreads();
-  s_prim[le][t] = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE);
+  {
+    // node logarithms only where some pair of the element leaves the series range of the means
+    NodeQ q = node_q_nolog(y, ops.gm1);
+    unsigned long long rmin = dbits(q.rho), rmax = rmin, bmin = dbits(q.beta), bmax = bmin;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {   // the element's 16 lanes
+      rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o, 16));
+      rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o, 16));
+      bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o, 16));
+      bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o, 16));
+    }
+    if (!series_only(rmin, rmax, bmin, bmax)) {
+      q.lnrho = log_tab(q.rho, s_log, s_log + LOG_TABLE);
+      q.lnbeta = log_tab(q.beta, s_log, s_log + LOG_TABLE);
+    }
+    s_prim[le][t] = q;
+  }
   __syncwarp();
 
   // the three pairs of this thread: slots t, t + 16, t + 32 of 48
