@@ -18,7 +18,7 @@ pattern at 114,688 cells, the roofline case), shear (Navier-Stokes shear
 layer, third order, dynamic AMR), ensemble (64 KH members in one context),
 adjoint (discrete-adjoint gradient over 200 steps), spectrum (spectrum-optimised
 stability polynomials against the disk polynomials), tgv (3D Taylor-Green vortex on
-a three-level octree, P-ERK3 {3,4,6}, N = 2).
+an octree adapted by the enstrophy indicator, levels 4-6, P-ERK3 {3,4,6}, N = 2).
 
 Multi-GPU: the step does not shard across GPUs here; N ranks run N
 independent replicas of the workload (weak scaling, no collective on the
@@ -885,18 +885,53 @@ def run_spectrum(args) -> None:
 # + 81 pairs x 50   (the 2D pair's 44 plus the third velocity's mean, product and flux component)
 # + 27 nodes x 6 partners x 5 variables (accumulation) + 270 (lifting on up to three faces, Jacobian)
 VOL3_SLOTS_PER_ELEM = 27 * 64 + 81 * 50 + 27 * 6 * 5 + 270
-TGV = dict(name="taylor_green_3d_octree_levels4-6_slab_n2_hlle", N=2, flux="hlle", E=[3, 4, 6], cfl=0.5,
-           level_min=4, level_max=6, width=1.0 / 32.0, x0=0.0, L=2.0 * math.pi, mach=0.1, t_end=20.0)
+TGV = dict(name="taylor_green_3d_octree_enstrophy_amr_levels4-6_n2_hlle", N=2, flux="hlle", E=[3, 4, 6], cfl=0.5,
+           base_level=4, amr=dict(level_min=4, level_max=6, refine_above=1.2, coarsen_below=0.3), n_amr=5,
+           init_cycles=2, x0=0.0, L=2.0 * math.pi, mach=0.1, t_end=20.0)
 
 
-def tgv_problem():
-    from perk_inputs.octree import nodal_state3, slab_cells3, taylor_green
+def tgv_initial():
+    from perk_inputs.octree import nodal_state3, taylor_green, uniform_cells3
     from paper_2403_05144_gb300 import reference_nodes
 
-    cells = slab_cells3(TGV["level_min"], TGV["level_max"], TGV["width"])
+    cells = uniform_cells3(TGV["base_level"])
     x, _ = reference_nodes(TGV["N"])
-    U0 = nodal_state3(taylor_green, cells, TGV["x0"], TGV["L"], x, mach=TGV["mach"])
-    return cells, U0
+    return cells, nodal_state3(taylor_green, cells, TGV["x0"], TGV["L"], x, mach=TGV["mach"])
+
+
+class Run3:
+    """One 3D run: the Taylor-Green state on 16^3 cells adapted by the enstrophy indicator
+    (init_cycles cycles), then P-ERK steps with an AMR cycle every n_amr steps (the step size
+    recomputed after each), all through the library."""
+
+    def __init__(self, torch, E):
+        from paper_2403_05144_gb300.perk3d import Perk3DSolver
+
+        cells, U0 = tgv_initial()
+        self.s = Perk3DSolver(N=TGV["N"], surface_flux=TGV["flux"], use_graph=True)
+        self.s.upload_mesh(cells, TGV["x0"], TGV["L"])
+        self.s.set_perk3_disk(E)
+        self.U = torch.from_numpy(U0).cuda()
+        self.k = 0
+        self.t = 0.0
+        self.cycles = 0
+        for _ in range(TGV["init_cycles"]):
+            self.adapt()
+        self.cycles = 0
+
+    def adapt(self):
+        self.U = self.s.adapt(self.U, **TGV["amr"])
+        self.dt = self.s.compute_dt(self.U, TGV["cfl"])
+        self.units = self.s.info()["dof_stage_updates"]
+        self.cycles += 1
+
+    def step(self) -> int:
+        if self.k > 0 and self.k % TGV["n_amr"] == 0:
+            self.adapt()
+        self.s.step(self.U, self.dt)
+        self.k += 1
+        self.t += self.dt
+        return self.units
 
 
 def tgv_oracle_sample(cells, U, n_stages: int = 0, budget_s: float = 10.0):
@@ -925,9 +960,10 @@ def tgv_oracle_sample(cells, U, n_stages: int = 0, budget_s: float = 10.0):
 
 
 def run_tgv(args) -> None:
-    """3D Taylor-Green vortex (the paper's Sec. 7.1.3 initial state, Mach 0.1) on a static
-    three-level octree (levels 4-6, 25,600 cells, N = 2: 691,200 nodes), HLLE surface flux,
-    P-ERK3 {3, 4, 6} against the standalone six-stage member (full RHS every stage)."""
+    """3D Taylor-Green vortex (the paper's Sec. 7.1.3 initial state, Mach 0.1): 16^3 cells adapted
+    twice by the enstrophy indicator (levels 4-6), N = 2, HLLE, an AMR cycle every five steps
+    inside the timed region; P-ERK3 {3, 4, 6} against the standalone six-stage member (full RHS
+    every stage, same AMR)."""
     import torch
 
     rank, local_rank, world = dist_info()
@@ -937,108 +973,98 @@ def run_tgv(args) -> None:
         dist.init_process_group("nccl")
     from paper_2403_05144_gb300 import PerkError, measure_fp64
     from paper_2403_05144_gb300.build import build
-    from paper_2403_05144_gb300.perk3d import Perk3DSolver
 
     build()
-    cells, U0 = tgv_problem()
     S = max(TGV["E"])
-
-    def make(E):
-        s = Perk3DSolver(N=TGV["N"], surface_flux=TGV["flux"], use_graph=True)
-        s.upload_mesh(cells, TGV["x0"], TGV["L"])
-        s.set_perk3_disk(E)
-        return s
-
-    perk, full = make(TGV["E"]), make([S])
-    Up = torch.from_numpy(U0).cuda()
-    Uf = Up.clone()
-    dt = perk.compute_dt(Up, TGV["cfl"])
+    perk, full = Run3(torch, TGV["E"]), Run3(torch, [S])
+    info0 = perk.s.info()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(args.warmup):
-        perk.step(Up, dt)
-        full.step(Uf, dt)
+        perk.step()
+        full.step()
     torch.cuda.synchronize()
-    units_step = perk.info()["dof_stage_updates"]
-    units_full = full.info()["dof_stage_updates"]
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(solver, U):
+    def timed(run):
         st = torch.cuda.current_stream()
-        evs = []
+        evs, units = [], 0
+        c0 = run.cycles
         for _ in range(args.steps):
             flush.fill_(1.0)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(st)
-            solver.step(U, dt)
+            units += run.step()
             b.record(st)
             evs.append((a, b))
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs)
+        return sum(a.elapsed_time(b) for a, b in evs), units, run.cycles - c0
 
     with ClockSampler(local_rank) as clk:
         barrier()
-        ms = timed(perk, Up)
+        ms, units, cycles = timed(perk)
         barrier()
-        ms_full = timed(full, Uf)
+        ms_full, units_full, _ = timed(full)
         barrier()
-    perk.check()
-    full.check()
+    perk.s.check()
+    full.s.check()
     ms, ms_full = max_over_ranks([ms, ms_full], world, "cuda")
-    value = replica_rate(units_step * args.steps, ms, world)
-    value_full = replica_rate(units_full * args.steps, ms_full, world)
-    info = perk.info()
+    value = replica_rate(units, ms, world)
+    value_full = replica_rate(units_full, ms_full, world)
+    info = perk.s.info()
 
     fma_flops, _, _ = measure_fp64()
-    Upr = Up.clone()
+    Upr = perk.U.clone()
     acc = None
     for _ in range(args.steps):
-        acc = perk.step_profiled(Upr, dt, acc)
+        acc = perk.s.step_profiled(Upr, perk.dt, acc)
     vol_ms, vol_launches = acc.ms[1], acc.launches[1]
     achieved = 2.0 * VOL3_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
     kernel_ms_total = sum(acc.ms[k] for k in range(3))
 
-    # end to end through the public API with the state in pinned host memory
+    # end to end through the public API with the state in pinned host memory (AMR included)
     st = torch.cuda.current_stream()
-    Uh = Up.cpu().pin_memory()
+    Uh = perk.U.cpu().pin_memory()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    h2d = d2h = units_e2e = 0
     barrier()
     e0.record(st)
     for _ in range(args.steps):
-        Ud = Uh.to("cuda", non_blocking=True)
-        perk.step(Ud, dt)
-        Uh.copy_(Ud, non_blocking=True)
+        perk.U = Uh.to("cuda", non_blocking=True)
+        h2d += Uh.numel() * 8
+        units_e2e += perk.step()
+        if perk.U.shape != Uh.shape:
+            Uh = torch.empty(perk.U.shape, dtype=torch.float64).pin_memory()
+        Uh.copy_(perk.U, non_blocking=True)
+        d2h += Uh.numel() * 8
     e1.record(st)
     torch.cuda.synchronize()
     (ms_e2e,) = max_over_ranks([e0.elapsed_time(e1)], world, "cuda")
-    nbytes = Uh.numel() * 8
 
-    # simulated time per wall second over a fixed wall budget (t_end = 20 is out of reach of it)
+    # simulated time per wall second over a fixed wall budget (t_end = 20 is out of its reach)
     tend = {"t_end": TGV["t_end"]}
     for key, E in (("perk", TGV["E"]), ("full_rk", [S])):
-        s = make(E)
-        U = torch.from_numpy(U0).cuda()
+        run = Run3(torch, E)
         torch.cuda.synchronize()
-        t, n, status = 0.0, 0, "budget"
+        status = "budget"
         t0 = time.perf_counter()
         try:
-            while t < TGV["t_end"] - 1e-12 and time.perf_counter() - t0 < args.t_end_budget:
-                for _ in range(50):
-                    s.step(U, dt)
-                s.check()
-                t += 50 * dt
-                n += 50
-            if t >= TGV["t_end"] - 1e-12:
+            while run.t < TGV["t_end"] - 1e-12 and time.perf_counter() - t0 < args.t_end_budget:
+                for _ in range(TGV["n_amr"] * 10):
+                    run.step()
+                run.s.check()
+            if run.t >= TGV["t_end"] - 1e-12:
                 status = "reached t_end"
         except PerkError:
             status = "rejected step"
         wall = time.perf_counter() - t0
-        tend[key] = {"t": t, "steps": n, "wall_s": wall, "status": status, "sim_time_per_wall_s": t / wall}
+        tend[key] = {"t": run.t, "steps": run.k, "amr_cycles": run.cycles, "wall_s": wall, "status": status,
+                     "sim_time_per_wall_s": run.t / wall, "n_elem_end": run.s.n_elem}
     tend["sim_time_ratio_perk_over_full_rk"] = (tend["perk"]["sim_time_per_wall_s"]
                                                / tend["full_rk"]["sim_time_per_wall_s"])
 
@@ -1046,12 +1072,17 @@ def run_tgv(args) -> None:
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": TGV["name"], "n_elem": info["n_elem"], "levels": [info["level_min"], info["level_max"]],
-                   "N": TGV["N"], "family": TGV["E"], "stages": S, "surface_flux": TGV["flux"], "cfl": TGV["cfl"],
-                   "dt": dt, "mach": TGV["mach"], "equations": "euler",
-                   "dof_stage_updates_per_step": units_step, "l2": "flushed (256 MB write) before every timed step",
+        "config": {"workload": TGV["name"], "n_elem": info["n_elem"], "n_elem_initial": info0["n_elem"],
+                   "levels": [info["level_min"], info["level_max"]], "N": TGV["N"], "family": TGV["E"],
+                   "stages": S, "surface_flux": TGV["flux"], "cfl": TGV["cfl"], "dt": perk.dt, "mach": TGV["mach"],
+                   "equations": "euler",
+                   "amr": {**TGV["amr"], "indicator": "enstrophy", "every_steps": TGV["n_amr"],
+                           "in_timed_region": True, "cycles_timed": cycles},
+                   "dof_stage_updates_per_step": units / args.steps,
+                   "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"{world} independent replica(s)", "graph": True},
-        "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps, "dof_stage_updates_per_step": units_full,
+        "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps,
+                    "dof_stage_updates_per_step": units_full / args.steps,
                     "ratio_ms_per_step_full_over_perk": ms_full / ms},
         "t_end": tend,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
@@ -1060,17 +1091,20 @@ def run_tgv(args) -> None:
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
                      "work_per_element_stage": {"fp64_slots": VOL3_SLOTS_PER_ELEM, "flops": 2 * VOL3_SLOTS_PER_ELEM}},
-        "e2e": {"value": replica_rate(units_step * args.steps, ms_e2e, world), "unit": UNIT,
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "gpu_launches": args.steps * (2 * S + 1),
+        "e2e": {"value": replica_rate(units_e2e, ms_e2e, world), "unit": UNIT,
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        # per step 2 launches per stage + the commit; per AMR cycle: indicator, transfer, partition,
+        # the step-size reset and reduction
+        "gpu_launches": args.steps * (2 * S + 1) + 5 * cycles,
         "clocks": clk.summary(),
     }
     if rank == 0:
         if world == 1:
-            u, sec, k, SS = tgv_oracle_sample(cells, U0)
+            u, sec, k, SS = tgv_oracle_sample(perk.s.cells, perk.U.cpu().numpy())
             line["cpu_baseline"] = {"value": u / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                                     "sample": f"{k} partitioned stage evaluations (cycling over S={SS}) of the "
-                                              f"{len(cells)}-cell octree, {sec:.1f} s, numpy float64, one thread"}
+                                              f"{perk.s.n_elem}-cell adapted octree, {sec:.1f} s, numpy float64, "
+                                              f"one thread"}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -1080,12 +1114,18 @@ def run_reference_tgv(args) -> None:
     rank, _, world = dist_info()
     if rank != 0:
         return
+    from oracle.amr3d import adapt3
     from oracle.lgl import lgl_nodes_weights
-    from perk_inputs.octree import nodal_state3, slab_cells3, taylor_green
+    from oracle.octree import OctreeMesh
+    from perk_inputs.octree import nodal_state3, taylor_green, uniform_cells3
 
-    cells = slab_cells3(TGV["level_min"], TGV["level_max"], TGV["width"])
+    cells = uniform_cells3(TGV["base_level"])
     x, _ = lgl_nodes_weights(TGV["N"])
     U = nodal_state3(taylor_green, cells, TGV["x0"], TGV["L"], x, mach=TGV["mach"])
+    mesh = OctreeMesh(np.asarray(cells), TGV["x0"], TGV["L"])
+    for _ in range(TGV["init_cycles"]):          # the same initial adaptation as the library run
+        mesh, U, _ = adapt3(mesh, U, **TGV["amr"], N=TGV["N"])
+    cells = [tuple(c) for c in mesh.cells.tolist()]
     tgv_oracle_sample(cells, U, n_stages=args.warmup)
     units, sec, k, S = tgv_oracle_sample(cells, U, n_stages=args.steps)
     value = units / sec
@@ -1093,10 +1133,10 @@ def run_reference_tgv(args) -> None:
             "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": TGV["name"], "n_elem": len(cells), "family": TGV["E"], "surface_flux": TGV["flux"],
-                       "step": "one partitioned stage evaluation of the 3D oracle"},
+                       "step": "one partitioned stage evaluation of the 3D oracle on the initially adapted octree"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"{args.steps} stage evaluations (cycling over the S={S} stages) of the "
-                                       f"{len(cells)}-cell octree"},
+                                       f"{len(cells)}-cell initially adapted octree"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -108,6 +108,38 @@ perk_status perk3d_step_profiled(perk3d_ctx* ctx, double* d_U, double dt, perk_k
 /* Steps, element-stage evaluations and node-stage (DoF-stage) updates since creation. */
 perk_status perk3d_get_counters(const perk3d_ctx* ctx, perk_counters* out);
 
+/* Adaptive refinement (Sec. 7.1.3: the enstrophy indicator of Eq. Enstrophy; the AMR cycle of
+ * Sec. 6.2 before the partition is re-assigned).  Thresholds apply to the indicator below. */
+typedef struct {
+  int32_t level_min, level_max;   /* allowed levels of the adapted mesh */
+  double refine_above;            /* refine cells whose indicator exceeds this */
+  double coarsen_below;           /* cells below this may coarsen (all eight siblings together) */
+} perk3d_amr_params;
+
+/* Indicator per element (device output d_eta[n_elem]): the largest nodal value of the enstrophy
+ * rho |curl v|^2 / 2, the velocity derivatives taken from the element's nodal polynomial,
+ * (2/h) D along each axis.  Asynchronous. */
+perk_status perk3d_amr_indicator(perk3d_ctx* ctx, const double* d_U, double* d_eta);
+
+/* Plans one AMR cycle on the host: desired levels either from the indicator of d_U and prm
+ * (level + 1 above refine_above up to level_max, level - 1 below coarsen_below down to
+ * level_min), or given (desired: host array n_elem, each within one level of the cell's), then
+ * raised to their least fixed point under the sibling rule (a cell coarsens only with its seven
+ * siblings, all wanting to) and the 2:1 rule across faces.  *n_new receives the number of
+ * cells of the new mesh.  Blocks when the indicator is computed. */
+perk_status perk3d_adapt_plan(perk3d_ctx* ctx, const perk3d_amr_params* prm, const int32_t* desired, const double* d_U,
+                              int64_t* n_new);
+
+/* Applies the plan: d_Unew (n_new elements, caller-owned, distinct from d_Uold) receives the
+ * transferred solution (kept cells copied, refined cells' children interpolated from the
+ * parent polynomial, coarsened groups L2-projected onto the parent), and the new leaves (in
+ * Morton order) become the context's mesh with its connectivity and partition rebuilt.  A plan
+ * that changes no cell copies the state and keeps the mesh. */
+perk_status perk3d_adapt_commit(perk3d_ctx* ctx, const double* d_Uold, double* d_Unew);
+
+/* The current leaves (host, 4 * n_elem int32: level, ix, iy, iz), cap in cells. */
+perk_status perk3d_get_cells(const perk3d_ctx* ctx, int32_t* cells, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,11 @@ class Perk3DProblem(C.Structure):
     _fields_ = [("N", C.c_int), ("gamma", C.c_double), ("surface_flux", C.c_int), ("use_graph", C.c_int)]
 
 
+class Perk3DAmrParams(C.Structure):
+    _fields_ = [("level_min", C.c_int32), ("level_max", C.c_int32), ("refine_above", C.c_double),
+                ("coarsen_below", C.c_double)]
+
+
 # the entry points of include/perk3d.h
 SIGNATURES_3D = [
     ("perk3d_create", C.c_int, [C.POINTER(Perk3DProblem), C.POINTER(C.c_void_p)]),
@@ -128,6 +133,11 @@ SIGNATURES_3D = [
     ("perk3d_compute_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk3d_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
     ("perk3d_get_counters", C.c_int, [C.c_void_p, C.POINTER(PerkCounters)]),
+    ("perk3d_amr_indicator", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk3d_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(Perk3DAmrParams), C.POINTER(C.c_int32), C.c_void_p,
+                                    C.POINTER(C.c_int64)]),
+    ("perk3d_adapt_commit", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk3d_get_cells", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
 ]
 SIGNATURES = SIGNATURES + SIGNATURES_3D
 

@@ -66,6 +66,15 @@ bool build_ops3(int N, double gamma, int surface_flux, Ops3& o) {
   }
   for (int i = 0; i < nn; ++i)
     for (int j = 0; j < nn; ++j) o.dsplit[i][j] = (i == j) ? 0.0 : 2.0 * (lam[j] / lam[i]) / (x[i] - x[j]);
+  for (int i = 0; i < nn; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < nn; ++j)
+      if (j != i) {
+        o.dmat[i][j] = 0.5 * o.dsplit[i][j];
+        row += o.dmat[i][j];
+      }
+    o.dmat[i][i] = -row;   // a derivative matrix annihilates constants
+  }
   o.inv_w0 = 1.0 / w[0];
   for (int k = 0; k < nn; ++k) {
     perk::lagrange_values(x, 0.5 * (x[k] - 1.0), o.p_lo[k]);
@@ -245,6 +254,15 @@ struct perk3d_ctx {
   int64_t n_elem = 0, n_if = 0, n_mort = 0;
   double x0 = 0.0, length = 1.0;
   std::vector<int32_t> h_level;
+  std::vector<int32_t> h_cells;                 // [n_elem][4] (level, ix, iy, iz)
+  std::vector<std::pair<int32_t, int32_t>> h_pairs;   // face neighbours (interfaces; large-small of mortars)
+
+  // pending AMR plan (perk3d_adapt_plan -> perk3d_adapt_commit)
+  bool has_plan = false, plan_identity = false;
+  int64_t plan_n = 0;                           // cells of the planned mesh
+  std::vector<int32_t> plan_cells, plan_map;    // [m][4], [m][9]
+  Buf<int32_t> d_map;
+  Buf<double> d_eta;
 
   bool has_tab = false;
   int order = 2, S = 0, R = 0;
@@ -487,8 +505,9 @@ void perk3d_destroy(perk3d_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto* b : {&ctx->d_level, &ctx->d_method, &ctx->d_elem_sorted, &ctx->d_minmem, &ctx->d_minmax,
-                  &ctx->d_member_lmax})
+                  &ctx->d_member_lmax, &ctx->d_map})
     b->release();
+  ctx->d_eta.release();
   for (auto* b : {&ctx->d_if_raw, &ctx->d_mort_raw, &ctx->d_if_sorted, &ctx->d_mort_sorted, &ctx->d_msmall})
     b->release();
   for (auto* b : {&ctx->d_surf, &ctx->d_K1, &ctx->d_Ka, &ctx->d_Kb, &ctx->d_dt, &ctx->d_dt_out, &ctx->d_logtab})
@@ -549,6 +568,15 @@ perk_status perk3d_mesh_upload(perk3d_ctx* ctx, int64_t n_cells, const int32_t* 
   ctx->length = length;
   ctx->h_level.resize(n_cells);
   for (int64_t q = 0; q < n_cells; ++q) ctx->h_level[q] = cells[4 * q];
+  ctx->h_cells.assign(cells, cells + 4 * n_cells);
+  ctx->h_pairs.clear();
+  ctx->h_pairs.reserve(c.ifs.size() + 4 * c.morts.size());
+  for (const int4& f : c.ifs) ctx->h_pairs.emplace_back(f.x, f.y);
+  for (const int4& m : c.morts) {
+    const int4 sm = c.msmall[m.z];
+    for (int32_t q : {sm.x, sm.y, sm.z, sm.w}) ctx->h_pairs.emplace_back(m.x, q);
+  }
+  ctx->has_plan = false;
   const size_t ne = (size_t)n_cells;
   P3_CUDA(ctx, ctx->d_level.ensure(ne));
   P3_CUDA(ctx, ctx->d_method.ensure(ne));
@@ -562,6 +590,7 @@ perk_status perk3d_mesh_upload(perk3d_ctx* ctx, int64_t n_cells, const int32_t* 
   P3_CUDA(ctx, ctx->d_K1.ensure(ne * elem3(ctx->nn)));
   P3_CUDA(ctx, ctx->d_Ka.ensure(ne * elem3(ctx->nn)));
   P3_CUDA(ctx, ctx->d_Kb.ensure(ne * elem3(ctx->nn)));
+  P3_CUDA(ctx, ctx->d_eta.ensure(ne));
   P3_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
                                ctx->stream));
   if (!c.ifs.empty())
@@ -762,6 +791,208 @@ perk_status perk3d_compute_dt(perk3d_ctx* ctx, const double* d_U, double cfl, do
 perk_status perk3d_get_counters(const perk3d_ctx* ctx, perk_counters* out) {
   if (!ctx || !out) return PERK_E_INVALID_ARG;
   *out = ctx->counters;
+  return PERK_OK;
+}
+
+perk_status perk3d_amr_indicator(perk3d_ctx* ctx, const double* d_U, double* d_eta) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  if (!d_U || !d_eta) return fail(ctx, PERK_E_INVALID_ARG, "null array");
+  P3_CUDA(ctx, launch_enstrophy3(ctx->stream, ctx->ops, ctx->n_elem, d_U, ctx->d_level.p, 2.0 / ctx->length, d_eta));
+  return PERK_OK;
+}
+
+perk_status perk3d_adapt_plan(perk3d_ctx* ctx, const perk3d_amr_params* prm, const int32_t* desired, const double* d_U,
+                              int64_t* n_new) {
+  if (!ctx || !n_new) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  const int64_t n = ctx->n_elem;
+  const int32_t* c = ctx->h_cells.data();
+  std::vector<int32_t> d(n);
+  if (desired) {
+    for (int64_t e = 0; e < n; ++e) {
+      if (desired[e] < c[4 * e] - 1 || desired[e] > c[4 * e] + 1 || desired[e] < 0 || desired[e] > MAX_LEVEL3)
+        return fail(ctx, PERK_E_INVALID_ARG, "desired level of cell %lld must differ by at most one", (long long)e);
+      d[e] = desired[e];
+    }
+  } else {
+    if (!prm || !d_U) return fail(ctx, PERK_E_INVALID_ARG, "need AMR parameters and U");
+    if (prm->level_min < 0 || prm->level_max > MAX_LEVEL3 || prm->level_min > prm->level_max)
+      return fail(ctx, PERK_E_INVALID_ARG, "bad level range");
+    P3_CUDA(ctx, launch_enstrophy3(ctx->stream, ctx->ops, n, d_U, ctx->d_level.p, 2.0 / ctx->length, ctx->d_eta.p));
+    std::vector<double> eta(n);
+    P3_CUDA(ctx, cudaMemcpyAsync(eta.data(), ctx->d_eta.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    P3_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t e = 0; e < n; ++e) {
+      const int l = c[4 * e];
+      d[e] = l;
+      if (eta[e] > prm->refine_above && l < prm->level_max)
+        d[e] = l + 1;
+      else if (eta[e] < prm->coarsen_below && l > prm->level_min && !(eta[e] > prm->refine_above))
+        d[e] = l - 1;
+    }
+  }
+  // no cell asks for a change: the current (balanced) mesh is the fixed point, nothing to plan
+  {
+    bool same = true;
+    for (int64_t e = 0; e < n && same; ++e) same = d[e] == c[4 * e];
+    if (same) {
+      ctx->plan_identity = true;
+      ctx->plan_n = n;
+      ctx->plan_cells.clear();
+      ctx->has_plan = true;
+      *n_new = n;
+      return PERK_OK;
+    }
+  }
+  // least fixed point of the sibling rule (eight leaves of one parent coarsen together) and the
+  // 2:1 rule across faces
+  std::unordered_map<uint64_t, int32_t> gid;
+  std::vector<int32_t> group_of(n, -1), gcount, gmembers;
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = c[4 * e];
+    if (l == 0) continue;
+    const uint64_t k = key3(l, c[4 * e + 1] >> 1, c[4 * e + 2] >> 1, c[4 * e + 3] >> 1);
+    auto it = gid.find(k);
+    int32_t g;
+    if (it == gid.end()) {
+      g = (int32_t)gcount.size();
+      gid.emplace(k, g);
+      gcount.push_back(0);
+      gmembers.insert(gmembers.end(), 8, -1);
+    } else {
+      g = it->second;
+    }
+    if (gcount[g] < 8) gmembers[8 * g + gcount[g]] = (int32_t)e;
+    gcount[g] += 1;
+    group_of[e] = g;
+  }
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int64_t e = 0; e < n; ++e) {
+      if (d[e] >= c[4 * e]) continue;
+      const int32_t g = group_of[e];
+      bool ok = g >= 0 && gcount[g] == 8;
+      for (int q = 0; ok && q < 8; ++q) ok = d[gmembers[8 * g + q]] < c[4 * gmembers[8 * g + q]];
+      if (ok) continue;
+      if (g < 0) {
+        d[e] = c[4 * e];
+        changed = true;
+        continue;
+      }
+      for (int q = 0; q < 8 && q < gcount[g]; ++q) {
+        const int32_t m = gmembers[8 * g + q];
+        if (d[m] < c[4 * m]) {
+          d[m] = c[4 * m];
+          changed = true;
+        }
+      }
+    }
+    for (const auto& pr : ctx->h_pairs) {
+      const int32_t a = pr.first, b = pr.second;
+      if (d[a] > d[b] + 1) {
+        d[b] = d[a] - 1;
+        changed = true;
+      } else if (d[b] > d[a] + 1) {
+        d[a] = d[b] - 1;
+        changed = true;
+      }
+    }
+  }
+  bool identity = true;
+  for (int64_t e = 0; e < n && identity; ++e) identity = d[e] == c[4 * e];
+  ctx->plan_identity = identity;
+  // new leaves (Morton order) and transfer records
+  std::unordered_map<uint64_t, int32_t> old;
+  old.reserve((size_t)n * 2);
+  int lmax = 0;
+  for (int64_t e = 0; e < n; ++e) {
+    old.emplace(key3(c[4 * e], c[4 * e + 1], c[4 * e + 2], c[4 * e + 3]), (int32_t)e);
+    lmax = std::max(lmax, d[e]);
+  }
+  struct NewCell {
+    int32_t l, x, y, z;
+  };
+  std::vector<NewCell> nc;
+  nc.reserve((size_t)n * 2);
+  std::unordered_map<uint64_t, int32_t> seen;
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = c[4 * e], x = c[4 * e + 1], y = c[4 * e + 2], z = c[4 * e + 3];
+    if (d[e] == l + 1) {
+      for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cx = 0; cx < 2; ++cx) nc.push_back({l + 1, 2 * x + cx, 2 * y + cy, 2 * z + cz});
+    } else if (d[e] == l) {
+      nc.push_back({l, x, y, z});
+    } else if (seen.emplace(key3(l - 1, x >> 1, y >> 1, z >> 1), 1).second) {
+      nc.push_back({l - 1, x >> 1, y >> 1, z >> 1});
+    }
+  }
+  std::vector<std::pair<uint64_t, int64_t>> order(nc.size());
+  for (size_t k = 0; k < nc.size(); ++k) order[k] = {morton3(nc[k].l, nc[k].x, nc[k].y, nc[k].z, lmax), (int64_t)k};
+  std::sort(order.begin(), order.end());
+  const int64_t m = (int64_t)nc.size();
+  ctx->plan_cells.resize(4 * m);
+  ctx->plan_map.assign(9 * m, 0);
+  for (int64_t k = 0; k < m; ++k) {
+    const NewCell& q = nc[order[k].second];
+    int32_t* cc = &ctx->plan_cells[4 * k];
+    cc[0] = q.l;
+    cc[1] = q.x;
+    cc[2] = q.y;
+    cc[3] = q.z;
+    int32_t* r = &ctx->plan_map[9 * k];
+    auto it = old.find(key3(q.l, q.x, q.y, q.z));
+    if (it != old.end()) {
+      r[0] = 0;
+      r[1] = it->second;
+      continue;
+    }
+    auto par = q.l > 0 ? old.find(key3(q.l - 1, q.x >> 1, q.y >> 1, q.z >> 1)) : old.end();
+    if (par != old.end()) {
+      r[0] = 1 | ((q.x & 1) << 2) | ((q.y & 1) << 3) | ((q.z & 1) << 4);
+      r[1] = par->second;
+      continue;
+    }
+    r[0] = 2;
+    for (int ch = 0; ch < 8; ++ch) {
+      auto ci = old.find(key3(q.l + 1, 2 * q.x + (ch & 1), 2 * q.y + ((ch >> 1) & 1), 2 * q.z + (ch >> 2)));
+      if (ci == old.end()) return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
+      r[1 + ch] = ci->second;
+    }
+  }
+  ctx->plan_n = m;
+  ctx->has_plan = true;
+  *n_new = m;
+  return PERK_OK;
+}
+
+perk_status perk3d_adapt_commit(perk3d_ctx* ctx, const double* d_Uold, double* d_Unew) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_plan) return fail(ctx, PERK_E_NOT_READY, "no AMR plan");
+  if (!d_Uold || !d_Unew || d_Uold == d_Unew) return fail(ctx, PERK_E_INVALID_ARG, "need distinct old and new U");
+  const int64_t m = ctx->plan_n;
+  if (ctx->plan_identity) {
+    P3_CUDA(ctx, cudaMemcpyAsync(d_Unew, d_Uold, (size_t)m * elem3(ctx->nn) * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->has_plan = false;
+    return PERK_OK;
+  }
+  P3_CUDA(ctx, ctx->d_map.ensure((size_t)9 * m));
+  P3_CUDA(ctx, cudaMemcpyAsync(ctx->d_map.p, ctx->plan_map.data(), ctx->plan_map.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, ctx->stream));
+  P3_CUDA(ctx, launch_transfer3(ctx->stream, ctx->ops, m, ctx->d_map.p, d_Uold, d_Unew));
+  ctx->has_plan = false;
+  const std::vector<int32_t> cells = std::move(ctx->plan_cells);
+  ctx->plan_cells.clear();
+  return perk3d_mesh_upload(ctx, m, cells.data(), ctx->x0, ctx->length);
+}
+
+perk_status perk3d_get_cells(const perk3d_ctx* ctx, int32_t* cells, int64_t cap) {
+  if (!ctx || !cells) return PERK_E_INVALID_ARG;
+  if (cap < ctx->n_elem) return PERK_E_INVALID_ARG;
+  std::copy(ctx->h_cells.begin(), ctx->h_cells.end(), cells);
   return PERK_OK;
 }
 

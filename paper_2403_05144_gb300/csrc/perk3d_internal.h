@@ -24,6 +24,7 @@ inline int64_t surf3(int nn) { return 6 * NV3 * nn * nn; }      // doubles of fa
 struct Ops3 {
   int nn;
   double dsplit[MAXNN][MAXNN];   // 2 D_ij off the diagonal, 0 on it
+  double dmat[MAXNN][MAXNN];     // the derivative matrix D_ij = l_j'(x_i)
   double inv_w0;                 // 1 / w_0 = 1 / w_N
   double p_lo[MAXNN][MAXNN];     // large-face trace -> lower half (interpolation, along one axis)
   double p_hi[MAXNN][MAXNN];
@@ -50,5 +51,13 @@ cudaError_t launch_commit3(cudaStream_t st, int64_t n_doubles, const UpdateArgs&
 // out[0] = min_e h_e / ((N+1) lambda_e) as a double (out is reset to +inf first).
 cudaError_t launch_dt3(cudaStream_t st, int nn, int64_t n_elem, const double* U, const int32_t* level, double length,
                        double gamma, double* out);
+
+// eta[e] = max over nodes of rho |curl v|^2 / 2 (the enstrophy indicator)
+cudaError_t launch_enstrophy3(cudaStream_t st, const Ops3& ops, int64_t n_elem, const double* U,
+                              const int32_t* level, double two_over_len, double* eta);
+// AMR transfer: map[9 * q] = kind | cx << 2 | cy << 3 | cz << 4 (kind 0 copy, 1 refine, 2 coarsen),
+// then the source cells (copy/refine: one; coarsen: the eight children by cx + 2 cy + 4 cz)
+cudaError_t launch_transfer3(cudaStream_t st, const Ops3& ops, int64_t n_new, const int32_t* map, const double* Uold,
+                             double* Unew);
 
 }  // namespace perk3

@@ -622,6 +622,122 @@ __global__ void __launch_bounds__(DT3_THREADS) k3_dt(int64_t n_nodes, const doub
 __global__ void k3_set(double* p, double v) { *p = v; }
 
 // ---------------------------------------------------------------------------
+// AMR: enstrophy indicator and solution transfer.
+
+// eta[e] = max over the element's nodes of rho |curl v|^2 / 2; one thread per node, VE elements
+// per 128-thread block; derivatives (2/h) D along each axis from the velocities in shared memory
+template <int NN>
+__global__ void __launch_bounds__(V3_THREADS) k3_enstrophy(Ops3 ops, int64_t n, const double* __restrict__ U,
+                                                            const int32_t* __restrict__ level, double two_over_len,
+                                                            double* __restrict__ eta) {
+  constexpr int FN = G<NN>::FN, NODES = G<NN>::NODES, ELEM = G<NN>::ELEM;
+  constexpr int VE = VolCfg<NN>::VE;
+  __shared__ double s_v[VE][3][NODES];
+  __shared__ unsigned long long s_max[VE];
+  const int t = threadIdx.x;
+  const int le = t / NODES, node = t - le * NODES;
+  const int64_t e = (int64_t)blockIdx.x * VE + le;
+  const bool valid = le < VE && e < n;
+  const int i = node % NN, j = (node / NN) % NN, k = node / FN;
+  double rho = 1.0;
+  if (valid) {
+    const double* u = U + e * ELEM + node;
+    rho = u[0];
+    const double ir = 1.0 / rho;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s_v[le][d][node] = u[(1 + d) * NODES] * ir;
+  }
+  if (t < VE) s_max[t] = 0ull;
+  __syncthreads();
+  if (valid) {
+    // g[d][a] = d v_d / d x_a in reference units
+    double g[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+      for (int m = 0; m < NN; ++m) {
+        gx = fma(ops.dmat[i][m], s_v[le][d][(k * NN + j) * NN + m], gx);
+        gy = fma(ops.dmat[j][m], s_v[le][d][(k * NN + m) * NN + i], gy);
+        gz = fma(ops.dmat[k][m], s_v[le][d][(m * NN + j) * NN + i], gz);
+      }
+      g[d][0] = gx;
+      g[d][1] = gy;
+      g[d][2] = gz;
+    }
+    const double s = ldexp(two_over_len, level[e]);   // 2 / h
+    const double wx = s * (g[2][1] - g[1][2]);
+    const double wy = s * (g[0][2] - g[2][0]);
+    const double wz = s * (g[1][0] - g[0][1]);
+    const double ens = 0.5 * rho * (wx * wx + wy * wy + wz * wz);
+    // non-negative doubles order like their bit patterns (a NaN sorts above every number)
+    atomicMax(&s_max[le], (unsigned long long)__double_as_longlong(ens));
+  }
+  __syncthreads();
+  if (valid && node == 0) eta[e] = __longlong_as_double((long long)s_max[le]);
+}
+
+// One thread per node of a new element: copy, interpolation of the parent polynomial to a child
+// (the 1D half-interval interpolation matrices along each axis), or the L2 projection of the eight
+// children onto the parent (the 1D half-interval projections along each axis, summed).
+template <int NN>
+__global__ void __launch_bounds__(V3_THREADS) k3_transfer(Ops3 ops, int64_t n, const int32_t* __restrict__ map,
+                                                           const double* __restrict__ Uold, double* __restrict__ Unew) {
+  constexpr int FN = G<NN>::FN, NODES = G<NN>::NODES, ELEM = G<NN>::ELEM;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * NODES) return;
+  const int64_t e = q / NODES;
+  const int node = (int)(q - e * NODES);
+  const int i = node % NN, j = (node / NN) % NN, k = node / FN;
+  const int32_t* r = map + 9 * e;
+  const int kind = r[0] & 3;
+  double* out = Unew + e * ELEM + node;
+  if (kind == 0) {
+    const double* src = Uold + (int64_t)r[1] * ELEM + node;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * NODES] = src[v * NODES];
+    return;
+  }
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int nsrc = kind == 1 ? 1 : 8;
+  for (int c = 0; c < nsrc; ++c) {
+    // kind 1: the child position (cx, cy, cz) of this cell in its parent; kind 2: child c
+    const int cx = kind == 1 ? (r[0] >> 2) & 1 : c & 1;
+    const int cy = kind == 1 ? (r[0] >> 3) & 1 : (c >> 1) & 1;
+    const int cz = kind == 1 ? (r[0] >> 4) & 1 : (c >> 2) & 1;
+    const double* src = Uold + (int64_t)r[1 + c] * ELEM;
+    double wx[NN], wy[NN], wz[NN];
+#pragma unroll
+    for (int m = 0; m < NN; ++m) {
+      if (kind == 1) {
+        wx[m] = cx ? ops.p_hi[i][m] : ops.p_lo[i][m];
+        wy[m] = cy ? ops.p_hi[j][m] : ops.p_lo[j][m];
+        wz[m] = cz ? ops.p_hi[k][m] : ops.p_lo[k][m];
+      } else {
+        wx[m] = cx ? ops.r_hi[i][m] : ops.r_lo[i][m];
+        wy[m] = cy ? ops.r_hi[j][m] : ops.r_lo[j][m];
+        wz[m] = cz ? ops.r_hi[k][m] : ops.r_lo[k][m];
+      }
+    }
+#pragma unroll
+    for (int c3 = 0; c3 < NN; ++c3)
+#pragma unroll
+      for (int b = 0; b < NN; ++b) {
+        const double wzy = wz[c3] * wy[b];
+#pragma unroll
+        for (int a = 0; a < NN; ++a) {
+          const double w = wzy * wx[a];
+          const int m = (c3 * NN + b) * NN + a;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) acc[v] = fma(w, __ldg(src + v * NODES + m), acc[v]);
+        }
+      }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v * NODES] = acc[v];
+}
+
+// ---------------------------------------------------------------------------
 template <int NN>
 static cudaError_t faces3(cudaStream_t st, YSource ys, const Ops3& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                           const int4* morts, const int4* msmall, const int32_t* method, const StageArgs& sa,
@@ -687,6 +803,34 @@ cudaError_t launch_commit3(cudaStream_t st, int64_t n_doubles, const UpdateArgs&
   if (n_doubles <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((n_doubles + 255) / 256, 152 * 16);
   k3_commit<<<(unsigned)blocks, 256, 0, st>>>(n_doubles, ua, Ks, dt, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_enstrophy3(cudaStream_t st, const Ops3& ops, int64_t n_elem, const double* U,
+                              const int32_t* level, double two_over_len, double* eta) {
+  if (n_elem <= 0) return cudaSuccess;
+  if (ops.nn == 3)
+    k3_enstrophy<3><<<(unsigned)((n_elem + VolCfg<3>::VE - 1) / VolCfg<3>::VE), V3_THREADS, 0, st>>>(
+        ops, n_elem, U, level, two_over_len, eta);
+  else if (ops.nn == 4)
+    k3_enstrophy<4><<<(unsigned)((n_elem + VolCfg<4>::VE - 1) / VolCfg<4>::VE), V3_THREADS, 0, st>>>(
+        ops, n_elem, U, level, two_over_len, eta);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer3(cudaStream_t st, const Ops3& ops, int64_t n_new, const int32_t* map, const double* Uold,
+                             double* Unew) {
+  if (n_new <= 0) return cudaSuccess;
+  const int64_t threads = n_new * nodes3(ops.nn);
+  const unsigned blocks = (unsigned)((threads + V3_THREADS - 1) / V3_THREADS);
+  if (ops.nn == 3)
+    k3_transfer<3><<<blocks, V3_THREADS, 0, st>>>(ops, n_new, map, Uold, Unew);
+  else if (ops.nn == 4)
+    k3_transfer<4><<<blocks, V3_THREADS, 0, st>>>(ops, n_new, map, Uold, Unew);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

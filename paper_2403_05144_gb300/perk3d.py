@@ -166,3 +166,38 @@ class Perk3DSolver:
         out = C.c_double()
         self._call(self.lib.perk3d_compute_dt, C.c_void_p(U.data_ptr()), C.c_double(cfl), C.byref(out))
         return out.value
+
+    # ------------------------------------------------------------------- AMR
+    def amr_indicator(self, U):
+        """Per-element enstrophy indicator (max over nodes of rho |curl v|^2 / 2), on the device."""
+        U = self._state(U)
+        eta = self.torch.empty(self.n_elem, dtype=self.torch.float64, device="cuda")
+        self._call(self.lib.perk3d_amr_indicator, C.c_void_p(U.data_ptr()), C.c_void_p(eta.data_ptr()))
+        return eta
+
+    def get_cells(self):
+        out = np.zeros((self.n_elem, 4), dtype=np.int32)
+        self._call(self.lib.perk3d_get_cells, out.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(self.n_elem))
+        return out
+
+    def adapt(self, U, level_min: int = 0, level_max: int = 19, refine_above: float = float("inf"),
+              coarsen_below: float = 0.0, desired=None):
+        """One AMR cycle: returns the transferred state on the new mesh (a new tensor; U is left
+        as it was).  ``desired`` (levels per cell) replaces the indicator's decisions."""
+        U = self._state(U)
+        n_new = C.c_int64()
+        if desired is not None:
+            d = np.ascontiguousarray(desired, dtype=np.int32)
+            if d.shape != (self.n_elem,):
+                raise ValueError("desired needs one level per cell")
+            self._call(self.lib.perk3d_adapt_plan, None, d.ctypes.data_as(C.POINTER(C.c_int32)), None,
+                       C.byref(n_new))
+        else:
+            prm = _lib.Perk3DAmrParams(int(level_min), int(level_max), float(refine_above), float(coarsen_below))
+            self._call(self.lib.perk3d_adapt_plan, C.byref(prm), None, C.c_void_p(U.data_ptr()), C.byref(n_new))
+        Unew = self.torch.empty((n_new.value, 5, self.n, self.n, self.n), dtype=self.torch.float64, device="cuda")
+        self._call(self.lib.perk3d_adapt_commit, C.c_void_p(U.data_ptr()), C.c_void_p(Unew.data_ptr()))
+        self.n_elem = n_new.value
+        self.cells = self.get_cells()
+        return Unew
+

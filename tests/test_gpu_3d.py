@@ -15,7 +15,7 @@ from oracle.dgsem3d import DGSEM3D, max_wave_speed_dt3
 from oracle.lgl import lgl_nodes_weights
 from oracle.octree import OctreeMesh
 from oracle.perk import element_methods, perk2_family, perk3_family, prkm_step
-from perk_inputs.octree import (block_refined_cells3, nodal_state3, prim_to_cons3, refine_cells3, slab_cells3,
+from perk_inputs.octree import (block_refined_cells3, nodal_state3, prim_to_cons3, refine_cells3,
                                 smooth_random_state3, taylor_green, uniform_cells3)
 
 pytestmark = pytest.mark.gpu
@@ -196,32 +196,46 @@ def test_rejected_step_leaves_state_unchanged():
     assert np.array_equal(U.cpu().numpy(), U0)
 
 
-def test_taylor_green_slab_mesh_full_size():
-    """The benchmark's mesh and launch configuration (25,600 cells, levels 4-6, N = 2, HLLE,
-    P-ERK3 {3,4,6}, graph replay): the RHS of the Taylor-Green state and one partially active
-    stage of a seeded state against the oracle on the full mesh, and the conservation of the
-    discrete integral after two steps."""
-    cells = slab_cells3(4, 6, 1.0 / 32.0)
-    mesh = OctreeMesh(np.asarray(cells), X0, L)
+def test_taylor_green_adapted_mesh_full_size():
+    """The benchmark's configuration: 16^3 cells adapted twice by the enstrophy indicator (levels
+    4-6, refine above 1.2, coarsen below 0.3: 30,080 cells), N = 2, HLLE, P-ERK3 {3,4,6}, graph
+    replay.  The library's own AMR decisions give the oracle's mesh; the RHS of the adapted
+    Taylor-Green state and one partially active stage of a seeded state match the oracle on the
+    full mesh; the discrete integral is conserved over two steps."""
+    from oracle.amr3d import adapt3
+    amr = dict(level_min=4, level_max=6, refine_above=1.2, coarsen_below=0.3)
+    cells0 = uniform_cells3(4)
     x, w = lgl_nodes_weights(2)
-    U0 = nodal_state3(taylor_green, cells, X0, L, x)
-    s = solver(cells, 2, "hlle")
+    U0 = nodal_state3(taylor_green, cells0, X0, L, x)
+    mesh = OctreeMesh(np.asarray(cells0), X0, L)
+    Uo = U0
+    for _ in range(2):
+        mesh, Uo, _ = adapt3(mesh, Uo, **amr, N=2)
+    s = solver(cells0, 2, "hlle")
     s.set_perk3_disk([3, 4, 6])
+    U = cuda(U0)
+    for _ in range(2):
+        U = s.adapt(U, **amr)
+    assert [tuple(c) for c in s.cells.tolist()] == [tuple(c) for c in mesh.cells.tolist()]
+    assert len(mesh.cells) == 30080
+    U = U.cpu().numpy()
+    assert np.max(np.abs(U - Uo)) <= 1e-13 * np.max(np.abs(Uo))
     op = DGSEM3D(mesh, 2, "hlle")
-    got = s.rhs_full(cuda(U0)).cpu().numpy()
-    want = op.rhs(U0)
+    got = s.rhs_full(cuda(U)).cpu().numpy()
+    want = op.rhs(U)
     # At Mach 0.1 the right-hand side is the small remainder of derivative terms of size up to
     # (2/h) |f(u)| (p0 = 71 against pressure variations of 0.25; the density RHS vanishes
     # analytically, the velocity being divergence-free at unit density), so its rounding is set by
     # those terms: each variable's error is measured against (2/h_min) max |f_v(u)| over the three
     # axes, of which a wrong or dropped term would be a visible fraction, not 1e-12.
     from oracle.euler3d import physical_flux
-    V = np.moveaxis(U0, 1, 0)
+    V = np.moveaxis(U, 1, 0)
     fmax = np.max([np.abs(physical_flux(V, d)).reshape(5, -1).max(axis=1) for d in range(3)], axis=0)
     scale = (2.0 / mesh.h.min()) * fmax
     for v in range(5):
         assert np.max(np.abs(got[:, v] - want[:, v])) / scale[v] < 1e-12, v
     # a seeded state without that cancellation, one partially active stage: relative per variable
+    cells = [tuple(c) for c in mesh.cells.tolist()]
     Ur = state(cells, 2, seed=33)
     fam = perk3_family([3, 4, 6])
     meth = element_methods(mesh.cells[:, 0], fam.R)
@@ -229,12 +243,11 @@ def test_taylor_green_slab_mesh_full_size():
     assert 0 < active.sum() < len(cells)
     got = s.rhs_active(3, cuda(Ur)).cpu().numpy()
     assert rel_err(got[active], op.rhs(Ur)[active]) < 1e-12
-    U = cuda(U0.copy())
-    dt = s.compute_dt(U, 0.5)
+    Ud = cuda(U.copy())
+    dt = s.compute_dt(Ud, 0.5)
     for _ in range(2):
-        s.step(U, dt)
+        s.step(Ud, dt)
     s.check()
-    Un = U.cpu().numpy()
-    before, after = op.integrate(U0), op.integrate(Un)
-    scale = np.max(np.abs(op.integrate(np.abs(U0))))
+    before, after = op.integrate(U), op.integrate(Ud.cpu().numpy())
+    scale = np.max(np.abs(op.integrate(np.abs(U))))
     assert np.max(np.abs(after - before)) < 1e-12 * scale
