@@ -17,8 +17,9 @@ two-level isentropic vortex, 448 cells), vortex_large (the same
 pattern at 114,688 cells, the roofline case), shear (Navier-Stokes shear
 layer, third order, dynamic AMR), ensemble (64 KH members in one context),
 adjoint (discrete-adjoint gradient over 200 steps), spectrum (spectrum-optimised
-stability polynomials against the disk polynomials), tgv (3D Taylor-Green vortex on
-an octree adapted by the enstrophy indicator, levels 4-6, P-ERK3 {3,4,6}, N = 2).
+stability polynomials against the disk polynomials), tgv (3D Taylor-Green vortex,
+Navier-Stokes at Re 1600, on an octree adapted by the enstrophy indicator, levels 4-6,
+P-ERK3 {3,4,6}, N = 2).
 
 Multi-GPU: the step does not shard across GPUs here; N ranks run N
 independent replicas of the workload (weak scaling, no collective on the
@@ -885,7 +886,8 @@ def run_spectrum(args) -> None:
 # + 81 pairs x 50   (the 2D pair's 44 plus the third velocity's mean, product and flux component)
 # + 27 nodes x 6 partners x 5 variables (accumulation) + 270 (lifting on up to three faces, Jacobian)
 VOL3_SLOTS_PER_ELEM = 27 * 64 + 81 * 50 + 27 * 6 * 5 + 270
-TGV = dict(name="taylor_green_3d_octree_enstrophy_amr_levels4-6_n2_hlle", N=2, flux="hlle", E=[3, 4, 6], cfl=0.5,
+TGV = dict(name="taylor_green_3d_navier_stokes_re1600_octree_enstrophy_amr_levels4-6_n2_hlle", N=2, flux="hlle",
+           E=[3, 4, 6], cfl=0.5, equations="navier_stokes", mu=1.0 / 1600.0, prandtl=0.72,
            base_level=4, amr=dict(level_min=4, level_max=6, refine_above=1.2, coarsen_below=0.3), n_amr=5,
            init_cycles=2, x0=0.0, L=2.0 * math.pi, mach=0.1, t_end=20.0)
 
@@ -908,7 +910,8 @@ class Run3:
         from paper_2403_05144_gb300.perk3d import Perk3DSolver
 
         cells, U0 = tgv_initial()
-        self.s = Perk3DSolver(N=TGV["N"], surface_flux=TGV["flux"], use_graph=True)
+        self.s = Perk3DSolver(N=TGV["N"], surface_flux=TGV["flux"], use_graph=True, equations=TGV["equations"],
+                              mu=TGV["mu"], prandtl=TGV["prandtl"])
         self.s.upload_mesh(cells, TGV["x0"], TGV["L"])
         self.s.set_perk3_disk(E)
         self.U = torch.from_numpy(U0).cuda()
@@ -937,14 +940,14 @@ class Run3:
 def tgv_oracle_sample(cells, U, n_stages: int = 0, budget_s: float = 10.0):
     """The 3D oracle's partitioned RHS I^(act(i)) F(U) for stages i = 0, 1, ... (cycling): n_stages
     evaluations or as many as fit in budget_s.  Returns (DoF-stage updates, seconds, evaluations, S)."""
-    from oracle.dgsem3d import DGSEM3D
+    from oracle.br1_3d import NavierStokesDGSEM3D
     from oracle.octree import OctreeMesh
     from oracle.perk import element_methods, perk3_family
 
     mesh = OctreeMesh(np.asarray(cells), TGV["x0"], TGV["L"])
     fam = perk3_family(TGV["E"])
     meth = element_methods(mesh.cells[:, 0], fam.R)
-    dg = DGSEM3D(mesh, TGV["N"], TGV["flux"])
+    dg = NavierStokesDGSEM3D(mesh, TGV["N"], TGV["flux"], mu=TGV["mu"], prandtl=TGV["prandtl"])
     nodes = (TGV["N"] + 1) ** 3
     act = [np.array([fam.active(int(r), i) for r in meth]) for i in range(fam.S)]
     units, k = 0, 0
@@ -960,7 +963,8 @@ def tgv_oracle_sample(cells, U, n_stages: int = 0, budget_s: float = 10.0):
 
 
 def run_tgv(args) -> None:
-    """3D Taylor-Green vortex (the paper's Sec. 7.1.3 initial state, Mach 0.1): 16^3 cells adapted
+    """3D Taylor-Green vortex (the paper's Sec. 7.1.3: Navier-Stokes at Re 1600, Pr 0.72, Mach 0.1
+    initial state of Eq. IC_TaylorGreen): 16^3 cells adapted
     twice by the enstrophy indicator (levels 4-6), N = 2, HLLE, an AMR cycle every five steps
     inside the timed region; P-ERK3 {3, 4, 6} against the standalone six-stage member (full RHS
     every stage, same AMR)."""
@@ -1024,7 +1028,7 @@ def run_tgv(args) -> None:
         acc = perk.s.step_profiled(Upr, perk.dt, acc)
     vol_ms, vol_launches = acc.ms[1], acc.launches[1]
     achieved = 2.0 * VOL3_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
-    kernel_ms_total = sum(acc.ms[k] for k in range(3))
+    kernel_ms_total = sum(acc.ms[k] for k in range(4))
 
     # end to end through the public API with the state in pinned host memory (AMR included)
     st = torch.cuda.current_stream()
@@ -1075,7 +1079,7 @@ def run_tgv(args) -> None:
         "config": {"workload": TGV["name"], "n_elem": info["n_elem"], "n_elem_initial": info0["n_elem"],
                    "levels": [info["level_min"], info["level_max"]], "N": TGV["N"], "family": TGV["E"],
                    "stages": S, "surface_flux": TGV["flux"], "cfl": TGV["cfl"], "dt": perk.dt, "mach": TGV["mach"],
-                   "equations": "euler",
+                   "equations": TGV["equations"], "reynolds": 1.0 / TGV["mu"], "prandtl": TGV["prandtl"],
                    "amr": {**TGV["amr"], "indicator": "enstrophy", "every_steps": TGV["n_amr"],
                            "in_timed_region": True, "cycles_timed": cycles},
                    "dof_stage_updates_per_step": units / args.steps,
@@ -1089,13 +1093,15 @@ def run_tgv(args) -> None:
                      "frac": achieved / fma_flops, "traffic": None, "kernel": "k3_volume",
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
+                     "kernel_ms_by_kind": {"faces": acc.ms[0], "volume": acc.ms[1], "commit": acc.ms[2],
+                                           "viscous_br1": acc.ms[3]},
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
                      "work_per_element_stage": {"fp64_slots": VOL3_SLOTS_PER_ELEM, "flops": 2 * VOL3_SLOTS_PER_ELEM}},
         "e2e": {"value": replica_rate(units_e2e, ms_e2e, world), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
-        # per step 2 launches per stage + the commit; per AMR cycle: indicator, transfer, partition,
-        # the step-size reset and reduction
-        "gpu_launches": args.steps * (2 * S + 1) + 5 * cycles,
+        # per step 6 launches per stage (faces, volume, the four BR1 kernels) + the commit; per AMR
+        # cycle: indicator, transfer, partition, the step-size reset and reduction
+        "gpu_launches": args.steps * (6 * S + 1) + 5 * cycles,
         "clocks": clk.summary(),
     }
     if rank == 0:

@@ -9,7 +9,7 @@
  * Sec. 6.1 on hexahedra: flux-differencing volume integral with Ranocha's
  * entropy-conservative two-point flux, HLL / HLLC / HLLE / EC surface fluxes,
  * and L2 mortars at hanging faces (one large face against four small ones).
- * Compressible Euler equations.
+ * Compressible Euler or Navier-Stokes (BR1) equations.
  *
  * Conventions (in addition to those of perk.h, whose status codes and surface
  * flux identifiers are shared)
@@ -41,10 +41,17 @@ typedef struct {
   double gamma;      /* ratio of specific heats, > 1 */
   int surface_flux;  /* perk_surface_flux: HLL, HLLC, EC or HLLE (the paper's choice in Sec. 7.1.3) */
   int use_graph;     /* nonzero: perk3d_step replays a captured CUDA graph of the whole step */
+  int equations;     /* perk_equations: Euler, or Navier-Stokes with BR1 viscous terms (gradients of
+                        (v1, v2, v3, T = p/rho) by central lifting, stress mu (grad v + grad v^T -
+                        (2/3) div v I), heat flux kappa grad T with kappa = mu gamma / ((gamma-1) Pr),
+                        central viscous face flux; mortar averages as for the inviscid traces) */
+  double mu;         /* dynamic viscosity (Navier-Stokes), > 0 */
+  double prandtl;    /* Prandtl number (Navier-Stokes), > 0 */
 } perk3d_problem;
 
-/* Creates a context on the current CUDA device (INVALID_ARG for N outside {2, 3}, gamma <= 1
- * or an unknown flux; CUDA when no device is usable). */
+/* Creates a context on the current CUDA device (INVALID_ARG for N outside {2, 3}, gamma <= 1,
+ * an unknown flux or equation set, or a non-positive mu or Pr for Navier-Stokes; CUDA when no
+ * device is usable). */
 perk_status perk3d_create(const perk3d_problem* prob, perk3d_ctx** out);
 /* Frees the context and every device buffer it owns.  NULL is ignored. */
 void perk3d_destroy(perk3d_ctx* ctx);
@@ -102,7 +109,8 @@ perk_status perk3d_check(perk3d_ctx* ctx);
 perk_status perk3d_compute_dt(perk3d_ctx* ctx, const double* d_U, double cfl, double* dt);
 
 /* perk3d_step without a graph, with CUDA events around every launch; blocks.  Kinds:
- * 0 = faces (interfaces and mortars, one launch per stage), 1 = volume, 2 = final update.
+ * 0 = faces (interfaces and mortars, one launch per stage), 1 = volume, 2 = final update,
+ * 3 = viscous terms (Navier-Stokes: the four BR1 launches of a stage, timed as one group).
  * Accumulates into acc (the struct of perk.h). */
 perk_status perk3d_step_profiled(perk3d_ctx* ctx, double* d_U, double dt, perk_kernel_times* acc);
 /* Steps, element-stage evaluations and node-stage (DoF-stage) updates since creation. */

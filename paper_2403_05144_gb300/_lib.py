@@ -106,7 +106,8 @@ SIGNATURES = [
 
 
 class Perk3DProblem(C.Structure):
-    _fields_ = [("N", C.c_int), ("gamma", C.c_double), ("surface_flux", C.c_int), ("use_graph", C.c_int)]
+    _fields_ = [("N", C.c_int), ("gamma", C.c_double), ("surface_flux", C.c_int), ("use_graph", C.c_int),
+                ("equations", C.c_int), ("mu", C.c_double), ("prandtl", C.c_double)]
 
 
 class Perk3DAmrParams(C.Structure):

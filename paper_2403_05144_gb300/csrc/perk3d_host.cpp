@@ -275,6 +275,11 @@ struct perk3d_ctx {
   int part_S = 0;
   int32_t lmin = 0, lmax = 0;
   int64_t act_el[MAX_S] = {}, act_if[MAX_S] = {}, act_mort[MAX_S] = {};
+  // per stage, the prefixes of the one-level halo of the active members (BR1 gradients)
+  int64_t halo_el[MAX_S] = {}, halo_if[MAX_S] = {}, halo_mort[MAX_S] = {};
+  bool viscous() const { return prob.equations == PERK_NAVIER_STOKES; }
+  double kappa() const { return prob.mu * prob.gamma / ((prob.gamma - 1.0) * prob.prandtl); }
+  Buf<double> d_q;   // BR1 gradients [n_elem][3][4][n^3]
 
   Buf<int32_t> d_level, d_method, d_elem_sorted, d_minmem, d_minmax, d_member_lmax;
   Buf<int4> d_if_raw, d_mort_raw, d_if_sorted, d_mort_sorted, d_msmall;
@@ -340,6 +345,9 @@ perk_status run_partition3(perk3d_ctx* ctx) {
     ctx->act_el[i] = i < S ? counts[i] : 0;
     ctx->act_if[i] = i < S ? counts[MAX_S + i] : 0;
     ctx->act_mort[i] = i < S ? counts[2 * MAX_S + i] : 0;
+    ctx->halo_el[i] = i < S ? counts[3 * MAX_S + i] : 0;
+    ctx->halo_if[i] = i < S ? counts[4 * MAX_S + i] : 0;
+    ctx->halo_mort[i] = i < S ? counts[5 * MAX_S + i] : 0;
   }
   ctx->lmin = mm[0];
   ctx->lmax = mm[1];
@@ -409,10 +417,18 @@ perk_status enqueue_step3(perk3d_ctx* ctx, cudaStream_t st, double* d_U, Timer3*
     if (last) K_before_last = Kbuf[prev];
     UpdateArgs chk = ua;
     chk.Kp = K_before_last;
+    const bool visc = ctx->viscous();
     P3_TIMED(ctx, timer, st, 1,
              launch_volume3(st, perk::Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                            ctx->d_method.p, two_over_len, sa, ctx->d_surf.p, Kbuf[cur], last ? &chk : nullptr,
-                            ctx->d_logtab.p));
+                            ctx->d_method.p, two_over_len, sa, ctx->d_surf.p, Kbuf[cur],
+                            (last && !visc) ? &chk : nullptr, ctx->d_logtab.p));
+    if (visc)
+      P3_TIMED(ctx, timer, st, 3,
+               launch_br1_3d(st, perk::Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->halo_if[i],
+                             ctx->halo_mort[i], ctx->act_if[i], ctx->act_mort[i], ctx->d_if_sorted.p,
+                             ctx->d_mort_sorted.p, ctx->d_msmall.p, ctx->halo_el[i], ctx->act_el[i],
+                             ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, two_over_len, sa, ctx->d_surf.p,
+                             ctx->d_q.p, Kbuf[cur], last ? &chk : nullptr));
     prev = cur;
   }
   ua.Kp = K_before_last;
@@ -468,6 +484,10 @@ perk_status perk3d_create(const perk3d_problem* prob, perk3d_ctx** out) {
   *out = nullptr;
   if ((prob->N != 2 && prob->N != 3) || !(prob->gamma > 1.0) || prob->surface_flux < 0 || prob->surface_flux > 3)
     return fail(nullptr, PERK_E_INVALID_ARG, "N must be 2 or 3, gamma > 1, and the surface flux known");
+  if (prob->equations != PERK_EULER && prob->equations != PERK_NAVIER_STOKES)
+    return fail(nullptr, PERK_E_INVALID_ARG, "unknown equations %d", prob->equations);
+  if (prob->equations == PERK_NAVIER_STOKES && (!(prob->mu > 0.0) || !(prob->prandtl > 0.0)))
+    return fail(nullptr, PERK_E_INVALID_ARG, "Navier-Stokes needs mu > 0 and Pr > 0");
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
     cudaGetLastError();
@@ -508,6 +528,7 @@ void perk3d_destroy(perk3d_ctx* ctx) {
                   &ctx->d_member_lmax, &ctx->d_map})
     b->release();
   ctx->d_eta.release();
+  ctx->d_q.release();
   for (auto* b : {&ctx->d_if_raw, &ctx->d_mort_raw, &ctx->d_if_sorted, &ctx->d_mort_sorted, &ctx->d_msmall})
     b->release();
   for (auto* b : {&ctx->d_surf, &ctx->d_K1, &ctx->d_Ka, &ctx->d_Kb, &ctx->d_dt, &ctx->d_dt_out, &ctx->d_logtab})
@@ -591,6 +612,7 @@ perk_status perk3d_mesh_upload(perk3d_ctx* ctx, int64_t n_cells, const int32_t* 
   P3_CUDA(ctx, ctx->d_Ka.ensure(ne * elem3(ctx->nn)));
   P3_CUDA(ctx, ctx->d_Kb.ensure(ne * elem3(ctx->nn)));
   P3_CUDA(ctx, ctx->d_eta.ensure(ne));
+  if (ctx->viscous()) P3_CUDA(ctx, ctx->d_q.ensure(ne * 12 * nodes3(ctx->nn)));
   P3_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
                                ctx->stream));
   if (!c.ifs.empty())
@@ -681,6 +703,13 @@ static perk_status rhs_given3(perk3d_ctx* ctx, int stage, const double* d_Y, dou
                              ctx->d_msmall.p, ctx->d_method.p, sa, ctx->d_logtab.p, ctx->d_surf.p));
   P3_CUDA(ctx, launch_volume3(ctx->stream, perk::Y_GIVEN, ctx->ops, ne, ctx->d_elem_sorted.p, ctx->d_level.p,
                               ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, d_K, nullptr, ctx->d_logtab.p));
+  if (ctx->viscous())
+    P3_CUDA(ctx, launch_br1_3d(ctx->stream, perk::Y_GIVEN, ctx->ops, ctx->prob.mu, ctx->kappa(),
+                               stage < 0 ? ctx->n_if : ctx->halo_if[stage],
+                               stage < 0 ? ctx->n_mort : ctx->halo_mort[stage], ni, nm, ctx->d_if_sorted.p,
+                               ctx->d_mort_sorted.p, ctx->d_msmall.p, stage < 0 ? ctx->n_elem : ctx->halo_el[stage],
+                               ne, ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa,
+                               ctx->d_surf.p, ctx->d_q.p, d_K, nullptr));
   return PERK_OK;
 }
 

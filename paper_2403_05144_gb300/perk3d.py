@@ -43,14 +43,17 @@ def mesh_faces3(cells):
 class Perk3DSolver:
     """One 3D libperk context: octree mesh, level partition, coefficient table, stage buffers."""
 
-    def __init__(self, N: int = 2, gamma: float = 1.4, surface_flux: str = "hlle", use_graph: bool = True):
+    def __init__(self, N: int = 2, gamma: float = 1.4, surface_flux: str = "hlle", use_graph: bool = True,
+                 equations: str = "euler", mu: float = 0.0, prandtl: float = 0.72):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("Perk3DSolver needs a CUDA device")
         self.torch = torch
         self.lib = _lib.load()
-        prob = _lib.Perk3DProblem(int(N), float(gamma), _lib.SURFACE[surface_flux], 1 if use_graph else 0)
+        eq = {"euler": 0, "navier_stokes": 1}[equations]
+        prob = _lib.Perk3DProblem(int(N), float(gamma), _lib.SURFACE[surface_flux], 1 if use_graph else 0, eq,
+                                  float(mu), float(prandtl))
         h = C.c_void_p()
         torch.cuda.init()
         _check(self.lib, None, self.lib.perk3d_create(C.byref(prob), C.byref(h)))

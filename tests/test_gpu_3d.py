@@ -198,8 +198,8 @@ def test_rejected_step_leaves_state_unchanged():
 
 def test_taylor_green_adapted_mesh_full_size():
     """The benchmark's configuration: 16^3 cells adapted twice by the enstrophy indicator (levels
-    4-6, refine above 1.2, coarsen below 0.3: 30,080 cells), N = 2, HLLE, P-ERK3 {3,4,6}, graph
-    replay.  The library's own AMR decisions give the oracle's mesh; the RHS of the adapted
+    4-6, refine above 1.2, coarsen below 0.3: 30,080 cells), Navier-Stokes at Re 1600 (BR1),
+    N = 2, HLLE, P-ERK3 {3,4,6}, graph replay.  The library's own AMR decisions give the oracle's mesh; the RHS of the adapted
     Taylor-Green state and one partially active stage of a seeded state match the oracle on the
     full mesh; the discrete integral is conserved over two steps."""
     from oracle.amr3d import adapt3
@@ -211,7 +211,10 @@ def test_taylor_green_adapted_mesh_full_size():
     Uo = U0
     for _ in range(2):
         mesh, Uo, _ = adapt3(mesh, Uo, **amr, N=2)
-    s = solver(cells0, 2, "hlle")
+    from paper_2403_05144_gb300.perk3d import Perk3DSolver
+    from oracle.br1_3d import NavierStokesDGSEM3D
+    s = Perk3DSolver(N=2, surface_flux="hlle", equations="navier_stokes", mu=1.0 / 1600.0, prandtl=0.72)
+    s.upload_mesh(cells0, X0, L)
     s.set_perk3_disk([3, 4, 6])
     U = cuda(U0)
     for _ in range(2):
@@ -220,7 +223,7 @@ def test_taylor_green_adapted_mesh_full_size():
     assert len(mesh.cells) == 30080
     U = U.cpu().numpy()
     assert np.max(np.abs(U - Uo)) <= 1e-13 * np.max(np.abs(Uo))
-    op = DGSEM3D(mesh, 2, "hlle")
+    op = NavierStokesDGSEM3D(mesh, 2, "hlle", mu=1.0 / 1600.0, prandtl=0.72)
     got = s.rhs_full(cuda(U)).cpu().numpy()
     want = op.rhs(U)
     # At Mach 0.1 the right-hand side is the small remainder of derivative terms of size up to
