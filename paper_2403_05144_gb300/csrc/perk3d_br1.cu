@@ -7,11 +7,14 @@
 //                   one-level halo of the active members (mortars: the small side averages with
 //                   the interpolated large trace, the large side takes the four-quadrant L2
 //                   projection)
-//   k3b_grad        q_d = (2/h) [D_d w + lifting of (w* - w)] at every node of the halo elements
+//   k3b_grad        q_d = (2/h) [D_d w + lifting of (w* - w)] at every node of the halo elements,
+//                   and from it and the stage state the viscous fluxes f_v,d along the three axes,
+//                   stored per node (the state and the gradients are not needed again)
 //   k3b_faces<1>    central viscous face flux f* = (f_v,L + f_v,R)/2 (normal component) on the
-//                   active faces
+//                   active faces, from the stored fluxes
 //   k3b_visc_volume K += (2/h) sum_d [D_d f_v,d + lifting of (f* - f_v,d)] on the active
-//                   elements; on the last stage also the admissibility check of the step
+//                   elements, from the stored fluxes; on the last stage also the admissibility
+//                   check of the step
 //
 // Face neighbours differ by at most one level, hence by at most one member, so the halo of
 // the active members is a prefix of the level-sorted lists (the partition's halo counts).
@@ -21,6 +24,7 @@
 #include <stdint.h>
 
 #include "perk3d_internal.h"
+#include "perk_devmath.cuh"
 
 namespace perk3 {
 namespace br1 {
@@ -31,7 +35,7 @@ using perk::Y_GIVEN;
 template <int NN>
 struct G {
   static constexpr int FN = NN * NN, NODES = NN * NN * NN, ELEM = NV3 * NODES, SURF = 6 * NV3 * FN;
-  static constexpr int Q = 12 * NODES;   // doubles of q per element: [axis][variable][node]
+  static constexpr int F = 15 * NODES;   // doubles of viscous fluxes per element: [axis][variable][node]
 };
 
 template <int NN>
@@ -65,7 +69,7 @@ __device__ __forceinline__ void state3(const StageArgs& sa, int64_t e, int m, in
 }
 
 __device__ __forceinline__ void grad_vars3(const double u[5], double gm1, double w[5]) {
-  const double ir = 1.0 / u[0];
+  const double ir = perk::rcp_nr(u[0]);
   w[0] = u[1] * ir;
   w[1] = u[2] * ir;
   w[2] = u[3] * ir;
@@ -74,11 +78,9 @@ __device__ __forceinline__ void grad_vars3(const double u[5], double gm1, double
   w[4] = 0.0;
 }
 
-// viscous flux along axis d from the state and q[a][v] = d w_v / d x_a
-__device__ __forceinline__ void visc_flux3(const double u[5], const double q[3][4], int d, double mu, double kappa,
+// viscous flux along axis d from the velocity v and q[a][var] = d w_var / d x_a
+__device__ __forceinline__ void visc_flux3(const double v[3], const double q[3][4], int d, double mu, double kappa,
                                            double f[5]) {
-  const double ir = 1.0 / u[0];
-  const double v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
   const double div = q[0][0] + q[1][1] + q[2][2];
   double tau[3];   // tau_{a d} = mu (dv_a/dx_d + dv_d/dx_a) - (2/3) mu div delta_ad
 #pragma unroll
@@ -90,14 +92,6 @@ __device__ __forceinline__ void visc_flux3(const double u[5], const double q[3][
   f[4] = fma(v[0], tau[0], fma(v[1], tau[1], fma(v[2], tau[2], kappa * q[d][3])));
 }
 
-template <int NN>
-__device__ __forceinline__ void load_q3(const double* q, int64_t e, int node, double out[3][4]) {
-  constexpr int ND = G<NN>::NODES;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) out[a][v] = __ldg(q + e * G<NN>::Q + (a * 4 + v) * ND + node);
-}
 
 constexpr int THREADS = 128;
 
@@ -116,14 +110,14 @@ __global__ void __launch_bounds__(THREADS) k3b_faces(Ops3 ops, int64_t n_if, con
   __shared__ double s_l[MB][5][FN];
   __shared__ double s_a[MB][4][5][FN];
   auto value = [&](int64_t e, int m, int node, int d, double r[5]) {
-    double u[5];
-    state3<NN, YS>(sa, e, m, node, u);
     if (PHASE == 0) {
+      double u[5];
+      state3<NN, YS>(sa, e, m, node, u);
       grad_vars3(u, ops.gm1, r);
     } else {
-      double qq[3][4];
-      load_q3<NN>(q, e, node, qq);
-      visc_flux3(u, qq, d, mu, kappa, r);
+      // the flux along the face's axis, stored by k3b_grad
+#pragma unroll
+      for (int v = 0; v < 5; ++v) r[v] = __ldg(q + e * G<NN>::F + (d * 5 + v) * G<NN>::NODES + node);
     }
   };
   if (blockIdx.x < if_blocks) {
@@ -214,13 +208,14 @@ struct Cfg {
   static constexpr int VE = THREADS / G<NN>::NODES;   // 4 (N = 2) or 2 (N = 3)
 };
 
-// q_d = (2/h) [D_d w + (1/w_N)(w* - w)|_N - (1/w_0)(w* - w)|_0] along the three axes
+// q_d = (2/h) [D_d w + (1/w_N)(w* - w)|_N - (1/w_0)(w* - w)|_0] along the three axes, then the
+// viscous fluxes f_v,d(u, q) at the node, stored in fv[e][d][variable][node]
 template <int NN, int YS>
 __global__ void __launch_bounds__(THREADS) k3b_grad(Ops3 ops, int64_t n, const int32_t* __restrict__ elems,
                                                      const int32_t* __restrict__ level,
                                                      const int32_t* __restrict__ method, double two_over_len,
-                                                     StageArgs sa, const double* __restrict__ surf,
-                                                     double* __restrict__ q) {
+                                                     StageArgs sa, const double* __restrict__ surf, double mu,
+                                                     double kappa, double* __restrict__ fv) {
   constexpr int FN = G<NN>::FN, NODES = G<NN>::NODES, SURF = G<NN>::SURF, VE = Cfg<NN>::VE;
   __shared__ double s_w[VE][4][NODES];
   const int t = threadIdx.x, le = t / NODES, node = t - le * NODES;
@@ -228,8 +223,9 @@ __global__ void __launch_bounds__(THREADS) k3b_grad(Ops3 ops, int64_t n, const i
   const bool valid = le < VE && slot < n;
   const int64_t e = valid ? elems[slot] : 0;
   const int i = node % NN, j = (node / NN) % NN, k = node / FN;
+  double w[5];
   if (valid) {
-    double u[5], w[5];
+    double u[5];
     state3<NN, YS>(sa, e, method[e], node, u);
     grad_vars3(u, ops.gm1, w);
 #pragma unroll
@@ -240,6 +236,7 @@ __global__ void __launch_bounds__(THREADS) k3b_grad(Ops3 ops, int64_t n, const i
   const double s = ldexp(two_over_len, level[e]);
   const double iw = ops.inv_w0;
   const double* ws = surf + e * SURF;
+  double qq[3][4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     double gx = 0.0, gy = 0.0, gz = 0.0;
@@ -256,9 +253,16 @@ __global__ void __launch_bounds__(THREADS) k3b_grad(Ops3 ops, int64_t n, const i
     if (j == NN - 1) gy = fma(iw, ws[3 * 5 * FN + v * FN + k * NN + i] - wv, gy);
     if (k == 0) gz = fma(-iw, ws[4 * 5 * FN + v * FN + j * NN + i] - wv, gz);
     if (k == NN - 1) gz = fma(iw, ws[5 * 5 * FN + v * FN + j * NN + i] - wv, gz);
-    q[e * G<NN>::Q + (0 * 4 + v) * NODES + node] = s * gx;
-    q[e * G<NN>::Q + (1 * 4 + v) * NODES + node] = s * gy;
-    q[e * G<NN>::Q + (2 * 4 + v) * NODES + node] = s * gz;
+    qq[0][v] = s * gx;
+    qq[1][v] = s * gy;
+    qq[2][v] = s * gz;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double f[5];
+    visc_flux3(w, qq, d, mu, kappa, f);   // w[0..2] is the velocity
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fv[e * G<NN>::F + (d * 5 + v) * NODES + node] = f[v];
   }
 }
 
@@ -268,9 +272,9 @@ __global__ void __launch_bounds__(THREADS) k3b_visc_volume(Ops3 ops, int64_t n, 
                                                             const int32_t* __restrict__ level,
                                                             const int32_t* __restrict__ method,
                                                             double two_over_len, StageArgs sa,
-                                                            const double* __restrict__ q,
-                                                            const double* __restrict__ surf, double mu,
-                                                            double kappa, double* __restrict__ K, UpdateArgs ua) {
+                                                            const double* __restrict__ fv,
+                                                            const double* __restrict__ surf,
+                                                            double* __restrict__ K, UpdateArgs ua) {
   constexpr int FN = G<NN>::FN, NODES = G<NN>::NODES, ELEM = G<NN>::ELEM, SURF = G<NN>::SURF;
   constexpr int VE = Cfg<NN>::VE;
   __shared__ double s_f[VE][3][5][NODES];
@@ -281,15 +285,13 @@ __global__ void __launch_bounds__(THREADS) k3b_visc_volume(Ops3 ops, int64_t n, 
   const int i = node % NN, j = (node / NN) % NN, k = node / FN;
   double f[3][5];
   if (valid) {
-    double u[5], qq[3][4];
-    state3<NN, YS>(sa, e, method[e], node, u);
-    load_q3<NN>(q, e, node, qq);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      visc_flux3(u, qq, d, mu, kappa, f[d]);
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s_f[le][d][v][node] = f[d][v];
-    }
+      for (int v = 0; v < 5; ++v) {
+        f[d][v] = __ldg(fv + e * G<NN>::F + (d * 5 + v) * NODES + node);
+        s_f[le][d][v][node] = f[d][v];
+      }
   }
   __syncthreads();
   if (!valid) return;
@@ -350,7 +352,7 @@ static void br1_launches(cudaStream_t st, const Ops3& ops, double mu, double kap
                                                                   method, sa, q, mu, kappa, surf);
   if (n_el_h)
     k3b_grad<NN, YS><<<(unsigned)((n_el_h + VE - 1) / VE), THREADS, 0, st>>>(ops, n_el_h, elems, level, method,
-                                                                             two_over_len, sa, surf, q);
+                                                                             two_over_len, sa, surf, mu, kappa, q);
   if (bia + bma)
     k3b_faces<NN, YS, 1><<<(unsigned)(bia + bma), THREADS, 0, st>>>(ops, n_if_a, ifs, n_mort_a, morts, msmall, bia,
                                                                     method, sa, q, mu, kappa, surf);
@@ -358,10 +360,10 @@ static void br1_launches(cudaStream_t st, const Ops3& ops, double mu, double kap
     const unsigned g = (unsigned)((n_el_a + VE - 1) / VE);
     if (check)
       k3b_visc_volume<NN, YS, true><<<g, THREADS, 0, st>>>(ops, n_el_a, elems, level, method, two_over_len, sa, q,
-                                                           surf, mu, kappa, K, ua);
+                                                           surf, K, ua);
     else
       k3b_visc_volume<NN, YS, false><<<g, THREADS, 0, st>>>(ops, n_el_a, elems, level, method, two_over_len, sa, q,
-                                                            surf, mu, kappa, K, ua);
+                                                            surf, K, ua);
   }
 }
 

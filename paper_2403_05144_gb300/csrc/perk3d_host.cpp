@@ -279,7 +279,7 @@ struct perk3d_ctx {
   int64_t halo_el[MAX_S] = {}, halo_if[MAX_S] = {}, halo_mort[MAX_S] = {};
   bool viscous() const { return prob.equations == PERK_NAVIER_STOKES; }
   double kappa() const { return prob.mu * prob.gamma / ((prob.gamma - 1.0) * prob.prandtl); }
-  Buf<double> d_q;   // BR1 gradients [n_elem][3][4][n^3]
+  Buf<double> d_q;   // BR1 viscous fluxes [n_elem][3 axes][5][n^3]
 
   Buf<int32_t> d_level, d_method, d_elem_sorted, d_minmem, d_minmax, d_member_lmax;
   Buf<int4> d_if_raw, d_mort_raw, d_if_sorted, d_mort_sorted, d_msmall;
@@ -612,7 +612,7 @@ perk_status perk3d_mesh_upload(perk3d_ctx* ctx, int64_t n_cells, const int32_t* 
   P3_CUDA(ctx, ctx->d_Ka.ensure(ne * elem3(ctx->nn)));
   P3_CUDA(ctx, ctx->d_Kb.ensure(ne * elem3(ctx->nn)));
   P3_CUDA(ctx, ctx->d_eta.ensure(ne));
-  if (ctx->viscous()) P3_CUDA(ctx, ctx->d_q.ensure(ne * 12 * nodes3(ctx->nn)));
+  if (ctx->viscous()) P3_CUDA(ctx, ctx->d_q.ensure(ne * 15 * nodes3(ctx->nn)));
   P3_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
                                ctx->stream));
   if (!c.ifs.empty())

@@ -63,7 +63,8 @@ cudaError_t launch_transfer3(cudaStream_t st, const Ops3& ops, int64_t n_new, co
 // BR1 viscous terms of one stage (perk3d_br1.cu): face averages of w and gradients on the halo
 // prefixes, viscous flux and divergence on the active prefixes; K += viscous part; surf (the
 // inviscid face-flux buffer, free once the volume kernel has run) holds the face averages,
-// q[e][axis][variable][node] the gradients; check: admissibility on the last stage
+// q[e][axis][variable][node] the viscous fluxes (15 n^3 doubles per element); check:
+// admissibility on the last stage
 cudaError_t launch_br1_3d(cudaStream_t st, YSource ys, const Ops3& ops, double mu, double kappa, int64_t n_if_halo,
                           int64_t n_mort_halo, int64_t n_if_act, int64_t n_mort_act, const int4* ifs,
                           const int4* morts, const int4* msmall, int64_t n_el_halo, int64_t n_el_act,
