@@ -7,10 +7,13 @@
 //                  interpolated large trace; large side takes the L2 projection)
 //   k_grad         q = (2/h) [D w + lifting of (w* - w)] at every node of every
 //                  element (inactive elements included: active neighbours need
-//                  their traces; this covers the one-ring halo)
-//   k_visc_faces   central viscous face flux f* = (f_v,L + f_v,R)/2 (normal component)
-//   k_visc_volume  K += (2/h) [D f_v + lifting of (f* - f_v)] on the active elements;
-//                  on the last stage also the admissibility check of the step
+//                  their traces; this covers the one-ring halo), and from it and the
+//                  stage state the viscous fluxes f_v along x and y, stored per node
+//   k_visc_faces   central viscous face flux f* = (f_v,L + f_v,R)/2 (normal component),
+//                  from the stored fluxes
+//   k_visc_volume  K += (2/h) [D f_v + lifting of (f* - f_v)] on the active elements,
+//                  from the stored fluxes; on the last stage also the admissibility
+//                  check of the step
 //
 // Stage states are formed on the fly exactly as in the inviscid kernels.
 
@@ -24,7 +27,7 @@
 namespace perk {
 namespace br1 {
 
-constexpr int QSTRIDE = 96;   // doubles of q per element: [direction][variable][node]
+constexpr int FSTRIDE = 128;  // doubles of viscous fluxes per element: [direction][variable][node]
 constexpr int WSTRIDE = 64;   // doubles of face data per element: [face][variable][node]
 
 __device__ __forceinline__ int face_node(int face, int k) {
@@ -80,12 +83,6 @@ __device__ __forceinline__ void visc_flux(const double u[4], const double qx[3],
   }
 }
 
-__device__ __forceinline__ void load_q(const double* q, int64_t e, int node, double qx[3], double qy[3]) {
-  for (int v = 0; v < 3; ++v) {
-    qx[v] = q[e * QSTRIDE + v * NODES + node];
-    qy[v] = q[e * QSTRIDE + 48 + v * NODES + node];
-  }
-}
 
 // ---------------------------------------------------------------------------
 template <int YS, int PHASE>
@@ -98,14 +95,13 @@ __global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4
   constexpr int NVAR = PHASE == 0 ? 3 : 4;
   __shared__ double s_half[16][2][4][NN];
   auto value = [&](int64_t e, int m, int node, int dir, double r[4]) {
-    double u[4];
-    state<YS>(sa, e, m, node, u);
     if (PHASE == 0) {
+      double u[4];
+      state<YS>(sa, e, m, node, u);
       grad_vars(u, ops.gm1, r);
     } else {
-      double qx[3], qy[3];
-      load_q(q, e, node, qx, qy);
-      visc_flux(u, qx, qy, dir, mu, kappa, r);
+      // the flux along the face's direction, stored by k_grad
+      for (int v = 0; v < 4; ++v) r[v] = q[e * FSTRIDE + dir * 64 + v * NODES + node];
     }
   };
   if (blockIdx.x < if_blocks) {
@@ -165,12 +161,13 @@ __global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4
   }
 }
 
-// q = (2/h) [D w + (1/w_N)(w* - w)|_N - (1/w_0)(w* - w)|_0] along x and y
+// q = (2/h) [D w + (1/w_N)(w* - w)|_N - (1/w_0)(w* - w)|_0] along x and y, then the viscous
+// fluxes f_v,x and f_v,y at the node, stored in fv[e][direction][variable][node]
 template <int YS>
 __global__ void __launch_bounds__(128) k_grad(Ops ops, int64_t n, const int32_t* __restrict__ elems,
                                                const int32_t* __restrict__ level, const int32_t* __restrict__ method,
                                                double two_over_len, StageArgs sa, const double* __restrict__ wsurf,
-                                               double* __restrict__ q) {
+                                               double mu, double kappa, double* __restrict__ fv) {
   __shared__ double s_w[8][3][NODES];
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
   const int64_t slot = (int64_t)blockIdx.x * 8 + le;
@@ -185,6 +182,7 @@ __global__ void __launch_bounds__(128) k_grad(Ops ops, int64_t n, const int32_t*
   const double s = ldexp(two_over_len, level[e]);
   const double iw = ops.inv_w0;
   const double* ws = wsurf + e * WSTRIDE;
+  double qx[3], qy[3];
   for (int v = 0; v < 3; ++v) {
     double gx = 0.0, gy = 0.0;
     for (int m = 0; m < NN; ++m) {
@@ -196,8 +194,15 @@ __global__ void __launch_bounds__(128) k_grad(Ops ops, int64_t n, const int32_t*
     if (i == 3) gx = fma(iw, ws[1 * 16 + 4 * v + j] - wv, gx);
     if (j == 0) gy = fma(-iw, ws[2 * 16 + 4 * v + i] - wv, gy);
     if (j == 3) gy = fma(iw, ws[3 * 16 + 4 * v + i] - wv, gy);
-    q[e * QSTRIDE + v * NODES + t] = s * gx;
-    q[e * QSTRIDE + 48 + v * NODES + t] = s * gy;
+    qx[v] = s * gx;
+    qy[v] = s * gy;
+  }
+  double fx[4], fy[4];
+  visc_flux(u, qx, qy, 0, mu, kappa, fx);
+  visc_flux(u, qx, qy, 1, mu, kappa, fy);
+  for (int v = 0; v < 4; ++v) {
+    fv[e * FSTRIDE + v * NODES + t] = fx[v];
+    fv[e * FSTRIDE + 64 + v * NODES + t] = fy[v];
   }
 }
 
@@ -206,21 +211,21 @@ template <int YS, bool CHECK>
 __global__ void __launch_bounds__(128) k_visc_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
                                                       const int32_t* __restrict__ level,
                                                       const int32_t* __restrict__ method, double two_over_len,
-                                                      StageArgs sa, const double* __restrict__ q,
-                                                      const double* __restrict__ vsurf, double mu, double kappa,
-                                                      double* __restrict__ K, UpdateArgs ua) {
+                                                      StageArgs sa, const double* __restrict__ fv,
+                                                      const double* __restrict__ vsurf, double* __restrict__ K,
+                                                      UpdateArgs ua) {
   __shared__ double s_f[8][2][4][NODES];
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
   const int64_t slot = (int64_t)blockIdx.x * 8 + le;
   const bool valid = slot < n;
   const int64_t e = valid ? elems[slot] : 0;
-  double u[4] = {1.0, 0.0, 0.0, 2.5}, qx[3] = {0, 0, 0}, qy[3] = {0, 0, 0}, fx[4], fy[4];
+  double fx[4] = {0.0, 0.0, 0.0, 0.0}, fy[4] = {0.0, 0.0, 0.0, 0.0};
   if (valid) {
-    state<YS>(sa, e, method[e], t, u);
-    load_q(q, e, t, qx, qy);
+    for (int v = 0; v < 4; ++v) {
+      fx[v] = fv[e * FSTRIDE + v * NODES + t];
+      fy[v] = fv[e * FSTRIDE + 64 + v * NODES + t];
+    }
   }
-  visc_flux(u, qx, qy, 0, mu, kappa, fx);
-  visc_flux(u, qx, qy, 1, mu, kappa, fy);
   for (int v = 0; v < 4; ++v) {
     s_f[le][0][v][t] = fx[v];
     s_f[le][1][v][t] = fy[v];
@@ -277,25 +282,25 @@ cudaError_t launch_br1(cudaStream_t st, YSource ysrc, const Ops& ops, double mu,
     if (bi + bm) br1::k_faces<Y_GIVEN, 0><<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if_all, ifs, n_mort_all, morts,
                                                                                bi, method, sa, q, mu, kappa, wsurf);
     if (n_all) br1::k_grad<Y_GIVEN><<<(unsigned)((n_all + 7) / 8), 128, 0, st>>>(ops, n_all, elems, level, method,
-                                                                                 two_over_len, sa, wsurf, q);
+                                                                                 two_over_len, sa, wsurf, mu, kappa, q);
     if (bia + bma) br1::k_faces<Y_GIVEN, 1><<<(unsigned)(bia + bma), 128, 0, st>>>(
         ops, n_if_act, ifs, n_mort_act, morts, bia, method, sa, q, mu, kappa, vsurf);
     if (n_act) br1::k_visc_volume<Y_GIVEN, false><<<(unsigned)((n_act + 7) / 8), 128, 0, st>>>(
-        ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, mu, kappa, K, ua);
+        ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, K, ua);
   } else {
     if (bi + bm) br1::k_faces<Y_COMBINE, 0><<<(unsigned)(bi + bm), 128, 0, st>>>(
         ops, n_if_all, ifs, n_mort_all, morts, bi, method, sa, q, mu, kappa, wsurf);
     if (n_all) br1::k_grad<Y_COMBINE><<<(unsigned)((n_all + 7) / 8), 128, 0, st>>>(ops, n_all, elems, level, method,
-                                                                                   two_over_len, sa, wsurf, q);
+                                                                                   two_over_len, sa, wsurf, mu, kappa, q);
     if (bia + bma) br1::k_faces<Y_COMBINE, 1><<<(unsigned)(bia + bma), 128, 0, st>>>(
         ops, n_if_act, ifs, n_mort_act, morts, bia, method, sa, q, mu, kappa, vsurf);
     if (n_act) {
       if (check)
         br1::k_visc_volume<Y_COMBINE, true><<<(unsigned)((n_act + 7) / 8), 128, 0, st>>>(
-            ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, mu, kappa, K, ua);
+            ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, K, ua);
       else
         br1::k_visc_volume<Y_COMBINE, false><<<(unsigned)((n_act + 7) / 8), 128, 0, st>>>(
-            ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, mu, kappa, K, ua);
+            ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, K, ua);
     }
   }
   return cudaGetLastError();

@@ -664,7 +664,7 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
   PERK_CUDA(ctx, ctx->d_eta.ensure(ne));
   if (ctx->viscous()) {
     PERK_CUDA(ctx, ctx->d_wsurf.ensure(ne * 64));
-    PERK_CUDA(ctx, ctx->d_q.ensure(ne * 96));
+    PERK_CUDA(ctx, ctx->d_q.ensure(ne * 128));   // BR1 viscous fluxes [e][2 directions][4][16]
     PERK_CUDA(ctx, ctx->d_vsurf.ensure(ne * 64));
   }
   const int nb = (int)std::min<int64_t>(1024, (n_cells * NODES + 255) / 256);
