@@ -60,10 +60,11 @@ UNIT = "DoF-stage updates/s"
 # + 16 nodes x 6 pairs x 4 variables (accumulation) + 128 (lifting, Jacobian)
 VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
 # DRAM bytes per element-stage of the same kernel (two elements per block, stage state formed from
-# U_n, K_1, K_{i-1}), measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum = 8.07 MB for a
-# launch over 3,904 elements); the algorithmic minimum is the 4 x 512 B read of U_n, K_1, K_{i-1}
-# and the face fluxes (K_i stays in L2 within the launch)
-VOL_DRAM_BYTES_PER_ELEM = 8.073984e6 / 3904
+# U_n, K_1, K_{i-1}), measured by ncu on the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum = 8.08 MB for a launch over all 3,904 elements of the KH mesh); the
+# algorithmic minimum is the 4 x 512 B read of U_n, K_1, K_{i-1} and the face fluxes (K_i stays in
+# L2 within the launch)
+VOL_DRAM_BYTES_PER_ELEM = 8.077312e6 / 3904
 
 
 AMR_KH = dict(level_min=4, level_max=7, refine_above=0.1, coarsen_below=0.02)
