@@ -20,6 +20,7 @@ LIB = os.path.join(PKG, "libperk.so")
 SOURCES = ["perk_kernels.cu", "perk_host.cpp", "perk_probe.cu", "perk_noalloc.cu", "perk_adjoint.cu", "perk_br1.cu",
            "perk3d_kernels.cu", "perk3d_host.cpp", "perk3d_br1.cu"]
 HEADERS = [os.path.join(INCLUDE, "perk.h"), os.path.join(INCLUDE, "perk3d.h"), os.path.join(CSRC, "perk_internal.h"),
+           os.path.join(CSRC, "perk3d_device.cuh"),
            os.path.join(CSRC, "perk3d_internal.h"), os.path.join(CSRC, "perk_devmath.cuh")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -23,6 +23,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "perk3d_device.cuh"
 #include "perk3d_internal.h"
 #include "perk_devmath.cuh"
 
@@ -31,42 +32,6 @@ namespace br1 {
 
 using perk::Y_COMBINE;
 using perk::Y_GIVEN;
-
-template <int NN>
-struct G {
-  static constexpr int FN = NN * NN, NODES = NN * NN * NN, ELEM = NV3 * NODES, SURF = 6 * NV3 * FN;
-  static constexpr int F = 15 * NODES;   // doubles of viscous fluxes per element: [axis][variable][node]
-};
-
-template <int NN>
-__device__ __forceinline__ int face_node3(int f, int q) {
-  const int t1 = q % NN, t2 = q / NN, b = (f & 1) ? NN - 1 : 0;
-  const int d = f >> 1;
-  return d == 0 ? (t2 * NN + t1) * NN + b : d == 1 ? (t2 * NN + b) * NN + t1 : (b * NN + t2) * NN + t1;
-}
-
-template <int NN, int YS>
-__device__ __forceinline__ void state3(const StageArgs& sa, int64_t e, int m, int node, double y[5]) {
-  constexpr int ND = G<NN>::NODES;
-  const int64_t base = e * G<NN>::ELEM + node;
-  if (YS == Y_GIVEN) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) y[v] = __ldg(sa.Y + base + v * ND);
-  } else {
-    const StageCoef c = sa.coef[m];
-    const double dt = sa.dt[0];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) y[v] = __ldg(sa.U + base + v * ND);
-    if (c.alpha != 0.0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) y[v] = fma(dt * c.alpha, __ldg(sa.K1 + base + v * ND), y[v]);
-    }
-    if (c.beta != 0.0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) y[v] = fma(dt * c.beta, __ldg(sa.Kp + base + v * ND), y[v]);
-    }
-  }
-}
 
 __device__ __forceinline__ void grad_vars3(const double u[5], double gm1, double w[5]) {
   const double ir = perk::rcp_nr(u[0]);
@@ -112,7 +77,7 @@ __global__ void __launch_bounds__(THREADS) k3b_faces(Ops3 ops, int64_t n_if, con
   auto value = [&](int64_t e, int m, int node, int d, double r[5]) {
     if (PHASE == 0) {
       double u[5];
-      state3<NN, YS>(sa, e, m, node, u);
+      stage_state3<NN, YS>(sa, e, m, node, u);
       grad_vars3(u, ops.gm1, r);
     } else {
       // the flux along the face's axis, stored by k3b_grad
@@ -226,7 +191,7 @@ __global__ void __launch_bounds__(THREADS) k3b_grad(Ops3 ops, int64_t n, const i
   double w[5];
   if (valid) {
     double u[5];
-    state3<NN, YS>(sa, e, method[e], node, u);
+    stage_state3<NN, YS>(sa, e, method[e], node, u);
     grad_vars3(u, ops.gm1, w);
 #pragma unroll
     for (int v = 0; v < 4; ++v) s_w[le][v][node] = w[v];

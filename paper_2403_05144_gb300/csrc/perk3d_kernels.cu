@@ -19,6 +19,7 @@
 
 #include <algorithm>
 
+#include "perk3d_device.cuh"
 #include "perk3d_internal.h"
 #include "perk_devmath.cuh"
 
@@ -33,50 +34,6 @@ using perk::series_2A;
 using perk::series_H;
 using perk::Y_COMBINE;
 using perk::Y_GIVEN;
-
-template <int NN>
-struct G {
-  static constexpr int FN = NN * NN;            // nodes per face
-  static constexpr int NODES = NN * NN * NN;    // nodes per element
-  static constexpr int ELEM = NV3 * NODES;      // doubles per element
-  static constexpr int SURF = 6 * NV3 * FN;     // face-flux doubles per element: [face][var][face node]
-  static constexpr int NPL = NN * (NN - 1) / 2; // symmetric pairs per grid line
-  static constexpr int NP = 3 * FN * NPL;       // symmetric pairs per element
-};
-
-// Volume node of face node q (t1 = q % NN, t2 = q / NN along the face's tangential axes t1 < t2)
-// on face f: 0/1 = -x/+x, 2/3 = -y/+y, 4/5 = -z/+z.  Volume node = (k NN + j) NN + i.
-template <int NN>
-__device__ __forceinline__ int face_node3(int f, int q) {
-  const int t1 = q % NN, t2 = q / NN, b = (f & 1) ? NN - 1 : 0;
-  const int d = f >> 1;
-  return d == 0 ? (t2 * NN + t1) * NN + b : d == 1 ? (t2 * NN + b) * NN + t1 : (b * NN + t2) * NN + t1;
-}
-
-template <int NN, int YS>
-__device__ __forceinline__ void stage_state3(const StageArgs& sa, int64_t e, int m, int node, double y[5]) {
-  const int64_t base = e * G<NN>::ELEM + node;
-  constexpr int ND = G<NN>::NODES;
-  if (YS == Y_GIVEN) {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) y[v] = __ldg(sa.Y + base + v * ND);
-  } else {
-    const StageCoef c = sa.coef[m];
-    const double dt = sa.dt[0];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) y[v] = __ldg(sa.U + base + v * ND);
-    if (c.alpha != 0.0) {
-      const double da = dt * c.alpha;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) y[v] = fma(da, __ldg(sa.K1 + base + v * ND), y[v]);
-    }
-    if (c.beta != 0.0) {
-      const double db = dt * c.beta;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) y[v] = fma(db, __ldg(sa.Kp + base + v * ND), y[v]);
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Two-point flux from node quantities (half values fold the 1/2 of the arithmetic means);
