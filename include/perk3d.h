@@ -145,6 +145,17 @@ perk_status perk3d_adapt_plan(perk3d_ctx* ctx, const perk3d_amr_params* prm, con
  * that changes no cell copies the state and keeps the mesh. */
 perk_status perk3d_adapt_commit(perk3d_ctx* ctx, const double* d_Uold, double* d_Unew);
 
+/* Host utility (no device work, no context): the plan perk3d_adapt_plan makes from given desired
+ * levels, for the leaf list cells[4 * n_cells] (a 2:1-balanced tiling of the cube, as for
+ * perk3d_mesh_upload).  levels[n_cells] receives the desired levels raised to the sibling and 2:1
+ * rules; *n_new the number of new leaves; when cap >= *n_new, new_cells[4 * n_new] receives them in
+ * Morton order and map[9 * n_new] their transfer records: map[9 q] = kind | cx << 2 | cy << 3 |
+ * cz << 4 (kind 0: copy of old cell map[9 q + 1]; 1: child (cx, cy, cz) of old cell map[9 q + 1];
+ * 2: parent of the old cells map[9 q + 1 + (cx + 2 cy + 4 cz)]).  INVALID_ARG for a malformed mesh
+ * or a desired level more than one away from its cell's. */
+perk_status perk3d_amr_plan_cells(int64_t n_cells, const int32_t* cells, const int32_t* desired, int32_t* levels,
+                                  int64_t* n_new, int32_t* new_cells, int32_t* map, int64_t cap);
+
 /* The current leaves (host, 4 * n_elem int32: level, ix, iy, iz), cap in cells. */
 perk_status perk3d_get_cells(const perk3d_ctx* ctx, int32_t* cells, int64_t cap);
 

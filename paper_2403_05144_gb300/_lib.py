@@ -139,6 +139,8 @@ SIGNATURES_3D = [
                                     C.POINTER(C.c_int64)]),
     ("perk3d_adapt_commit", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk3d_get_cells", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
+    ("perk3d_amr_plan_cells", C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64]),
 ]
 SIGNATURES = SIGNATURES + SIGNATURES_3D
 

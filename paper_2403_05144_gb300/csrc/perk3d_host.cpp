@@ -475,6 +475,133 @@ void count_step3(perk3d_ctx* ctx) {
   }
 }
 
+// One AMR plan on the host (the part of perk3d_adapt_plan after the desired levels): d (one level
+// per cell, within one of the cell's) raised in place to the least fixed point of the sibling rule
+// (eight leaves of one parent coarsen together) and the 2:1 rule across the face pairs; the new
+// leaves in Morton order (new_cells [m][4]) and their transfer records (map [m][9]: kind | child
+// bits, then the source cells).  False only if a coarsened parent misses a child, which a tiling
+// of the cube rules out.
+bool plan_cells3(int64_t n, const int32_t* c, const std::vector<std::pair<int32_t, int32_t>>& pairs,
+                 std::vector<int32_t>& d, bool* identity_out, std::vector<int32_t>& new_cells,
+                 std::vector<int32_t>& map) {
+  std::unordered_map<uint64_t, int32_t> gid;
+  std::vector<int32_t> group_of(n, -1), gcount, gmembers;
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = c[4 * e];
+    if (l == 0) continue;
+    const uint64_t k = key3(l, c[4 * e + 1] >> 1, c[4 * e + 2] >> 1, c[4 * e + 3] >> 1);
+    auto it = gid.find(k);
+    int32_t g;
+    if (it == gid.end()) {
+      g = (int32_t)gcount.size();
+      gid.emplace(k, g);
+      gcount.push_back(0);
+      gmembers.insert(gmembers.end(), 8, -1);
+    } else {
+      g = it->second;
+    }
+    if (gcount[g] < 8) gmembers[8 * g + gcount[g]] = (int32_t)e;
+    gcount[g] += 1;
+    group_of[e] = g;
+  }
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int64_t e = 0; e < n; ++e) {
+      if (d[e] >= c[4 * e]) continue;
+      const int32_t g = group_of[e];
+      bool ok = g >= 0 && gcount[g] == 8;
+      for (int q = 0; ok && q < 8; ++q) ok = d[gmembers[8 * g + q]] < c[4 * gmembers[8 * g + q]];
+      if (ok) continue;
+      if (g < 0) {
+        d[e] = c[4 * e];
+        changed = true;
+        continue;
+      }
+      for (int q = 0; q < 8 && q < gcount[g]; ++q) {
+        const int32_t m = gmembers[8 * g + q];
+        if (d[m] < c[4 * m]) {
+          d[m] = c[4 * m];
+          changed = true;
+        }
+      }
+    }
+    for (const auto& pr : pairs) {
+      const int32_t a = pr.first, b = pr.second;
+      if (d[a] > d[b] + 1) {
+        d[b] = d[a] - 1;
+        changed = true;
+      } else if (d[b] > d[a] + 1) {
+        d[a] = d[b] - 1;
+        changed = true;
+      }
+    }
+  }
+  bool identity = true;
+  for (int64_t e = 0; e < n && identity; ++e) identity = d[e] == c[4 * e];
+  *identity_out = identity;
+  // new leaves (Morton order) and transfer records
+  std::unordered_map<uint64_t, int32_t> old;
+  old.reserve((size_t)n * 2);
+  int lmax = 0;
+  for (int64_t e = 0; e < n; ++e) {
+    old.emplace(key3(c[4 * e], c[4 * e + 1], c[4 * e + 2], c[4 * e + 3]), (int32_t)e);
+    lmax = std::max(lmax, d[e]);
+  }
+  struct NewCell {
+    int32_t l, x, y, z;
+  };
+  std::vector<NewCell> nc;
+  nc.reserve((size_t)n * 2);
+  std::unordered_map<uint64_t, int32_t> seen;
+  for (int64_t e = 0; e < n; ++e) {
+    const int l = c[4 * e], x = c[4 * e + 1], y = c[4 * e + 2], z = c[4 * e + 3];
+    if (d[e] == l + 1) {
+      for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+          for (int cx = 0; cx < 2; ++cx) nc.push_back({l + 1, 2 * x + cx, 2 * y + cy, 2 * z + cz});
+    } else if (d[e] == l) {
+      nc.push_back({l, x, y, z});
+    } else if (seen.emplace(key3(l - 1, x >> 1, y >> 1, z >> 1), 1).second) {
+      nc.push_back({l - 1, x >> 1, y >> 1, z >> 1});
+    }
+  }
+  std::vector<std::pair<uint64_t, int64_t>> order(nc.size());
+  for (size_t k = 0; k < nc.size(); ++k) order[k] = {morton3(nc[k].l, nc[k].x, nc[k].y, nc[k].z, lmax), (int64_t)k};
+  std::sort(order.begin(), order.end());
+  const int64_t m = (int64_t)nc.size();
+  new_cells.resize(4 * m);
+  map.assign(9 * m, 0);
+  for (int64_t k = 0; k < m; ++k) {
+    const NewCell& q = nc[order[k].second];
+    int32_t* cc = &new_cells[4 * k];
+    cc[0] = q.l;
+    cc[1] = q.x;
+    cc[2] = q.y;
+    cc[3] = q.z;
+    int32_t* r = &map[9 * k];
+    auto it = old.find(key3(q.l, q.x, q.y, q.z));
+    if (it != old.end()) {
+      r[0] = 0;
+      r[1] = it->second;
+      continue;
+    }
+    auto par = q.l > 0 ? old.find(key3(q.l - 1, q.x >> 1, q.y >> 1, q.z >> 1)) : old.end();
+    if (par != old.end()) {
+      r[0] = 1 | ((q.x & 1) << 2) | ((q.y & 1) << 3) | ((q.z & 1) << 4);
+      r[1] = par->second;
+      continue;
+    }
+    r[0] = 2;
+    for (int ch = 0; ch < 8; ++ch) {
+      auto ci = old.find(key3(q.l + 1, 2 * q.x + (ch & 1), 2 * q.y + ((ch >> 1) & 1), 2 * q.z + (ch >> 2)));
+      if (ci == old.end()) return false;
+      r[1 + ch] = ci->second;
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -874,123 +1001,11 @@ perk_status perk3d_adapt_plan(perk3d_ctx* ctx, const perk3d_amr_params* prm, con
       return PERK_OK;
     }
   }
-  // least fixed point of the sibling rule (eight leaves of one parent coarsen together) and the
-  // 2:1 rule across faces
-  std::unordered_map<uint64_t, int32_t> gid;
-  std::vector<int32_t> group_of(n, -1), gcount, gmembers;
-  for (int64_t e = 0; e < n; ++e) {
-    const int l = c[4 * e];
-    if (l == 0) continue;
-    const uint64_t k = key3(l, c[4 * e + 1] >> 1, c[4 * e + 2] >> 1, c[4 * e + 3] >> 1);
-    auto it = gid.find(k);
-    int32_t g;
-    if (it == gid.end()) {
-      g = (int32_t)gcount.size();
-      gid.emplace(k, g);
-      gcount.push_back(0);
-      gmembers.insert(gmembers.end(), 8, -1);
-    } else {
-      g = it->second;
-    }
-    if (gcount[g] < 8) gmembers[8 * g + gcount[g]] = (int32_t)e;
-    gcount[g] += 1;
-    group_of[e] = g;
-  }
-  bool changed = true;
-  while (changed) {
-    changed = false;
-    for (int64_t e = 0; e < n; ++e) {
-      if (d[e] >= c[4 * e]) continue;
-      const int32_t g = group_of[e];
-      bool ok = g >= 0 && gcount[g] == 8;
-      for (int q = 0; ok && q < 8; ++q) ok = d[gmembers[8 * g + q]] < c[4 * gmembers[8 * g + q]];
-      if (ok) continue;
-      if (g < 0) {
-        d[e] = c[4 * e];
-        changed = true;
-        continue;
-      }
-      for (int q = 0; q < 8 && q < gcount[g]; ++q) {
-        const int32_t m = gmembers[8 * g + q];
-        if (d[m] < c[4 * m]) {
-          d[m] = c[4 * m];
-          changed = true;
-        }
-      }
-    }
-    for (const auto& pr : ctx->h_pairs) {
-      const int32_t a = pr.first, b = pr.second;
-      if (d[a] > d[b] + 1) {
-        d[b] = d[a] - 1;
-        changed = true;
-      } else if (d[b] > d[a] + 1) {
-        d[a] = d[b] - 1;
-        changed = true;
-      }
-    }
-  }
-  bool identity = true;
-  for (int64_t e = 0; e < n && identity; ++e) identity = d[e] == c[4 * e];
+  bool identity = false;
+  if (!plan_cells3(n, c, ctx->h_pairs, d, &identity, ctx->plan_cells, ctx->plan_map))
+    return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
   ctx->plan_identity = identity;
-  // new leaves (Morton order) and transfer records
-  std::unordered_map<uint64_t, int32_t> old;
-  old.reserve((size_t)n * 2);
-  int lmax = 0;
-  for (int64_t e = 0; e < n; ++e) {
-    old.emplace(key3(c[4 * e], c[4 * e + 1], c[4 * e + 2], c[4 * e + 3]), (int32_t)e);
-    lmax = std::max(lmax, d[e]);
-  }
-  struct NewCell {
-    int32_t l, x, y, z;
-  };
-  std::vector<NewCell> nc;
-  nc.reserve((size_t)n * 2);
-  std::unordered_map<uint64_t, int32_t> seen;
-  for (int64_t e = 0; e < n; ++e) {
-    const int l = c[4 * e], x = c[4 * e + 1], y = c[4 * e + 2], z = c[4 * e + 3];
-    if (d[e] == l + 1) {
-      for (int cz = 0; cz < 2; ++cz)
-        for (int cy = 0; cy < 2; ++cy)
-          for (int cx = 0; cx < 2; ++cx) nc.push_back({l + 1, 2 * x + cx, 2 * y + cy, 2 * z + cz});
-    } else if (d[e] == l) {
-      nc.push_back({l, x, y, z});
-    } else if (seen.emplace(key3(l - 1, x >> 1, y >> 1, z >> 1), 1).second) {
-      nc.push_back({l - 1, x >> 1, y >> 1, z >> 1});
-    }
-  }
-  std::vector<std::pair<uint64_t, int64_t>> order(nc.size());
-  for (size_t k = 0; k < nc.size(); ++k) order[k] = {morton3(nc[k].l, nc[k].x, nc[k].y, nc[k].z, lmax), (int64_t)k};
-  std::sort(order.begin(), order.end());
-  const int64_t m = (int64_t)nc.size();
-  ctx->plan_cells.resize(4 * m);
-  ctx->plan_map.assign(9 * m, 0);
-  for (int64_t k = 0; k < m; ++k) {
-    const NewCell& q = nc[order[k].second];
-    int32_t* cc = &ctx->plan_cells[4 * k];
-    cc[0] = q.l;
-    cc[1] = q.x;
-    cc[2] = q.y;
-    cc[3] = q.z;
-    int32_t* r = &ctx->plan_map[9 * k];
-    auto it = old.find(key3(q.l, q.x, q.y, q.z));
-    if (it != old.end()) {
-      r[0] = 0;
-      r[1] = it->second;
-      continue;
-    }
-    auto par = q.l > 0 ? old.find(key3(q.l - 1, q.x >> 1, q.y >> 1, q.z >> 1)) : old.end();
-    if (par != old.end()) {
-      r[0] = 1 | ((q.x & 1) << 2) | ((q.y & 1) << 3) | ((q.z & 1) << 4);
-      r[1] = par->second;
-      continue;
-    }
-    r[0] = 2;
-    for (int ch = 0; ch < 8; ++ch) {
-      auto ci = old.find(key3(q.l + 1, 2 * q.x + (ch & 1), 2 * q.y + ((ch >> 1) & 1), 2 * q.z + (ch >> 2)));
-      if (ci == old.end()) return fail(ctx, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
-      r[1 + ch] = ci->second;
-    }
-  }
+  const int64_t m = (int64_t)ctx->plan_cells.size() / 4;
   ctx->plan_n = m;
   ctx->has_plan = true;
   *n_new = m;
@@ -1016,6 +1031,40 @@ perk_status perk3d_adapt_commit(perk3d_ctx* ctx, const double* d_Uold, double* d
   const std::vector<int32_t> cells = std::move(ctx->plan_cells);
   ctx->plan_cells.clear();
   return perk3d_mesh_upload(ctx, m, cells.data(), ctx->x0, ctx->length);
+}
+
+perk_status perk3d_amr_plan_cells(int64_t n_cells, const int32_t* cells, const int32_t* desired, int32_t* levels,
+                                  int64_t* n_new, int32_t* new_cells, int32_t* map, int64_t cap) {
+  if (n_cells <= 0 || !cells || !desired || !levels || !n_new) return fail(nullptr, PERK_E_INVALID_ARG, "bad arguments");
+  Conn conn;
+  const std::string e = build_connectivity3(n_cells, cells, conn);
+  if (!e.empty()) return fail(nullptr, PERK_E_INVALID_ARG, "%s", e.c_str());
+  std::vector<int32_t> d(n_cells);
+  for (int64_t q = 0; q < n_cells; ++q) {
+    const int l = cells[4 * q];
+    if (desired[q] < l - 1 || desired[q] > l + 1 || desired[q] < 0 || desired[q] > MAX_LEVEL3)
+      return fail(nullptr, PERK_E_INVALID_ARG, "desired level of cell %lld must differ by at most one", (long long)q);
+    d[q] = desired[q];
+  }
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  pairs.reserve(conn.ifs.size() + 4 * conn.morts.size());
+  for (const int4& f : conn.ifs) pairs.emplace_back(f.x, f.y);
+  for (const int4& m : conn.morts) {
+    const int4 sm = conn.msmall[m.z];
+    for (int32_t q : {sm.x, sm.y, sm.z, sm.w}) pairs.emplace_back(m.x, q);
+  }
+  bool identity = false;
+  std::vector<int32_t> nc, mp;
+  if (!plan_cells3(n_cells, cells, pairs, d, &identity, nc, mp))
+    return fail(nullptr, PERK_E_INVALID_ARG, "internal: missing child in AMR plan");
+  std::copy(d.begin(), d.end(), levels);
+  const int64_t m = (int64_t)nc.size() / 4;
+  *n_new = m;
+  if (cap >= m) {
+    if (new_cells) std::copy(nc.begin(), nc.end(), new_cells);
+    if (map) std::copy(mp.begin(), mp.end(), map);
+  }
+  return PERK_OK;
 }
 
 perk_status perk3d_get_cells(const perk3d_ctx* ctx, int32_t* cells, int64_t cap) {

@@ -16,7 +16,7 @@ import numpy as np
 from . import _lib
 from ._lib import PerkError
 
-__all__ = ["Perk3DSolver", "mesh_faces3"]
+__all__ = ["Perk3DSolver", "mesh_faces3", "amr_plan_cells"]
 
 
 def _check(lib, ctx, status: int):
@@ -38,6 +38,27 @@ def mesh_faces3(cells):
     _check(lib, None, lib.perk3d_mesh_faces(len(arr), cp, C.byref(ni), ifs.ctypes.data_as(C.POINTER(C.c_int32)),
                                             ni.value, C.byref(nm), ms.ctypes.data_as(C.POINTER(C.c_int32)), nm.value))
     return ifs, ms
+
+
+def amr_plan_cells(cells, desired):
+    """(balanced levels [n], new leaves [m, 4], transfer records [m, 9]) of one AMR cycle with the
+    given desired levels (host only; the plan perk3d_adapt_plan makes)."""
+    lib = _lib.load()
+    arr = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 4))
+    d = np.ascontiguousarray(np.asarray(desired, dtype=np.int32).reshape(-1))
+    if len(d) != len(arr):
+        raise ValueError("desired needs one level per cell")
+    levels = np.zeros(len(arr), dtype=np.int32)
+    m = C.c_int64()
+    P = C.POINTER(C.c_int32)
+    _check(lib, None, lib.perk3d_amr_plan_cells(len(arr), arr.ctypes.data_as(P), d.ctypes.data_as(P),
+                                                levels.ctypes.data_as(P), C.byref(m), None, None, 0))
+    new = np.zeros((m.value, 4), dtype=np.int32)
+    mp = np.zeros((m.value, 9), dtype=np.int32)
+    _check(lib, None, lib.perk3d_amr_plan_cells(len(arr), arr.ctypes.data_as(P), d.ctypes.data_as(P),
+                                                levels.ctypes.data_as(P), C.byref(m), new.ctypes.data_as(P),
+                                                mp.ctypes.data_as(P), m.value))
+    return levels, new, mp
 
 
 class Perk3DSolver:

@@ -52,3 +52,53 @@ def test_rejects_unbalanced_and_untiled_meshes(lib):
         mesh_faces3(uniform_cells3(1)[:-1])
     with pytest.raises(PerkError, match="duplicated"):
         mesh_faces3(uniform_cells3(1) + [uniform_cells3(1)[0]])
+
+
+def _plan_cases():
+    from perk_inputs.octree import block_refined_cells3, refine_cells3, uniform_cells3
+    rng = np.random.default_rng(31)
+    three = refine_cells3(refine_cells3(uniform_cells3(2), lambda l, ix, iy, iz: 1 <= ix < 3 and iy < 2 and 1 <= iz),
+                          lambda l, ix, iy, iz: l == 3 and 3 <= ix < 5 and 1 <= iy < 3 and 3 <= iz < 5)
+    cases = []
+    for cells in (uniform_cells3(2), block_refined_cells3(2, 1, 3), three):
+        lev = np.asarray(cells)[:, 0]
+        for _ in range(3):
+            cases.append((cells, np.clip(lev + rng.integers(-1, 2, size=len(lev)), 1, 5)))
+        cases.append((cells, lev - (lev > 1)))        # every cell asks to coarsen
+    return cases
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_amr_plan_matches_the_oracle(lib, case):
+    """Balanced levels, new leaves (Morton order) and transfer records of the library's octree AMR
+    plan against the oracle's balance and new leaves (Sec. 7.1.3's AMR cycle)."""
+    from oracle.amr3d import balance3, new_cells3
+    from paper_2403_05144_gb300.perk3d import amr_plan_cells
+    cells, desired = _plan_cases()[case]
+    mesh = OctreeMesh(np.asarray(cells), 0.0, 1.0)
+    levels, new, mp = amr_plan_cells(cells, desired)
+    want_levels = balance3(mesh, desired)
+    assert np.array_equal(levels, want_levels)
+    want_cells = new_cells3(mesh, want_levels)
+    assert [tuple(c) for c in new.tolist()] == [tuple(c) for c in want_cells]
+    old = {tuple(c): e for e, c in enumerate(cells)}
+    for (l, x, y, z), r in zip(new.tolist(), mp.tolist()):
+        kind = r[0] & 3
+        if kind == 0:
+            assert old[(l, x, y, z)] == r[1]
+        elif kind == 1:
+            assert old[(l - 1, x >> 1, y >> 1, z >> 1)] == r[1]
+            assert ((r[0] >> 2) & 1, (r[0] >> 3) & 1, (r[0] >> 4) & 1) == (x & 1, y & 1, z & 1)
+        else:
+            for ch in range(8):
+                assert old[(l + 1, 2 * x + (ch & 1), 2 * y + ((ch >> 1) & 1), 2 * z + (ch >> 2))] == r[1 + ch]
+
+
+def test_amr_plan_rejects_jumps_of_two_levels(lib):
+    from paper_2403_05144_gb300._lib import PerkError
+    from paper_2403_05144_gb300.perk3d import amr_plan_cells
+    cells = uniform_cells3(2)
+    d = np.full(len(cells), 2)
+    d[0] = 4
+    with pytest.raises(PerkError, match="at most one"):
+        amr_plan_cells(cells, d)
