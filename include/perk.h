@@ -358,6 +358,13 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
  * cells); then the mesh is replaced and re-partitioned on the device.  Blocks. */
 perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew);
 
+/* Host utility (no device work, no context): the balanced levels perk_adapt_plan derives from
+ * desired levels for a single mesh: desired[n_cells] (each within one level of its cell's)
+ * raised to the least fixed point of the sibling rule (a cell coarsens only with its three
+ * siblings, all wanting to) and the 2:1 rule across faces, written to levels[n_cells].  cells as
+ * for perk_mesh_upload; INVALID_ARG for a malformed mesh or a jump of more than one level. */
+perk_status perk_amr_balance(int64_t n_cells, const int32_t* cells, const int32_t* desired, int32_t* levels);
+
 /* The current leaves (host, 3 * n_elem int32: level, ix, iy), cap in cells. */
 perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap);
 

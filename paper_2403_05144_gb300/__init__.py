@@ -128,6 +128,20 @@ def mesh_faces(cells):
     return ifs, ms
 
 
+def amr_balance(cells, desired):
+    """Balanced levels of one AMR cycle for desired levels (host only; what perk_adapt_plan applies)."""
+    lib = _lib.load()
+    arr = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 3))
+    d = np.ascontiguousarray(np.asarray(desired, dtype=np.int32).reshape(-1))
+    if len(d) != len(arr):
+        raise ValueError("desired needs one level per cell")
+    out = np.zeros(len(arr), dtype=np.int32)
+    P = C.POINTER(C.c_int32)
+    _check(lib, None, lib.perk_amr_balance(len(arr), arr.ctypes.data_as(P), d.ctypes.data_as(P),
+                                           out.ctypes.data_as(P)))
+    return out
+
+
 def measure_fp64():
     """Measured FP64 rates of the current device: (FMA flop/s, divisions/s, logarithms/s)."""
     lib = _lib.load()

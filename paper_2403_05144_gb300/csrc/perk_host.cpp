@@ -2066,6 +2066,29 @@ perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Une
   return set_mesh(ctx, m, cells.data(), ctx->n_members > 1 ? members.data() : nullptr, ctx->x0, ctx->length);
 }
 
+perk_status perk_amr_balance(int64_t n_cells, const int32_t* cells, const int32_t* desired, int32_t* levels) {
+  if (n_cells <= 0 || !cells || !desired || !levels) return fail(nullptr, PERK_E_INVALID_ARG, "bad arguments");
+  // the host state balance_levels reads, in a context that owns no device memory
+  perk_ctx tmp;
+  std::vector<int4> ifs, morts;
+  if (build_connectivity(nullptr, n_cells, cells, nullptr, ifs, morts) != PERK_OK) return PERK_E_INVALID_ARG;
+  tmp.n_elem = n_cells;
+  tmp.h_cells.assign(cells, cells + 3 * n_cells);
+  tmp.h_member.assign(n_cells, 0);
+  tmp.h_if = std::move(ifs);
+  tmp.h_mort = std::move(morts);
+  std::vector<int32_t> d(n_cells);
+  for (int64_t e = 0; e < n_cells; ++e) {
+    const int l = cells[3 * e];
+    if (desired[e] < l - 1 || desired[e] > l + 1 || desired[e] < 0 || desired[e] > 27)
+      return fail(nullptr, PERK_E_INVALID_ARG, "desired level of cell %lld must differ by at most one", (long long)e);
+    d[e] = desired[e];
+  }
+  balance_levels(&tmp, d);
+  std::copy(d.begin(), d.end(), levels);
+  return PERK_OK;
+}
+
 perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap) {
   if (!ctx || !cells) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return PERK_E_NOT_READY;

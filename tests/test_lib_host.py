@@ -164,3 +164,25 @@ def test_pattern_tableau_matches_oracle(lib, E, pattern):
             A[i, 0] += c[i] - a[r, i]
         np.testing.assert_allclose(A, fam.A[r], rtol=1e-13, atol=1e-15)
         assert [bool(x) for x in ev[r]] == [fam.active(r, i) for i in range(fam.S)]
+
+
+def _balance_cases():
+    rng = np.random.default_rng(41)
+    cases = []
+    for cells in (uniform_cells(3), vortex_two_level_cells(3, 2, 6), kh_band_cells(3, 6, 0.05)):
+        lev = np.asarray(cells)[:, 0]
+        for _ in range(3):
+            cases.append((cells, np.clip(lev + rng.integers(-1, 2, size=len(lev)), 1, 7)))
+        cases.append((cells, lev - (lev > 1)))
+    return cases
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_amr_balance_matches_the_oracle(lib, case):
+    """The quadtree AMR plan's balanced levels (sibling and 2:1 rules) against the oracle's."""
+    from oracle.amr import balance
+    from paper_2403_05144_gb300 import amr_balance
+    cells, desired = _balance_cases()[case]
+    got = amr_balance(cells, desired)
+    want = balance(TreeMesh(np.asarray(cells), 0.0, 1.0), desired)
+    assert np.array_equal(got, want)
