@@ -102,3 +102,26 @@ def test_amr_plan_rejects_jumps_of_two_levels(lib):
     d[0] = 4
     with pytest.raises(PerkError, match="at most one"):
         amr_plan_cells(cells, d)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_connectivity_of_random_balanced_octrees(lib, seed):
+    """Random meshes grown by the oracle's balanced AMR cycle (random wishes, three cycles from
+    level 1): the library's interfaces and mortars equal the oracle's geometric face matching."""
+    from oracle.amr3d import balance3, new_cells3
+    from paper_2403_05144_gb300.perk3d import mesh_faces3
+    rng = np.random.default_rng(100 + seed)
+    cells = uniform_cells3(1)
+    for _ in range(3):
+        mesh = OctreeMesh(np.asarray(cells), 0.0, 1.0)
+        lev = mesh.cells[:, 0]
+        wish = np.clip(lev + rng.choice([-1, 0, 1], size=len(lev), p=[0.2, 0.5, 0.3]), 0, 4)
+        cells = new_cells3(mesh, balance3(mesh, wish))
+    mesh = OctreeMesh(np.asarray(cells), 0.0, 1.0)
+    ifs, morts = mesh_faces3(cells)
+    assert sorted(map(tuple, ifs[:, :3].tolist())) == sorted(mesh.conforming)
+    want = {}
+    for (A, B, d, large, q1, q2) in mesh.hanging:
+        want.setdefault((large, d, 0 if large == A else 1), {})[q1 + 2 * q2] = B if large == A else A
+    got = {(l, f & 3, (f >> 2) & 1): {0: a, 1: b, 2: c, 3: e} for (l, a, b, c, e, f) in morts.tolist()}
+    assert got == want
