@@ -3,7 +3,6 @@ by its pins: a transposed mortar quadrant, a wrong energy term of the two-point 
 a dropped cross term of the 3D viscous stress.  This checks that the pins of
 test_oracle_dgsem3d.py and test_oracle_br1_3d.py constrain what they are meant to."""
 import numpy as np
-import pytest
 
 import oracle.br1_3d as br1_3d
 import oracle.dgsem3d as dgsem3d
