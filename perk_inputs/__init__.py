@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the CUDA path and the oracle.
 
 This package holds input construction only: quadtree leaf-cell lists for the
-benchmark meshes, analytic initial conditions, and seeded random draws. It
+benchmark meshes (octree lists and 3D initial states in ``perk_inputs.octree``), analytic initial conditions, and seeded random draws. It
 holds none of the method's arithmetic (no DGSEM operator, no flux, no
 Runge-Kutta coefficient), so both the product library and the oracle can take
 their inputs from here without sharing any of the computation under test.
