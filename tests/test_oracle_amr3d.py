@@ -131,3 +131,19 @@ def test_desired_levels_thresholds():
     eta[0] = 5.0
     d = desired_levels3(mesh, eta, 1, 3, refine_above=1.0, coarsen_below=0.5)
     assert d[0] == 3 and is_balanced3(_mesh(new_cells3(mesh, d)))
+
+
+def test_taylor_green_bench_mesh_recipe():
+    """The benchmark's 3D mesh: 16^3 cells adapted twice by the enstrophy indicator (levels 4-6,
+    refine above 1.2, coarsen below 0.3) has 30,080 cells (3,136 / 4,928 / 22,016 on levels
+    4 / 5 / 6), and a third cycle leaves it unchanged."""
+    x, _ = lgl_nodes_weights(2)
+    cells = uniform_cells3(4)
+    U = nodal_state3(taylor_green, cells, 0.0, 2 * math.pi, x)
+    m = OctreeMesh(np.asarray(cells), 0.0, 2 * math.pi)
+    for _ in range(2):
+        m, U, _ = adapt3(m, U, 4, 6, 1.2, 0.3)
+    assert m.n_elem == 30080
+    assert np.bincount(m.cells[:, 0]).tolist()[4:] == [3136, 4928, 22016]
+    m3, _, d = adapt3(m, U, 4, 6, 1.2, 0.3)
+    assert np.array_equal(d, m.cells[:, 0])
