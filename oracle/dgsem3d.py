@@ -184,10 +184,14 @@ class DGSEM3D:
 
 def max_wave_speed_dt3(U: np.ndarray, h: np.ndarray, N: int, cfl: float, gamma: float = euler3d.GAMMA) -> float:
     """dt = cfl * min_e h_e / ((N + 1) lambda_e), lambda_e = max over the element's nodes of
-    |v1| + |v2| + |v3| + 3c (the 2D rule of Eq. TimestepConstraint summed over three axes)."""
+    |v1| + |v2| + |v3| + 3c (the 2D rule of Eq. TimestepConstraint summed over three axes).
+    NaN if any node has rho <= 0, p <= 0 or a non-finite entry (no sound speed exists)."""
     rho = U[:, 0]
-    v = [U[:, 1 + d] / rho for d in range(3)]
-    p = (gamma - 1.0) * (U[:, 4] - 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
-    c = np.sqrt(gamma * p / rho)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v = [U[:, 1 + d] / rho for d in range(3)]
+        p = (gamma - 1.0) * (U[:, 4] - 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+        if not (np.all(rho > 0.0) and np.all(p > 0.0)):
+            return float("nan")
+        c = np.sqrt(gamma * p / rho)
     lam = (np.abs(v[0]) + np.abs(v[1]) + np.abs(v[2]) + 3.0 * c).reshape(len(h), -1).max(axis=1)
     return float(cfl * np.min(h / ((N + 1) * lam)))

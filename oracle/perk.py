@@ -216,12 +216,17 @@ def rk_step(rhs: Callable[[np.ndarray], np.ndarray], U: np.ndarray, dt: float, A
 def max_wave_speed_dt(U: np.ndarray, h: np.ndarray, N: int, cfl: float, gamma: float = 1.4) -> float:
     """dt = cfl * min_e h_e / ((N + 1) lambda_e), lambda_e = max over the
     element's nodes of |v1| + |v2| + 2c (the convective time scale of
-    Eq. CFL_DG summed over both directions)."""
+    Eq. CFL_DG summed over both directions).  The sound speed, and with it the
+    step, exists only for admissible states: NaN if any node has rho <= 0,
+    p <= 0 or a non-finite entry."""
     rho = U[:, 0]
-    v1 = U[:, 1] / rho
-    v2 = U[:, 2] / rho
-    p = (gamma - 1.0) * (U[:, 3] - 0.5 * rho * (v1 * v1 + v2 * v2))
-    c = np.sqrt(gamma * p / rho)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v1 = U[:, 1] / rho
+        v2 = U[:, 2] / rho
+        p = (gamma - 1.0) * (U[:, 3] - 0.5 * rho * (v1 * v1 + v2 * v2))
+        if not (np.all(rho > 0.0) and np.all(p > 0.0)):
+            return float("nan")
+        c = np.sqrt(gamma * p / rho)
     lam = (np.abs(v1) + np.abs(v2) + 2.0 * c).reshape(len(h), -1).max(axis=1)
     return float(cfl * np.min(h / ((N + 1) * lam)))
 
