@@ -51,10 +51,18 @@ from perk_inputs import (isentropic_vortex, kelvin_helmholtz, nodal_state, shear
 METRIC = "P-ERK DoF-stage updates/s and wall time to t_end vs full-RK on same GB300"
 UNIT = "DoF-stage updates/s"
 
+# Algorithmic FP64 operations of one element-stage of the volume term (Euler, N = 3), counted
+# by the oracle's operation counter (oracle/opcount.py; add/mul 1, divide and logarithm 1 each;
+# tests/test_oracle_opcount.py checks that this constant is its result): stage state 256, node
+# quantities 192 (48 divides, 32 logarithms), the 48 symmetric pair fluxes 1,392 (144 divides),
+# flux differencing 640, surface lifting and Jacobian 192.  The roofline's `achieved` is this
+# count times the element-stages of the profiled volume launches over their CUDA-event time.
+VOL_ALG_FLOPS_PER_ELEM = 2672
 # FP64 issue slots of one element-stage of the volume kernel (flux
 # differencing + surface lifting + stage combination) in the library's
 # formulation (add, mul, FMA, compare = 1 slot; reciprocal = 4 FMA after the
-# approximate seed; table logarithm = 15 slots):
+# approximate seed; table logarithm = 15 slots), reported beside the roofline as
+# how busy the kernel keeps the FP64 issue slots:
 #   16 nodes x 60   (combination 10, pressure 5, reciprocal 5, primitives 10, two logarithms 30)
 # + 48 pairs x 44   (means' branches 9, reciprocal 5, quotients 3, two log-mean series 15, flux 12)
 # + 16 nodes x 6 pairs x 4 variables (accumulation) + 128 (lifting, Jacobian)
@@ -496,7 +504,8 @@ def run_perk(args) -> None:
     for _ in range(args.steps):
         acc = perk.solver.step_profiled(Up, perk.dt, acc)
     vol_ms, vol_launches = acc.ms[1], acc.launches[1]
-    achieved = 2.0 * VOL_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
+    achieved = VOL_ALG_FLOPS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
+    slot_rate = 2.0 * VOL_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)   # FMA-equivalent slots
     kernel_ms_total = sum(acc.ms[k] for k in range(4))
 
     # end to end through the public API: the state lives in pinned host memory;
@@ -569,8 +578,15 @@ def run_perk(args) -> None:
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
-                     "work_per_element_stage": {"fp64_slots": VOL_SLOTS_PER_ELEM, "flops": 2 * VOL_SLOTS_PER_ELEM,
-                                                "note": "FMA-equivalent: every FP64 issue slot counted as 2 flops"},
+                     "work_per_element_stage": {"algorithmic_flops": VOL_ALG_FLOPS_PER_ELEM,
+                                                "source": "oracle operation counter (add/mul 1, divide and "
+                                                          "logarithm 1 each; 48 symmetric pairs)"},
+                     "issue_slot_frac": slot_rate / fma_flops,
+                     "issue_slot_note": f"{VOL_SLOTS_PER_ELEM} FP64 issue slots per element-stage in the "
+                                        "kernel's own formulation, each counted as an FMA (2 flops), "
+                                        "over the measured FMA peak: how busy the FP64 issue slots are",
+                     "fp64_pipe_active_source": "ncu sm__pipe_fp64_cycles_active in "
+                                                "profiles/k_volume_kelvin_helmholtz_amr_3904cells.md",
                      "cuda_fp64_rates": {"div_per_s": div_s, "log_per_s": log_s}},
         "e2e": {"value": replica_rate(units_e2e, ms_e2e, world), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
