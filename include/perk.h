@@ -253,11 +253,14 @@ perk_status perk_step_dts(perk_ctx* ctx, double* d_U, const double* dts);
 perk_status perk_check(perk_ctx* ctx);
 
 /* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed
- * on the device (Eq. CFL_DG, Eq. TimestepConstraint).  Blocks; *dt receives it. */
+ * on the device (Eq. CFL_DG, Eq. TimestepConstraint).  Blocks; *dt receives it.
+ * NONFINITE (and *dt untouched) when some node has no admissible wave speed:
+ * rho <= 0, p <= 0 or a NaN/Inf entry. */
 perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double* dt);
 
 /* The step size of every ensemble member (host array dts[n_members]); for a
- * single mesh dts[0] equals perk_compute_dt's value.  Blocks. */
+ * single mesh dts[0] equals perk_compute_dt's value.  Blocks.  NONFINITE as
+ * for perk_compute_dt if any member has a node without an admissible state. */
 perk_status perk_compute_dt_members(perk_ctx* ctx, const double* d_U, double cfl, double* dts);
 
 /* Counters accumulated since creation (reporting, Sec. 6.4.1). */
@@ -406,9 +409,12 @@ perk_status perk_measure_fp64(double* fma_flops, double* div_per_s, double* log_
  * Scratch: a file-scope device array of 64 KiB + 8 B that every GPU which
  * loads the library holds until the process exits; n_elem may not exceed
  * PERK_NOALLOC_MAX_ELEM (else INVALID_ARG).  The first call on a device looks
- * the array's device address up (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the one array, so calls that
- * overlap on the GPU (other streams, other host threads) race; serialise them. */
+ * the array's device address up (cudaGetSymbolAddress) and keeps it for later
+ * calls on that device; make that first call before any stream capture.  The
+ * kept address does not survive cudaDeviceReset: after a reset of a device, do
+ * not call this entry point on it again in the same process.  Every call
+ * shares the one array, so calls that overlap on the GPU (other streams, other
+ * host threads) race; serialise them.  NONFINITE as for perk_compute_dt. */
 #define PERK_NOALLOC_MAX_ELEM 131072
 perk_status perk_compute_dt_noalloc(const double* d_U, const int32_t* d_level, int64_t n_elem, double length,
                                     double gamma, double cfl, void* stream, double* dt);

@@ -623,6 +623,7 @@ perk_status perk3d_create(const perk3d_problem* prob, perk3d_ctx** out) {
   perk3d_ctx* ctx = new perk3d_ctx();
   ctx->prob = *prob;
   ctx->nn = prob->N + 1;
+  perk::device_sm_count();   // cached before any graph capture
   if (!build_ops3(prob->N, prob->gamma, prob->surface_flux, ctx->ops)) {
     delete ctx;
     return fail(nullptr, PERK_E_INVALID_ARG, "singular mass matrix");

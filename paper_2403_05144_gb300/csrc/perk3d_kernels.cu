@@ -546,7 +546,9 @@ __global__ void k3_commit(int64_t nd, UpdateArgs ua, const double* __restrict__ 
 constexpr int DT3_THREADS = 256;
 
 // min over nodes of h_e / ((N+1) lambda), lambda = |v1| + |v2| + |v3| + 3c; positive doubles order
-// like their bit patterns, so the block minimum goes to *out by an integer atomicMin
+// like their bit patterns, so the block minimum goes to *out by an integer atomicMin.  A node
+// without an admissible state (rho <= 0, p <= 0, NaN or Inf) contributes the pattern 0 (+0.0),
+// which the host reports as such.
 template <int NN>
 __global__ void __launch_bounds__(DT3_THREADS) k3_dt(int64_t n_nodes, const double* __restrict__ U,
                                                       const int32_t* __restrict__ level, double length,
@@ -563,7 +565,8 @@ __global__ void __launch_bounds__(DT3_THREADS) k3_dt(int64_t n_nodes, const doub
     const double p = (gamma - 1.0) * (u[4 * NODES] - 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3));
     const double lam = fabs(v1) + fabs(v2) + fabs(v3) + 3.0 * sqrt(gamma * p * ir);
     const double h = ldexp(length, -level[e]);
-    best = fmin(best, h / (NN * lam));
+    const double r = h / (NN * lam);
+    best = (rho > 0.0 && p > 0.0 && r > 0.0 && r < INFINITY) ? fmin(best, r) : 0.0;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -758,7 +761,7 @@ cudaError_t launch_volume3(cudaStream_t st, YSource ys, const Ops3& ops, int64_t
 cudaError_t launch_commit3(cudaStream_t st, int64_t n_doubles, const UpdateArgs& ua, const double* Ks,
                            const double* dt, double* U) {
   if (n_doubles <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n_doubles + 255) / 256, 152 * 16);
+  const int64_t blocks = std::min<int64_t>((n_doubles + 255) / 256, (int64_t)perk::device_sm_count() * 16);
   k3_commit<<<(unsigned)blocks, 256, 0, st>>>(n_doubles, ua, Ks, dt, U);
   return cudaGetLastError();
 }
@@ -797,7 +800,7 @@ cudaError_t launch_dt3(cudaStream_t st, int nn, int64_t n_elem, const double* U,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || n_elem <= 0) return e;
   const int64_t n_nodes = n_elem * nodes3(nn);
-  const unsigned blocks = (unsigned)std::min<int64_t>((n_nodes + DT3_THREADS - 1) / DT3_THREADS, 152 * 8);
+  const unsigned blocks = (unsigned)std::min<int64_t>((n_nodes + DT3_THREADS - 1) / DT3_THREADS, (int64_t)perk::device_sm_count() * 8);
   unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
   if (nn == 3)
     k3_dt<3><<<blocks, DT3_THREADS, 0, st>>>(n_nodes, U, level, length, gamma, o);

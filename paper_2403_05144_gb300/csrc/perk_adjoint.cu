@@ -1133,8 +1133,8 @@ __global__ void k_adj_seed(int64_t n, double dt, double b1, double bp, double bs
 }  // namespace ad
 
 static unsigned ew_blocks(int64_t n) {
-  int64_t b = (n * ELEM + 255) / 256;
-  return (unsigned)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+  const int64_t b = (n * ELEM + 255) / 256, cap = (int64_t)device_sm_count() * 32;
+  return (unsigned)(b > cap ? cap : (b < 1 ? 1 : b));
 }
 
 cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const StageCoef* coef,

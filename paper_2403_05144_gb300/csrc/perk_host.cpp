@@ -848,6 +848,7 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   perk_ctx* ctx = new perk_ctx();
   ctx->prob = *prob;
   ctx->ops = build_ops(prob->gamma, prob->surface_flux, prob->shock_capturing, prob->alpha_max);
+  device_sm_count();   // cached before any graph capture
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
       ctx->d_logtab.ensure(2 * LOG_TABLE_SIZE) != cudaSuccess ||
@@ -1623,6 +1624,9 @@ perk_status perk_compute_dt_members(perk_ctx* ctx, const double* d_U, double cfl
   PERK_CUDA(ctx, cudaMemcpyAsync(m.data(), ctx->d_block_min.p, m.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                  ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < ctx->n_members; ++q)
+    if (!std::isfinite(m[q]) || !(m[q] > 0.0))
+      return fail(ctx, PERK_E_NONFINITE, "member %d: a node has no admissible wave speed (rho or p <= 0, or NaN)", q);
   for (int q = 0; q < ctx->n_members; ++q) dts[q] = cfl * m[q] / (double)NN;
   return PERK_OK;
 }
@@ -1651,6 +1655,8 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
   double m = 0.0;
   PERK_CUDA(ctx, cudaMemcpyAsync(&m, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (!std::isfinite(m) || !(m > 0.0))
+    return fail(ctx, PERK_E_NONFINITE, "a node has no admissible wave speed (rho or p <= 0, or NaN)");
   *dt = cfl * m / (double)NN;
   return PERK_OK;
 }

@@ -17,6 +17,11 @@ constexpr int NV = 4;             // conserved variables
 constexpr int ELEM = NV * NODES;  // doubles per element
 constexpr int MAX_S = 64;
 constexpr int MAX_R = 8;
+constexpr int DT_THREADS = 256;   // threads per block of the CFL step-size reduction
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount), looked up
+// once per device and cached; grid caps of the grid-stride kernels are multiples of it.
+int device_sm_count();
 
 // Reference-element operators, computed on the host once per context.
 struct Ops {

@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "perk.h"
 #include "perk_internal.h"
@@ -854,8 +855,10 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
 }
 
 // ---------------------------------------------------------------------------
-// CFL step size: min over elements of h_e / max_nodes(|v1| + |v2| + 2c).
-constexpr int DT_THREADS = 256;
+// CFL step size: min over elements of h_e / max_nodes(|v1| + |v2| + 2c).  A node without an
+// admissible state (rho <= 0, p <= 0, NaN or Inf) poisons the minimum with NaN, so that the host
+// reports it instead of a step size taken from the other nodes.
+__device__ __forceinline__ double nan_min(double a, double b) { return (a != a || b != b) ? NAN : fmin(a, b); }
 
 __global__ void __launch_bounds__(DT_THREADS) k_dt_partial(int64_t n_nodes, const double* __restrict__ U,
                                                             const int32_t* __restrict__ level, double length,
@@ -872,22 +875,23 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_partial(int64_t n_nodes, cons
     const double c = sqrt(gamma * p * ir);
     const double lam = fabs(v1) + fabs(v2) + 2.0 * c;
     const double h = ldexp(length, -level[e]);
-    best = fmin(best, h / lam);
+    const double r = h / lam;
+    best = (rho > 0.0 && p > 0.0 && r > 0.0 && r < INFINITY) ? nan_min(best, r) : NAN;
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  for (int o = 16; o > 0; o >>= 1) best = nan_min(best, __shfl_xor_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x < 32) {
     best = threadIdx.x < DT_THREADS / 32 ? s[threadIdx.x] : INFINITY;
-    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    for (int o = 16; o > 0; o >>= 1) best = nan_min(best, __shfl_xor_sync(0xffffffffu, best, o));
     if (threadIdx.x == 0) block_min[blockIdx.x] = best;
   }
 }
 
 __global__ void k_dt_final(int n, const double* block_min, double* out) {
   double best = INFINITY;
-  for (int q = threadIdx.x; q < n; q += 32) best = fmin(best, block_min[q]);
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  for (int q = threadIdx.x; q < n; q += 32) best = nan_min(best, block_min[q]);
+  for (int o = 16; o > 0; o >>= 1) best = nan_min(best, __shfl_xor_sync(0xffffffffu, best, o));
   if (threadIdx.x == 0) *out = best;
 }
 
@@ -1029,7 +1033,9 @@ cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int6
   return cudaGetLastError();
 }
 
-// per-member minimum of h_e / lambda_e: positive doubles order like their bit patterns
+// per-member minimum of h_e / lambda_e: positive doubles order like their bit patterns; a node
+// without an admissible state (rho <= 0, p <= 0, NaN or Inf) contributes the pattern 0 (+0.0),
+// which the host reports as such
 __global__ void __launch_bounds__(DT_THREADS) k_dt_members(int64_t n_nodes, const double* __restrict__ U,
                                                             const int32_t* __restrict__ level,
                                                             const int32_t* __restrict__ member, double length,
@@ -1043,7 +1049,8 @@ __global__ void __launch_bounds__(DT_THREADS) k_dt_members(int64_t n_nodes, cons
     const double p = (gamma - 1.0) * (u[3 * NODES] - 0.5 * rho * (v1 * v1 + v2 * v2));
     const double lam = fabs(v1) + fabs(v2) + 2.0 * sqrt(gamma * p * ir);
     const double r = ldexp(length, -level[e]) / lam;
-    if (r > 0.0) atomicMin(out + member[e], (unsigned long long)__double_as_longlong(r));
+    const bool ok = rho > 0.0 && p > 0.0 && r > 0.0 && r < INFINITY;
+    atomicMin(out + member[e], ok ? (unsigned long long)__double_as_longlong(r) : 0ull);
   }
 }
 
@@ -1055,7 +1062,7 @@ cudaError_t launch_dt_members(cudaStream_t st, int64_t n_elem, const double* U, 
                               const int32_t* member, int n_members, double length, double gamma, double* out) {
   k_fill<<<1, 256, 0, st>>>(out, n_members, INFINITY);
   const int64_t nodes = n_elem * NODES;
-  const unsigned blocks = (unsigned)std::min<int64_t>(152 * 8, (nodes + DT_THREADS - 1) / DT_THREADS);
+  const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)device_sm_count() * 8, (nodes + DT_THREADS - 1) / DT_THREADS);
   if (blocks > 0)
     k_dt_members<<<blocks, DT_THREADS, 0, st>>>(nodes, U, level, member, length, gamma,
                                                 reinterpret_cast<unsigned long long*>(out));
@@ -1128,6 +1135,21 @@ cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t
   return cudaGetLastError();
 }
 
+int device_sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 // Diagnostics: the volume kernel's logarithm and reciprocal on n inputs.
 __global__ void k_selftest_math(int64_t n, const double* __restrict__ x, double* __restrict__ out,
                                 const double* __restrict__ log_table) {
@@ -1148,7 +1170,8 @@ cudaError_t launch_commit(cudaStream_t st, int64_t n_elem, const UpdateArgs& ua,
   const int64_t n2 = n_elem * ELEM / 2;
   if (n2 == 0) return cudaSuccess;
   int64_t blocks = (n2 + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const int64_t cap = (int64_t)device_sm_count() * 16;
+  if (blocks > cap) blocks = cap;
   k_commit<<<(unsigned)blocks, 256, 0, st>>>(n2, ua, reinterpret_cast<const double2*>(Ks), dt,
                                              reinterpret_cast<double2*>(U));
   return cudaGetLastError();

@@ -10,6 +10,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "perk.h"
@@ -18,8 +19,14 @@
 namespace {
 
 // Partial minima of the reduction (one per block) plus the final minimum.
-// 8,193 doubles (64 KiB + 8 B) on every device that loads the library.
-constexpr int kMaxBlocks = PERK_NOALLOC_MAX_ELEM / 16;  // 256-thread blocks over 16 nodes per element
+// 8,193 doubles (64 KiB + 8 B) on every device that loads the library: enough for one block per
+// DT_THREADS nodes of PERK_NOALLOC_MAX_ELEM cells, although the grid-stride reduction is launched
+// with at most kLaunchBlocks blocks.
+constexpr int kMaxBlocks = PERK_NOALLOC_MAX_ELEM / 16;
+constexpr int kLaunchBlocks = 1024;
+static_assert((int64_t)kMaxBlocks * perk::DT_THREADS >= (int64_t)PERK_NOALLOC_MAX_ELEM * perk::NODES,
+              "scratch too small for one block per DT_THREADS nodes");
+static_assert(kLaunchBlocks <= kMaxBlocks, "launch grid larger than the scratch");
 static __device__ __align__(256) double g_dt_scratch[kMaxBlocks + 1];
 
 constexpr int kMaxDevices = 64;
@@ -58,7 +65,8 @@ extern "C" perk_status perk_compute_dt_noalloc(const double* d_U, const int32_t*
   if (e != cudaSuccess)
     return perk::set_context_free_error(PERK_E_CUDA, "perk_compute_dt_noalloc: cudaGetSymbolAddress failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int n_blocks = (int)((n_elem * perk::NODES + 255) / 256);
+  const int64_t need = (n_elem * perk::NODES + perk::DT_THREADS - 1) / perk::DT_THREADS;
+  const int n_blocks = (int)(need < kLaunchBlocks ? need : kLaunchBlocks);   // the reduction is grid-stride
   e = perk::launch_dt(st, n_elem, d_U, d_level, length, gamma, scratch, n_blocks, scratch + kMaxBlocks);
   if (e != cudaSuccess) return perk::set_context_free_error(PERK_E_CUDA, "perk_compute_dt_noalloc: launch failed");
   double m = 0.0;
@@ -66,6 +74,9 @@ extern "C" perk_status perk_compute_dt_noalloc(const double* d_U, const int32_t*
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess)
     return perk::set_context_free_error(PERK_E_CUDA, "perk_compute_dt_noalloc: reading the result failed");
+  if (!std::isfinite(m) || !(m > 0.0))
+    return perk::set_context_free_error(PERK_E_NONFINITE,
+                                        "perk_compute_dt_noalloc: a node has no admissible wave speed");
   *dt = cfl * m / (double)perk::NN;
   return PERK_OK;
 }

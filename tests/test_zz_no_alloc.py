@@ -60,3 +60,20 @@ def test_noalloc_dt_rejects_sizes_beyond_its_scratch():
                                      0.7, None, C.byref(out))
     assert st == 1
     assert "PERK_NOALLOC_MAX_ELEM" in lib.perk_last_error(None).decode()
+
+
+def test_noalloc_dt_reports_inadmissible_states():
+    # a node with negative density poisons the reduction: NONFINITE, not a step size from the rest
+    from paper_2403_05144_gb300 import _lib
+    lib = _lib.load()
+    x, _ = lgl_nodes_weights(3)
+    cells = kh_band_cells(4, 6, 0.05)
+    U0 = nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, x)
+    U0[17, 0, 2, 1] = -0.25
+    U = torch.from_numpy(U0).cuda()
+    lev = torch.tensor([c[0] for c in cells], dtype=torch.int32, device="cuda")
+    out = C.c_double(-1.0)
+    st = lib.perk_compute_dt_noalloc(C.c_void_p(U.data_ptr()), C.c_void_p(lev.data_ptr()), len(cells), 2.0, 1.4,
+                                     0.7, None, C.byref(out))
+    assert st == 3
+    assert out.value == -1.0
