@@ -14,6 +14,7 @@ from .meshes import (  # noqa: F401
     morton_sort,
     vortex_two_level_cells,
     kh_band_cells,
+    nested_band_cells,
     three_level_band_cells,
 )
 from .initial import (  # noqa: F401

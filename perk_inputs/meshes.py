@@ -90,6 +90,21 @@ def kh_band_cells(level_min: int = 4, level_max: int = 7, width: float = 0.06) -
     return cells
 
 
+def nested_band_cells(level_min: int = 2, level_max: int = 5, center: float = 0.75) -> List[Cell]:
+    """Mesh refined towards one horizontal line ``y = center`` (domain units, [0, 1)): at every
+    level the cells whose centres lie within 1.5 of their own widths of the line are refined,
+    so each level forms a band two cells high around the next finer one (2:1 balanced).  With
+    the defaults: four levels 2..5, 184 cells, the upper shear line of the Kelvin-Helmholtz
+    state on [-1, 1]^2."""
+    cells = uniform_cells(level_min)
+    for _ in range(level_max - level_min):
+        def near(l: int, ix: int, iy: int) -> bool:
+            d = abs((iy + 0.5) / (1 << l) - center)
+            return min(d, 1.0 - d) < 1.5 / (1 << l)
+        cells = refine_cells(cells, near)
+    return cells
+
+
 def three_level_band_cells(level_min: int = 5, level_max: int = 7, width: float = 0.1) -> List[Cell]:
     """Frozen three-level graded mesh around the shear lines (adjoint window)."""
     return kh_band_cells(level_min, level_max, width)

@@ -11,8 +11,8 @@ torch = pytest.importorskip("torch")
 from oracle.dgsem import DGSEM
 from oracle.perk import element_methods, max_wave_speed_dt, perk2_family, prkm_step
 from oracle.treemesh import TreeMesh
-from perk_inputs import (isentropic_vortex, kelvin_helmholtz, kh_band_cells, nodal_state, uniform_cells,
-                         vortex_two_level_cells)
+from perk_inputs import (isentropic_vortex, kelvin_helmholtz, kh_band_cells, nested_band_cells, nodal_state,
+                         uniform_cells, vortex_two_level_cells)
 from tests.gpu_common import X3, discontinuous_state, rel_err_per_var, solver_for
 
 pytestmark = pytest.mark.gpu
@@ -115,6 +115,35 @@ def test_twenty_steps_vortex448():
     assert c["steps"] == 20 and c["rejected_steps_checked"] == 0
 
 
+def test_hundred_steps_vortex448():
+    # the two-level vortex workload itself (448 cells, 32 mortars, P-ERK2 {4, 8}, HLL) for 100
+    # steps against the oracle's dense partitioned step: 1e-10 relative after 100 steps
+    cells = vortex_two_level_cells()
+    U0 = nodal_state(isentropic_vortex, cells, -10.0, 20.0, X3)
+    dt = max_wave_speed_dt(U0, TreeMesh(cells, -10.0, 20.0).h, 3, 0.5 * 7)
+    got, s = gpu_steps(cells, VORTEX, [4, 8], U0, dt, 100)
+    want = oracle_steps(cells, VORTEX, [4, 8], U0, dt, 100)
+    assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 1e-10
+    assert s.counters()["steps"] == 100
+
+
+def test_hundred_steps_kh_four_levels():
+    # Kelvin-Helmholtz state on a four-level mesh (levels 2-5, 184 cells) so that every member of
+    # the P-ERK2 {4, 6, 10, 16} family (HLLC) owns cells: 100 steps at CFL 0.7 in the bench's
+    # launch configuration (graph replay) against the oracle's dense step
+    cells = nested_band_cells(2, 5)
+    assert sorted({c[0] for c in cells}) == [2, 3, 4, 5]
+    E = [4, 6, 10, 16]
+    U0 = nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)
+    dt = max_wave_speed_dt(U0, TreeMesh(cells, -1.0, 2.0).h, 3, 0.7)
+    got, s = gpu_steps(cells, KH, E, U0, dt, 100, "hllc")
+    info = s.info()
+    assert info["active_elements"][0] == len(cells) and info["active_elements"][15] == len(cells)
+    assert min(info["active_elements"][:16]) == sum(1 for c in cells if c[0] == 5)
+    want = oracle_steps(cells, KH, E, U0, dt, 100, "hllc")
+    assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 1e-10
+
+
 def test_hundred_steps_small_mesh():
     cells = vortex_two_level_cells(3, 2, 6)
     U0 = nodal_state(isentropic_vortex, cells, -10.0, 20.0, X3)
@@ -168,6 +197,32 @@ def test_dt_matches_oracle():
     s = solver_for(cells, KH["x0"], KH["L"], "hllc")
     want = max_wave_speed_dt(U0, TreeMesh(cells, -1.0, 2.0).h, 3, 0.7)
     assert s.compute_dt(cuda(U0), 0.7) == pytest.approx(want, rel=1e-14)
+
+
+@pytest.mark.parametrize("bad", ["negative_density", "negative_pressure", "nan"])
+def test_dt_refuses_inadmissible_states(bad):
+    # the oracle's step size is NaN when a node has rho <= 0, p <= 0 or a NaN entry; the library
+    # reports NONFINITE instead of a step size taken from the other nodes
+    from paper_2403_05144_gb300 import PerkError
+    cells = vortex_two_level_cells(3, 2, 6)
+    U0 = nodal_state(isentropic_vortex, cells, -10.0, 20.0, X3)
+    if bad == "negative_density":
+        U0[5, 0, 1, 2] = -0.5
+    elif bad == "negative_pressure":
+        U0[7, 3, 3, 0] = -1.0
+    else:
+        U0[9, 2, 0, 3] = np.nan
+    assert np.isnan(max_wave_speed_dt(U0, TreeMesh(cells, -10.0, 20.0).h, 3, 0.5))
+    s = solver_for(cells, VORTEX["x0"], VORTEX["L"], "hll")
+    with pytest.raises(PerkError) as ei:
+        s.compute_dt(cuda(U0), 0.5)
+    assert ei.value.status == 3
+    with pytest.raises(PerkError) as ei:
+        s.compute_dt_members(cuda(U0), 0.5)
+    assert ei.value.status == 3
+    good = nodal_state(isentropic_vortex, cells, -10.0, 20.0, X3)
+    assert s.compute_dt(cuda(good), 0.5) == pytest.approx(
+        max_wave_speed_dt(good, TreeMesh(cells, -10.0, 20.0).h, 3, 0.5), rel=1e-14)
 
 
 def test_partition_counts_match_oracle():
