@@ -269,8 +269,33 @@ typedef struct {
   int64_t element_stage_evaluations; /* sum over steps and stages of active elements */
   int64_t dof_stage_updates;         /* the same in nodes */
   int64_t rejected_steps_checked;    /* steps found rejected by perk_check */
+  int64_t device_allocations;        /* cudaMalloc calls the context made since its creation */
 } perk_counters;
 perk_status perk_get_counters(const perk_ctx* ctx, perk_counters* out);
+
+/* Caller-owned workspace (the statement of the problem in Sec. 2 leaves memory to the caller;
+ * the library's own device memory can be replaced by one block the caller allocates, e.g. a
+ * torch tensor, bound once).  The block holds every device buffer of the mesh (levels, members,
+ * interface and mortar records), of the level partition (method ids, sorted lists, per-stage
+ * counts), of the step (K_1 and the two alternating stage buffers, the face fluxes, the
+ * Navier-Stokes gradient and viscous-flux buffers, all S stages for a stage pattern), of the step
+ * size and of an AMR cycle (indicator values, transfer records), laid out for meshes of up to
+ * a given number of cells (at most 2 interfaces and 2 mortars per cell).
+ * perk_workspace_bytes: *bytes receives the size of that layout for meshes of up to n_cells cells
+ * (0: the current mesh's count) with the context's present equations and tableau; query it after
+ * perk_set_tableau (a stage pattern adds S x n_cells x 512 B).
+ * perk_bind_workspace: d_ws is device memory of `bytes` bytes, 256-byte aligned, owned by the
+ * caller, which must keep it alive and unused by others until the context is destroyed or
+ * another block is bound.  The call synchronises the context's stream, moves the buffers'
+ * contents into the block, frees the library's own copies and drops the captured step graph.
+ * After it, mesh upload, partition, step, step size, AMR and tuning make no device allocation
+ * (perk_counters.device_allocations stays put); a mesh with more cells than the block serves is
+ * refused with OOM (before any work of the call).  d_ws == NULL with bytes == 0 unbinds: the
+ * buffers move back to the library's own allocations.  INVALID_ARG for a block smaller than the
+ * current mesh needs or misaligned.  The derivative entry points (JVP, VJP, step adjoint) keep
+ * allocating their own work arrays. */
+perk_status perk_workspace_bytes(const perk_ctx* ctx, int64_t n_cells, size_t* bytes);
+perk_status perk_bind_workspace(perk_ctx* ctx, void* d_ws, size_t bytes);
 
 /* Derivatives of the partitioned right-hand side (the Jacobian apply that the
  * spectrum estimation of Sec. 4.1 iterates with, and the discrete adjoint).

@@ -269,6 +269,26 @@ class PerkSolver:
                 "active_interfaces": list(inf.active_interfaces[:S]), "active_mortars": list(inf.active_mortars[:S]),
                 "index_bytes": inf.index_bytes}
 
+    def workspace_bytes(self, n_cells: int = 0) -> int:
+        """Bytes of a caller-owned workspace serving meshes of up to n_cells cells (0: the current mesh)."""
+        out = C.c_size_t()
+        _check(self.lib, self.ctx, self.lib.perk_workspace_bytes(self.ctx, C.c_int64(n_cells), C.byref(out)))
+        return out.value
+
+    def bind_workspace(self, ws):
+        """Binds a caller-owned device block (a CUDA tensor of at least workspace_bytes() bytes, 256-byte
+        aligned) as the context's device memory; None returns to the library's own allocations.  The
+        tensor is kept referenced while bound."""
+        if ws is None:
+            self._call(self.lib.perk_bind_workspace, None, C.c_size_t(0))
+            self._ws = None
+            return
+        if not ws.is_cuda or not ws.is_contiguous():
+            raise ValueError("the workspace must be a contiguous CUDA tensor")
+        self._call(self.lib.perk_bind_workspace, C.c_void_p(ws.data_ptr()),
+                   C.c_size_t(ws.numel() * ws.element_size()))
+        self._ws = ws
+
     def counters(self) -> dict:
         c = _lib.PerkCounters()
         _check(self.lib, self.ctx, self.lib.perk_get_counters(self.ctx, C.byref(c)))

@@ -33,7 +33,7 @@ class PerkMeshInfo(C.Structure):
 
 class PerkCounters(C.Structure):
     _fields_ = [("steps", C.c_int64), ("element_stage_evaluations", C.c_int64), ("dof_stage_updates", C.c_int64),
-                ("rejected_steps_checked", C.c_int64)]
+                ("rejected_steps_checked", C.c_int64), ("device_allocations", C.c_int64)]
 
 
 class PerkAmrParams(C.Structure):
@@ -101,6 +101,8 @@ SIGNATURES = [
     ("perk_selftest_math", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("perk_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
     ("perk_measure_fp64", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk_workspace_bytes", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_size_t)]),
+    ("perk_bind_workspace", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("perk_compute_dt_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double,
                                           C.c_void_p, C.POINTER(C.c_double)]),
 ]

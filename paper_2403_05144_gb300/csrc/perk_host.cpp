@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -225,24 +226,34 @@ Ops build_ops(double gamma, int surface_flux, int shock = PERK_SHOCK_OFF, double
 }
 
 
+// A device buffer of the context: allocated by the library (cudaMalloc, counted in *allocs), or
+// carved from a caller-bound workspace (ext: never freed here, and never grown: a request beyond
+// the carved capacity fails with cudaErrorMemoryAllocation).
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   size_t cap = 0;
+  bool ext = false;
+  int64_t* allocs = nullptr;
   cudaError_t ensure(size_t n) {
     if (n <= cap && p) return cudaSuccess;
+    if (ext) return cudaErrorMemoryAllocation;
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
     const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
     cudaError_t e = cudaMalloc(&p, bytes);
-    if (e == cudaSuccess) cap = std::max<size_t>(n, 1);
+    if (e == cudaSuccess) {
+      cap = std::max<size_t>(n, 1);
+      if (allocs) *allocs += 1;
+    }
     return e;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p && !ext) cudaFree(p);
     p = nullptr;
     cap = 0;
+    ext = false;
   }
 };
 
@@ -326,6 +337,11 @@ struct perk_ctx {
   bool graph_valid = false;
   double* graph_U = nullptr;
 
+  // caller-bound workspace (perk_bind_workspace): base, size and the cells its layout serves
+  char* ws_base = nullptr;
+  size_t ws_bytes = 0;
+  int64_t ws_cells = 0;
+
   perk_counters counters{};
 };
 
@@ -362,6 +378,50 @@ void destroy_graph(perk_ctx* ctx) {
   ctx->graph = nullptr;
   ctx->graph_valid = false;
   ctx->graph_U = nullptr;
+}
+
+// ---- device buffers and the caller-bound workspace ----
+
+// Every device buffer of the context.
+template <class F>
+void for_each_buffer(perk_ctx* c, F&& f) {
+  f(c->d_level); f(c->d_member); f(c->d_member_lmax); f(c->d_method); f(c->d_elem_sorted); f(c->d_E);
+  f(c->d_minmax); f(c->d_if_raw); f(c->d_mort_raw); f(c->d_if_sorted); f(c->d_mort_sorted); f(c->d_counts);
+  f(c->d_surf); f(c->d_K1); f(c->d_Ka); f(c->d_Kb); f(c->d_dt); f(c->d_block_min); f(c->d_dt_out); f(c->d_coef);
+  f(c->d_flag); f(c->d_logtab); f(c->d_map); f(c->d_eta); f(c->d_surf_d); f(c->d_Kall); f(c->d_Kpat); f(c->d_g);
+  f(c->d_lamK1); f(c->d_lamKa); f(c->d_lamKb); f(c->d_wsurf); f(c->d_q); f(c->d_vsurf);
+}
+
+// The buffers a caller-bound workspace holds, in layout order, with their sizes (elements of
+// their type) for meshes of up to `cells` cells: everything the mesh, the partition, the
+// step's stages, the step size and an AMR cycle use.  A mesh has at most 2 interfaces and 2
+// mortars per cell (four faces per cell; an interface takes two of them, a mortar three).
+// The derivative entry points keep allocating their own work arrays.
+template <class F>
+void for_each_workspace_buffer(perk_ctx* c, int64_t cells, F&& f) {
+  const size_t n = (size_t)std::max<int64_t>(cells, 1);
+  f(c->d_surf, n * ELEM); f(c->d_K1, n * ELEM); f(c->d_Ka, n * ELEM); f(c->d_Kb, n * ELEM);
+  if (c->pattern_mode) f(c->d_Kpat, n * ELEM * (size_t)c->S);
+  if (c->viscous()) {
+    f(c->d_wsurf, n * 64); f(c->d_q, n * 128); f(c->d_vsurf, n * 64);
+  }
+  f(c->d_eta, n); f(c->d_dt, n); f(c->d_block_min, std::max<size_t>(n, 1024)); f(c->d_dt_out, (size_t)1);
+  f(c->d_coef, (size_t)MAX_S * MAX_R); f(c->d_counts, (size_t)6 * MAX_S); f(c->d_logtab, (size_t)2 * LOG_TABLE_SIZE);
+  f(c->d_if_raw, 2 * n); f(c->d_if_sorted, 2 * n); f(c->d_mort_raw, 2 * n); f(c->d_mort_sorted, 2 * n);
+  f(c->d_level, n); f(c->d_method, n); f(c->d_elem_sorted, n); f(c->d_member, n); f(c->d_member_lmax, n);
+  f(c->d_map, 5 * n); f(c->d_E, (size_t)MAX_S); f(c->d_minmax, (size_t)2); f(c->d_flag, (size_t)1);
+}
+
+constexpr size_t WS_ALIGN = 256;
+inline size_t ws_align(size_t off) { return (off + WS_ALIGN - 1) / WS_ALIGN * WS_ALIGN; }
+
+// bytes of the workspace layout for meshes of up to `cells` cells
+size_t workspace_layout_bytes(perk_ctx* c, int64_t cells) {
+  size_t off = 0;
+  for_each_workspace_buffer(c, cells, [&](auto& b, size_t count) {
+    off = ws_align(off) + count * sizeof(*b.p);
+  });
+  return off;
 }
 
 struct CellKey {
@@ -618,6 +678,10 @@ struct LaunchTimer {
 
 perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const int32_t* member, double x0,
                      double length) {
+  if (ctx->ws_base && n_cells > ctx->ws_cells)
+    return fail(ctx, PERK_E_OOM,
+                "the bound workspace serves meshes of up to %lld cells, this one has %lld: bind a larger one "
+                "(perk_workspace_bytes)", (long long)ctx->ws_cells, (long long)n_cells);
   std::vector<int4> ifs, morts;
   ifs.reserve((size_t)n_cells * 2);
   perk_status s = build_connectivity(ctx, n_cells, cells, member, ifs, morts);
@@ -848,6 +912,7 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   perk_ctx* ctx = new perk_ctx();
   ctx->prob = *prob;
   ctx->ops = build_ops(prob->gamma, prob->surface_flux, prob->shock_capturing, prob->alpha_max);
+  for_each_buffer(ctx, [ctx](auto& b) { b.allocs = &ctx->counters.device_allocations; });
   device_sm_count();   // cached before any graph capture
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
@@ -877,40 +942,7 @@ void perk_destroy(perk_ctx* ctx) {
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-  ctx->d_level.release();
-  ctx->d_member.release();
-  ctx->d_member_lmax.release();
-  ctx->d_method.release();
-  ctx->d_elem_sorted.release();
-  ctx->d_E.release();
-  ctx->d_minmax.release();
-  ctx->d_if_raw.release();
-  ctx->d_mort_raw.release();
-  ctx->d_if_sorted.release();
-  ctx->d_mort_sorted.release();
-  ctx->d_counts.release();
-  ctx->d_surf.release();
-  ctx->d_K1.release();
-  ctx->d_Ka.release();
-  ctx->d_Kb.release();
-  ctx->d_dt.release();
-  ctx->d_block_min.release();
-  ctx->d_dt_out.release();
-  ctx->d_coef.release();
-  ctx->d_flag.release();
-  ctx->d_logtab.release();
-  ctx->d_map.release();
-  ctx->d_eta.release();
-  ctx->d_surf_d.release();
-  ctx->d_Kall.release();
-  ctx->d_Kpat.release();
-  ctx->d_g.release();
-  ctx->d_lamK1.release();
-  ctx->d_lamKa.release();
-  ctx->d_lamKb.release();
-  ctx->d_wsurf.release();
-  ctx->d_q.release();
-  ctx->d_vsurf.release();
+  for_each_buffer(ctx, [](auto& b) { b.release(); });
   delete ctx;
 }
 
@@ -1502,7 +1534,13 @@ perk_status perk_rhs_active(perk_ctx* ctx, int stage, const double* d_Y, double*
 
 // device memory a step needs beyond the mesh buffers (allocated outside any graph capture)
 static perk_status prepare_step(perk_ctx* ctx) {
-  if (ctx->pattern_mode) PERK_CUDA(ctx, ctx->d_Kpat.ensure((size_t)ctx->n_elem * ELEM * ctx->S));
+  if (ctx->pattern_mode) {
+    if (ctx->ws_base && (!ctx->d_Kpat.ext || ctx->d_Kpat.cap < (size_t)ctx->n_elem * ELEM * ctx->S))
+      return fail(ctx, PERK_E_OOM,
+                  "a stage pattern keeps all S stages, which the bound workspace does not hold: query "
+                  "perk_workspace_bytes after setting the tableau and bind again");
+    PERK_CUDA(ctx, ctx->d_Kpat.ensure((size_t)ctx->n_elem * ELEM * ctx->S));
+  }
   return PERK_OK;
 }
 
@@ -1876,8 +1914,8 @@ perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elem
   if (!ctx->has_mesh || !ctx->partitioned) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_U) return fail(ctx, PERK_E_INVALID_ARG, "null U");
   const size_t nd = (size_t)ctx->n_elem * ELEM;
-  PERK_CUDA(ctx, ctx->d_g.ensure(nd));   // scratch output (the adjoint's work array)
-  DevBuf<double>& K = ctx->d_g;
+  PERK_CUDA(ctx, ctx->d_Ka.ensure(nd));   // scratch output: a stage buffer, free between steps
+  DevBuf<double>& K = ctx->d_Ka;
   StageArgs sa{};
   sa.Y = d_U;
   cudaStream_t st = ctx->stream;
@@ -2059,6 +2097,10 @@ perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Une
     ctx->plan_member.clear();
     return PERK_OK;
   }
+  if (ctx->ws_base && m > ctx->ws_cells)
+    return fail(ctx, PERK_E_OOM,
+                "the adapted mesh has %lld cells, the bound workspace serves up to %lld: bind a larger one "
+                "(perk_workspace_bytes) and commit again", (long long)m, (long long)ctx->ws_cells);
   PERK_CUDA(ctx, ctx->d_map.ensure((size_t)5 * m));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_map.p, ctx->plan_map.data(), ctx->plan_map.size() * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, ctx->stream));
@@ -2100,6 +2142,89 @@ perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap) {
   if (!ctx->has_mesh) return PERK_E_NOT_READY;
   if (cap < ctx->n_elem) return PERK_E_INVALID_ARG;
   std::copy(ctx->h_cells.begin(), ctx->h_cells.end(), cells);
+  return PERK_OK;
+}
+
+perk_status perk_workspace_bytes(const perk_ctx* ctx, int64_t n_cells, size_t* bytes) {
+  if (!ctx || !bytes) return PERK_E_INVALID_ARG;
+  perk_ctx* c = const_cast<perk_ctx*>(ctx);   // the layout walk reads the buffers' types only
+  if (n_cells < 0 || n_cells > ((int64_t)1 << 30)) return fail(c, PERK_E_INVALID_ARG, "bad cell count");
+  if (n_cells == 0) n_cells = std::max<int64_t>(ctx->n_elem, 1);
+  *bytes = workspace_layout_bytes(c, n_cells);
+  return PERK_OK;
+}
+
+perk_status perk_bind_workspace(perk_ctx* ctx, void* d_ws, size_t bytes) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  const bool unbind = d_ws == nullptr && bytes == 0;
+  if (!unbind && (!d_ws || ((uintptr_t)d_ws % WS_ALIGN) != 0))
+    return fail(ctx, PERK_E_INVALID_ARG, "the workspace must be device memory aligned to %d bytes", (int)WS_ALIGN);
+  const int64_t need = std::max<int64_t>(ctx->n_elem, 1);
+  int64_t cells = need;
+  if (!unbind) {
+    const size_t need_bytes = workspace_layout_bytes(ctx, need);
+    if (bytes < need_bytes)
+      return fail(ctx, PERK_E_INVALID_ARG, "workspace of %zu bytes; the current mesh needs %zu", bytes, need_bytes);
+    // the largest mesh the block serves (the layout grows with the cell count)
+    int64_t lo = need, hi = (int64_t)1 << 30;
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo + 1) / 2;
+      if (workspace_layout_bytes(ctx, mid) <= bytes)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    cells = lo;
+  }
+  // move every covered buffer's contents to its new place (the workspace, or fresh allocations),
+  // then let go of the old memory
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  struct Old {
+    void* p;
+    bool ext;
+  };
+  std::vector<Old> old;
+  std::vector<const void*> moved;
+  cudaError_t err = cudaSuccess;
+  size_t off = 0;
+  for_each_workspace_buffer(ctx, cells, [&](auto& b, size_t count) {
+    moved.push_back(&b);
+    using T = std::remove_reference_t<decltype(*b.p)>;
+    if (err != cudaSuccess) return;
+    T* np = nullptr;
+    if (unbind) {
+      err = cudaMalloc(&np, count * sizeof(T));
+      if (err != cudaSuccess) return;
+      ctx->counters.device_allocations += 1;
+    } else {
+      off = ws_align(off);
+      np = reinterpret_cast<T*>(static_cast<char*>(d_ws) + off);
+      off += count * sizeof(T);
+    }
+    if (b.p && b.cap) err = cudaMemcpyAsync(np, b.p, std::min(b.cap, count) * sizeof(T), cudaMemcpyDeviceToDevice,
+                                            ctx->stream);
+    old.push_back({b.p, b.ext});
+    b.p = np;
+    b.cap = count;
+    b.ext = !unbind;
+  });
+  const cudaError_t sync = cudaStreamSynchronize(ctx->stream);
+  for (const Old& o : old)
+    if (o.p && !o.ext) cudaFree(o.p);
+  // buffers of another mode left in a previous block (scratch only): allocated afresh when needed
+  for_each_buffer(ctx, [&](auto& b) {
+    if (b.ext && std::find(moved.begin(), moved.end(), (const void*)&b) == moved.end()) {
+      b.p = nullptr;
+      b.cap = 0;
+      b.ext = false;
+    }
+  });
+  PERK_CUDA(ctx, err);
+  PERK_CUDA(ctx, sync);
+  ctx->ws_base = unbind ? nullptr : static_cast<char*>(d_ws);
+  ctx->ws_bytes = unbind ? 0 : bytes;
+  ctx->ws_cells = unbind ? 0 : cells;
+  destroy_graph(ctx);   // the step's buffers moved
   return PERK_OK;
 }
 
