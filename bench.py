@@ -355,6 +355,66 @@ def equal_error_kh(torch, t_end: float = 0.5) -> dict:
     return out
 
 
+def state_l1(torch, solver, U, ref: np.ndarray, L: float, variables=(0,)) -> float:
+    """(1/|Omega|) sum over the given conserved variables of ||U_v - ref_v||_L1 (LGL quadrature)."""
+    from paper_2403_05144_gb300 import reference_nodes
+    _, w = reference_nodes(3)
+    h = L / 2.0 ** solver.cells[:, 0]
+    e = np.abs(U.cpu().numpy()[:, list(variables)] - ref[:, list(variables)])
+    return float(np.sum((0.5 * h) ** 2 * np.einsum("evji,j,i->e", e, w, w))) / (L * L)
+
+
+def equal_error_cfl(torch, wl: dict, t_window: float, variables=(0,), cfl0: float | None = None) -> dict:
+    """Step sizes at equal temporal error (the comparison of Sec. 5 at matched accuracy).
+
+    On the frozen initially adapted mesh of the workload, from its initial state over
+    [0, t_window]: the error of a run at CFL c is measured against the full-RK method (the
+    standalone largest member, every element every stage) at a quarter of the step of CFL cfl0.
+    The target is the full-RK error at cfl0; the P-ERK family's CFL for that error is found from
+    its errors at cfl0 and cfl0/2 (the measured order p: c* = cfl0 (target / e(cfl0))^(1/p)),
+    refined once by the local slope, and its error there is measured."""
+    cfl0 = wl["cfl"] if cfl0 is None else cfl0
+    base = Run(torch, wl, wl["E"])
+    cells, U0 = base.solver.cells.copy(), base.U.clone()
+    frozen = dict(wl, amr=None, cells=cells, init_cycles=0)
+    S = max(wl["E"])
+
+    def run_at(E, cfl, div=1):
+        run = Run(torch, frozen, E)
+        run.U = U0.clone()
+        dt = run.solver.compute_dt(U0, cfl) / div
+        n = math.ceil(t_window / dt)
+        run.dt = t_window / n
+        for _ in range(n):
+            run.step()
+        run.solver.check()
+        return run, n
+
+    ref_run, _ = run_at([S], cfl0, 4)
+    ref = ref_run.U.cpu().numpy()
+
+    def err(E, cfl):
+        run, n = run_at(E, cfl)
+        return state_l1(torch, run.solver, run.U, ref, wl["L"], variables), n
+
+    e_full, n_full = err([S], cfl0)
+    e0, n0 = err(wl["E"], cfl0)
+    e1, _ = err(wl["E"], 0.5 * cfl0)
+    p = math.log(e0 / e1) / math.log(2.0)
+    c1 = cfl0 * (e_full / e0) ** (1.0 / p)
+    ec1, _ = err(wl["E"], c1)
+    p_loc = math.log(e0 / ec1) / math.log(cfl0 / c1) if abs(c1 - cfl0) > 1e-3 * cfl0 else p
+    c2 = c1 * (e_full / ec1) ** (1.0 / p_loc)
+    ec2, n2 = err(wl["E"], c2)
+    return {"window": [0.0, t_window], "mesh": f"{wl['name']}: initially adapted, frozen, {len(cells)} cells",
+            "error": "L1 of conserved variables %s against full-RK (S=%d) at a quarter of the CFL-%g step"
+                     % (list(variables), S, cfl0),
+            "full_rk": {"cfl": cfl0, "error": e_full, "steps": n_full},
+            "perk_same_cfl": {"cfl": cfl0, "error": e0, "steps": n0, "ratio_to_full_rk": e0 / e_full},
+            "perk_half_cfl_error": e1, "perk_measured_order": p,
+            "perk_equal_error": {"cfl": c2, "error": ec2, "steps": n2, "ratio_to_full_rk": ec2 / e_full}}
+
+
 def oracle_problem(wl: dict, cells):
     """The oracle's mesh, P-ERK family, member of each cell and RHS for a workload."""
     from oracle.br1 import NavierStokesDGSEM
@@ -548,12 +608,32 @@ def run_perk(args) -> None:
             tend[k]["sim_time_per_wall_s"] = tend[k]["t"] / tend[k]["wall_s"]
     tend["t_end"] = wl["t_end"]
     if tend["perk"]["status"] == tend["full_rk"]["status"] == "reached t_end":
-        tend["wall_ratio_full_over_perk"] = tend["full_rk"]["wall_s"] / tend["perk"]["wall_s"]
+        # both at the workload's CFL (the same dt rule), not at equal error: see t_end.equal_error
+        tend["wall_ratio_full_over_perk_same_cfl"] = tend["full_rk"]["wall_s"] / tend["perk"]["wall_s"]
     equal_error = None
     if args.workload in ("kh", "vortex"):
         equal_error = {"vortex": equal_error_vortex(torch)}
     if args.workload == "kh":
         equal_error["kelvin_helmholtz"] = equal_error_kh(torch)
+    if args.workload in ("kh", "shear"):
+        # both methods to t_end at equal temporal error: the family at the CFL where its error on the
+        # frozen window equals the full-RK error at the workload's CFL (AMR interval scaled with the
+        # step, so that the mesh adapts at about the same physical times)
+        ee = equal_error_cfl(torch, wl, 0.5 if args.workload == "kh" else 0.1,
+                             variables=(0,) if args.workload == "kh" else (0, 1, 2, 3))
+        c_eq = ee["perk_equal_error"]["cfl"]
+        wl_eq = dict(wl, cfl=c_eq, n_amr=max(1, int(round(wl["n_amr"] * wl["cfl"] / c_eq))))
+        run_eq = run_to_t_end(torch, wl_eq, wl["E"], args.t_end_budget)
+        run_eq["sim_time_per_wall_s"] = run_eq["t"] / run_eq["wall_s"]
+        ee["t_end"] = {"perk_at_equal_error": {**run_eq, "cfl": c_eq, "n_amr": wl_eq["n_amr"]},
+                       "full_rk": {k: tend["full_rk"][k] for k in ("status", "t", "steps", "wall_s")}}
+        if run_eq["status"] == tend["full_rk"]["status"] == "reached t_end":
+            ee["t_end"]["wall_ratio_full_over_perk_at_equal_error"] = tend["full_rk"]["wall_s"] / run_eq["wall_s"]
+        else:   # compare simulated time per wall second when a budget ends a run
+            ee["t_end"]["sim_rate_ratio_perk_over_full_at_equal_error"] = (
+                run_eq["sim_time_per_wall_s"] / tend["full_rk"]["sim_time_per_wall_s"])
+        equal_error = dict(equal_error or {}, **{"equal_error_" + wl["name"]: ee})
+        tend["equal_error"] = ee["t_end"]
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
