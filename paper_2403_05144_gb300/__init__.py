@@ -176,6 +176,7 @@ class PerkSolver:
         _check(self.lib, None, self.lib.perk_create(C.byref(prob), C.byref(h)))
         self.ctx = h
         self.gamma = gamma
+        self._cells = None
         self.n_elem = 0
         self.S = 0
 
@@ -420,11 +421,22 @@ class PerkSolver:
         Unew = self.torch.empty((n_new.value, 4, 4, 4), dtype=self.torch.float64, device="cuda")
         self._call(self.lib.perk_adapt_commit, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(Unew)))
         self.n_elem = n_new.value
-        cells = np.zeros((self.n_elem, 3), dtype=np.int32)
         self.n_members = getattr(self, "n_members", 1)
-        self._call(self.lib.perk_get_cells, cells.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(self.n_elem))
-        self.cells = cells
+        self._cells = None                  # read back from the library when first asked for
         return Unew
+
+    @property
+    def cells(self):
+        """The current leaves (n_elem x 3 int32: level, ix, iy)."""
+        if self._cells is None:
+            cells = np.zeros((self.n_elem, 3), dtype=np.int32)
+            self._call(self.lib.perk_get_cells, cells.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(self.n_elem))
+            self._cells = cells
+        return self._cells
+
+    @cells.setter
+    def cells(self, value):
+        self._cells = value
 
     def check(self):
         self._call(self.lib.perk_check)

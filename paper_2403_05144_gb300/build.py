@@ -18,6 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libperk.so")
 SOURCES = ["perk_kernels.cu", "perk_host.cpp", "perk_probe.cu", "perk_noalloc.cu", "perk_adjoint.cu", "perk_br1.cu",
+           "perk_amr.cu",
            "perk3d_kernels.cu", "perk3d_host.cpp", "perk3d_br1.cu"]
 HEADERS = [os.path.join(INCLUDE, "perk.h"), os.path.join(INCLUDE, "perk3d.h"), os.path.join(CSRC, "perk_internal.h"),
            os.path.join(CSRC, "perk3d_device.cuh"),

@@ -277,8 +277,20 @@ struct perk_ctx {
   std::vector<double> cur_dts;    // dt of each member as last set on the device
   std::vector<int4> h_if, h_mort;
 
+  // device copy of the leaves (level, ix, iy, member) and whether they are in member-major
+  // Morton order (then AMR plans and the new mesh's connectivity are computed on the device);
+  // host_stale: the host copies (h_cells, h_level, h_member, h_if, h_mort) lag a device-built mesh
+  DevBuf<int4> d_cells, d_newcells;
+  DevBuf<unsigned long long> d_key;
+  DevBuf<int32_t> d_des, d_off, d_cnt_if, d_cnt_mort, d_off_if, d_off_mort;
+  DevBuf<int64_t> d_info;
+  bool mesh_morton = false;
+  bool host_stale = false;
+
   // pending AMR plan (perk_adapt_plan -> perk_adapt_commit)
   bool has_plan = false;
+  bool plan_device = false;          // planned on the device (plan_n_new cells)
+  int64_t plan_n_new = 0;
   bool plan_identity = false;        // the plan changes no cell
   std::vector<int32_t> plan_cells;   // new leaves [n][3]
   std::vector<int32_t> plan_member;  // their ensemble members
@@ -390,6 +402,8 @@ void for_each_buffer(perk_ctx* c, F&& f) {
   f(c->d_surf); f(c->d_K1); f(c->d_Ka); f(c->d_Kb); f(c->d_dt); f(c->d_block_min); f(c->d_dt_out); f(c->d_coef);
   f(c->d_flag); f(c->d_logtab); f(c->d_map); f(c->d_eta); f(c->d_surf_d); f(c->d_Kall); f(c->d_Kpat); f(c->d_g);
   f(c->d_lamK1); f(c->d_lamKa); f(c->d_lamKb); f(c->d_wsurf); f(c->d_q); f(c->d_vsurf);
+  f(c->d_cells); f(c->d_newcells); f(c->d_key); f(c->d_des); f(c->d_off); f(c->d_cnt_if); f(c->d_cnt_mort);
+  f(c->d_off_if); f(c->d_off_mort); f(c->d_info);
 }
 
 // The buffers a caller-bound workspace holds, in layout order, with their sizes (elements of
@@ -405,11 +419,21 @@ void for_each_workspace_buffer(perk_ctx* c, int64_t cells, F&& f) {
   if (c->viscous()) {
     f(c->d_wsurf, n * 64); f(c->d_q, n * 128); f(c->d_vsurf, n * 64);
   }
-  f(c->d_eta, n); f(c->d_dt, n); f(c->d_block_min, std::max<size_t>(n, 1024)); f(c->d_dt_out, (size_t)1);
+  f(c->d_eta, n); f(c->d_dt, n); f(c->d_block_min, std::max<size_t>(n, DT_MAX_BLOCKS)); f(c->d_dt_out, (size_t)1);
   f(c->d_coef, (size_t)MAX_S * MAX_R); f(c->d_counts, (size_t)6 * MAX_S); f(c->d_logtab, (size_t)2 * LOG_TABLE_SIZE);
   f(c->d_if_raw, 2 * n); f(c->d_if_sorted, 2 * n); f(c->d_mort_raw, 2 * n); f(c->d_mort_sorted, 2 * n);
   f(c->d_level, n); f(c->d_method, n); f(c->d_elem_sorted, n); f(c->d_member, n); f(c->d_member_lmax, n);
   f(c->d_map, 5 * n); f(c->d_E, (size_t)MAX_S); f(c->d_minmax, (size_t)2); f(c->d_flag, (size_t)1);
+  f(c->d_cells, n); f(c->d_newcells, n); f(c->d_key, n); f(c->d_des, n); f(c->d_off, n + 1);
+  f(c->d_cnt_if, n); f(c->d_cnt_mort, n); f(c->d_off_if, n); f(c->d_off_mort, n); f(c->d_info, (size_t)8);
+}
+
+// a mesh-sized buffer for n entries: a quarter of headroom when the library allocates it (the
+// mesh grows over a run), the exact size from a bound workspace (carved for its cell count)
+template <class T>
+cudaError_t grow(DevBuf<T>& b, size_t n) {
+  if (n <= b.cap && b.p) return cudaSuccess;
+  return b.ext ? b.ensure(n) : b.ensure(n + n / 4);
 }
 
 constexpr size_t WS_ALIGN = 256;
@@ -586,7 +610,10 @@ perk_status build_connectivity(perk_ctx* ctx, int64_t n, const int32_t* cells, c
   return PERK_OK;
 }
 
-perk_status run_partition(perk_ctx* ctx) {
+// Level partition on the device and its per-stage counts on the host.  device_faces: the
+// interface and mortar counts of the mesh are on the device (d_info[2], d_info[3], written by the
+// device connectivity build) and come back with the partition's counts.
+perk_status run_partition(perk_ctx* ctx, bool device_faces = false) {
   if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   int R = 1, S = 1;
   int32_t minmem[MAX_S] = {0};
@@ -600,12 +627,18 @@ perk_status run_partition(perk_ctx* ctx) {
   PERK_CUDA(ctx, launch_partition(ctx->stream, ctx->n_elem, ctx->n_if, ctx->n_mort, ctx->d_level.p, ctx->d_if_raw.p,
                                   ctx->d_mort_raw.p, R, S, ctx->d_E.p, ctx->n_members > 1 ? ctx->d_member.p : nullptr,
                                   ctx->n_members, ctx->d_member_lmax.p, ctx->d_method.p, ctx->d_elem_sorted.p,
-                                  ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_counts.p, ctx->d_minmax.p));
+                                  ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_counts.p, ctx->d_minmax.p, 2,
+                                  device_faces ? ctx->d_info.p + 2 : nullptr));
   int64_t counts[6 * MAX_S];
   int32_t mm[2];
+  int64_t nf[2] = {ctx->n_if, ctx->n_mort};
   PERK_CUDA(ctx, cudaMemcpyAsync(counts, ctx->d_counts.p, sizeof counts, cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaMemcpyAsync(mm, ctx->d_minmax.p, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream));
+  if (device_faces)
+    PERK_CUDA(ctx, cudaMemcpyAsync(nf, ctx->d_info.p + 2, sizeof nf, cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->n_if = nf[0];
+  ctx->n_mort = nf[1];
   for (int i = 0; i < MAX_S; ++i) {
     ctx->act_el[i] = i < S ? counts[i] : 0;
     ctx->act_if[i] = i < S ? counts[MAX_S + i] : 0;
@@ -731,8 +764,8 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
     PERK_CUDA(ctx, ctx->d_q.ensure(ne * 128));   // BR1 viscous fluxes [e][2 directions][4][16]
     PERK_CUDA(ctx, ctx->d_vsurf.ensure(ne * 64));
   }
-  const int nb = (int)std::min<int64_t>(1024, (n_cells * NODES + 255) / 256);
-  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(nb, 1)));
+  // per-block minima of the step-size reduction: its grid is capped at DT_MAX_BLOCKS blocks
+  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)DT_MAX_BLOCKS));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
                                  ctx->stream));
   if (!ctx->h_if.empty())
@@ -741,8 +774,54 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
   if (!ctx->h_mort.empty())
     PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_mort_raw.p, ctx->h_mort.data(), ctx->h_mort.size() * sizeof(int4),
                                    cudaMemcpyHostToDevice, ctx->stream));
+  {
+    // device copy of the leaves; member-major Morton order enables the device AMR path
+    std::vector<int4> c4(ne);
+    bool sorted = true;
+    uint64_t prev = 0;
+    for (size_t e = 0; e < ne; ++e) {
+      const int m = member ? member[e] : 0;
+      c4[e] = make_int4(cells[3 * e], cells[3 * e + 1], cells[3 * e + 2], m);
+      const uint64_t key = ((uint64_t)m << 40) | morton_key(cells[3 * e], cells[3 * e + 1], cells[3 * e + 2], MAX_LEVEL);
+      if (e > 0 && key <= prev) sorted = false;
+      prev = key;
+    }
+    PERK_CUDA(ctx, ctx->d_cells.ensure(ne));
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_cells.p, c4.data(), ne * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->mesh_morton = sorted;
+    ctx->host_stale = false;
+  }
   ctx->has_mesh = true;
   return run_partition(ctx);
+}
+
+// Host copies of a mesh the device built (AMR on the device): leaves, levels, members, face records.
+perk_status sync_host_mesh(perk_ctx* ctx) {
+  if (!ctx->host_stale) return PERK_OK;
+  const int64_t n = ctx->n_elem;
+  std::vector<int4> c4((size_t)n);
+  ctx->h_if.resize((size_t)ctx->n_if);
+  ctx->h_mort.resize((size_t)ctx->n_mort);
+  PERK_CUDA(ctx, cudaMemcpyAsync(c4.data(), ctx->d_cells.p, n * sizeof(int4), cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->n_if)
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->h_if.data(), ctx->d_if_raw.p, ctx->n_if * sizeof(int4), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+  if (ctx->n_mort)
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->h_mort.data(), ctx->d_mort_raw.p, ctx->n_mort * sizeof(int4),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->h_cells.resize(3 * (size_t)n);
+  ctx->h_level.resize((size_t)n);
+  ctx->h_member.resize((size_t)n);
+  for (int64_t e = 0; e < n; ++e) {
+    ctx->h_cells[3 * e] = c4[e].x;
+    ctx->h_cells[3 * e + 1] = c4[e].y;
+    ctx->h_cells[3 * e + 2] = c4[e].z;
+    ctx->h_level[e] = c4[e].x;
+    ctx->h_member[e] = c4[e].w;
+  }
+  ctx->host_stale = false;
+  return PERK_OK;
 }
 
 
@@ -981,6 +1060,10 @@ perk_status perk_get_members(const perk_ctx* ctx, int32_t* member, int64_t cap) 
   if (!ctx || !member) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return PERK_E_NOT_READY;
   if (cap < ctx->n_elem) return PERK_E_INVALID_ARG;
+  {
+    perk_status s = sync_host_mesh(const_cast<perk_ctx*>(ctx));
+    if (s != PERK_OK) return s;
+  }
   std::copy(ctx->h_member.begin(), ctx->h_member.end(), member);
   return PERK_OK;
 }
@@ -1655,7 +1738,7 @@ perk_status perk_compute_dt_members(perk_ctx* ctx, const double* d_U, double cfl
   if (!ctx || !dts) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_U || !(cfl > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or cfl");
-  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(ctx->n_members, 1024)));
+  PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)std::max(ctx->n_members, DT_MAX_BLOCKS)));
   PERK_CUDA(ctx, launch_dt_members(ctx->stream, ctx->n_elem, d_U, ctx->d_level.p, ctx->d_member.p, ctx->n_members,
                                    ctx->length, ctx->ops.gamma, ctx->d_block_min.p));
   std::vector<double> m(ctx->n_members);
@@ -1687,7 +1770,8 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
   if (!ctx || !dt) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
   if (!d_U || !(cfl > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad U or cfl");
-  const int nb = (int)std::min<int64_t>(1024, (ctx->n_elem * NODES + 255) / 256);
+  const int nb = (int)std::min<int64_t>(DT_MAX_BLOCKS, (ctx->n_elem * NODES + DT_THREADS - 1) / DT_THREADS);
+  if (ctx->d_block_min.cap < (size_t)nb) return fail(ctx, PERK_E_INVALID_ARG, "internal: step-size scratch too small");
   PERK_CUDA(ctx, launch_dt(ctx->stream, ctx->n_elem, d_U, ctx->d_level.p, ctx->length, ctx->ops.gamma,
                            ctx->d_block_min.p, nb, ctx->d_dt_out.p));
   double m = 0.0;
@@ -1976,23 +2060,67 @@ perk_status perk_amr_indicator(perk_ctx* ctx, int32_t indicator, const double* d
   return PERK_OK;
 }
 
+// perk_adapt_plan on the device (a mesh in member-major Morton order): desired levels from the
+// indicator (or the caller's), balance, and the new leaves' offsets; only the new cell count and
+// whether anything changes come back to the host.
+static perk_status adapt_plan_device(perk_ctx* ctx, const perk_amr_params* prm, const int32_t* desired,
+                                     const double* d_U, int64_t* n_new) {
+  const int64_t n = ctx->n_elem;
+  cudaStream_t st = ctx->stream;
+  PERK_CUDA(ctx, ctx->d_des.ensure((size_t)n));
+  PERK_CUDA(ctx, ctx->d_off.ensure((size_t)n + 1));
+  PERK_CUDA(ctx, ctx->d_info.ensure(8));
+  AmrPlanArgs a{0, 0, 0.0, 0.0};
+  const double* eta = nullptr;
+  if (desired) {
+    PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_des.p, desired, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<double> x, w;
+    lgl(NN - 1, x, w);
+    PERK_CUDA(ctx, launch_indicator(st, n, d_U, ctx->ops, w[0], w[1], prm->indicator, ctx->d_eta.p));
+    a = AmrPlanArgs{prm->level_min, prm->level_max, prm->refine_above, prm->coarsen_below};
+    eta = ctx->d_eta.p;
+  }
+  PERK_CUDA(ctx, launch_amr_plan(st, n, ctx->d_cells.p, eta, a, ctx->n_if, ctx->d_if_raw.p, ctx->n_mort,
+                                 ctx->d_mort_raw.p, ctx->d_des.p, ctx->d_off.p, ctx->d_info.p));
+  int64_t info[5];
+  PERK_CUDA(ctx, cudaMemcpyAsync(info, ctx->d_info.p, sizeof info, cudaMemcpyDeviceToHost, st));
+  PERK_CUDA(ctx, cudaStreamSynchronize(st));
+  if (info[4] != 0) return fail(ctx, PERK_E_CUDA, "AMR balance did not settle within its pass bound");
+  ctx->plan_device = true;
+  ctx->plan_n_new = info[0];
+  ctx->plan_identity = info[1] == 0;
+  ctx->has_plan = true;
+  *n_new = info[0];
+  return PERK_OK;
+}
+
 perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int32_t* desired, const double* d_U,
                             int64_t* n_new) {
   if (!ctx || !n_new) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return fail(ctx, PERK_E_NOT_READY, "no mesh");
+  ctx->has_plan = false;
+  ctx->plan_device = false;
   const int64_t n = ctx->n_elem;
+  if (desired || ctx->host_stale || !ctx->mesh_morton) {
+    perk_status s = sync_host_mesh(ctx);   // the desired levels are checked against the host's levels
+    if (s != PERK_OK) return s;
+  }
   const int32_t* c = ctx->h_cells.data();
-  std::vector<int32_t> d(n);
   if (desired) {
-    for (int64_t e = 0; e < n; ++e) {
+    for (int64_t e = 0; e < n; ++e)
       if (desired[e] < c[3 * e] - 1 || desired[e] > c[3 * e] + 1 || desired[e] < 0 || desired[e] > 27)
         return fail(ctx, PERK_E_INVALID_ARG, "desired level of cell %lld must differ by at most one", (long long)e);
-      d[e] = desired[e];
-    }
   } else {
     if (!prm || !d_U) return fail(ctx, PERK_E_INVALID_ARG, "need AMR parameters and U");
     if (prm->indicator != PERK_INDICATOR_DENSITY && prm->indicator != PERK_INDICATOR_LOHNER_VX)
       return fail(ctx, PERK_E_INVALID_ARG, "unknown indicator %d", prm->indicator);
+  }
+  if (ctx->mesh_morton) return adapt_plan_device(ctx, prm, desired, d_U, n_new);
+  std::vector<int32_t> d(n);
+  if (desired) {
+    for (int64_t e = 0; e < n; ++e) d[e] = desired[e];
+  } else {
     std::vector<double> x, w;
     lgl(NN - 1, x, w);
     PERK_CUDA(ctx, launch_indicator(ctx->stream, n, d_U, ctx->ops, w[0], w[1], prm->indicator, ctx->d_eta.p));
@@ -2083,16 +2211,74 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
   return PERK_OK;
 }
 
+// perk_adapt_commit of a device plan: new leaves, transfer, connectivity and partition on the
+// device; the host receives the counts the launches need (one synchronisation)
+static perk_status adapt_commit_device(perk_ctx* ctx, const double* d_Uold, double* d_Unew) {
+  const int64_t n = ctx->n_elem, m = ctx->plan_n_new;
+  cudaStream_t st = ctx->stream;
+  if (ctx->ws_base && m > ctx->ws_cells)
+    return fail(ctx, PERK_E_OOM,
+                "the adapted mesh has %lld cells, the bound workspace serves up to %lld: bind a larger one "
+                "(perk_workspace_bytes) and commit again", (long long)m, (long long)ctx->ws_cells);
+  // Every buffer of the new mesh is sized before the first launch of this call (the plan left the
+  // stream empty, so no reallocation frees memory that queued work still reads).  The old leaves
+  // (d_cells), desired levels and offsets keep their sizes: the new-leaf kernel reads them.
+  const size_t mm = (size_t)m;
+  PERK_CUDA(ctx, grow(ctx->d_newcells, mm));
+  PERK_CUDA(ctx, grow(ctx->d_key, mm));
+  PERK_CUDA(ctx, grow(ctx->d_map, 5 * mm));
+  PERK_CUDA(ctx, grow(ctx->d_level, mm));
+  PERK_CUDA(ctx, grow(ctx->d_member, mm));
+  PERK_CUDA(ctx, grow(ctx->d_method, mm));
+  PERK_CUDA(ctx, grow(ctx->d_elem_sorted, mm));
+  PERK_CUDA(ctx, grow(ctx->d_if_raw, 2 * mm));
+  PERK_CUDA(ctx, grow(ctx->d_if_sorted, 2 * mm));
+  PERK_CUDA(ctx, grow(ctx->d_mort_raw, 2 * mm));
+  PERK_CUDA(ctx, grow(ctx->d_mort_sorted, 2 * mm));
+  PERK_CUDA(ctx, grow(ctx->d_cnt_if, mm));
+  PERK_CUDA(ctx, grow(ctx->d_cnt_mort, mm));
+  PERK_CUDA(ctx, grow(ctx->d_off_if, mm));
+  PERK_CUDA(ctx, grow(ctx->d_off_mort, mm));
+  PERK_CUDA(ctx, grow(ctx->d_surf, mm * ELEM));
+  PERK_CUDA(ctx, grow(ctx->d_K1, mm * ELEM));
+  PERK_CUDA(ctx, grow(ctx->d_Ka, mm * ELEM));
+  PERK_CUDA(ctx, grow(ctx->d_Kb, mm * ELEM));
+  PERK_CUDA(ctx, grow(ctx->d_eta, mm));
+  if (ctx->viscous()) {
+    PERK_CUDA(ctx, grow(ctx->d_wsurf, mm * 64));
+    PERK_CUDA(ctx, grow(ctx->d_q, mm * 128));
+    PERK_CUDA(ctx, grow(ctx->d_vsurf, mm * 64));
+  }
+  PERK_CUDA(ctx, launch_amr_leaves(st, n, ctx->d_cells.p, ctx->d_des.p, ctx->d_off.p, ctx->d_newcells.p,
+                                   ctx->d_key.p, ctx->d_map.p));
+  PERK_CUDA(ctx, launch_transfer(st, m, ctx->d_map.p, d_Uold, ctx->ops, d_Unew));
+  std::swap(ctx->d_cells, ctx->d_newcells);
+  PERK_CUDA(ctx, launch_amr_install(st, m, ctx->d_cells.p, ctx->d_level.p, ctx->d_member.p));
+  PERK_CUDA(ctx, launch_connect(st, m, ctx->d_cells.p, ctx->d_key.p, ctx->d_cnt_if.p, ctx->d_cnt_mort.p,
+                                ctx->d_off_if.p, ctx->d_off_mort.p, ctx->d_if_raw.p, ctx->d_mort_raw.p, ctx->d_info.p));
+  drop_graph(ctx);
+  ctx->has_plan = false;
+  ctx->plan_device = false;
+  ctx->n_elem = m;
+  ctx->n_if = 2 * m;     // upper bounds until the partition brings the counts back
+  ctx->n_mort = 2 * m;
+  ctx->host_stale = true;
+  ctx->mesh_morton = true;
+  return run_partition(ctx, true);
+}
+
 perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew) {
   if (!ctx) return PERK_E_INVALID_ARG;
   if (!ctx->has_plan) return fail(ctx, PERK_E_NOT_READY, "no AMR plan");
   if (!d_Uold || !d_Unew || d_Uold == d_Unew) return fail(ctx, PERK_E_INVALID_ARG, "need distinct old and new U");
-  const int64_t m = (int64_t)ctx->plan_cells.size() / 3;
+  if (ctx->plan_device && !ctx->plan_identity) return adapt_commit_device(ctx, d_Uold, d_Unew);
+  const int64_t m = ctx->plan_device ? ctx->plan_n_new : (int64_t)ctx->plan_cells.size() / 3;
   if (ctx->plan_identity) {
     // nothing changes: the new state is a copy and the mesh, partition and graph stay
     PERK_CUDA(ctx, cudaMemcpyAsync(d_Unew, d_Uold, (size_t)m * ELEM * sizeof(double), cudaMemcpyDeviceToDevice,
                                    ctx->stream));
     ctx->has_plan = false;
+    ctx->plan_device = false;
     ctx->plan_cells.clear();
     ctx->plan_member.clear();
     return PERK_OK;
@@ -2141,6 +2327,10 @@ perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap) {
   if (!ctx || !cells) return PERK_E_INVALID_ARG;
   if (!ctx->has_mesh) return PERK_E_NOT_READY;
   if (cap < ctx->n_elem) return PERK_E_INVALID_ARG;
+  {
+    perk_status s = sync_host_mesh(const_cast<perk_ctx*>(ctx));
+    if (s != PERK_OK) return s;
+  }
   std::copy(ctx->h_cells.begin(), ctx->h_cells.end(), cells);
   return PERK_OK;
 }

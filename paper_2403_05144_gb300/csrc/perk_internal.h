@@ -18,6 +18,7 @@ constexpr int ELEM = NV * NODES;  // doubles per element
 constexpr int MAX_S = 64;
 constexpr int MAX_R = 8;
 constexpr int DT_THREADS = 256;   // threads per block of the CFL step-size reduction
+constexpr int DT_MAX_BLOCKS = 1024;   // its grid cap (grid-stride), the size of its per-block scratch
 
 // Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount), looked up
 // once per device and cached; grid caps of the grid-stride kernels are multiples of it.
@@ -102,7 +103,9 @@ cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int6
                              const int32_t* member, int n_members, int32_t* member_lmax /* [n_members] */,
                              int32_t* method, int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted,
                              int64_t* counts /* [3][MAX_S] */, int32_t* level_minmax /* [2] */,
-                             int mort_flag_bits = 2);
+                             int mort_flag_bits = 2, const int64_t* d_nfaces = nullptr);
+// (d_nfaces: if set, the interface and mortar counts are read from d_nfaces[0], d_nfaces[1] on the
+// device instead of n_if, n_mort, which are then only upper bounds)
 
 // per-member CFL reduction: out[m] = min over member m's elements of h_e / lambda_e (out pre-set to +inf)
 cudaError_t launch_dt_members(cudaStream_t st, int64_t n_elem, const double* U, const int32_t* level,
@@ -129,6 +132,29 @@ cudaError_t launch_set_scalar(cudaStream_t st, double* p, double v);
 
 cudaError_t launch_indicator(cudaStream_t st, int64_t n, const double* U, const Ops& ops, double w0, double w1,
                              int kind, double* eta);
+
+// ---- AMR cycle on the device (perk_amr.cu); cells are int4 (level, ix, iy, member) in
+// member-major Morton order ----
+struct AmrPlanArgs {
+  int level_min, level_max;
+  double refine_above, coarsen_below;
+};
+// desired levels from eta (when eta is set; else d holds them already), balanced in place; then
+// off[n + 1] = exclusive offsets of the new leaves, info[0] = new cell count, info[1] = changed,
+// info[4] = 1 if the balance did not settle within its pass bound
+cudaError_t launch_amr_plan(cudaStream_t st, int64_t n, const int4* cells, const double* eta, const AmrPlanArgs& a,
+                            int64_t n_if, const int4* ifs, int64_t n_mort, const int4* morts, int32_t* d,
+                            int32_t* off, int64_t* info);
+// new leaves (out), their Morton keys and transfer records (5 int32 each)
+cudaError_t launch_amr_leaves(cudaStream_t st, int64_t n, const int4* cells, const int32_t* d, const int32_t* off,
+                              int4* out, unsigned long long* key, int32_t* map);
+// interfaces and mortars of a leaf list with its keys (scratch cnt_*, off_*: n each); counts to
+// info[2], info[3]; ifs and morts need room for 2 n records each
+cudaError_t launch_connect(cudaStream_t st, int64_t n, const int4* cells, const unsigned long long* key,
+                           int32_t* cnt_if, int32_t* cnt_mort, int32_t* off_if, int32_t* off_mort, int4* ifs,
+                           int4* morts, int64_t* info);
+// level and member of every cell
+cudaError_t launch_amr_install(cudaStream_t st, int64_t n, const int4* cells, int32_t* level, int32_t* member);
 cudaError_t launch_transfer(cudaStream_t st, int64_t n, const int32_t* map, const double* Uold, const Ops& ops,
                             double* Unew);
 

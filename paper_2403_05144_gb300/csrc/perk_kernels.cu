@@ -739,7 +739,12 @@ __global__ void __launch_bounds__(PART_THREADS) k_partition(int64_t n_elem, int6
                                                               int32_t* member_lmax, int32_t* method,
                                                               int32_t* elem_sorted, int4* if_sorted,
                                                               int4* mort_sorted, int64_t* counts,
-                                                              int32_t* level_minmax, int mort_flag_bits) {
+                                                              int32_t* level_minmax, int mort_flag_bits,
+                                                              const int64_t* __restrict__ d_nfaces) {
+  if (d_nfaces) {
+    n_if = d_nfaces[0];
+    n_mort = d_nfaces[1];
+  }
   __shared__ int s_min, s_max;
   __shared__ int s_cnt[3][MAX_R];
   __shared__ int s_base[MAX_R];
@@ -1025,11 +1030,11 @@ cudaError_t launch_partition(cudaStream_t st, int64_t n_elem, int64_t n_if, int6
                              const int4* if_raw, const int4* mort_raw, int R, int S, const int32_t* stage_minmem,
                              const int32_t* member, int n_members, int32_t* member_lmax, int32_t* method,
                              int32_t* elem_sorted, int4* if_sorted, int4* mort_sorted, int64_t* counts,
-                             int32_t* level_minmax, int mort_flag_bits) {
+                             int32_t* level_minmax, int mort_flag_bits, const int64_t* d_nfaces) {
   if (mort_flag_bits < 1 || mort_flag_bits > 8) return cudaErrorInvalidValue;
   k_partition<<<1, PART_THREADS, 0, st>>>(n_elem, n_if, n_mort, level, if_raw, mort_raw, R, S, stage_minmem, member, n_members,
                                           member_lmax, method, elem_sorted, if_sorted, mort_sorted, counts,
-                                          level_minmax, mort_flag_bits);
+                                          level_minmax, mort_flag_bits, d_nfaces);
   return cudaGetLastError();
 }
 

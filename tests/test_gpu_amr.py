@@ -120,3 +120,47 @@ def test_dynamic_kh_run_with_replayed_decisions():
     s.check()
     got = Ug.cpu().numpy()
     assert np.max(np.abs(got - U)) / np.max(np.abs(U)) < 1e-10
+
+
+def test_device_built_mesh_equals_a_fresh_upload():
+    # after each indicator-driven cycle (plan, balance, new leaves, connectivity and partition on
+    # the device) the context must hold exactly what uploading the same leaves builds on the host:
+    # the same counts per stage and bitwise the same right-hand side (a wrong neighbour or mortar
+    # would change it)
+    from paper_2403_05144_gb300 import _lib
+    cells = uniform_cells(4)
+    U = cuda(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3))
+    s = solver_for(cells, -1.0, 2.0, "hllc", [4, 6, 10, 16])
+    for cycle in range(4):
+        U = s.adapt(U, **AMR)
+        fresh = solver_for(s.cells, -1.0, 2.0, "hllc", [4, 6, 10, 16])
+        a, b = s.info(), fresh.info()
+        for k in ("n_elem", "n_interfaces", "n_mortars", "level_min", "level_max", "active_elements",
+                  "active_interfaces", "active_mortars", "dof_stage_updates"):
+            assert a[k] == b[k], (cycle, k)
+        assert torch.equal(s.rhs_full(U), fresh.rhs_full(U))
+        for i in (0, 7, 15):
+            assert torch.equal(s.rhs_active(i, U, out=torch.zeros_like(U)), fresh.rhs_active(i, U, out=torch.zeros_like(U)))
+    assert s.info()["level_max"] == 7 and s.info()["n_mortars"] > 0
+
+
+def test_unsorted_upload_is_planned_on_the_host_then_matches_oracle():
+    # a leaf list not in Morton order takes the host plan (its result is in Morton order, after
+    # which plans run on the device); both cycles match the oracle's meshes and transfer
+    cells = kh_band_cells(4, 6, 0.05)
+    perm = np.random.default_rng(9).permutation(len(cells))
+    shuffled = [cells[k] for k in perm]
+    U = discontinuous_state(shuffled, -1.0, 2.0)
+    m = TreeMesh(shuffled, -1.0, 2.0)
+    s = solver_for(shuffled, -1.0, 2.0, "hllc", [4, 6, 10, 16])
+    Ug = cuda(U)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        lev = m.cells[:, 0]
+        raw = np.clip(lev + rng.integers(-1, 2, size=len(lev)), 4, 7)
+        want_cells = new_cells(m, balance(m, raw))
+        U = transfer([tuple(c) for c in m.cells.tolist()], U, want_cells)
+        m = TreeMesh(want_cells, -1.0, 2.0)
+        Ug = s.adapt(Ug, desired=raw)
+        assert [tuple(c) for c in s.cells.tolist()] == want_cells
+        np.testing.assert_allclose(Ug.cpu().numpy(), U, rtol=0, atol=1e-13 * np.max(np.abs(U)))
