@@ -454,27 +454,66 @@ def oracle_stage_sample(wl: dict, cells, U: np.ndarray, n_stages: int = 0, budge
 
 
 def host_cpu() -> dict:
-    """The host's logical core count and CPU model (from /proc/cpuinfo where present)."""
+    """The host's logical core count and CPU model (lscpu, else /proc/cpuinfo)."""
     import platform
     model = platform.processor() or platform.machine()
     try:
-        for line in open("/proc/cpuinfo"):
-            key = line.split(":")[0].strip().lower()
-            if key in ("model name", "cpu model", "hardware") and ":" in line:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
                 model = line.split(":", 1)[1].strip()
                 break
-    except OSError:
-        pass
+    except (OSError, subprocess.SubprocessError):
+        try:
+            for line in open("/proc/cpuinfo"):
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
     return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
 
 
-def cpu_baseline(wl: dict, cells, U0: np.ndarray, dt: float) -> dict:
+def _oracle_worker(job):
+    """One host process timing the oracle's partitioned stage evaluations (cpu_baseline)."""
+    wl_name, cells, U, budget_s = job
+    units, sec, k, _ = oracle_stage_sample(workload(wl_name), cells, U, budget_s=budget_s)
+    return units, sec, k
+
+
+def cpu_baseline(wl_name: str, wl: dict, cells, U0: np.ndarray, budget_s: float = 10.0) -> dict:
     """The oracle as it stands, on a bounded sample of the same workload: partitioned stage
-    evaluations of the workload's current mesh for about ten seconds."""
-    units, sec, k, S = oracle_stage_sample(wl, cells, U0)
-    return {"value": units / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-            "sample": f"{k} partitioned stage evaluations (stages 0.. of S={S}, cycling) of the workload's "
-                      f"current mesh ({len(cells)} cells), {sec:.1f} s, numpy float64 on one host thread"}
+    evaluations of the workload's current mesh for about ten seconds, in one host process (one
+    thread), then in one process per host core at once (spawned, each single-threaded)."""
+    import multiprocessing as mp
+    cells = [tuple(int(v) for v in c) for c in cells]
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"                      # inherited by the spawned workers
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            units, sec, k = pool.map(_oracle_worker, [(wl_name, cells, U0, budget_s)])[0]
+        n = os.cpu_count() or 1
+        with ctx.Pool(n) as pool:
+            res = pool.map(_oracle_worker, [(wl_name, cells, U0, budget_s)] * n)
+    finally:
+        for k_, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k_, None)
+            else:
+                os.environ[k_] = v
+    all_units = sum(r[0] for r in res)
+    all_sec = max(r[1] for r in res)
+    S = max(wl["E"])
+    return {"value": all_units / all_sec, "unit": UNIT, "cores": n, "kind": "oracle", "host": host_cpu(),
+            "sample": f"{n} processes (one per host core, each single-threaded) evaluating the oracle's partitioned "
+                      f"stages (stages 0.. of S={S}, cycling) of the workload's current mesh ({len(cells)} cells) "
+                      f"for about {budget_s:.0f} s each: {sum(r[2] for r in res)} evaluations",
+            "single_core": {"value": units / sec, "unit": UNIT, "cores": 1,
+                            "sample": f"{k} partitioned stage evaluations in one single-threaded process, "
+                                      f"{sec:.1f} s"}}
 
 
 def run_reference(args) -> None:
@@ -550,6 +589,17 @@ def run_perk(args) -> None:
         barrier()
         ms_full, units_full = time_steps(torch, full, args.steps, flush)
         barrier()
+    # the same steps without AMR cycles (graph replays only, on the mesh the timed steps ended on):
+    # the difference is the cost of the AMR cycles inside the timed region
+    ms_no_amr = None
+    if wl["amr"] and timed_cycles:
+        Ukeep, wl_keep = perk.U.clone(), perk.wl
+        perk.wl = dict(wl, amr=None)
+        for _ in range(2):
+            perk.step()
+        ms_no_amr, _ = time_steps(torch, perk, args.steps, flush)
+        perk.wl, perk.U = wl_keep, Ukeep
+        (ms_no_amr,) = max_over_ranks([ms_no_amr], world, "cuda")
     perk.solver.check()
     full.solver.check()
     ms, ms_full = max_over_ranks([ms, ms_full], world, "cuda")
@@ -643,6 +693,11 @@ def run_perk(args) -> None:
                    "family": wl["E"], "stages": S, "surface_flux": wl["flux"], "cfl": wl["cfl"], "dt": perk.dt,
                    "amr": ({**wl["amr"], "every_steps": wl["n_amr"], "in_timed_region": True} if wl["amr"] else None),
                    "dof_stage_updates_per_step": units / args.steps,
+                   "amr_cycles_in_timed_region": timed_cycles,
+                   "ms_per_step_without_amr": None if ms_no_amr is None else ms_no_amr / args.steps,
+                   "amr_ms_per_cycle": (None if ms_no_amr is None
+                                        else (ms - ms_no_amr) / timed_cycles),
+                   "amr_share_of_step_time": None if ms_no_amr is None else (ms - ms_no_amr) / ms,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"{world} independent replica(s)", "graph": True},
         "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps,
@@ -678,7 +733,7 @@ def run_perk(args) -> None:
     }
     if rank == 0:
         if world == 1:
-            line["cpu_baseline"] = cpu_baseline(wl, perk.solver.cells, perk.U.cpu().numpy(), perk.dt)
+            line["cpu_baseline"] = cpu_baseline(args.workload, wl, perk.solver.cells, perk.U.cpu().numpy())
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -1180,6 +1235,11 @@ def run_tgv(args) -> None:
                    "amr": {**TGV["amr"], "indicator": "enstrophy", "every_steps": TGV["n_amr"],
                            "in_timed_region": True, "cycles_timed": cycles},
                    "dof_stage_updates_per_step": units / args.steps,
+                   "amr_cycles_in_timed_region": timed_cycles,
+                   "ms_per_step_without_amr": None if ms_no_amr is None else ms_no_amr / args.steps,
+                   "amr_ms_per_cycle": (None if ms_no_amr is None
+                                        else (ms - ms_no_amr) / timed_cycles),
+                   "amr_share_of_step_time": None if ms_no_amr is None else (ms - ms_no_amr) / ms,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"{world} independent replica(s)", "graph": True},
         "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps,

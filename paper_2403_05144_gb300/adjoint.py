@@ -5,9 +5,11 @@
 (Jacobian transposes of the partitioned RHS and of the stage combinations).
 ``gradient`` differentiates a functional of the end state over many steps on a
 frozen mesh with step checkpointing: the state is stored every
-``checkpoint_every`` steps and each window's steps are recomputed from its
-checkpoint during the reverse sweep, keeping their stages, so memory holds one
-window of states and stages.
+``checkpoint_every`` steps; the windows whose stages fit in a device-memory
+budget (the last ones, which the reverse sweep meets first) keep their states
+and stages from the forward pass itself, and every other window's steps are
+recomputed from its checkpoint during the reverse sweep, keeping their stages
+in one reused buffer.
 """
 
 from __future__ import annotations
@@ -47,40 +49,67 @@ def kinetic_energy(U: torch.Tensor, h: torch.Tensor, w: torch.Tensor) -> torch.T
 
 def gradient(solver: PerkSolver, U0: torch.Tensor, dt: float, n_steps: int,
              functional: Callable[[torch.Tensor], torch.Tensor], checkpoint_every: int = 20,
-             store_stages: bool = True):
+             store_stages: bool = True, memory_budget: int | None = None):
     """(J(U_N), dJ/dU_0) for N = n_steps P-ERK steps from U0 on the solver's (frozen) mesh.
 
-    With ``store_stages`` the recomputation of a window keeps every step's stages
-    (checkpoint_every x S states) and the reverse sweep reads them; otherwise each
-    reverse step recomputes its own stages."""
-    checkpoints = {}
+    With ``store_stages`` the reverse sweep reads every step's stages (S states per
+    step): the last windows of ``checkpoint_every`` steps keep theirs from the forward
+    pass, as many as fit in ``memory_budget`` bytes (default: half the free device
+    memory), and the others recompute them from their checkpoint into one reused
+    buffer.  Without it each reverse step recomputes its own stages.  Returns the
+    functional and the gradient; ``gradient.last_stats`` holds the windows kept."""
+    n_windows = (n_steps + checkpoint_every - 1) // checkpoint_every
+    state_bytes = U0.numel() * U0.element_size()
+    window_bytes = checkpoint_every * (solver.S + 1) * state_bytes
+    kept = 0
+    if store_stages:
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info(U0.device)
+            memory_budget = free // 2
+        kept = int(min(n_windows, max(0, memory_budget) // window_bytes))
+    first_kept = n_windows - kept                # windows first_kept.. keep their forward stages
+    checkpoints, stored = {}, {}
     U = U0.detach().clone()
-    for n in range(n_steps):
-        if n % checkpoint_every == 0:
-            checkpoints[n] = U.clone()
-        solver.step(U, dt)
+    for w in range(n_windows):
+        w_start, w_end = w * checkpoint_every, min((w + 1) * checkpoint_every, n_steps)
+        if w < first_kept:
+            checkpoints[w_start] = U.clone()
+            for _ in range(w_end - w_start):
+                solver.step(U, dt)
+        else:
+            K = torch.empty((w_end - w_start, solver.S) + tuple(U0.shape), dtype=U0.dtype, device=U0.device)
+            states = []
+            for k in range(w_end - w_start):
+                states.append(U.clone())
+                solver.step_store(U, dt, stages=K[k])
+            stored[w_start] = (states, K)
     UN = U.detach().requires_grad_(True)
     J = functional(UN)
     (lam,) = torch.autograd.grad(J, UN)
     lam = lam.contiguous()
     lam_next = torch.empty_like(lam)
-    starts = sorted(checkpoints)
     buf = None
-    if store_stages:
+    if store_stages and first_kept > 0:
         buf = torch.empty((min(checkpoint_every, n_steps), solver.S) + tuple(U0.shape), dtype=U0.dtype,
                           device=U0.device)
-    for w_start in reversed(starts):
-        w_end = min(w_start + checkpoint_every, n_steps)
-        Uw = checkpoints[w_start].clone()
-        states = []
-        for k in range(w_end - w_start):
-            states.append(Uw.clone())
-            if store_stages:
-                solver.step_store(Uw, dt, stages=buf[k])
-            elif k < w_end - w_start - 1:
-                solver.step(Uw, dt)
+    for w in reversed(range(n_windows)):
+        w_start, w_end = w * checkpoint_every, min((w + 1) * checkpoint_every, n_steps)
+        if w_start in stored:
+            states, K = stored.pop(w_start)
+        else:
+            Uw = checkpoints[w_start].clone()
+            states, K = [], buf
+            for k in range(w_end - w_start):
+                states.append(Uw.clone())
+                if store_stages:
+                    solver.step_store(Uw, dt, stages=buf[k])
+                elif k < w_end - w_start - 1:
+                    solver.step(Uw, dt)
         for k in reversed(range(len(states))):
-            solver.step_vjp(states[k], dt, lam, out=lam_next, stages=buf[k] if store_stages else None)
+            solver.step_vjp(states[k], dt, lam, out=lam_next, stages=K[k] if store_stages else None)
             lam, lam_next = lam_next, lam
+        del states, K
     solver.check()
+    gradient.last_stats = {"windows": n_windows, "windows_kept_from_forward": kept,
+                           "windows_recomputed": n_windows - kept, "window_bytes": window_bytes}
     return J.detach(), lam
