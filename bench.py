@@ -58,6 +58,12 @@ UNIT = "DoF-stage updates/s"
 # flux differencing 640, surface lifting and Jacobian 192.  The roofline's `achieved` is this
 # count times the element-stages of the profiled volume launches over their CUDA-event time.
 VOL_ALG_FLOPS_PER_ELEM = 2672
+# The same counter on the numerical surface flux at one face node (subsonic case) and on one
+# mortar's interpolation and L2 projection: the face work of a stage, which the fused stage
+# kernel performs beside the volume work (per stage: 4 face nodes per active interface, 8 per
+# active mortar, and one mortar's operators per active mortar).
+FACE_ALG_FLOPS_PER_NODE = {"hll": 70, "hllc": 69, "ec": 53, "hlle": 93}
+MORTAR_ALG_FLOPS = 380
 # FP64 issue slots of one element-stage of the volume kernel (flux
 # differencing + surface lifting + stage combination) in the library's
 # formulation (add, mul, FMA, compare = 1 slot; reciprocal = 4 FMA after the
@@ -614,7 +620,13 @@ def run_perk(args) -> None:
     for _ in range(args.steps):
         acc = perk.solver.step_profiled(Up, perk.dt, acc)
     vol_ms, vol_launches = acc.ms[1], acc.launches[1]
-    achieved = VOL_ALG_FLOPS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)
+    fused = acc.launches[0] == 0            # one launch per stage: the face work is in kind 1 too
+    face_nodes = args.steps * sum(4 * a + 8 * b for a, b in zip(info["active_interfaces"], info["active_mortars"]))
+    mortars = args.steps * sum(info["active_mortars"])
+    alg_flops = VOL_ALG_FLOPS_PER_ELEM * acc.element_stages
+    if fused:
+        alg_flops += FACE_ALG_FLOPS_PER_NODE[wl["flux"]] * face_nodes + MORTAR_ALG_FLOPS * mortars
+    achieved = alg_flops / (vol_ms * 1e-3)
     slot_rate = 2.0 * VOL_SLOTS_PER_ELEM * acc.element_stages / (vol_ms * 1e-3)   # FMA-equivalent slots
     kernel_ms_total = sum(acc.ms[k] for k in range(4))
 
@@ -707,15 +719,21 @@ def run_perk(args) -> None:
         "equal_error": equal_error,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / fma_flops,
-                     "traffic": VOL_DRAM_BYTES_PER_ELEM * acc.element_stages / max(vol_launches, 1),
+                     "traffic": (None if fused else VOL_DRAM_BYTES_PER_ELEM * acc.element_stages / max(vol_launches, 1)),
                      "traffic_note": "DRAM bytes per launch: ncu bytes per element-stage x element-stages "
-                                     "per launch", "kernel": "k_volume",
+                                     "per launch",
+                     "kernel": "k_stage (face fluxes and volume terms of a stage in one launch)" if fused
+                               else "k_volume",
                      "launches": vol_launches, "avg_launch_ms": vol_ms / max(vol_launches, 1),
                      "share_of_kernel_time": vol_ms / kernel_ms_total,
                      "peak_source": "FP64 FMA microbenchmark measured live on this GPU (perk_measure_fp64)",
-                     "work_per_element_stage": {"algorithmic_flops": VOL_ALG_FLOPS_PER_ELEM,
-                                                "source": "oracle operation counter (add/mul 1, divide and "
-                                                          "logarithm 1 each; 48 symmetric pairs)"},
+                     "work": {"volume_flops_per_element_stage": VOL_ALG_FLOPS_PER_ELEM,
+                              "face_flops_per_face_node": FACE_ALG_FLOPS_PER_NODE[wl["flux"]] if fused else 0,
+                              "mortar_operator_flops": MORTAR_ALG_FLOPS if fused else 0,
+                              "element_stages": acc.element_stages, "face_node_fluxes": face_nodes if fused else 0,
+                              "mortars": mortars if fused else 0, "algorithmic_flops": alg_flops,
+                              "source": "oracle operation counter (add/mul 1, divide, square root and logarithm "
+                                        "1 each; 48 symmetric pairs; subsonic face fluxes)"},
                      "issue_slot_frac": slot_rate / fma_flops,
                      "issue_slot_note": f"{VOL_SLOTS_PER_ELEM} FP64 issue slots per element-stage in the "
                                         "kernel's own formulation, each counted as an FMA (2 flops), "
