@@ -249,8 +249,20 @@ perk_status perk_step(perk_ctx* ctx, double* d_U, double dt);
 perk_status perk_step_dts(perk_ctx* ctx, double* d_U, const double* dts);
 
 /* Synchronises the stream and returns PERK_E_NONFINITE if any step since the
- * last check was rejected (then clears the flag), else PERK_OK. */
+ * last check was rejected (then clears the flag), PERK_E_TIMEOUT if a fused
+ * stage gave up waiting for its face fluxes (the step was not committed
+ * either), else PERK_OK. */
 perk_status perk_check(perk_ctx* ctx);
+
+/* One launch per stage (Eq. PartitionedRKSystem, each stage's partitioned RHS): for the
+ * Euler equations with the plain volume term, the numerical fluxes of a stage's active
+ * interfaces and mortars and the volume terms of its active elements run as one kernel whose
+ * work items (faces first) are dealt in order to its blocks; each element's volume work waits,
+ * with a bounded wait, for its four face fluxes before the surface lifting.  Off by default
+ * (two launches per stage: face fluxes, then volume terms); enabled != 0 selects one launch.
+ * Results are bitwise the same either way.  Other equations and shock capturing always use two
+ * launches. */
+perk_status perk_set_stage_fusion(perk_ctx* ctx, int enabled);
 
 /* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed
  * on the device (Eq. CFL_DG, Eq. TimestepConstraint).  Blocks; *dt receives it.
@@ -399,7 +411,8 @@ perk_status perk_get_cells(const perk_ctx* ctx, int32_t* cells, int64_t cap);
 /* Per-kernel timing of one step (tracing).  Runs the step like perk_step but
  * without a graph, with CUDA events recorded on the context's stream around
  * every launch, and blocks until the step is done.  Kernel kinds:
- * 0 = face fluxes, 1 = volume integral, 2 = final update, 3 = viscous terms
+ * 0 = face fluxes, 1 = volume integral (with stage fusion: the whole stage, face
+ * fluxes included, and kind 0 stays empty), 2 = final update, 3 = viscous terms
  * (Navier-Stokes: the four BR1 kernels of a stage, timed and counted as one
  * group).  ms[k] and launches[k] are accumulated (not reset) so a caller can
  * sum over steps. */

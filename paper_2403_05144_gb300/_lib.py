@@ -101,6 +101,7 @@ SIGNATURES = [
     ("perk_selftest_math", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     ("perk_step_profiled", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.POINTER(PerkKernelTimes)]),
     ("perk_measure_fp64", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("perk_set_stage_fusion", C.c_int, [C.c_void_p, C.c_int]),
     ("perk_workspace_bytes", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_size_t)]),
     ("perk_bind_workspace", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("perk_compute_dt_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_double,

@@ -344,6 +344,16 @@ struct perk_ctx {
   DevBuf<int> d_flag;
   DevBuf<double> d_logtab;   // table of the volume kernel's logarithm
 
+  // one launch per stage (k_stage: faces and volume together; perk_set_stage_fusion) where the
+  // equations allow it; its work counters and per-face stamps.  Off by default: on GB300 the two
+  // launches are as fast (the stage is FP64-bound either way; KH 3,904 cells 0.669 against 0.674
+  // ms/step, 114,688 cells 6.26 against 6.22)
+  bool fuse_stage = false;
+  DevBuf<unsigned long long> d_ctl, d_stamp;
+  bool stage_fused() const {
+    return fuse_stage && !viscous() && prob.shock_capturing == PERK_SHOCK_OFF;
+  }
+
   // graph of one step (graph_valid: matches the current mesh, tableau and buffers)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -403,7 +413,7 @@ void for_each_buffer(perk_ctx* c, F&& f) {
   f(c->d_flag); f(c->d_logtab); f(c->d_map); f(c->d_eta); f(c->d_surf_d); f(c->d_Kall); f(c->d_Kpat); f(c->d_g);
   f(c->d_lamK1); f(c->d_lamKa); f(c->d_lamKb); f(c->d_wsurf); f(c->d_q); f(c->d_vsurf);
   f(c->d_cells); f(c->d_newcells); f(c->d_key); f(c->d_des); f(c->d_off); f(c->d_cnt_if); f(c->d_cnt_mort);
-  f(c->d_off_if); f(c->d_off_mort); f(c->d_info);
+  f(c->d_off_if); f(c->d_off_mort); f(c->d_info); f(c->d_ctl); f(c->d_stamp);
 }
 
 // The buffers a caller-bound workspace holds, in layout order, with their sizes (elements of
@@ -426,6 +436,7 @@ void for_each_workspace_buffer(perk_ctx* c, int64_t cells, F&& f) {
   f(c->d_map, 5 * n); f(c->d_E, (size_t)MAX_S); f(c->d_minmax, (size_t)2); f(c->d_flag, (size_t)1);
   f(c->d_cells, n); f(c->d_newcells, n); f(c->d_key, n); f(c->d_des, n); f(c->d_off, n + 1);
   f(c->d_cnt_if, n); f(c->d_cnt_mort, n); f(c->d_off_if, n); f(c->d_off_mort, n); f(c->d_info, (size_t)8);
+  f(c->d_ctl, (size_t)MAX_S + 1); f(c->d_stamp, 4 * n);
 }
 
 // a mesh-sized buffer for n entries: a quarter of headroom when the library allocates it (the
@@ -766,6 +777,9 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
   }
   // per-block minima of the step-size reduction: its grid is capped at DT_MAX_BLOCKS blocks
   PERK_CUDA(ctx, ctx->d_block_min.ensure((size_t)DT_MAX_BLOCKS));
+  // face stamps of the fused stage kernel: zero is older than any launch
+  PERK_CUDA(ctx, ctx->d_stamp.ensure(4 * ne));
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_stamp.p, 0, 4 * ne * sizeof(unsigned long long), ctx->stream));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
                                  ctx->stream));
   if (!ctx->h_if.empty())
@@ -929,14 +943,23 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
     sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
     sa.dt = ctx->d_dt.p;
     sa.member = ctx->n_members > 1 ? ctx->d_member.p : nullptr;
-    TIMED(ctx, timer, st, 0,
-          launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
-                       ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     const bool last = (i == S - 1);
     if (last && !Kall) K_before_last = Kbuf[prev];
     UpdateArgs chk = ua;
     chk.Kp = K_before_last;
     const bool visc = ctx->viscous();
+    if (ctx->stage_fused()) {
+      TIMED(ctx, timer, st, 1,
+            launch_stage(st, i, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p,
+                         ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length,
+                         sa, ctx->d_surf.p, stage_out(i, cur), last ? &chk : nullptr, ctx->d_logtab.p,
+                         ctx->d_ctl.p, ctx->d_stamp.p, ctx->d_flag.p));
+      prev = cur;
+      continue;
+    }
+    TIMED(ctx, timer, st, 0,
+          launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
+                       ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     TIMED(ctx, timer, st, 1,
           launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
                         ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, stage_out(i, cur),
@@ -951,6 +974,7 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
     prev = cur;
   }
   ua.Kp = K_before_last;
+  ua.stage_ctl = ctx->stage_fused() ? ctx->d_ctl.p : nullptr;
   TIMED(ctx, timer, st, 2, launch_commit(st, ctx->n_elem, ua, stage_out(S - 1, cur), ctx->d_dt.p, d_U));
   return PERK_OK;
 }
@@ -993,15 +1017,17 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   ctx->ops = build_ops(prob->gamma, prob->surface_flux, prob->shock_capturing, prob->alpha_max);
   for_each_buffer(ctx, [ctx](auto& b) { b.allocs = &ctx->counters.device_allocations; });
   device_sm_count();   // cached before any graph capture
+  stage_resident_blocks();
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
       ctx->d_logtab.ensure(2 * LOG_TABLE_SIZE) != cudaSuccess ||
       ctx->d_counts.ensure(6 * MAX_S) != cudaSuccess || ctx->d_minmax.ensure(2) != cudaSuccess ||
-      ctx->d_dt_out.ensure(1) != cudaSuccess) {
+      ctx->d_dt_out.ensure(1) != cudaSuccess || ctx->d_ctl.ensure(MAX_S + 1) != cudaSuccess) {
     perk_destroy(ctx);
     return PERK_E_CUDA;
   }
   cudaMemset(ctx->d_flag.p, 0, sizeof(int));
+  cudaMemset(ctx->d_ctl.p, 0, (MAX_S + 1) * sizeof(unsigned long long));
   {
     const std::vector<double> t = log_table();
     cudaMemcpy(ctx->d_logtab.p, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -1761,7 +1787,19 @@ perk_status perk_check(perk_ctx* ctx) {
     PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), ctx->stream));
     PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->counters.rejected_steps_checked += 1;
+    if (flag & 2)
+      return fail(ctx, PERK_E_TIMEOUT, "a stage's volume work gave up waiting for its face fluxes; the step was "
+                                       "not committed");
     return fail(ctx, PERK_E_NONFINITE, "a step produced a non-admissible state and was not committed");
+  }
+  return PERK_OK;
+}
+
+perk_status perk_set_stage_fusion(perk_ctx* ctx, int enabled) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (ctx->fuse_stage != (enabled != 0)) {
+    ctx->fuse_stage = enabled != 0;
+    drop_graph(ctx);
   }
   return PERK_OK;
 }
@@ -2249,6 +2287,8 @@ static perk_status adapt_commit_device(perk_ctx* ctx, const double* d_Uold, doub
     PERK_CUDA(ctx, grow(ctx->d_q, mm * 128));
     PERK_CUDA(ctx, grow(ctx->d_vsurf, mm * 64));
   }
+  PERK_CUDA(ctx, grow(ctx->d_stamp, 4 * mm));
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_stamp.p, 0, 4 * mm * sizeof(unsigned long long), st));
   PERK_CUDA(ctx, launch_amr_leaves(st, n, ctx->d_cells.p, ctx->d_des.p, ctx->d_off.p, ctx->d_newcells.p,
                                    ctx->d_key.p, ctx->d_map.p));
   PERK_CUDA(ctx, launch_transfer(st, m, ctx->d_map.p, d_Uold, ctx->ops, d_Unew));

@@ -23,6 +23,9 @@ constexpr int DT_MAX_BLOCKS = 1024;   // its grid cap (grid-stride), the size of
 // Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount), looked up
 // once per device and cached; grid caps of the grid-stride kernels are multiples of it.
 int device_sm_count();
+// Blocks of the fused stage kernel the current device holds at once (0 if unknown), cached per
+// device; looked up when a context is created.
+int stage_resident_blocks();
 
 // Reference-element operators, computed on the host once per context.
 struct Ops {
@@ -85,6 +88,7 @@ struct UpdateArgs {
   const double* Kp;
   int* flag;              // raised (set to 1) when any new state is not admissible
   const int32_t* member;  // ensemble member of each element (nullptr: member 0)
+  unsigned long long* stage_ctl;  // fused stage kernels' counters, advanced by the final update (or nullptr)
 };
 
 // ---- reference-element routines for any degree N (perk_host.cpp; host only) ----
@@ -120,6 +124,16 @@ cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t
                           const int32_t* level, const int32_t* method, double inv_len2, const StageArgs& sa,
                           const double* surf, double* K, const UpdateArgs* check, const double* log_table,
                           int elems_per_block = VOL_EPB_DEFAULT);
+
+// One stage in one launch (faces and volume; Euler without shock capturing): ctl[MAX_S + 1] (zero
+// before the first step; the step's final update, with UpdateArgs::stage_ctl = ctl, makes it ready
+// for the next step), stamps[4 * n_elem] (zero, or stamps of earlier launches with the same ctl),
+// err: bit 1 raised if a volume item gives up waiting.
+cudaError_t launch_stage(cudaStream_t st, int stage, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+                         const int4* morts, int64_t n_el, const int32_t* elems, const int32_t* level,
+                         const int32_t* method, double two_over_len, const StageArgs& sa, double* surf, double* K,
+                         const UpdateArgs* check, const double* log_table, unsigned long long* ctl,
+                         unsigned long long* stamps, int* err);
 
 // log_table: [inv_c[128], ln_c[128]] of the volume kernel's logarithm (see perk_kernels.cu)
 constexpr int LOG_TABLE_SIZE = 128;

@@ -1,11 +1,13 @@
 // sm_103a kernels of the P-ERK / DGSEM hot path.
 //
-// One P-ERK stage (Eq. PartitionedRKSystem; Sec. 3.1) is two launches over the
-// active prefixes of the level-sorted lists:
+// One P-ERK stage (Eq. PartitionedRKSystem; Sec. 3.1) works on the active
+// prefixes of the level-sorted lists:
 //   k_faces   numerical fluxes of the active interfaces and mortars (Sec. 6.2),
 //             stage states formed on the fly at the face nodes;
 //   k_volume  flux-differencing volume integral + surface lifting + Jacobian
-//             of the active elements, stage state formed on the fly.
+//             of the active elements, stage state formed on the fly;
+//   k_stage   both in one launch (Euler, plain volume term): face items first,
+//             volume items waiting per element for their four faces.
 // The step ends with k_commit (guarded final update).  k_partition rebuilds
 // the level partition; k_dt_* reduce the CFL step size (Eq. CFL_DG).
 //
@@ -379,17 +381,34 @@ constexpr int FACE_THREADS = 32;
 constexpr int IF_PER_BLOCK = FACE_THREADS / 4;
 constexpr int MORT_PER_BLOCK = FACE_THREADS / 8;
 
-template <int YS>
-__global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
-                                                         int64_t n_mort, const int4* __restrict__ morts,
-                                                         int64_t if_blocks, const int32_t* __restrict__ method,
-                                                         StageArgs sa, double* __restrict__ surf) {
-  __shared__ double s_half[MORT_PER_BLOCK][2][4][NN];  // [mortar][half][var][node]
-  if (blockIdx.x < if_blocks) {
-    const int64_t idx = (int64_t)blockIdx.x * IF_PER_BLOCK + (threadIdx.x >> 2);
-    const int k = threadIdx.x & 3;
-    if (idx >= n_if) return;
-    const int4 r = ifs[idx];
+// Stamps of the fused stage kernel (k_stage): the launch that last wrote a face's numerical flux.
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// 8 interfaces (4 threads each, one per face node) starting at `first`.  STAMP: after the
+// fluxes are written, each interface's two element faces are stamped with `stamp` (release), so
+// that a volume item of the same launch may read them.
+template <int YS, bool STAMP>
+__device__ __forceinline__ void face_item_interfaces(const Ops& ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                     int64_t first, const StageArgs& sa, double* __restrict__ surf,
+                                                     unsigned long long* stamps, unsigned long long stamp) {
+  const int64_t idx = first + (threadIdx.x >> 2);
+  const int k = threadIdx.x & 3;
+  const bool valid = idx < n_if;
+  int4 r = make_int4(0, 0, 0, 0);
+  if (valid) {
+    r = ifs[idx];
     const int dir = r.z;
     double uL[4], uR[4], f[4];
     stage_state<YS>(sa, r.x, r.w, face_node(2 * dir + 1, k), uL);
@@ -402,11 +421,27 @@ __global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, c
       sL[4 * v] = f[v];
       sR[4 * v] = f[v];
     }
-    return;
   }
-  // mortars
+  if (STAMP) {
+    __threadfence();
+    __syncwarp();
+    if (valid && k == 0) {
+      st_release(stamps + 4 * (int64_t)r.x + 2 * r.z + 1, stamp);
+      st_release(stamps + 4 * (int64_t)r.y + 2 * r.z, stamp);
+    }
+  }
+}
+
+// 4 mortars (8 threads each: half, node) starting at `first`: the large trace interpolated to
+// each half, the flux at the small side's nodes, its L2 projection back onto the large face.
+template <int YS, bool STAMP>
+__device__ __forceinline__ void face_item_mortars(const Ops& ops, int64_t n_mort, const int4* __restrict__ morts,
+                                                  int64_t first, const int32_t* __restrict__ method,
+                                                  const StageArgs& sa, double* __restrict__ surf,
+                                                  double (*s_half)[2][4][NN], unsigned long long* stamps,
+                                                  unsigned long long stamp) {
   const int lm = threadIdx.x >> 3;
-  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * MORT_PER_BLOCK + lm;
+  const int64_t idx = first + lm;
   const int half = (threadIdx.x >> 2) & 1;
   const int k = threadIdx.x & 3;
   const bool valid = idx < n_mort;
@@ -442,7 +477,7 @@ __global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, c
       s_half[lm][half][v][k] = f[v];
     }
   }
-  __syncthreads();
+  __syncwarp();
   if (valid) {
     // projection onto the large face: thread (half, k) produces vars 2*half, 2*half+1 at node k
 #pragma unroll
@@ -457,6 +492,27 @@ __global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, c
       surf[(int64_t)r.x * ELEM + large_face * 16 + 4 * v + k] = acc;
     }
   }
+  if (STAMP) {
+    __threadfence();
+    __syncwarp();
+    if (valid && k == 0) {
+      st_release(stamps + 4 * (int64_t)small + small_face, stamp);
+      if (half == 0) st_release(stamps + 4 * (int64_t)r.x + large_face, stamp);
+    }
+  }
+}
+
+template <int YS>
+__global__ void __launch_bounds__(FACE_THREADS) k_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                         int64_t n_mort, const int4* __restrict__ morts,
+                                                         int64_t if_blocks, const int32_t* __restrict__ method,
+                                                         StageArgs sa, double* __restrict__ surf) {
+  __shared__ double s_half[MORT_PER_BLOCK][2][4][NN];  // [mortar][half][var][node]
+  if (blockIdx.x < if_blocks)
+    face_item_interfaces<YS, false>(ops, n_if, ifs, (int64_t)blockIdx.x * IF_PER_BLOCK, sa, surf, nullptr, 0);
+  else
+    face_item_mortars<YS, false>(ops, n_mort, morts, (int64_t)(blockIdx.x - if_blocks) * MORT_PER_BLOCK, method, sa,
+                                 surf, s_half, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -470,22 +526,64 @@ __device__ __forceinline__ int pair_slot(int a, int b) {  // a < b, slots 0..5
   return (a * (7 - a)) / 2 + b - a - 1;
 }
 
-template <int YS, bool CHECK, int VOL_ELEMS, bool SHOCK>
-__global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
-                                                         const int32_t* __restrict__ level,
-                                                         const int32_t* __restrict__ method, double two_over_len,
-                                                         StageArgs sa, const double* __restrict__ surf,
-                                                         double* __restrict__ K, UpdateArgs ua,
-                                                         const double* __restrict__ log_table) {
-  __shared__ NodeQ s_prim[VOL_ELEMS][NODES];
-  __shared__ double s_flux[VOL_ELEMS][4][NPAIR];
-  __shared__ double s_log[2 * LOG_TABLE];
-  __shared__ double s_u[SHOCK ? VOL_ELEMS : 1][4][NODES];     // stage state (shock capturing)
-  __shared__ double s_eps[SHOCK ? VOL_ELEMS : 1][NODES];      // indicator variable
+// Where a volume item of the fused stage kernel finds its element's face fluxes: the stamps of
+// the face items of the same launch (its faces are done once all four carry `stamp`).
+struct FaceWait {
+  const unsigned long long* stamps;
+  unsigned long long stamp;
+  int* err;   // bit 1 raised if a wait gives up
+};
+constexpr int STAMP_WAIT_LIMIT = 1 << 23;   // polls (about 32 ns apart) before a wait gives up
+
+// waits until the stamp at p reaches v (relaxed polls, then one fence: the face's values were
+// written before its stamp was released); false if the wait gives up
+__device__ __forceinline__ bool wait_stamp(const unsigned long long* p, unsigned long long v) {
+  for (int it = 0; it < STAMP_WAIT_LIMIT; ++it) {
+    if (ld_relaxed(p) == v) {
+      __threadfence();
+      return true;
+    }
+    __nanosleep(32);
+  }
+  return false;
+}
+
+// Shared memory of a volume item (VOL_ELEMS elements, 16 threads each); with shock capturing
+// also the stage state and the indicator variable.
+template <int VOL_ELEMS, bool SHOCK>
+struct VolumeShared {
+  NodeQ prim[VOL_ELEMS][NODES];
+  double flux[VOL_ELEMS][4][NPAIR];
+  double u[VOL_ELEMS][4][NODES];
+  double eps[VOL_ELEMS][NODES];
+};
+template <int VOL_ELEMS>
+struct VolumeShared<VOL_ELEMS, false> {
+  NodeQ prim[VOL_ELEMS][NODES];
+  double flux[VOL_ELEMS][4][NPAIR];
+  double (*u)[4][NODES];    // unused without shock capturing
+  double (*eps)[NODES];
+};
+
+// Volume term of VOL_ELEMS active elements (list slots slot0 ..), their surface lifting and
+// Jacobian; the log table is in s_log.  FUSED: the face fluxes come from face items of the same
+// launch, read once the element's four faces carry the launch's stamp.
+template <int YS, bool CHECK, int VOL_ELEMS, bool SHOCK, bool FUSED>
+__device__ __forceinline__ void volume_item(const Ops& ops, int64_t n, int64_t slot0, const int32_t* __restrict__ elems,
+                                            const int32_t* __restrict__ level, const int32_t* __restrict__ method,
+                                            double two_over_len, const StageArgs& sa,
+                                            const double* __restrict__ surf, double* __restrict__ K,
+                                            const UpdateArgs& ua, const double* __restrict__ log_table,
+                                            double* s_log, VolumeShared<VOL_ELEMS, SHOCK>& sh,
+                                            const FaceWait& fw) {
+  auto& s_prim = sh.prim;
+  auto& s_flux = sh.flux;
+  auto& s_u = sh.u;
+  auto& s_eps = sh.eps;
   const int le = threadIdx.x >> 4;
   const int t = threadIdx.x & 15;
   const int i = t & 3, j = t >> 2;
-  const int64_t slot = (int64_t)blockIdx.x * VOL_ELEMS + le;
+  const int64_t slot = slot0 + le;
   const bool valid = slot < n;
   const int64_t e = valid ? elems[slot] : 0;
   const int m = valid ? method[e] : 0;
@@ -500,7 +598,7 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   }
   // numerical fluxes of the faces through this node (x face at i = 0 or 3, y face at j = 0 or 3)
   double fsx[4] = {0.0, 0.0, 0.0, 0.0}, fsy[4] = {0.0, 0.0, 0.0, 0.0};
-  if (valid) {
+  if (!FUSED && valid) {
     const double* sf = surf + e * ELEM;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -632,6 +730,21 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   }
   if (!valid) return;
 
+  if (FUSED) {
+    // the element's four faces, written by face items of the same launch that were all dispensed
+    // before this item: lane t < 4 of the element watches face t, then the element's lanes meet
+    if (t < 4 && !wait_stamp(fw.stamps + 4 * e + t, fw.stamp)) atomicOr(fw.err, 2);
+    __syncwarp(0xFFFFu << (threadIdx.x & 16));
+    const double* sf = surf + e * ELEM;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (i == 0) fsx[v] = __ldcg(sf + 0 * 16 + 4 * v + j);
+      if (i == 3) fsx[v] = __ldcg(sf + 1 * 16 + 4 * v + j);
+      if (j == 0) fsy[v] = __ldcg(sf + 2 * 16 + 4 * v + i);
+      if (j == 3) fsy[v] = __ldcg(sf + 3 * 16 + 4 * v + i);
+    }
+  }
+
   // surface lifting with the numerical fluxes of the four faces (w_0 = w_N)
   const double iw = ops.inv_w0;
 #pragma unroll
@@ -667,10 +780,100 @@ __global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n
   }
 }
 
+template <int YS, bool CHECK, int VOL_ELEMS, bool SHOCK>
+__global__ void __launch_bounds__(VOL_ELEMS * NODES) k_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
+                                                         const int32_t* __restrict__ level,
+                                                         const int32_t* __restrict__ method, double two_over_len,
+                                                         StageArgs sa, const double* __restrict__ surf,
+                                                         double* __restrict__ K, UpdateArgs ua,
+                                                         const double* __restrict__ log_table) {
+  __shared__ VolumeShared<VOL_ELEMS, SHOCK> sh;
+  __shared__ double s_log[2 * LOG_TABLE];
+  volume_item<YS, CHECK, VOL_ELEMS, SHOCK, false>(ops, n, (int64_t)blockIdx.x * VOL_ELEMS, elems, level, method,
+                                                  two_over_len, sa, surf, K, ua, log_table, s_log, sh, FaceWait{});
+}
+
+// ---------------------------------------------------------------------------
+// One stage in one launch (Euler, the plain volume term): the face items (8 interfaces or 4
+// mortars each) and the volume items (2 elements each) of the stage's active prefixes are one
+// work list, one item per one-warp block.  A volume item computes its flux differencing, then
+// waits for the stamps of its element's four faces (set by the face items with release
+// semantics) before the surface lifting.  Face items never wait.  When every block of the launch
+// can be resident at once (`resident`), block b takes item b of a list that spreads the face
+// items evenly among the volume items, so each SM gets its share of both kinds of work; the
+// blocks a volume item waits for are running.  Otherwise items are dealt faces first by an
+// atomic counter: every face item has then been handed out, to a block already running, before
+// any volume item, so the waits end either way.  The face work runs beside the volume work and
+// the stage needs no second launch.  ctl[stage] counts the stage's dealt items and ctl[MAX_S] the
+// steps; both are advanced by the step's final update (k_commit), so a stamp
+// (steps * MAX_S + stage + 1) names one stage of one step.
+struct StageSync {
+  unsigned long long* ctl;      // [MAX_S] per-stage item counters, then [MAX_S] the step count
+  unsigned long long* stamps;   // [n_elem][4 faces]
+  int* err;                     // bit 1: a wait gave up (the step is then not committed)
+  int stage;
+};
+
+constexpr int STAGE_VE = 2;   // elements per volume item
+
+template <bool CHECK>
+__global__ void __launch_bounds__(FACE_THREADS) k_stage(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                       int64_t n_mort, const int4* __restrict__ morts, int64_t n_el,
+                                                       const int32_t* __restrict__ elems,
+                                                       const int32_t* __restrict__ level,
+                                                       const int32_t* __restrict__ method, double two_over_len,
+                                                       StageArgs sa, double* __restrict__ surf,
+                                                       double* __restrict__ K, UpdateArgs ua,
+                                                       const double* __restrict__ log_table, StageSync sync,
+                                                       bool resident) {
+  static_assert(STAGE_VE * NODES == FACE_THREADS, "one warp per work item");
+  __shared__ unsigned long long s_item, s_launch;
+  __shared__ double s_log[2 * LOG_TABLE];
+  __shared__ union {
+    VolumeShared<STAGE_VE, false> vol;
+    double half[MORT_PER_BLOCK][2][4][NN];
+  } sh;
+  const int64_t if_items = (n_if + IF_PER_BLOCK - 1) / IF_PER_BLOCK;
+  const int64_t face_items = if_items + (n_mort + MORT_PER_BLOCK - 1) / MORT_PER_BLOCK;
+  const int64_t items = face_items + (n_el + STAGE_VE - 1) / STAGE_VE;
+  const int64_t face_items0 = face_items;
+  if (threadIdx.x == 0) {
+    if (resident) {
+      // every block of the launch is resident at once: block b takes item b of a list in which
+      // the face items are spread evenly over the volume items (F of T items are faces; block b is
+      // a face block when floor((b + 1) F / T) > floor(b F / T)), so every SM gets its share of both
+      const int64_t b = blockIdx.x, F = face_items0, T = (int64_t)gridDim.x;
+      const int64_t f0 = b * F / T, f1 = (b + 1) * F / T;
+      s_item = f1 > f0 ? (unsigned long long)f0 : (unsigned long long)(F + b - f1);
+    } else {
+      s_item = atomicAdd(sync.ctl + sync.stage, 1ull);
+    }
+    s_launch = *(volatile unsigned long long*)(sync.ctl + MAX_S);
+  }
+  __syncwarp();
+  const int64_t item = (int64_t)s_item;
+  const unsigned long long stamp = s_launch * MAX_S + sync.stage + 1;
+  if (item < if_items) {
+    face_item_interfaces<Y_COMBINE, true>(ops, n_if, ifs, item * IF_PER_BLOCK, sa, surf, sync.stamps, stamp);
+  } else if (item < face_items) {
+    face_item_mortars<Y_COMBINE, true>(ops, n_mort, morts, (item - if_items) * MORT_PER_BLOCK, method, sa, surf,
+                                       sh.half, sync.stamps, stamp);
+  } else if (item < items) {
+    volume_item<Y_COMBINE, CHECK, STAGE_VE, false, true>(ops, n_el, (item - face_items) * STAGE_VE, elems, level,
+                                                         method, two_over_len, sa, surf, K, ua, log_table, s_log,
+                                                         sh.vol, FaceWait{sync.stamps, stamp, sync.err});
+  }
+}
+
 // Guarded final update U += dt (b1 K1 + bp Kp + bs Ks), skipped entirely when
 // the admissibility flag is raised.
 __global__ void k_commit(int64_t n2, UpdateArgs ua, const double2* __restrict__ Ks, const double* dtp,
                          double2* __restrict__ U) {
+  if (ua.stage_ctl && blockIdx.x == 0 && threadIdx.x == 0) {
+    // the fused stage kernels of this step are done: their item counters restart, the step count advances
+    for (int s = 0; s < MAX_S; ++s) ua.stage_ctl[s] = 0;
+    ua.stage_ctl[MAX_S] += 1;
+  }
   if (*ua.flag != 0) return;
   const double2* K1 = reinterpret_cast<const double2*>(ua.K1);
   const double2* Kp = reinterpret_cast<const double2*>(ua.Kp);
@@ -1084,6 +1287,49 @@ cudaError_t launch_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t 
   else
     k_faces<Y_COMBINE><<<(unsigned)(bi + bm), FACE_THREADS, 0, st>>>(ops, n_if, ifs, n_mort, morts, bi, method, sa,
                                                                      surf);
+  return cudaGetLastError();
+}
+
+// blocks of k_stage the current device holds at once (occupancy x SMs), cached per device
+int stage_resident_blocks() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  int per_sm = 0, per_sm2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<false>, FACE_THREADS, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_stage<true>, FACE_THREADS, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  n = std::min(per_sm, per_sm2) * device_sm_count();
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+cudaError_t launch_stage(cudaStream_t st, int stage, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
+                         const int4* morts, int64_t n_el, const int32_t* elems, const int32_t* level,
+                         const int32_t* method, double two_over_len, const StageArgs& sa, double* surf, double* K,
+                         const UpdateArgs* check, const double* log_table, unsigned long long* ctl,
+                         unsigned long long* stamps, int* err) {
+  if (stage < 0 || stage >= MAX_S) return cudaErrorInvalidValue;
+  if (ops.shock != PERK_SHOCK_OFF) return cudaErrorInvalidValue;
+  const int64_t items = (n_if + IF_PER_BLOCK - 1) / IF_PER_BLOCK + (n_mort + MORT_PER_BLOCK - 1) / MORT_PER_BLOCK +
+                        (n_el + STAGE_VE - 1) / STAGE_VE;
+  if (items == 0) return cudaSuccess;
+  UpdateArgs ua{};
+  if (check) ua = *check;
+  const StageSync sync{ctl, stamps, err, stage};
+  const bool resident = items <= stage_resident_blocks();
+  if (check)
+    k_stage<true><<<(unsigned)items, FACE_THREADS, 0, st>>>(ops, n_if, ifs, n_mort, morts, n_el, elems, level, method,
+                                                             two_over_len, sa, surf, K, ua, log_table, sync, resident);
+  else
+    k_stage<false><<<(unsigned)items, FACE_THREADS, 0, st>>>(ops, n_if, ifs, n_mort, morts, n_el, elems, level,
+                                                              method, two_over_len, sa, surf, K, ua, log_table, sync,
+                                                              resident);
   return cudaGetLastError();
 }
 
