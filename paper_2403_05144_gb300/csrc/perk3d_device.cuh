@@ -42,12 +42,12 @@ __device__ __forceinline__ void stage_state3(const StageArgs& sa, int64_t e, int
     const double dt = sa.dt[0];
 #pragma unroll
     for (int v = 0; v < 5; ++v) y[v] = __ldg(sa.U + base + v * ND);
-    if (c.alpha != 0.0) {
+    if (__double_as_longlong(c.alpha) != 0) {   // integer test, off the FP64 pipe
       const double da = dt * c.alpha;
 #pragma unroll
       for (int v = 0; v < 5; ++v) y[v] = fma(da, __ldg(sa.K1 + base + v * ND), y[v]);
     }
-    if (c.beta != 0.0) {
+    if (__double_as_longlong(c.beta) != 0) {
       const double db = dt * c.beta;
 #pragma unroll
       for (int v = 0; v < 5; ++v) y[v] = fma(db, __ldg(sa.Kp + base + v * ND), y[v]);

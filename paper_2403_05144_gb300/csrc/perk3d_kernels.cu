@@ -28,6 +28,7 @@ namespace perk3 {
 using perk::LOG_TABLE;
 using perk::dbits;
 using perk::series_only;
+using perk::near_pair;
 using perk::log_tab;
 using perk::rcp_nr;
 using perk::series_2A;
@@ -78,8 +79,8 @@ __device__ __forceinline__ NodeQ3 node_q3(const double u[5], double gm1, const d
 __device__ __forceinline__ void ec_flux_q3(const NodeQ3& A, const NodeQ3& B, int dir, double inv_gm1, double f[5]) {
   const double dr = B.rho - A.rho, sr = A.rho + B.rho;
   const double db = B.beta - A.beta, sb = A.beta + B.beta;
-  const bool ser_r = fabs(dr) < 0.03 * sr;
-  const bool ser_b = fabs(db) < 0.03 * sb;
+  const bool ser_r = near_pair(A.rho, B.rho);
+  const bool ser_b = near_pair(A.beta, B.beta);
   const double den_r = ser_r ? sr : B.lnrho - A.lnrho;
   const double den_b = ser_b ? sb : db;
   const double r = rcp_nr(den_r * den_b);

@@ -43,9 +43,9 @@ __device__ __forceinline__ void state(const StageArgs& sa, int64_t e, int m, int
     const StageCoef c = sa.coef[m];
     const double dt = sa.dt[sa.member ? sa.member[e] : 0];
     for (int v = 0; v < 4; ++v) y[v] = sa.U[base + v * NODES];
-    if (c.alpha != 0.0)
+    if (__double_as_longlong(c.alpha) != 0)
       for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.alpha, sa.K1[base + v * NODES], y[v]);
-    if (c.beta != 0.0) {
+    if (__double_as_longlong(c.beta) != 0) {
       const double* Kp = coupled_stage(sa, c);
       for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, Kp[base + v * NODES], y[v]);
     }

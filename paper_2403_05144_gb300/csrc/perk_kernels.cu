@@ -122,8 +122,8 @@ __device__ __forceinline__ NodeQ node_q(const double u[4], double gm1, const dou
 __device__ __forceinline__ void ec_flux_q(const NodeQ& A, const NodeQ& B, int dir, double inv_gm1, double f[4]) {
   const double dr = B.rho - A.rho, sr = A.rho + B.rho;
   const double db = B.beta - A.beta, sb = A.beta + B.beta;
-  const bool ser_r = fabs(dr) < 0.03 * sr;
-  const bool ser_b = fabs(db) < 0.03 * sb;
+  const bool ser_r = near_pair(A.rho, B.rho);
+  const bool ser_b = near_pair(A.beta, B.beta);
   const double den_r = ser_r ? sr : B.lnrho - A.lnrho;
   const double den_b = ser_b ? sb : db;
   const double r = rcp_nr(den_r * den_b);
@@ -361,12 +361,12 @@ __device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int 
     const double dt = sa.dt[sa.member ? sa.member[e] : 0];
 #pragma unroll
     for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.U + base + v * NODES);
-    if (c.alpha != 0.0) {
+    if (__double_as_longlong(c.alpha) != 0) {   // integer test, off the FP64 pipe
       const double da = dt * c.alpha;
 #pragma unroll
       for (int v = 0; v < 4; ++v) y[v] = fma(da, __ldg(sa.K1 + base + v * NODES), y[v]);
     }
-    if (c.beta != 0.0) {
+    if (__double_as_longlong(c.beta) != 0) {
       const double db = dt * c.beta;
       const double* Kp = coupled_stage(sa, c);
 #pragma unroll
