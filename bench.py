@@ -734,7 +734,7 @@ def run_perk(args) -> None:
                               "mortars": mortars if fused else 0, "algorithmic_flops": alg_flops,
                               "source": "oracle operation counter (add/mul 1, divide, square root and logarithm "
                                         "1 each; 48 symmetric pairs; subsonic face fluxes)"},
-                     "issue_slot_frac": slot_rate / fma_flops,
+                     "issue_slot_frac": None if fused else slot_rate / fma_flops,
                      "issue_slot_note": f"{VOL_SLOTS_PER_ELEM} FP64 issue slots per element-stage in the "
                                         "kernel's own formulation, each counted as an FMA (2 flops), "
                                         "over the measured FMA peak: how busy the FP64 issue slots are",

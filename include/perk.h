@@ -258,10 +258,9 @@ perk_status perk_check(perk_ctx* ctx);
  * Euler equations with the plain volume term, the numerical fluxes of a stage's active
  * interfaces and mortars and the volume terms of its active elements run as one kernel whose
  * work items (faces first) are dealt in order to its blocks; each element's volume work waits,
- * with a bounded wait, for its four face fluxes before the surface lifting.  Off by default
- * (two launches per stage: face fluxes, then volume terms); enabled != 0 selects one launch.
- * Results are bitwise the same either way.  Other equations and shock capturing always use two
- * launches. */
+ * with a bounded wait, for its four face fluxes before the surface lifting.  On by default;
+ * enabled = 0 selects two launches per stage (face fluxes, then volume terms).  Results are
+ * bitwise the same either way.  Other equations and shock capturing always use two launches. */
 perk_status perk_set_stage_fusion(perk_ctx* ctx, int enabled);
 
 /* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed

@@ -17,6 +17,7 @@
 
 #include "perk.h"
 #include "perk_internal.h"
+#include "perk_devmath.cuh"
 
 namespace perk {
 namespace ad {
@@ -226,8 +227,7 @@ __device__ __forceinline__ NodeQ<T> node_q(const T u[4], double gm1, const doubl
 
 template <class T>
 __device__ __forceinline__ T series_H(const T& u) {
-  T r = cst_like(u, -5098.0 / 467775.0);
-  r = fma_(r, u, cst_like(u, -214.0 / 14175.0));
+  T r = cst_like(u, -214.0 / 14175.0);
   r = fma_(r, u, cst_like(u, -22.0 / 945.0));
   r = fma_(r, u, cst_like(u, -2.0 / 45.0));
   r = fma_(r, u, cst_like(u, -1.0 / 6.0));
@@ -235,8 +235,7 @@ __device__ __forceinline__ T series_H(const T& u) {
 }
 template <class T>
 __device__ __forceinline__ T series_2A(const T& u) {
-  T r = cst_like(u, 2.0 / 11.0);
-  r = fma_(r, u, cst_like(u, 2.0 / 9.0));
+  T r = cst_like(u, 2.0 / 9.0);
   r = fma_(r, u, cst_like(u, 2.0 / 7.0));
   r = fma_(r, u, cst_like(u, 2.0 / 5.0));
   r = fma_(r, u, cst_like(u, 2.0 / 3.0));
@@ -247,8 +246,8 @@ template <class T>
 __device__ __forceinline__ void ec_flux(const NodeQ<T>& A, const NodeQ<T>& B, int dir, double inv_gm1, T f[4]) {
   const T dr = B.rho - A.rho, sr = A.rho + B.rho;
   const T db = B.beta - A.beta, sb = A.beta + B.beta;
-  const bool ser_r = fabs(val(dr)) < 0.03 * val(sr);
-  const bool ser_b = fabs(val(db)) < 0.03 * val(sb);
+  const bool ser_r = near_pair(val(A.rho), val(B.rho));
+  const bool ser_b = near_pair(val(A.beta), val(B.beta));
   const T den_r = ser_r ? sr : B.lnrho - A.lnrho;
   const T den_b = ser_b ? sb : db;
   const T r = rcp_(den_r * den_b);
@@ -374,9 +373,9 @@ __device__ __forceinline__ void stage_y(const StageArgs& sa, const int32_t* meth
     const StageCoef c = sa.coef ? sa.coef[method[e]] : StageCoef{0.0, 0.0, 0, 0};
     const double dt = sa.dt[sa.member ? sa.member[e] : 0];
     for (int v = 0; v < 4; ++v) y[v] = sa.U[base + v * NODES];
-    if (c.alpha != 0.0)
+    if (__double_as_longlong(c.alpha) != 0)
       for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.alpha, sa.K1[base + v * NODES], y[v]);
-    if (c.beta != 0.0) {
+    if (__double_as_longlong(c.beta) != 0) {
       const double* Kp = coupled_stage(sa, c);
       for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, Kp[base + v * NODES], y[v]);
     }
@@ -559,15 +558,13 @@ enum { Q_RHO = 0, Q_LNRHO, Q_BETA, Q_LNBETA, Q_V1, Q_V2, Q_HV1, Q_HV2, Q_HP, NQ 
 
 // derivatives of the log-mean series in u
 __device__ __forceinline__ double series_H_d(double u) {   // H'(u)
-  double r = 5.0 * (-5098.0 / 467775.0);
-  r = fma(r, u, 4.0 * (-214.0 / 14175.0));
+  double r = 4.0 * (-214.0 / 14175.0);
   r = fma(r, u, 3.0 * (-22.0 / 945.0));
   r = fma(r, u, 2.0 * (-2.0 / 45.0));
   return fma(r, u, -1.0 / 6.0);
 }
 __device__ __forceinline__ double series_2A_d(double u) {  // (2A)'(u)
-  double r = 5.0 * (2.0 / 11.0);
-  r = fma(r, u, 4.0 * (2.0 / 9.0));
+  double r = 4.0 * (2.0 / 9.0);
   r = fma(r, u, 3.0 * (2.0 / 7.0));
   r = fma(r, u, 2.0 * (2.0 / 5.0));
   return fma(r, u, 2.0 / 3.0);
@@ -581,8 +578,8 @@ __device__ __forceinline__ void ec_flux_rev(const NodeQ<double>& A, const NodeQ<
   // forward
   const double dr = B.rho - A.rho, sr = A.rho + B.rho;
   const double db = B.beta - A.beta, sb = A.beta + B.beta;
-  const bool ser_r = fabs(dr) < 0.03 * sr;
-  const bool ser_b = fabs(db) < 0.03 * sb;
+  const bool ser_r = near_pair(A.rho, B.rho);
+  const bool ser_b = near_pair(A.beta, B.beta);
   const double den_r = ser_r ? sr : B.lnrho - A.lnrho;
   const double den_b = ser_b ? sb : db;
   const double r = rcp_val(den_r * den_b);
@@ -1095,23 +1092,43 @@ __global__ void k_vjp_gather(int64_t n, const int32_t* __restrict__ method, int 
 // adjoint of the stage combination, with gq = J(Y_i)^T lam_i formed as in
 // k_vjp_gather: lamU += gq; lamK1 += dt alpha gq; lamKp (+)= dt beta gq
 // (lamKp may alias lamK1; assign_p: lamKp receives its first contribution, no prior zeroing)
-__global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ method, int min_member,
-                            const StageCoef* __restrict__ coef, double dt, const double* __restrict__ g,
-                            const double* __restrict__ gsurf, double* __restrict__ lamU,
+// face_gather that also clears the entries it read (each face entry belongs to one node), so that
+// the face adjoints start from zero at the next stage without a separate clearing pass
+__device__ __forceinline__ double face_gather_clear(double* __restrict__ gs, int c, int t) {
+  const int i = t & 3, j = t >> 2;
+  double o = 0.0;
+  if (i == 0) { o += gs[0 * 16 + 4 * c + j]; gs[0 * 16 + 4 * c + j] = 0.0; }
+  if (i == 3) { o += gs[1 * 16 + 4 * c + j]; gs[1 * 16 + 4 * c + j] = 0.0; }
+  if (j == 0) { o += gs[2 * 16 + 4 * c + i]; gs[2 * 16 + 4 * c + i] = 0.0; }
+  if (j == 3) { o += gs[3 * 16 + 4 * c + i]; gs[3 * 16 + 4 * c + i] = 0.0; }
+  return o;
+}
+
+// Over the elements elems[0 .. n) of the stage's halo (the active elements and their face
+// neighbours: every element whose volume or face adjoint can be nonzero), add the gathered
+// adjoint gq to lamU and the stage combination's shares to lamK1 and lamKp (assigned or added);
+// the face adjoints read are cleared.  Elements outside the halo receive nothing at this stage,
+// and their lamKp entries are read later only where the element is active, which it is not at
+// any earlier stage.
+__global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ elems, const int32_t* __restrict__ method,
+                            int min_member, const StageCoef* __restrict__ coef, double dt,
+                            const double* __restrict__ g, double* __restrict__ gsurf, double* __restrict__ lamU,
                             double* __restrict__ lamK1, double* lamKp, int assign_p) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = q / ELEM;
-    const int r = (int)(q - e * ELEM);
+    const int64_t slot = q / ELEM;
+    const int r = (int)(q - slot * ELEM);
+    const int64_t e = elems[slot];
     const int m = method[e];
-    const double gq = (m >= min_member ? g[q] : 0.0) + face_gather(gsurf + e * ELEM, r >> 4, r & 15);
-    lamU[q] += gq;
+    const double gq = (m >= min_member ? g[e * ELEM + r] : 0.0) + face_gather_clear(gsurf + e * ELEM, r >> 4, r & 15);
+    const int64_t qe = e * ELEM + r;
+    lamU[qe] += gq;
     if (coef) {
       const StageCoef c = coef[m];
       if (lamKp == lamK1) {
-        lamK1[q] += dt * (c.alpha + c.beta) * gq;
+        lamK1[qe] += dt * (c.alpha + c.beta) * gq;
       } else {
-        lamK1[q] += dt * c.alpha * gq;
-        lamKp[q] = assign_p ? dt * c.beta * gq : lamKp[q] + dt * c.beta * gq;
+        lamK1[qe] += dt * c.alpha * gq;
+        lamKp[qe] = assign_p ? dt * c.beta * gq : lamKp[qe] + dt * c.beta * gq;
       }
     }
   }
@@ -1137,10 +1154,11 @@ static unsigned ew_blocks(int64_t n) {
   return (unsigned)(b > cap ? cap : (b < 1 ? 1 : b));
 }
 
-cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const StageCoef* coef,
-                             double dt, const double* g, const double* gsurf, double* lamU, double* lamK1,
-                             double* lamKp, int assign_p) {
-  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, method, min_member, coef, dt, g, gsurf, lamU, lamK1, lamKp,
+cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* elems, const int32_t* method, int min_member,
+                             const StageCoef* coef, double dt, const double* g, double* gsurf, double* lamU,
+                             double* lamK1, double* lamKp, int assign_p) {
+  if (n <= 0) return cudaSuccess;
+  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, elems, method, min_member, coef, dt, g, gsurf, lamU, lamK1, lamKp,
                                                 assign_p);
   return cudaGetLastError();
 }
@@ -1167,9 +1185,11 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
 cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs,
                              int64_t n_mort, const int4* morts, int64_t n_all, const int32_t* level,
                              const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
-                             const double* lam, const double* logt, double* gsurf) {
-  cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
-  if (e != cudaSuccess) return e;
+                             const double* lam, const double* logt, double* gsurf, bool clear) {
+  if (clear) {
+    cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t bi = (n_if + ad::FREV_IF - 1) / ad::FREV_IF, bm = (n_mort + ad::FREV_MORT - 1) / ad::FREV_MORT;
   if (bi + bm == 0) return cudaSuccess;
   if (ysrc == Y_GIVEN)

@@ -345,10 +345,9 @@ struct perk_ctx {
   DevBuf<double> d_logtab;   // table of the volume kernel's logarithm
 
   // one launch per stage (k_stage: faces and volume together; perk_set_stage_fusion) where the
-  // equations allow it; its work counters and per-face stamps.  Off by default: on GB300 the two
-  // launches are as fast (the stage is FP64-bound either way; KH 3,904 cells 0.669 against 0.674
-  // ms/step, 114,688 cells 6.26 against 6.22)
-  bool fuse_stage = false;
+  // equations allow it; its work counters and per-face stamps.  On by default: on GB300 it is the
+  // faster form (KH 3,904 cells 0.603 against 0.618 ms/step, 114,688 cells 5.53 against 5.58)
+  bool fuse_stage = true;
   DevBuf<unsigned long long> d_ctl, d_stamp;
   bool stage_fused() const {
     return fuse_stage && !viscous() && prob.shock_capturing == PERK_SHOCK_OFF;
@@ -1898,6 +1897,7 @@ static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, 
   ua.Kp = K + (size_t)(ctx->S > 1 ? ctx->S - 2 : 0) * nd;   // K_{S-1}
   ua.flag = ctx->d_flag.p;
   const int n_stages = d_U ? ctx->S : ctx->S - 1;
+  const bool fused = d_U && ctx->stage_fused();
   for (int i = 0; i < n_stages; ++i) {
     StageArgs sa{};
     sa.U = d_Un;
@@ -1906,12 +1906,22 @@ static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, 
     sa.coef = ctx->d_coef.p + (size_t)i * MAX_R;
     sa.dt = ctx->d_dt.p;
     const bool check = d_U && i == ctx->S - 1;
+    // one launch per stage only when the final update follows (it restarts the stage counters)
+    if (fused) {
+      PERK_CUDA(ctx, launch_stage(st, i, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
+                                  ctx->d_mort_sorted.p, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
+                                  ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, K + (size_t)i * nd,
+                                  check ? &ua : nullptr, ctx->d_logtab.p, ctx->d_ctl.p, ctx->d_stamp.p,
+                                  ctx->d_flag.p));
+      continue;
+    }
     PERK_CUDA(ctx, launch_faces(st, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i],
                                 ctx->d_mort_sorted.p, ctx->d_method.p, sa, ctx->d_surf.p));
     PERK_CUDA(ctx, launch_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
                                  ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, K + (size_t)i * nd,
                                  check ? &ua : nullptr, ctx->d_logtab.p, ctx->vol_epb));
   }
+  ua.stage_ctl = fused ? ctx->d_ctl.p : nullptr;
   if (d_U) PERK_CUDA(ctx, launch_commit(st, ctx->n_elem, ua, K + (size_t)(ctx->S - 1) * nd, ctx->d_dt.p, d_U));
   return PERK_OK;
 }
@@ -1937,6 +1947,8 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
   double* lam_cur = ctx->d_lamKa.p;    // adjoint of K_i at the current stage i
   double* lam_prev = ctx->d_lamKb.p;   // adjoint of K_{i-1}, being accumulated
   double* lamK1 = ctx->d_lamK1.p;
+  // face adjoints start from zero; each stage's accumulation clears what it gathers
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_surf_d.p, 0, nd * sizeof(double), st));
   if (S == 1) {
     PERK_CUDA(ctx, launch_adj_seed(st, ctx->n_elem, dt, 0.0, 0.0, b1 + bp + bs, d_lam_np1, d_lam_n, lam_prev, nullptr,
                                    lamK1));
@@ -1962,21 +1974,23 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
     PERK_CUDA(ctx, launch_vjp_faces(ctx->aux_stream, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p,
                                     ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->n_elem, ctx->d_level.p,
                                     ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p,
-                                    ctx->d_surf_d.p));
+                                    ctx->d_surf_d.p, false));
     PERK_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux_stream));
     PERK_CUDA(ctx, launch_vjp_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
                                      ctx->d_method.p, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p));
     PERK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    // the stage's halo: its active elements and their face neighbours (a prefix of the sorted list)
+    const int64_t halo = ctx->halo_el[i];
     if (i == 0) {
-      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, mm, nullptr, dt, ctx->d_g.p, ctx->d_surf_d.p,
-                                      d_lam_n, nullptr, nullptr, 0));
+      PERK_CUDA(ctx, launch_adj_accum(st, halo, ctx->d_elem_sorted.p, ctx->d_method.p, mm, nullptr, dt, ctx->d_g.p,
+                                      ctx->d_surf_d.p, d_lam_n, nullptr, nullptr, 0));
     } else {
       // contributions to K_{i-1}: into lamK1 when i - 1 == 0; else into lam_prev, which holds the
       // final-update seed only for K_{S-1} (i == S-1) and is otherwise assigned here
       double* target = (i - 1 == 0) ? lamK1 : lam_prev;
       const int assign = (i - 1 == 0 || i == S - 1) ? 0 : 1;
-      PERK_CUDA(ctx, launch_adj_accum(st, ctx->n_elem, ctx->d_method.p, mm, coef, dt, ctx->d_g.p, ctx->d_surf_d.p,
-                                      d_lam_n, lamK1, target, assign));
+      PERK_CUDA(ctx, launch_adj_accum(st, halo, ctx->d_elem_sorted.p, ctx->d_method.p, mm, coef, dt, ctx->d_g.p,
+                                      ctx->d_surf_d.p, d_lam_n, lamK1, target, assign));
       if (i - 1 > 0) std::swap(lam_cur, lam_prev);   // lam_cur <- adjoint of K_{i-1}
     }
   }

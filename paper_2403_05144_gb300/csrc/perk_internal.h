@@ -180,18 +180,20 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
 // VJP of one partitioned RHS evaluation in three parts: the face adjoints into gsurf (zeroed
 // first), the volume adjoint of the active prefix into g, and the gather g = (active ? g : 0)
 // + face adjoints.  The first two are independent and may run on different streams.
+// (clear: zero gsurf first; otherwise the caller guarantees it is zero)
 cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs,
                              int64_t n_mort, const int4* morts, int64_t n_all, const int32_t* level,
                              const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
-                             const double* lam, const double* logt, double* gsurf);
+                             const double* lam, const double* logt, double* gsurf, bool clear = true);
 cudaError_t launch_vjp_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
                               const int32_t* level, const int32_t* method, double two_over_len,
                               const StageArgs& sa, const double* lam, const double* logt, double* g);
 cudaError_t launch_vjp_gather(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const double* gsurf,
                               double* g);
-cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const StageCoef* coef,
-                             double dt, const double* g, const double* gsurf, double* lamU, double* lamK1,
-                             double* lamKp, int assign_p);
+// over the elements elems[0 .. n) (the stage's halo); clears the face adjoints it gathers
+cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* elems, const int32_t* method, int min_member,
+                             const StageCoef* coef, double dt, const double* g, double* gsurf, double* lamU,
+                             double* lamK1, double* lamKp, int assign_p);
 cudaError_t launch_adj_seed(cudaStream_t st, int64_t n, double dt, double b1, double bp, double bs, const double* lam,
                             double* lamU, double* lamK1, double* lamKp, double* lamKs);
 
