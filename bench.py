@@ -79,6 +79,10 @@ VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
 # algorithmic minimum is the 4 x 512 B read of U_n, K_1, K_{i-1} and the face fluxes (K_i stays in
 # L2 within the launch)
 VOL_DRAM_BYTES_PER_ELEM = 8.077312e6 / 3904
+# DRAM bytes per element-stage of the one-launch stage kernel (face and volume work), measured by
+# ncu on the current kernel (5.943 MB for a fully active stage of the 3,904-cell KH mesh,
+# profiles/k_stage_kelvin_helmholtz_amr_3904cells.md)
+STAGE_DRAM_BYTES_PER_ELEM = 5.943296e6 / 3904
 
 
 AMR_KH = dict(level_min=4, level_max=7, refine_above=0.1, coarsen_below=0.02)
@@ -361,13 +365,19 @@ def equal_error_kh(torch, t_end: float = 0.5) -> dict:
     return out
 
 
-def state_l1(torch, solver, U, ref: np.ndarray, L: float, variables=(0,)) -> float:
-    """(1/|Omega|) sum over the given conserved variables of ||U_v - ref_v||_L1 (LGL quadrature)."""
+def state_l1(torch, solver, U, ref: np.ndarray, L: float, variables=(0,), by_level: bool = False):
+    """(1/|Omega|) sum over the given conserved variables of ||U_v - ref_v||_L1 (LGL quadrature);
+    with by_level also the contributions of the cells of each refinement level."""
     from paper_2403_05144_gb300 import reference_nodes
     _, w = reference_nodes(3)
-    h = L / 2.0 ** solver.cells[:, 0]
+    lev = solver.cells[:, 0]
+    h = L / 2.0 ** lev
     e = np.abs(U.cpu().numpy()[:, list(variables)] - ref[:, list(variables)])
-    return float(np.sum((0.5 * h) ** 2 * np.einsum("evji,j,i->e", e, w, w))) / (L * L)
+    per_cell = (0.5 * h) ** 2 * np.einsum("evji,j,i->e", e, w, w) / (L * L)
+    total = float(np.sum(per_cell))
+    if not by_level:
+        return total
+    return total, {int(l): float(np.sum(per_cell[lev == l])) for l in sorted(set(lev.tolist()))}
 
 
 def equal_error_cfl(torch, wl: dict, t_window: float, variables=(0,), cfl0: float | None = None) -> dict:
@@ -399,12 +409,13 @@ def equal_error_cfl(torch, wl: dict, t_window: float, variables=(0,), cfl0: floa
     ref_run, _ = run_at([S], cfl0, 4)
     ref = ref_run.U.cpu().numpy()
 
-    def err(E, cfl):
+    def err(E, cfl, by_level=False):
         run, n = run_at(E, cfl)
-        return state_l1(torch, run.solver, run.U, ref, wl["L"], variables), n
+        r = state_l1(torch, run.solver, run.U, ref, wl["L"], variables, by_level)
+        return (r[0], n, r[1]) if by_level else (r, n)
 
-    e_full, n_full = err([S], cfl0)
-    e0, n0 = err(wl["E"], cfl0)
+    e_full, n_full, lev_full = err([S], cfl0, True)
+    e0, n0, lev_perk = err(wl["E"], cfl0, True)
     e1, _ = err(wl["E"], 0.5 * cfl0)
     p = math.log(e0 / e1) / math.log(2.0)
     c1 = cfl0 * (e_full / e0) ** (1.0 / p)
@@ -415,8 +426,10 @@ def equal_error_cfl(torch, wl: dict, t_window: float, variables=(0,), cfl0: floa
     return {"window": [0.0, t_window], "mesh": f"{wl['name']}: initially adapted, frozen, {len(cells)} cells",
             "error": "L1 of conserved variables %s against full-RK (S=%d) at a quarter of the CFL-%g step"
                      % (list(variables), S, cfl0),
-            "full_rk": {"cfl": cfl0, "error": e_full, "steps": n_full},
-            "perk_same_cfl": {"cfl": cfl0, "error": e0, "steps": n0, "ratio_to_full_rk": e0 / e_full},
+            "full_rk": {"cfl": cfl0, "error": e_full, "steps": n_full, "error_by_level": lev_full},
+            "perk_same_cfl": {"cfl": cfl0, "error": e0, "steps": n0, "ratio_to_full_rk": e0 / e_full,
+                              "error_by_level": lev_perk,
+                              "member_E_by_level": dict(zip(sorted(lev_perk), sorted(wl["E"])[-len(lev_perk):]))},
             "perk_half_cfl_error": e1, "perk_measured_order": p,
             "perk_equal_error": {"cfl": c2, "error": ec2, "steps": n2, "ratio_to_full_rk": ec2 / e_full}}
 
@@ -719,7 +732,8 @@ def run_perk(args) -> None:
         "equal_error": equal_error,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fma_flops / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / fma_flops,
-                     "traffic": (None if fused else VOL_DRAM_BYTES_PER_ELEM * acc.element_stages / max(vol_launches, 1)),
+                     "traffic": ((STAGE_DRAM_BYTES_PER_ELEM if fused else VOL_DRAM_BYTES_PER_ELEM)
+                                 * acc.element_stages / max(vol_launches, 1)),
                      "traffic_note": "DRAM bytes per launch: ncu bytes per element-stage x element-stages "
                                      "per launch",
                      "kernel": "k_stage (face fluxes and volume terms of a stage in one launch)" if fused
@@ -739,7 +753,7 @@ def run_perk(args) -> None:
                                         "kernel's own formulation, each counted as an FMA (2 flops), "
                                         "over the measured FMA peak: how busy the FP64 issue slots are",
                      "fp64_pipe_active_source": "ncu sm__pipe_fp64_cycles_active in "
-                                                "profiles/k_volume_kelvin_helmholtz_amr_3904cells.md",
+                                                "profiles/k_stage_kelvin_helmholtz_amr_3904cells.md",
                      "cuda_fp64_rates": {"div_per_s": div_s, "log_per_s": log_s}},
         "e2e": {"value": replica_rate(units_e2e, ms_e2e, world), "unit": UNIT,
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
