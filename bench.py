@@ -1267,11 +1267,6 @@ def run_tgv(args) -> None:
                    "amr": {**TGV["amr"], "indicator": "enstrophy", "every_steps": TGV["n_amr"],
                            "in_timed_region": True, "cycles_timed": cycles},
                    "dof_stage_updates_per_step": units / args.steps,
-                   "amr_cycles_in_timed_region": timed_cycles,
-                   "ms_per_step_without_amr": None if ms_no_amr is None else ms_no_amr / args.steps,
-                   "amr_ms_per_cycle": (None if ms_no_amr is None
-                                        else (ms - ms_no_amr) / timed_cycles),
-                   "amr_share_of_step_time": None if ms_no_amr is None else (ms - ms_no_amr) / ms,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"{world} independent replica(s)", "graph": True},
         "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps,
