@@ -434,6 +434,57 @@ def equal_error_cfl(torch, wl: dict, t_window: float, variables=(0,), cfl0: floa
             "perk_equal_error": {"cfl": c2, "error": ec2, "steps": n2, "ratio_to_full_rk": ec2 / e_full}}
 
 
+def cell_means(U: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Cell averages [n, 4] of a nodal DGSEM state by the LGL quadrature."""
+    return 0.25 * np.einsum("evji,j,i->ev", U, w, w)
+
+
+def total_error_kh(torch, t_window: float = 0.5, ref_level: int = 8) -> dict:
+    """Total (spatial + temporal) density error of the P-ERK family and of full-RK at the
+    workload's CFL on the frozen initially adapted KH mesh at t_window, against full-RK on the
+    uniformly refined level-ref_level mesh from the same initial state (cell averages of the
+    reference aggregated onto the coarse cells; L1 over the domain)."""
+    from paper_2403_05144_gb300 import reference_nodes
+    wl = workload("kh")
+    _, w = reference_nodes(3)
+    base = Run(torch, wl, wl["E"])
+    cells, U0 = base.solver.cells.copy(), base.U.clone()
+    frozen = dict(wl, amr=None, cells=cells, init_cycles=0)
+    S = max(wl["E"])
+
+    def run(wl_, E, U_init):
+        r = Run(torch, wl_, E)
+        if U_init is not None:
+            r.U = U_init.clone()
+        n = math.ceil(t_window / r.solver.compute_dt(r.U, wl_["cfl"]))
+        r.dt = t_window / n
+        for _ in range(n):
+            r.step()
+        r.solver.check()
+        return r, n
+
+    fine = dict(wl, amr=None, cells=uniform_cells(ref_level), init_cycles=0)
+    ref_run, n_ref = run(fine, [S], None)
+    ref_means = cell_means(ref_run.U.cpu().numpy(), w)[:, 0]
+    side = 1 << ref_level
+    ref_grid = np.zeros((side, side))
+    for (l, ix, iy), m in zip(ref_run.solver.cells.tolist(), ref_means):
+        ref_grid[iy, ix] = m
+    out = {"reference": f"full-RK S={S} on the uniform level-{ref_level} mesh ({side * side} cells), "
+                        f"{n_ref} steps", "window": [0.0, t_window]}
+    for name, E in (("perk", wl["E"]), ("full_rk", [S])):
+        r, n = run(frozen, E, U0)
+        means = cell_means(r.U.cpu().numpy(), w)[:, 0]
+        err = 0.0
+        for (l, ix, iy), m in zip(r.solver.cells.tolist(), means):
+            k = 1 << (ref_level - l)
+            err += abs(m - ref_grid[iy * k:(iy + 1) * k, ix * k:(ix + 1) * k].mean()) / (1 << (2 * l))
+        out[name] = {"l1_cell_average_density_error": err, "steps": n, "cfl": wl["cfl"]}
+    out["ratio_perk_over_full_rk"] = out["perk"]["l1_cell_average_density_error"] / \
+        out["full_rk"]["l1_cell_average_density_error"]
+    return out
+
+
 def oracle_problem(wl: dict, cells):
     """The oracle's mesh, P-ERK family, member of each cell and RHS for a workload."""
     from oracle.br1 import NavierStokesDGSEM
@@ -690,6 +741,7 @@ def run_perk(args) -> None:
         equal_error = {"vortex": equal_error_vortex(torch)}
     if args.workload == "kh":
         equal_error["kelvin_helmholtz"] = equal_error_kh(torch)
+        equal_error["kelvin_helmholtz_total_error"] = total_error_kh(torch)
     if args.workload in ("kh", "shear"):
         # both methods to t_end at equal temporal error: the family at the CFL where its error on the
         # frozen window equals the full-RK error at the workload's CFL (AMR interval scaled with the
