@@ -552,9 +552,13 @@ __device__ __forceinline__ double lift_coef(int face, double two_over_len, int l
 // ---------------------------------------------------------------------------
 // Reverse (adjoint) sweep of the volume term, written out by hand.
 //
-// Field order of the node quantities and of their adjoints:
-//   0 rho, 1 ln rho, 2 beta = rho/p, 3 ln beta, 4 v1, 5 v2, 6 v1/2, 7 v2/2, 8 p/2
-enum { Q_RHO = 0, Q_LNRHO, Q_BETA, Q_LNBETA, Q_V1, Q_V2, Q_HV1, Q_HV2, Q_HP, NQ };
+// Adjoint fields of a node's quantities.  The half velocities v/2 of the node records enter the
+// flux through the arithmetic means; their adjoints are folded into those of v1 and v2 (a
+// contribution g to v/2 is one of g/2 to v), so that a pair passes seven values per side on to
+// its nodes, and five where both logarithmic means take their series (no logarithm is read).
+//   0 rho, 1 beta = rho/p, 2 v1, 3 v2, 4 p/2, 5 ln rho, 6 ln beta
+enum { F_RHO = 0, F_BETA, F_V1, F_V2, F_HP, F_LNRHO, F_LNBETA, NF };
+constexpr int NF_SER = F_LNRHO;   // fields of a pair whose means both take their series
 
 // derivatives of the log-mean series in u
 __device__ __forceinline__ double series_H_d(double u) {   // H'(u)
@@ -570,11 +574,70 @@ __device__ __forceinline__ double series_2A_d(double u) {  // (2A)'(u)
   return fma(r, u, 2.0 / 3.0);
 }
 
-// Given the adjoint g of the flux f#(A, B) in direction dir, accumulate the
-// adjoints of A's and B's node quantities into gA, gB (the forward
-// intermediates are recomputed; branch decisions as in the forward flux).
+// The part of the reverse sweep shared by both branches of the means: given the adjoint g of the
+// flux f#(A, B) in direction dir and the forward values rho_ln, 1/{{beta}}_ln (ibeta), accumulate
+// the adjoints of the velocities and of p/2 into gA, gB and return those of rho_ln and ibeta.
+__device__ __forceinline__ void ec_flux_rev_common(const NodeQ<double>& A, const NodeQ<double>& B, int dir,
+                                                   double inv_gm1, const double g[4], double rho_ln, double ibeta,
+                                                   double* gA, double* gB, double& g_rho_ln, double& g_ibeta) {
+  const double v1m = A.hv1 + B.hv1, v2m = A.hv2 + B.hv2;
+  const double vnA = dir ? A.v2 : A.v1, vnB = dir ? B.v2 : B.v1;
+  const double vnm = dir ? v2m : v1m;
+  const double frho = rho_ln * vnm;
+  const double kin = fma(A.hv1, B.v1, A.hv2 * B.v2);
+  const double T = fma(ibeta, inv_gm1, kin);
+  // f = (frho, frho v1m + [dir = 0] pm, frho v2m + [dir = 1] pm, frho T + (A.hp vnB + B.hp vnA))
+  const double g_frho = fma(g[3], T, fma(g[2], v2m, fma(g[1], v1m, g[0])));
+  const double g_pm = dir ? g[2] : g[1];
+  const double g_T = g[3] * frho;                  // = adjoint of kin
+  g_ibeta = g_T * inv_gm1;
+  g_rho_ln = g_frho * vnm;
+  gA[F_HP] += fma(g[3], vnB, g_pm);
+  gB[F_HP] += fma(g[3], vnA, g_pm);
+  // half the adjoints of the means v1m, v2m (each mean is (vA + vB)/2)
+  const double hfrho = 0.5 * frho, hrho_ln = 0.5 * rho_ln;
+  double h1 = g[1] * hfrho, h2 = g[2] * hfrho;
+  if (dir)
+    h2 = fma(g_frho, hrho_ln, h2);
+  else
+    h1 = fma(g_frho, hrho_ln, h1);
+  // kin = (A.v1 B.v1 + A.v2 B.v2) / 2
+  gA[F_V1] += fma(g_T, B.hv1, h1);
+  gB[F_V1] += fma(g_T, A.hv1, h1);
+  gA[F_V2] += fma(g_T, B.hv2, h2);
+  gB[F_V2] += fma(g_T, A.hv2, h2);
+  // the normal velocities of the pressure term
+  if (dir) {
+    gA[F_V2] += g[3] * B.hp;
+    gB[F_V2] += g[3] * A.hp;
+  } else {
+    gA[F_V1] += g[3] * B.hp;
+    gB[F_V1] += g[3] * A.hp;
+  }
+}
+
+// Series branch of a logarithmic mean, m = s M(u), u = (d/s)^2 (d = b - a, s = a + b; M = H for
+// {{rho}}_ln, and 1/{{beta}}_ln = M(u)/s with M = 2A): the adjoints of s and d from that of m,
+// from the derivative of the closed form (dm/dd = 2 (d/s) M'(u) for H; for 2A the 1/s factor adds
+// -m/s to dm/ds).  Differentiating the closed form rather than the shared reciprocal of the
+// forward evaluation changes the result only by rounding.
+__device__ __forceinline__ void ser_rho_rev(double g, double H, double Hd, double ur, double fr, double& g_s,
+                                            double& g_d) {
+  g_s = g * fma(-2.0 * ur, Hd, H);          // d(s H)/ds = H - 2 u H'
+  g_d = g * ((fr + fr) * Hd);               // d(s H)/dd = 2 f H'
+}
+__device__ __forceinline__ void ser_beta_rev(double g, double A2, double A2d, double ub, double fb, double isb,
+                                             double& g_s, double& g_d) {
+  const double w = g * (isb * isb);
+  g_s = -w * fma(ub + ub, A2d, A2);         // d(2A/s)/ds = -(2A + 2 u (2A)') / s^2
+  g_d = w * ((fb + fb) * A2d);              // d(2A/s)/dd = 2 f (2A)' / s^2
+}
+
+// Given the adjoint g of the flux f#(A, B) in direction dir, accumulate the adjoints of A's and
+// B's node quantities (NF fields) into gA, gB: the forward intermediates are recomputed, branch
+// decisions as in the forward flux.
 __device__ __forceinline__ void ec_flux_rev(const NodeQ<double>& A, const NodeQ<double>& B, int dir, double inv_gm1,
-                                            const double g[4], double gA[NQ], double gB[NQ]) {
+                                            const double g[4], double gA[NF], double gB[NF]) {
   // forward
   const double dr = B.rho - A.rho, sr = A.rho + B.rho;
   const double db = B.beta - A.beta, sb = A.beta + B.beta;
@@ -593,94 +656,96 @@ __device__ __forceinline__ void ec_flux_rev(const NodeQ<double>& A, const NodeQ<
   const double A2 = ser_b ? series_2A(ub) : 0.0;
   const double dlb = B.lnbeta - A.lnbeta;
   const double ibeta = ser_b ? qb * A2 : dlb * qb;
-  const double v1m = A.hv1 + B.hv1, v2m = A.hv2 + B.hv2;
-  const double vnA = dir ? A.v2 : A.v1, vnB = dir ? B.v2 : B.v1;
-  const double vnm = dir ? v2m : v1m;
-  const double frho = rho_ln * vnm;
-  const double kin = fma(A.hv1, B.v1, A.hv2 * B.v2);
-  const double T = fma(ibeta, inv_gm1, kin);
-  // reverse
-  double g_v1m = g[1] * frho, g_v2m = g[2] * frho;
-  const double g_frho = g[0] + g[1] * v1m + g[2] * v2m + g[3] * T;
-  const double g_pm = dir ? g[2] : g[1];
-  const double g_T = g[3] * frho;
-  const double g_ibeta = g_T * inv_gm1;
-  const double g_kin = g_T;
-  gA[Q_HP] += g[3] * vnB + g_pm;
-  gB[Q_HP] += g[3] * vnA + g_pm;
-  const double g_vnB = g[3] * A.hp, g_vnA = g[3] * B.hp;
-  gA[Q_HV1] += g_kin * B.v1;
-  gB[Q_V1] += g_kin * A.hv1;
-  gA[Q_HV2] += g_kin * B.v2;
-  gB[Q_V2] += g_kin * A.hv2;
-  const double g_rho_ln = g_frho * vnm;
-  const double g_vnm = g_frho * rho_ln;
-  if (dir) {
-    g_v2m += g_vnm;
-    gA[Q_V2] += g_vnA;
-    gB[Q_V2] += g_vnB;
+  double g_rho_ln, g_ibeta;
+  ec_flux_rev_common(A, B, dir, inv_gm1, g, rho_ln, ibeta, gA, gB, g_rho_ln, g_ibeta);
+  // {{rho}}_ln: series s H(u), else d / (ln b - ln a)
+  double g_sr, g_dr;
+  if (ser_r) {
+    ser_rho_rev(g_rho_ln, Hr, series_H_d(ur), ur, fr, g_sr, g_dr);
   } else {
-    g_v1m += g_vnm;
-    gA[Q_V1] += g_vnA;
-    gB[Q_V1] += g_vnB;
+    g_sr = 0.0;
+    g_dr = g_rho_ln * qr;
+    const double g_den = -g_rho_ln * fr * qr;       // d(d / D)/dD = -(d/D) / D
+    gB[F_LNRHO] += g_den;
+    gA[F_LNRHO] -= g_den;
   }
-  gA[Q_HV1] += g_v1m;
-  gB[Q_HV1] += g_v1m;
-  gA[Q_HV2] += g_v2m;
-  gB[Q_HV2] += g_v2m;
-  // 1 / {{beta}}_ln
-  double g_qb = 0.0, g_db = 0.0, g_sb = 0.0;
+  // 1/{{beta}}_ln: series 2A(u) / s, else (ln b - ln a) / d
+  double g_sb, g_db;
   if (ser_b) {
-    g_qb += g_ibeta * A2;
-    const double g_fb = 2.0 * fb * (g_ibeta * qb * series_2A_d(ub));
-    g_db += g_fb * qb;
-    g_qb += g_fb * db;
+    ser_beta_rev(g_ibeta, A2, series_2A_d(ub), ub, fb, qb, g_sb, g_db);
   } else {
-    gB[Q_LNBETA] += g_ibeta * qb;
-    gA[Q_LNBETA] -= g_ibeta * qb;
-    g_qb += g_ibeta * dlb;
+    g_sb = 0.0;
+    g_db = -g_ibeta * ibeta * qb;                    // d(L / d)/dd = -(L/d) / d
+    gB[F_LNBETA] += g_ibeta * qb;
+    gA[F_LNBETA] -= g_ibeta * qb;
   }
-  // {{rho}}_ln
-  double g_sr = 0.0, g_fr;
-  if (ser_r) {
-    g_sr += g_rho_ln * Hr;
-    g_fr = 2.0 * fr * (g_rho_ln * sr * series_H_d(ur));
-  } else {
-    g_fr = g_rho_ln;
-  }
-  const double g_dr = g_fr * qr;
-  const double g_qr = g_fr * dr;
-  // qr = 1/den_r, qb = 1/den_b
-  const double g_den_r = -g_qr * qr * qr;
-  const double g_den_b = -g_qb * qb * qb;
-  if (ser_r) {
-    g_sr += g_den_r;
-  } else {
-    gB[Q_LNRHO] += g_den_r;
-    gA[Q_LNRHO] -= g_den_r;
-  }
-  if (ser_b)
-    g_sb += g_den_b;
-  else
-    g_db += g_den_b;
-  gA[Q_RHO] += g_sr - g_dr;
-  gB[Q_RHO] += g_sr + g_dr;
-  gA[Q_BETA] += g_sb - g_db;
-  gB[Q_BETA] += g_sb + g_db;
+  gA[F_RHO] += g_sr - g_dr;
+  gB[F_RHO] += g_sr + g_dr;
+  gA[F_BETA] += g_sb - g_db;
+  gB[F_BETA] += g_sb + g_db;
 }
 
-// adjoint of the node quantities with respect to the conserved state u
-__device__ __forceinline__ void node_q_rev(const double u[4], const NodeQ<double>& q, double gm1, const double gq[NQ],
+// The same for a pair of an element whose node pairs all take the series of both means (known
+// from the element's extremes, see series_only): five fields, no logarithm read.
+__device__ __forceinline__ void ec_flux_rev_ser(const NodeQ<double>& A, const NodeQ<double>& B, int dir,
+                                                double inv_gm1, const double g[4], double gA[NF_SER],
+                                                double gB[NF_SER]) {
+  const double dr = B.rho - A.rho, sr = A.rho + B.rho;
+  const double db = B.beta - A.beta, sb = A.beta + B.beta;
+  const double r = rcp_val(sr * sb);
+  const double isr = sb * r, isb = sr * r;
+  const double fr = dr * isr, ur = fr * fr;
+  const double Hr = series_H(ur);
+  const double fb = db * isb, ub = fb * fb;
+  const double A2 = series_2A(ub);
+  double g_rho_ln, g_ibeta;
+  ec_flux_rev_common(A, B, dir, inv_gm1, g, sr * Hr, isb * A2, gA, gB, g_rho_ln, g_ibeta);
+  double g_sr, g_dr, g_sb, g_db;
+  ser_rho_rev(g_rho_ln, Hr, series_H_d(ur), ur, fr, g_sr, g_dr);
+  ser_beta_rev(g_ibeta, A2, series_2A_d(ub), ub, fb, isb, g_sb, g_db);
+  gA[F_RHO] += g_sr - g_dr;
+  gB[F_RHO] += g_sr + g_dr;
+  gA[F_BETA] += g_sb - g_db;
+  gB[F_BETA] += g_sb + g_db;
+}
+
+// Node quantities as node_q computes them, without the logarithms (set to 0), plus 1/rho and
+// p/rho = 1/beta for the reverse sweep (from the same reciprocal: rho p = (gamma-1)(rho E - |m|^2/2),
+// r = 1/(rho^2 p), 1/rho = rho p r, p/rho = rho p (1/rho)^2).
+__device__ __forceinline__ NodeQ<double> node_q_rec(const double u[4], double gm1, double& ir, double& ib) {
+  NodeQ<double> q;
+  const double rp = gm1 * fma(u[0], u[3], -0.5 * fma(u[1], u[1], u[2] * u[2]));
+  const double r = rcp_val(u[0] * rp);
+  ir = rp * r;
+  q.rho = u[0];
+  q.v1 = u[1] * ir;
+  q.v2 = u[2] * ir;
+  q.hp = 0.5 * (rp * ir);
+  q.beta = (u[0] * u[0]) * (u[0] * r);
+  q.hv1 = 0.5 * q.v1;
+  q.hv2 = 0.5 * q.v2;
+  q.lnrho = 0.0;
+  q.lnbeta = 0.0;
+  ib = (rp * ir) * ir;
+  return q;
+}
+
+// adjoint of the node quantities with respect to the conserved state u (gq: NF fields, or
+// NF_SER when LOGS is false and the logarithms were not read); ir = 1/rho, ib = 1/beta
+template <bool LOGS>
+__device__ __forceinline__ void node_q_rev(const NodeQ<double>& q, double gm1, const double* gq, double ir, double ib,
                                            double gu[4]) {
-  const double rho = q.rho, ir = rcp_val(rho);
   const double beta = q.beta;
   const double ip = beta * ir;                 // 1/p = (rho/p)/rho
-  double g_rho = gq[Q_RHO] + gq[Q_LNRHO] * ir;
-  const double g_beta = gq[Q_BETA] + gq[Q_LNBETA] * rcp_val(beta);
-  const double g_v1 = gq[Q_V1] + 0.5 * gq[Q_HV1];
-  const double g_v2 = gq[Q_V2] + 0.5 * gq[Q_HV2];
-  double g_p = 0.5 * gq[Q_HP];
-  g_rho += g_beta * ip;                        // beta = rho / p
+  double g_rho = gq[F_RHO];
+  double g_beta = gq[F_BETA];
+  if (LOGS) {
+    g_rho = fma(gq[F_LNRHO], ir, g_rho);
+    g_beta = fma(gq[F_LNBETA], ib, g_beta);
+  }
+  const double g_v1 = gq[F_V1], g_v2 = gq[F_V2];
+  double g_p = 0.5 * gq[F_HP];
+  g_rho = fma(g_beta, ip, g_rho);              // beta = rho / p
   g_p -= g_beta * beta * ip;
   const double v1 = q.v1, v2 = q.v2;
   gu[0] = g_rho - (g_v1 * v1 + g_v2 * v2) * ir + g_p * gm1 * 0.5 * (v1 * v1 + v2 * v2);
@@ -881,11 +946,16 @@ __device__ void hllc_rev(const double uL[4], const double uR[4], int dir, const 
 
 __device__ void ec_surface_rev(const double uL[4], const double uR[4], int dir, const Ops& ops, const double* ic,
                                const double* lc, const double gf[4], double guL[4], double guR[4]) {
-  const NodeQ<double> A = node_q(uL, ops.gm1, ic, lc), B = node_q(uR, ops.gm1, ic, lc);
-  double gA[NQ] = {}, gB[NQ] = {};
+  double irA, ibA, irB, ibB;
+  NodeQ<double> A = node_q_rec(uL, ops.gm1, irA, ibA), B = node_q_rec(uR, ops.gm1, irB, ibB);
+  A.lnrho = log_val(A.rho, ic, lc);
+  A.lnbeta = log_val(A.beta, ic, lc);
+  B.lnrho = log_val(B.rho, ic, lc);
+  B.lnbeta = log_val(B.beta, ic, lc);
+  double gA[NF] = {}, gB[NF] = {};
   ec_flux_rev(A, B, dir, ops.inv_gm1, gf, gA, gB);
-  node_q_rev(uL, A, ops.gm1, gA, guL);
-  node_q_rev(uR, B, ops.gm1, gB, guR);
+  node_q_rev<true>(A, ops.gm1, gA, irA, ibA, guL);
+  node_q_rev<true>(B, ops.gm1, gB, irB, ibB, guR);
 }
 
 __device__ __forceinline__ void surface_flux_rev(const double uL[4], const double uR[4], int dir, const Ops& ops,
@@ -904,22 +974,28 @@ __device__ __forceinline__ void surface_flux_rev(const double uL[4], const doubl
 // face reverse blocks: 4 threads per interface, 8 per mortar
 constexpr int FREV_THREADS = 64, FREV_IF = FREV_THREADS / 4, FREV_MORT = FREV_THREADS / 8;
 
+struct FaceRevShared {
+  double gphi[FREV_MORT][4][NN];
+  double gui[FREV_MORT][2][4][NN];
+};
+
+// face block fb of a 64-thread block: interfaces fb*FREV_IF.. (fb < if_blocks), else mortars
 template <int YS>
-__global__ void __launch_bounds__(FREV_THREADS) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
-                                                        int64_t n_mort, const int4* __restrict__ morts,
-                                                        int64_t if_blocks, const int32_t* __restrict__ level,
-                                                        const int32_t* __restrict__ method, int min_member,
-                                                        double two_over_len, StageArgs sa,
-                                                        const double* __restrict__ lam,
-                                                        const double* __restrict__ logt, double* __restrict__ gsurf) {
-  __shared__ double s_gphi[FREV_MORT][4][NN];
-  __shared__ double s_gui[FREV_MORT][2][4][NN];
+__device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int64_t n_if, const int4* __restrict__ ifs,
+                                                int64_t n_mort, const int4* __restrict__ morts, int64_t if_blocks,
+                                                const int32_t* __restrict__ level,
+                                                const int32_t* __restrict__ method, int min_member,
+                                                double two_over_len, const StageArgs& sa,
+                                                const double* __restrict__ lam, const double* __restrict__ logt,
+                                                double* __restrict__ gsurf, FaceRevShared& sh) {
+  auto& s_gphi = sh.gphi;
+  auto& s_gui = sh.gui;
   const double* ic = logt;
   const double* lc = logt + LOG_TABLE_SIZE;
   const double iw = ops.inv_w0;
   auto load = [&](int64_t e, int node, double u[4]) { stage_y<YS>(sa, method, e, node, u); };
-  if (blockIdx.x < if_blocks) {
-    const int64_t idx = (int64_t)blockIdx.x * FREV_IF + (threadIdx.x >> 2);
+  if (fb < if_blocks) {
+    const int64_t idx = fb * FREV_IF + (threadIdx.x >> 2);
     const int k = threadIdx.x & 3;
     if (idx >= n_if) return;
     const int4 r = ifs[idx];
@@ -942,7 +1018,7 @@ __global__ void __launch_bounds__(FREV_THREADS) k_vjp_faces_rev(Ops ops, int64_t
     return;
   }
   const int lm = threadIdx.x >> 3;
-  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * FREV_MORT + lm;
+  const int64_t idx = (fb - if_blocks) * FREV_MORT + lm;
   const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
   const bool valid = idx < n_mort;
   int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
@@ -994,12 +1070,128 @@ __global__ void __launch_bounds__(FREV_THREADS) k_vjp_faces_rev(Ops ops, int64_t
   }
 }
 
+template <int YS>
+__global__ void __launch_bounds__(FREV_THREADS) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
+                                                        int64_t n_mort, const int4* __restrict__ morts,
+                                                        int64_t if_blocks, const int32_t* __restrict__ level,
+                                                        const int32_t* __restrict__ method, int min_member,
+                                                        double two_over_len, StageArgs sa,
+                                                        const double* __restrict__ lam,
+                                                        const double* __restrict__ logt, double* __restrict__ gsurf) {
+  __shared__ FaceRevShared sh;
+  faces_rev_block<YS>(ops, blockIdx.x, n_if, ifs, n_mort, morts, if_blocks, level, method, min_member, two_over_len,
+                      sa, lam, logt, gsurf, sh);
+}
+
 // Element kernel over the active prefix of the sorted list (the volume adjoint
 // by the reverse sweep above); g receives the volume part only.  Each group of
 // 16 threads (one per node) strides over the active elements, so that a grid
 // sized to the resident capacity keeps every SM busy to the end.  The face
-// adjoints (gsurf) are gathered afterwards by face_gather.
+// adjoints (gsurf) are gathered afterwards.  Where every node pair of the
+// element takes the series of both logarithmic means (judged from the element's
+// extremes, as in the forward kernel), the pairs take the five-field sweep and
+// no node logarithm is computed.
 constexpr int VJP_ELEMS = 4;
+
+// the pairs of one element (three per thread) and the adjoint of this thread's node
+template <bool SER>
+__device__ __forceinline__ void vjp_element(const Ops& ops, const NodeQ<double>* __restrict__ sq,
+                                            const double (*__restrict__ mu)[NODES], double (*__restrict__ sg)[2 * NF],
+                                            unsigned gmask, int t, const NodeQ<double>& myq, double ir, double ib,
+                                            double out[4]) {
+  constexpr int K = SER ? NF_SER : NF;
+  const int i = t & 3, j = t >> 2;
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    const int p = t + 16 * kk;
+    const int dir = p >= 24;
+    const int q = dir ? p - 24 : p;
+    const int line = q / 6, qq = q - 6 * line;
+    const int a = (qq >= 3) + (qq >= 5);
+    const int b = qq + 1 - (a * (5 - a)) / 2;
+    const int na = dir ? a * 4 + line : line * 4 + a;
+    const int nb = dir ? b * 4 + line : line * 4 + b;
+    double gf[4], gA[K], gB[K];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[a][b] * mu[v][na] + ops.dsplit[b][a] * mu[v][nb];
+#pragma unroll
+    for (int m = 0; m < K; ++m) gA[m] = gB[m] = 0.0;
+    if constexpr (SER)
+      ec_flux_rev_ser(sq[na], sq[nb], dir, ops.inv_gm1, gf, gA, gB);
+    else
+      ec_flux_rev(sq[na], sq[nb], dir, ops.inv_gm1, gf, gA, gB);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      sg[p][m] = gA[m];
+      sg[p][K + m] = gB[m];
+    }
+  }
+  __syncwarp(gmask);
+  double gq[K];
+#pragma unroll
+  for (int m = 0; m < K; ++m) gq[m] = 0.0;
+#pragma unroll
+  for (int mm = 0; mm < 4; ++mm) {
+    if (mm != i) {
+      const int p = j * 6 + pair_slot(min(i, mm), max(i, mm));
+      const int side = i < mm ? 0 : K;
+#pragma unroll
+      for (int m = 0; m < K; ++m) gq[m] += sg[p][side + m];
+    }
+    if (mm != j) {
+      const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
+      const int side = j < mm ? 0 : K;
+#pragma unroll
+      for (int m = 0; m < K; ++m) gq[m] += sg[p][side + m];
+    }
+  }
+  node_q_rev<!SER>(myq, ops.gm1, gq, ir, ib, out);
+}
+
+struct VolRevShared {
+  NodeQ<double> q[VJP_ELEMS][NODES];
+  double mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
+  double g[VJP_ELEMS][48][2 * NF];      // per pair: adjoints of its two node records
+};
+
+// the volume adjoint of element elems[slot] by the 16-thread group le (node t); g receives it
+template <int YS>
+__device__ __forceinline__ void volume_rev_elem(const Ops& ops, int64_t slot, const int32_t* __restrict__ elems,
+                                                const int32_t* __restrict__ level,
+                                                const int32_t* __restrict__ method, double two_over_len,
+                                                const StageArgs& sa, const double* __restrict__ lam,
+                                                const double* __restrict__ s_log, double* __restrict__ g,
+                                                VolRevShared& sh, int le, int t, unsigned gmask) {
+  const int64_t e = elems[slot];
+  double y[4];
+  stage_y<YS>(sa, method, e, t, y);
+  const double scale = -ldexp(two_over_len, level[e]);
+  __syncwarp(gmask);   // the previous element's shared records are consumed
+  for (int v = 0; v < 4; ++v) sh.mu[le][v][t] = scale * lam[e * ELEM + v * NODES + t];
+  double ir, ib;
+  NodeQ<double> myq = node_q_rec(y, ops.gm1, ir, ib);
+  unsigned long long rmin = dbits(myq.rho), rmax = rmin, bmin = dbits(myq.beta), bmax = bmin;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {   // the element's 16 lanes
+    rmin = min(rmin, __shfl_xor_sync(gmask, rmin, o, 16));
+    rmax = max(rmax, __shfl_xor_sync(gmask, rmax, o, 16));
+    bmin = min(bmin, __shfl_xor_sync(gmask, bmin, o, 16));
+    bmax = max(bmax, __shfl_xor_sync(gmask, bmax, o, 16));
+  }
+  const bool ser = series_only(rmin, rmax, bmin, bmax);
+  if (!ser) {
+    myq.lnrho = log_val(myq.rho, s_log, s_log + LOG_TABLE_SIZE);
+    myq.lnbeta = log_val(myq.beta, s_log, s_log + LOG_TABLE_SIZE);
+  }
+  sh.q[le][t] = myq;
+  __syncwarp(gmask);
+  double out[4];
+  if (ser)
+    vjp_element<true>(ops, sh.q[le], sh.mu[le], sh.g[le], gmask, t, myq, ir, ib, out);
+  else
+    vjp_element<false>(ops, sh.q[le], sh.mu[le], sh.g[le], gmask, t, myq, ir, ib, out);
+  for (int c = 0; c < 4; ++c) g[e * ELEM + c * NODES + t] = out[c];
+}
 
 template <int YS>
 __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_act, const int32_t* __restrict__ elems,
@@ -1007,61 +1199,58 @@ __global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_act, const
                                                     const int32_t* __restrict__ method, double two_over_len,
                                                     StageArgs sa, const double* __restrict__ lam,
                                                     const double* __restrict__ logt, double* __restrict__ g) {
-  __shared__ NodeQ<double> s_q[VJP_ELEMS][NODES];
-  __shared__ double s_mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
-  __shared__ double s_g[VJP_ELEMS][48][2 * NQ];       // per pair: adjoints of its two node records
+  __shared__ VolRevShared sh;
   __shared__ double s_log[2 * LOG_TABLE_SIZE];
-  const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15;
   const unsigned gmask = 0xFFFFu << (threadIdx.x & 16);   // the 16 lanes of this group
   for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * VJP_ELEMS;
-  for (int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le; slot < n_act; slot += stride) {
-    const int64_t e = elems[slot];
-    double y[4];
-    stage_y<YS>(sa, method, e, t, y);
-    const double scale = -ldexp(two_over_len, level[e]);
-    __syncwarp(gmask);   // the previous element's shared records are consumed
-    for (int v = 0; v < 4; ++v) s_mu[le][v][t] = scale * lam[e * ELEM + v * NODES + t];
-    const NodeQ<double> myq = node_q(y, ops.gm1, s_log, s_log + LOG_TABLE_SIZE);
-    s_q[le][t] = myq;
-    __syncwarp(gmask);
-    for (int kk = 0; kk < 3; ++kk) {
-      const int p = t + 16 * kk;
-      const int dir = p >= 24;
-      const int q = dir ? p - 24 : p;
-      const int line = q / 6, qq = q - 6 * line;
-      const int a = (qq >= 3) + (qq >= 5);
-      const int b = qq + 1 - (a * (5 - a)) / 2;
-      const int na = dir ? a * 4 + line : line * 4 + a;
-      const int nb = dir ? b * 4 + line : line * 4 + b;
-      double gf[4], gA[NQ], gB[NQ];
-      for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[a][b] * s_mu[le][v][na] + ops.dsplit[b][a] * s_mu[le][v][nb];
-      for (int m = 0; m < NQ; ++m) gA[m] = gB[m] = 0.0;
-      ec_flux_rev(s_q[le][na], s_q[le][nb], dir, ops.inv_gm1, gf, gA, gB);
-      for (int m = 0; m < NQ; ++m) {
-        s_g[le][p][m] = gA[m];
-        s_g[le][p][NQ + m] = gB[m];
-      }
+  for (int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le; slot < n_act; slot += stride)
+    volume_rev_elem<YS>(ops, slot, elems, level, method, two_over_len, sa, lam, s_log, g, sh, le, t, gmask);
+}
+
+// One launch per reverse stage: the volume items (VJP_ELEMS active elements each) and the face
+// items (FREV_IF interfaces or FREV_MORT mortars each) of the stage, dealt to a grid of resident
+// 64-thread blocks from the stage's counter *ticket (zero at launch), volume items first, so that
+// the short face items fill the end.  The two kinds write disjoint outputs (g, gsurf) and depend
+// on nothing the launch writes, so their order does not change the results.
+union RevStageShared {
+  VolRevShared v;
+  FaceRevShared f;
+};
+
+template <int YS>
+__global__ void __launch_bounds__(64) k_vjp_stage(Ops ops, int64_t n_act, const int32_t* __restrict__ elems,
+                                                   int64_t n_if, const int4* __restrict__ ifs, int64_t n_mort,
+                                                   const int4* __restrict__ morts, int64_t if_blocks,
+                                                   int64_t face_blocks, const int32_t* __restrict__ level,
+                                                   const int32_t* __restrict__ method, int min_member,
+                                                   double two_over_len, StageArgs sa, const double* __restrict__ lam,
+                                                   const double* __restrict__ logt, double* __restrict__ g,
+                                                   double* __restrict__ gsurf, unsigned long long* ticket) {
+  __shared__ RevStageShared sh;
+  __shared__ double s_log[2 * LOG_TABLE_SIZE];
+  __shared__ unsigned long long s_item;
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15;
+  const unsigned gmask = 0xFFFFu << (threadIdx.x & 16);
+  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
+  const unsigned long long vol_items = (unsigned long long)((n_act + VJP_ELEMS - 1) / VJP_ELEMS);
+  const unsigned long long items = vol_items + (unsigned long long)face_blocks;
+  for (;;) {
+    __syncthreads();   // the previous item is done in every thread (shared buffers free)
+    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const unsigned long long it = s_item;
+    if (it >= items) break;
+    if (it < vol_items) {
+      const int64_t slot = (int64_t)it * VJP_ELEMS + le;
+      if (slot < n_act)
+        volume_rev_elem<YS>(ops, slot, elems, level, method, two_over_len, sa, lam, s_log, g, sh.v, le, t, gmask);
+    } else {
+      faces_rev_block<YS>(ops, (int64_t)(it - vol_items), n_if, ifs, n_mort, morts, if_blocks, level, method,
+                          min_member, two_over_len, sa, lam, logt, gsurf, sh.f);
     }
-    __syncwarp(gmask);
-    double gq[NQ];
-    for (int m = 0; m < NQ; ++m) gq[m] = 0.0;
-    for (int mm = 0; mm < 4; ++mm) {
-      if (mm != i) {
-        const int p = j * 6 + pair_slot(min(i, mm), max(i, mm));
-        const int side = i < mm ? 0 : NQ;
-        for (int m = 0; m < NQ; ++m) gq[m] += s_g[le][p][side + m];
-      }
-      if (mm != j) {
-        const int p = 24 + i * 6 + pair_slot(min(j, mm), max(j, mm));
-        const int side = j < mm ? 0 : NQ;
-        for (int m = 0; m < NQ; ++m) gq[m] += s_g[le][p][side + m];
-      }
-    }
-    double out[4];
-    node_q_rev(y, myq, ops.gm1, gq, out);
-    for (int c = 0; c < 4; ++c) g[e * ELEM + c * NODES + t] = out[c];
   }
 }
 
@@ -1092,44 +1281,50 @@ __global__ void k_vjp_gather(int64_t n, const int32_t* __restrict__ method, int 
 // adjoint of the stage combination, with gq = J(Y_i)^T lam_i formed as in
 // k_vjp_gather: lamU += gq; lamK1 += dt alpha gq; lamKp (+)= dt beta gq
 // (lamKp may alias lamK1; assign_p: lamKp receives its first contribution, no prior zeroing)
-// face_gather that also clears the entries it read (each face entry belongs to one node), so that
-// the face adjoints start from zero at the next stage without a separate clearing pass
-__device__ __forceinline__ double face_gather_clear(double* __restrict__ gs, int c, int t) {
-  const int i = t & 3, j = t >> 2;
-  double o = 0.0;
-  if (i == 0) { o += gs[0 * 16 + 4 * c + j]; gs[0 * 16 + 4 * c + j] = 0.0; }
-  if (i == 3) { o += gs[1 * 16 + 4 * c + j]; gs[1 * 16 + 4 * c + j] = 0.0; }
-  if (j == 0) { o += gs[2 * 16 + 4 * c + i]; gs[2 * 16 + 4 * c + i] = 0.0; }
-  if (j == 3) { o += gs[3 * 16 + 4 * c + i]; gs[3 * 16 + 4 * c + i] = 0.0; }
-  return o;
-}
-
 // Over the elements elems[0 .. n) of the stage's halo (the active elements and their face
 // neighbours: every element whose volume or face adjoint can be nonzero), add the gathered
 // adjoint gq to lamU and the stage combination's shares to lamK1 and lamKp (assigned or added);
-// the face adjoints read are cleared.  Elements outside the halo receive nothing at this stage,
-// and their lamKp entries are read later only where the element is active, which it is not at
-// any earlier stage.
+// the face adjoints read are cleared, so that they start from zero at the next stage.  Elements
+// outside the halo receive nothing at this stage, and their lamKp entries are read later only
+// where the element is active, which it is not at any earlier stage.
+// One thread per element value (node t = 4 j + i, variable c).  Every load is issued before any
+// store (the volume part is loaded for every element and discarded where the element is
+// inactive): with the stores of the cleared face records between them the loads would
+// otherwise wait on one another, and the kernel, which mostly misses in L2 here, would run at
+// a small fraction of the memory bandwidth.
 __global__ void k_adj_accum(int64_t n, const int32_t* __restrict__ elems, const int32_t* __restrict__ method,
                             int min_member, const StageCoef* __restrict__ coef, double dt,
                             const double* __restrict__ g, double* __restrict__ gsurf, double* __restrict__ lamU,
-                            double* __restrict__ lamK1, double* lamKp, int assign_p) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * ELEM; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t slot = q / ELEM;
-    const int r = (int)(q - slot * ELEM);
-    const int64_t e = elems[slot];
-    const int m = method[e];
-    const double gq = (m >= min_member ? g[e * ELEM + r] : 0.0) + face_gather_clear(gsurf + e * ELEM, r >> 4, r & 15);
-    const int64_t qe = e * ELEM + r;
-    lamU[qe] += gq;
-    if (coef) {
-      const StageCoef c = coef[m];
-      if (lamKp == lamK1) {
-        lamK1[qe] += dt * (c.alpha + c.beta) * gq;
-      } else {
-        lamK1[qe] += dt * c.alpha * gq;
-        lamKp[qe] = assign_p ? dt * c.beta * gq : lamKp[qe] + dt * c.beta * gq;
-      }
+                            double* lamK1, double* lamKp, int assign_p) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * ELEM) return;
+  const int64_t slot = q / ELEM;
+  const int r = (int)(q - slot * ELEM), c = r >> 4, t = r & 15, i = t & 3, j = t >> 2;
+  const int64_t e = elems[slot];
+  const int64_t qe = e * ELEM + r;
+  double* gs = gsurf + e * ELEM;
+  // the element faces through this node: -x / +x (i = 0 / 3) and -y / +y (j = 0 / 3)
+  const int fa = i == 0 ? 4 * c + j : (i == 3 ? 16 + 4 * c + j : -1);
+  const int fb = j == 0 ? 32 + 4 * c + i : (j == 3 ? 48 + 4 * c + i : -1);
+  const bool alias = lamKp == lamK1;
+  const int m = method[e];
+  const double gv = g[qe];
+  const double sa = fa >= 0 ? gs[fa] : 0.0;
+  const double sb = fb >= 0 ? gs[fb] : 0.0;
+  const double u = lamU[qe];
+  const double k1 = coef ? lamK1[qe] : 0.0;
+  const double kp = (coef && !alias && !assign_p) ? lamKp[qe] : 0.0;
+  const double gq = (m >= min_member ? gv : 0.0) + (sa + sb);
+  if (fa >= 0) gs[fa] = 0.0;
+  if (fb >= 0) gs[fb] = 0.0;
+  lamU[qe] = u + gq;
+  if (coef) {
+    const StageCoef cf = coef[m];
+    if (alias) {
+      lamK1[qe] = k1 + dt * (cf.alpha + cf.beta) * gq;
+    } else {
+      lamK1[qe] = k1 + dt * cf.alpha * gq;
+      lamKp[qe] = assign_p ? dt * cf.beta * gq : kp + dt * cf.beta * gq;
     }
   }
 }
@@ -1158,7 +1353,8 @@ cudaError_t launch_adj_accum(cudaStream_t st, int64_t n, const int32_t* elems, c
                              const StageCoef* coef, double dt, const double* g, double* gsurf, double* lamU,
                              double* lamK1, double* lamKp, int assign_p) {
   if (n <= 0) return cudaSuccess;
-  ad::k_adj_accum<<<ew_blocks(n), 256, 0, st>>>(n, elems, method, min_member, coef, dt, g, gsurf, lamU, lamK1, lamKp,
+  // one thread per element value: at most 2^31 - 1 blocks, i.e. 8.5e9 elements
+  ad::k_adj_accum<<<(unsigned)((n * ELEM + 255) / 256), 256, 0, st>>>(n, elems, method, min_member, coef, dt, g, gsurf, lamU, lamK1, lamKp,
                                                 assign_p);
   return cudaGetLastError();
 }
@@ -1201,24 +1397,47 @@ cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int6
   return cudaGetLastError();
 }
 
-// blocks of the volume VJP: at most what is resident at once (the kernel strides); the capacity is
-// computed once per device (a repeated computation by racing threads gives the same value)
-template <int YS>
-static unsigned vjp_volume_blocks(int64_t n_act) {
+// blocks of a persistent reverse kernel: at most what is resident at once (the kernels stride or
+// deal items); the capacity is computed once per device and kernel (a repeated computation by
+// racing threads gives the same value); slot: 0, 1 the volume kernels, 2, 3 the stage kernels
+template <class Kernel>
+static unsigned resident_blocks(Kernel kernel, int slot, int64_t need) {
   constexpr int MAX_DEVICES = 64;
-  static int cached[MAX_DEVICES] = {};
+  static int cached[4][MAX_DEVICES] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  int resident = (dev >= 0 && dev < MAX_DEVICES) ? cached[dev] : 0;
+  int resident = (dev >= 0 && dev < MAX_DEVICES) ? cached[slot][dev] : 0;
   if (resident == 0) {
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ad::k_vjp_volume<YS>, 64, 0);
-    resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    if (dev >= 0 && dev < MAX_DEVICES) cached[dev] = resident;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 64, 0);
+    resident = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < MAX_DEVICES) cached[slot][dev] = resident;
   }
-  const int64_t need = (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS;
-  return (unsigned)(need < resident ? need : resident);
+  return (unsigned)(need < resident ? (need > 0 ? need : 1) : resident);
+}
+
+template <int YS>
+static unsigned vjp_volume_blocks(int64_t n_act) {
+  return resident_blocks(ad::k_vjp_volume<YS>, YS, (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS);
+}
+
+cudaError_t launch_vjp_stage(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
+                             int64_t n_if, const int4* ifs, int64_t n_mort, const int4* morts, const int32_t* level,
+                             const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
+                             const double* lam, const double* logt, double* g, double* gsurf,
+                             unsigned long long* ticket) {
+  const int64_t bi = (n_if + ad::FREV_IF - 1) / ad::FREV_IF, bm = (n_mort + ad::FREV_MORT - 1) / ad::FREV_MORT;
+  const int64_t items = (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS + bi + bm;
+  if (items <= 0) return cudaSuccess;
+  if (ysrc == Y_GIVEN)
+    ad::k_vjp_stage<Y_GIVEN><<<resident_blocks(ad::k_vjp_stage<Y_GIVEN>, 2 + Y_GIVEN, items), 64, 0, st>>>(
+        ops, n_act, elems, n_if, ifs, n_mort, morts, bi, bi + bm, level, method, min_member, two_over_len, sa, lam,
+        logt, g, gsurf, ticket);
+  else
+    ad::k_vjp_stage<Y_COMBINE><<<resident_blocks(ad::k_vjp_stage<Y_COMBINE>, 2 + Y_COMBINE, items), 64, 0, st>>>(
+        ops, n_act, elems, n_if, ifs, n_mort, morts, bi, bi + bm, level, method, min_member, two_over_len, sa, lam,
+        logt, g, gsurf, ticket);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_vjp_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,

@@ -300,6 +300,7 @@ struct perk_ctx {
 
   // adjoint work space
   DevBuf<double> d_surf_d, d_Kall, d_g, d_lamK1, d_lamKa, d_lamKb;
+  DevBuf<unsigned long long> d_rctl;   // item counters of the fused reverse stages
   // elements per block of the volume kernel (perk_autotune_volume)
   int vol_epb = VOL_EPB_DEFAULT;
   // second stream of the reverse sweep: face adjoints run beside the volume adjoint
@@ -410,7 +411,7 @@ void for_each_buffer(perk_ctx* c, F&& f) {
   f(c->d_minmax); f(c->d_if_raw); f(c->d_mort_raw); f(c->d_if_sorted); f(c->d_mort_sorted); f(c->d_counts);
   f(c->d_surf); f(c->d_K1); f(c->d_Ka); f(c->d_Kb); f(c->d_dt); f(c->d_block_min); f(c->d_dt_out); f(c->d_coef);
   f(c->d_flag); f(c->d_logtab); f(c->d_map); f(c->d_eta); f(c->d_surf_d); f(c->d_Kall); f(c->d_Kpat); f(c->d_g);
-  f(c->d_lamK1); f(c->d_lamKa); f(c->d_lamKb); f(c->d_wsurf); f(c->d_q); f(c->d_vsurf);
+  f(c->d_lamK1); f(c->d_lamKa); f(c->d_lamKb); f(c->d_rctl); f(c->d_wsurf); f(c->d_q); f(c->d_vsurf);
   f(c->d_cells); f(c->d_newcells); f(c->d_key); f(c->d_des); f(c->d_off); f(c->d_cnt_if); f(c->d_cnt_mort);
   f(c->d_off_if); f(c->d_off_mort); f(c->d_info); f(c->d_ctl); f(c->d_stamp);
 }
@@ -1949,6 +1950,11 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
   double* lamK1 = ctx->d_lamK1.p;
   // face adjoints start from zero; each stage's accumulation clears what it gathers
   PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_surf_d.p, 0, nd * sizeof(double), st));
+  const bool fused = ctx->stage_fused();
+  if (fused) {
+    PERK_CUDA(ctx, ctx->d_rctl.ensure(MAX_S));
+    PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_rctl.p, 0, MAX_S * sizeof(unsigned long long), st));
+  }
   if (S == 1) {
     PERK_CUDA(ctx, launch_adj_seed(st, ctx->n_elem, dt, 0.0, 0.0, b1 + bp + bs, d_lam_np1, d_lam_n, lam_prev, nullptr,
                                    lamK1));
@@ -1968,17 +1974,25 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
     sa.Kp = K + (size_t)(i > 0 ? i - 1 : 0) * nd;
     sa.coef = coef;
     sa.dt = ctx->d_dt.p;
-    // face adjoints on the second stream, beside the volume adjoint
-    PERK_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
-    PERK_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0));
-    PERK_CUDA(ctx, launch_vjp_faces(ctx->aux_stream, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p,
-                                    ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->n_elem, ctx->d_level.p,
-                                    ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p,
-                                    ctx->d_surf_d.p, false));
-    PERK_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux_stream));
-    PERK_CUDA(ctx, launch_vjp_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                                     ctx->d_method.p, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p));
-    PERK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    if (fused) {
+      // face and volume adjoints in one launch
+      PERK_CUDA(ctx, launch_vjp_stage(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->act_if[i],
+                                      ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->d_level.p,
+                                      ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p,
+                                      ctx->d_surf_d.p, ctx->d_rctl.p + i));
+    } else {
+      // face adjoints on the second stream, beside the volume adjoint
+      PERK_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
+      PERK_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0));
+      PERK_CUDA(ctx, launch_vjp_faces(ctx->aux_stream, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p,
+                                      ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->n_elem, ctx->d_level.p,
+                                      ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p,
+                                      ctx->d_surf_d.p, false));
+      PERK_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux_stream));
+      PERK_CUDA(ctx, launch_vjp_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
+                                       ctx->d_method.p, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p));
+      PERK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    }
     // the stage's halo: its active elements and their face neighbours (a prefix of the sorted list)
     const int64_t halo = ctx->halo_el[i];
     if (i == 0) {

@@ -188,6 +188,13 @@ cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int6
 cudaError_t launch_vjp_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
                               const int32_t* level, const int32_t* method, double two_over_len,
                               const StageArgs& sa, const double* lam, const double* logt, double* g);
+// The face and volume parts of one reverse stage in one launch (the outputs of the two above);
+// *ticket is the stage's item counter and must be zero at launch.
+cudaError_t launch_vjp_stage(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
+                             int64_t n_if, const int4* ifs, int64_t n_mort, const int4* morts, const int32_t* level,
+                             const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
+                             const double* lam, const double* logt, double* g, double* gsurf,
+                             unsigned long long* ticket);
 cudaError_t launch_vjp_gather(cudaStream_t st, int64_t n, const int32_t* method, int min_member, const double* gsurf,
                               double* g);
 // over the elements elems[0 .. n) (the stage's halo); clears the face adjoints it gathers
