@@ -559,6 +559,9 @@ __device__ __forceinline__ double lift_coef(int face, double two_over_len, int l
 //   0 rho, 1 beta = rho/p, 2 v1, 3 v2, 4 p/2, 5 ln rho, 6 ln beta
 enum { F_RHO = 0, F_BETA, F_V1, F_V2, F_HP, F_LNRHO, F_LNBETA, NF };
 constexpr int NF_SER = F_LNRHO;   // fields of a pair whose means both take their series
+// Adjoint accumulators start at -0.0, not +0.0: -0.0 + x is x exactly for every x, so the
+// compiler drops the first addition into each of them (+0.0 + x differs from x for x = -0.0
+// and must be kept).
 
 // derivatives of the log-mean series in u
 __device__ __forceinline__ double series_H_d(double u) {   // H'(u)
@@ -663,7 +666,7 @@ __device__ __forceinline__ void ec_flux_rev(const NodeQ<double>& A, const NodeQ<
   if (ser_r) {
     ser_rho_rev(g_rho_ln, Hr, series_H_d(ur), ur, fr, g_sr, g_dr);
   } else {
-    g_sr = 0.0;
+    g_sr = -0.0;
     g_dr = g_rho_ln * qr;
     const double g_den = -g_rho_ln * fr * qr;       // d(d / D)/dD = -(d/D) / D
     gB[F_LNRHO] += g_den;
@@ -674,7 +677,7 @@ __device__ __forceinline__ void ec_flux_rev(const NodeQ<double>& A, const NodeQ<
   if (ser_b) {
     ser_beta_rev(g_ibeta, A2, series_2A_d(ub), ub, fb, qb, g_sb, g_db);
   } else {
-    g_sb = 0.0;
+    g_sb = -0.0;
     g_db = -g_ibeta * ibeta * qb;                    // d(L / d)/dd = -(L/d) / d
     gB[F_LNBETA] += g_ibeta * qb;
     gA[F_LNBETA] -= g_ibeta * qb;
@@ -762,7 +765,7 @@ struct SideF {
   double rho, mn, mt, E, ir, v, p, c;
 };
 struct SideG {
-  double rho = 0, mn = 0, mt = 0, E = 0, ir = 0, v = 0, p = 0, c = 0;
+  double rho = -0.0, mn = -0.0, mt = -0.0, E = -0.0, ir = -0.0, v = -0.0, p = -0.0, c = -0.0;
 };
 
 __device__ __forceinline__ void side_fwd(const double u[4], int dir, const Ops& ops, SideF& s) {
@@ -779,7 +782,7 @@ __device__ __forceinline__ void side_fwd(const double u[4], int dir, const Ops& 
 // adjoints of (ir, v, p, c) -> adjoints of (rho, mn, mt, E), then rotated back to u's order
 __device__ __forceinline__ void side_rev(const SideF& s, SideG& g, int dir, const Ops& ops, double gu[4]) {
   if (s.c > 0.0) {
-    const double h = 0.5 * ops.gamma / s.c;
+    const double h = 0.5 * ops.gamma * rcp_val(s.c);
     g.p += g.c * h * s.ir;
     g.ir += g.c * h * s.p;
   }
@@ -848,7 +851,7 @@ __device__ void hll_rev(const double uL[4], const double uR[4], int dir, const O
     phys_fwd(R, FR);
     const double iD = rcp_val(SR - SL);
     const double dU[4] = {R.rho - L.rho, R.mn - L.mn, R.mt - L.mt, R.E - L.E};
-    double gSL = 0.0, gSR = 0.0, GL[4], GR[4];
+    double gSL = -0.0, gSR = -0.0, GL[4], GR[4];
     for (int v = 0; v < 4; ++v) {
       F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * dU[v]) * iD;
       GL[v] = G[v] * SR * iD;
@@ -899,7 +902,7 @@ __device__ void hllc_rev(const double uL[4], const double uR[4], int dir, const 
     const double Uk[4] = {K.rho, K.mn, K.mt, K.E};
     // F = F_K + S (Us - U_K)
     phys_rev(K, G, gk);
-    double gS = 0.0;
+    double gS = -0.0;
     for (int v = 0; v < 4; ++v) gS += G[v] * (Us[v] - Uk[v]);
     gk.rho -= S * G[0];
     gk.mn -= S * G[1];
@@ -952,7 +955,8 @@ __device__ void ec_surface_rev(const double uL[4], const double uR[4], int dir, 
   A.lnbeta = log_val(A.beta, ic, lc);
   B.lnrho = log_val(B.rho, ic, lc);
   B.lnbeta = log_val(B.beta, ic, lc);
-  double gA[NF] = {}, gB[NF] = {};
+  double gA[NF], gB[NF];
+  for (int m = 0; m < NF; ++m) gA[m] = gB[m] = -0.0;
   ec_flux_rev(A, B, dir, ops.inv_gm1, gf, gA, gB);
   node_q_rev<true>(A, ops.gm1, gA, irA, ibA, guL);
   node_q_rev<true>(B, ops.gm1, gB, irB, ibB, guR);
@@ -972,17 +976,18 @@ __device__ __forceinline__ void surface_flux_rev(const double uL[4], const doubl
 // Faces: the adjoint weight of every face-node flux (its lifting coefficients times
 // lam on both sides) through the hand-written reverse sweeps.
 // face reverse blocks: 4 threads per interface, 8 per mortar
-constexpr int FREV_THREADS = 64, FREV_IF = FREV_THREADS / 4, FREV_MORT = FREV_THREADS / 8;
+constexpr int FREV_IF = 32 / 4, FREV_MORT = 32 / 8;
 
+// one warp's face item: FREV_IF interfaces (4 lanes each) or FREV_MORT mortars (8 lanes each)
 struct FaceRevShared {
   double gphi[FREV_MORT][4][NN];
   double gui[FREV_MORT][2][4][NN];
 };
 
-// face block fb of a 64-thread block: interfaces fb*FREV_IF.. (fb < if_blocks), else mortars
+// face item fb of a warp: interfaces fb*FREV_IF.. (fb < if_items), else mortars
 template <int YS>
-__device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int64_t n_if, const int4* __restrict__ ifs,
-                                                int64_t n_mort, const int4* __restrict__ morts, int64_t if_blocks,
+__device__ __forceinline__ void faces_rev_warp(const Ops& ops, int64_t fb, int64_t n_if, const int4* __restrict__ ifs,
+                                               int64_t n_mort, const int4* __restrict__ morts, int64_t if_items,
                                                 const int32_t* __restrict__ level,
                                                 const int32_t* __restrict__ method, int min_member,
                                                 double two_over_len, const StageArgs& sa,
@@ -994,9 +999,10 @@ __device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int6
   const double* lc = logt + LOG_TABLE_SIZE;
   const double iw = ops.inv_w0;
   auto load = [&](int64_t e, int node, double u[4]) { stage_y<YS>(sa, method, e, node, u); };
-  if (fb < if_blocks) {
-    const int64_t idx = fb * FREV_IF + (threadIdx.x >> 2);
-    const int k = threadIdx.x & 3;
+  const int lane = threadIdx.x & 31;
+  if (fb < if_items) {
+    const int64_t idx = fb * FREV_IF + (lane >> 2);
+    const int k = lane & 3;
     if (idx >= n_if) return;
     const int4 r = ifs[idx];
     const int dir = r.z;
@@ -1017,9 +1023,9 @@ __device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int6
     }
     return;
   }
-  const int lm = threadIdx.x >> 3;
-  const int64_t idx = (fb - if_blocks) * FREV_MORT + lm;
-  const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
+  const int lm = lane >> 3;
+  const int64_t idx = (fb - if_items) * FREV_MORT + lm;
+  const int half = (lane >> 2) & 1, k = lane & 3;
   const bool valid = idx < n_mort;
   int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
   const int dir = r.w & 1, large_side = (r.w >> 1) & 1;
@@ -1030,7 +1036,7 @@ __device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int6
     const double cl = method[r.x] >= min_member ? lift_coef(large_face, two_over_len, level[r.x], iw) : 0.0;
     for (int v = 0; v < 4; ++v) s_gphi[lm][v][k] = cl * lam[(int64_t)r.x * ELEM + v * NODES + face_node(large_face, k)];
   }
-  __syncthreads();
+  __syncwarp();
   if (valid) {
     double ui[4] = {0.0, 0.0, 0.0, 0.0}, us[4], gi[4], gs[4];
     for (int l = 0; l < NN; ++l) {
@@ -1056,7 +1062,7 @@ __device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int6
       s_gui[lm][half][c][k] = gi[c];
     }
   }
-  __syncthreads();
+  __syncwarp();
   if (valid) {
     for (int cc = 0; cc < 2; ++cc) {
       const int c = 2 * half + cc;
@@ -1070,35 +1076,18 @@ __device__ __forceinline__ void faces_rev_block(const Ops& ops, int64_t fb, int6
   }
 }
 
-template <int YS>
-__global__ void __launch_bounds__(FREV_THREADS) k_vjp_faces_rev(Ops ops, int64_t n_if, const int4* __restrict__ ifs,
-                                                        int64_t n_mort, const int4* __restrict__ morts,
-                                                        int64_t if_blocks, const int32_t* __restrict__ level,
-                                                        const int32_t* __restrict__ method, int min_member,
-                                                        double two_over_len, StageArgs sa,
-                                                        const double* __restrict__ lam,
-                                                        const double* __restrict__ logt, double* __restrict__ gsurf) {
-  __shared__ FaceRevShared sh;
-  faces_rev_block<YS>(ops, blockIdx.x, n_if, ifs, n_mort, morts, if_blocks, level, method, min_member, two_over_len,
-                      sa, lam, logt, gsurf, sh);
-}
-
-// Element kernel over the active prefix of the sorted list (the volume adjoint
-// by the reverse sweep above); g receives the volume part only.  Each group of
-// 16 threads (one per node) strides over the active elements, so that a grid
-// sized to the resident capacity keeps every SM busy to the end.  The face
-// adjoints (gsurf) are gathered afterwards.  Where every node pair of the
-// element takes the series of both logarithmic means (judged from the element's
-// extremes, as in the forward kernel), the pairs take the five-field sweep and
-// no node logarithm is computed.
-constexpr int VJP_ELEMS = 4;
+// Volume adjoint of one element per group of 16 threads (one per node); g receives the volume
+// part only, the face adjoints (gsurf) are gathered afterwards.  Where every node pair of the
+// element takes the series of both logarithmic means (judged from the element's extremes, as in
+// the forward kernel), the pairs take the five-field sweep and no node logarithm is computed.
+constexpr int VJP_ELEMS = 2;   // elements of a warp's volume item
 
 // the pairs of one element (three per thread) and the adjoint of this thread's node
+// (mu: -(2/h) lam at this thread's node; the pairs read their nodes' values by shuffles)
 template <bool SER>
 __device__ __forceinline__ void vjp_element(const Ops& ops, const NodeQ<double>* __restrict__ sq,
-                                            const double (*__restrict__ mu)[NODES], double (*__restrict__ sg)[2 * NF],
-                                            unsigned gmask, int t, const NodeQ<double>& myq, double ir, double ib,
-                                            double out[4]) {
+                                            const double mu[4], double (*__restrict__ sg)[2 * NF], unsigned gmask,
+                                            int t, const NodeQ<double>& myq, double ir, double ib, double out[4]) {
   constexpr int K = SER ? NF_SER : NF;
   const int i = t & 3, j = t >> 2;
 #pragma unroll
@@ -1113,9 +1102,12 @@ __device__ __forceinline__ void vjp_element(const Ops& ops, const NodeQ<double>*
     const int nb = dir ? b * 4 + line : line * 4 + b;
     double gf[4], gA[K], gB[K];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) gf[v] = ops.dsplit[a][b] * mu[v][na] + ops.dsplit[b][a] * mu[v][nb];
+    for (int v = 0; v < 4; ++v) {
+      const double ma = __shfl_sync(gmask, mu[v], na, 16), mb = __shfl_sync(gmask, mu[v], nb, 16);
+      gf[v] = ops.dsplit[a][b] * ma + ops.dsplit[b][a] * mb;
+    }
 #pragma unroll
-    for (int m = 0; m < K; ++m) gA[m] = gB[m] = 0.0;
+    for (int m = 0; m < K; ++m) gA[m] = gB[m] = -0.0;
     if constexpr (SER)
       ec_flux_rev_ser(sq[na], sq[nb], dir, ops.inv_gm1, gf, gA, gB);
     else
@@ -1129,7 +1121,7 @@ __device__ __forceinline__ void vjp_element(const Ops& ops, const NodeQ<double>*
   __syncwarp(gmask);
   double gq[K];
 #pragma unroll
-  for (int m = 0; m < K; ++m) gq[m] = 0.0;
+  for (int m = 0; m < K; ++m) gq[m] = -0.0;
 #pragma unroll
   for (int mm = 0; mm < 4; ++mm) {
     if (mm != i) {
@@ -1150,7 +1142,6 @@ __device__ __forceinline__ void vjp_element(const Ops& ops, const NodeQ<double>*
 
 struct VolRevShared {
   NodeQ<double> q[VJP_ELEMS][NODES];
-  double mu[VJP_ELEMS][4][NODES];       // -(2/h) lam at the nodes
   double g[VJP_ELEMS][48][2 * NF];      // per pair: adjoints of its two node records
 };
 
@@ -1160,14 +1151,14 @@ __device__ __forceinline__ void volume_rev_elem(const Ops& ops, int64_t slot, co
                                                 const int32_t* __restrict__ level,
                                                 const int32_t* __restrict__ method, double two_over_len,
                                                 const StageArgs& sa, const double* __restrict__ lam,
-                                                const double* __restrict__ s_log, double* __restrict__ g,
+                                                const double* __restrict__ logt, double* __restrict__ g,
                                                 VolRevShared& sh, int le, int t, unsigned gmask) {
   const int64_t e = elems[slot];
   double y[4];
   stage_y<YS>(sa, method, e, t, y);
   const double scale = -ldexp(two_over_len, level[e]);
-  __syncwarp(gmask);   // the previous element's shared records are consumed
-  for (int v = 0; v < 4; ++v) sh.mu[le][v][t] = scale * lam[e * ELEM + v * NODES + t];
+  double mu[4];
+  for (int v = 0; v < 4; ++v) mu[v] = scale * lam[e * ELEM + v * NODES + t];
   double ir, ib;
   NodeQ<double> myq = node_q_rec(y, ops.gm1, ir, ib);
   unsigned long long rmin = dbits(myq.rho), rmax = rmin, bmin = dbits(myq.beta), bmax = bmin;
@@ -1180,77 +1171,59 @@ __device__ __forceinline__ void volume_rev_elem(const Ops& ops, int64_t slot, co
   }
   const bool ser = series_only(rmin, rmax, bmin, bmax);
   if (!ser) {
-    myq.lnrho = log_val(myq.rho, s_log, s_log + LOG_TABLE_SIZE);
-    myq.lnbeta = log_val(myq.beta, s_log, s_log + LOG_TABLE_SIZE);
+    myq.lnrho = log_val(myq.rho, logt, logt + LOG_TABLE_SIZE);
+    myq.lnbeta = log_val(myq.beta, logt, logt + LOG_TABLE_SIZE);
   }
+  __syncwarp(gmask);   // the previous element's shared records are consumed
   sh.q[le][t] = myq;
   __syncwarp(gmask);
   double out[4];
   if (ser)
-    vjp_element<true>(ops, sh.q[le], sh.mu[le], sh.g[le], gmask, t, myq, ir, ib, out);
+    vjp_element<true>(ops, sh.q[le], mu, sh.g[le], gmask, t, myq, ir, ib, out);
   else
-    vjp_element<false>(ops, sh.q[le], sh.mu[le], sh.g[le], gmask, t, myq, ir, ib, out);
+    vjp_element<false>(ops, sh.q[le], mu, sh.g[le], gmask, t, myq, ir, ib, out);
   for (int c = 0; c < 4; ++c) g[e * ELEM + c * NODES + t] = out[c];
 }
 
-template <int YS>
-__global__ void __launch_bounds__(64) k_vjp_volume(Ops ops, int64_t n_act, const int32_t* __restrict__ elems,
-                                                    const int32_t* __restrict__ level,
-                                                    const int32_t* __restrict__ method, double two_over_len,
-                                                    StageArgs sa, const double* __restrict__ lam,
-                                                    const double* __restrict__ logt, double* __restrict__ g) {
-  __shared__ VolRevShared sh;
-  __shared__ double s_log[2 * LOG_TABLE_SIZE];
-  const int le = threadIdx.x >> 4, t = threadIdx.x & 15;
-  const unsigned gmask = 0xFFFFu << (threadIdx.x & 16);   // the 16 lanes of this group
-  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * VJP_ELEMS;
-  for (int64_t slot = (int64_t)blockIdx.x * VJP_ELEMS + le; slot < n_act; slot += stride)
-    volume_rev_elem<YS>(ops, slot, elems, level, method, two_over_len, sa, lam, s_log, g, sh, le, t, gmask);
-}
-
-// One launch per reverse stage: the volume items (VJP_ELEMS active elements each) and the face
-// items (FREV_IF interfaces or FREV_MORT mortars each) of the stage, dealt to a grid of resident
-// 64-thread blocks from the stage's counter *ticket (zero at launch), volume items first, so that
-// the short face items fill the end.  The two kinds write disjoint outputs (g, gsurf) and depend
-// on nothing the launch writes, so their order does not change the results.
-union RevStageShared {
+// One launch per reverse stage: the volume items (VJP_ELEMS active elements) and the face items
+// (FREV_IF interfaces or FREV_MORT mortars) of the stage, one warp each, dealt to the warps of a
+// resident grid from the stage's counter *ticket (zero at launch): volume items first, so that the
+// shorter face items fill the end.  The two kinds write disjoint outputs (g, gsurf) and depend on
+// nothing the launch writes, so the order of the items does not change the results.
+union RevWarpShared {
   VolRevShared v;
   FaceRevShared f;
 };
+constexpr int VJP_STAGE_THREADS = 64;
 
 template <int YS>
-__global__ void __launch_bounds__(64) k_vjp_stage(Ops ops, int64_t n_act, const int32_t* __restrict__ elems,
-                                                   int64_t n_if, const int4* __restrict__ ifs, int64_t n_mort,
-                                                   const int4* __restrict__ morts, int64_t if_blocks,
-                                                   int64_t face_blocks, const int32_t* __restrict__ level,
-                                                   const int32_t* __restrict__ method, int min_member,
-                                                   double two_over_len, StageArgs sa, const double* __restrict__ lam,
-                                                   const double* __restrict__ logt, double* __restrict__ g,
-                                                   double* __restrict__ gsurf, unsigned long long* ticket) {
-  __shared__ RevStageShared sh;
-  __shared__ double s_log[2 * LOG_TABLE_SIZE];
-  __shared__ unsigned long long s_item;
-  const int le = threadIdx.x >> 4, t = threadIdx.x & 15;
-  const unsigned gmask = 0xFFFFu << (threadIdx.x & 16);
-  for (int q = threadIdx.x; q < 2 * LOG_TABLE_SIZE; q += 64) s_log[q] = logt[q];
+__global__ void __launch_bounds__(VJP_STAGE_THREADS, 8)
+    k_vjp_stage(Ops ops, int64_t n_act, const int32_t* __restrict__ elems, int64_t n_if,
+                const int4* __restrict__ ifs, int64_t n_mort, const int4* __restrict__ morts, int64_t if_items,
+                int64_t face_items, const int32_t* __restrict__ level, const int32_t* __restrict__ method,
+                int min_member, double two_over_len, StageArgs sa, const double* __restrict__ lam,
+                const double* __restrict__ logt, double* __restrict__ g, double* __restrict__ gsurf,
+                unsigned long long* ticket) {
+  __shared__ RevWarpShared sh[VJP_STAGE_THREADS / 32];
+  const int lane = threadIdx.x & 31, le = lane >> 4, t = lane & 15;
+  RevWarpShared& ws = sh[threadIdx.x >> 5];
+  const unsigned gmask = 0xFFFFu << (lane & 16);
   const unsigned long long vol_items = (unsigned long long)((n_act + VJP_ELEMS - 1) / VJP_ELEMS);
-  const unsigned long long items = vol_items + (unsigned long long)face_blocks;
+  const unsigned long long items = vol_items + (unsigned long long)face_items;
   for (;;) {
-    __syncthreads();   // the previous item is done in every thread (shared buffers free)
-    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1ull);
-    __syncthreads();
-    const unsigned long long it = s_item;
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(ticket, 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= items) break;
     if (it < vol_items) {
       const int64_t slot = (int64_t)it * VJP_ELEMS + le;
       if (slot < n_act)
-        volume_rev_elem<YS>(ops, slot, elems, level, method, two_over_len, sa, lam, s_log, g, sh.v, le, t, gmask);
+        volume_rev_elem<YS>(ops, slot, elems, level, method, two_over_len, sa, lam, logt, g, ws.v, le, t, gmask);
     } else {
-      faces_rev_block<YS>(ops, (int64_t)(it - vol_items), n_if, ifs, n_mort, morts, if_blocks, level, method,
-                          min_member, two_over_len, sa, lam, logt, gsurf, sh.f);
+      faces_rev_warp<YS>(ops, (int64_t)(it - vol_items), n_if, ifs, n_mort, morts, if_items, level, method,
+                         min_member, two_over_len, sa, lam, logt, gsurf, ws.f);
     }
+    __syncwarp();   // the item's shared records are consumed before the next item writes them
   }
 }
 
@@ -1378,47 +1351,23 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
   return cudaGetLastError();
 }
 
-cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs,
-                             int64_t n_mort, const int4* morts, int64_t n_all, const int32_t* level,
-                             const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
-                             const double* lam, const double* logt, double* gsurf, bool clear) {
-  if (clear) {
-    cudaError_t e = cudaMemsetAsync(gsurf, 0, (size_t)n_all * ELEM * sizeof(double), st);
-    if (e != cudaSuccess) return e;
-  }
-  const int64_t bi = (n_if + ad::FREV_IF - 1) / ad::FREV_IF, bm = (n_mort + ad::FREV_MORT - 1) / ad::FREV_MORT;
-  if (bi + bm == 0) return cudaSuccess;
-  if (ysrc == Y_GIVEN)
-    ad::k_vjp_faces_rev<Y_GIVEN><<<(unsigned)(bi + bm), ad::FREV_THREADS, 0, st>>>(
-        ops, n_if, ifs, n_mort, morts, bi, level, method, min_member, two_over_len, sa, lam, logt, gsurf);
-  else
-    ad::k_vjp_faces_rev<Y_COMBINE><<<(unsigned)(bi + bm), ad::FREV_THREADS, 0, st>>>(
-        ops, n_if, ifs, n_mort, morts, bi, level, method, min_member, two_over_len, sa, lam, logt, gsurf);
-  return cudaGetLastError();
-}
-
-// blocks of a persistent reverse kernel: at most what is resident at once (the kernels stride or
-// deal items); the capacity is computed once per device and kernel (a repeated computation by
-// racing threads gives the same value); slot: 0, 1 the volume kernels, 2, 3 the stage kernels
+// blocks of the persistent reverse stage kernel: at most what is resident at once (it deals
+// items); the capacity is computed once per device and stage-state source (a repeated
+// computation by racing threads gives the same value)
 template <class Kernel>
 static unsigned resident_blocks(Kernel kernel, int slot, int64_t need) {
   constexpr int MAX_DEVICES = 64;
-  static int cached[4][MAX_DEVICES] = {};
+  static int cached[2][MAX_DEVICES] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   int resident = (dev >= 0 && dev < MAX_DEVICES) ? cached[slot][dev] : 0;
   if (resident == 0) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 64, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ad::VJP_STAGE_THREADS, 0);
     resident = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     if (dev >= 0 && dev < MAX_DEVICES) cached[slot][dev] = resident;
   }
   return (unsigned)(need < resident ? (need > 0 ? need : 1) : resident);
-}
-
-template <int YS>
-static unsigned vjp_volume_blocks(int64_t n_act) {
-  return resident_blocks(ad::k_vjp_volume<YS>, YS, (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS);
 }
 
 cudaError_t launch_vjp_stage(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
@@ -1426,30 +1375,22 @@ cudaError_t launch_vjp_stage(cudaStream_t st, YSource ysrc, const Ops& ops, int6
                              const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
                              const double* lam, const double* logt, double* g, double* gsurf,
                              unsigned long long* ticket) {
+  // items of one warp each: the blocks needed for them, capped at the resident capacity
   const int64_t bi = (n_if + ad::FREV_IF - 1) / ad::FREV_IF, bm = (n_mort + ad::FREV_MORT - 1) / ad::FREV_MORT;
   const int64_t items = (n_act + ad::VJP_ELEMS - 1) / ad::VJP_ELEMS + bi + bm;
   if (items <= 0) return cudaSuccess;
+  constexpr int WARPS = ad::VJP_STAGE_THREADS / 32;
+  const int64_t blocks = (items + WARPS - 1) / WARPS;
   if (ysrc == Y_GIVEN)
-    ad::k_vjp_stage<Y_GIVEN><<<resident_blocks(ad::k_vjp_stage<Y_GIVEN>, 2 + Y_GIVEN, items), 64, 0, st>>>(
+    ad::k_vjp_stage<Y_GIVEN><<<resident_blocks(ad::k_vjp_stage<Y_GIVEN>, Y_GIVEN, blocks), ad::VJP_STAGE_THREADS, 0,
+                               st>>>(
         ops, n_act, elems, n_if, ifs, n_mort, morts, bi, bi + bm, level, method, min_member, two_over_len, sa, lam,
         logt, g, gsurf, ticket);
   else
-    ad::k_vjp_stage<Y_COMBINE><<<resident_blocks(ad::k_vjp_stage<Y_COMBINE>, 2 + Y_COMBINE, items), 64, 0, st>>>(
+    ad::k_vjp_stage<Y_COMBINE><<<resident_blocks(ad::k_vjp_stage<Y_COMBINE>, Y_COMBINE, blocks),
+                                 ad::VJP_STAGE_THREADS, 0, st>>>(
         ops, n_act, elems, n_if, ifs, n_mort, morts, bi, bi + bm, level, method, min_member, two_over_len, sa, lam,
         logt, g, gsurf, ticket);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_vjp_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
-                              const int32_t* level, const int32_t* method, double two_over_len,
-                              const StageArgs& sa, const double* lam, const double* logt, double* g) {
-  if (n_act <= 0) return cudaSuccess;
-  if (ysrc == Y_GIVEN)
-    ad::k_vjp_volume<Y_GIVEN><<<vjp_volume_blocks<Y_GIVEN>(n_act), 64, 0, st>>>(ops, n_act, elems, level, method,
-                                                                              two_over_len, sa, lam, logt, g);
-  else
-    ad::k_vjp_volume<Y_COMBINE><<<vjp_volume_blocks<Y_COMBINE>(n_act), 64, 0, st>>>(ops, n_act, elems, level, method,
-                                                                                  two_over_len, sa, lam, logt, g);
   return cudaGetLastError();
 }
 

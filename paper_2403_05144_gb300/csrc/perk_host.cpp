@@ -354,6 +354,15 @@ struct perk_ctx {
     return fuse_stage && !viscous() && prob.shock_capturing == PERK_SHOCK_OFF;
   }
 
+  // graphs of the stage-storing step and of the reverse step, keyed by their arguments (valid
+  // flags cleared with the step graph's)
+  cudaGraphExec_t graph_store = nullptr, graph_rev = nullptr;
+  bool store_valid = false, rev_valid = false;
+  const void* store_key[2] = {nullptr, nullptr};
+  const void* rev_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  double rev_dt = 0.0;
+  bool rev_recompute = false;
+
   // graph of one step (graph_valid: matches the current mesh, tableau and buffers)
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
@@ -393,12 +402,18 @@ perk_status fail(perk_ctx* ctx, perk_status s, const char* fmt, ...) {
   } while (0)
 
 // marks the step graph stale; the executable graph is kept for an in-place update
-void drop_graph(perk_ctx* ctx) { ctx->graph_valid = false; }
+void drop_graph(perk_ctx* ctx) {
+  ctx->graph_valid = false;
+  ctx->store_valid = false;
+  ctx->rev_valid = false;
+}
 
 void destroy_graph(perk_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
-  ctx->graph = nullptr;
-  ctx->graph_valid = false;
+  if (ctx->graph_store) cudaGraphExecDestroy(ctx->graph_store);
+  if (ctx->graph_rev) cudaGraphExecDestroy(ctx->graph_rev);
+  ctx->graph = ctx->graph_store = ctx->graph_rev = nullptr;
+  drop_graph(ctx);
   ctx->graph_U = nullptr;
 }
 
@@ -1861,11 +1876,12 @@ perk_status perk_rhs_vjp(perk_ctx* ctx, int stage, const double* d_Y, const doub
   StageArgs sa{};
   sa.Y = d_Y;
   const int mm = min_active_member(ctx, stage);
-  PERK_CUDA(ctx, launch_vjp_faces(ctx->stream, Y_GIVEN, ctx->ops, ni, ctx->d_if_sorted.p, nm, ctx->d_mort_sorted.p,
-                                  ctx->n_elem, ctx->d_level.p, ctx->d_method.p, mm, 2.0 / ctx->length, sa, d_lam,
-                                  ctx->d_logtab.p, ctx->d_surf_d.p));
-  PERK_CUDA(ctx, launch_vjp_volume(ctx->stream, Y_GIVEN, ctx->ops, na, ctx->d_elem_sorted.p, ctx->d_level.p,
-                                   ctx->d_method.p, 2.0 / ctx->length, sa, d_lam, ctx->d_logtab.p, d_g));
+  PERK_CUDA(ctx, ctx->d_rctl.ensure(2 * MAX_S));
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_surf_d.p, 0, (size_t)ctx->n_elem * ELEM * sizeof(double), ctx->stream));
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_rctl.p, 0, sizeof(unsigned long long), ctx->stream));
+  PERK_CUDA(ctx, launch_vjp_stage(ctx->stream, Y_GIVEN, ctx->ops, na, ctx->d_elem_sorted.p, ni, ctx->d_if_sorted.p, nm,
+                                  ctx->d_mort_sorted.p, ctx->d_level.p, ctx->d_method.p, mm, 2.0 / ctx->length, sa,
+                                  d_lam, ctx->d_logtab.p, d_g, ctx->d_surf_d.p, ctx->d_rctl.p));
   PERK_CUDA(ctx, launch_vjp_gather(ctx->stream, ctx->n_elem, ctx->d_method.p, mm, ctx->d_surf_d.p, d_g));
   return PERK_OK;
 }
@@ -1886,9 +1902,8 @@ static perk_status step_ready_adjoint(perk_ctx* ctx, const double* d_Un, double 
 // all S stages are evaluated, the last one checks admissibility and the commit updates d_U (as
 // perk_step does); without d_U only K_1 .. K_{S-1} are evaluated: the reverse sweep needs the
 // stage states Y_1 .. Y_S, and none of them is formed from K_S
-static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, double* d_U) {
+static perk_status enqueue_stages(perk_ctx* ctx, cudaStream_t st, const double* d_Un, double* K, double* d_U) {
   const size_t nd = (size_t)ctx->n_elem * ELEM;
-  cudaStream_t st = ctx->stream;
   UpdateArgs ua{};
   ua.b1 = ctx->w_b1;
   ua.bp = ctx->w_bp;
@@ -1927,22 +1942,28 @@ static perk_status enqueue_stages(perk_ctx* ctx, const double* d_Un, double* K, 
   return PERK_OK;
 }
 
-// the reverse sweep of one step whose stages K (from U_n) are stored
-static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt, const double* K,
-                                   const double* d_lam_np1, double* d_lam_n) {
-  const int S = ctx->S;
+// buffers, the second stream and its events of the reverse sweep (allocated outside any capture)
+static perk_status prepare_reverse(perk_ctx* ctx) {
   const size_t nd = (size_t)ctx->n_elem * ELEM;
-  cudaStream_t st = ctx->stream;
   PERK_CUDA(ctx, ctx->d_g.ensure(nd));
   PERK_CUDA(ctx, ctx->d_lamK1.ensure(nd));
   PERK_CUDA(ctx, ctx->d_lamKa.ensure(nd));
   PERK_CUDA(ctx, ctx->d_lamKb.ensure(nd));
   PERK_CUDA(ctx, ctx->d_surf_d.ensure(nd));
+  PERK_CUDA(ctx, ctx->d_rctl.ensure(2 * MAX_S));
   if (!ctx->aux_stream) {
     PERK_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
     PERK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     PERK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   }
+  return PERK_OK;
+}
+
+// the reverse sweep of one step whose stages K (from U_n) are stored (prepare_reverse first)
+static perk_status enqueue_reverse(perk_ctx* ctx, cudaStream_t st, const double* d_Un, double dt, const double* K,
+                                   const double* d_lam_np1, double* d_lam_n) {
+  const int S = ctx->S;
+  const size_t nd = (size_t)ctx->n_elem * ELEM;
   // seed with the final update U_{n+1} = U_n + dt (b1 K_1 + b_{S-1} K_{S-1} + b_S K_S)
   const double b1 = ctx->w_b1, bp = ctx->w_bp, bs = ctx->w_bs;
   double* lam_cur = ctx->d_lamKa.p;    // adjoint of K_i at the current stage i
@@ -1951,10 +1972,8 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
   // face adjoints start from zero; each stage's accumulation clears what it gathers
   PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_surf_d.p, 0, nd * sizeof(double), st));
   const bool fused = ctx->stage_fused();
-  if (fused) {
-    PERK_CUDA(ctx, ctx->d_rctl.ensure(MAX_S));
-    PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_rctl.p, 0, MAX_S * sizeof(unsigned long long), st));
-  }
+  // item counters of the reverse stage launches (two per stage when faces and volume run apart)
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_rctl.p, 0, 2 * MAX_S * sizeof(unsigned long long), st));
   if (S == 1) {
     PERK_CUDA(ctx, launch_adj_seed(st, ctx->n_elem, dt, 0.0, 0.0, b1 + bp + bs, d_lam_np1, d_lam_n, lam_prev, nullptr,
                                    lamK1));
@@ -1981,16 +2000,19 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
                                       ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p,
                                       ctx->d_surf_d.p, ctx->d_rctl.p + i));
     } else {
-      // face adjoints on the second stream, beside the volume adjoint
+      // the face items on the second stream, beside the volume items (the same kernel, so the
+      // results do not depend on the mode)
       PERK_CUDA(ctx, cudaEventRecord(ctx->ev_fork, st));
       PERK_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0));
-      PERK_CUDA(ctx, launch_vjp_faces(ctx->aux_stream, Y_COMBINE, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p,
-                                      ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->n_elem, ctx->d_level.p,
-                                      ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p,
-                                      ctx->d_surf_d.p, false));
+      PERK_CUDA(ctx, launch_vjp_stage(ctx->aux_stream, Y_COMBINE, ctx->ops, 0, ctx->d_elem_sorted.p, ctx->act_if[i],
+                                      ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p, ctx->d_level.p,
+                                      ctx->d_method.p, mm, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p,
+                                      ctx->d_surf_d.p, ctx->d_rctl.p + MAX_S + i));
       PERK_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux_stream));
-      PERK_CUDA(ctx, launch_vjp_volume(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p,
-                                       ctx->d_method.p, 2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p));
+      PERK_CUDA(ctx, launch_vjp_stage(st, Y_COMBINE, ctx->ops, ctx->act_el[i], ctx->d_elem_sorted.p, 0,
+                                      ctx->d_if_sorted.p, 0, ctx->d_mort_sorted.p, ctx->d_level.p, ctx->d_method.p, mm,
+                                      2.0 / ctx->length, sa, lam_i, ctx->d_logtab.p, ctx->d_g.p, ctx->d_surf_d.p,
+                                      ctx->d_rctl.p + i));
       PERK_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0));
     }
     // the stage's halo: its active elements and their face neighbours (a prefix of the sorted list)
@@ -2011,12 +2033,56 @@ static perk_status enqueue_reverse(perk_ctx* ctx, const double* d_Un, double dt,
   return PERK_OK;
 }
 
+// Replays the graph exec of the work enqueue(stream) issues, capturing it again (and updating the
+// executable graph in place where it can) when valid is false; without graphs the work is issued
+// on the context's stream directly.
+extern "C++" {   // (a template, inside the C-linkage block)
+template <class F>
+static perk_status run_captured(perk_ctx* ctx, cudaGraphExec_t& exec, bool& valid, F&& enqueue) {
+  if (!ctx->prob.use_graph) return enqueue(ctx->stream);
+  if (!valid) {
+    cudaGraph_t g = nullptr;
+    PERK_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    perk_status s = enqueue(ctx->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (s != PERK_OK) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return s;
+    }
+    PERK_CUDA(ctx, ce);
+    bool updated = false;
+    if (exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(exec, g, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+      }
+    }
+    cudaError_t ie = updated ? cudaSuccess : cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    PERK_CUDA(ctx, ie);
+    valid = true;
+  }
+  PERK_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+  return PERK_OK;
+}
+}  // extern "C++"
+
 perk_status perk_step_store(perk_ctx* ctx, double* d_U, double dt, double* d_K) {
   if (!ctx) return PERK_E_INVALID_ARG;
   perk_status s = step_ready_adjoint(ctx, d_U, dt);
   if (s != PERK_OK) return s;
   if (!d_K) return fail(ctx, PERK_E_INVALID_ARG, "null stage array");
-  s = enqueue_stages(ctx, d_U, d_K, d_U);
+  if (ctx->store_key[0] != d_U || ctx->store_key[1] != d_K) {
+    ctx->store_valid = false;
+    ctx->store_key[0] = d_U;
+    ctx->store_key[1] = d_K;
+  }
+  s = run_captured(ctx, ctx->graph_store, ctx->store_valid,
+                   [&](cudaStream_t st) { return enqueue_stages(ctx, st, d_U, d_K, d_U); });
   if (s != PERK_OK) return s;
   ctx->counters.steps += 1;
   for (int i = 0; i < ctx->S; ++i) {
@@ -2026,6 +2092,27 @@ perk_status perk_step_store(perk_ctx* ctx, double* d_U, double dt, double* d_K) 
   return PERK_OK;
 }
 
+// the reverse step (with the stages recomputed into the context's array first when recompute)
+static perk_status run_reverse(perk_ctx* ctx, const double* d_Un, double dt, const double* K, bool recompute,
+                               const double* d_lam_np1, double* d_lam_n) {
+  perk_status s = prepare_reverse(ctx);
+  if (s != PERK_OK) return s;
+  const void* key[4] = {d_Un, K, d_lam_np1, d_lam_n};
+  if (!std::equal(key, key + 4, ctx->rev_key) || ctx->rev_dt != dt || ctx->rev_recompute != recompute) {
+    ctx->rev_valid = false;
+    std::copy(key, key + 4, ctx->rev_key);
+    ctx->rev_dt = dt;
+    ctx->rev_recompute = recompute;
+  }
+  return run_captured(ctx, ctx->graph_rev, ctx->rev_valid, [&](cudaStream_t st) {
+    if (recompute) {
+      perk_status r = enqueue_stages(ctx, st, d_Un, const_cast<double*>(K), nullptr);
+      if (r != PERK_OK) return r;
+    }
+    return enqueue_reverse(ctx, st, d_Un, dt, K, d_lam_np1, d_lam_n);
+  });
+}
+
 perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, const double* d_K,
                                  const double* d_lam_np1, double* d_lam_n) {
   if (!ctx) return PERK_E_INVALID_ARG;
@@ -2033,7 +2120,7 @@ perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, c
   if (s != PERK_OK) return s;
   if (!d_K || !d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1)
     return fail(ctx, PERK_E_INVALID_ARG, "bad arguments (lam_n and lam_np1 must be distinct)");
-  return enqueue_reverse(ctx, d_Un, dt, d_K, d_lam_np1, d_lam_n);
+  return run_reverse(ctx, d_Un, dt, d_K, false, d_lam_np1, d_lam_n);
 }
 
 perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const double* d_lam_np1, double* d_lam_n) {
@@ -2043,9 +2130,7 @@ perk_status perk_step_vjp(perk_ctx* ctx, const double* d_Un, double dt, const do
   if (!d_lam_np1 || !d_lam_n || d_lam_n == d_lam_np1)
     return fail(ctx, PERK_E_INVALID_ARG, "bad arguments (lam_n and lam_np1 must be distinct)");
   PERK_CUDA(ctx, ctx->d_Kall.ensure((size_t)ctx->n_elem * ELEM * ctx->S));
-  s = enqueue_stages(ctx, d_Un, ctx->d_Kall.p, nullptr);
-  if (s != PERK_OK) return s;
-  return enqueue_reverse(ctx, d_Un, dt, ctx->d_Kall.p, d_lam_np1, d_lam_n);
+  return run_reverse(ctx, d_Un, dt, ctx->d_Kall.p, true, d_lam_np1, d_lam_n);
 }
 
 perk_status perk_set_volume_blocks(perk_ctx* ctx, int32_t elems_per_block) {
@@ -2054,7 +2139,7 @@ perk_status perk_set_volume_blocks(perk_ctx* ctx, int32_t elems_per_block) {
     return fail(ctx, PERK_E_INVALID_ARG, "elements per block must be 2, 4 or 8");
   if (elems_per_block != ctx->vol_epb) {
     ctx->vol_epb = elems_per_block;
-    ctx->graph_valid = false;
+    drop_graph(ctx);
   }
   return PERK_OK;
 }
@@ -2103,7 +2188,7 @@ perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elem
   PERK_CUDA(ctx, err);
   if (best != ctx->vol_epb) {
     ctx->vol_epb = best;
-    ctx->graph_valid = false;   // the next step re-captures its launches
+    drop_graph(ctx);   // the next step re-captures its launches
   }
   if (elems_per_block) *elems_per_block = best;
   return PERK_OK;

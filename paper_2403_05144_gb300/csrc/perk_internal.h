@@ -177,19 +177,10 @@ cudaError_t launch_jvp(cudaStream_t st, const Ops& ops, int64_t n_if, const int4
                        const int4* morts, int64_t n_el, const int32_t* elems, const int32_t* level,
                        double two_over_len, const double* Y, const double* V, const double* logt, double* surf,
                        double* surf_d, double* K, double* Kd);
-// VJP of one partitioned RHS evaluation in three parts: the face adjoints into gsurf (zeroed
-// first), the volume adjoint of the active prefix into g, and the gather g = (active ? g : 0)
-// + face adjoints.  The first two are independent and may run on different streams.
-// (clear: zero gsurf first; otherwise the caller guarantees it is zero)
-cudaError_t launch_vjp_faces(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_if, const int4* ifs,
-                             int64_t n_mort, const int4* morts, int64_t n_all, const int32_t* level,
-                             const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
-                             const double* lam, const double* logt, double* gsurf, bool clear = true);
-cudaError_t launch_vjp_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
-                              const int32_t* level, const int32_t* method, double two_over_len,
-                              const StageArgs& sa, const double* lam, const double* logt, double* g);
-// The face and volume parts of one reverse stage in one launch (the outputs of the two above);
-// *ticket is the stage's item counter and must be zero at launch.
+// VJP of one partitioned RHS evaluation: the face adjoints into gsurf (which must be zero) and the
+// volume adjoint of the active prefix into g, in one launch of dealt items (n_act = 0: faces only;
+// n_if = n_mort = 0: volume only; *ticket is the launch's item counter and must be zero); then the
+// gather g = (active ? g : 0) + face adjoints.
 cudaError_t launch_vjp_stage(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t n_act, const int32_t* elems,
                              int64_t n_if, const int4* ifs, int64_t n_mort, const int4* morts, const int32_t* level,
                              const int32_t* method, int min_member, double two_over_len, const StageArgs& sa,
