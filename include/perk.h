@@ -258,9 +258,14 @@ perk_status perk_check(perk_ctx* ctx);
  * Euler equations with the plain volume term, the numerical fluxes of a stage's active
  * interfaces and mortars and the volume terms of its active elements run as one kernel whose
  * work items (faces first) are dealt in order to its blocks; each element's volume work waits,
- * with a bounded wait, for its four face fluxes before the surface lifting.  On by default;
- * enabled = 0 selects two launches per stage (face fluxes, then volume terms).  Results are
- * bitwise the same either way.  Other equations and shock capturing always use two launches. */
+ * with a bounded wait, for its four face fluxes before the surface lifting.  On by default
+ * (enabled = 1); enabled = 0 selects two launches per stage (face fluxes, then volume terms).
+ * enabled = 2 selects one launch per step for steps of at most 32 stages without a stage
+ * pattern: the items of all stages are dealt in stage order from one counter, and an item waits
+ * (bounded) for the stage vectors of the elements it reads through per-element progress stamps;
+ * a wait that gives up abandons the step, which is then not committed (perk_check reports
+ * PERK_E_TIMEOUT).  Results are bitwise the same in every mode.  Other equations and shock
+ * capturing always use two launches.  Returns PERK_E_INVALID_ARG for other values. */
 perk_status perk_set_stage_fusion(perk_ctx* ctx, int enabled);
 
 /* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed

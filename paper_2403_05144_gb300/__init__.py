@@ -270,9 +270,10 @@ class PerkSolver:
                 "active_interfaces": list(inf.active_interfaces[:S]), "active_mortars": list(inf.active_mortars[:S]),
                 "index_bytes": inf.index_bytes}
 
-    def set_stage_fusion(self, enabled: bool):
-        """One launch per stage (faces and volume together; the default) or two."""
-        self._call(self.lib.perk_set_stage_fusion, C.c_int(1 if enabled else 0))
+    def set_stage_fusion(self, mode):
+        """0 / False: two launches per stage; 1 / True: one launch per stage (faces and volume
+        together); 2: one launch per step (all stages' items in order)."""
+        self._call(self.lib.perk_set_stage_fusion, C.c_int(int(mode)))
 
     def workspace_bytes(self, n_cells: int = 0) -> int:
         """Bytes of a caller-owned workspace serving meshes of up to n_cells cells (0: the current mesh)."""

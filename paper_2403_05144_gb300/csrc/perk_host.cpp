@@ -349,10 +349,14 @@ struct perk_ctx {
   // equations allow it; its work counters and per-face stamps.  On by default: on GB300 it is the
   // faster form (KH 3,904 cells 0.603 against 0.618 ms/step, 114,688 cells 5.53 against 5.58)
   bool fuse_stage = true;
-  DevBuf<unsigned long long> d_ctl, d_stamp;
+  // one launch per step (k_step: all stages' items dealt in order, element progress stamps), where
+  // one launch per stage would be used and the step has at most STEP_MAX_S stages
+  bool fuse_step = false;
+  DevBuf<unsigned long long> d_ctl, d_stamp, d_prog;   // d_prog: element progress of the one-launch step
   bool stage_fused() const {
     return fuse_stage && !viscous() && prob.shock_capturing == PERK_SHOCK_OFF;
   }
+  bool step_fused() const { return fuse_step && stage_fused() && !pattern_mode && S <= STEP_MAX_S; }
 
   // graphs of the stage-storing step and of the reverse step, keyed by their arguments (valid
   // flags cleared with the step graph's)
@@ -428,7 +432,7 @@ void for_each_buffer(perk_ctx* c, F&& f) {
   f(c->d_flag); f(c->d_logtab); f(c->d_map); f(c->d_eta); f(c->d_surf_d); f(c->d_Kall); f(c->d_Kpat); f(c->d_g);
   f(c->d_lamK1); f(c->d_lamKa); f(c->d_lamKb); f(c->d_rctl); f(c->d_wsurf); f(c->d_q); f(c->d_vsurf);
   f(c->d_cells); f(c->d_newcells); f(c->d_key); f(c->d_des); f(c->d_off); f(c->d_cnt_if); f(c->d_cnt_mort);
-  f(c->d_off_if); f(c->d_off_mort); f(c->d_info); f(c->d_ctl); f(c->d_stamp);
+  f(c->d_off_if); f(c->d_off_mort); f(c->d_info); f(c->d_ctl); f(c->d_stamp); f(c->d_prog);
 }
 
 // The buffers a caller-bound workspace holds, in layout order, with their sizes (elements of
@@ -451,7 +455,7 @@ void for_each_workspace_buffer(perk_ctx* c, int64_t cells, F&& f) {
   f(c->d_map, 5 * n); f(c->d_E, (size_t)MAX_S); f(c->d_minmax, (size_t)2); f(c->d_flag, (size_t)1);
   f(c->d_cells, n); f(c->d_newcells, n); f(c->d_key, n); f(c->d_des, n); f(c->d_off, n + 1);
   f(c->d_cnt_if, n); f(c->d_cnt_mort, n); f(c->d_off_if, n); f(c->d_off_mort, n); f(c->d_info, (size_t)8);
-  f(c->d_ctl, (size_t)MAX_S + 1); f(c->d_stamp, 4 * n);
+  f(c->d_ctl, (size_t)MAX_S + 1); f(c->d_stamp, 4 * n); f(c->d_prog, n);
 }
 
 // a mesh-sized buffer for n entries: a quarter of headroom when the library allocates it (the
@@ -795,6 +799,8 @@ perk_status set_mesh(perk_ctx* ctx, int64_t n_cells, const int32_t* cells, const
   // face stamps of the fused stage kernel: zero is older than any launch
   PERK_CUDA(ctx, ctx->d_stamp.ensure(4 * ne));
   PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_stamp.p, 0, 4 * ne * sizeof(unsigned long long), ctx->stream));
+  PERK_CUDA(ctx, ctx->d_prog.ensure(ne));
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_prog.p, 0, ne * sizeof(unsigned long long), ctx->stream));
   PERK_CUDA(ctx, cudaMemcpyAsync(ctx->d_level.p, ctx->h_level.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice,
                                  ctx->stream));
   if (!ctx->h_if.empty())
@@ -947,6 +953,39 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
   ua.K1 = Kall ? Kall : ctx->d_K1.p;
   ua.flag = ctx->d_flag.p;
   ua.member = ctx->n_members > 1 ? ctx->d_member.p : nullptr;
+  if (ctx->step_fused() && !timer) {
+    // one launch for all stages: the same buffers as the stage-by-stage loop below
+    StepPlan plan{};
+    plan.S = S;
+    plan.first[0] = 0;
+    for (int i = 0; i < S; ++i) {
+      cur = (i == 0) ? 0 : (i % 2 == 1 ? 1 : 2);
+      plan.n_if[i] = ctx->act_if[i];
+      plan.n_mort[i] = ctx->act_mort[i];
+      plan.n_el[i] = ctx->act_el[i];
+      plan.first[i + 1] = plan.first[i] + step_stage_items(ctx->act_if[i], ctx->act_mort[i], ctx->act_el[i]);
+      plan.K[i] = Kbuf[cur];
+      plan.Kp[i] = Kbuf[prev];
+      if (i == S - 1) K_before_last = Kbuf[prev];
+      prev = cur;
+    }
+    StageArgs sa{};
+    sa.U = d_U;
+    sa.K1 = ctx->d_K1.p;
+    sa.nd = (int64_t)nd;
+    sa.coef = ctx->d_coef.p;
+    sa.dt = ctx->d_dt.p;
+    sa.member = ua.member;
+    UpdateArgs chk = ua;
+    chk.Kp = K_before_last;
+    PERK_CUDA(ctx, launch_step(st, ctx->ops, plan, ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_elem_sorted.p,
+                               ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length, sa, ctx->d_surf.p, chk,
+                               ctx->d_logtab.p, ctx->d_ctl.p, ctx->d_stamp.p, ctx->d_prog.p, ctx->d_flag.p));
+    ua.Kp = K_before_last;
+    ua.stage_ctl = ctx->d_ctl.p;
+    PERK_CUDA(ctx, launch_commit(st, ctx->n_elem, ua, Kbuf[cur], ctx->d_dt.p, d_U));
+    return PERK_OK;
+  }
   for (int i = 0; i < S; ++i) {
     cur = (i == 0) ? 0 : (i % 2 == 1 ? 1 : 2);
     StageArgs sa{};
@@ -1812,8 +1851,10 @@ perk_status perk_check(perk_ctx* ctx) {
 
 perk_status perk_set_stage_fusion(perk_ctx* ctx, int enabled) {
   if (!ctx) return PERK_E_INVALID_ARG;
-  if (ctx->fuse_stage != (enabled != 0)) {
+  if (enabled < 0 || enabled > 2) return fail(ctx, PERK_E_INVALID_ARG, "fusion mode must be 0, 1 or 2");
+  if (ctx->fuse_stage != (enabled != 0) || ctx->fuse_step != (enabled == 2)) {
     ctx->fuse_stage = enabled != 0;
+    ctx->fuse_step = enabled == 2;
     drop_graph(ctx);
   }
   return PERK_OK;
@@ -2402,6 +2443,8 @@ static perk_status adapt_commit_device(perk_ctx* ctx, const double* d_Uold, doub
   }
   PERK_CUDA(ctx, grow(ctx->d_stamp, 4 * mm));
   PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_stamp.p, 0, 4 * mm * sizeof(unsigned long long), st));
+  PERK_CUDA(ctx, grow(ctx->d_prog, mm));
+  PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_prog.p, 0, mm * sizeof(unsigned long long), st));
   PERK_CUDA(ctx, launch_amr_leaves(st, n, ctx->d_cells.p, ctx->d_des.p, ctx->d_off.p, ctx->d_newcells.p,
                                    ctx->d_key.p, ctx->d_map.p));
   PERK_CUDA(ctx, launch_transfer(st, m, ctx->d_map.p, d_Uold, ctx->ops, d_Unew));

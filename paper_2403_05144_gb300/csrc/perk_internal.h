@@ -71,6 +71,12 @@ struct StageArgs {
   const int32_t* member;  //            ensemble member of each element (nullptr: member 0)
   const double* Kall;     //            all stages, stage s at Kall + s * nd (nullptr: use Kp)
   int64_t nd;
+  // one launch per step only: the elements' progress stamps (stage s of the step complete at
+  // prog_base + s + 1), the stage these arguments serve, and the flag raised if a wait gives up
+  const unsigned long long* prog;
+  unsigned long long prog_base;
+  int stage;
+  int* err;
 };
 
 #ifdef __CUDACC__
@@ -129,6 +135,25 @@ cudaError_t launch_volume(cudaStream_t st, YSource ysrc, const Ops& ops, int64_t
 // before the first step; the step's final update, with UpdateArgs::stage_ctl = ctl, makes it ready
 // for the next step), stamps[4 * n_elem] (zero, or stamps of earlier launches with the same ctl),
 // err: bit 1 raised if a volume item gives up waiting.
+// One launch per step (k_step): the work items of all stages, dealt in stage order (faces, then
+// volume items, within each stage) from one counter; stage i's items are first[i] .. first[i+1].
+constexpr int STEP_MAX_S = 32;
+struct StepPlan {
+  int S;
+  int64_t first[STEP_MAX_S + 1];
+  int64_t n_if[STEP_MAX_S], n_mort[STEP_MAX_S], n_el[STEP_MAX_S];   // active counts of each stage
+  double* K[STEP_MAX_S];          // stage i's output
+  const double* Kp[STEP_MAX_S];   // K_{i-1} as stage i reads it
+};
+// items of one stage (faces first), as k_step deals them
+int64_t step_stage_items(int64_t n_if, int64_t n_mort, int64_t n_el);
+// sa: U, K_1, the coefficients of stage 0 (stage i at sa.coef + i * MAX_R), dt, member;
+// check: the last stage's admissibility arguments; ctl[0] is the item counter (zero at launch;
+// the commit resets it), ctl[MAX_S] the step count; prog: n progress stamps
+cudaError_t launch_step(cudaStream_t st, const Ops& ops, const StepPlan& plan, const int4* ifs, const int4* morts,
+                        const int32_t* elems, const int32_t* level, const int32_t* method, double two_over_len,
+                        const StageArgs& sa, double* surf, const UpdateArgs& check, const double* log_table,
+                        unsigned long long* ctl, unsigned long long* stamps, unsigned long long* prog, int* err);
 cudaError_t launch_stage(cudaStream_t st, int stage, const Ops& ops, int64_t n_if, const int4* ifs, int64_t n_mort,
                          const int4* morts, int64_t n_el, const int32_t* elems, const int32_t* level,
                          const int32_t* method, double two_over_len, const StageArgs& sa, double* surf, double* K,

@@ -343,45 +343,8 @@ __device__ __forceinline__ void surface_flux(const double uL[4], const double uR
     flux_hll(uL, uR, dir, ops, f);
 }
 
-// ---------------------------------------------------------------------------
-// Stage state at one node of element e.
-__device__ __forceinline__ int face_node(int face, int k) {
-  // faces: 0 = -x (i = 0), 1 = +x (i = N), 2 = -y (j = 0), 3 = +y (j = N); node index = j * 4 + i
-  return face == 0 ? 4 * k : face == 1 ? 4 * k + 3 : face == 2 ? k : 12 + k;
-}
-
-template <int YS>
-__device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int m, int node, double y[4]) {
-  const int64_t base = e * ELEM + node;
-  if (YS == Y_GIVEN) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.Y + base + v * NODES);
-  } else {
-    const StageCoef c = sa.coef[m];
-    const double dt = sa.dt[sa.member ? sa.member[e] : 0];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.U + base + v * NODES);
-    if (__double_as_longlong(c.alpha) != 0) {   // integer test, off the FP64 pipe
-      const double da = dt * c.alpha;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) y[v] = fma(da, __ldg(sa.K1 + base + v * NODES), y[v]);
-    }
-    if (__double_as_longlong(c.beta) != 0) {
-      const double db = dt * c.beta;
-      const double* Kp = coupled_stage(sa, c);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) y[v] = fma(db, __ldg(Kp + base + v * NODES), y[v]);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Faces: 4 threads per interface (one per face node), 8 per mortar (half, node).
-constexpr int FACE_THREADS = 32;
-constexpr int IF_PER_BLOCK = FACE_THREADS / 4;
-constexpr int MORT_PER_BLOCK = FACE_THREADS / 8;
-
-// Stamps of the fused stage kernel (k_stage): the launch that last wrote a face's numerical flux.
+// Stamps of the fused kernels: the stage of the step that last wrote a face's numerical flux
+// (k_stage, k_step) or completed an element's stage vector (k_step).
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -395,6 +358,78 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+
+constexpr int STAMP_WAIT_LIMIT = 1 << 23;   // polls (about 32 ns apart) before a wait gives up
+
+// waits until the stamp at p reaches v (relaxed polls, then one fence: the values were written
+// before the stamp was released; stamps only grow); false if the wait gives up
+__device__ __forceinline__ bool wait_stamp(const unsigned long long* p, unsigned long long v) {
+  unsigned ns = 32;
+  for (int it = 0; it < STAMP_WAIT_LIMIT; ++it) {
+    if (ld_relaxed(p) >= v) {
+      __threadfence();
+      return true;
+    }
+    __nanosleep(ns);
+    ns = ns < 512 ? 2 * ns : 512;   // back off: few polls from many waiting warps
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Stage state at one node of element e.
+__device__ __forceinline__ int face_node(int face, int k) {
+  // faces: 0 = -x (i = 0), 1 = +x (i = N), 2 = -y (j = 0), 3 = +y (j = N); node index = j * 4 + i
+  return face == 0 ? 4 * k : face == 1 ? 4 * k + 3 : face == 2 ? k : 12 + k;
+}
+
+// Y_LIVE (one launch per step): as Y_COMBINE, but K_1 and K_{i-1} are written by the same launch:
+// the element's progress stamp is awaited first, and they are read through L2 (not the read-only
+// path, which may hold values from before the launch wrote them).
+constexpr int Y_LIVE = 2;
+
+template <int YS>
+__device__ __forceinline__ double ld_stage_vec(const double* p) {
+  if (YS == Y_LIVE) return __ldcg(p);
+  return __ldg(p);
+}
+
+template <int YS>
+__device__ __forceinline__ void stage_state(const StageArgs& sa, int64_t e, int m, int node, double y[4]) {
+  const int64_t base = e * ELEM + node;
+  if (YS == Y_GIVEN) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.Y + base + v * NODES);
+  } else {
+    const StageCoef c = sa.coef[m];
+    const double dt = sa.dt[sa.member ? sa.member[e] : 0];
+    const bool use_a = __double_as_longlong(c.alpha) != 0;   // integer tests, off the FP64 pipe
+    const bool use_b = __double_as_longlong(c.beta) != 0;
+    if (YS == Y_LIVE && sa.prog && (use_a || use_b)) {
+      // K_{i-1} is complete once stage i-1 of the element is, K_1 once stage 0 is
+      if (!wait_stamp(sa.prog + e, sa.prog_base + (use_b ? sa.stage : 1))) atomicOr(sa.err, 2);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.U + base + v * NODES);
+    if (use_a) {
+      const double da = dt * c.alpha;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) y[v] = fma(da, ld_stage_vec<YS>(sa.K1 + base + v * NODES), y[v]);
+    }
+    if (use_b) {
+      const double db = dt * c.beta;
+      const double* Kp = coupled_stage(sa, c);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) y[v] = fma(db, ld_stage_vec<YS>(Kp + base + v * NODES), y[v]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Faces: 4 threads per interface (one per face node), 8 per mortar (half, node).
+constexpr int FACE_THREADS = 32;
+constexpr int IF_PER_BLOCK = FACE_THREADS / 4;
+constexpr int MORT_PER_BLOCK = FACE_THREADS / 8;
 
 // 8 interfaces (4 threads each, one per face node) starting at `first`.  STAMP: after the
 // fluxes are written, each interface's two element faces are stamped with `stamp` (release), so
@@ -531,23 +566,9 @@ __device__ __forceinline__ int pair_slot(int a, int b) {  // a < b, slots 0..5
 struct FaceWait {
   const unsigned long long* stamps;
   unsigned long long stamp;
-  int* err;   // bit 1 raised if a wait gives up
+  int* err;                    // bit 1 raised if a wait gives up
+  unsigned long long* prog;    // one launch per step: the elements' progress stamps (else nullptr)
 };
-constexpr int STAMP_WAIT_LIMIT = 1 << 23;   // polls (about 32 ns apart) before a wait gives up
-
-// waits until the stamp at p reaches v (relaxed polls, then one fence: the face's values were
-// written before its stamp was released); false if the wait gives up
-__device__ __forceinline__ bool wait_stamp(const unsigned long long* p, unsigned long long v) {
-  for (int it = 0; it < STAMP_WAIT_LIMIT; ++it) {
-    if (ld_relaxed(p) == v) {
-      __threadfence();
-      return true;
-    }
-    __nanosleep(32);
-  }
-  return false;
-}
-
 // Shared memory of a volume item (VOL_ELEMS elements, 16 threads each); with shock capturing
 // also the stage state and the indicator variable.
 template <int VOL_ELEMS, bool SHOCK>
@@ -761,16 +782,24 @@ __device__ __forceinline__ void volume_item(const Ops& ops, int64_t n, int64_t s
     kv[v] = scale * acc[v];
     K[e * ELEM + v * NODES + t] = kv[v];
   }
+  if (FUSED && fw.prog) {
+    // one launch per step: this stage of the element is complete (its K values written first)
+    __threadfence();
+    __syncwarp(0xFFFFu << (threadIdx.x & 16));
+    if (t == 0) st_release(fw.prog + e, fw.stamp);
+  }
   if (CHECK) {
-    // admissibility of the state this step would commit at this node
+    // admissibility of the state this step would commit at this node (K_1 and K_{S-1} were written
+    // earlier in the same launch where YS is Y_LIVE, and are complete: this element's stage
+    // state waited for them)
     const double dt = sa.dt[sa.member ? sa.member[e] : 0];
     const int64_t base = e * ELEM + t;
     double un[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       double inc = ua.bs * kv[v];
-      if (ua.b1 != 0.0) inc = fma(ua.b1, __ldg(ua.K1 + base + v * NODES), inc);
-      if (ua.bp != 0.0) inc = fma(ua.bp, __ldg(ua.Kp + base + v * NODES), inc);
+      if (ua.b1 != 0.0) inc = fma(ua.b1, ld_stage_vec<YS>(ua.K1 + base + v * NODES), inc);
+      if (ua.bp != 0.0) inc = fma(ua.bp, ld_stage_vec<YS>(ua.Kp + base + v * NODES), inc);
       un[v] = fma(dt, inc, __ldg(ua.U + base + v * NODES));
     }
     const double p = ops.gm1 * (un[3] - 0.5 * (un[1] * un[1] + un[2] * un[2]) / un[0]);
@@ -861,7 +890,115 @@ __global__ void __launch_bounds__(FACE_THREADS) k_stage(Ops ops, int64_t n_if, c
   } else if (item < items) {
     volume_item<Y_COMBINE, CHECK, STAGE_VE, false, true>(ops, n_el, (item - face_items) * STAGE_VE, elems, level,
                                                          method, two_over_len, sa, surf, K, ua, log_table, s_log,
-                                                         sh.vol, FaceWait{sync.stamps, stamp, sync.err});
+                                                         sh.vol, FaceWait{sync.stamps, stamp, sync.err, nullptr});
+  }
+}
+
+// One launch per step: every warp takes items in stage order from one counter (the next one
+// fetched while the current one runs).  An item waits, with bounded waits, only for items dealt
+// before it (a face item for the stage vectors of its elements, a volume item for those and for
+// its four faces), so the warp holding the smallest unfinished item never waits and every
+// wait ends.  The waits also order the reuse of the buffers: the two buffers that alternate for
+// K_2, K_3, .. and the face fluxes are overwritten only by items that waited for every reader
+// of the previous contents.
+int64_t step_stage_items(int64_t n_if, int64_t n_mort, int64_t n_el) {
+  return (n_if + IF_PER_BLOCK - 1) / IF_PER_BLOCK + (n_mort + MORT_PER_BLOCK - 1) / MORT_PER_BLOCK +
+         (n_el + STAGE_VE - 1) / STAGE_VE;
+}
+
+__global__ void __launch_bounds__(FACE_THREADS) k_step(Ops ops, StepPlan plan, const int4* __restrict__ ifs,
+                                                      const int4* __restrict__ morts,
+                                                      const int32_t* __restrict__ elems,
+                                                      const int32_t* __restrict__ level,
+                                                      const int32_t* __restrict__ method, double two_over_len,
+                                                      StageArgs sa, double* __restrict__ surf, UpdateArgs check,
+                                                      const double* __restrict__ log_table, StageSync sync,
+                                                      unsigned long long* prog) {
+  static_assert(STAGE_VE * NODES == FACE_THREADS, "one warp per work item");
+  __shared__ unsigned long long s_launch;
+  __shared__ double s_log[2 * LOG_TABLE];
+  __shared__ union {
+    VolumeShared<STAGE_VE, false> vol;
+    double half[MORT_PER_BLOCK][2][4][NN];
+  } sh;
+  const int lane = threadIdx.x;
+  if (lane == 0) s_launch = *(volatile unsigned long long*)(sync.ctl + MAX_S);
+  __syncwarp();
+  const unsigned long long base = s_launch * MAX_S;
+  const int64_t items = plan.first[plan.S];
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(sync.ctl, 1ull);
+  next = __shfl_sync(0xffffffffu, next, 0);
+  for (;;) {
+    const int64_t item = (int64_t)next;
+    // a wait that gave up abandons the launch (the step is then not committed): no further item
+    // waits its full bound
+    int gave_up = 0;
+    if (lane == 0) gave_up = *(volatile int*)sync.err & 2;
+    if (item >= items || __shfl_sync(0xffffffffu, gave_up, 0)) break;
+    if (lane == 0) next = atomicAdd(sync.ctl, 1ull);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    int i = 0;
+    while (item >= plan.first[i + 1]) ++i;
+    const int64_t local = item - plan.first[i];
+    StageArgs s = sa;
+    s.Kp = plan.Kp[i];
+    s.coef = sa.coef + (size_t)i * MAX_R;
+    s.prog = nullptr;   // the item's waits are done here, one lane per element
+    const unsigned long long stamp = base + i + 1;
+    const int64_t if_items = (plan.n_if[i] + IF_PER_BLOCK - 1) / IF_PER_BLOCK;
+    const int64_t face_items = if_items + (plan.n_mort[i] + MORT_PER_BLOCK - 1) / MORT_PER_BLOCK;
+    {
+      // the element whose stage vectors this lane waits for (-1: none), and its member
+      int64_t we = -1;
+      int wm = 0;
+      if (local < if_items) {
+        const int64_t idx = local * IF_PER_BLOCK + (lane >> 2);
+        if (idx < plan.n_if[i] && (lane & 3) < 2) {
+          const int4 r = ifs[idx];
+          we = (lane & 3) == 0 ? r.x : r.y;
+          wm = r.w;
+        }
+      } else if (local < face_items) {
+        const int64_t idx = (local - if_items) * MORT_PER_BLOCK + (lane >> 3);
+        const int sub = lane & 7;   // 0: the large element, 1, 2: the small ones
+        if (idx < plan.n_mort[i] && sub < 3) {
+          const int4 r = morts[idx];
+          we = sub == 0 ? r.x : (sub == 1 ? r.y : r.z);
+          wm = sub == 0 ? method[r.x] : r.w >> 2;
+        }
+      } else {
+        const int64_t slot = (local - face_items) * STAGE_VE + (lane >> 4);
+        if (slot < plan.n_el[i] && (lane & 15) == 0) {
+          we = elems[slot];
+          wm = method[we];
+        }
+      }
+      if (we >= 0) {
+        const StageCoef c = s.coef[wm];
+        const bool use_a = __double_as_longlong(c.alpha) != 0, use_b = __double_as_longlong(c.beta) != 0;
+        // K_{i-1} is complete once stage i-1 of the element is, K_1 once stage 0 is
+        if ((use_a || use_b) && !wait_stamp(prog + we, base + (use_b ? i : 1))) atomicOr(sync.err, 2);
+      }
+      __syncwarp();
+    }
+    if (local < if_items) {
+      face_item_interfaces<Y_LIVE, true>(ops, plan.n_if[i], ifs, local * IF_PER_BLOCK, s, surf, sync.stamps, stamp);
+    } else if (local < face_items) {
+      face_item_mortars<Y_LIVE, true>(ops, plan.n_mort[i], morts, (local - if_items) * MORT_PER_BLOCK, method, s,
+                                      surf, sh.half, sync.stamps, stamp);
+    } else {
+      const FaceWait fw{sync.stamps, stamp, sync.err, prog};
+      const int64_t slot0 = (local - face_items) * STAGE_VE;
+      if (i == plan.S - 1)
+        volume_item<Y_LIVE, true, STAGE_VE, false, true>(ops, plan.n_el[i], slot0, elems, level, method, two_over_len,
+                                                         s, surf, plan.K[i], check, log_table, s_log, sh.vol, fw);
+      else
+        volume_item<Y_LIVE, false, STAGE_VE, false, true>(ops, plan.n_el[i], slot0, elems, level, method,
+                                                          two_over_len, s, surf, plan.K[i], check, log_table, s_log,
+                                                          sh.vol, fw);
+    }
+    __syncwarp();   // the item's shared records are consumed before the next item writes them
   }
 }
 
@@ -1330,6 +1467,39 @@ cudaError_t launch_stage(cudaStream_t st, int stage, const Ops& ops, int64_t n_i
     k_stage<false><<<(unsigned)items, FACE_THREADS, 0, st>>>(ops, n_if, ifs, n_mort, morts, n_el, elems, level,
                                                               method, two_over_len, sa, surf, K, ua, log_table, sync,
                                                               resident);
+  return cudaGetLastError();
+}
+
+// blocks of k_step: the resident capacity (computed once per device)
+static int step_resident_blocks() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, FACE_THREADS, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  n = per_sm * device_sm_count();
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
+cudaError_t launch_step(cudaStream_t st, const Ops& ops, const StepPlan& plan, const int4* ifs, const int4* morts,
+                        const int32_t* elems, const int32_t* level, const int32_t* method, double two_over_len,
+                        const StageArgs& sa, double* surf, const UpdateArgs& check, const double* log_table,
+                        unsigned long long* ctl, unsigned long long* stamps, unsigned long long* prog, int* err) {
+  if (plan.S < 1 || plan.S > STEP_MAX_S || ops.shock != PERK_SHOCK_OFF) return cudaErrorInvalidValue;
+  const int64_t items = plan.first[plan.S];
+  if (items <= 0) return cudaSuccess;
+  const int64_t cap = step_resident_blocks();
+  if (cap <= 0) return cudaErrorInvalidConfiguration;
+  const StageSync sync{ctl, stamps, err, 0};
+  k_step<<<(unsigned)std::min<int64_t>(cap, items), FACE_THREADS, 0, st>>>(
+      ops, plan, ifs, morts, elems, level, method, two_over_len, sa, surf, check, log_table, sync, prog);
   return cudaGetLastError();
 }
 

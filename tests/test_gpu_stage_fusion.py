@@ -1,6 +1,7 @@
-"""One launch per stage (k_stage: face fluxes and volume terms together) against two launches per
-stage: the same arithmetic on the same data, so the steps must agree bit for bit; the fused
-steps are also checked against the oracle by the parity tests, which run with fusion on."""
+"""One launch per step (k_step: all stages' items dealt in order, mode 2) and one launch per stage
+(k_stage: face fluxes and volume terms together, mode 1) against two launches per stage (mode 0):
+the same arithmetic on the same data, so the steps must agree bit for bit; the fused steps are also
+checked against the oracle here and by the parity tests, which run in the default mode."""
 import numpy as np
 import pytest
 
@@ -38,22 +39,22 @@ def test_fused_steps_bitwise_equal_to_two_launches(use_graph, flux):
     cells = kh_band_cells(4, 7, 0.03)
     U0 = torch.from_numpy(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)).cuda()
     out = []
-    for fused in (True, False):
-        s = solver(cells, fused, use_graph, flux)
+    for mode in (2, 1, 0):
+        s = solver(cells, mode, use_graph, flux)
         U = U0.clone()
         dt = s.compute_dt(U, 0.7)
         for _ in range(5):
             s.step(U, dt)
         s.check()
         out.append(U)
-    assert torch.equal(out[0], out[1])
+    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
 
 
 def test_fused_steps_with_amr_and_ensembles():
     # dynamic AMR (device-built meshes) and a two-member ensemble with per-member dt
     amr = dict(level_min=3, level_max=6, refine_above=0.1, coarsen_below=0.02)
     out = []
-    for fused in (True, False):
+    for fused in (2, 1, 0):
         s = solver(uniform_cells(3), fused)
         U = torch.from_numpy(nodal_state(kelvin_helmholtz, uniform_cells(3), -1.0, 2.0, X3)).cuda()
         for _ in range(4):
@@ -63,11 +64,11 @@ def test_fused_steps_with_amr_and_ensembles():
                 s.step(U, dt)
         s.check()
         out.append(U)
-    assert torch.equal(out[0], out[1])
+    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
     from paper_2403_05144_gb300 import PerkSolver
     meshes = [kh_band_cells(4, 6, 0.05), nested_band_cells(2, 5)]
     res = []
-    for fused in (True, False):
+    for fused in (2, 1, 0):
         e = PerkSolver(surface_flux="hllc")
         e.set_stage_fusion(fused)
         e.upload_ensemble(meshes, -1.0, 2.0)
@@ -78,14 +79,14 @@ def test_fused_steps_with_amr_and_ensembles():
             e.step(U, dts)
         e.check()
         res.append(U)
-    assert torch.equal(res[0], res[1])
+    assert torch.equal(res[0], res[2]) and torch.equal(res[1], res[2])
 
 
 def test_fused_pattern_steps_and_profile():
     cells = nested_band_cells(2, 5)
     U0 = torch.from_numpy(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)).cuda()
     out = []
-    for fused in (True, False):
+    for fused in (2, True, False):   # stage patterns keep one launch per stage in mode 2
         s = solver(cells, fused, E=(4, 8))
         s.set_perk2_pattern([4, 8], "early")
         U = U0.clone()
@@ -93,20 +94,21 @@ def test_fused_pattern_steps_and_profile():
             s.step(U, 2e-3)
         s.check()
         out.append(U)
-    assert torch.equal(out[0], out[1])
+    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
     s = solver(cells, True)
     U = U0.clone()
     acc = s.step_profiled(U, 2e-3)
     assert acc.launches[0] == 0 and acc.launches[1] == 16 and acc.launches[2] == 1
 
 
-def test_fused_step_matches_oracle_on_four_levels():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fused_step_matches_oracle_on_four_levels(mode):
     cells = nested_band_cells(2, 5)
     U0 = nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)
     m = TreeMesh(cells, -1.0, 2.0)
     fam = perk2_family([4, 6, 10, 16])
     dt = max_wave_speed_dt(U0, m.h, 3, 0.7)
-    s = solver(cells, True)
+    s = solver(cells, mode)
     U = torch.from_numpy(U0.copy()).cuda()
     want = U0
     dg = DGSEM(m, 3, "hllc")
