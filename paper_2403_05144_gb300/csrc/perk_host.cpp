@@ -264,6 +264,17 @@ struct perk_ctx {
   Ops ops{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // pinned host block for the small readbacks (counts, plan sizes, dt, flag): copies into it are
+  // asynchronous, so a call that reads several values back waits once
+  struct Pinned {
+    int64_t counts[6 * MAX_S];
+    int64_t info[8];
+    int64_t nf[2];
+    int32_t minmax[2];
+    double dt;
+    int flag;
+  };
+  Pinned* h_pin = nullptr;
   std::string err;
 
   // mesh (host)
@@ -659,13 +670,18 @@ perk_status run_partition(perk_ctx* ctx, bool device_faces = false) {
                                   ctx->n_members, ctx->d_member_lmax.p, ctx->d_method.p, ctx->d_elem_sorted.p,
                                   ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->d_counts.p, ctx->d_minmax.p, 2,
                                   device_faces ? ctx->d_info.p + 2 : nullptr));
-  int64_t counts[6 * MAX_S];
-  int32_t mm[2];
-  int64_t nf[2] = {ctx->n_if, ctx->n_mort};
-  PERK_CUDA(ctx, cudaMemcpyAsync(counts, ctx->d_counts.p, sizeof counts, cudaMemcpyDeviceToHost, ctx->stream));
-  PERK_CUDA(ctx, cudaMemcpyAsync(mm, ctx->d_minmax.p, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream));
+  perk_ctx::Pinned* pin = ctx->h_pin;
+  const int64_t* counts = pin->counts;
+  const int32_t* mm = pin->minmax;
+  const int64_t* nf = pin->nf;
+  pin->nf[0] = ctx->n_if;
+  pin->nf[1] = ctx->n_mort;
+  PERK_CUDA(ctx, cudaMemcpyAsync(pin->counts, ctx->d_counts.p, sizeof pin->counts, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  PERK_CUDA(ctx, cudaMemcpyAsync(pin->minmax, ctx->d_minmax.p, sizeof pin->minmax, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
   if (device_faces)
-    PERK_CUDA(ctx, cudaMemcpyAsync(nf, ctx->d_info.p + 2, sizeof nf, cudaMemcpyDeviceToHost, ctx->stream));
+    PERK_CUDA(ctx, cudaMemcpyAsync(pin->nf, ctx->d_info.p + 2, sizeof pin->nf, cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->n_if = nf[0];
   ctx->n_mort = nf[1];
@@ -1073,6 +1089,7 @@ perk_status perk_create(const perk_problem* prob, perk_ctx** out) {
   device_sm_count();   // cached before any graph capture
   stage_resident_blocks();
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&ctx->h_pin), sizeof(perk_ctx::Pinned)) != cudaSuccess ||
       ctx->d_dt.ensure(1) != cudaSuccess || ctx->d_flag.ensure(1) != cudaSuccess ||
       ctx->d_logtab.ensure(2 * LOG_TABLE_SIZE) != cudaSuccess ||
       ctx->d_counts.ensure(6 * MAX_S) != cudaSuccess || ctx->d_minmax.ensure(2) != cudaSuccess ||
@@ -1098,6 +1115,7 @@ void perk_destroy(perk_ctx* ctx) {
   if (!ctx) return;
   destroy_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -1834,9 +1852,9 @@ perk_status perk_compute_dt_members(perk_ctx* ctx, const double* d_U, double cfl
 
 perk_status perk_check(perk_ctx* ctx) {
   if (!ctx) return PERK_E_INVALID_ARG;
-  int flag = 0;
-  PERK_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaMemcpyAsync(&ctx->h_pin->flag, ctx->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int flag = ctx->h_pin->flag;
   if (flag) {
     PERK_CUDA(ctx, cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), ctx->stream));
     PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1868,9 +1886,10 @@ perk_status perk_compute_dt(perk_ctx* ctx, const double* d_U, double cfl, double
   if (ctx->d_block_min.cap < (size_t)nb) return fail(ctx, PERK_E_INVALID_ARG, "internal: step-size scratch too small");
   PERK_CUDA(ctx, launch_dt(ctx->stream, ctx->n_elem, d_U, ctx->d_level.p, ctx->length, ctx->ops.gamma,
                            ctx->d_block_min.p, nb, ctx->d_dt_out.p));
-  double m = 0.0;
-  PERK_CUDA(ctx, cudaMemcpyAsync(&m, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PERK_CUDA(ctx, cudaMemcpyAsync(&ctx->h_pin->dt, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const double m = ctx->h_pin->dt;
   if (!std::isfinite(m) || !(m > 0.0))
     return fail(ctx, PERK_E_NONFINITE, "a node has no admissible wave speed (rho or p <= 0, or NaN)");
   *dt = cfl * m / (double)NN;
@@ -2275,8 +2294,8 @@ static perk_status adapt_plan_device(perk_ctx* ctx, const perk_amr_params* prm, 
   }
   PERK_CUDA(ctx, launch_amr_plan(st, n, ctx->d_cells.p, eta, a, ctx->n_if, ctx->d_if_raw.p, ctx->n_mort,
                                  ctx->d_mort_raw.p, ctx->d_des.p, ctx->d_off.p, ctx->d_info.p));
-  int64_t info[5];
-  PERK_CUDA(ctx, cudaMemcpyAsync(info, ctx->d_info.p, sizeof info, cudaMemcpyDeviceToHost, st));
+  const int64_t* info = ctx->h_pin->info;
+  PERK_CUDA(ctx, cudaMemcpyAsync(ctx->h_pin->info, ctx->d_info.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   PERK_CUDA(ctx, cudaStreamSynchronize(st));
   if (info[4] != 0) return fail(ctx, PERK_E_CUDA, "AMR balance did not settle within its pass bound");
   ctx->plan_device = true;
