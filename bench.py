@@ -80,9 +80,9 @@ VOL_SLOTS_PER_ELEM = 16 * 60 + 48 * 44 + 16 * 6 * 4 + 128
 # L2 within the launch)
 VOL_DRAM_BYTES_PER_ELEM = 8.077312e6 / 3904
 # DRAM bytes per element-stage of the one-launch stage kernel (face and volume work), measured by
-# ncu on the current kernel (5.943 MB for a fully active stage of the 3,904-cell KH mesh,
-# profiles/k_stage_kelvin_helmholtz_amr_3904cells.md)
-STAGE_DRAM_BYTES_PER_ELEM = 5.943296e6 / 3904
+# ncu on the current kernel: the 16 stage launches of one step of the 3,904-cell KH mesh read
+# 86.87 MB for 55,936 element-stages (profiles/k_stage_kelvin_helmholtz_amr_3904cells.md)
+STAGE_DRAM_BYTES_PER_ELEM = 86.868736e6 / 55936
 
 
 AMR_KH = dict(level_min=4, level_max=7, refine_above=0.1, coarsen_below=0.02)
