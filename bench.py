@@ -640,6 +640,8 @@ def run_perk(args) -> None:
     S = max(wl["E"])
     perk = Run(torch, wl, wl["E"])
     full = Run(torch, wl, [S])
+    # the launch structure of each method's step, chosen by the library's autotuner on this mesh
+    modes = {"perk": perk.solver.autotune_step(perk.U, perk.dt), "full_rk": full.solver.autotune_step(full.U, full.dt)}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(args.warmup):
         perk.step()
@@ -776,7 +778,9 @@ def run_perk(args) -> None:
                                         else (ms - ms_no_amr) / timed_cycles),
                    "amr_share_of_step_time": None if ms_no_amr is None else (ms - ms_no_amr) / ms,
                    "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"{world} independent replica(s)", "graph": True},
+                   "parallelism": f"{world} independent replica(s)", "graph": True,
+                   "launch_structure_autotuned": dict(modes, meaning="perk_set_stage_fusion mode: 0 two launches "
+                                                      "per stage, 1 one per stage, 2 one per step")},
         "full_rk": {"value": value_full, "ms_per_step": ms_full / args.steps,
                     "dof_stage_updates_per_step": units_full / args.steps,
                     "ratio_ms_per_step_full_over_perk": ms_full / ms},
@@ -874,6 +878,7 @@ def run_ensemble(args) -> None:
         return ens.info()["dof_stage_updates"]
 
     epb = ens.autotune(U)          # elements per block of the volume kernel, timed on this mesh
+    mode = ens.autotune_step(U, dts)   # launch structure of the step, timed on this mesh
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -897,7 +902,10 @@ def run_ensemble(args) -> None:
             "config": {"workload": "kelvin_helmholtz_ensemble_64_members", "members": n,
                        "member_dof_initial_min_max": [min(dof_member), max(dof_member)],
                        "n_elem_total": info["n_elem"], "family": [4, 6, 10, 16], "amr_every_steps": 5,
-                       "graph": True, "launches_per_stage": 2, "volume_elems_per_block_autotuned": epb,
+                       "graph": True, "launch_structure_autotuned": mode,
+                       "launch_structure_meaning": "perk_set_stage_fusion mode: 0 two launches per stage, 1 one "
+                                                   "per stage, 2 one per step",
+                       "volume_elems_per_block_autotuned": epb,
                        "l2": "flushed (256 MB write) before every timed step"},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

@@ -356,6 +356,15 @@ perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, c
  * *elems_per_block (may be NULL) receives the choice.  Results do not depend
  * on the choice.  Blocks. */
 perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elems_per_block);
+
+/* Chooses the launch structure of the step for this context and mesh (the modes of
+ * perk_set_stage_fusion: 1 one launch per stage, 2 one launch per step, 0 two launches per
+ * stage; only 0 where the equations or shock capturing allow no fusion): one untimed and five
+ * timed steps from the state d_U (device, U layout; left unchanged) with the step sizes dts
+ * (host, one per ensemble member) in each mode (CUDA events), and the fastest is kept for every
+ * later step.  *mode (may be NULL) receives it.  Results do not depend on the mode.
+ * PERK_E_NOT_READY if a rejected step is pending (perk_check first).  Blocks. */
+perk_status perk_autotune_step(perk_ctx* ctx, const double* d_U, const double* dts, int32_t* mode);
 /* Sets the elements per block of the volume kernel (2, 4 or 8; INVALID_ARG
  * otherwise) without timing. */
 perk_status perk_set_volume_blocks(perk_ctx* ctx, int32_t elems_per_block);

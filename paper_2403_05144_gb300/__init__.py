@@ -399,6 +399,17 @@ class PerkSolver:
         self._call(self.lib.perk_autotune_volume, C.c_void_p(_ptr(U)), C.byref(out))
         return out.value
 
+    def autotune_step(self, U, dt) -> int:
+        """Times whole steps from U (left unchanged) with one launch per stage (1), one launch per
+        step (2) and two launches per stage (0), keeps the fastest and returns it; dt: a step size,
+        or one per ensemble member."""
+        U = self._state(U)
+        dts = np.ascontiguousarray(np.atleast_1d(np.asarray(dt, dtype=np.float64)))
+        out = C.c_int32()
+        self._call(self.lib.perk_autotune_step, C.c_void_p(_ptr(U)), dts.ctypes.data_as(C.POINTER(C.c_double)),
+                   C.byref(out))
+        return out.value
+
     def set_volume_blocks(self, elems_per_block: int):
         self._call(self.lib.perk_set_volume_blocks, C.c_int32(elems_per_block))
 

@@ -91,6 +91,7 @@ SIGNATURES = [
     ("perk_step_store", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     ("perk_step_vjp_stored", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("perk_autotune_volume", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    ("perk_autotune_step", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     ("perk_set_volume_blocks", C.c_int, [C.c_void_p, C.c_int32]),
     ("perk_amr_indicator", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("perk_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(PerkAmrParams), C.POINTER(C.c_int32), C.c_void_p,

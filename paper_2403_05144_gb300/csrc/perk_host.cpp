@@ -2254,6 +2254,70 @@ perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elem
   return PERK_OK;
 }
 
+perk_status perk_autotune_step(perk_ctx* ctx, const double* d_U, const double* dts, int32_t* mode) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!ctx->has_mesh || !ctx->has_tab || !ctx->partitioned || ctx->part_S != ctx->S)
+    return fail(ctx, PERK_E_NOT_READY, "mesh or tableau missing");
+  if (!d_U || !dts) return fail(ctx, PERK_E_INVALID_ARG, "null U or dt");
+  perk_status s = set_dts(ctx, dts, 0.0);
+  if (s != PERK_OK) return s;
+  s = prepare_step(ctx);
+  if (s != PERK_OK) return s;
+  cudaStream_t st = ctx->stream;
+  PERK_CUDA(ctx, cudaMemcpyAsync(&ctx->h_pin->flag, ctx->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PERK_CUDA(ctx, cudaStreamSynchronize(st));
+  if (ctx->h_pin->flag != 0) return fail(ctx, PERK_E_NOT_READY, "a rejected step is pending: call perk_check first");
+  const bool old_stage = ctx->fuse_stage, old_step = ctx->fuse_step;
+  int cand[3], nc = 0;
+  ctx->fuse_stage = true;
+  if (ctx->stage_fused()) {
+    cand[nc++] = 1;
+    ctx->fuse_step = true;
+    if (ctx->step_fused()) cand[nc++] = 2;
+  }
+  cand[nc++] = 0;
+  int best = cand[0];
+  float best_ms = 0.f;
+  cudaError_t err = cudaSuccess;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (nc > 1) {
+    err = cudaEventCreate(&a);
+    if (err == cudaSuccess) err = cudaEventCreate(&b);
+    for (int k = 0; k < nc && err == cudaSuccess; ++k) {
+      ctx->fuse_stage = cand[k] != 0;
+      ctx->fuse_step = cand[k] == 2;
+      // one untimed and five timed steps from the same U: the admissibility flag is raised
+      // before each, so the final update (which still restarts the stage counters and
+      // advances the step count) leaves U unchanged
+      for (int r = 0; r < 6 && err == cudaSuccess; ++r) {
+        err = cudaMemsetAsync(ctx->d_flag.p, 1, sizeof(int), st);
+        if (err == cudaSuccess && r == 1) err = cudaEventRecord(a, st);
+        if (err == cudaSuccess && enqueue_step(ctx, st, const_cast<double*>(d_U)) != PERK_OK) err = cudaErrorUnknown;
+      }
+      if (err == cudaSuccess) err = cudaEventRecord(b, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+      if (err == cudaSuccess && (k == 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = cand[k];
+      }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  ctx->fuse_stage = best != 0;
+  ctx->fuse_step = best == 2;
+  if (ctx->fuse_stage != old_stage || ctx->fuse_step != old_step) drop_graph(ctx);
+  const cudaError_t clear = cudaMemsetAsync(ctx->d_flag.p, 0, sizeof(int), st);
+  const cudaError_t sync = cudaStreamSynchronize(st);
+  PERK_CUDA(ctx, err);
+  PERK_CUDA(ctx, clear);
+  PERK_CUDA(ctx, sync);
+  if (mode) *mode = best;
+  return PERK_OK;
+}
+
 perk_status perk_selftest_math(perk_ctx* ctx, int64_t n, const double* d_x, double* d_out) {
   if (!ctx || !d_x || !d_out || n < 0) return PERK_E_INVALID_ARG;
   PERK_CUDA(ctx, launch_selftest_math(ctx->stream, n, d_x, d_out, ctx->d_logtab.p));

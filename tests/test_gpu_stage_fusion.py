@@ -142,3 +142,25 @@ def test_fused_reverse_stages_bitwise_equal_to_two_launches(flux, stored):
         out.append(r)
     assert torch.isfinite(out[0]).all()
     assert torch.equal(out[0], out[1])
+
+
+def test_step_autotuner_keeps_state_and_results():
+    # the tuner times whole steps from U without changing it; the mode it keeps gives the same
+    # bits as any other mode
+    cells = kh_band_cells(4, 7, 0.03)
+    U0 = torch.from_numpy(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3)).cuda()
+    s = solver(cells, 1)
+    dt = s.compute_dt(U0, 0.7)
+    U = U0.clone()
+    mode = s.autotune_step(U, dt)
+    assert mode in (0, 1, 2)
+    assert torch.equal(U, U0)
+    for _ in range(3):
+        s.step(U, dt)
+    s.check()
+    ref = solver(cells, 0)
+    V = U0.clone()
+    for _ in range(3):
+        ref.step(V, dt)
+    ref.check()
+    assert torch.equal(U, V)
