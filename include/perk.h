@@ -264,8 +264,10 @@ perk_status perk_check(perk_ctx* ctx);
  * pattern: the items of all stages are dealt in stage order from one counter, and an item waits
  * (bounded) for the stage vectors of the elements it reads through per-element progress stamps;
  * a wait that gives up abandons the step, which is then not committed (perk_check reports
- * PERK_E_TIMEOUT).  Results are bitwise the same in every mode.  Other equations and shock
- * capturing always use two launches.  Returns PERK_E_INVALID_ARG for other values. */
+ * PERK_E_TIMEOUT).  Results are bitwise the same in every mode.  For the Navier-Stokes
+ * equations mode 1 puts the inviscid face and volume terms of a stage in one launch (BR1's
+ * launches follow it) and mode 2 acts as mode 1; shock capturing always uses two launches.
+ * Returns PERK_E_INVALID_ARG for other values. */
 perk_status perk_set_stage_fusion(perk_ctx* ctx, int enabled);
 
 /* Step size dt = cfl * min_e h_e / ((N+1) max_nodes(|v1| + |v2| + 2c)) computed

@@ -364,10 +364,9 @@ struct perk_ctx {
   // one launch per stage would be used and the step has at most STEP_MAX_S stages
   bool fuse_step = false;
   DevBuf<unsigned long long> d_ctl, d_stamp, d_prog;   // d_prog: element progress of the one-launch step
-  bool stage_fused() const {
-    return fuse_stage && !viscous() && prob.shock_capturing == PERK_SHOCK_OFF;
-  }
-  bool step_fused() const { return fuse_step && stage_fused() && !pattern_mode && S <= STEP_MAX_S; }
+  // (Navier-Stokes: the inviscid face and volume terms in one launch, BR1's launches after it)
+  bool stage_fused() const { return fuse_stage && prob.shock_capturing == PERK_SHOCK_OFF; }
+  bool step_fused() const { return fuse_step && stage_fused() && !viscous() && !pattern_mode && S <= STEP_MAX_S; }
 
   // graphs of the stage-storing step and of the reverse step, keyed by their arguments (valid
   // flags cleared with the step graph's)
@@ -1022,8 +1021,14 @@ perk_status enqueue_step(perk_ctx* ctx, cudaStream_t st, double* d_U, LaunchTime
       TIMED(ctx, timer, st, 1,
             launch_stage(st, i, ctx->ops, ctx->act_if[i], ctx->d_if_sorted.p, ctx->act_mort[i], ctx->d_mort_sorted.p,
                          ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length,
-                         sa, ctx->d_surf.p, stage_out(i, cur), last ? &chk : nullptr, ctx->d_logtab.p,
+                         sa, ctx->d_surf.p, stage_out(i, cur), (last && !visc) ? &chk : nullptr, ctx->d_logtab.p,
                          ctx->d_ctl.p, ctx->d_stamp.p, ctx->d_flag.p));
+      if (visc)
+        TIMED(ctx, timer, st, 3,
+              launch_br1(st, Y_COMBINE, ctx->ops, ctx->prob.mu, ctx->kappa(), ctx->halo_if[i], ctx->halo_mort[i],
+                         ctx->act_if[i], ctx->act_mort[i], ctx->d_if_sorted.p, ctx->d_mort_sorted.p, ctx->halo_el[i],
+                         ctx->act_el[i], ctx->d_elem_sorted.p, ctx->d_level.p, ctx->d_method.p, 2.0 / ctx->length,
+                         sa, ctx->d_wsurf.p, ctx->d_q.p, ctx->d_vsurf.p, stage_out(i, cur), last ? &chk : nullptr));
       prev = cur;
       continue;
     }

@@ -113,3 +113,31 @@ def test_third_order_steps(equations):
     for _ in range(3):
         want = prkm_step(rhs, want, dt, fam, element_methods(m.cells[:, 0], fam.R))
     assert np.max(np.abs(U.cpu().numpy() - want)) / np.max(np.abs(want)) < 1e-11
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_inviscid_terms_in_one_launch_bitwise_equal(use_graph):
+    # one launch for a stage's inviscid face and volume terms (then BR1's launches) against two:
+    # the same arithmetic, so the same bits; a one-launch step mode falls back for Navier-Stokes
+    from paper_2403_05144_gb300 import PerkSolver
+    cells = kh_band_cells(3, 5, 0.05)
+    U0 = cuda(nodal_state(shear_layer, cells, 0.0, 1.0, X3))
+    out = []
+    for mode in (1, 2, 0):
+        s = PerkSolver(surface_flux="hll", equations="navier_stokes", mu=MU, prandtl=0.72, use_graph=use_graph)
+        s.set_stage_fusion(mode)
+        s.upload_mesh(cells, 0.0, 1.0)
+        s.set_perk2_disk([4, 8, 16])
+        U = U0.clone()
+        dt = s.compute_dt(U, 0.5)
+        for _ in range(3):
+            s.step(U, dt)
+        s.check()
+        out.append(U)
+    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[2])
+    acc = None
+    s = PerkSolver(surface_flux="hll", equations="navier_stokes", mu=MU, prandtl=0.72)
+    s.upload_mesh(cells, 0.0, 1.0)
+    s.set_perk2_disk([4, 8, 16])
+    acc = s.step_profiled(U0.clone(), 1e-4, acc)
+    assert acc.launches[0] == 0 and acc.launches[1] == 16 and acc.launches[3] == 16
