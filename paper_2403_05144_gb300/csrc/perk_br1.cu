@@ -23,12 +23,17 @@
 
 #include "perk.h"
 #include "perk_internal.h"
+#include "perk_devmath.cuh"
 
 namespace perk {
 namespace br1 {
 
 constexpr int FSTRIDE = 128;  // doubles of viscous fluxes per element: [direction][variable][node]
 constexpr int WSTRIDE = 64;   // doubles of face data per element: [face][variable][node]
+// one-warp blocks: 8 interfaces (4 threads each) or 4 mortars (8 threads each) per face block,
+// 2 elements (16 threads each) per element block, so that the few thousand elements of a stage
+// spread over all SMs
+constexpr int BR1_THREADS = 32, BR1_IF = BR1_THREADS / 4, BR1_MORT = BR1_THREADS / 8, BR1_ELEMS = BR1_THREADS / 16;
 
 __device__ __forceinline__ int face_node(int face, int k) {
   return face == 0 ? 4 * k : face == 1 ? 4 * k + 3 : face == 2 ? k : 12 + k;
@@ -38,33 +43,33 @@ template <int YS>
 __device__ __forceinline__ void state(const StageArgs& sa, int64_t e, int m, int node, double y[4]) {
   const int64_t base = e * ELEM + node;
   if (YS == Y_GIVEN) {
-    for (int v = 0; v < 4; ++v) y[v] = sa.Y[base + v * NODES];
+    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.Y + base + v * NODES);
   } else {
     const StageCoef c = sa.coef[m];
     const double dt = sa.dt[sa.member ? sa.member[e] : 0];
-    for (int v = 0; v < 4; ++v) y[v] = sa.U[base + v * NODES];
+    for (int v = 0; v < 4; ++v) y[v] = __ldg(sa.U + base + v * NODES);
     if (__double_as_longlong(c.alpha) != 0)
-      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.alpha, sa.K1[base + v * NODES], y[v]);
+      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.alpha, __ldg(sa.K1 + base + v * NODES), y[v]);
     if (__double_as_longlong(c.beta) != 0) {
       const double* Kp = coupled_stage(sa, c);
-      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, Kp[base + v * NODES], y[v]);
+      for (int v = 0; v < 4; ++v) y[v] = fma(dt * c.beta, __ldg(Kp + base + v * NODES), y[v]);
     }
   }
 }
 
+// the gradient variables (v1, v2, T = p/rho) of a state (1/rho by the Newton-refined reciprocal)
 __device__ __forceinline__ void grad_vars(const double u[4], double gm1, double w[3]) {
-  const double ir = 1.0 / u[0];
+  const double ir = rcp_nr(u[0]);
   w[0] = u[1] * ir;
   w[1] = u[2] * ir;
   const double p = gm1 * (u[3] - 0.5 * (u[1] * w[0] + u[2] * w[1]));
   w[2] = p * ir;
 }
 
-// normal viscous flux (direction dir) from the state and the gradients (dvars/dx, dvars/dy)
-__device__ __forceinline__ void visc_flux(const double u[4], const double qx[3], const double qy[3], int dir,
+// normal viscous flux (direction dir) from the velocities (v1, v2) and the gradients
+// (dvars/dx, dvars/dy)
+__device__ __forceinline__ void visc_flux(double v1, double v2, const double qx[3], const double qy[3], int dir,
                                           double mu, double kappa, double f[4]) {
-  const double ir = 1.0 / u[0];
-  const double v1 = u[1] * ir, v2 = u[2] * ir;
   const double div = qx[0] + qy[1];
   if (dir == 0) {
     const double txx = mu * (2.0 * qx[0] - (2.0 / 3.0) * div);
@@ -86,14 +91,14 @@ __device__ __forceinline__ void visc_flux(const double u[4], const double qx[3],
 
 // ---------------------------------------------------------------------------
 template <int YS, int PHASE>
-__global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs, int64_t n_mort,
+__global__ void __launch_bounds__(BR1_THREADS) k_faces(Ops ops, int64_t n_if, const int4* __restrict__ ifs, int64_t n_mort,
                                                 const int4* __restrict__ morts, int64_t if_blocks,
                                                 const int32_t* __restrict__ method, StageArgs sa,
                                                 const double* __restrict__ q, double mu, double kappa,
                                                 double* __restrict__ out) {
   // PHASE 0: central w* (3 variables); PHASE 1: central viscous flux (4 variables)
   constexpr int NVAR = PHASE == 0 ? 3 : 4;
-  __shared__ double s_half[16][2][4][NN];
+  __shared__ double s_half[BR1_MORT][2][4][NN];
   auto value = [&](int64_t e, int m, int node, int dir, double r[4]) {
     if (PHASE == 0) {
       double u[4];
@@ -101,11 +106,11 @@ __global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4
       grad_vars(u, ops.gm1, r);
     } else {
       // the flux along the face's direction, stored by k_grad
-      for (int v = 0; v < 4; ++v) r[v] = q[e * FSTRIDE + dir * 64 + v * NODES + node];
+      for (int v = 0; v < 4; ++v) r[v] = __ldg(q + e * FSTRIDE + dir * 64 + v * NODES + node);
     }
   };
   if (blockIdx.x < if_blocks) {
-    const int64_t idx = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 2);
+    const int64_t idx = (int64_t)blockIdx.x * BR1_IF + (threadIdx.x >> 2);
     const int k = threadIdx.x & 3;
     if (idx >= n_if) return;
     const int4 r = ifs[idx];
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4
     return;
   }
   const int lm = threadIdx.x >> 3;
-  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * 16 + lm;
+  const int64_t idx = (int64_t)(blockIdx.x - if_blocks) * BR1_MORT + lm;
   const int half = (threadIdx.x >> 2) & 1, k = threadIdx.x & 3;
   const bool valid = idx < n_mort;
   int4 r = valid ? morts[idx] : make_int4(0, 0, 0, 0);
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4
       s_half[lm][half][v][k] = avg;
     }
   }
-  __syncthreads();
+  __syncwarp();
   if (valid) {
     for (int vv = 0; vv < 2; ++vv) {
       const int v = 2 * half + vv;
@@ -164,13 +169,13 @@ __global__ void __launch_bounds__(128) k_faces(Ops ops, int64_t n_if, const int4
 // q = (2/h) [D w + (1/w_N)(w* - w)|_N - (1/w_0)(w* - w)|_0] along x and y, then the viscous
 // fluxes f_v,x and f_v,y at the node, stored in fv[e][direction][variable][node]
 template <int YS>
-__global__ void __launch_bounds__(128) k_grad(Ops ops, int64_t n, const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(BR1_THREADS) k_grad(Ops ops, int64_t n, const int32_t* __restrict__ elems,
                                                const int32_t* __restrict__ level, const int32_t* __restrict__ method,
                                                double two_over_len, StageArgs sa, const double* __restrict__ wsurf,
                                                double mu, double kappa, double* __restrict__ fv) {
-  __shared__ double s_w[8][3][NODES];
+  __shared__ double s_w[BR1_ELEMS][3][NODES];
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
-  const int64_t slot = (int64_t)blockIdx.x * 8 + le;
+  const int64_t slot = (int64_t)blockIdx.x * BR1_ELEMS + le;
   const bool valid = slot < n;
   const int64_t e = valid ? elems[slot] : 0;
   double u[4] = {1.0, 0.0, 0.0, 2.5}, w[3];
@@ -198,8 +203,8 @@ __global__ void __launch_bounds__(128) k_grad(Ops ops, int64_t n, const int32_t*
     qy[v] = s * gy;
   }
   double fx[4], fy[4];
-  visc_flux(u, qx, qy, 0, mu, kappa, fx);
-  visc_flux(u, qx, qy, 1, mu, kappa, fy);
+  visc_flux(w[0], w[1], qx, qy, 0, mu, kappa, fx);
+  visc_flux(w[0], w[1], qx, qy, 1, mu, kappa, fy);
   for (int v = 0; v < 4; ++v) {
     fv[e * FSTRIDE + v * NODES + t] = fx[v];
     fv[e * FSTRIDE + 64 + v * NODES + t] = fy[v];
@@ -208,22 +213,22 @@ __global__ void __launch_bounds__(128) k_grad(Ops ops, int64_t n, const int32_t*
 
 // K += (2/h) [D f_v,x + D f_v,y + lifting of (f* - f_v)] on the active elements
 template <int YS, bool CHECK>
-__global__ void __launch_bounds__(128) k_visc_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
+__global__ void __launch_bounds__(BR1_THREADS) k_visc_volume(Ops ops, int64_t n, const int32_t* __restrict__ elems,
                                                       const int32_t* __restrict__ level,
                                                       const int32_t* __restrict__ method, double two_over_len,
                                                       StageArgs sa, const double* __restrict__ fv,
                                                       const double* __restrict__ vsurf, double* __restrict__ K,
                                                       UpdateArgs ua) {
-  __shared__ double s_f[8][2][4][NODES];
+  __shared__ double s_f[BR1_ELEMS][2][4][NODES];
   const int le = threadIdx.x >> 4, t = threadIdx.x & 15, i = t & 3, j = t >> 2;
-  const int64_t slot = (int64_t)blockIdx.x * 8 + le;
+  const int64_t slot = (int64_t)blockIdx.x * BR1_ELEMS + le;
   const bool valid = slot < n;
   const int64_t e = valid ? elems[slot] : 0;
   double fx[4] = {0.0, 0.0, 0.0, 0.0}, fy[4] = {0.0, 0.0, 0.0, 0.0};
   if (valid) {
     for (int v = 0; v < 4; ++v) {
-      fx[v] = fv[e * FSTRIDE + v * NODES + t];
-      fy[v] = fv[e * FSTRIDE + 64 + v * NODES + t];
+      fx[v] = __ldg(fv + e * FSTRIDE + v * NODES + t);
+      fy[v] = __ldg(fv + e * FSTRIDE + 64 + v * NODES + t);
     }
   }
   for (int v = 0; v < 4; ++v) {
@@ -274,32 +279,32 @@ cudaError_t launch_br1(cudaStream_t st, YSource ysrc, const Ops& ops, double mu,
                        int64_t n_all, int64_t n_act, const int32_t* elems, const int32_t* level, const int32_t* method,
                        double two_over_len, const StageArgs& sa, double* wsurf, double* q, double* vsurf, double* K,
                        const UpdateArgs* check) {
-  const int64_t bi = (n_if_all + 31) / 32, bm = (n_mort_all + 15) / 16;
-  const int64_t bia = (n_if_act + 31) / 32, bma = (n_mort_act + 15) / 16;
+  const int64_t bi = (n_if_all + br1::BR1_IF - 1) / br1::BR1_IF, bm = (n_mort_all + br1::BR1_MORT - 1) / br1::BR1_MORT;
+  const int64_t bia = (n_if_act + br1::BR1_IF - 1) / br1::BR1_IF, bma = (n_mort_act + br1::BR1_MORT - 1) / br1::BR1_MORT;
   UpdateArgs ua{};
   if (check) ua = *check;
   if (ysrc == Y_GIVEN) {
-    if (bi + bm) br1::k_faces<Y_GIVEN, 0><<<(unsigned)(bi + bm), 128, 0, st>>>(ops, n_if_all, ifs, n_mort_all, morts,
+    if (bi + bm) br1::k_faces<Y_GIVEN, 0><<<(unsigned)(bi + bm), br1::BR1_THREADS, 0, st>>>(ops, n_if_all, ifs, n_mort_all, morts,
                                                                                bi, method, sa, q, mu, kappa, wsurf);
-    if (n_all) br1::k_grad<Y_GIVEN><<<(unsigned)((n_all + 7) / 8), 128, 0, st>>>(ops, n_all, elems, level, method,
+    if (n_all) br1::k_grad<Y_GIVEN><<<(unsigned)((n_all + br1::BR1_ELEMS - 1) / br1::BR1_ELEMS), br1::BR1_THREADS, 0, st>>>(ops, n_all, elems, level, method,
                                                                                  two_over_len, sa, wsurf, mu, kappa, q);
-    if (bia + bma) br1::k_faces<Y_GIVEN, 1><<<(unsigned)(bia + bma), 128, 0, st>>>(
+    if (bia + bma) br1::k_faces<Y_GIVEN, 1><<<(unsigned)(bia + bma), br1::BR1_THREADS, 0, st>>>(
         ops, n_if_act, ifs, n_mort_act, morts, bia, method, sa, q, mu, kappa, vsurf);
-    if (n_act) br1::k_visc_volume<Y_GIVEN, false><<<(unsigned)((n_act + 7) / 8), 128, 0, st>>>(
+    if (n_act) br1::k_visc_volume<Y_GIVEN, false><<<(unsigned)((n_act + br1::BR1_ELEMS - 1) / br1::BR1_ELEMS), br1::BR1_THREADS, 0, st>>>(
         ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, K, ua);
   } else {
-    if (bi + bm) br1::k_faces<Y_COMBINE, 0><<<(unsigned)(bi + bm), 128, 0, st>>>(
+    if (bi + bm) br1::k_faces<Y_COMBINE, 0><<<(unsigned)(bi + bm), br1::BR1_THREADS, 0, st>>>(
         ops, n_if_all, ifs, n_mort_all, morts, bi, method, sa, q, mu, kappa, wsurf);
-    if (n_all) br1::k_grad<Y_COMBINE><<<(unsigned)((n_all + 7) / 8), 128, 0, st>>>(ops, n_all, elems, level, method,
+    if (n_all) br1::k_grad<Y_COMBINE><<<(unsigned)((n_all + br1::BR1_ELEMS - 1) / br1::BR1_ELEMS), br1::BR1_THREADS, 0, st>>>(ops, n_all, elems, level, method,
                                                                                    two_over_len, sa, wsurf, mu, kappa, q);
-    if (bia + bma) br1::k_faces<Y_COMBINE, 1><<<(unsigned)(bia + bma), 128, 0, st>>>(
+    if (bia + bma) br1::k_faces<Y_COMBINE, 1><<<(unsigned)(bia + bma), br1::BR1_THREADS, 0, st>>>(
         ops, n_if_act, ifs, n_mort_act, morts, bia, method, sa, q, mu, kappa, vsurf);
     if (n_act) {
       if (check)
-        br1::k_visc_volume<Y_COMBINE, true><<<(unsigned)((n_act + 7) / 8), 128, 0, st>>>(
+        br1::k_visc_volume<Y_COMBINE, true><<<(unsigned)((n_act + br1::BR1_ELEMS - 1) / br1::BR1_ELEMS), br1::BR1_THREADS, 0, st>>>(
             ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, K, ua);
       else
-        br1::k_visc_volume<Y_COMBINE, false><<<(unsigned)((n_act + 7) / 8), 128, 0, st>>>(
+        br1::k_visc_volume<Y_COMBINE, false><<<(unsigned)((n_act + br1::BR1_ELEMS - 1) / br1::BR1_ELEMS), br1::BR1_THREADS, 0, st>>>(
             ops, n_act, elems, level, method, two_over_len, sa, q, vsurf, K, ua);
     }
   }
