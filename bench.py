@@ -169,9 +169,11 @@ class Run:
     def step(self):
         """One step (preceded by an AMR cycle every n_amr steps); returns its DoF-stage updates."""
         if self.wl["amr"] and self.k > 0 and self.k % self.wl["n_amr"] == 0:
-            self.U = self.solver.adapt(self.U, **self.wl["amr"])
+            # the new state's step size comes back with the partition's counts (one wait)
+            self.U = self.solver.adapt(self.U, cfl=self.wl["cfl"], **self.wl["amr"])
             self.amr_cycles += 1
-            self._refresh()
+            self.dt = self.solver.last_dt
+            self.dof = self.solver.info()["dof_stage_updates"]
         self.solver.step(self.U, self.dt)
         self.k += 1
         self.t += self.dt

@@ -413,6 +413,11 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
  * cells); then the mesh is replaced and re-partitioned on the device.  Blocks. */
 perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew);
 
+/* perk_adapt_commit, then the step size of d_Unew on the new mesh for `cfl` (as
+ * perk_compute_dt): on the device path it is computed with the partition's counts and read back
+ * with them, so the call waits once.  PERK_E_NONFINITE as perk_compute_dt.  Blocks. */
+perk_status perk_adapt_commit_dt(perk_ctx* ctx, const double* d_Uold, double* d_Unew, double cfl, double* dt);
+
 /* Host utility (no device work, no context): the balanced levels perk_adapt_plan derives from
  * desired levels for a single mesh: desired[n_cells] (each within one level of its cell's)
  * raised to the least fixed point of the sibling rule (a cell coarsens only with its three

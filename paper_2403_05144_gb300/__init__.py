@@ -423,8 +423,10 @@ class PerkSolver:
         return eta
 
     def adapt(self, U, level_min: int = 4, level_max: int = 7, refine_above: float = 0.1,
-              coarsen_below: float = 0.02, desired=None, indicator: str = "density"):
-        """One AMR cycle: returns the solution on the new mesh (a new tensor)."""
+              coarsen_below: float = 0.02, desired=None, indicator: str = "density", cfl: float | None = None):
+        """One AMR cycle: returns the solution on the new mesh (a new tensor).  With cfl, the step
+        size of the new state (as compute_dt) is computed in the same call and left in
+        ``last_dt``."""
         U = self._state(U)
         prm = _lib.PerkAmrParams(level_min, level_max, refine_above, coarsen_below, self.INDICATORS[indicator])
         n_new = C.c_int64()
@@ -435,7 +437,13 @@ class PerkSolver:
         else:
             self._call(self.lib.perk_adapt_plan, C.byref(prm), None, C.c_void_p(_ptr(U)), C.byref(n_new))
         Unew = self.torch.empty((n_new.value, 4, 4, 4), dtype=self.torch.float64, device="cuda")
-        self._call(self.lib.perk_adapt_commit, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(Unew)))
+        if cfl is None:
+            self._call(self.lib.perk_adapt_commit, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(Unew)))
+        else:
+            dt = C.c_double()
+            self._call(self.lib.perk_adapt_commit_dt, C.c_void_p(_ptr(U)), C.c_void_p(_ptr(Unew)), C.c_double(cfl),
+                       C.byref(dt))
+            self.last_dt = dt.value
         self.n_elem = n_new.value
         self.n_members = getattr(self, "n_members", 1)
         self._cells = None                  # read back from the library when first asked for

@@ -97,6 +97,7 @@ SIGNATURES = [
     ("perk_adapt_plan", C.c_int, [C.c_void_p, C.POINTER(PerkAmrParams), C.POINTER(C.c_int32), C.c_void_p,
                                   C.POINTER(C.c_int64)]),
     ("perk_adapt_commit", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("perk_adapt_commit_dt", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     ("perk_get_cells", C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int64]),
     ("perk_amr_balance", C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("perk_selftest_math", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),

@@ -275,6 +275,9 @@ struct perk_ctx {
     int flag;
   };
   Pinned* h_pin = nullptr;
+  // perk_adapt_commit_dt: the new state whose step size the partition's readback brings along
+  const double* pending_dt_U = nullptr;
+  bool dt_folded = false;
   std::string err;
 
   // mesh (host)
@@ -681,6 +684,15 @@ perk_status run_partition(perk_ctx* ctx, bool device_faces = false) {
                                  ctx->stream));
   if (device_faces)
     PERK_CUDA(ctx, cudaMemcpyAsync(pin->nf, ctx->d_info.p + 2, sizeof pin->nf, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->pending_dt_U) {
+    // the step size of the new state, read back with the counts (one wait for both)
+    const int nb = (int)std::min<int64_t>(DT_MAX_BLOCKS, (ctx->n_elem * NODES + DT_THREADS - 1) / DT_THREADS);
+    if (ctx->d_block_min.cap < (size_t)nb) return fail(ctx, PERK_E_INVALID_ARG, "internal: step-size scratch too small");
+    PERK_CUDA(ctx, launch_dt(ctx->stream, ctx->n_elem, ctx->pending_dt_U, ctx->d_level.p, ctx->length, ctx->ops.gamma,
+                             ctx->d_block_min.p, nb, ctx->d_dt_out.p));
+    PERK_CUDA(ctx, cudaMemcpyAsync(&pin->dt, ctx->d_dt_out.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->dt_folded = true;
+  }
   PERK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->n_if = nf[0];
   ctx->n_mort = nf[1];
@@ -2549,6 +2561,24 @@ static perk_status adapt_commit_device(perk_ctx* ctx, const double* d_Uold, doub
   ctx->host_stale = true;
   ctx->mesh_morton = true;
   return run_partition(ctx, true);
+}
+
+perk_status perk_adapt_commit_dt(perk_ctx* ctx, const double* d_Uold, double* d_Unew, double cfl, double* dt) {
+  if (!ctx) return PERK_E_INVALID_ARG;
+  if (!dt || !(cfl > 0.0)) return fail(ctx, PERK_E_INVALID_ARG, "bad cfl or null dt");
+  ctx->pending_dt_U = d_Unew;
+  ctx->dt_folded = false;
+  const perk_status s = perk_adapt_commit(ctx, d_Uold, d_Unew);
+  const bool folded = ctx->dt_folded;
+  ctx->pending_dt_U = nullptr;
+  ctx->dt_folded = false;
+  if (s != PERK_OK) return s;
+  if (!folded) return perk_compute_dt(ctx, d_Unew, cfl, dt);   // the commit read nothing back
+  const double m = ctx->h_pin->dt;
+  if (!std::isfinite(m) || !(m > 0.0))
+    return fail(ctx, PERK_E_NONFINITE, "a node has no admissible wave speed (rho or p <= 0, or NaN)");
+  *dt = cfl * m / (double)NN;
+  return PERK_OK;
 }
 
 perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew) {

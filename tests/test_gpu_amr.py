@@ -164,3 +164,18 @@ def test_unsorted_upload_is_planned_on_the_host_then_matches_oracle():
         Ug = s.adapt(Ug, desired=raw)
         assert [tuple(c) for c in s.cells.tolist()] == want_cells
         np.testing.assert_allclose(Ug.cpu().numpy(), U, rtol=0, atol=1e-13 * np.max(np.abs(U)))
+
+
+def test_step_size_read_back_with_the_partition():
+    # adapt(..., cfl) computes the new state's step size with the partition's readback: the same
+    # value as compute_dt on the new state, also on a cycle that changes nothing
+    cells = uniform_cells(4)
+    U = cuda(nodal_state(kelvin_helmholtz, cells, -1.0, 2.0, X3))
+    s = solver_for(cells, -1.0, 2.0, "hllc", [4, 6, 10, 16])
+    for cycle in range(3):
+        U = s.adapt(U, cfl=0.7, **AMR)
+        assert s.last_dt == s.compute_dt(U, 0.7), cycle
+    frozen = dict(AMR, refine_above=1e30, coarsen_below=-1.0)   # no cell changes level
+    n = s.info()["n_elem"]
+    U = s.adapt(U, cfl=0.7, **frozen)
+    assert s.info()["n_elem"] == n and s.last_dt == s.compute_dt(U, 0.7)
