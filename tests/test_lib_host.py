@@ -186,3 +186,26 @@ def test_amr_balance_matches_the_oracle(lib, case):
     got = amr_balance(cells, desired)
     want = balance(TreeMesh(np.asarray(cells), 0.0, 1.0), desired)
     assert np.array_equal(got, want)
+
+
+def test_entry_points_refuse_a_null_context(lib):
+    # the calls that drive the launch structure, the adjoint and the AMR cycle check their context
+    # before any CUDA call: a null context is PERK_E_INVALID_ARG, here without a GPU
+    import ctypes as C
+    INVALID = 1
+    out_i, out_d, out_z = C.c_int32(), C.c_double(), C.c_size_t()
+    calls = {
+        "perk_set_stage_fusion": (None, 1),
+        "perk_autotune_step": (None, None, None, C.byref(out_i)),
+        "perk_autotune_volume": (None, None, C.byref(out_i)),
+        "perk_adapt_commit_dt": (None, None, None, C.c_double(0.7), C.byref(out_d)),
+        "perk_adapt_commit": (None, None, None),
+        "perk_step_store": (None, None, C.c_double(1e-3), None),
+        "perk_step_vjp_stored": (None, None, C.c_double(1e-3), None, None, None),
+        "perk_step_vjp": (None, None, C.c_double(1e-3), None, None),
+        "perk_workspace_bytes": (None, C.c_int64(0), C.byref(out_z)),
+        "perk_bind_workspace": (None, None, C.c_size_t(0)),
+        "perk_check": (None,),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == INVALID, name
