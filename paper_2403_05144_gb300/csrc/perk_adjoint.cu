@@ -975,7 +975,7 @@ __device__ __forceinline__ void surface_flux_rev(const double uL[4], const doubl
 
 // Faces: the adjoint weight of every face-node flux (its lifting coefficients times
 // lam on both sides) through the hand-written reverse sweeps.
-// face reverse blocks: 4 threads per interface, 8 per mortar
+// face items of one warp: 4 threads per interface (8 interfaces), 8 per mortar (4 mortars)
 constexpr int FREV_IF = 32 / 4, FREV_MORT = 32 / 8;
 
 // one warp's face item: FREV_IF interfaces (4 lanes each) or FREV_MORT mortars (8 lanes each)
