@@ -441,6 +441,17 @@ def cell_means(U: np.ndarray, w: np.ndarray) -> np.ndarray:
     return 0.25 * np.einsum("evji,j,i->ev", U, w, w)
 
 
+def l1_against_fine(cells, means: np.ndarray, ref_grid: np.ndarray, ref_level: int) -> float:
+    """L1 difference (as a fraction of the domain's area) between the cell averages `means` of the
+    leaves `cells` (level, ix, iy) and the averages over the same squares of `ref_grid`, the cell
+    averages of the uniform level-ref_level mesh indexed [iy, ix]."""
+    err = 0.0
+    for (l, ix, iy), m in zip(np.asarray(cells).tolist(), means):
+        k = 1 << (ref_level - l)
+        err += abs(m - ref_grid[iy * k:(iy + 1) * k, ix * k:(ix + 1) * k].mean()) / (1 << (2 * l))
+    return err
+
+
 def total_error_kh(torch, t_window: float = 0.5, ref_level: int = 8) -> dict:
     """Total (spatial + temporal) density error of the P-ERK family and of full-RK at the
     workload's CFL on the frozen initially adapted KH mesh at t_window, against full-RK on the
@@ -477,10 +488,7 @@ def total_error_kh(torch, t_window: float = 0.5, ref_level: int = 8) -> dict:
     for name, E in (("perk", wl["E"]), ("full_rk", [S])):
         r, n = run(frozen, E, U0)
         means = cell_means(r.U.cpu().numpy(), w)[:, 0]
-        err = 0.0
-        for (l, ix, iy), m in zip(r.solver.cells.tolist(), means):
-            k = 1 << (ref_level - l)
-            err += abs(m - ref_grid[iy * k:(iy + 1) * k, ix * k:(ix + 1) * k].mean()) / (1 << (2 * l))
+        err = l1_against_fine(r.solver.cells, means, ref_grid, ref_level)
         out[name] = {"l1_cell_average_density_error": err, "steps": n, "cfl": wl["cfl"]}
     out["ratio_perk_over_full_rk"] = out["perk"]["l1_cell_average_density_error"] / \
         out["full_rk"]["l1_cell_average_density_error"]
