@@ -359,7 +359,8 @@ perk_status perk_step_vjp_stored(perk_ctx* ctx, const double* d_Un, double dt, c
  * on the choice.  Blocks. */
 perk_status perk_autotune_volume(perk_ctx* ctx, const double* d_U, int32_t* elems_per_block);
 
-/* Chooses the launch structure of the step for this context and mesh (the modes of
+/* Chooses the launch structure of the step for this context and mesh: how the stages of
+ * Eq. PartitionedRKSystem are launched, not what they compute (the modes of
  * perk_set_stage_fusion: 1 one launch per stage, 2 one launch per step, 0 two launches per
  * stage; only 0 where the equations or shock capturing allow no fusion): one untimed and five
  * timed steps from the state d_U (device, U layout; left unchanged) with the step sizes dts
@@ -414,8 +415,9 @@ perk_status perk_adapt_plan(perk_ctx* ctx, const perk_amr_params* prm, const int
 perk_status perk_adapt_commit(perk_ctx* ctx, const double* d_Uold, double* d_Unew);
 
 /* perk_adapt_commit, then the step size of d_Unew on the new mesh for `cfl` (as
- * perk_compute_dt): on the device path it is computed with the partition's counts and read back
- * with them, so the call waits once.  PERK_E_NONFINITE as perk_compute_dt.  Blocks. */
+ * perk_compute_dt, Eq. CFL_DG, Eq. TimestepConstraint): on the device path it is computed with
+ * the partition's counts and read back with them, so the call waits once.  PERK_E_NONFINITE as
+ * perk_compute_dt.  Blocks. */
 perk_status perk_adapt_commit_dt(perk_ctx* ctx, const double* d_Uold, double* d_Unew, double cfl, double* dt);
 
 /* Host utility (no device work, no context): the balanced levels perk_adapt_plan derives from
